@@ -1,0 +1,253 @@
+/*
+ * relcp.h -- C ABI of the GB300 ReLCP library.
+ *
+ * One time step of frictionless contact between smooth, strictly convex rigid
+ * bodies (ellipsoids) by recursive constraint augmentation, following
+ * "Smooth-Rigid-Body Contact as a ReLCP" (arXiv 2506.14097):
+ *
+ *   Algorithm 1 (overdamped recursive augmentation time step) and its
+ *   inertial variant (Eq. relcp_inertial): build single-constraint
+ *   shared-normal signed-distance (SNSD) constraints between near-contacting
+ *   pairs, solve the LCP, move to the trial configuration, evaluate the true
+ *   SNSD of every candidate pair there, append one frozen-normal, pulled-back
+ *   constraint per pair that overlaps by more than eps_NCP (Sec. 3.1.3),
+ *   re-solve, and repeat until the geometric stopping rule
+ *   max overlap <= eps_NCP (Eq. gap_stopping_rule) holds.
+ *
+ * Conventions
+ *   - Arrays are row-major: x is n x 3, q is n x 4 as (s, w1, w2, w3)
+ *     (Hamilton product, R(q) maps body to world), semi-axes n x 3,
+ *     velocities and forces n x 6 as (u, omega) / (f, tau), omega and tau in
+ *     the world frame (Sec. 2.1.1: C = [.., x, s, w, ..], U = [.., u, omega, ..]).
+ *   - Units are the caller's.  A box side of 0 makes that axis open.
+ *   - Every call returns relcp_status; nothing throws across the ABI.  On
+ *     RELCP_ERR_CUDA / RELCP_ERR_INVALID_ARG a message is available from
+ *     relcp_last_error() (per thread, valid until the next failing call).
+ *   - Device-side failures (an LCP that hits its iteration cap, a Newton
+ *     solve that does not converge, a bounded device wait that gives up) set
+ *     a status word that relcp_step reads back and returns; the GPU never
+ *     traps and every wait inside the library is bounded.
+ *   - Ownership: the caller owns every pointer it passes; inputs are copied.
+ *     The context owns all device memory it allocates (stream-ordered, on
+ *     the stream given to relcp_create) and frees it in relcp_destroy.
+ *   - Pointers marked "ptr_kind" may be host (RELCP_PTR_HOST) or device
+ *     (RELCP_PTR_DEVICE) memory; entry points documented as "device" take
+ *     device pointers only.
+ */
+#ifndef RELCP_H
+#define RELCP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum relcp_status {
+    RELCP_OK = 0,
+    RELCP_ERR_INVALID_ARG = 1,      /* bad size, NaN, non-unit quaternion, bad enum */
+    RELCP_ERR_CUDA = 2,             /* a CUDA runtime call failed */
+    RELCP_ERR_CAPACITY = 3,         /* a caller-sized output was too small */
+    RELCP_ERR_NOT_CONVERGED = 4,    /* an LCP stopped at lcp_max_iter above lcp_tol */
+    RELCP_ERR_RECURSION_LIMIT = 5,  /* overlap remained after max_recursion augmentations */
+    RELCP_ERR_NEWTON = 6,           /* an SNSD Newton solve did not converge */
+    RELCP_ERR_TIMEOUT = 7,          /* a bounded device-side wait gave up */
+    RELCP_ERR_STATE = 8             /* call out of order (e.g. step before set_bodies) */
+} relcp_status;
+
+enum { RELCP_INERTIAL = 0, RELCP_OVERDAMPED = 1 };
+enum { RELCP_FP64 = 0, RELCP_MIXED = 1 };
+enum { RELCP_GUESS_COLD = 0, RELCP_GUESS_MLP = 1 };
+enum { RELCP_PTR_HOST = 0, RELCP_PTR_DEVICE = 1 };
+
+/* Time-step parameters (Algorithm 1: Require C^k, F_ext, M, eps_NCP). */
+typedef struct relcp_config {
+    int32_t dynamics;      /* RELCP_INERTIAL (Eq. law_inertia) or RELCP_OVERDAMPED (Eq. law_overdamped) */
+    int32_t precision;     /* RELCP_FP64: every operation FP64.  RELCP_MIXED: FP32 LCP mat-vecs and
+                              SNSD iterations; FP64 SNSD polish, overlap test and LCP residual. */
+    int32_t guess;         /* SNSD Newton start: RELCP_GUESS_COLD or RELCP_GUESS_MLP (needs relcp_load_mlp) */
+    int32_t lcp_max_iter;  /* projected-gradient iteration cap per LCP (> 0) */
+    int32_t max_recursion; /* augmentation cap; 0 gives the single-constraint SNSD-LCP */
+    int32_t n_scenes;      /* 1 (batched scenes are a separate entry point) */
+    double dt;             /* time step (> 0) */
+    double eps_ncp;        /* overlap tolerance eps_NCP (> 0, Eq. gap_stopping_rule) */
+    double box[3];         /* periodic box sides at C^k; 0 = open axis */
+    double skin;           /* candidate pair: centre distance <= R_i + R_j + skin, R = largest semi-axis */
+    double phi_skin;       /* initial constraint set A_0: pairs with Phi(C^k) <= phi_skin */
+    double drag_xi;        /* overdamped drag coefficient xi of Eq. ellipsoid_mobility (> 0) */
+    double density;        /* inertial: mass density (> 0) */
+    double strain_rate;    /* overdamped, fully periodic box only: affine background velocity
+                              strain_rate * (x - box/2); the box scales by (1 + strain_rate dt) per step */
+    double lcp_tol;        /* LCP stop: max_a |min(A_aa gamma_a, g_a)| <= lcp_tol (distance units) */
+    uint64_t seed;         /* reserved for randomised components (MLP training batches) */
+    uint32_t fault_inject; /* host-side fault injection mask, RELCP_FAULT_* (tests) */
+    uint32_t flags;        /* RELCP_FLAG_* */
+} relcp_config;
+
+/* fault injection (host side only; nothing is injected on the GPU) */
+enum {
+    RELCP_FAULT_ROW_CAPACITY = 1u, /* pretend the row buffer is full: the step reports RELCP_ERR_CAPACITY */
+    RELCP_FAULT_LCP_ITERS = 2u     /* run every LCP with a cap of 1 iteration */
+};
+enum {
+    RELCP_FLAG_PHASE_TIMING = 1u   /* record per-phase CUDA-event timings in relcp_step_stats */
+};
+
+#define RELCP_MAX_DEPTH_STATS 64
+
+/* Diagnostics of the last relcp_step call (its last step when nsteps > 1). */
+typedef struct relcp_step_stats {
+    int64_t n_bodies;
+    int64_t n_pairs;            /* candidate pairs at C^k */
+    int64_t n_rows;             /* constraints after the last augmentation */
+    int64_t n_rows0;            /* |A_0| */
+    int32_t depth;              /* augmentations performed (0 = accepted after the first LCP) */
+    int32_t status;             /* relcp_status of the step */
+    int32_t lcp_iters_total;
+    int32_t newton_iters_max;   /* largest SNSD Newton iteration count of the step */
+    int32_t lcp_iters[RELCP_MAX_DEPTH_STATS];        /* per recursion */
+    int32_t rows_per_rec[RELCP_MAX_DEPTH_STATS];     /* constraints solved at each recursion */
+    double lcp_residual;        /* final LCP residual (FP64) */
+    double max_overlap;         /* max_p (-Phi_p)_+ at the accepted configuration (FP64) */
+    double box[3];              /* box sides after the step */
+    double ms_broadphase, ms_snsd, ms_lcp, ms_augment, ms_total; /* only with RELCP_FLAG_PHASE_TIMING */
+    int64_t steps_done;         /* steps since relcp_set_bodies */
+    int32_t guess_used;         /* 1 when the learned SNSD guess seeded the C^k evaluation */
+    int32_t newton_fallbacks;   /* pairs whose learned guess was rejected and re-solved cold */
+    /* kernel-level timing (only with RELCP_FLAG_PHASE_TIMING): CUDA events around
+     * each launch of the persistent LCP kernel and of the SNSD kernel */
+    double ms_lcp_kernel;       /* sum over the step's LCP launches */
+    double lcp_alg_bytes;       /* algorithmic bytes of those launches: per projected-gradient
+                                   iteration 120 B per row + 152 B per body (FP64), 68 B + 104 B (mixed) */
+    double ms_snsd_kernel;      /* sum over the step's SNSD launches */
+    int64_t snsd_evals;         /* pair evaluations in those launches */
+    int32_t lcp_launches;
+    int32_t snsd_launches;
+} relcp_step_stats;
+
+typedef struct relcp_ctx relcp_ctx;
+
+/* Last error message of the calling thread ("" when none). */
+const char* relcp_last_error(void);
+
+/* Number of CUDA kernels this library has launched in this process (all
+ * contexts and stateless calls); lets a caller count the launches of a region. */
+int64_t relcp_kernel_launches(void);
+
+/* Library and device description (sm_103a build, SM count). */
+relcp_status relcp_version(int32_t* major, int32_t* minor, int32_t* sm_count);
+
+/* Create a context on the current CUDA device.  cuda_stream: a cudaStream_t
+ * (NULL = legacy default stream) on which every later call of this context
+ * enqueues its work.  *out receives the context. */
+relcp_status relcp_create(const relcp_config* cfg, void* cuda_stream, relcp_ctx** out);
+
+/* Replace the configuration (dt, tolerances, box, precision ...).  The body
+ * state is kept. */
+relcp_status relcp_set_config(relcp_ctx* ctx, const relcp_config* cfg);
+
+/* Load the body state C^k (and U^k, F_ext).  n >= 0.  scene_offsets must be
+ * NULL (single scene).  x: n x 3; q: n x 4 (normalised on load; |q| must be
+ * within 1e-6 of 1); semi_axes: n x 3 (> 0); vel: n x 6 or NULL (= 0):
+ * inertial, the velocity U^k; overdamped, a background velocity added to
+ * U = M (F_ext + D gamma); f_ext: n x 6 or NULL (= 0).  dt_per_scene must be
+ * NULL.  Periodic positions are wrapped into [0, box).  Resets steps_done. */
+relcp_status relcp_set_bodies(relcp_ctx* ctx, int64_t n, const int32_t* scene_offsets, const double* x,
+                              const double* q, const double* semi_axes, const double* vel,
+                              const double* f_ext, const double* dt_per_scene, int32_t ptr_kind);
+
+/* Advance nsteps >= 1 ReLCP time steps (Algorithm 1 per step).  Returns the
+ * first non-OK status; the state then holds the configuration accepted by
+ * that step (or the last good one for RELCP_ERR_CUDA). */
+relcp_status relcp_step(relcp_ctx* ctx, int32_t nsteps);
+
+/* Copy out the state: x n x 3 (wrapped), q n x 4, vel n x 6 = velocity of
+ * the last step (inertial: U^{k+1}; overdamped: U = U_free + M D gamma).
+ * Any pointer may be NULL.  Synchronises the context stream. */
+relcp_status relcp_get_bodies(relcp_ctx* ctx, double* x, double* q, double* vel, int32_t ptr_kind);
+
+/* Current periodic box sides (they change under strain_rate). */
+relcp_status relcp_get_box(relcp_ctx* ctx, double* box3);
+
+/* Diagnostics of the last step. */
+relcp_status relcp_stats(relcp_ctx* ctx, relcp_step_stats* out);
+
+/* Candidate pairs of the last step (at its C^k), i-major with j ascending:
+ * pairs cap x 2 int32.  *n_out = number of pairs (RELCP_ERR_CAPACITY when it
+ * exceeds cap; nothing is written then).  phi0: SNSD at C^k per pair (cap
+ * doubles) or NULL. */
+relcp_status relcp_get_pairs(relcp_ctx* ctx, int32_t* pairs, double* phi0, int64_t cap, int64_t* n_out,
+                             int32_t ptr_kind);
+
+/* Constraint rows of the last step in creation order (A_0 first, then each
+ * augmentation block in pair order).  ids: cap x 4 int32 = (body a, body b,
+ * recursion index, candidate-pair index); geom: cap x 11 doubles =
+ * (n[3], r_a x n [3], r_b x n [3], offset q, A_aa); gamma: cap doubles (the
+ * final LCP solution).  Any pointer may be NULL. */
+relcp_status relcp_get_rows(relcp_ctx* ctx, int32_t* ids, double* geom, double* gamma, int64_t cap,
+                            int64_t* n_out, int32_t ptr_kind);
+
+/* Contact velocity K D gamma of the last LCP (n x 6; K = M or dt M^-1). */
+relcp_status relcp_get_contact_velocity(relcp_ctx* ctx, double* uc, int32_t ptr_kind);
+
+void relcp_destroy(relcp_ctx* ctx);
+
+/* ------------------------------------------------------------------ */
+/* Stateless entry points: one hot-path step each, on device pointers,  */
+/* enqueued on `stream`.  They allocate their scratch stream-ordered.   */
+/* ------------------------------------------------------------------ */
+
+/* Candidate pairs (near-contacting pairs of Algorithm 1's initialisation):
+ * all i < j with |min_image(x_j - x_i)|^2 <= (rb_i + rb_j + skin)^2, the
+ * squared length summed as ((dx dx + dy dy) + dz dz), every operation
+ * rounded separately (decisions are reproducible bit for bit).
+ * x: n x 3 device; rb: n device; box3: host (0 = open axis).  pairs: device
+ * cap x 2 int32, i-major, j ascending.  *n_out (host) = pair count
+ * (RELCP_ERR_CAPACITY when > cap).  Synchronises `stream`. */
+relcp_status relcp_broadphase(int64_t n, const double* x, const double* rb, const double* box3, double skin,
+                              int32_t* pairs, int64_t cap, int64_t* n_out, void* stream);
+
+/* Shared-normal signed distance (Sec. 2.1.4, n_a = -n_b; y_b - y_a = Phi n)
+ * of every listed pair: Phi = max_{|n|=1} n.d - sqrt(n.P_a n) - sqrt(n.P_b n)
+ * with P = R diag(a^2) R^T and d the minimum-image c_b - c_a, by damped
+ * Newton on the unit sphere.  pairs: npairs x 2 int32 device; x n x 3, q n x 4,
+ * axes n x 3 device; box3 host.  out: npairs x 10 device =
+ * (Phi, n[3], r_a[3] = y_a - c_a, r_b[3] = y_b - c_b).  iters: npairs int32
+ * device or NULL (Newton iterations; negative when not converged).
+ * precision: RELCP_FP64 or RELCP_MIXED.  Returns RELCP_ERR_NEWTON if any
+ * pair did not converge (outputs still written).  Synchronises `stream`. */
+relcp_status relcp_snsd_eval(int64_t npairs, const int32_t* pairs, int64_t n, const double* x, const double* q,
+                             const double* axes, const double* box3, int32_t precision, double* out,
+                             int32_t* iters, void* stream);
+
+/* Result of one LCP solve. */
+typedef struct relcp_lcp_info {
+    int32_t iterations;
+    int32_t status;       /* relcp_status */
+    double residual;      /* max_a |min(A_aa gamma_a, g_a)| at exit (FP64) */
+    int32_t grid_blocks;  /* persistent-kernel CTAs used */
+    int32_t pad;
+} relcp_lcp_info;
+
+/* Matrix-free LCP (Eq. cqpp / Lemma LCP <=> CQP): find gamma >= 0 with
+ *   g = q + c D^T K D gamma >= 0,  gamma . g = 0,
+ * by projected gradient with Barzilai-Borwein steps.  Rows (device):
+ * ia, ib: nrows int32 bodies; geom: nrows x 9 doubles (n, r_a x n, r_b x n),
+ * the row [-n, -(r_a x n), n, (r_b x n)] on the (u, omega) blocks of a, b;
+ * qv: nrows doubles.  K: nbodies x 7 doubles = (k_t, Kr_xx, Kr_yy, Kr_zz,
+ * Kr_xy, Kr_xz, Kr_yz): the body operator diag(k_t I, Kr) (K = M overdamped,
+ * dt M^-1 inertial).  gamma: nrows doubles, in = warm start (>= 0), out =
+ * solution.  uc: nbodies x 6 doubles out = K D gamma.  precision as above.
+ * tol: stop when max_a |min(A_aa gamma_a, g_a)| <= tol.  info: host.
+ * Synchronises `stream`. */
+relcp_status relcp_lcp_solve(int64_t nrows, int64_t nbodies, const int32_t* ia, const int32_t* ib,
+                             const double* geom, const double* qv, const double* K, double c,
+                             int32_t precision, double tol, int32_t max_iter, double* gamma, double* uc,
+                             relcp_lcp_info* info, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RELCP_H */

@@ -1,0 +1,239 @@
+// Broad phase: candidate ("near-contacting", Algorithm 1 initialisation)
+// pairs i < j whose bounding spheres grown by `skin` overlap under the
+// periodic minimum image.
+//
+// Fully periodic boxes with at least three cells per axis use a cell list:
+// cell side >= 2 max(rb) + skin, counting sort of bodies into cells (count,
+// exclusive scan, fill), then one thread per body i scans the 27 neighbour
+// cells for j > i.  Other cases (open axes, small scenes) test all j > i.
+// Either way a first pass counts the pairs of each i, a scan gives each i
+// its output segment, and a second pass writes the segment and sorts it by
+// j, so the list is i-major with j ascending and independent of atomics.
+//
+// The distance test is a fixed sequence of separately rounded FP64
+// operations (no contraction), so the decision is reproducible bit for bit.
+#include "relcp_internal.cuh"
+
+namespace relcp {
+
+namespace {
+
+constexpr int kThreads = 256;
+
+__device__ __forceinline__ bool near_pair(View<3, const double> x, const double* __restrict__ rb, int64_t i,
+                                          int64_t j, double L0, double L1, double L2, double skin) {
+    double dx = min_image(__dsub_rn(x(0, j), x(0, i)), L0);
+    double dy = min_image(__dsub_rn(x(1, j), x(1, i)), L1);
+    double dz = min_image(__dsub_rn(x(2, j), x(2, i)), L2);
+    double d2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+    double s = __dadd_rn(__dadd_rn(rb[i], rb[j]), skin);
+    return d2 <= __dmul_rn(s, s);
+}
+
+__global__ void brute_count(int64_t n, View<3, const double> x, const double* __restrict__ rb, double L0,
+                            double L1, double L2, double skin, int* __restrict__ count) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int c = 0;
+    for (int64_t j = i + 1; j < n; ++j) c += near_pair(x, rb, i, j, L0, L1, L2, skin) ? 1 : 0;
+    count[i] = c;
+}
+
+__global__ void brute_fill(int64_t n, View<3, const double> x, const double* __restrict__ rb, double L0,
+                           double L1, double L2, double skin, const int* __restrict__ off, int* __restrict__ pa,
+                           int* __restrict__ pb) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int o = off[i];
+    for (int64_t j = i + 1; j < n; ++j)
+        if (near_pair(x, rb, i, j, L0, L1, L2, skin)) {
+            pa[o] = (int)i;
+            pb[o] = (int)j;
+            ++o;
+        }
+}
+
+struct Grid {
+    int nc[3];
+    double inv_cs[3];
+    double L[3];
+};
+
+__device__ __forceinline__ int cell_coord(double v, double L, double inv_cs, int nc) {
+    double w = v - L * floor(v / L);  // wrap into [0, L)
+    int c = (int)floor(w * inv_cs);
+    return c < 0 ? 0 : (c >= nc ? nc - 1 : c);
+}
+
+__global__ void cell_assign(int64_t n, View<3, const double> x, Grid g, int* __restrict__ cell_of,
+                            int* __restrict__ cell_count) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int cx = cell_coord(x(0, i), g.L[0], g.inv_cs[0], g.nc[0]);
+    int cy = cell_coord(x(1, i), g.L[1], g.inv_cs[1], g.nc[1]);
+    int cz = cell_coord(x(2, i), g.L[2], g.inv_cs[2], g.nc[2]);
+    int cid = (cz * g.nc[1] + cy) * g.nc[0] + cx;
+    cell_of[i] = cid;
+    atomicAdd(&cell_count[cid], 1);
+}
+
+__global__ void cell_fill(int64_t n, const int* __restrict__ cell_of, const int* __restrict__ cell_start,
+                          int* __restrict__ cursor, int* __restrict__ cell_body) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int cid = cell_of[i];
+    int slot = atomicAdd(&cursor[cid], 1);
+    cell_body[cell_start[cid] + slot] = (int)i;
+}
+
+template <bool FILL>
+__global__ void cell_pairs(int64_t n, View<3, const double> x, const double* __restrict__ rb, Grid g, double skin,
+                           const int* __restrict__ cell_of, const int* __restrict__ cell_start,
+                           const int* __restrict__ cell_body, int* __restrict__ count, const int* __restrict__ off,
+                           int* __restrict__ pa, int* __restrict__ pb) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int cid = cell_of[i];
+    int cx = cid % g.nc[0];
+    int cy = (cid / g.nc[0]) % g.nc[1];
+    int cz = cid / (g.nc[0] * g.nc[1]);
+    int c = 0;
+    int o = FILL ? off[i] : 0;
+    for (int dz = -1; dz <= 1; ++dz) {
+        int z = cz + dz;
+        z = z < 0 ? z + g.nc[2] : (z >= g.nc[2] ? z - g.nc[2] : z);
+        for (int dy = -1; dy <= 1; ++dy) {
+            int y = cy + dy;
+            y = y < 0 ? y + g.nc[1] : (y >= g.nc[1] ? y - g.nc[1] : y);
+            for (int dx = -1; dx <= 1; ++dx) {
+                int xx = cx + dx;
+                xx = xx < 0 ? xx + g.nc[0] : (xx >= g.nc[0] ? xx - g.nc[0] : xx);
+                int nb = (z * g.nc[1] + y) * g.nc[0] + xx;
+                int e = cell_start[nb + 1];
+                for (int k = cell_start[nb]; k < e; ++k) {
+                    int j = cell_body[k];
+                    if (j <= i) continue;
+                    if (near_pair(x, rb, i, j, g.L[0], g.L[1], g.L[2], skin)) {
+                        if (FILL) {
+                            pa[o + c] = (int)i;
+                            pb[o + c] = j;
+                        }
+                        ++c;
+                    }
+                }
+            }
+        }
+    }
+    if (!FILL) {
+        count[i] = c;
+    } else {
+        // insertion sort of this body's segment by j
+        for (int a = 1; a < c; ++a) {
+            int v = pb[o + a];
+            int b = a - 1;
+            while (b >= 0 && pb[o + b] > v) {
+                pb[o + b + 1] = pb[o + b];
+                --b;
+            }
+            pb[o + b + 1] = v;
+        }
+    }
+}
+
+__global__ void max_reduce(int64_t n, const double* __restrict__ v, double* __restrict__ out) {
+    __shared__ double sh[32];
+    double m = 0.0;
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) m = fmax(m, v[i]);
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        m = threadIdx.x < (blockDim.x >> 5) ? sh[threadIdx.x] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+        if (threadIdx.x == 0) *out = m;
+    }
+}
+
+}  // namespace
+
+relcp_status broadphase(int64_t n, View<3, const double> x, const double* rb, const double box[3], double skin,
+                        DBuf<int>& pa, DBuf<int>& pb, int64_t* npairs, BroadphaseScratch& sc, cudaStream_t s) {
+    *npairs = 0;
+    if (n < 2) return RELCP_OK;
+    unsigned nb = (unsigned)((n + kThreads - 1) / kThreads);
+    RELCP_TRY(sc.pair_count.ensure((size_t)n, s));
+    RELCP_TRY(sc.pair_off.ensure((size_t)n + 1, s));
+
+    bool periodic = box[0] > 0 && box[1] > 0 && box[2] > 0;
+    Grid g{};
+    bool use_cells = false;
+    if (periodic && n > 2048) {
+        // largest bounding radius decides the cell side
+        DBuf<double> mx;
+        RELCP_TRY(mx.ensure(1, s));
+        note_launch();
+        max_reduce<<<1, 1024, 0, s>>>(n, rb, mx.p);
+        RELCP_CUDA(cudaGetLastError());
+        double rbmax = 0.0;
+        RELCP_CUDA(cudaMemcpyAsync(&rbmax, mx.p, sizeof(double), cudaMemcpyDeviceToHost, s));
+        RELCP_CUDA(cudaStreamSynchronize(s));
+        mx.release(s);
+        double cut = (2.0 * rbmax + skin) * (1.0 + 1e-9);
+        use_cells = true;
+        int64_t ncells = 1;
+        for (int k = 0; k < 3; ++k) {
+            int nc = (int)floor(box[k] / cut);
+            if (nc < 3) use_cells = false;
+            nc = nc > 1024 ? 1024 : nc;
+            g.nc[k] = nc;
+            g.L[k] = box[k];
+            g.inv_cs[k] = nc / box[k];
+            ncells *= nc > 0 ? nc : 1;
+        }
+        if (use_cells) {
+            RELCP_TRY(sc.cell_of.ensure((size_t)n, s));
+            RELCP_TRY(sc.cell_count.ensure((size_t)ncells, s));
+            RELCP_TRY(sc.cell_cursor.ensure((size_t)ncells, s));
+            RELCP_TRY(sc.cell_start.ensure((size_t)ncells + 1, s));
+            RELCP_TRY(sc.cell_body.ensure((size_t)n, s));
+            RELCP_CUDA(cudaMemsetAsync(sc.cell_count.p, 0, ncells * sizeof(int), s));
+            RELCP_CUDA(cudaMemsetAsync(sc.cell_cursor.p, 0, ncells * sizeof(int), s));
+            note_launch();
+            cell_assign<<<nb, kThreads, 0, s>>>(n, x, g, sc.cell_of.p, sc.cell_count.p);
+            RELCP_CUDA(cudaGetLastError());
+            RELCP_TRY(exclusive_scan(sc.cell_count.p, sc.cell_start.p, ncells, sc.scan, s));
+            note_launch();
+            cell_fill<<<nb, kThreads, 0, s>>>(n, sc.cell_of.p, sc.cell_start.p, sc.cell_cursor.p, sc.cell_body.p);
+            RELCP_CUDA(cudaGetLastError());
+            note_launch();
+            cell_pairs<false><<<nb, kThreads, 0, s>>>(n, x, rb, g, skin, sc.cell_of.p, sc.cell_start.p,
+                                                       sc.cell_body.p, sc.pair_count.p, nullptr, nullptr, nullptr);
+            RELCP_CUDA(cudaGetLastError());
+        }
+    }
+    if (!use_cells) {
+        note_launch();
+        brute_count<<<nb, kThreads, 0, s>>>(n, x, rb, box[0], box[1], box[2], skin, sc.pair_count.p);
+        RELCP_CUDA(cudaGetLastError());
+    }
+    RELCP_TRY(exclusive_scan(sc.pair_count.p, sc.pair_off.p, n, sc.scan, s));
+    int total = 0;
+    RELCP_CUDA(cudaMemcpyAsync(&total, sc.pair_off.p + n, sizeof(int), cudaMemcpyDeviceToHost, s));
+    RELCP_CUDA(cudaStreamSynchronize(s));
+    *npairs = total;
+    if (total == 0) return RELCP_OK;
+    RELCP_TRY(pa.ensure((size_t)total, s));
+    RELCP_TRY(pb.ensure((size_t)total, s));
+    if (use_cells) {
+        note_launch();
+        cell_pairs<true><<<nb, kThreads, 0, s>>>(n, x, rb, g, skin, sc.cell_of.p, sc.cell_start.p, sc.cell_body.p,
+                                                  nullptr, sc.pair_off.p, pa.p, pb.p);
+    } else {
+        note_launch();
+        brute_fill<<<nb, kThreads, 0, s>>>(n, x, rb, box[0], box[1], box[2], skin, sc.pair_off.p, pa.p, pb.p);
+    }
+    RELCP_CUDA(cudaGetLastError());
+    return RELCP_OK;
+}
+
+}  // namespace relcp

@@ -1,0 +1,309 @@
+// Shared-normal signed distance (SNSD) of ellipsoid pairs, one thread per pair.
+//
+// For a unit direction n (from body a to body b) the gap between the two
+// support slabs is
+//     G(n) = n.d - sqrt(n.Pa n) - sqrt(n.Pb n),   d = c_b - c_a (minimum image),
+// with Pa = R_a diag(a^2) R_a^T.  Its gradient is y_b(n) - y_a(n) (support
+// points y_a = c_a + Pa n/|.|, y_b = c_b - Pb n/|.|), so a stationary point on
+// the sphere is a pair of surface points with opposite normals whose
+// difference is parallel to n -- the shared-normal points of Sec. 2.1.4, with
+// y_b - y_a = Phi n as in the interior tangent-ball lemma -- and the signed
+// distance is Phi = max_n G(n) (distance when separated, minus the
+// penetration depth when overlapping).
+//
+// Newton ascent on the sphere: tangent-plane gradient and Hessian
+// (G is 1-homogeneous, so the Riemannian Hessian is T^T H T - G I), shifted
+// to be negative definite when it is not, with step halving until G does not
+// fall.  Start: a supplied normal (warm start from an earlier evaluation or the
+// learned guess) or the best of four seeds d, Pa^-1 d, Pb^-1 d,
+// (Pa + Pb)^-1 d.  The mixed path iterates in FP32 and finishes with FP64
+// Newton steps (the polish); the plain path is FP64 throughout.
+#include "relcp_internal.cuh"
+
+namespace relcp {
+
+namespace {
+
+constexpr int kThreads = 128;
+
+template <class T>
+struct Tol;
+template <>
+struct Tol<double> {
+    static constexpr double grad = 1e-13;   // tangent-gradient stop, x (1 + |d|)
+    static constexpr double drop = 1e-15;   // admissible G decrease per step from rounding
+    static constexpr double kappa = 1e-6;
+};
+template <>
+struct Tol<float> {
+    static constexpr float grad = 2e-6f;
+    static constexpr float drop = 1e-6f;
+    static constexpr float kappa = 1e-4f;
+};
+
+template <class T>
+__device__ __forceinline__ T g_value(const T* n, const T* d, const Sym3<T>& Pa, const Sym3<T>& Pb) {
+    T va[3], vb[3];
+    symv(Pa, n, va);
+    symv(Pb, n, vb);
+    return dot3(n, d) - sqrt(dot3(n, va)) - sqrt(dot3(n, vb));
+}
+
+template <class T>
+__device__ __forceinline__ void normalize3(T* v) {
+    T l = sqrt(dot3(v, v));
+    v[0] /= l;
+    v[1] /= l;
+    v[2] /= l;
+}
+
+template <class T>
+__device__ __forceinline__ void tangent_basis(const T* n, T* t1, T* t2) {
+    T ax = fabs(n[0]), ay = fabs(n[1]), az = fabs(n[2]);
+    T e0 = 0, e1 = 0, e2 = 0;
+    if (ax <= ay && ax <= az) e0 = 1;
+    else if (ay <= az) e1 = 1;
+    else e2 = 1;
+    T en = e0 * n[0] + e1 * n[1] + e2 * n[2];
+    t1[0] = e0 - en * n[0];
+    t1[1] = e1 - en * n[1];
+    t1[2] = e2 - en * n[2];
+    normalize3(t1);
+    cross3(n, t1, t2);
+}
+
+// adj(P) v  (P symmetric positive definite: same direction as P^-1 v)
+template <class T>
+__device__ __forceinline__ void adj_solve(const Sym3<T>& P, const T* v, T* o) {
+    T A00 = P.yy * P.zz - P.yz * P.yz, A11 = P.xx * P.zz - P.xz * P.xz, A22 = P.xx * P.yy - P.xy * P.xy;
+    T A01 = P.xz * P.yz - P.xy * P.zz, A02 = P.xy * P.yz - P.yy * P.xz, A12 = P.xy * P.xz - P.xx * P.yz;
+    o[0] = A00 * v[0] + A01 * v[1] + A02 * v[2];
+    o[1] = A01 * v[0] + A11 * v[1] + A12 * v[2];
+    o[2] = A02 * v[0] + A12 * v[1] + A22 * v[2];
+}
+
+template <class T>
+__device__ void cold_start(const T* d, const Sym3<T>& Pa, const Sym3<T>& Pb, T* n) {
+    T cand[4][3];
+    T l = sqrt(dot3(d, d));
+    if (!(l > 0)) {
+        n[0] = 1;
+        n[1] = 0;
+        n[2] = 0;
+        return;
+    }
+    for (int k = 0; k < 3; ++k) cand[0][k] = d[k] / l;
+    adj_solve(Pa, d, cand[1]);
+    adj_solve(Pb, d, cand[2]);
+    Sym3<T> S{Pa.xx + Pb.xx, Pa.yy + Pb.yy, Pa.zz + Pb.zz, Pa.xy + Pb.xy, Pa.xz + Pb.xz, Pa.yz + Pb.yz};
+    adj_solve(S, d, cand[3]);
+    T best = -INFINITY;
+    int arg = 0;
+    for (int c = 0; c < 4; ++c) {
+        T lc = sqrt(dot3(cand[c], cand[c]));
+        if (!(lc > 0)) continue;
+        for (int k = 0; k < 3; ++k) cand[c][k] /= lc;
+        T g = g_value(cand[c], d, Pa, Pb);
+        if (g > best) {
+            best = g;
+            arg = c;
+        }
+    }
+    for (int k = 0; k < 3; ++k) n[k] = cand[arg][k];
+}
+
+// Newton ascent of G on the unit sphere from n (updated in place).
+// Returns the iteration count when the tangent gradient falls to tol, or
+// -(count+1) otherwise.  *Gout = G at the returned n.
+template <class T>
+__device__ int newton_sphere(T* n, const T* d, const Sym3<T>& Pa, const Sym3<T>& Pb, T scale, int maxit, T* Gout) {
+    const T tol = Tol<T>::grad * scale;
+    const T gfloor = Tol<T>::drop * scale;
+    const T kappa = Tol<T>::kappa * scale;
+    T G = 0;
+    int it;
+    for (it = 0; it < maxit; ++it) {
+        T va[3], vb[3];
+        symv(Pa, n, va);
+        symv(Pb, n, vb);
+        T sa = sqrt(dot3(n, va)), sb = sqrt(dot3(n, vb));
+        G = dot3(n, d) - sa - sb;
+        T t1[3], t2[3];
+        tangent_basis(n, t1, t2);
+        T Pa1[3], Pa2[3], Pb1[3], Pb2[3];
+        symv(Pa, t1, Pa1);
+        symv(Pa, t2, Pa2);
+        symv(Pb, t1, Pb1);
+        symv(Pb, t2, Pb2);
+        T ia = T(1) / sa, ib = T(1) / sb;
+        T a1 = dot3(n, Pa1), a2 = dot3(n, Pa2);
+        T b1 = dot3(n, Pb1), b2 = dot3(n, Pb2);
+        T g1 = dot3(t1, d) - a1 * ia - b1 * ib;
+        T g2 = dot3(t2, d) - a2 * ia - b2 * ib;
+        T gn = sqrt(g1 * g1 + g2 * g2);
+        if (gn <= tol) {
+            *Gout = G;
+            return it;
+        }
+        T ia3 = ia * ia * ia, ib3 = ib * ib * ib;
+        T h11 = -(dot3(t1, Pa1) * ia - a1 * a1 * ia3) - (dot3(t1, Pb1) * ib - b1 * b1 * ib3) - G;
+        T h22 = -(dot3(t2, Pa2) * ia - a2 * a2 * ia3) - (dot3(t2, Pb2) * ib - b2 * b2 * ib3) - G;
+        T h12 = -(dot3(t1, Pa2) * ia - a1 * a2 * ia3) - (dot3(t1, Pb2) * ib - b1 * b2 * ib3);
+        T tr = T(0.5) * (h11 + h22), df = T(0.5) * (h11 - h22);
+        T lmax = tr + sqrt(df * df + h12 * h12);
+        if (lmax > -kappa) {
+            T sh = lmax + kappa;
+            h11 -= sh;
+            h22 -= sh;
+        }
+        T det = h11 * h22 - h12 * h12;
+        T d1 = -(h22 * g1 - h12 * g2) / det;
+        T d2 = -(-h12 * g1 + h11 * g2) / det;
+        T step = 1;
+        bool acc = false;
+        for (int bt = 0; bt < 40; ++bt) {
+            T m[3];
+            for (int k = 0; k < 3; ++k) m[k] = n[k] + step * (d1 * t1[k] + d2 * t2[k]);
+            normalize3(m);
+            T Gm = g_value(m, d, Pa, Pb);
+            if (Gm >= G - gfloor) {
+                n[0] = m[0];
+                n[1] = m[1];
+                n[2] = m[2];
+                acc = true;
+                break;
+            }
+            step *= T(0.5);
+        }
+        if (!acc) break;
+    }
+    *Gout = G;
+    return -(it + 1);
+}
+
+__device__ __forceinline__ Sym3<double> load_P(View<6, const double> P, int64_t i) {
+    return Sym3<double>{P(0, i), P(1, i), P(2, i), P(3, i), P(4, i), P(5, i)};
+}
+
+__global__ void __launch_bounds__(kThreads) snsd_kernel(SnsdArgs a) {
+    int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    double maxov = 0.0;
+    if (p < a.npairs) {
+        int i = a.pa[p * a.pstride];
+        int j = a.pb[p * a.pstride];
+        double d[3];
+        for (int k = 0; k < 3; ++k) d[k] = min_image(a.x(k, j) - a.x(k, i), a.box[k]);
+        Sym3<double> Pa = load_P(a.P, i), Pb = load_P(a.P, j);
+        double scale = 1.0 + sqrt(dot3(d, d));
+        double n[3];
+        int iters = 0;
+        bool have = false;
+        if (a.guess.c[0]) {
+            n[0] = a.guess(0, p);
+            n[1] = a.guess(1, p);
+            n[2] = a.guess(2, p);
+            double l = sqrt(dot3(n, n));
+            if (l > 0.5 && l < 2.0) {
+                normalize3(n);
+                have = true;
+            }
+        }
+        double G = 0.0;
+        int r;
+        if (a.mixed) {
+            float df[3] = {(float)d[0], (float)d[1], (float)d[2]};
+            Sym3<float> Pfa{(float)Pa.xx, (float)Pa.yy, (float)Pa.zz, (float)Pa.xy, (float)Pa.xz, (float)Pa.yz};
+            Sym3<float> Pfb{(float)Pb.xx, (float)Pb.yy, (float)Pb.zz, (float)Pb.xy, (float)Pb.xz, (float)Pb.yz};
+            float nf[3];
+            if (have) {
+                nf[0] = (float)n[0];
+                nf[1] = (float)n[1];
+                nf[2] = (float)n[2];
+            } else {
+                cold_start(df, Pfa, Pfb, nf);
+            }
+            float Gf;
+            int rf = newton_sphere(nf, df, Pfa, Pfb, (float)scale, 30, &Gf);
+            iters = rf >= 0 ? rf : -rf;
+            n[0] = nf[0];
+            n[1] = nf[1];
+            n[2] = nf[2];
+            normalize3(n);
+            // FP64 polish (full FP64 Newton when the FP32 phase failed)
+            r = newton_sphere(n, d, Pa, Pb, scale, rf >= 0 ? 4 : 50, &G);
+        } else {
+            if (!have) cold_start(d, Pa, Pb, n);
+            r = newton_sphere(n, d, Pa, Pb, scale, 50, &G);
+        }
+        if (r < 0) {
+            atomicOr(a.status, DEV_NEWTON);
+            iters = -(iters + (-r));
+        } else {
+            iters += r;
+        }
+        double va[3], vb[3];
+        symv(Pa, n, va);
+        symv(Pb, n, vb);
+        double sa = sqrt(dot3(n, va)), sb = sqrt(dot3(n, vb));
+        a.out.phi[p * a.out.phi_s] = G;
+        for (int k = 0; k < 3; ++k) {
+            a.out.n(k, p) = n[k];
+            a.out.ra(k, p) = va[k] / sa;
+            a.out.rb(k, p) = -vb[k] / sb;
+        }
+        if (a.out.iters) a.out.iters[p] = iters;
+        if (a.viol) a.viol[p] = (G < -a.eps) ? 1 : 0;
+        maxov = G < 0.0 ? -G : 0.0;
+    }
+    if (a.block_maxov) {
+        __shared__ double sh[kThreads / 32];
+        for (int o = 16; o > 0; o >>= 1) maxov = fmax(maxov, __shfl_xor_sync(0xffffffffu, maxov, o));
+        if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = maxov;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double m = 0.0;
+            for (int w = 0; w < kThreads / 32; ++w) m = fmax(m, sh[w]);
+            a.block_maxov[blockIdx.x] = m;
+        }
+    }
+}
+
+__global__ void shape_kernel(int64_t n, View<4, const double> q, View<3, const double> axes, View<6, double> P) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double s = q(0, i), x = q(1, i), y = q(2, i), z = q(3, i);
+    double l = sqrt(s * s + x * x + y * y + z * z);
+    double R[9];
+    quat_to_R(s / l, x / l, y / l, z / l, R);
+    double a0 = axes(0, i), a1 = axes(1, i), a2 = axes(2, i);
+    Sym3<double> S = rot_diag_rot(R, a0 * a0, a1 * a1, a2 * a2);
+    P(0, i) = S.xx;
+    P(1, i) = S.yy;
+    P(2, i) = S.zz;
+    P(3, i) = S.xy;
+    P(4, i) = S.xz;
+    P(5, i) = S.yz;
+}
+
+}  // namespace
+
+relcp_status snsd_launch(const SnsdArgs& a, int* nblocks_out, cudaStream_t s) {
+    unsigned nb = (unsigned)((a.npairs + kThreads - 1) / kThreads);
+    if (nblocks_out) *nblocks_out = (int)nb;
+    if (a.npairs == 0) return RELCP_OK;
+    note_launch();
+    snsd_kernel<<<nb, kThreads, 0, s>>>(a);
+    RELCP_CUDA(cudaGetLastError());
+    return RELCP_OK;
+}
+
+relcp_status shape_launch(int64_t n, View<4, const double> q, View<3, const double> axes, View<6, double> P,
+                          cudaStream_t s) {
+    if (n == 0) return RELCP_OK;
+    note_launch();
+    shape_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, q, axes, P);
+    RELCP_CUDA(cudaGetLastError());
+    return RELCP_OK;
+}
+
+}  // namespace relcp

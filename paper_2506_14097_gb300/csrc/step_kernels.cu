@@ -1,0 +1,314 @@
+// Per-body and per-row kernels of one ReLCP time step (Algorithm 1).
+//
+//   prep      : normalised q, shape matrix P = R diag(a^2) R^T, the body
+//               operator K (overdamped: the local-drag mobility of Eq.
+//               ellipsoid_mobility, (1/xi) diag(I/L, 12 I/L^3), L = twice the
+//               largest semi-axis; inertial: dt M^-1 with m = 4/3 pi abc rho
+//               and I_body = m/5 (b^2+c^2, a^2+c^2, a^2+b^2), rotated to the
+//               world frame at C^k), bounding radius, and
+//               U_free = vel + K F_ext (+ the affine background velocity).
+//   rows      : one constraint row per flagged pair, written at position
+//               base + exclusive-scan(flags): the Jacobian row
+//               [-n, -(r_a x n), n, (r_b x n)] (Appendix, proof of the
+//               stopping rule), its diagonal A_aa = c d^T K d and its offset:
+//                 A_0 rows       q = Phi(C^k) + c d^T U_free      (Eq. relcp, n = 0)
+//                 appended rows  q = Phi(C_n) - c d^T K D gamma_{n-1}
+//               (the pull-back of Sec. 3.1.3: retained rows keep their q).
+//   trial     : C_{n+1} = C^k + dt G^k (U_free + K D gamma_n), the telescoped
+//               trial configuration of Eq. relcp; q normalised.
+//   accept    : C^{k+1} = the last trial, positions wrapped into the box.
+#include "relcp_internal.cuh"
+#include "step_kernels.cuh"
+
+namespace relcp {
+
+namespace {
+
+constexpr int kT = 256;
+inline unsigned nb(int64_t n) { return (unsigned)((n + kT - 1) / kT); }
+
+__global__ void prep_kernel(PrepArgs a) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= a.n) return;
+    double s = a.q[i], x = a.q[a.n + i], y = a.q[2 * a.n + i], z = a.q[3 * a.n + i];
+    double l = sqrt(s * s + x * x + y * y + z * z);
+    s /= l;
+    x /= l;
+    y /= l;
+    z /= l;
+    a.q[i] = s;
+    a.q[a.n + i] = x;
+    a.q[2 * a.n + i] = y;
+    a.q[3 * a.n + i] = z;
+    double R[9];
+    quat_to_R(s, x, y, z, R);
+    double a0 = a.axes[i], a1 = a.axes[a.n + i], a2 = a.axes[2 * a.n + i];
+    Sym3<double> P = rot_diag_rot(R, a0 * a0, a1 * a1, a2 * a2);
+    a.P[i] = P.xx;
+    a.P[a.n + i] = P.yy;
+    a.P[2 * a.n + i] = P.zz;
+    a.P[3 * a.n + i] = P.xy;
+    a.P[4 * a.n + i] = P.xz;
+    a.P[5 * a.n + i] = P.yz;
+    double amax = fmax(a0, fmax(a1, a2));
+    a.rb[i] = amax;
+    double kt;
+    Sym3<double> Kr;
+    if (a.dynamics == RELCP_OVERDAMPED) {
+        double L = 2.0 * amax;
+        kt = 1.0 / (a.drag_xi * L);
+        double kr = 12.0 / (a.drag_xi * L * L * L);
+        Kr = Sym3<double>{kr, kr, kr, 0.0, 0.0, 0.0};
+    } else {
+        const double pi = 3.14159265358979323846;
+        double m = a.density * 4.0 / 3.0 * pi * a0 * a1 * a2;
+        double I0 = m / 5.0 * (a1 * a1 + a2 * a2), I1 = m / 5.0 * (a0 * a0 + a2 * a2), I2 = m / 5.0 * (a0 * a0 + a1 * a1);
+        kt = a.dt / m;
+        Kr = rot_diag_rot(R, a.dt / I0, a.dt / I1, a.dt / I2);
+    }
+    a.K[i] = kt;
+    a.K[a.n + i] = Kr.xx;
+    a.K[2 * a.n + i] = Kr.yy;
+    a.K[3 * a.n + i] = Kr.zz;
+    a.K[4 * a.n + i] = Kr.xy;
+    a.K[5 * a.n + i] = Kr.xz;
+    a.K[6 * a.n + i] = Kr.yz;
+    // U_free = vel + K F_ext (+ affine background velocity)
+    double f[6], u[6];
+    for (int k = 0; k < 6; ++k) {
+        f[k] = a.fext[k * a.n + i];
+        u[k] = a.vel[k * a.n + i];
+    }
+    u[0] += kt * f[0];
+    u[1] += kt * f[1];
+    u[2] += kt * f[2];
+    u[3] += Kr.xx * f[3] + Kr.xy * f[4] + Kr.xz * f[5];
+    u[4] += Kr.xy * f[3] + Kr.yy * f[4] + Kr.yz * f[5];
+    u[5] += Kr.xz * f[3] + Kr.yz * f[4] + Kr.zz * f[5];
+    if (a.strain_rate != 0.0)
+        for (int k = 0; k < 3; ++k)
+            if (a.box[k] > 0.0) u[k] += a.strain_rate * (a.x[k * a.n + i] - 0.5 * a.box[k]);
+    for (int k = 0; k < 6; ++k) a.ufree[k * a.n + i] = u[k];
+}
+
+__global__ void flag_le_kernel(int64_t np, const double* __restrict__ phi, double thr, int* __restrict__ flags) {
+    int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p < np) flags[p] = phi[p] <= thr ? 1 : 0;
+}
+
+__device__ __forceinline__ double body_rate(const double* U, int64_t n, int i, int j, const double* nn,
+                                            const double* ta, const double* tb) {
+    double r = 0.0;
+    for (int k = 0; k < 3; ++k) r += nn[k] * (U[k * n + j] - U[k * n + i]);
+    for (int k = 0; k < 3; ++k) r += tb[k] * U[(3 + k) * n + j] - ta[k] * U[(3 + k) * n + i];
+    return r;
+}
+
+__global__ void rows_kernel(RowsArgs a) {
+    int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= a.npairs || !a.flags[p]) return;
+    int64_t r = a.base + a.scan[p];
+    if (r >= a.cap) {
+        atomicOr(a.status, DEV_CAPACITY);
+        return;
+    }
+    int i = a.pa[p], j = a.pb[p];
+    const int64_t P = a.npairs;
+    double nn[3], ra[3], rb[3], ta[3], tb[3];
+    for (int k = 0; k < 3; ++k) {
+        nn[k] = a.snsd[(1 + k) * P + p];
+        ra[k] = a.snsd[(4 + k) * P + p];
+        rb[k] = a.snsd[(7 + k) * P + p];
+    }
+    double phi = a.snsd[p];
+    cross3(ra, nn, ta);
+    cross3(rb, nn, tb);
+    const int64_t C = a.cap;
+    a.ia[r] = i;
+    a.ib[r] = j;
+    a.rec[r] = a.rec_index;
+    a.pair[r] = (int)p;
+    for (int k = 0; k < 3; ++k) {
+        a.geom[k * C + r] = nn[k];
+        a.geom[(3 + k) * C + r] = ta[k];
+        a.geom[(6 + k) * C + r] = tb[k];
+    }
+    // offset
+    double qv;
+    if (a.rec_index == 0) {
+        double rate = body_rate(a.ufree, a.nbodies, i, j, nn, ta, tb);
+        if (a.strain_rate != 0.0) {
+            double corr = 0.0;
+            for (int k = 0; k < 3; ++k) {
+                double raw = a.x[k * a.nbodies + j] - a.x[k * a.nbodies + i];
+                corr += nn[k] * (min_image(raw, a.box[k]) - raw);
+            }
+            rate += a.strain_rate * corr;
+        }
+        qv = phi + a.c * rate;
+    } else {
+        qv = phi - a.c * body_rate(a.uc, a.nbodies, i, j, nn, ta, tb);
+    }
+    a.q[r] = qv;
+    // diagonal c d^T K d
+    double acc = (a.K[i] + a.K[j]) * (nn[0] * nn[0] + nn[1] * nn[1] + nn[2] * nn[2]);
+    for (int side = 0; side < 2; ++side) {
+        int b = side ? j : i;
+        const double* t = side ? tb : ta;
+        const int64_t n = a.nbodies;
+        double kxx = a.K[n + b], kyy = a.K[2 * n + b], kzz = a.K[3 * n + b];
+        double kxy = a.K[4 * n + b], kxz = a.K[5 * n + b], kyz = a.K[6 * n + b];
+        acc += t[0] * (kxx * t[0] + kxy * t[1] + kxz * t[2]) + t[1] * (kxy * t[0] + kyy * t[1] + kyz * t[2]) +
+               t[2] * (kxz * t[0] + kyz * t[1] + kzz * t[2]);
+    }
+    a.diag[r] = a.c * acc;
+    a.gamma[r] = 0.0;
+}
+
+__global__ void trial_kernel(TrialArgs a) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= a.n) return;
+    const int64_t n = a.n;
+    double U[6];
+    for (int k = 0; k < 6; ++k) {
+        U[k] = a.ufree[k * n + i] + a.uc[k * n + i];
+        a.ustep[k * n + i] = U[k];
+    }
+    for (int k = 0; k < 3; ++k) a.xt[k * n + i] = a.x[k * n + i] + a.dt * U[k];
+    double s = a.q[i], x = a.q[n + i], y = a.q[2 * n + i], z = a.q[3 * n + i];
+    // q + dt/2 (0, w) (x) q
+    double h = 0.5 * a.dt;
+    double w0 = U[3], w1 = U[4], w2 = U[5];
+    double ns = s - h * (w0 * x + w1 * y + w2 * z);
+    double nx = x + h * (s * w0 + (w1 * z - w2 * y));
+    double ny = y + h * (s * w1 + (w2 * x - w0 * z));
+    double nz = z + h * (s * w2 + (w0 * y - w1 * x));
+    double l = sqrt(ns * ns + nx * nx + ny * ny + nz * nz);
+    ns /= l;
+    nx /= l;
+    ny /= l;
+    nz /= l;
+    a.qt[i] = ns;
+    a.qt[n + i] = nx;
+    a.qt[2 * n + i] = ny;
+    a.qt[3 * n + i] = nz;
+    double R[9];
+    quat_to_R(ns, nx, ny, nz, R);
+    double a0 = a.axes[i], a1 = a.axes[n + i], a2 = a.axes[2 * n + i];
+    Sym3<double> P = rot_diag_rot(R, a0 * a0, a1 * a1, a2 * a2);
+    a.Pt[i] = P.xx;
+    a.Pt[n + i] = P.yy;
+    a.Pt[2 * n + i] = P.zz;
+    a.Pt[3 * n + i] = P.xy;
+    a.Pt[4 * n + i] = P.xz;
+    a.Pt[5 * n + i] = P.yz;
+}
+
+__global__ void accept_kernel(AcceptArgs a) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= a.n) return;
+    const int64_t n = a.n;
+    for (int k = 0; k < 3; ++k) {
+        double v = a.xt[k * n + i];
+        double L = a.box[k];
+        if (L > 0.0) v = v - L * floor(v / L);
+        a.x[k * n + i] = v;
+    }
+    for (int k = 0; k < 4; ++k) a.q[k * n + i] = a.qt[k * n + i];
+    if (a.inertial)
+        for (int k = 0; k < 6; ++k) a.vel[k * n + i] = a.ustep[k * n + i];
+}
+
+__global__ void max_blocks_kernel(int nblocks, const double* __restrict__ v, double* __restrict__ out) {
+    __shared__ double sh[32];
+    double m = 0.0;
+    for (int i = threadIdx.x; i < nblocks; i += blockDim.x) m = fmax(m, v[i]);
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        m = threadIdx.x < (blockDim.x >> 5) ? sh[threadIdx.x] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+        if (threadIdx.x == 0) *out = m;
+    }
+}
+
+__global__ void iters_max_kernel(int64_t np, const int* __restrict__ it, int* __restrict__ out) {
+    int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p < np) {
+        int v = it[p];
+        atomicMax(out, v < 0 ? -v : v);
+    }
+}
+
+__global__ void wrap_kernel(int64_t n, double* x, double L0, double L1, double L2) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double L[3] = {L0, L1, L2};
+    for (int k = 0; k < 3; ++k)
+        if (L[k] > 0.0) x[k * n + i] = x[k * n + i] - L[k] * floor(x[k * n + i] / L[k]);
+}
+
+}  // namespace
+
+relcp_status prep_launch(const PrepArgs& a, cudaStream_t s) {
+    if (a.n == 0) return RELCP_OK;
+    note_launch();
+    prep_kernel<<<nb(a.n), kT, 0, s>>>(a);
+    RELCP_CUDA(cudaGetLastError());
+    return RELCP_OK;
+}
+relcp_status flag_le_launch(int64_t np, const double* phi, double thr, int* flags, cudaStream_t s) {
+    if (np == 0) return RELCP_OK;
+    note_launch();
+    flag_le_kernel<<<nb(np), kT, 0, s>>>(np, phi, thr, flags);
+    RELCP_CUDA(cudaGetLastError());
+    return RELCP_OK;
+}
+relcp_status rows_launch(const RowsArgs& a, cudaStream_t s) {
+    if (a.npairs == 0) return RELCP_OK;
+    note_launch();
+    rows_kernel<<<nb(a.npairs), kT, 0, s>>>(a);
+    RELCP_CUDA(cudaGetLastError());
+    return RELCP_OK;
+}
+relcp_status trial_launch(const TrialArgs& a, cudaStream_t s) {
+    if (a.n == 0) return RELCP_OK;
+    note_launch();
+    trial_kernel<<<nb(a.n), kT, 0, s>>>(a);
+    RELCP_CUDA(cudaGetLastError());
+    return RELCP_OK;
+}
+relcp_status accept_launch(const AcceptArgs& a, cudaStream_t s) {
+    if (a.n == 0) return RELCP_OK;
+    note_launch();
+    accept_kernel<<<nb(a.n), kT, 0, s>>>(a);
+    RELCP_CUDA(cudaGetLastError());
+    return RELCP_OK;
+}
+relcp_status max_blocks_launch(int nblocks, const double* v, double* out, cudaStream_t s) {
+    if (nblocks <= 0) {
+        RELCP_CUDA(cudaMemsetAsync(out, 0, sizeof(double), s));
+        return RELCP_OK;
+    }
+    note_launch();
+    max_blocks_kernel<<<1, 1024, 0, s>>>(nblocks, v, out);
+    RELCP_CUDA(cudaGetLastError());
+    return RELCP_OK;
+}
+relcp_status iters_max_launch(int64_t np, const int* it, int* out, cudaStream_t s) {
+    if (np == 0) return RELCP_OK;
+    note_launch();
+    iters_max_kernel<<<nb(np), kT, 0, s>>>(np, it, out);
+    RELCP_CUDA(cudaGetLastError());
+    return RELCP_OK;
+}
+relcp_status wrap_launch(int64_t n, double* x, const double box[3], cudaStream_t s) {
+    if (n == 0) return RELCP_OK;
+    note_launch();
+    wrap_kernel<<<nb(n), kT, 0, s>>>(n, x, box[0], box[1], box[2]);
+    RELCP_CUDA(cudaGetLastError());
+    return RELCP_OK;
+}
+
+}  // namespace relcp

@@ -1,0 +1,345 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Tolerances (stated here, derived in the design notes):
+  * candidate pairs and constraint index sets: bit-exact;
+  * FP64 path: normwise relative 1e-9 on velocities and gamma
+    (max |a - b| <= 1e-9 max |b|), SNSD Phi/n/r to 1e-10;
+  * mixed path: normwise relative 1e-5, and the accepted configuration's
+    max overlap <= eps_NCP.
+Decisions that sit within 1e-9 of a threshold in the oracle are reported as
+ambiguous; the seeded cases below have none (asserted).
+"""
+import numpy as np
+import pytest
+import torch
+
+from paper_2506_14097_gb300 import scenes
+
+pytestmark = pytest.mark.gpu
+
+
+def rel_err(a, b):
+    a, b = np.asarray(a, float), np.asarray(b, float)
+    if b.size == 0:
+        return 0.0
+    return float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300))
+
+
+def dev(a, dtype=torch.float64):
+    return torch.as_tensor(np.ascontiguousarray(a), dtype=dtype, device="cuda")
+
+
+def cfg_pair(R, orc, sc, dynamics, precision, dt=None, **kw):
+    amin = float(sc.axes.min())
+    dt = sc.dt if dt is None else dt
+    base = dict(dynamics=dynamics, dt=dt, eps_ncp=1e-3 * amin, box=tuple(sc.box), skin=0.1 * amin)
+    base.update(kw)
+    ocfg = orc.Config(**{k: v for k, v in base.items() if k in orc.Config.__dataclass_fields__})
+    gkw = dict(base)
+    gkw["precision"] = precision
+    gkw["length_scale"] = amin
+    gcfg = R.make_config(**gkw)
+    return ocfg, gcfg
+
+
+# ---------------------------------------------------------------------------
+# broad phase
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("n,side,skin", [(0, 10.0, 0.1), (1, 10.0, 0.1), (300, 12.0, 0.05), (5000, 40.0, 0.04),
+                                         (20000, 55.0, 0.05)])
+def test_broadphase_bitexact(relcp_gpu, orc, n, side, skin):
+    R = relcp_gpu
+    rng = np.random.default_rng(100 + n)
+    x = rng.random((n, 3)) * side
+    rb = rng.uniform(0.4, 1.0, n)
+    box = np.array([side] * 3)
+    ref = orc.candidate_pairs(x, rb, box, skin)
+    got = R.relcp_broadphase(dev(x), dev(rb), box, skin).cpu().numpy()
+    assert got.shape == ref.shape
+    assert np.array_equal(got, ref)
+
+
+def test_broadphase_open_box_and_threshold(relcp_gpu, orc):
+    R = relcp_gpu
+    x = np.array([[0.0, 0.0, 0.0], [2.0, 0.0, 0.0], [0.0, 3.0000001, 0.0], [0.1, 0.2, 1.5]])
+    rb = np.array([0.75, 0.75, 0.75, 0.5])
+    ref = orc.candidate_pairs(x, rb, np.zeros(3), 0.5)
+    got = R.relcp_broadphase(dev(x), dev(rb), np.zeros(3), 0.5).cpu().numpy()
+    assert np.array_equal(got, ref)
+
+
+# ---------------------------------------------------------------------------
+# SNSD
+# ---------------------------------------------------------------------------
+def random_pairs_scene(rng, n, side):
+    x = rng.random((n, 3)) * side
+    q = scenes.random_quaternions(rng, n)
+    axes = rng.uniform(0.4, 1.0, (n, 3))
+    return x, q, axes
+
+
+@pytest.mark.parametrize("precision,tol", [(0, 1e-10), (1, 1e-9)])
+def test_snsd_parity(relcp_gpu, orc, precision, tol):
+    R = relcp_gpu
+    rng = np.random.default_rng(7)
+    x, q, axes = random_pairs_scene(rng, 400, 9.0)
+    box = np.array([9.0] * 3)
+    pairs = orc.candidate_pairs(x, axes.max(axis=1), box, 0.3)
+    assert pairs.shape[0] > 200
+    phi, n, ra, rb, fl = orc.snsd(pairs, x, q, axes, box)
+    assert fl.max() == 0
+    out, iters = R.relcp_snsd_eval(dev(pairs, torch.int32), dev(x), dev(q), dev(axes), box, precision)
+    out = out.cpu().numpy()
+    assert (iters.cpu().numpy() >= 0).all()
+    assert np.abs(out[:, 0] - phi).max() <= tol * (1 + np.abs(phi).max())
+    assert np.abs(out[:, 1:4] - n).max() <= 1e3 * tol
+    assert np.abs(out[:, 4:7] - ra).max() <= 1e3 * tol
+    assert np.abs(out[:, 7:10] - rb).max() <= 1e3 * tol
+    # overlapping pairs are present and agree in sign
+    assert (phi < 0).sum() > 10
+    assert np.array_equal(out[:, 0] < 0, phi < 0)
+
+
+def test_snsd_spheres_closed_form(relcp_gpu):
+    R = relcp_gpu
+    rng = np.random.default_rng(8)
+    n = 200
+    x = rng.random((n, 3)) * 6.0
+    r = rng.uniform(0.3, 1.0, n)
+    axes = np.repeat(r[:, None], 3, axis=1)
+    q = scenes.random_quaternions(rng, n)
+    pairs = np.array([(i, j) for i in range(n) for j in range(i + 1, n)][:3000], dtype=np.int32)
+    out, _ = R.relcp_snsd_eval(dev(pairs, torch.int32), dev(x), dev(q), dev(axes), np.zeros(3), 0)
+    out = out.cpu().numpy()
+    d = x[pairs[:, 1]] - x[pairs[:, 0]]
+    L = np.linalg.norm(d, axis=1)
+    assert np.abs(out[:, 0] - (L - r[pairs[:, 0]] - r[pairs[:, 1]])).max() < 1e-12 * (1 + L.max())
+
+
+# ---------------------------------------------------------------------------
+# one LCP from identical rows
+# ---------------------------------------------------------------------------
+def contact_rows_from_scene(orc, sc, dt, dynamics):
+    """A_0 rows of a scene built with the oracle, with K and q."""
+    amin = float(sc.axes.min())
+    box = np.asarray(sc.box)
+    kt, Kr = orc.operator_K(dynamics, dt, sc.q, sc.axes)
+    pairs = orc.candidate_pairs(sc.x, sc.axes.max(axis=1), box, 0.1 * amin)
+    phi, n, ra, rb, _ = orc.snsd(pairs, sc.x, sc.q, sc.axes, box)
+    keep = phi <= 0.1 * amin
+    ia, ib = pairs[keep, 0].astype(np.int64), pairs[keep, 1].astype(np.int64)
+    nn = n[keep]
+    ta, tb = np.cross(ra[keep], nn), np.cross(rb[keep], nn)
+    U = orc.free_velocity(orc.Config(dynamics=dynamics, dt=dt, box=tuple(box)), sc.x, sc.vel, sc.fext, kt, Kr, box)
+    qv = phi[keep] + dt * orc.rows_dot_U(ia, ib, nn, ta, tb, U)
+    K7 = np.stack([kt, Kr[:, 0, 0], Kr[:, 1, 1], Kr[:, 2, 2], Kr[:, 0, 1], Kr[:, 0, 2], Kr[:, 1, 2]], axis=1)
+    return ia, ib, nn, ta, tb, qv, kt, Kr, K7
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_lcp_parity(relcp_gpu, orc, precision):
+    R = relcp_gpu
+    sc = scenes.lattice_scene(seed=3, n=125, spacing=1.8, dt=1e-2, vel_sigma=3.0, omega_sigma=1.5)
+    dt = 1e-2
+    ia, ib, nn, ta, tb, qv, kt, Kr, K7 = contact_rows_from_scene(orc, sc, dt, orc.INERTIAL)
+    m = ia.size
+    assert m > 20
+    A = orc.dense_A(dt, kt, Kr, ia, ib, nn, ta, tb)
+    gam_ref, w, st, _ = orc.lemke(A, qv)
+    assert st == 0
+    Uc_ref = orc.apply_K(kt, Kr, orc.wrench(sc.n, ia, ib, nn, ta, tb, gam_ref))
+    geom = np.concatenate([nn, ta, tb], axis=1)
+    tol = 1e-13 if precision == 0 else 1e-8
+    gam, uc, info = R.relcp_lcp_solve(dev(ia, torch.int32), dev(ib, torch.int32), dev(geom), dev(qv), dev(K7), dt,
+                                      precision=precision, tol=tol, max_iter=200000)
+    gam, uc = gam.cpu().numpy(), uc.cpu().numpy()
+    assert info.status == 0, (info.iterations, info.residual)
+    bound = 1e-9 if precision == 0 else 1e-5
+    assert rel_err(uc, Uc_ref) <= bound, (rel_err(uc, Uc_ref), info.iterations)
+    # gamma is unique here (A positive definite on this instance)
+    if np.linalg.eigvalsh(A).min() > 1e-8 * np.abs(A).max():
+        assert rel_err(gam, gam_ref) <= bound
+    # complementarity of the GPU result, checked with the oracle's A
+    g = A @ gam + qv
+    assert gam.min() >= 0 and g.min() >= -10 * tol
+
+
+def test_lcp_empty_and_zero_rows(relcp_gpu):
+    R = relcp_gpu
+    K7 = dev(np.ones((3, 7)))
+    e = torch.zeros(0, dtype=torch.int32, device="cuda")
+    gam, uc, info = R.relcp_lcp_solve(e, e, torch.zeros((0, 9), dtype=torch.float64, device="cuda"),
+                                      torch.zeros(0, dtype=torch.float64, device="cuda"), K7, 1e-3)
+    assert gam.numel() == 0 and float(uc.abs().max()) == 0.0 and info.iterations == 0
+
+
+# ---------------------------------------------------------------------------
+# full steps from identical states
+# ---------------------------------------------------------------------------
+def compare_step(R, orc, sc, ocfg, gcfg, vel=None, fext=None, bound=1e-9):
+    ref = orc.step(ocfg, sc.x, sc.q, sc.axes, vel, fext)
+    assert ref.ambiguous == 0 and ref.status == 0
+    sim = R.Simulation(gcfg)
+    sim.set_bodies(np.ascontiguousarray(sc.x), np.ascontiguousarray(sc.q), np.ascontiguousarray(sc.axes),
+                   None if vel is None else np.ascontiguousarray(vel),
+                   None if fext is None else np.ascontiguousarray(fext))
+    st = sim.step(1)
+    assert st == 0
+    stats = sim.stats()
+    pairs, phi0 = R.relcp_get_pairs(sim.ctx)
+    assert np.array_equal(pairs, ref.pairs)
+    assert np.abs(phi0 - ref.phi0).max() <= 1e-10 * (1 + np.abs(ref.phi0).max()) if ref.phi0.size else True
+    ids, geom, gam = R.relcp_get_rows(sim.ctx)
+    assert stats.depth == ref.depth
+    ref_ids = np.stack([ref.rows_ia, ref.rows_ib, ref.rows_rec, ref.rows_pair], axis=1)
+    assert np.array_equal(ids, ref_ids)
+    x, q, v = sim.bodies()
+    assert rel_err(v, ref.vel) <= bound, rel_err(v, ref.vel)
+    dx = orc.min_image(x - ref.x, np.asarray(ref.box))
+    assert np.abs(dx).max() <= bound * (1 + np.abs(ref.x).max())
+    qs = np.sign(np.sum(q * ref.q, axis=1))[:, None]
+    assert np.abs(q - qs * ref.q).max() <= bound
+    if ref.gamma.size:
+        uc = R.relcp_get_contact_velocity(sim.ctx, sc.n)
+        assert rel_err(uc, ref.U_contact) <= bound
+    assert stats.max_overlap <= ocfg.eps_ncp
+    sim.close()
+    return ref, stats
+
+
+@pytest.mark.parametrize("precision,bound", [(0, 1e-9), (1, 1e-5)])
+def test_step_parity_inertial_with_recursion(relcp_gpu, orc, precision, bound):
+    R = relcp_gpu
+    sc = scenes.lattice_scene(seed=2, n=64, spacing=1.8, dt=1e-2, vel_sigma=3.0, omega_sigma=1.5)
+    ocfg, gcfg = cfg_pair(R, orc, sc, orc.INERTIAL, precision)
+    x, q, v = sc.x, sc.q, sc.vel
+    depths = []
+    for k in range(12):
+        sck = scenes.Scene(x=x, q=q, axes=sc.axes, vel=v, fext=sc.fext, box=sc.box, dt=sc.dt)
+        ref, stats = compare_step(R, orc, sck, ocfg, gcfg, vel=v, bound=bound)
+        depths.append(ref.depth)
+        x, q, v = ref.x, ref.q, ref.vel
+    assert max(depths) >= 1
+
+
+def test_step_parity_overdamped_two_ellipsoids(relcp_gpu, orc):
+    R = relcp_gpu
+    sc = scenes.two_ellipsoid_scene(offset_y=4.2)
+    ocfg = orc.Config(dynamics=orc.OVERDAMPED, dt=0.1, eps_ncp=1e-5, box=(0, 0, 0), skin=0.5)
+    gcfg = R.make_config(dynamics=R.RELCP_OVERDAMPED, dt=0.1, eps_ncp=1e-5, box=(0, 0, 0), skin=0.5,
+                         length_scale=1.0)
+    x, q = sc.x, sc.q
+    for k in range(40):
+        r = orc.step(ocfg, x, q, sc.axes, None, sc.fext)
+        if k >= 22:
+            sck = scenes.Scene(x=x, q=q, axes=sc.axes, vel=np.zeros((2, 6)), fext=sc.fext, box=sc.box, dt=0.1)
+            ref, stats = compare_step(R, orc, sck, ocfg, gcfg, fext=sc.fext)
+        x, q = r.x, r.q
+    assert stats.depth >= 1
+
+
+def test_step_parity_compacting_suspension(relcp_gpu, orc):
+    R = relcp_gpu
+    sc = scenes.suspension_scene(seed=1, n=256, phi=0.1, steps=300, dt=5e-3)
+    amin = float(sc.axes.min())
+    rate = sc.meta["strain_rate"]
+    ocfg = orc.Config(dynamics=orc.OVERDAMPED, dt=sc.dt, eps_ncp=1e-3 * amin, box=tuple(sc.box), skin=0.1 * amin,
+                      strain_rate=rate)
+    x, q, box = sc.x, sc.q, np.asarray(sc.box)
+    # advance with the oracle to a dense state, then compare single steps
+    for k in range(260):
+        r = orc.step(orc.Config(**{**ocfg.__dict__, "box": tuple(box)}), x, q, sc.axes)
+        x, q, box = r.x, r.q, r.box
+    for k in range(3):
+        oc = orc.Config(**{**ocfg.__dict__, "box": tuple(box)})
+        gcfg = R.make_config(dynamics=R.RELCP_OVERDAMPED, dt=sc.dt, eps_ncp=1e-3 * amin, box=tuple(box),
+                             skin=0.1 * amin, strain_rate=rate, length_scale=amin)
+        sck = scenes.Scene(x=x, q=q, axes=sc.axes, vel=np.zeros((sc.n, 6)), fext=np.zeros((sc.n, 6)), box=box,
+                           dt=sc.dt)
+        ref, stats = compare_step(R, orc, sck, oc, gcfg)
+        assert ref.rows_ia.size > 100
+        x, q, box = ref.x, ref.q, ref.box
+
+
+# ---------------------------------------------------------------------------
+# edge cases and error paths
+# ---------------------------------------------------------------------------
+def test_empty_and_single_body(relcp_gpu):
+    R = relcp_gpu
+    cfg = R.make_config(dt=1e-3, eps_ncp=1e-3, box=(10, 10, 10), skin=0.05)
+    sim = R.Simulation(cfg)
+    sim.set_bodies(np.zeros((0, 3)), np.zeros((0, 4)), np.zeros((0, 3)))
+    assert sim.step(3) == 0
+    sim.set_bodies(np.array([[1.0, 2.0, 3.0]]), np.array([[1.0, 0, 0, 0]]), np.array([[0.5, 0.6, 0.7]]),
+                   np.array([[1.0, 0, 0, 0, 0, 0]]))
+    assert sim.step(1) == 0
+    x, q, v = sim.bodies()
+    assert abs(x[0, 0] - 1.001) < 1e-15 and sim.stats().n_pairs == 0
+    sim.close()
+
+
+def test_invalid_arguments_rejected(relcp_gpu):
+    R = relcp_gpu
+    cfg = R.make_config(dt=1e-3, eps_ncp=1e-3, box=(10, 10, 10), skin=0.05)
+    sim = R.Simulation(cfg)
+    x = np.array([[1.0, 2.0, 3.0]])
+    with pytest.raises(R.RelcpError) as e:
+        sim.set_bodies(x, np.array([[2.0, 0, 0, 0]]), np.array([[0.5, 0.6, 0.7]]))
+    assert e.value.status == R.RELCP_ERR_INVALID_ARG
+    with pytest.raises(R.RelcpError):
+        sim.set_bodies(np.array([[np.nan, 0, 0]]), np.array([[1.0, 0, 0, 0]]), np.array([[0.5, 0.6, 0.7]]))
+    with pytest.raises(R.RelcpError):
+        sim.set_bodies(x, np.array([[1.0, 0, 0, 0]]), np.array([[0.5, -0.6, 0.7]]))
+    bad = R.make_config(dt=-1.0)
+    with pytest.raises(R.RelcpError):
+        R.relcp_create(bad)
+    sim2 = R.Simulation(cfg)
+    with pytest.raises(R.RelcpError) as e:
+        sim2.step(1)
+    assert e.value.status == R.RELCP_ERR_STATE
+    sim.close()
+    sim2.close()
+
+
+def test_fault_injection_and_caps(relcp_gpu, orc):
+    R = relcp_gpu
+    sc = scenes.lattice_scene(seed=2, n=64, spacing=1.8, dt=1e-2, vel_sigma=3.0, omega_sigma=1.5)
+    amin = float(sc.axes.min())
+    base = dict(dynamics=R.RELCP_INERTIAL, dt=1e-2, eps_ncp=1e-3 * amin, box=tuple(sc.box), skin=0.1 * amin,
+                length_scale=amin)
+    for fault, expect in ((R.RELCP_FAULT_ROW_CAPACITY, R.RELCP_ERR_CAPACITY),
+                          (R.RELCP_FAULT_LCP_ITERS, R.RELCP_ERR_NOT_CONVERGED)):
+        sim = R.Simulation(R.make_config(fault_inject=fault, **base))
+        sim.set_bodies(sc.x, sc.q, sc.axes, sc.vel)
+        assert sim.step(1, allow=(expect,)) == expect
+        sim.close()
+    # recursion cap 0 reports the limit when the full method would augment
+    x, q, v = sc.x, sc.q, sc.vel
+    ocfg = orc.Config(dynamics=orc.INERTIAL, dt=1e-2, eps_ncp=1e-3 * amin, box=tuple(sc.box), skin=0.1 * amin)
+    while True:
+        r = orc.step(ocfg, x, q, sc.axes, v)
+        if r.depth >= 1:
+            break
+        x, q, v = r.x, r.q, r.vel
+    sim = R.Simulation(R.make_config(max_recursion=0, **base))
+    sim.set_bodies(x, q, sc.axes, v)
+    assert sim.step(1, allow=(R.RELCP_ERR_RECURSION_LIMIT,)) == R.RELCP_ERR_RECURSION_LIMIT
+    ids, geom, gam = R.relcp_get_rows(sim.ctx)
+    assert (ids[:, 2] == 0).all()
+    sim.close()
+
+
+def test_deterministic_bitwise(relcp_gpu):
+    R = relcp_gpu
+    sc = scenes.lattice_scene(seed=2, n=64, spacing=1.8, dt=1e-2, vel_sigma=3.0, omega_sigma=1.5)
+    amin = float(sc.axes.min())
+    outs = []
+    for rep in range(2):
+        sim = R.Simulation(R.make_config(dynamics=R.RELCP_INERTIAL, dt=1e-2, eps_ncp=1e-3 * amin, box=tuple(sc.box),
+                                         skin=0.1 * amin, length_scale=amin))
+        sim.set_bodies(sc.x, sc.q, sc.axes, sc.vel)
+        sim.step(10)
+        outs.append(sim.bodies())
+        sim.close()
+    for a, b in zip(outs[0], outs[1]):
+        assert np.array_equal(a, b)
