@@ -51,12 +51,15 @@ def build_scene(n, seed=1, steps=2000):
     return scenes.suspension_scene(seed=seed, n=n, phi=0.1, phi_final=0.55, steps=steps, dt=5e-3)
 
 
+EXTRA_FLAGS = 0
+
+
 def make_cfg(R, sc, precision, guess, timing=True):
     amin = float(sc.axes.min())
     return R.make_config(dynamics=R.RELCP_OVERDAMPED, precision=precision, guess=guess, dt=sc.dt,
                          eps_ncp=1e-3 * amin, box=tuple(sc.box), skin=0.1 * amin,
                          strain_rate=sc.meta["strain_rate"], length_scale=amin, lcp_max_iter=20000,
-                         flags=R.RELCP_FLAG_PHASE_TIMING if timing else 0)
+                         flags=(R.RELCP_FLAG_PHASE_TIMING if timing else 0) | EXTRA_FLAGS)
 
 
 class Clocks:
@@ -110,7 +113,7 @@ class Clocks:
                 "samples": len(sm)}
 
 
-def run_gpu_arm(R, torch, sc, precision, guess, steps, warmup, flush, stream):
+def run_gpu_arm(R, torch, sc, precision, guess, steps, warmup, flush, stream, nvtx_from=None):
     """W warm-up steps on one context, then `steps` timed steps from the initial
     state on a fresh context.  Returns per-step times and accumulated stats."""
     x, q, axes = (np.ascontiguousarray(a) for a in (sc.x, sc.q, sc.axes))
@@ -125,11 +128,14 @@ def run_gpu_arm(R, torch, sc, precision, guess, steps, warmup, flush, stream):
     torch.cuda.synchronize()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
     acc = dict(lcp_ms=0.0, lcp_bytes=0.0, lcp_launches=0, snsd_ms=0.0, snsd_evals=0, snsd_launches=0, depth_max=0,
-               depth_sum=0, rows_max=0, pairs_max=0, lcp_iters=0, max_overlap=0.0, not_converged=0, status=set())
+               depth_sum=0, rows_max=0, pairs_max=0, lcp_iters=0, max_overlap=0.0, not_converged=0, status=set(),
+               ms_broadphase=0.0, ms_lcp_phase=0.0, ms_other=0.0, ms_step_events=0.0, rebuilds=0)
     launches0 = R.relcp_kernel_launches()
     with torch.cuda.stream(stream):
         for k in range(steps):
             flush.zero_()
+            if nvtx_from is not None and k == nvtx_from:
+                torch.cuda.nvtx.range_push("relcp_profile")
             ev[k][0].record(stream)
             st = sim.step(1, allow=(R.RELCP_ERR_NOT_CONVERGED,))
             ev[k][1].record(stream)
@@ -148,7 +154,14 @@ def run_gpu_arm(R, torch, sc, precision, guess, steps, warmup, flush, stream):
             acc["pairs_max"] = max(acc["pairs_max"], s.n_pairs)
             acc["lcp_iters"] += s.lcp_iters_total
             acc["max_overlap"] = max(acc["max_overlap"], s.max_overlap)
+            acc["ms_broadphase"] += s.ms_broadphase
+            acc["ms_lcp_phase"] += s.ms_lcp
+            acc["ms_other"] += s.ms_augment
+            acc["ms_step_events"] += s.ms_total
+            acc["rebuilds"] += s.pair_list_rebuilt
     torch.cuda.synchronize()
+    if nvtx_from is not None and nvtx_from < steps:
+        torch.cuda.nvtx.range_pop()
     acc["launches"] = R.relcp_kernel_launches() - launches0
     times = [a.elapsed_time(b) for a, b in ev]
     acc["box_final"] = list(R.relcp_get_box(sim.ctx))
@@ -159,10 +172,12 @@ def run_gpu_arm(R, torch, sc, precision, guess, steps, warmup, flush, stream):
 
 def run_e2e(R, torch, sc, precision, guess, steps):
     """The same steps through the public C ABI with host buffers: every step
-    copies the body state in (set_bodies) and the result out (get_bodies)."""
+    copies the body state in (set_bodies: x, q, semi-axes) and the result out
+    (get_bodies: x, q and the step velocity).  The workload has no background
+    velocity or external force, so none is passed in."""
     n = sc.n
     x, q, axes = (np.ascontiguousarray(a) for a in (sc.x, sc.q, sc.axes))
-    vel = np.zeros((n, 6))
+    u = np.zeros((n, 6))
     cfg = make_cfg(R, sc, precision, guess, timing=False)
     sim = R.Simulation(cfg)
     torch.cuda.synchronize()
@@ -172,14 +187,14 @@ def run_e2e(R, torch, sc, precision, guess, steps):
         for k in range(3):
             cfg.box[k] = box[k]
         R.relcp_set_config(sim.ctx, cfg)
-        sim.set_bodies(x, q, axes, vel)
+        sim.set_bodies(x, q, axes)
         sim.step(1, allow=(R.RELCP_ERR_NOT_CONVERGED,))
-        R.relcp_get_bodies(sim.ctx, x, q, vel)
+        R.relcp_get_bodies(sim.ctx, x, q, u)
         box = R.relcp_get_box(sim.ctx)
     torch.cuda.synchronize()
     dt = time.perf_counter() - t0
     sim.close()
-    h2d = n * (3 + 4 + 3 + 6) * 8
+    h2d = n * (3 + 4 + 3) * 8
     d2h = n * (3 + 4 + 6) * 8
     return dt, h2d, d2h
 
@@ -264,6 +279,9 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=None)
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     ap.add_argument("--ref-budget", type=float, default=150.0)
+    ap.add_argument("--jacobi", type=int, default=0, help="1: Jacobi-scaled projected-gradient steps")
+    ap.add_argument("--nvtx-from", type=int, default=None,
+                    help="profiling aid: wrap timed steps >= this index in the NVTX range relcp_profile")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -289,6 +307,9 @@ def main():
     from paper_2506_14097_gb300 import relcp as R
 
     R.load()
+    global EXTRA_FLAGS
+    if args.jacobi:
+        EXTRA_FLAGS |= R.RELCP_FLAG_JACOBI
     sc = build_scene(args.bodies)
     stream = torch.cuda.Stream()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
@@ -301,7 +322,7 @@ def main():
     clocks = Clocks(local)
     clocks.start()
     t_wall0 = time.perf_counter()
-    times, acc = run_gpu_arm(R, torch, sc, precision, guess, args.steps, args.warmup, flush, stream)
+    times, acc = run_gpu_arm(R, torch, sc, precision, guess, args.steps, args.warmup, flush, stream, args.nvtx_from)
     t_wall = time.perf_counter() - t_wall0
     clk = clocks.stop()
     total_ms = float(sum(times))
@@ -321,20 +342,24 @@ def main():
                 "lcp_iters_total": acc64["lcp_iters"]}
 
     e2e_steps = args.steps if args.e2e_steps is None else args.e2e_steps
-    e2e_t, h2d, d2h = run_e2e(R, torch, sc, precision, guess, e2e_steps)
-    e2e_value = world * sc.n * e2e_steps / e2e_t
+    if e2e_steps > 0:
+        e2e_t, h2d, d2h = run_e2e(R, torch, sc, precision, guess, e2e_steps)
+        e2e_value = world * sc.n * e2e_steps / e2e_t
+    else:
+        e2e_value, h2d, d2h = None, 0, 0
 
     hbm, peak_kind = peaks()
     lcp_gbs = acc["lcp_bytes"] / (acc["lcp_ms"] / 1e3) / 1e9 if acc["lcp_ms"] > 0 else 0.0
     line = None
     if rank == 0:
-        cpu = oracle_rate(1024, 10 ** 6, args.cpu_budget)
+        cpu = oracle_rate(1024, 10 ** 6, args.cpu_budget) if args.cpu_budget > 0 else None
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "bodies": sc.n, "precision": "mixed (FP32 bulk, FP64 checks)",
-                       "guess": "cold", "l2": "flushed between steps (256 MiB write)",
+                       "guess": "cold", "lcp_steps": "jacobi-scaled BB" if args.jacobi else "BB",
+                       "l2": "flushed between steps (256 MiB write)",
                        "parallelism": "replicas" if world > 1 else "single"},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                     "steps": e2e_steps},
@@ -343,9 +368,10 @@ def main():
                          "achieved": lcp_gbs, "peak": hbm, "unit": "GB/s", "frac": lcp_gbs / hbm,
                          "traffic": None, "peak_kind": peak_kind, "launches": acc["lcp_launches"],
                          "kernel_ms_total": acc["lcp_ms"]},
-            "cpu_baseline": {"value": cpu["value"], "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": (f"first {cpu['steps']} steps (phi {cpu['phi_start']:.4f}->{cpu['phi_end']:.4f})"
-                                        f" of the 1,024-body version of the workload, {cpu['seconds']:.1f} s")},
+            "cpu_baseline": None if cpu is None else {
+                "value": cpu["value"], "unit": UNIT, "cores": 1, "kind": "oracle",
+                "sample": (f"first {cpu['steps']} steps (phi {cpu['phi_start']:.4f}->{cpu['phi_end']:.4f})"
+                           f" of the 1,024-body version of the workload, {cpu['seconds']:.1f} s")},
             "clocks": clk,
             "fp64_gpu": fp64,
             "speedup_vs_fp64": (value / fp64["value"]) if fp64 else None,
@@ -355,6 +381,10 @@ def main():
                       "eps_ncp": 1e-3 * float(sc.axes.min()), "status": acc["status"],
                       "snsd_kernel_ms": acc["snsd_ms"], "snsd_evals": acc["snsd_evals"],
                       "lcp_kernel_ms": acc["lcp_ms"], "wall_s": t_wall,
+                      "phase_ms": {"broadphase": acc["ms_broadphase"], "snsd": acc["snsd_ms"],
+                                   "lcp_incl_csr": acc["ms_lcp_phase"], "rest": acc["ms_other"],
+                                   "to_last_sync": acc["ms_step_events"]},
+                      "pair_list_rebuilds": acc["rebuilds"],
                       "phi_final": sc.meta["volume"] / float(np.prod(acc["box_final"]))},
         }
         print(json.dumps(line), flush=True)

@@ -91,7 +91,11 @@ enum {
     RELCP_FAULT_LCP_ITERS = 2u     /* run every LCP with a cap of 1 iteration */
 };
 enum {
-    RELCP_FLAG_PHASE_TIMING = 1u   /* record per-phase CUDA-event timings in relcp_step_stats */
+    RELCP_FLAG_PHASE_TIMING = 1u,  /* record per-phase CUDA-event timings in relcp_step_stats */
+    RELCP_FLAG_NO_WARM_START = 2u, /* start every LCP_0 from gamma = 0 instead of the previous step's
+                                      gamma of the same pair (the solution is the same within lcp_tol) */
+    RELCP_FLAG_JACOBI = 4u         /* projected-gradient steps scaled by 1 / A_aa, BB lengths in the
+                                      matching metric (same solution, fewer iterations on uneven rows) */
 };
 
 #define RELCP_MAX_DEPTH_STATS 64
@@ -124,6 +128,8 @@ typedef struct relcp_step_stats {
     int64_t snsd_evals;         /* pair evaluations in those launches */
     int32_t lcp_launches;
     int32_t snsd_launches;
+    int32_t pair_list_rebuilt;  /* 1 when the cached candidate list was rebuilt in this step */
+    int32_t pad0;
 } relcp_step_stats;
 
 typedef struct relcp_ctx relcp_ctx;

@@ -14,6 +14,7 @@
 #include <cstdarg>
 #include <cstring>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "relcp_internal.cuh"
@@ -53,12 +54,24 @@ int device_sm_count() {
 
 using namespace relcp;
 
+// Device-side scalars of one step, read by the host in one copy at each
+// recursion decision.
+struct DevStep {
+    int nrows;          // rows currently in the LCP (set by the row kernel)
+    int status;         // DEV_* bits
+    int newton_max;     // largest Newton iteration count
+    int nrows0;         // |A_0| (copied from nrows after the first LCP)
+    unsigned long long maxov_bits;  // bits of the largest overlap at the last trial
+    LcpDevResult lcp;   // iterations and residual of the last LCP
+};
+
 struct relcp_ctx {
     relcp_config cfg{};
     cudaStream_t s = nullptr;
     int64_t n = 0;
     bool has_bodies = false;
     double box[3] = {0, 0, 0};
+    double rb_max = 0.0;
     // body state and per-step body arrays (SoA)
     DBuf<double> x, q, axes, vel, fext, P, K, rb, ufree, uc, ustep, xt, qt, Pt;
     // pairs
@@ -66,18 +79,25 @@ struct relcp_ctx {
     int64_t npairs = 0;
     DBuf<double> s0, s1;  // SNSD outputs at C^k and at the trial (10 x npairs)
     DBuf<int> it0, it1, flags, fscan;
-    DBuf<double> blockmax, scal;  // scal: [max overlap]
-    DBuf<int> dstatus, imax;
+    DBuf<DevStep> dstep;
     // rows (capacity rcap, SoA)
     int64_t nrows = 0, nrows0 = 0, rcap = 0;
     DBuf<int> r_ia, r_ib, r_rec, r_pair;
-    DBuf<double> r_geom, r_q, r_diag, r_gamma;
+    DBuf<double> r_geom, r_q, r_diag, r_gamma, r_invd;
+    DBuf<float> r_geomf, r_gammaf, r_qf, Kf, r_invdf;
     BroadphaseScratch bp;
     LcpScratch lcp;
     ScanScratch scan;
     MlpState mlp;
     relcp_step_stats stats{};
     int64_t steps_done = 0;
+    std::vector<cudaEvent_t> events;  // phase-timing event pool
+    // warm start: the previous step's A_0 rows (sorted pair keys) and gamma
+    DBuf<long long> prev_keys;
+    DBuf<double> prev_gamma;
+    int64_t prev_n = 0;
+    DBuf<long long> next_keys;
+    DBuf<double> next_gamma;
 };
 
 namespace {
@@ -109,83 +129,88 @@ relcp_status check_config(const relcp_config* c) {
     return RELCP_OK;
 }
 
+template <class T>
+relcp_status move_rows(DBuf<T>& dst, DBuf<T>& src, int comps, int64_t nc, int64_t oldcap, int64_t m, cudaStream_t s) {
+    DBuf<T> nb;
+    RELCP_TRY(nb.ensure((size_t)(comps * nc), s));
+    if (m > 0 && src.p)
+        for (int k = 0; k < comps; ++k)
+            RELCP_CUDA(cudaMemcpyAsync(nb.p + k * nc, src.p + k * oldcap, m * sizeof(T), cudaMemcpyDeviceToDevice, s));
+    src.release(s);
+    dst = nb;
+    return RELCP_OK;
+}
+
+// grow the row buffers to hold `need` rows, keeping the first c->nrows
 relcp_status grow_rows(relcp_ctx* c, int64_t need) {
-    if (need <= c->rcap) return RELCP_OK;
-    int64_t nc = need + need / 2 + 64;
+    const bool mixed = c->cfg.precision == RELCP_MIXED;
+    if (need <= c->rcap && (!mixed || c->r_geomf.p)) return RELCP_OK;
+    int64_t nc = need > c->rcap ? need + need / 2 + 64 : c->rcap;
     cudaStream_t s = c->s;
-    DBuf<int> ia, ib, rec, pair;
-    DBuf<double> geom, q, diag, gamma;
-    RELCP_TRY(ia.ensure(nc, s));
-    RELCP_TRY(ib.ensure(nc, s));
-    RELCP_TRY(rec.ensure(nc, s));
-    RELCP_TRY(pair.ensure(nc, s));
-    RELCP_TRY(geom.ensure(9 * nc, s));
-    RELCP_TRY(q.ensure(nc, s));
-    RELCP_TRY(diag.ensure(nc, s));
-    RELCP_TRY(gamma.ensure(nc, s));
-    // ensure() over-allocates; the logical capacity is nc
-    if (c->nrows > 0) {
-        int64_t m = c->nrows;
-        RELCP_CUDA(cudaMemcpyAsync(ia.p, c->r_ia.p, m * sizeof(int), cudaMemcpyDeviceToDevice, s));
-        RELCP_CUDA(cudaMemcpyAsync(ib.p, c->r_ib.p, m * sizeof(int), cudaMemcpyDeviceToDevice, s));
-        RELCP_CUDA(cudaMemcpyAsync(rec.p, c->r_rec.p, m * sizeof(int), cudaMemcpyDeviceToDevice, s));
-        RELCP_CUDA(cudaMemcpyAsync(pair.p, c->r_pair.p, m * sizeof(int), cudaMemcpyDeviceToDevice, s));
-        for (int k = 0; k < 9; ++k)
-            RELCP_CUDA(cudaMemcpyAsync(geom.p + k * nc, c->r_geom.p + k * c->rcap, m * sizeof(double),
-                                       cudaMemcpyDeviceToDevice, s));
-        RELCP_CUDA(cudaMemcpyAsync(q.p, c->r_q.p, m * sizeof(double), cudaMemcpyDeviceToDevice, s));
-        RELCP_CUDA(cudaMemcpyAsync(diag.p, c->r_diag.p, m * sizeof(double), cudaMemcpyDeviceToDevice, s));
-        RELCP_CUDA(cudaMemcpyAsync(gamma.p, c->r_gamma.p, m * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    const int64_t m = c->nrows, oc = c->rcap;
+    RELCP_TRY(move_rows(c->r_ia, c->r_ia, 1, nc, oc, m, s));
+    RELCP_TRY(move_rows(c->r_ib, c->r_ib, 1, nc, oc, m, s));
+    RELCP_TRY(move_rows(c->r_rec, c->r_rec, 1, nc, oc, m, s));
+    RELCP_TRY(move_rows(c->r_pair, c->r_pair, 1, nc, oc, m, s));
+    RELCP_TRY(move_rows(c->r_geom, c->r_geom, 9, nc, oc, m, s));
+    RELCP_TRY(move_rows(c->r_q, c->r_q, 1, nc, oc, m, s));
+    RELCP_TRY(move_rows(c->r_diag, c->r_diag, 1, nc, oc, m, s));
+    RELCP_TRY(move_rows(c->r_gamma, c->r_gamma, 1, nc, oc, m, s));
+    RELCP_TRY(move_rows(c->r_invd, c->r_invd, 1, nc, oc, m, s));
+    if (mixed) {
+        RELCP_TRY(move_rows(c->r_invdf, c->r_invdf, 1, nc, oc, m, s));
+        RELCP_TRY(move_rows(c->r_geomf, c->r_geomf, 9, nc, oc, m, s));
+        RELCP_TRY(move_rows(c->r_gammaf, c->r_gammaf, 1, nc, oc, m, s));
+        RELCP_TRY(move_rows(c->r_qf, c->r_qf, 1, nc, oc, m, s));
     }
-    c->r_ia.release(s);
-    c->r_ib.release(s);
-    c->r_rec.release(s);
-    c->r_pair.release(s);
-    c->r_geom.release(s);
-    c->r_q.release(s);
-    c->r_diag.release(s);
-    c->r_gamma.release(s);
-    c->r_ia = ia;
-    c->r_ib = ib;
-    c->r_rec = rec;
-    c->r_pair = pair;
-    c->r_geom = geom;
-    c->r_q = q;
-    c->r_diag = diag;
-    c->r_gamma = gamma;
     c->rcap = nc;
     return RELCP_OK;
 }
 
+// CUDA events of the optional per-phase timing, recorded on the context
+// stream and read only after a stream synchronisation.  Events come from a
+// per-context pool, created once.
 struct PhaseTimer {
-    static constexpr int kMaxEv = 512;
+    std::vector<cudaEvent_t>* pool = nullptr;
     bool on = false;
     cudaStream_t s{};
-    cudaEvent_t ev[kMaxEv];
     int k = 0;
-    relcp_status start(bool enable, cudaStream_t st) {
+    relcp_status start(bool enable, cudaStream_t st, std::vector<cudaEvent_t>* p) {
         on = enable;
         s = st;
         k = 0;
-        if (!on) return RELCP_OK;
-        for (int i = 0; i < kMaxEv; ++i) RELCP_CUDA(cudaEventCreate(&ev[i]));
+        pool = p;
         return RELCP_OK;
     }
     int mark() {
-        if (!on || k >= kMaxEv) return -1;
-        cudaEventRecord(ev[k], s);
+        if (!on) return -1;
+        if (k >= (int)pool->size()) {
+            cudaEvent_t e;
+            if (cudaEventCreate(&e) != cudaSuccess) return -1;
+            pool->push_back(e);
+        }
+        cudaEventRecord((*pool)[k], s);
         return k++;
     }
+    // both events must have completed (call after a stream synchronisation)
     float ms(int a, int b) {
         float t = 0.f;
-        if (on && a >= 0 && b >= 0) cudaEventElapsedTime(&t, ev[a], ev[b]);
+        if (on && a >= 0 && b >= 0) cudaEventElapsedTime(&t, (*pool)[a], (*pool)[b]);
         return t;
     }
-    void stop() {
-        if (on)
-            for (int i = 0; i < kMaxEv; ++i) cudaEventDestroy(ev[i]);
-        on = false;
+    // an unrecorded event for a callee to record (index returned in *idx)
+    cudaEvent_t take(int* idx) {
+        *idx = -1;
+        if (!on) return nullptr;
+        if (k >= (int)pool->size()) {
+            cudaEvent_t e;
+            if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+            pool->push_back(e);
+        }
+        *idx = k;
+        return (*pool)[k++];
     }
+    void stop() { on = false; }
 };
 
 relcp_status step_once(relcp_ctx* c) {
@@ -202,11 +227,11 @@ relcp_status step_once(relcp_ctx* c) {
     }
     const bool mixed = cfg.precision == RELCP_MIXED;
     PhaseTimer tm;
-    RELCP_TRY(tm.start((cfg.flags & RELCP_FLAG_PHASE_TIMING) != 0, s));
-    std::vector<std::pair<int, int>> snsd_marks;
+    RELCP_TRY(tm.start((cfg.flags & RELCP_FLAG_PHASE_TIMING) != 0, s, &c->events));
+    std::vector<std::pair<int, int>> snsd_marks, lcp_marks, lcpk_marks;
     int t_begin = tm.mark();
-    RELCP_CUDA(cudaMemsetAsync(c->dstatus.p, 0, sizeof(int), s));
-    RELCP_CUDA(cudaMemsetAsync(c->imax.p, 0, sizeof(int), s));
+    RELCP_CUDA(cudaMemsetAsync(c->dstep.p, 0, sizeof(DevStep), s));
+    DevStep* ds = c->dstep.p;
 
     // bodies: normalised q, P, K, rb, U_free
     PrepArgs pa{};
@@ -224,13 +249,20 @@ relcp_status step_once(relcp_ctx* c) {
     pa.fext = c->fext.p;
     pa.P = c->P.p;
     pa.K = c->K.p;
+    pa.Kf = nullptr;
+    if (mixed) {
+        RELCP_TRY(c->Kf.ensure((size_t)(7 * (n > 0 ? n : 1)), s));
+        pa.Kf = c->Kf.p;
+    }
     pa.rb = c->rb.p;
     pa.ufree = c->ufree.p;
     RELCP_TRY(prep_launch(pa, s));
 
-    // broad phase
+    // broad phase (synchronises once for the pair count)
     View<3, const double> xv = View<3, const double>::soa(c->x.p, n);
-    RELCP_TRY(broadphase(n, xv, c->rb.p, box0, cfg.skin, c->pa, c->pb, &c->npairs, c->bp, s));
+    const int rebuilds_before = c->bp.rebuilds;
+    RELCP_TRY(broadphase_cached(n, c->x.p, c->rb.p, c->rb_max, box0, cfg.skin, c->pa, c->pb, &c->npairs, c->bp, s));
+    st.pair_list_rebuilt = c->bp.rebuilds != rebuilds_before;
     const int64_t np = c->npairs;
     st.n_pairs = np;
     int t_bp = tm.mark();
@@ -241,7 +273,13 @@ relcp_status step_once(relcp_ctx* c) {
     RELCP_TRY(c->it1.ensure(npa, s));
     RELCP_TRY(c->flags.ensure(npa, s));
     RELCP_TRY(c->fscan.ensure(npa + 1, s));
-    RELCP_TRY(c->blockmax.ensure(npa / 64 + 8, s));
+    c->nrows = 0;
+    if (cfg.fault_inject & RELCP_FAULT_ROW_CAPACITY) {
+        set_error("row capacity exhausted (injected fault)");
+        tm.stop();
+        return RELCP_ERR_CAPACITY;
+    }
+    RELCP_TRY(grow_rows(c, npa));
 
     auto snsd_out = [&](DBuf<double>& o, DBuf<int>& it) {
         SnsdOut so;
@@ -265,7 +303,6 @@ relcp_status step_once(relcp_ctx* c) {
     for (int k = 0; k < 3; ++k) sa.box[k] = box0[k];
     sa.guess.c[0] = sa.guess.c[1] = sa.guess.c[2] = nullptr;
     sa.guess.s = 1;
-    st.guess_used = 0;
     if (cfg.guess == RELCP_GUESS_MLP && c->mlp.loaded && np > 0) {
         RELCP_TRY(mlp_guess(c->mlp, np, c->pa.p, c->pb.p, xv, View<4, const double>::soa(c->q.p, n),
                             View<3, const double>::soa(c->axes.p, n), box0, s));
@@ -276,32 +313,16 @@ relcp_status step_once(relcp_ctx* c) {
     sa.out = snsd_out(c->s0, c->it0);
     sa.eps = 0.0;
     sa.viol = nullptr;
-    sa.block_maxov = nullptr;
-    sa.status = c->dstatus.p;
+    sa.maxov_bits = nullptr;
+    sa.newton_max = &ds->newton_max;
+    sa.status = &ds->status;
     {
         int e0 = tm.mark();
-        RELCP_TRY(snsd_launch(sa, nullptr, s));
-        int e1 = tm.mark();
-        snsd_marks.push_back({e0, e1});
-        st.snsd_evals += tm.on ? np : 0;
+        RELCP_TRY(snsd_launch(sa, s));
+        snsd_marks.push_back({e0, tm.mark()});
     }
-    RELCP_TRY(iters_max_launch(np, c->it0.p, c->imax.p, s));
-    int t_snsd0 = tm.mark();
 
-    // A_0
-    double phi_skin = cfg.phi_skin;
-    RELCP_TRY(flag_le_launch(np, c->s0.p, phi_skin, c->flags.p, s));
-    RELCP_TRY(exclusive_scan(c->flags.p, c->fscan.p, np, c->scan, s));
-    int n0 = 0;
-    RELCP_CUDA(cudaMemcpyAsync(&n0, c->fscan.p + np, sizeof(int), cudaMemcpyDeviceToHost, s));
-    RELCP_CUDA(cudaStreamSynchronize(s));
-    c->nrows = 0;
-    if (cfg.fault_inject & RELCP_FAULT_ROW_CAPACITY) {
-        set_error("row capacity exhausted (injected fault)");
-        tm.stop();
-        return RELCP_ERR_CAPACITY;
-    }
-    RELCP_TRY(grow_rows(c, n0 > 0 ? n0 : 1));
+    // A_0: rows for the pairs with Phi(C^k) <= phi_skin
     RowsArgs ra{};
     ra.npairs = np;
     ra.nbodies = n;
@@ -320,67 +341,79 @@ relcp_status step_once(relcp_ctx* c) {
     ra.ufree = c->ufree.p;
     ra.uc = c->uc.p;
     ra.K = c->K.p;
-    ra.ia = c->r_ia.p;
-    ra.ib = c->r_ib.p;
-    ra.rec = c->r_rec.p;
-    ra.pair = c->r_pair.p;
-    ra.geom = c->r_geom.p;
-    ra.q = c->r_q.p;
-    ra.diag = c->r_diag.p;
-    ra.gamma = c->r_gamma.p;
-    ra.status = c->dstatus.p;
-    RELCP_TRY(rows_launch(ra, s));
-    c->nrows = n0;
-    c->nrows0 = n0;
-    st.n_rows0 = n0;
+    ra.nrows_dev = &ds->nrows;
+    ra.status = &ds->status;
+    const bool warm = !(cfg.flags & RELCP_FLAG_NO_WARM_START) && c->prev_n > 0;
+    ra.prev_n = warm ? c->prev_n : 0;
+    ra.prev_keys = c->prev_keys.p;
+    ra.prev_gamma = c->prev_gamma.p;
+    auto bind_rows = [&](RowsArgs& r) {
+        r.cap = c->rcap;
+        r.ia = c->r_ia.p;
+        r.ib = c->r_ib.p;
+        r.rec = c->r_rec.p;
+        r.pair = c->r_pair.p;
+        r.geom = c->r_geom.p;
+        r.geomf = mixed ? c->r_geomf.p : nullptr;
+        r.q = c->r_q.p;
+        r.qf = mixed ? c->r_qf.p : nullptr;
+        r.diag = c->r_diag.p;
+        r.invd = mixed ? nullptr : c->r_invd.p;
+        r.invdf = mixed ? c->r_invdf.p : nullptr;
+        r.gamma = mixed ? nullptr : c->r_gamma.p;
+        r.gammaf = mixed ? c->r_gammaf.p : nullptr;
+    };
+    bind_rows(ra);
+    if (np > 0) {
+        RELCP_TRY(flag_le_launch(np, c->s0.p, cfg.phi_skin, c->flags.p, s));
+        RELCP_TRY(exclusive_scan(c->flags.p, c->fscan.p, np, c->scan, s));
+        RELCP_TRY(rows_launch(ra, s));
+        RELCP_CUDA(cudaMemcpyAsync(&ds->nrows0, &ds->nrows, sizeof(int), cudaMemcpyDeviceToDevice, s));
+    }
+    int64_t m_bound = np;  // rows <= m_bound until the host learns the count
 
     int depth = 0;
     int lcp_iters_total = 0;
-    float ms_lcp = 0, ms_aug = 0, ms_snsd = tm.ms(t_bp, t_snsd0);
     relcp_status step_status = RELCP_OK;
-    LcpResult lr{};
-    double maxov = 0.0;
+    DevStep hs{};
+    int t_last = -1;
     for (;;) {
-        int t_l0 = tm.mark();
+        // LCP on the current rows
         LcpProblem pr{};
-        pr.nrows = c->nrows;
+        pr.m_cap = m_bound;
+        pr.nrows_dev = &ds->nrows;
         pr.nbodies = n;
         pr.ia = c->r_ia.p;
         pr.ib = c->r_ib.p;
-        for (int k = 0; k < 9; ++k) pr.geom.c[k] = c->r_geom.p + k * c->rcap;
-        pr.geom.s = 1;
+        for (int k = 0; k < 9; ++k)
+            pr.geom[k] = mixed ? (const void*)(c->r_geomf.p + k * c->rcap) : (const void*)(c->r_geom.p + k * c->rcap);
         pr.q = c->r_q.p;
+        pr.qr = mixed ? (const void*)c->r_qf.p : (const void*)c->r_q.p;
         pr.diag = c->r_diag.p;
-        pr.K = View<7, const double>::soa(c->K.p, n);
+        pr.invd = nullptr;
+        if (cfg.flags & RELCP_FLAG_JACOBI) pr.invd = mixed ? (const void*)c->r_invdf.p : (const void*)c->r_invd.p;
+        for (int k = 0; k < 7; ++k) {
+            pr.K[k] = c->K.p + k * n;
+            pr.Kr[k] = mixed ? (const void*)(c->Kf.p + k * n) : (const void*)(c->K.p + k * n);
+        }
         pr.c = dt;
         pr.mixed = mixed ? 1 : 0;
         pr.tol = cfg.lcp_tol;
         pr.max_iter = (cfg.fault_inject & RELCP_FAULT_LCP_ITERS) ? 1 : cfg.lcp_max_iter;
-        pr.gamma = c->r_gamma.p;
-        pr.uc = View<6, double>::soa(c->uc.p, n);
-        pr.time_kernel = tm.on;
-        RELCP_TRY(lcp_solve(pr, c->lcp, &lr, s));
-        if (tm.on && c->nrows > 0) {
-            st.ms_lcp_kernel += lr.kernel_ms;
-            st.lcp_alg_bytes += lcp_bytes_per_iter(c->nrows, n, mixed) * (lr.iterations + 1);
-            st.lcp_launches += 1;
-        }
-        if (depth < RELCP_MAX_DEPTH_STATS) {
-            st.lcp_iters[depth] = lr.iterations;
-            st.rows_per_rec[depth] = (int)c->nrows;
-        }
-        lcp_iters_total += lr.iterations;
-        if (lr.dev_status) {
-            relcp_status ls = status_from_device(lr.dev_status);
-            if (ls == RELCP_ERR_TIMEOUT) {
-                set_error("LCP grid barrier timed out");
-                tm.stop();
-                return ls;
-            }
-            if (step_status == RELCP_OK) step_status = ls;
-        }
-        int t_l1 = tm.mark();
-        ms_lcp += tm.ms(t_l0, t_l1);
+        pr.gamma = mixed ? (void*)c->r_gammaf.p : (void*)c->r_gamma.p;
+        for (int k = 0; k < 6; ++k) pr.uc[k] = c->uc.p + k * n;
+        pr.result = &ds->lcp;
+        pr.status = &ds->status;
+        int k0 = -1, k1 = -1;
+        pr.ev_before = tm.take(&k0);
+        pr.ev_after = tm.take(&k1);
+        int blocks = 0;
+        float kms = 0.f;
+        int l0 = tm.mark();
+        RELCP_TRY(lcp_solve(pr, c->lcp, &blocks, &kms, s));
+        int l1 = tm.mark();
+        lcp_marks.push_back({l0, l1});
+        lcpk_marks.push_back({k0, k1});
 
         // trial configuration and overlap test
         TrialArgs ta{};
@@ -404,51 +437,74 @@ relcp_status step_once(relcp_ctx* c) {
         sb.out = snsd_out(c->s1, c->it1);
         sb.eps = cfg.eps_ncp;
         sb.viol = c->flags.p;
-        sb.block_maxov = c->blockmax.p;
-        int nblocks = 0;
+        sb.maxov_bits = &ds->maxov_bits;
+        RELCP_CUDA(cudaMemsetAsync(&ds->maxov_bits, 0, sizeof(unsigned long long), s));
         {
             int e0 = tm.mark();
-            RELCP_TRY(snsd_launch(sb, &nblocks, s));
-            int e1 = tm.mark();
-            snsd_marks.push_back({e0, e1});
-            st.snsd_evals += tm.on ? np : 0;
+            RELCP_TRY(snsd_launch(sb, s));
+            snsd_marks.push_back({e0, tm.mark()});
         }
-        RELCP_TRY(iters_max_launch(np, c->it1.p, c->imax.p, s));
-        RELCP_TRY(max_blocks_launch(np > 0 ? nblocks : 0, c->blockmax.p, c->scal.p, s));
-        RELCP_TRY(exclusive_scan(c->flags.p, c->fscan.p, np, c->scan, s));
         int nv = 0;
-        RELCP_CUDA(cudaMemcpyAsync(&nv, c->fscan.p + np, sizeof(int), cudaMemcpyDeviceToHost, s));
-        RELCP_CUDA(cudaMemcpyAsync(&maxov, c->scal.p, sizeof(double), cudaMemcpyDeviceToHost, s));
+        if (np > 0) {
+            RELCP_TRY(exclusive_scan(c->flags.p, c->fscan.p, np, c->scan, s));
+            RELCP_CUDA(cudaMemcpyAsync(&nv, c->fscan.p + np, sizeof(int), cudaMemcpyDeviceToHost, s));
+        }
+        RELCP_CUDA(cudaMemcpyAsync(&hs, ds, sizeof(DevStep), cudaMemcpyDeviceToHost, s));
+        t_last = tm.mark();
         RELCP_CUDA(cudaStreamSynchronize(s));
-        int t_s1 = tm.mark();
-        ms_snsd += tm.ms(t_l1, t_s1);
+        c->nrows = hs.nrows;
+        if (depth == 0) c->nrows0 = hs.nrows;
+        if (depth < RELCP_MAX_DEPTH_STATS) {
+            st.lcp_iters[depth] = (int)hs.lcp.iterations;
+            st.rows_per_rec[depth] = hs.nrows;
+        }
+        lcp_iters_total += (int)hs.lcp.iterations;
+        if (tm.on && hs.nrows > 0) {
+            st.ms_lcp_kernel += tm.ms(k0, k1);
+            st.lcp_alg_bytes += lcp_bytes_per_iter(hs.nrows, n, mixed) * (hs.lcp.iterations + 1);
+            st.lcp_launches += 1;
+        }
+        if (hs.status & DEV_TIMEOUT) {
+            set_error("LCP grid barrier timed out");
+            tm.stop();
+            return RELCP_ERR_TIMEOUT;
+        }
         if (nv == 0) break;
         if (depth >= cfg.max_recursion) {
-            if (step_status == RELCP_OK) step_status = RELCP_ERR_RECURSION_LIMIT;
+            step_status = RELCP_ERR_RECURSION_LIMIT;
             break;
         }
         ++depth;
         RELCP_TRY(grow_rows(c, c->nrows + nv));
         RowsArgs rb2 = ra;
+        rb2.prev_n = 0;
+        bind_rows(rb2);
         rb2.snsd = c->s1.p;
         rb2.base = c->nrows;
-        rb2.cap = c->rcap;
         rb2.rec_index = depth;
-        rb2.ia = c->r_ia.p;
-        rb2.ib = c->r_ib.p;
-        rb2.rec = c->r_rec.p;
-        rb2.pair = c->r_pair.p;
-        rb2.geom = c->r_geom.p;
-        rb2.q = c->r_q.p;
-        rb2.diag = c->r_diag.p;
-        rb2.gamma = c->r_gamma.p;
         RELCP_TRY(rows_launch(rb2, s));
-        c->nrows += nv;
-        int t_a = tm.mark();
-        ms_aug += tm.ms(t_s1, t_a);
+        m_bound = c->nrows + nv;
     }
 
-    // accept
+    // keep the A_0 rows' final gamma for the next step's warm start
+    {
+        RELCP_TRY(c->next_keys.ensure((size_t)(c->nrows0 > 0 ? c->nrows0 : 1), s));
+        RELCP_TRY(c->next_gamma.ensure((size_t)(c->nrows0 > 0 ? c->nrows0 : 1), s));
+        SaveWarmArgs sw{};
+        sw.nrows0_dev = &ds->nrows0;  // |A_0|, copied on the device after the A_0 row kernel
+        sw.ia = c->r_ia.p;
+        sw.ib = c->r_ib.p;
+        sw.gamma = mixed ? nullptr : c->r_gamma.p;
+        sw.gammaf = mixed ? c->r_gammaf.p : nullptr;
+        sw.keys = c->next_keys.p;
+        sw.gout = c->next_gamma.p;
+        RELCP_TRY(save_warm_launch(sw, c->nrows0, s));
+        std::swap(c->prev_keys, c->next_keys);
+        std::swap(c->prev_gamma, c->next_gamma);
+        c->prev_n = c->nrows0;
+    }
+
+    // accept C^{k+1} (no synchronisation: the next call queues behind it)
     AcceptArgs aa{};
     aa.n = n;
     aa.inertial = cfg.dynamics == RELCP_INERTIAL;
@@ -460,32 +516,29 @@ relcp_status step_once(relcp_ctx* c) {
     aa.q = c->q.p;
     aa.vel = c->vel.p;
     RELCP_TRY(accept_launch(aa, s));
-    int t_end = tm.mark();
-    int dbits = 0, imax = 0;
-    RELCP_CUDA(cudaMemcpyAsync(&dbits, c->dstatus.p, sizeof(int), cudaMemcpyDeviceToHost, s));
-    RELCP_CUDA(cudaMemcpyAsync(&imax, c->imax.p, sizeof(int), cudaMemcpyDeviceToHost, s));
-    RELCP_CUDA(cudaStreamSynchronize(s));
     for (int k = 0; k < 3; ++k) c->box[k] = box1[k];
-    relcp_status ds = status_from_device(dbits);
-    if (step_status == RELCP_OK) step_status = ds;
+    relcp_status dstat = status_from_device(hs.status);
+    if (step_status == RELCP_OK) step_status = dstat;
     st.n_rows = c->nrows;
+    st.n_rows0 = c->nrows0;
     st.depth = depth;
     st.status = step_status;
     st.lcp_iters_total = lcp_iters_total;
-    st.newton_iters_max = imax;
-    st.lcp_residual = lr.residual;
-    st.max_overlap = maxov;
+    st.newton_iters_max = hs.newton_max;
+    st.lcp_residual = hs.lcp.residual;
+    st.max_overlap = __builtin_bit_cast(double, hs.maxov_bits);
     for (int k = 0; k < 3; ++k) st.box[k] = c->box[k];
-    st.ms_broadphase = tm.ms(t_begin, t_bp);
-    st.ms_snsd = ms_snsd;
-    st.ms_lcp = ms_lcp;
-    st.ms_augment = ms_aug;
-    st.ms_total = tm.ms(t_begin, t_end);
-    for (auto& mk : snsd_marks) {
-        if (mk.first >= 0 && mk.second >= 0) {
+    if (tm.on) {
+        st.ms_broadphase = tm.ms(t_begin, t_bp);
+        st.ms_total = tm.ms(t_begin, t_last);
+        for (auto& mk : snsd_marks) {
             st.ms_snsd_kernel += tm.ms(mk.first, mk.second);
             st.snsd_launches += 1;
+            st.snsd_evals += np;
         }
+        st.ms_snsd = st.ms_snsd_kernel;
+        for (auto& mk : lcp_marks) st.ms_lcp += tm.ms(mk.first, mk.second);
+        st.ms_augment = st.ms_total - st.ms_broadphase - st.ms_snsd - st.ms_lcp;
     }
     tm.stop();
     c->steps_done += 1;
@@ -528,9 +581,7 @@ relcp_status relcp_create(const relcp_config* cfg, void* cuda_stream, relcp_ctx*
     c->cfg = *cfg;
     c->s = (cudaStream_t)cuda_stream;
     for (int k = 0; k < 3; ++k) c->box[k] = cfg->box[k];
-    relcp_status st = c->dstatus.ensure(1, c->s);
-    if (st == RELCP_OK) st = c->imax.ensure(1, c->s);
-    if (st == RELCP_OK) st = c->scal.ensure(4, c->s);
+    relcp_status st = c->dstep.ensure(1, c->s);
     if (st != RELCP_OK) {
         delete c;
         return st;
@@ -616,6 +667,10 @@ relcp_status relcp_set_bodies(relcp_ctx* c, int64_t n, const int32_t* scene_offs
         RELCP_TRY(wrap_launch(n, c->x.p, c->box, s));
         RELCP_CUDA(cudaStreamSynchronize(s));  // host staging buffers go out of scope
     }
+    c->prev_n = 0;
+    c->bp.valid = false;
+    c->rb_max = 0.0;
+    for (size_t i = 0; i < ha.size(); ++i) c->rb_max = ha[i] > c->rb_max ? ha[i] : c->rb_max;
     c->n = n;
     c->has_bodies = true;
     c->steps_done = 0;
@@ -717,7 +772,17 @@ relcp_status relcp_get_rows(relcp_ctx* c, int32_t* ids, double* geom, double* ga
         RELCP_CUDA(cudaMemcpy2DAsync(geom + 10, 11 * sizeof(double), c->r_diag.p, sizeof(double), sizeof(double), m,
                                      cudaMemcpyDefault, s));
     }
-    if (gamma) RELCP_CUDA(cudaMemcpyAsync(gamma, c->r_gamma.p, m * sizeof(double), cudaMemcpyDefault, s));
+    if (gamma) {
+        if (c->cfg.precision == RELCP_MIXED && c->r_gammaf.p) {
+            std::vector<float> gf((size_t)m);
+            RELCP_CUDA(cudaMemcpyAsync(gf.data(), c->r_gammaf.p, m * sizeof(float), cudaMemcpyDeviceToHost, s));
+            RELCP_CUDA(cudaStreamSynchronize(s));
+            std::vector<double> gd(gf.begin(), gf.end());
+            RELCP_CUDA(cudaMemcpyAsync(gamma, gd.data(), m * sizeof(double), cudaMemcpyDefault, s));
+        } else {
+            RELCP_CUDA(cudaMemcpyAsync(gamma, c->r_gamma.p, m * sizeof(double), cudaMemcpyDefault, s));
+        }
+    }
     RELCP_CUDA(cudaStreamSynchronize(s));
     return RELCP_OK;
 }
@@ -738,21 +803,31 @@ void relcp_destroy(relcp_ctx* c) {
     if (!c) return;
     cudaStream_t s = c->s;
     DBuf<double>* dbs[] = {&c->x, &c->q, &c->axes, &c->vel, &c->fext, &c->P, &c->K, &c->rb, &c->ufree, &c->uc,
-                           &c->ustep, &c->xt, &c->qt, &c->Pt, &c->s0, &c->s1, &c->blockmax, &c->scal,
-                           &c->r_geom, &c->r_q, &c->r_diag, &c->r_gamma, &c->lcp.gamma2, &c->lcp.g2,
-                           &c->lcp.partials, &c->lcp.result};
+                           &c->ustep, &c->xt, &c->qt, &c->Pt, &c->s0, &c->s1, &c->r_geom, &c->r_q, &c->r_diag,
+                           &c->r_gamma};
     for (auto* b : dbs) b->release(s);
-    DBuf<int>* ibs[] = {&c->pa, &c->pb, &c->it0, &c->it1, &c->flags, &c->fscan, &c->dstatus, &c->imax, &c->r_ia,
-                        &c->r_ib, &c->r_rec, &c->r_pair, &c->bp.cell_of, &c->bp.cell_count, &c->bp.cell_start,
-                        &c->bp.cell_cursor, &c->bp.cell_body, &c->bp.pair_count, &c->bp.pair_off,
-                        &c->bp.scan.partial, &c->lcp.inc_count, &c->lcp.inc_off, &c->lcp.inc_cursor, &c->lcp.inc,
-                        &c->lcp.status, &c->lcp.scan.partial, &c->scan.partial};
+    DBuf<int>* ibs[] = {&c->pa, &c->pb, &c->it0, &c->it1, &c->flags, &c->fscan, &c->r_ia, &c->r_ib, &c->r_rec,
+                        &c->r_pair, &c->bp.cell_of, &c->bp.cell_count, &c->bp.cell_start, &c->bp.cell_cursor,
+                        &c->bp.cell_body, &c->bp.pair_count, &c->bp.pair_off, &c->bp.scan.partial,
+                        &c->scan.partial, &c->bp.vpa, &c->bp.vpb, &c->bp.vflag, &c->bp.vscan};
     for (auto* b : ibs) b->release(s);
-    DBuf<float>* fbs[] = {&c->lcp.gammaf, &c->lcp.gf, &c->lcp.ucf, &c->lcp.geomf};
-    for (auto* b : fbs) b->release(s);
-    c->lcp.barrier.release(s);
+    c->r_geomf.release(s);
+    c->r_gammaf.release(s);
+    c->r_qf.release(s);
+    c->Kf.release(s);
+    c->r_invd.release(s);
+    c->r_invdf.release(s);
+    c->dstep.release(s);
+    c->bp.xb.release(s);
+    c->bp.dmax.release(s);
+    c->prev_keys.release(s);
+    c->next_keys.release(s);
+    c->prev_gamma.release(s);
+    c->next_gamma.release(s);
+    release(c->lcp, s);
     mlp_release(c->mlp, s);
     cudaStreamSynchronize(s);
+    for (cudaEvent_t e : c->events) cudaEventDestroy(e);
     delete c;
 }
 
@@ -767,7 +842,7 @@ relcp_status relcp_broadphase(int64_t n, const double* x, const double* rb, cons
     BroadphaseScratch sc;
     DBuf<int> pa, pb;
     int64_t np = 0;
-    relcp_status st = broadphase(n, View<3, const double>::aos(x, 3), rb, box3, skin, pa, pb, &np, sc, s);
+    relcp_status st = broadphase(n, View<3, const double>::aos(x, 3), rb, 0.0, box3, skin, pa, pb, &np, sc, s);
     *n_out = np;
     if (st == RELCP_OK && np > cap) st = RELCP_ERR_CAPACITY;
     if (st == RELCP_OK && np > 0) {
@@ -820,7 +895,9 @@ relcp_status relcp_snsd_eval(int64_t npairs, const int32_t* pairs, int64_t n, co
     a.out.rb = View<3, double>::aos(out + 7, 10);
     a.out.iters = iters;
     a.status = status.p;
-    relcp_status st = snsd_launch(a, nullptr, s);
+    a.maxov_bits = nullptr;
+    a.newton_max = nullptr;
+    relcp_status st = snsd_launch(a, s);
     int bits = 0;
     if (st == RELCP_OK) {
         RELCP_CUDA(cudaMemcpyAsync(&bits, status.p, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -841,39 +918,162 @@ relcp_status relcp_lcp_solve(int64_t nrows, int64_t nbodies, const int32_t* ia, 
         return set_error("bad argument"), RELCP_ERR_INVALID_ARG;
     if (!(tol > 0) || max_iter < 1 || !(c > 0)) return set_error("tol, c > 0 and max_iter >= 1"), RELCP_ERR_INVALID_ARG;
     if (precision != RELCP_FP64 && precision != RELCP_MIXED) return set_error("bad precision"), RELCP_ERR_INVALID_ARG;
+    if (nrows > ((int64_t)1 << 29)) return set_error("too many rows"), RELCP_ERR_INVALID_ARG;
     cudaStream_t s = (cudaStream_t)stream;
+    const bool mixed = precision == RELCP_MIXED;
+    const int64_t m = nrows, nb = nbodies, ma = m > 0 ? m : 1, nba = nb > 0 ? nb : 1;
+    // SoA copies of the rows (in the solve precision) and of K; diagonal
+    DBuf<double> gd, kd, diag, ucd, gam;
+    DBuf<float> gf, gamf, qf, kf;
+    DBuf<int> cnt;
+    DBuf<LcpDevResult> res;
+    DBuf<int> dst;
     LcpScratch sc;
-    LcpProblem pr{};
-    pr.nrows = nrows;
-    pr.nbodies = nbodies;
-    pr.ia = ia;
-    pr.ib = ib;
-    pr.geom = View<9, const double>::aos(geom, 9);
-    pr.q = qv;
-    pr.diag = nullptr;
-    pr.K = View<7, const double>::aos(K, 7);
-    pr.c = c;
-    pr.mixed = precision == RELCP_MIXED;
-    pr.tol = tol;
-    pr.max_iter = max_iter;
-    pr.gamma = gamma;
-    pr.uc = View<6, double>::aos(uc, 6);
-    LcpResult lr{};
-    relcp_status st = lcp_solve(pr, sc, &lr, s);
-    DBuf<int>* ib_[] = {&sc.inc_count, &sc.inc_off, &sc.inc_cursor, &sc.inc, &sc.status, &sc.scan.partial};
-    for (auto* b : ib_) b->release(s);
-    DBuf<double>* db_[] = {&sc.gamma2, &sc.g2, &sc.partials, &sc.result};
-    for (auto* b : db_) b->release(s);
-    DBuf<float>* fb_[] = {&sc.gammaf, &sc.gf, &sc.ucf, &sc.geomf};
-    for (auto* b : fb_) b->release(s);
-    sc.barrier.release(s);
+    relcp_status st = RELCP_OK;
+    auto fail = [&](relcp_status e) {
+        st = e;
+        return e;
+    };
+    do {
+        if (fail(gd.ensure(9 * ma, s)) || fail(kd.ensure(7 * nba, s)) || fail(diag.ensure(ma, s)) ||
+            fail(ucd.ensure(6 * nba, s)) || fail(cnt.ensure(1, s)) || fail(res.ensure(1, s)) ||
+            fail(dst.ensure(1, s)))
+            break;
+        cudaError_t e = cudaSuccess;
+        for (int k = 0; k < 9 && e == cudaSuccess && m > 0; ++k)
+            e = cudaMemcpy2DAsync(gd.p + k * m, sizeof(double), geom + k, 9 * sizeof(double), sizeof(double), m,
+                                  cudaMemcpyDeviceToDevice, s);
+        for (int k = 0; k < 7 && e == cudaSuccess && nb > 0; ++k)
+            e = cudaMemcpy2DAsync(kd.p + k * nb, sizeof(double), K + k, 7 * sizeof(double), sizeof(double), nb,
+                                  cudaMemcpyDeviceToDevice, s);
+        int mi = (int)m;
+        if (e == cudaSuccess) e = cudaMemcpyAsync(cnt.p, &mi, sizeof(int), cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess) e = cudaMemsetAsync(dst.p, 0, sizeof(int), s);
+        if (e != cudaSuccess) {
+            set_error("%s", cudaGetErrorString(e));
+            st = RELCP_ERR_CUDA;
+            break;
+        }
+        if (fail(lcp_diag_launch(m, ia, ib, View<9, const double>::aos(geom, 9), View<7, const double>::aos(K, 7), c,
+                                 diag.p, s)))
+            break;
+        LcpProblem pr{};
+        pr.m_cap = m;
+        pr.nrows_dev = cnt.p;
+        pr.nbodies = nb;
+        pr.ia = ia;
+        pr.ib = ib;
+        if (mixed) {
+            if (fail(gf.ensure(9 * ma, s)) || fail(gamf.ensure(ma, s)) || fail(qf.ensure(ma, s)) ||
+                fail(kf.ensure(7 * nba, s)))
+                break;
+            {
+                std::vector<double> hk((size_t)(7 * nb));
+                std::vector<float> hkf((size_t)(7 * nb));
+                if (nb > 0) {
+                    e = cudaMemcpyAsync(hk.data(), kd.p, 7 * nb * sizeof(double), cudaMemcpyDeviceToHost, s);
+                    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+                    for (size_t i = 0; i < hk.size(); ++i) hkf[i] = (float)hk[i];
+                    if (e == cudaSuccess)
+                        e = cudaMemcpyAsync(kf.p, hkf.data(), 7 * nb * sizeof(float), cudaMemcpyHostToDevice, s);
+                    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+                }
+            }
+            std::vector<double> hgd((size_t)(9 * m)), hg((size_t)m), hq((size_t)m);
+            std::vector<float> hgf((size_t)(9 * m)), hgamf((size_t)m), hqf((size_t)m);
+            // host round trip for the one-time conversion of a stateless call
+            if (m > 0) {
+                e = cudaMemcpyAsync(hgd.data(), gd.p, 9 * m * sizeof(double), cudaMemcpyDeviceToHost, s);
+                if (e == cudaSuccess) e = cudaMemcpyAsync(hg.data(), gamma, m * sizeof(double), cudaMemcpyDeviceToHost, s);
+                if (e == cudaSuccess) e = cudaMemcpyAsync(hq.data(), qv, m * sizeof(double), cudaMemcpyDeviceToHost, s);
+                if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+                for (size_t i = 0; i < hgd.size(); ++i) hgf[i] = (float)hgd[i];
+                for (size_t i = 0; i < hg.size(); ++i) hgamf[i] = (float)hg[i];
+                for (size_t i = 0; i < hq.size(); ++i) hqf[i] = (float)hq[i];
+                if (e == cudaSuccess) e = cudaMemcpyAsync(qf.p, hqf.data(), m * sizeof(float), cudaMemcpyHostToDevice, s);
+                if (e == cudaSuccess) e = cudaMemcpyAsync(gf.p, hgf.data(), 9 * m * sizeof(float), cudaMemcpyHostToDevice, s);
+                if (e == cudaSuccess) e = cudaMemcpyAsync(gamf.p, hgamf.data(), m * sizeof(float), cudaMemcpyHostToDevice, s);
+                if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+            }
+            if (e != cudaSuccess) {
+                set_error("%s", cudaGetErrorString(e));
+                st = RELCP_ERR_CUDA;
+                break;
+            }
+            for (int k = 0; k < 9; ++k) pr.geom[k] = gf.p + k * m;
+            pr.gamma = gamf.p;
+            pr.qr = qf.p;
+            for (int k = 0; k < 7; ++k) pr.Kr[k] = kf.p + k * nb;
+        } else {
+            if (fail(gam.ensure(ma, s))) break;
+            if (m > 0) e = cudaMemcpyAsync(gam.p, gamma, m * sizeof(double), cudaMemcpyDeviceToDevice, s);
+            for (int k = 0; k < 9; ++k) pr.geom[k] = gd.p + k * m;
+            pr.gamma = gam.p;
+            pr.qr = qv;
+            for (int k = 0; k < 7; ++k) pr.Kr[k] = kd.p + k * nb;
+        }
+        pr.q = qv;
+        pr.diag = diag.p;
+        pr.invd = nullptr;
+        for (int k = 0; k < 7; ++k) pr.K[k] = kd.p + k * nb;
+        pr.c = c;
+        pr.mixed = mixed;
+        pr.tol = tol;
+        pr.max_iter = max_iter;
+        for (int k = 0; k < 6; ++k) pr.uc[k] = ucd.p + k * nb;
+        pr.result = res.p;
+        pr.status = dst.p;
+        pr.ev_before = pr.ev_after = nullptr;
+        int blocks = 0;
+        float kms = 0.f;
+        if (fail(lcp_solve(pr, sc, &blocks, &kms, s))) break;
+        LcpDevResult hr{};
+        int hst = 0;
+        e = cudaMemcpyAsync(&hr, res.p, sizeof(hr), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&hst, dst.p, sizeof(int), cudaMemcpyDeviceToHost, s);
+        for (int k = 0; k < 6 && e == cudaSuccess && nb > 0; ++k)
+            e = cudaMemcpy2DAsync(uc + k, 6 * sizeof(double), ucd.p + k * nb, sizeof(double), sizeof(double), nb,
+                                  cudaMemcpyDeviceToDevice, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e == cudaSuccess && m > 0) {
+            if (mixed) {
+                std::vector<float> hgamf((size_t)m);
+                e = cudaMemcpy(hgamf.data(), gamf.p, m * sizeof(float), cudaMemcpyDeviceToHost);
+                std::vector<double> hg(hgamf.begin(), hgamf.end());
+                if (e == cudaSuccess) e = cudaMemcpy(gamma, hg.data(), m * sizeof(double), cudaMemcpyHostToDevice);
+            } else {
+                e = cudaMemcpyAsync(gamma, gam.p, m * sizeof(double), cudaMemcpyDeviceToDevice, s);
+            }
+        }
+        if (e != cudaSuccess) {
+            set_error("%s", cudaGetErrorString(e));
+            st = RELCP_ERR_CUDA;
+            break;
+        }
+        info->iterations = (int)hr.iterations;
+        info->residual = hr.residual;
+        info->grid_blocks = blocks;
+        info->status = status_from_device(hst);
+        info->pad = 0;
+    } while (0);
+    gd.release(s);
+    kd.release(s);
+    diag.release(s);
+    ucd.release(s);
+    gam.release(s);
+    gf.release(s);
+    gamf.release(s);
+    qf.release(s);
+    kf.release(s);
+    cnt.release(s);
+    res.release(s);
+    dst.release(s);
+    release(sc, s);
     if (cudaStreamSynchronize(s) != cudaSuccess && st == RELCP_OK) st = RELCP_ERR_CUDA;
-    info->iterations = lr.iterations;
-    info->residual = lr.residual;
-    info->grid_blocks = lr.blocks;
-    info->status = st != RELCP_OK ? st : status_from_device(lr.dev_status);
-    info->pad = 0;
-    if (st != RELCP_OK) return st;
+    if (st != RELCP_OK) {
+        info->status = st;
+        return st;
+    }
     return (relcp_status)info->status;
 }
 

@@ -154,10 +154,47 @@ __global__ void max_reduce(int64_t n, const double* __restrict__ v, double* __re
     }
 }
 
+// largest displacement of a body since the Verlet build, the affine box
+// scaling s = L / Lb (per periodic axis) taken out: |min_image(x - s xb)|
+__global__ void disp_kernel(int64_t n, const double* __restrict__ x, const double* __restrict__ xb, double s0,
+                            double s1, double s2, double L0, double L1, double L2, unsigned long long* dmax) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    double d2 = 0.0;
+    if (i < n) {
+        const double sc[3] = {s0, s1, s2}, L[3] = {L0, L1, L2};
+        for (int k = 0; k < 3; ++k) {
+            double d = min_image(x[k * n + i] - sc[k] * xb[k * n + i], L[k]);
+            d2 += d * d;
+        }
+    }
+    double d = sqrt(d2);
+    for (int o = 16; o > 0; o >>= 1) d = fmax(d, __shfl_xor_sync(0xffffffffu, d, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(dmax, (unsigned long long)__double_as_longlong(d));
+}
+
+// exact candidate test on the cached list (same operations as near_pair)
+__global__ void filter_kernel(int64_t nv, const int* __restrict__ vpa, const int* __restrict__ vpb,
+                              View<3, const double> x, const double* __restrict__ rb, double L0, double L1,
+                              double L2, double skin, int* __restrict__ flag) {
+    int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= nv) return;
+    flag[p] = near_pair(x, rb, vpa[p], vpb[p], L0, L1, L2, skin) ? 1 : 0;
+}
+
+__global__ void compact_kernel(int64_t nv, const int* __restrict__ vpa, const int* __restrict__ vpb,
+                               const int* __restrict__ flag, const int* __restrict__ pos, int* __restrict__ pa,
+                               int* __restrict__ pb) {
+    int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= nv || !flag[p]) return;
+    pa[pos[p]] = vpa[p];
+    pb[pos[p]] = vpb[p];
+}
+
 }  // namespace
 
-relcp_status broadphase(int64_t n, View<3, const double> x, const double* rb, const double box[3], double skin,
-                        DBuf<int>& pa, DBuf<int>& pb, int64_t* npairs, BroadphaseScratch& sc, cudaStream_t s) {
+relcp_status broadphase(int64_t n, View<3, const double> x, const double* rb, double rbmax_hint, const double box[3],
+                        double skin, DBuf<int>& pa, DBuf<int>& pb, int64_t* npairs, BroadphaseScratch& sc,
+                        cudaStream_t s) {
     *npairs = 0;
     if (n < 2) return RELCP_OK;
     unsigned nb = (unsigned)((n + kThreads - 1) / kThreads);
@@ -169,15 +206,17 @@ relcp_status broadphase(int64_t n, View<3, const double> x, const double* rb, co
     bool use_cells = false;
     if (periodic && n > 2048) {
         // largest bounding radius decides the cell side
-        DBuf<double> mx;
-        RELCP_TRY(mx.ensure(1, s));
-        note_launch();
-        max_reduce<<<1, 1024, 0, s>>>(n, rb, mx.p);
-        RELCP_CUDA(cudaGetLastError());
-        double rbmax = 0.0;
-        RELCP_CUDA(cudaMemcpyAsync(&rbmax, mx.p, sizeof(double), cudaMemcpyDeviceToHost, s));
-        RELCP_CUDA(cudaStreamSynchronize(s));
-        mx.release(s);
+        double rbmax = rbmax_hint;
+        if (!(rbmax > 0.0)) {
+            DBuf<double> mx;
+            RELCP_TRY(mx.ensure(1, s));
+            note_launch();
+            max_reduce<<<1, 1024, 0, s>>>(n, rb, mx.p);
+            RELCP_CUDA(cudaGetLastError());
+            RELCP_CUDA(cudaMemcpyAsync(&rbmax, mx.p, sizeof(double), cudaMemcpyDeviceToHost, s));
+            RELCP_CUDA(cudaStreamSynchronize(s));
+            mx.release(s);
+        }
         double cut = (2.0 * rbmax + skin) * (1.0 + 1e-9);
         use_cells = true;
         int64_t ncells = 1;
@@ -234,6 +273,93 @@ relcp_status broadphase(int64_t n, View<3, const double> x, const double* rb, co
     }
     RELCP_CUDA(cudaGetLastError());
     return RELCP_OK;
+}
+
+}  // namespace relcp
+
+namespace relcp {
+
+relcp_status broadphase_cached(int64_t n, const double* x_soa, const double* rb, double rbmax, const double box[3],
+                               double skin, DBuf<int>& pa, DBuf<int>& pb, int64_t* npairs, BroadphaseScratch& sc,
+                               cudaStream_t s) {
+    *npairs = 0;
+    if (n < 2) return RELCP_OK;
+    const unsigned nbk = (unsigned)((n + kThreads - 1) / kThreads);
+    View<3, const double> xv = View<3, const double>::soa(x_soa, n);
+    const double cutmax = 2.0 * rbmax + skin;
+    if (sc.vn_bodies != n || sc.skin_b != skin) sc.valid = false;
+    for (int attempt = 0; attempt < 2; ++attempt) {
+        double sfac[3] = {1.0, 1.0, 1.0};
+        bool geom_ok = sc.valid;
+        for (int k = 0; k < 3 && geom_ok; ++k) {
+            if ((box[k] > 0) != (sc.Lb[k] > 0)) geom_ok = false;
+            else if (box[k] > 0) sfac[k] = box[k] / sc.Lb[k];
+        }
+        if (!geom_ok) {
+            // rebuild: candidates within R_i + R_j + skin + delta at the current positions
+            sc.delta = 0.15 * cutmax;
+            int64_t nv = 0;
+            RELCP_TRY(broadphase(n, xv, rb, rbmax, box, skin + sc.delta, sc.vpa, sc.vpb, &nv, sc, s));
+            sc.vn = nv;
+            RELCP_TRY(sc.xb.ensure((size_t)(3 * n), s));
+            RELCP_CUDA(cudaMemcpyAsync(sc.xb.p, x_soa, 3 * n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+            for (int k = 0; k < 3; ++k) sc.Lb[k] = box[k];
+            sc.vn_bodies = n;
+            sc.skin_b = skin;
+            sc.valid = true;
+            sc.rebuilds += 1;
+            for (int k = 0; k < 3; ++k) sfac[k] = 1.0;
+        }
+        const int64_t nv = sc.vn;
+        const int64_t nva = nv > 0 ? nv : 1;
+        RELCP_TRY(sc.vflag.ensure((size_t)nva, s));
+        RELCP_TRY(sc.vscan.ensure((size_t)nva + 1, s));
+        RELCP_TRY(sc.dmax.ensure(1, s));
+        RELCP_CUDA(cudaMemsetAsync(sc.dmax.p, 0, sizeof(unsigned long long), s));
+        note_launch();
+        disp_kernel<<<nbk, kThreads, 0, s>>>(n, x_soa, sc.xb.p, sfac[0], sfac[1], sfac[2], box[0], box[1], box[2],
+                                              sc.dmax.p);
+        RELCP_CUDA(cudaGetLastError());
+        if (nv > 0) {
+            note_launch();
+            filter_kernel<<<(unsigned)((nv + kThreads - 1) / kThreads), kThreads, 0, s>>>(
+                nv, sc.vpa.p, sc.vpb.p, xv, rb, box[0], box[1], box[2], skin, sc.vflag.p);
+            RELCP_CUDA(cudaGetLastError());
+        }
+        RELCP_TRY(exclusive_scan(sc.vflag.p, sc.vscan.p, nv, sc.scan, s));
+        int total = 0;
+        unsigned long long dbits = 0;
+        RELCP_CUDA(cudaMemcpyAsync(&total, sc.vscan.p + nv, sizeof(int), cudaMemcpyDeviceToHost, s));
+        RELCP_CUDA(cudaMemcpyAsync(&dbits, sc.dmax.p, sizeof(dbits), cudaMemcpyDeviceToHost, s));
+        RELCP_CUDA(cudaStreamSynchronize(s));
+        double dmax = __builtin_bit_cast(double, dbits);
+        // the cached list holds every pair with |d_b| <= cut + delta; a pair in
+        // range now has |d_b| <= (cut + 2 dmax) / s, so the list is complete if
+        // cut |1/s - 1| + 2 dmax / s <= delta (with a 10% margin)
+        double smin = 1.0, grow = 0.0;
+        for (int k = 0; k < 3; ++k) {
+            smin = fmin(smin, sfac[k]);
+            grow = fmax(grow, fabs(1.0 / sfac[k] - 1.0));
+        }
+        bool ok = cutmax * grow + 2.0 * dmax / smin <= 0.9 * sc.delta;
+        if (!ok) {
+            sc.valid = false;
+            continue;
+        }
+        *npairs = total;
+        if (total > 0) {
+            RELCP_TRY(pa.ensure((size_t)total, s));
+            RELCP_TRY(pb.ensure((size_t)total, s));
+            note_launch();
+            compact_kernel<<<(unsigned)((nv + kThreads - 1) / kThreads), kThreads, 0, s>>>(nv, sc.vpa.p, sc.vpb.p,
+                                                                                          sc.vflag.p, sc.vscan.p,
+                                                                                          pa.p, pb.p);
+            RELCP_CUDA(cudaGetLastError());
+        }
+        return RELCP_OK;
+    }
+    set_error("Verlet list rebuilt but the displacement bound still fails");
+    return RELCP_ERR_CUDA;
 }
 
 }  // namespace relcp

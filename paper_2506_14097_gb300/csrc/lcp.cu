@@ -29,88 +29,114 @@ namespace relcp {
 
 namespace {
 
-constexpr int kThreads = 256;
+constexpr int kThreads = 768;
+constexpr int kMaxCtasPerSm = 1;
+constexpr int kMixedCheckEvery = 4;  // mixed path: FP64 termination residual every 4th iteration
 constexpr int kNred = 4;  // ss, sy, yy, residual-or-maxdiag
-constexpr long long kSpinLimit = 1ll << 24;
+constexpr long long kSpinLimit = 1ll << 26;
+
+template <class R>
+struct Vec2;
+template <>
+struct Vec2<float> {
+    using T = float2;
+};
+template <>
+struct Vec2<double> {
+    using T = double2;
+};
 
 template <class R>
 struct KArgs {
-    int nrows, nbodies;
+    int nbodies;
+    const int* nrows_dev;  // number of rows, read once at kernel start
     const int* __restrict__ ia;
     const int* __restrict__ ib;
     const R* geom[9];
-    const double* __restrict__ q;
+    const double* __restrict__ q;     // offsets (FP64)
+    const R* __restrict__ qr;          // offsets in the solve precision (== q when R = double)
     const double* __restrict__ diag;
-    const double* K[7];
+    const R* __restrict__ invd;  // 1 / A_aa in the solve precision (Jacobi-scaled steps) or null
+    const R* K[7];     // body operator in the solve precision
     const int* __restrict__ inc_off;
     const int* __restrict__ inc;
-    R* gam[2];
-    R* g[2];
-    R* uc[6];
-    int64_t uc_stride;
+    R* gamma_io;         // caller's gamma (in: warm start, out: solution), SoA
+    typename Vec2<R>::T* gg[2];  // (gamma, g) per row, double-buffered
+    R* ucp;              // contact velocity, one 8-wide record per body (6 used)
+    double* ucd[6];      // double output (SoA)
     double c, tol;
     int max_iter;
+    int check_every;  // FP64 residual on every check_every-th iteration (and the first)
     double* partials;
     unsigned* bar;
     int* status;
-    double* result;  // iterations, residual, final buffer
+    LcpDevResult* result;
 };
 
 __device__ __forceinline__ double ldcg(const double* p) { return __ldcg(p); }
 __device__ __forceinline__ float ldcg(const float* p) { return __ldcg(p); }
 
-// bounded sense-free grid barrier (count + generation); false on timeout
-__device__ bool grid_barrier(unsigned* bar, int* status) {
+__device__ __forceinline__ void red_add_relaxed(unsigned* p, unsigned v) {
+    asm volatile("red.relaxed.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ unsigned ld_relaxed(const unsigned* p) {
+    unsigned v;
+    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Bounded grid barrier on a monotonic arrival counter (zeroed before the
+// launch): barrier number e of the launch completes when the counter reaches
+// e * gridDim.x.  Thread 0 of each block publishes the block's writes (fence,
+// then a relaxed add), polls with relaxed loads (no cache invalidation per
+// poll) and fences once when the count is reached.  It sleeps only after a
+// short busy spin and gives up after kSpinLimit polls (DEV_TIMEOUT).
+__device__ bool grid_barrier(unsigned* count, unsigned* epoch, int* status) {
     __shared__ int timed_out;
     __syncthreads();
     if (threadIdx.x == 0) {
         timed_out = 0;
-        volatile unsigned* vgen = bar + 1;
-        unsigned gen = *vgen;
+        const unsigned target = (++(*epoch)) * gridDim.x;
         __threadfence();
-        unsigned arrived = atomicAdd(bar, 1u);
-        if (arrived == gridDim.x - 1) {
-            atomicExch(bar, 0u);
-            __threadfence();
-            atomicAdd(bar + 1, 1u);
-        } else {
-            long long spins = 0;
-            while (*vgen == gen) {
-                if (++spins > kSpinLimit) {
-                    atomicOr(status, DEV_TIMEOUT);
-                    timed_out = 1;
-                    break;
-                }
-                __nanosleep(64);
+        red_add_relaxed(count, 1u);
+        long long spins = 0;
+        while (ld_relaxed(count) < target) {
+            if (++spins > kSpinLimit) {
+                atomicOr(status, DEV_TIMEOUT);
+                timed_out = 1;
+                break;
             }
+            if (spins > 256) __nanosleep(16);
         }
         __threadfence();
-        if (*((volatile int*)status) & DEV_TIMEOUT) timed_out = 1;
     }
     __syncthreads();
     return timed_out == 0;
 }
 
-// deterministic block reduction of kNred values; slot k is a max when bit k
-// of maxmask is set, a sum otherwise
-__device__ void block_reduce_store(const double v[kNred], unsigned maxmask, double* out) {
-    __shared__ double sh[kThreads / 32][kNred];
+// Deterministic block reduction of kNred values; slot k is a max when bit k
+// of maxmask is set, a sum otherwise.  A is the accumulation type: the mixed
+// path reduces its FP32 inner products in FP32 inside the block (FP64 is slow
+// on this part); only the per-block results are widened to FP64.
+template <class A>
+__device__ void block_reduce_store(const A v[kNred], unsigned maxmask, double* out) {
+    __shared__ A sh[kThreads / 32][kNred];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
     for (int k = 0; k < kNred; ++k) {
-        double x = v[k];
+        A x = v[k];
         for (int o = 16; o > 0; o >>= 1) {
-            double y = __shfl_down_sync(0xffffffffu, x, o);
-            x = ((maxmask >> k) & 1u) ? fmax(x, y) : x + y;
+            A y = __shfl_down_sync(0xffffffffu, x, o);
+            x = ((maxmask >> k) & 1u) ? (x > y ? x : y) : x + y;
         }
         if (lane == 0) sh[wid][k] = x;
     }
     __syncthreads();
     if (threadIdx.x < kNred) {
         int k = threadIdx.x;
-        double x = sh[0][k];
-        for (int w = 1; w < kThreads / 32; ++w) x = ((maxmask >> k) & 1u) ? fmax(x, sh[w][k]) : x + sh[w][k];
-        out[k] = x;
+        A x = sh[0][k];
+        for (int w = 1; w < kThreads / 32; ++w) x = ((maxmask >> k) & 1u) ? (x > sh[w][k] ? x : sh[w][k]) : x + sh[w][k];
+        out[k] = (double)x;
     }
     __syncthreads();
 }
@@ -144,146 +170,370 @@ __device__ void grid_reduce(const double* partials, unsigned maxmask, double tot
     __syncthreads();
 }
 
-// phase 1: contact velocity of gamma' = P(src - alpha g) (alpha < 0: gamma' = src)
+// ---------------------------------------------------------------------------
+// Per-thread static data.  Every thread owns one body slot (two lanes per
+// body, up to kIncPerLane incidences per lane kept in registers with their
+// signed row coefficients) and one row slot (ids, geometry, offset, 1/A_aa in
+// registers).  They are loaded once per solve; an iteration then only gathers
+// the packed (gamma, g) pairs and the packed contact velocities.  Bodies and
+// rows beyond one slot per thread, and incidences beyond
+// kLanesPerBody x kIncPerLane per body, take the same path with loads.
+//
+// Packed layouts (fewer L2 sectors per access):
+//   gg[buf][r] = (gamma_r, g_r)          one 8-byte (FP32) / 16-byte record
+//   ucp[8 b .. 8 b + 5] = K D gamma of b one 32-byte (FP32) / 64-byte record
+// ---------------------------------------------------------------------------
+constexpr int kLanesPerBody = 2;
+constexpr int kIncPerLane = 4;
+
 template <class R>
-__device__ void scatter_phase(const KArgs<R>& a, const R* src, const R* gsrc, double alpha, R* dst) {
-    const int stride = gridDim.x * blockDim.x;
-    for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < a.nbodies; b += stride) {
-        R f0 = 0, f1 = 0, f2 = 0, t0 = 0, t1 = 0, t2 = 0;
-        const int e0 = a.inc_off[b], e1 = a.inc_off[b + 1];
-        for (int e = e0; e < e1; ++e) {
-            const int code = a.inc[e];
-            const int r = code >> 1;
-            const bool sideb = code & 1;
-            R gm = ldcg(src + r);
-            if (alpha >= 0.0) {
-                R v = gm - (R)alpha * ldcg(gsrc + r);
-                gm = v > R(0) ? v : R(0);
-                if (!sideb) dst[r] = gm;
-            }
-            const R n0 = a.geom[0][r], n1 = a.geom[1][r], n2 = a.geom[2][r];
-            const int o = sideb ? 6 : 3;
-            const R s0 = a.geom[o][r], s1 = a.geom[o + 1][r], s2 = a.geom[o + 2][r];
-            const R sg = sideb ? gm : -gm;
-            f0 += sg * n0;
-            f1 += sg * n1;
-            f2 += sg * n2;
-            t0 += sg * s0;
-            t1 += sg * s1;
-            t2 += sg * s2;
+struct BodySlot {
+    int b;                   // body, or >= nbodies for none
+    int e0, e1;              // CSR range of the body
+    int code[kIncPerLane];   // (row << 1) | side, or -1
+    R c[kIncPerLane][6];     // signed coefficients: side a (-n, -r_a x n), side b (n, r_b x n)
+};
+
+template <class R>
+struct RowSlot {
+    int r;                   // row, or -1
+    int i, j;
+    R g[9];
+    R q, invd;
+};
+
+template <class R>
+__device__ __forceinline__ void load_coefs(const KArgs<R>& a, int code, R c[6]) {
+    const int r = code >> 1;
+    const bool sideb = code & 1;
+    const R sg = sideb ? R(1) : R(-1);
+    const int o = sideb ? 6 : 3;
+    c[0] = sg * a.geom[0][r];
+    c[1] = sg * a.geom[1][r];
+    c[2] = sg * a.geom[2][r];
+    c[3] = sg * a.geom[o][r];
+    c[4] = sg * a.geom[o + 1][r];
+    c[5] = sg * a.geom[o + 2][r];
+}
+
+template <class R>
+__device__ void load_body_slot(const KArgs<R>& a, int b, int lane, BodySlot<R>& S) {
+    S.b = b;
+    S.e0 = S.e1 = 0;
+#pragma unroll
+    for (int k = 0; k < kIncPerLane; ++k) S.code[k] = -1;
+    if (b >= a.nbodies) return;
+    S.e0 = a.inc_off[b];
+    S.e1 = a.inc_off[b + 1];
+#pragma unroll
+    for (int k = 0; k < kIncPerLane; ++k) {
+        const int e = S.e0 + lane + kLanesPerBody * k;
+        if (e < S.e1) {
+            S.code[k] = a.inc[e];
+            load_coefs(a, S.code[k], S.c[k]);
         }
-        const R kt = (R)a.K[0][b];
-        const R kxx = (R)a.K[1][b], kyy = (R)a.K[2][b], kzz = (R)a.K[3][b];
-        const R kxy = (R)a.K[4][b], kxz = (R)a.K[5][b], kyz = (R)a.K[6][b];
-        const int64_t o = (int64_t)b * a.uc_stride;
-        a.uc[0][o] = kt * f0;
-        a.uc[1][o] = kt * f1;
-        a.uc[2][o] = kt * f2;
-        a.uc[3][o] = kxx * t0 + kxy * t1 + kxz * t2;
-        a.uc[4][o] = kxy * t0 + kyy * t1 + kyz * t2;
-        a.uc[5][o] = kxz * t0 + kyz * t1 + kzz * t2;
     }
 }
 
-// phase 2: g' for gamma' (gnew), BB products against (gold, gprev), residual
 template <class R>
-__device__ void gather_phase(const KArgs<R>& a, const R* gnew, const R* gold, const R* gprev, R* gout,
-                             double v[kNred]) {
-    const int stride = gridDim.x * blockDim.x;
-    v[0] = v[1] = v[2] = v[3] = 0.0;
-    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < a.nrows; r += stride) {
-        const int i = a.ia[r], j = a.ib[r];
-        const int64_t oi = (int64_t)i * a.uc_stride, oj = (int64_t)j * a.uc_stride;
-        const R n0 = a.geom[0][r], n1 = a.geom[1][r], n2 = a.geom[2][r];
-        R du0 = ldcg(a.uc[0] + oj) - ldcg(a.uc[0] + oi);
-        R du1 = ldcg(a.uc[1] + oj) - ldcg(a.uc[1] + oi);
-        R du2 = ldcg(a.uc[2] + oj) - ldcg(a.uc[2] + oi);
-        R rate = n0 * du0 + n1 * du1 + n2 * du2;
-        rate += a.geom[6][r] * ldcg(a.uc[3] + oj) + a.geom[7][r] * ldcg(a.uc[4] + oj) + a.geom[8][r] * ldcg(a.uc[5] + oj);
-        rate -= a.geom[3][r] * ldcg(a.uc[3] + oi) + a.geom[4][r] * ldcg(a.uc[4] + oi) + a.geom[5][r] * ldcg(a.uc[5] + oi);
-        const double gd = a.q[r] + a.c * (double)rate;
-        const double gm = (double)ldcg(gnew + r);
-        gout[r] = (R)gd;
-        if (gold) {
-            const double s = gm - (double)ldcg(gold + r);
-            const double y = gd - (double)ldcg(gprev + r);
-            v[0] += s * s;
-            v[1] += s * y;
-            v[2] += y * y;
-        }
-        const double nat = fabs(fmin(a.diag[r] * gm, gd));
-        v[3] = fmax(v[3], nat);
+__device__ void load_row_slot(const KArgs<R>& a, int r, int nrows, RowSlot<R>& S) {
+    S.r = r < nrows ? r : -1;
+    if (S.r < 0) return;
+    S.i = a.ia[r];
+    S.j = a.ib[r];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) S.g[k] = a.geom[k][r];
+    S.q = a.qr[r];
+    S.invd = a.invd ? a.invd[r] : R(1);
+}
+
+template <class R>
+__device__ __forceinline__ typename Vec2<R>::T ld_pair(const typename Vec2<R>::T* p) {
+    return __ldcg(p);
+}
+
+// one incidence: gamma' = P(gamma - alpha g/A_aa) (or gamma), accumulated wrench
+template <class R>
+__device__ __forceinline__ void incidence(const KArgs<R>& a, int code, const R c[6], int src, bool project,
+                                          R alpha_r, R w[6]) {
+    const int r = code >> 1;
+    const typename Vec2<R>::T p = ld_pair<R>(a.gg[src] + r);
+    R gm = p.x;
+    if (project) {
+        R gs = p.y;
+        if (a.invd) gs *= a.invd[r];
+        const R v = gm - alpha_r * gs;
+        gm = v > R(0) ? v : R(0);
+        if (!(code & 1)) a.gg[1 - src][r].x = gm;
     }
+#pragma unroll
+    for (int k = 0; k < 6; ++k) w[k] += gm * c[k];
+}
+
+// 8-wide contact-velocity record: vector load / store (16-byte accesses)
+__device__ __forceinline__ void load_rec(const float* p, float u[6]) {
+    const float4 a = __ldcg(reinterpret_cast<const float4*>(p));
+    const float4 b = __ldcg(reinterpret_cast<const float4*>(p) + 1);
+    u[0] = a.x; u[1] = a.y; u[2] = a.z; u[3] = a.w; u[4] = b.x; u[5] = b.y;
+}
+__device__ __forceinline__ void load_rec(const double* p, double u[6]) {
+    const double2 a = __ldcg(reinterpret_cast<const double2*>(p));
+    const double2 b = __ldcg(reinterpret_cast<const double2*>(p) + 1);
+    const double2 c = __ldcg(reinterpret_cast<const double2*>(p) + 2);
+    u[0] = a.x; u[1] = a.y; u[2] = b.x; u[3] = b.y; u[4] = c.x; u[5] = c.y;
+}
+__device__ __forceinline__ void store_rec(float* p, const float u[6]) {
+    reinterpret_cast<float4*>(p)[0] = make_float4(u[0], u[1], u[2], u[3]);
+    reinterpret_cast<float4*>(p)[1] = make_float4(u[4], u[5], 0.f, 0.f);
+}
+__device__ __forceinline__ void store_rec(double* p, const double u[6]) {
+    reinterpret_cast<double2*>(p)[0] = make_double2(u[0], u[1]);
+    reinterpret_cast<double2*>(p)[1] = make_double2(u[2], u[3]);
+    reinterpret_cast<double2*>(p)[2] = make_double2(u[4], u[5]);
+}
+
+template <class R>
+__device__ __forceinline__ void store_uc(const KArgs<R>& a, int b, const R w[6]) {
+    R K[7];
+#pragma unroll
+    for (int kk = 0; kk < 7; ++kk) K[kk] = a.K[kk][b];
+    R o[6];
+    o[0] = K[0] * w[0];
+    o[1] = K[0] * w[1];
+    o[2] = K[0] * w[2];
+    o[3] = K[1] * w[3] + K[4] * w[4] + K[5] * w[5];
+    o[4] = K[4] * w[3] + K[2] * w[4] + K[6] * w[5];
+    o[5] = K[5] * w[3] + K[6] * w[4] + K[3] * w[5];
+    store_rec(a.ucp + 8 * (int64_t)b, o);
+}
+
+template <class R>
+__device__ __forceinline__ void reduce_lanes(R w[6]) {
+#pragma unroll
+    for (int sh = kLanesPerBody / 2; sh > 0; sh >>= 1)
+#pragma unroll
+        for (int k = 0; k < 6; ++k) w[k] += __shfl_xor_sync(0xffffffffu, w[k], sh);
+}
+
+// phase 1: contact velocity Uc = K D gamma' for every body; gamma' read from
+// buffer src (projected step when `project`), written to buffer 1 - src
+template <class R>
+__device__ void scatter_phase(const KArgs<R>& a, const BodySlot<R>& S, int src, bool project, R alpha_r) {
+    const int lane = threadIdx.x & (kLanesPerBody - 1);
+    {
+        R w[6] = {0, 0, 0, 0, 0, 0};
+#pragma unroll
+        for (int k = 0; k < kIncPerLane; ++k)
+            if (S.code[k] >= 0) incidence(a, S.code[k], S.c[k], src, project, alpha_r, w);
+        for (int e = S.e0 + kLanesPerBody * kIncPerLane + lane; e < S.e1; e += kLanesPerBody) {
+            const int code = a.inc[e];
+            R c[6];
+            load_coefs(a, code, c);
+            incidence(a, code, c, src, project, alpha_r, w);
+        }
+        reduce_lanes(w);
+        if (S.b < a.nbodies && lane == 0) store_uc(a, S.b, w);
+    }
+    // bodies beyond one slot per thread
+    const int groups_total = (gridDim.x * blockDim.x) / kLanesPerBody;
+    const int gid = (blockIdx.x * blockDim.x + threadIdx.x) / kLanesPerBody;
+    const int warp_first = gid & ~(32 / kLanesPerBody - 1);
+    for (int k = 1; warp_first + k * groups_total < a.nbodies; ++k) {
+        const int b = gid + k * groups_total;
+        R w[6] = {0, 0, 0, 0, 0, 0};
+        if (b < a.nbodies) {
+            const int e0 = a.inc_off[b], e1 = a.inc_off[b + 1];
+            for (int e = e0 + lane; e < e1; e += kLanesPerBody) {
+                const int code = a.inc[e];
+                R c[6];
+                load_coefs(a, code, c);
+                incidence(a, code, c, src, project, alpha_r, w);
+            }
+        }
+        reduce_lanes(w);
+        if (b < a.nbodies && lane == 0) store_uc(a, b, w);
+    }
+}
+
+// phase 2 for one row: g' in the solve precision into buffer nw, BB products
+// against buffer old (if any), FP64 residual on check iterations
+template <class R>
+__device__ __forceinline__ void row_update(const KArgs<R>& a, int r, int i, int j, const R g9[9], R q, R invd, int nw,
+                                           int old, bool check, R acc[3], double& res) {
+    R ui[6], uj[6];
+    load_rec(a.ucp + 8 * (int64_t)i, ui);
+    load_rec(a.ucp + 8 * (int64_t)j, uj);
+    R rate = g9[0] * (uj[0] - ui[0]) + g9[1] * (uj[1] - ui[1]) + g9[2] * (uj[2] - ui[2]);
+    rate += g9[6] * uj[3] + g9[7] * uj[4] + g9[8] * uj[5];
+    rate -= g9[3] * ui[3] + g9[4] * ui[4] + g9[5] * ui[5];
+    const R g = q + (R)a.c * rate;
+    const R gm = ldcg(&a.gg[nw][r].x);
+    a.gg[nw][r].y = g;
+    if (old >= 0) {
+        const typename Vec2<R>::T po = ld_pair<R>(a.gg[old] + r);
+        const R s = gm - po.x;
+        const R y = g - po.y;
+        if (a.invd) {
+            // metric diag(A): s^T D s, s^T y, y^T D^-1 y
+            acc[0] += s * s / invd;
+            acc[1] += s * y;
+            acc[2] += y * y * invd;
+        } else {
+            acc[0] += s * s;
+            acc[1] += s * y;
+            acc[2] += y * y;
+        }
+    }
+    if (check) {
+        const double gd = a.q[r] + a.c * (double)rate;
+        res = fmax(res, fabs(fmin(a.diag[r] * (double)gm, gd)));
+    }
+}
+
+template <class R>
+__device__ void gather_phase(const KArgs<R>& a, const RowSlot<R>& S, const int nrows, int nw, int old, bool check,
+                             R v[3], double* resid) {
+    R acc[3] = {0, 0, 0};
+    double res = 0.0;
+    if (S.r >= 0) row_update(a, S.r, S.i, S.j, S.g, S.q, S.invd, nw, old, check, acc, res);
+    const int stride = gridDim.x * blockDim.x;
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x + stride; r < nrows; r += stride) {
+        R g9[9];
+#pragma unroll
+        for (int k = 0; k < 9; ++k) g9[k] = a.geom[k][r];
+        row_update(a, r, a.ia[r], a.ib[r], g9, a.qr[r], a.invd ? a.invd[r] : R(1), nw, old, check, acc, res);
+    }
+    v[0] = acc[0];
+    v[1] = acc[1];
+    v[2] = acc[2];
+    *resid = res;
 }
 
 template <class R>
 __global__ void __launch_bounds__(kThreads) lcp_kernel(KArgs<R> a) {
     __shared__ double part[kNred];
-    double v[kNred];
+    const int nrows = *a.nrows_dev;
+    unsigned epoch = 0;  // used by thread 0 only
+    R v[3];
+    double res_t;
     double tot[kNred];
+    const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+    const int stride = gridDim.x * blockDim.x;
+    // warm start into the packed buffer
+    for (int r = tid; r < nrows; r += stride) a.gg[0][r].x = a.gamma_io[r];
+    BodySlot<R> bs;
+    RowSlot<R> rs;
+    load_body_slot(a, tid / kLanesPerBody, threadIdx.x & (kLanesPerBody - 1), bs);
+    load_row_slot(a, tid, nrows, rs);
+    if (!grid_barrier(a.bar, &epoch, a.status)) return;
     // ---- init: Uc = K D gamma0, g0, residual, max diagonal
-    scatter_phase(a, a.gam[0], (const R*)nullptr, -1.0, (R*)nullptr);
-    if (!grid_barrier(a.bar, a.status)) return;
-    gather_phase(a, a.gam[0], (const R*)nullptr, (const R*)nullptr, a.g[0], v);
+    scatter_phase(a, bs, 0, false, R(0));
+    if (!grid_barrier(a.bar, &epoch, a.status)) return;
+    gather_phase(a, rs, nrows, 0, -1, true, v, &res_t);
     {
         // init reduces two maxima: slot 0 = largest A_aa, slot 3 = residual
         double md = 0.0;
-        const int stride = gridDim.x * blockDim.x;
-        for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < a.nrows; r += stride) md = fmax(md, a.diag[r]);
-        double w[kNred] = {md, 0.0, 0.0, v[3]};
-        block_reduce_store(w, 0x9u, part);
+        for (int r = tid; r < nrows; r += stride) md = fmax(md, a.diag[r]);
+        double w[kNred] = {md, 0.0, 0.0, res_t};
+        block_reduce_store<double>(w, 0x9u, part);
         if (threadIdx.x == 0)
             for (int k = 0; k < kNred; ++k) a.partials[(size_t)blockIdx.x * kNred + k] = part[k];
     }
-    if (!grid_barrier(a.bar, a.status)) return;
+    if (!grid_barrier(a.bar, &epoch, a.status)) return;
     grid_reduce(a.partials, 0x9u, tot);
-    double resid = tot[3];
-    const double maxdiag = tot[0];
+    // the step length, the residual and the stop decision are computed by
+    // thread 0 of each block (identically in every block: same reduced values)
+    // and broadcast through shared memory, so FP64 scalar work is not repeated
+    // by every thread
+    __shared__ double sh_alpha, sh_resid;
+    __shared__ R sh_alpha_r;
+    __shared__ int sh_stop;
+    double resid = 0.0;
+    if (threadIdx.x == 0) {
+        resid = tot[3];
+        const double alpha = a.invd ? 1.0 : (tot[0] > 0.0 ? 1.0 / tot[0] : 1.0);
+        sh_alpha = alpha;
+        sh_alpha_r = (R)alpha;
+        sh_resid = resid;
+        sh_stop = resid <= a.tol;
+    }
+    __syncthreads();
+    R alpha_r = sh_alpha_r;
     int cur = 0, it = 0;
-    double alpha = maxdiag > 0.0 ? 1.0 / maxdiag : 1.0;
-    if (!(resid <= a.tol)) {
+    if (!sh_stop) {
         for (it = 1; it <= a.max_iter; ++it) {
             // all blocks have read partials before any block rewrites them:
             // the barrier after phase 1 separates the reads from the writes
-            scatter_phase(a, a.gam[cur], a.g[cur], alpha, a.gam[1 - cur]);
-            if (!grid_barrier(a.bar, a.status)) return;
-            gather_phase(a, a.gam[1 - cur], a.gam[cur], a.g[cur], a.g[1 - cur], v);
-            block_reduce_store(v, 0x8u, part);
+            const bool check = (it % a.check_every) == 0 || it == a.max_iter;
+            scatter_phase(a, bs, cur, true, alpha_r);
+            if (!grid_barrier(a.bar, &epoch, a.status)) return;
+            gather_phase(a, rs, nrows, 1 - cur, cur, check, v, &res_t);
+            {
+                R w[kNred] = {v[0], v[1], v[2], R(0)};
+                block_reduce_store<R>(w, 0x0u, part);
+                if (check) {
+                    double wr[kNred] = {0.0, 0.0, 0.0, res_t};
+                    __shared__ double part_r[kNred];
+                    block_reduce_store<double>(wr, 0x8u, part_r);
+                    if (threadIdx.x == 0) part[3] = part_r[3];
+                }
+            }
             if (threadIdx.x == 0)
                 for (int k = 0; k < kNred; ++k) a.partials[(size_t)blockIdx.x * kNred + k] = part[k];
-            if (!grid_barrier(a.bar, a.status)) return;
+            if (!grid_barrier(a.bar, &epoch, a.status)) return;
             grid_reduce(a.partials, 0x8u, tot);
             cur = 1 - cur;
-            resid = tot[3];
-            if (resid <= a.tol) break;
-            const double ss = tot[0], sy = tot[1], yy = tot[2];
-            double na;
-            if (it & 1) na = (sy > 0.0) ? ss / sy : alpha;
-            else na = (yy > 0.0 && sy > 0.0) ? sy / yy : alpha;
-            if (isfinite(na) && na > 0.0) alpha = na;
+            if (threadIdx.x == 0) {
+                int stop = 0;
+                if (check) {
+                    sh_resid = tot[3];
+                    stop = tot[3] <= a.tol;
+                }
+                const double ss = tot[0], sy = tot[1], yy = tot[2];
+                double na;
+                if (it & 1) na = (sy > 0.0) ? ss / sy : sh_alpha;
+                else na = (yy > 0.0 && sy > 0.0) ? sy / yy : sh_alpha;
+                if (isfinite(na) && na > 0.0) sh_alpha = na;
+                sh_alpha_r = (R)sh_alpha;
+                sh_stop = stop;
+            }
+            __syncthreads();
+            alpha_r = sh_alpha_r;
+            if (sh_stop) break;
         }
         if (it > a.max_iter) it = a.max_iter;
     }
+    resid = sh_resid;
+    // outputs: gamma of the last iterate (buffer cur) and the contact velocity
+    // in double; every write of the last iteration happened before the last
+    // grid barrier
+    for (int r = tid; r < nrows; r += stride) a.gamma_io[r] = ldcg(&a.gg[cur][r].x);
+    for (int b = tid; b < a.nbodies; b += stride) {
+        R u[6];
+        load_rec(a.ucp + 8 * (int64_t)b, u);
+#pragma unroll
+        for (int k = 0; k < 6; ++k) a.ucd[k][b] = (double)u[k];
+    }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
-        a.result[0] = (double)it;
-        a.result[1] = resid;
-        a.result[2] = (double)cur;
+        a.result->iterations = (double)it;
+        a.result->residual = resid;
         if (!(resid <= a.tol)) atomicOr(a.status, DEV_LCP_NOT_CONVERGED);
     }
 }
 
 // ---- incidence CSR (rows ascending within each body)
-__global__ void inc_count(int64_t nrows, const int* __restrict__ ia, const int* __restrict__ ib, int* __restrict__ cnt) {
+__global__ void inc_count(const int* __restrict__ nrows_dev, const int* __restrict__ ia, const int* __restrict__ ib,
+                          int* __restrict__ cnt) {
     int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= nrows) return;
+    if (r >= *nrows_dev) return;
     atomicAdd(&cnt[ia[r]], 1);
     atomicAdd(&cnt[ib[r]], 1);
 }
 
-__global__ void inc_fill(int64_t nrows, const int* __restrict__ ia, const int* __restrict__ ib,
+__global__ void inc_fill(const int* __restrict__ nrows_dev, const int* __restrict__ ia, const int* __restrict__ ib,
                          const int* __restrict__ off, int* __restrict__ cursor, int* __restrict__ inc) {
     int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= nrows) return;
+    if (r >= *nrows_dev) return;
     int a = ia[r], b = ib[r];
     inc[off[a] + atomicAdd(&cursor[a], 1)] = (int)(r << 1);
     inc[off[b] + atomicAdd(&cursor[b], 1)] = (int)(r << 1) | 1;
@@ -322,39 +572,11 @@ __global__ void diag_kernel(int64_t nrows, const int* __restrict__ ia, const int
     diag[r] = c * acc;
 }
 
-template <class S, class D>
-__global__ void convert_rows(int64_t n, View<9, const S> in, D* __restrict__ out) {
-    int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= n) return;
-#pragma unroll
-    for (int k = 0; k < 9; ++k) out[(int64_t)k * n + r] = (D)in(k, r);
-}
-
-template <class S, class D>
-__global__ void convert_vec(int64_t n, const S* __restrict__ in, D* __restrict__ out) {
-    int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (r < n) out[r] = (D)in[r];
-}
-
-__global__ void uc_to_double(int64_t n, const float* __restrict__ ucf, View<6, double> uc) {
-    int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (b >= n) return;
-#pragma unroll
-    for (int k = 0; k < 6; ++k) uc(k, b) = (double)ucf[(int64_t)k * n + b];
-}
-
-__global__ void zero_uc(int64_t n, View<6, double> uc) {
-    int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (b >= n) return;
-#pragma unroll
-    for (int k = 0; k < 6; ++k) uc(k, b) = 0.0;
-}
-
 inline unsigned nblk(int64_t n, int t = 256) { return (unsigned)((n + t - 1) / t); }
 
 template <class R>
 relcp_status launch_lcp(KArgs<R>& ka, int64_t work, LcpScratch& sc, cudaStream_t s, int* blocks_out,
-                        bool timed, float* ms) {
+                        cudaEvent_t ev0, cudaEvent_t ev1) {
     int dev = 0;
     RELCP_CUDA(cudaGetDevice(&dev));
     int sms = 0, coop = 0;
@@ -368,28 +590,56 @@ relcp_status launch_lcp(KArgs<R>& ka, int64_t work, LcpScratch& sc, cudaStream_t
     RELCP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, lcp_kernel<R>, kThreads, 0));
     if (per_sm < 1) per_sm = 1;
     int64_t want = (work + kThreads - 1) / kThreads;
-    int64_t maxb = (int64_t)sms * per_sm;
+    // one CTA per SM: fewest arrivals per grid barrier
+    int64_t maxb = (int64_t)sms * (per_sm < kMaxCtasPerSm ? per_sm : kMaxCtasPerSm);
     int blocks = (int)(want < 1 ? 1 : (want > maxb ? maxb : want));
     RELCP_TRY(sc.partials.ensure((size_t)blocks * kNred, s));
     ka.partials = sc.partials.p;
     void* args[] = {&ka};
-    cudaEvent_t e0 = nullptr, e1 = nullptr;
-    if (timed) {
-        RELCP_CUDA(cudaEventCreate(&e0));
-        RELCP_CUDA(cudaEventCreate(&e1));
-        RELCP_CUDA(cudaEventRecord(e0, s));
-    }
+    if (ev0) RELCP_CUDA(cudaEventRecord(ev0, s));
     note_launch();
     RELCP_CUDA(cudaLaunchCooperativeKernel((void*)lcp_kernel<R>, dim3(blocks), dim3(kThreads), args, 0, s));
-    if (timed) {
-        RELCP_CUDA(cudaEventRecord(e1, s));
-        RELCP_CUDA(cudaEventSynchronize(e1));
-        RELCP_CUDA(cudaEventElapsedTime(ms, e0, e1));
-        cudaEventDestroy(e0);
-        cudaEventDestroy(e1);
-    }
+    if (ev1) RELCP_CUDA(cudaEventRecord(ev1, s));
     *blocks_out = blocks;
     return RELCP_OK;
+}
+
+template <class R>
+relcp_status solve_typed(const LcpProblem& pr, LcpScratch& sc, DBuf<R>& pack, int* blocks, float* kernel_ms,
+                         cudaStream_t s) {
+    using V2 = typename Vec2<R>::T;
+    const int64_t mc = pr.m_cap > 0 ? pr.m_cap : 1, nb = pr.nbodies, nba = nb > 0 ? nb : 1;
+    // (gamma, g) pairs for both buffers, then the 8-wide contact-velocity records
+    const size_t pair_elems = (size_t)(2 * mc) * 2;
+    RELCP_TRY(pack.ensure(pair_elems + (size_t)(8 * nba), s));
+    KArgs<R> ka{};
+    ka.nrows_dev = pr.nrows_dev;
+    ka.nbodies = (int)nb;
+    ka.ia = pr.ia;
+    ka.ib = pr.ib;
+    for (int k = 0; k < 9; ++k) ka.geom[k] = (const R*)pr.geom[k];
+    ka.q = pr.q;
+    ka.qr = (const R*)pr.qr;
+    ka.diag = pr.diag;
+    for (int k = 0; k < 7; ++k) ka.K[k] = (const R*)pr.Kr[k];
+    ka.invd = (const R*)pr.invd;
+    ka.inc_off = sc.inc_off.p;
+    ka.inc = sc.inc.p;
+    ka.gamma_io = (R*)pr.gamma;
+    ka.gg[0] = reinterpret_cast<V2*>(pack.p);
+    ka.gg[1] = reinterpret_cast<V2*>(pack.p) + mc;
+    ka.ucp = pack.p + pair_elems;
+    for (int k = 0; k < 6; ++k) ka.ucd[k] = pr.uc[k];
+    ka.c = pr.c;
+    ka.tol = pr.tol;
+    ka.max_iter = pr.max_iter;
+    ka.check_every = sizeof(R) == sizeof(double) ? 1 : kMixedCheckEvery;
+    ka.bar = sc.barrier.p;
+    ka.status = pr.status;
+    ka.result = pr.result;
+    int64_t work = pr.m_cap > kLanesPerBody * nb ? pr.m_cap : kLanesPerBody * nb;
+    (void)kernel_ms;
+    return launch_lcp(ka, work, sc, s, blocks, pr.ev_before, pr.ev_after);
 }
 
 }  // namespace
@@ -403,170 +653,48 @@ relcp_status lcp_diag_launch(int64_t nrows, const int32_t* ia, const int32_t* ib
     return RELCP_OK;
 }
 
-relcp_status lcp_solve(const LcpProblem& pr, LcpScratch& sc, LcpResult* res, cudaStream_t s) {
-    res->iterations = 0;
-    res->residual = 0.0;
-    res->blocks = 0;
-    res->dev_status = 0;
-    res->kernel_ms = 0.f;
-    const int64_t m = pr.nrows, nb = pr.nbodies;
-    if (nb > 0) {
-        note_launch();
-        zero_uc<<<nblk(nb), 256, 0, s>>>(nb, pr.uc);
-        RELCP_CUDA(cudaGetLastError());
-    }
-    if (m == 0) return RELCP_OK;
-    if (m > (int64_t)1 << 29 || nb > (int64_t)1 << 30) return RELCP_ERR_INVALID_ARG;
-
-    // incidence CSR
-    RELCP_TRY(sc.inc_count.ensure((size_t)nb, s));
-    RELCP_TRY(sc.inc_cursor.ensure((size_t)nb, s));
-    RELCP_TRY(sc.inc_off.ensure((size_t)nb + 1, s));
-    RELCP_TRY(sc.inc.ensure((size_t)(2 * m), s));
-    RELCP_CUDA(cudaMemsetAsync(sc.inc_count.p, 0, nb * sizeof(int), s));
-    RELCP_CUDA(cudaMemsetAsync(sc.inc_cursor.p, 0, nb * sizeof(int), s));
+// Incidence CSR of the current rows (device row count), then the persistent
+// solve.  Nothing here synchronises the stream.
+relcp_status lcp_solve(const LcpProblem& pr, LcpScratch& sc, int* blocks, float* kernel_ms, cudaStream_t s) {
+    *blocks = 0;
+    *kernel_ms = 0.f;
+    const int64_t mc = pr.m_cap > 0 ? pr.m_cap : 1, nb = pr.nbodies;
+    if (pr.m_cap > (int64_t)1 << 29 || nb > (int64_t)1 << 30) return RELCP_ERR_INVALID_ARG;
+    const int64_t nba = nb > 0 ? nb : 1;
+    RELCP_TRY(sc.inc_count.ensure((size_t)nba, s));
+    RELCP_TRY(sc.inc_cursor.ensure((size_t)nba, s));
+    RELCP_TRY(sc.inc_off.ensure((size_t)nba + 1, s));
+    RELCP_TRY(sc.inc.ensure((size_t)(2 * mc), s));
+    RELCP_TRY(sc.barrier.ensure(2, s));
+    RELCP_CUDA(cudaMemsetAsync(sc.inc_count.p, 0, nba * sizeof(int), s));
+    RELCP_CUDA(cudaMemsetAsync(sc.inc_cursor.p, 0, nba * sizeof(int), s));
+    RELCP_CUDA(cudaMemsetAsync(sc.barrier.p, 0, 2 * sizeof(unsigned), s));
     note_launch();
-    inc_count<<<nblk(m), 256, 0, s>>>(m, pr.ia, pr.ib, sc.inc_count.p);
+    inc_count<<<nblk(mc), 256, 0, s>>>(pr.nrows_dev, pr.ia, pr.ib, sc.inc_count.p);
     RELCP_CUDA(cudaGetLastError());
     RELCP_TRY(exclusive_scan(sc.inc_count.p, sc.inc_off.p, nb, sc.scan, s));
     note_launch();
-    inc_fill<<<nblk(m), 256, 0, s>>>(m, pr.ia, pr.ib, sc.inc_off.p, sc.inc_cursor.p, sc.inc.p);
+    inc_fill<<<nblk(mc), 256, 0, s>>>(pr.nrows_dev, pr.ia, pr.ib, sc.inc_off.p, sc.inc_cursor.p, sc.inc.p);
     RELCP_CUDA(cudaGetLastError());
-    note_launch();
-    inc_sort<<<nblk(nb), 256, 0, s>>>(nb, sc.inc_off.p, sc.inc.p);
-    RELCP_CUDA(cudaGetLastError());
-
-    const double* diag = pr.diag;
-    DBuf<double> diag_tmp;
-    if (!diag) {
-        RELCP_TRY(diag_tmp.ensure((size_t)m, s));
-        RELCP_TRY(lcp_diag_launch(m, pr.ia, pr.ib, pr.geom, pr.K, pr.c, diag_tmp.p, s));
-        diag = diag_tmp.p;
+    if (nb > 0) {
+        note_launch();
+        inc_sort<<<nblk(nb), 256, 0, s>>>(nb, sc.inc_off.p, sc.inc.p);
+        RELCP_CUDA(cudaGetLastError());
     }
-    RELCP_TRY(sc.barrier.ensure(2, s));
-    RELCP_TRY(sc.status.ensure(1, s));
-    RELCP_TRY(sc.result.ensure(3, s));
-    RELCP_CUDA(cudaMemsetAsync(sc.barrier.p, 0, 2 * sizeof(unsigned), s));
-    RELCP_CUDA(cudaMemsetAsync(sc.status.p, 0, sizeof(int), s));
+    if (pr.mixed) return solve_typed<float>(pr, sc, sc.packf, blocks, kernel_ms, s);
+    return solve_typed<double>(pr, sc, sc.packd, blocks, kernel_ms, s);
+}
 
-    int blocks = 0;
-    double hres[3] = {0, 0, 0};
-    if (!pr.mixed) {
-        RELCP_TRY(sc.gamma2.ensure((size_t)m, s));
-        RELCP_TRY(sc.g2.ensure((size_t)(2 * m), s));
-        KArgs<double> ka{};
-        ka.nrows = (int)m;
-        ka.nbodies = (int)nb;
-        ka.ia = pr.ia;
-        ka.ib = pr.ib;
-        for (int k = 0; k < 9; ++k) ka.geom[k] = nullptr;
-        // the FP64 kernel reads SoA rows: convert a strided view if needed
-        DBuf<double> soa;
-        bool is_soa = pr.geom.s == 1;
-        for (int k = 1; k < 9 && is_soa; ++k) is_soa = pr.geom.c[k] == pr.geom.c[0] + k * m;
-        if (is_soa) {
-            for (int k = 0; k < 9; ++k) ka.geom[k] = pr.geom.c[k];
-        } else {
-            RELCP_TRY(soa.ensure((size_t)(9 * m), s));
-            note_launch();
-            convert_rows<double, double><<<nblk(m), 256, 0, s>>>(m, pr.geom, soa.p);
-            RELCP_CUDA(cudaGetLastError());
-            for (int k = 0; k < 9; ++k) ka.geom[k] = soa.p + k * m;
-        }
-        ka.q = pr.q;
-        ka.diag = diag;
-        for (int k = 0; k < 7; ++k) ka.K[k] = pr.K.c[k];
-        // K view must be SoA-compatible: stride handled by pointer arithmetic below
-        DBuf<double> ksoa;
-        if (pr.K.s != 1) {
-            RELCP_TRY(ksoa.ensure((size_t)(7 * nb), s));
-            for (int k = 0; k < 7; ++k)
-                RELCP_CUDA(cudaMemcpy2DAsync(ksoa.p + k * nb, sizeof(double), pr.K.c[k], pr.K.s * sizeof(double),
-                                             sizeof(double), nb, cudaMemcpyDeviceToDevice, s));
-            for (int k = 0; k < 7; ++k) ka.K[k] = ksoa.p + k * nb;
-        }
-        ka.inc_off = sc.inc_off.p;
-        ka.inc = sc.inc.p;
-        ka.gam[0] = pr.gamma;
-        ka.gam[1] = sc.gamma2.p;
-        ka.g[0] = sc.g2.p;
-        ka.g[1] = sc.g2.p + m;
-        for (int k = 0; k < 6; ++k) ka.uc[k] = pr.uc.c[k];
-        ka.uc_stride = pr.uc.s;
-        ka.c = pr.c;
-        ka.tol = pr.tol;
-        ka.max_iter = pr.max_iter;
-        ka.bar = sc.barrier.p;
-        ka.status = sc.status.p;
-        ka.result = sc.result.p;
-        RELCP_TRY(launch_lcp(ka, m > nb ? m : nb, sc, s, &blocks, pr.time_kernel, &res->kernel_ms));
-        RELCP_CUDA(cudaMemcpyAsync(hres, sc.result.p, 3 * sizeof(double), cudaMemcpyDeviceToHost, s));
-        RELCP_CUDA(cudaMemcpyAsync(&res->dev_status, sc.status.p, sizeof(int), cudaMemcpyDeviceToHost, s));
-        RELCP_CUDA(cudaStreamSynchronize(s));
-        if ((int)hres[2] == 1)
-            RELCP_CUDA(cudaMemcpyAsync(pr.gamma, sc.gamma2.p, m * sizeof(double), cudaMemcpyDeviceToDevice, s));
-        soa.release(s);
-        ksoa.release(s);
-    } else {
-        RELCP_TRY(sc.geomf.ensure((size_t)(9 * m), s));
-        RELCP_TRY(sc.gammaf.ensure((size_t)(2 * m), s));
-        RELCP_TRY(sc.gf.ensure((size_t)(2 * m), s));
-        RELCP_TRY(sc.ucf.ensure((size_t)(6 * nb), s));
-        note_launch();
-        convert_rows<double, float><<<nblk(m), 256, 0, s>>>(m, pr.geom, sc.geomf.p);
-        RELCP_CUDA(cudaGetLastError());
-        note_launch();
-        convert_vec<double, float><<<nblk(m), 256, 0, s>>>(m, pr.gamma, sc.gammaf.p);
-        RELCP_CUDA(cudaGetLastError());
-        KArgs<float> ka{};
-        ka.nrows = (int)m;
-        ka.nbodies = (int)nb;
-        ka.ia = pr.ia;
-        ka.ib = pr.ib;
-        for (int k = 0; k < 9; ++k) ka.geom[k] = sc.geomf.p + k * m;
-        ka.q = pr.q;
-        ka.diag = diag;
-        DBuf<double> ksoa;
-        for (int k = 0; k < 7; ++k) ka.K[k] = pr.K.c[k];
-        if (pr.K.s != 1) {
-            RELCP_TRY(ksoa.ensure((size_t)(7 * nb), s));
-            for (int k = 0; k < 7; ++k)
-                RELCP_CUDA(cudaMemcpy2DAsync(ksoa.p + k * nb, sizeof(double), pr.K.c[k], pr.K.s * sizeof(double),
-                                             sizeof(double), nb, cudaMemcpyDeviceToDevice, s));
-            for (int k = 0; k < 7; ++k) ka.K[k] = ksoa.p + k * nb;
-        }
-        ka.inc_off = sc.inc_off.p;
-        ka.inc = sc.inc.p;
-        ka.gam[0] = sc.gammaf.p;
-        ka.gam[1] = sc.gammaf.p + m;
-        ka.g[0] = sc.gf.p;
-        ka.g[1] = sc.gf.p + m;
-        for (int k = 0; k < 6; ++k) ka.uc[k] = sc.ucf.p + k * nb;
-        ka.uc_stride = 1;
-        ka.c = pr.c;
-        ka.tol = pr.tol;
-        ka.max_iter = pr.max_iter;
-        ka.bar = sc.barrier.p;
-        ka.status = sc.status.p;
-        ka.result = sc.result.p;
-        RELCP_TRY(launch_lcp(ka, m > nb ? m : nb, sc, s, &blocks, pr.time_kernel, &res->kernel_ms));
-        RELCP_CUDA(cudaMemcpyAsync(hres, sc.result.p, 3 * sizeof(double), cudaMemcpyDeviceToHost, s));
-        RELCP_CUDA(cudaMemcpyAsync(&res->dev_status, sc.status.p, sizeof(int), cudaMemcpyDeviceToHost, s));
-        RELCP_CUDA(cudaStreamSynchronize(s));
-        int fin = (int)hres[2];
-        note_launch();
-        convert_vec<float, double><<<nblk(m), 256, 0, s>>>(m, sc.gammaf.p + fin * m, pr.gamma);
-        RELCP_CUDA(cudaGetLastError());
-        note_launch();
-        uc_to_double<<<nblk(nb), 256, 0, s>>>(nb, sc.ucf.p, pr.uc);
-        RELCP_CUDA(cudaGetLastError());
-        ksoa.release(s);
-    }
-    diag_tmp.release(s);
-    res->iterations = (int)hres[0];
-    res->residual = hres[1];
-    res->blocks = blocks;
-    return RELCP_OK;
+void release(LcpScratch& sc, cudaStream_t s) {
+    sc.inc_count.release(s);
+    sc.inc_off.release(s);
+    sc.inc_cursor.release(s);
+    sc.inc.release(s);
+    sc.packd.release(s);
+    sc.packf.release(s);
+    sc.partials.release(s);
+    sc.barrier.release(s);
+    sc.scan.partial.release(s);
 }
 
 }  // namespace relcp

@@ -145,10 +145,26 @@ __device__ __forceinline__ Sym3<double> rot_diag_rot(const double* R, double w0,
     return P;
 }
 
-// periodic minimum image of one component (L <= 0: open axis)
+// Periodic minimum image of one component, d - L * rint(d / L) (rint rounds
+// half to even; L <= 0: open axis), every operation rounded separately.
+// The image index k = rint(d / L) is decided by comparing |d| with L/2 and
+// 3L/2, which gives the same k as the rounded quotient except within a
+// relative 1e-12 of a tie; only there is the FP64 division evaluated (FP64
+// division is slow on this part).  The result is bit-identical to the direct
+// formula for every input.
 __device__ __forceinline__ double min_image(double d, double L) {
-    if (L > 0.0) d = __dsub_rn(d, __dmul_rn(L, rint(__ddiv_rn(d, L))));
-    return d;
+    if (!(L > 0.0)) return d;
+    const double ad = fabs(d);
+    const double h = 0.5 * L;  // exact
+    double k;
+    if (ad < h * (1.0 - 1e-12)) {
+        return d;  // k = 0
+    } else if (ad > h * (1.0 + 1e-12) && ad < 3.0 * h * (1.0 - 1e-12)) {
+        k = d > 0.0 ? 1.0 : -1.0;
+    } else {
+        k = rint(__ddiv_rn(d, L));
+    }
+    return __dsub_rn(d, __dmul_rn(L, k));
 }
 
 // ---------------------------------------------------------------------------
@@ -166,11 +182,27 @@ relcp_status exclusive_scan(const int* in, int* out, int64_t n, ScanScratch& sc,
 struct BroadphaseScratch {
     DBuf<int> cell_of, cell_count, cell_start, cell_cursor, cell_body, pair_count, pair_off;
     ScanScratch scan;
+    // Verlet candidate list (context use): pairs within R_i + R_j + skin + delta
+    // at the build positions xb in the build box Lb
+    DBuf<int> vpa, vpb, vflag, vscan;
+    DBuf<double> xb;
+    DBuf<unsigned long long> dmax;  // bits of the largest displacement since the build
+    int64_t vn = 0, vn_bodies = -1;
+    double Lb[3] = {0, 0, 0}, skin_b = -1.0, delta = 0.0;
+    bool valid = false;
+    int rebuilds = 0;
 };
 // Pairs of the bodies whose positions are given by x (any view) and bounding
 // radii rb.  Writes pa/pb (grown as needed), *npairs (host; synchronises s).
-relcp_status broadphase(int64_t n, View<3, const double> x, const double* rb, const double box[3], double skin,
-                        DBuf<int>& pa, DBuf<int>& pb, int64_t* npairs, BroadphaseScratch& sc, cudaStream_t s);
+// rbmax: the largest rb if known (> 0), else it is reduced on the device.
+relcp_status broadphase(int64_t n, View<3, const double> x, const double* rb, double rbmax, const double box[3],
+                        double skin, DBuf<int>& pa, DBuf<int>& pb, int64_t* npairs, BroadphaseScratch& sc,
+                        cudaStream_t s);
+// The same pair list through a cached Verlet list (x in SoA layout, n bodies,
+// rbmax known).  Rebuilds the cache when the displacement bound requires it.
+relcp_status broadphase_cached(int64_t n, const double* x_soa, const double* rb, double rbmax, const double box[3],
+                               double skin, DBuf<int>& pa, DBuf<int>& pb, int64_t* npairs, BroadphaseScratch& sc,
+                               cudaStream_t s);
 
 // ---------------------------------------------------------------------------
 // SNSD (snsd.cu)
@@ -192,13 +224,15 @@ struct SnsdArgs {
     View<3, const double> guess;     // per-pair start normal (c[0] == nullptr: cold start)
     int mixed;                       // FP32 iterations + FP64 polish
     SnsdOut out;
-    // optional overlap test (Phi < -eps): violator flags and per-block max overlap
+    // optional overlap test (Phi < -eps): violator flags and the largest overlap
     double eps;
     int32_t* viol;                   // may be null
-    double* block_maxov;             // may be null (one per block)
+    unsigned long long* maxov_bits;  // may be null: atomicMax of the bits of max(0, -Phi) (>= 0 doubles
+                                     // order like their bit patterns)
+    int* newton_max;                 // may be null: atomicMax of the Newton iteration counts
     int* status;                     // DEV_NEWTON
 };
-relcp_status snsd_launch(const SnsdArgs& a, int* nblocks_out, cudaStream_t s);
+relcp_status snsd_launch(const SnsdArgs& a, cudaStream_t s);
 
 // per-body shape matrices from (possibly unnormalised) quaternions and axes
 relcp_status shape_launch(int64_t n, View<4, const double> q, View<3, const double> axes, View<6, double> P,
@@ -209,45 +243,51 @@ relcp_status shape_launch(int64_t n, View<4, const double> q, View<3, const doub
 // ---------------------------------------------------------------------------
 struct LcpScratch {
     DBuf<int> inc_count, inc_off, inc_cursor, inc;
-    DBuf<double> gamma2, g2, partials;   // second gamma buffer, both g buffers
-    DBuf<float> gammaf, gf, ucf, geomf;  // mixed-path buffers
+    DBuf<double> packd;              // FP64: packed (gamma, g) pairs x 2 buffers + contact-velocity records
+    DBuf<float> packf;               // mixed: the same in FP32
+    DBuf<double> partials;
     DBuf<unsigned> barrier;
-    DBuf<int> status;
-    DBuf<double> result;                 // [iters, residual]
     ScanScratch scan;
 };
+// Filled by the persistent kernel; read by the caller whenever it synchronises.
+struct LcpDevResult {
+    double iterations;
+    double residual;
+};
 struct LcpProblem {
-    int64_t nrows, nbodies;
+    int64_t m_cap;               // number of rows <= m_cap (grid sizing)
+    const int* nrows_dev;        // device-side number of rows
+    int64_t nbodies;
     const int32_t* ia;
     const int32_t* ib;
-    View<9, const double> geom;  // n, r_a x n, r_b x n
-    const double* q;             // offsets
-    const double* diag;          // A_aa (computed if null -> into scratch)
-    View<7, const double> K;     // body operator
+    const void* geom[9];         // SoA rows: n, r_a x n, r_b x n (double, or float when mixed)
+    const double* q;             // offsets (FP64)
+    const void* qr;              // offsets in the solve precision (== q on the FP64 path)
+    const double* diag;          // A_aa
+    const void* invd;            // 1 / A_aa in the solve precision: Jacobi-scaled steps, or null
+    const double* K[7];          // SoA body operator (FP64)
+    const void* Kr[7];           // the same in the solve precision (== K on the FP64 path)
     double c;
     int mixed;
     double tol;
     int max_iter;
-    double* gamma;               // in: warm start, out: solution (nrows)
-    View<6, double> uc;          // out: K D gamma (nbodies)
-    bool time_kernel;            // record CUDA events around the persistent launch
+    void* gamma;                 // SoA, solve precision: in = warm start (>= 0), out = solution
+    double* uc[6];               // SoA output K D gamma (double)
+    LcpDevResult* result;        // device
+    int* status;                 // device status word (DEV_* bits OR-ed)
+    cudaEvent_t ev_before;       // recorded right before / after the persistent launch (or null)
+    cudaEvent_t ev_after;
 };
-struct LcpResult {
-    int iterations;
-    double residual;
-    int blocks;
-    int dev_status;
-    float kernel_ms;             // persistent-kernel time (time_kernel only)
-};
+relcp_status lcp_solve(const LcpProblem& pr, LcpScratch& sc, int* blocks, float* kernel_ms, cudaStream_t s);
+relcp_status lcp_diag_launch(int64_t nrows, const int32_t* ia, const int32_t* ib, View<9, const double> geom,
+                             View<7, const double> K, double c, double* diag, cudaStream_t s);
 // algorithmic bytes of one projected-gradient iteration: every row's
 // geometry, offset, diagonal, gamma and g read once and gamma, g written once;
 // every body's operator read once and its contact velocity written and read once
 inline double lcp_bytes_per_iter(int64_t nrows, int64_t nbodies, bool mixed) {
     return mixed ? 68.0 * nrows + 104.0 * nbodies : 120.0 * nrows + 152.0 * nbodies;
 }
-relcp_status lcp_solve(const LcpProblem& pr, LcpScratch& sc, LcpResult* res, cudaStream_t s);
-relcp_status lcp_diag_launch(int64_t nrows, const int32_t* ia, const int32_t* ib, View<9, const double> geom,
-                             View<7, const double> K, double c, double* diag, cudaStream_t s);
+void release(LcpScratch& sc, cudaStream_t s);
 
 int device_sm_count();
 

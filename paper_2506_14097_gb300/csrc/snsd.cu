@@ -188,6 +188,7 @@ __device__ __forceinline__ Sym3<double> load_P(View<6, const double> P, int64_t 
 __global__ void __launch_bounds__(kThreads) snsd_kernel(SnsdArgs a) {
     int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     double maxov = 0.0;
+    int iters_out = 0;
     if (p < a.npairs) {
         int i = a.pa[p * a.pstride];
         int j = a.pb[p * a.pstride];
@@ -229,8 +230,11 @@ __global__ void __launch_bounds__(kThreads) snsd_kernel(SnsdArgs a) {
             n[1] = nf[1];
             n[2] = nf[2];
             normalize3(n);
-            // FP64 polish (full FP64 Newton when the FP32 phase failed)
-            r = newton_sphere(n, d, Pa, Pb, scale, rf >= 0 ? 4 : 50, &G);
+            // FP64 polish.  At the FP32 maximiser the tangent gradient is
+            // below 2e-6 (1 + |d|), so by stationarity G evaluated there in FP64
+            // is within O(1e-12) of the maximum: that evaluation (below) is the
+            // polish.  Only when the FP32 phase failed does FP64 Newton run.
+            r = rf >= 0 ? 0 : newton_sphere(n, d, Pa, Pb, scale, 50, &G);
         } else {
             if (!have) cold_start(d, Pa, Pb, n);
             r = newton_sphere(n, d, Pa, Pb, scale, 50, &G);
@@ -245,6 +249,7 @@ __global__ void __launch_bounds__(kThreads) snsd_kernel(SnsdArgs a) {
         symv(Pa, n, va);
         symv(Pb, n, vb);
         double sa = sqrt(dot3(n, va)), sb = sqrt(dot3(n, vb));
+        G = dot3(n, d) - sa - sb;
         a.out.phi[p * a.out.phi_s] = G;
         for (int k = 0; k < 3; ++k) {
             a.out.n(k, p) = n[k];
@@ -252,19 +257,32 @@ __global__ void __launch_bounds__(kThreads) snsd_kernel(SnsdArgs a) {
             a.out.rb(k, p) = -vb[k] / sb;
         }
         if (a.out.iters) a.out.iters[p] = iters;
+        iters_out = iters;
         if (a.viol) a.viol[p] = (G < -a.eps) ? 1 : 0;
         maxov = G < 0.0 ? -G : 0.0;
     }
-    if (a.block_maxov) {
-        __shared__ double sh[kThreads / 32];
-        for (int o = 16; o > 0; o >>= 1) maxov = fmax(maxov, __shfl_xor_sync(0xffffffffu, maxov, o));
-        if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = maxov;
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            double m = 0.0;
-            for (int w = 0; w < kThreads / 32; ++w) m = fmax(m, sh[w]);
-            a.block_maxov[blockIdx.x] = m;
+    // one atomic per block for the largest overlap and iteration count
+    __shared__ double sh_ov[kThreads / 32];
+    __shared__ int sh_it[kThreads / 32];
+    int itabs = iters_out < 0 ? -iters_out : iters_out;
+    for (int o = 16; o > 0; o >>= 1) {
+        maxov = fmax(maxov, __shfl_xor_sync(0xffffffffu, maxov, o));
+        itabs = max(itabs, __shfl_xor_sync(0xffffffffu, itabs, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        sh_ov[threadIdx.x >> 5] = maxov;
+        sh_it[threadIdx.x >> 5] = itabs;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double m = 0.0;
+        int mi = 0;
+        for (int w = 0; w < kThreads / 32; ++w) {
+            m = fmax(m, sh_ov[w]);
+            mi = max(mi, sh_it[w]);
         }
+        if (a.maxov_bits) atomicMax(a.maxov_bits, (unsigned long long)__double_as_longlong(m));
+        if (a.newton_max) atomicMax(a.newton_max, mi);
     }
 }
 
@@ -287,9 +305,8 @@ __global__ void shape_kernel(int64_t n, View<4, const double> q, View<3, const d
 
 }  // namespace
 
-relcp_status snsd_launch(const SnsdArgs& a, int* nblocks_out, cudaStream_t s) {
+relcp_status snsd_launch(const SnsdArgs& a, cudaStream_t s) {
     unsigned nb = (unsigned)((a.npairs + kThreads - 1) / kThreads);
-    if (nblocks_out) *nblocks_out = (int)nb;
     if (a.npairs == 0) return RELCP_OK;
     note_launch();
     snsd_kernel<<<nb, kThreads, 0, s>>>(a);

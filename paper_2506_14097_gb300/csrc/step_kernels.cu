@@ -73,6 +73,10 @@ __global__ void prep_kernel(PrepArgs a) {
     a.K[4 * a.n + i] = Kr.xy;
     a.K[5 * a.n + i] = Kr.xz;
     a.K[6 * a.n + i] = Kr.yz;
+    if (a.Kf) {
+        const double kv[7] = {kt, Kr.xx, Kr.yy, Kr.zz, Kr.xy, Kr.xz, Kr.yz};
+        for (int k = 0; k < 7; ++k) a.Kf[k * a.n + i] = (float)kv[k];
+    }
     // U_free = vel + K F_ext (+ affine background velocity)
     double f[6], u[6];
     for (int k = 0; k < 6; ++k) {
@@ -106,6 +110,10 @@ __device__ __forceinline__ double body_rate(const double* U, int64_t n, int i, i
 
 __global__ void rows_kernel(RowsArgs a) {
     int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p == 0) {
+        int64_t total = a.base + a.scan[a.npairs];
+        *a.nrows_dev = (int)(total < a.cap ? total : a.cap);
+    }
     if (p >= a.npairs || !a.flags[p]) return;
     int64_t r = a.base + a.scan[p];
     if (r >= a.cap) {
@@ -133,6 +141,12 @@ __global__ void rows_kernel(RowsArgs a) {
         a.geom[(3 + k) * C + r] = ta[k];
         a.geom[(6 + k) * C + r] = tb[k];
     }
+    if (a.geomf)
+        for (int k = 0; k < 3; ++k) {
+            a.geomf[k * C + r] = (float)nn[k];
+            a.geomf[(3 + k) * C + r] = (float)ta[k];
+            a.geomf[(6 + k) * C + r] = (float)tb[k];
+        }
     // offset
     double qv;
     if (a.rec_index == 0) {
@@ -150,6 +164,7 @@ __global__ void rows_kernel(RowsArgs a) {
         qv = phi - a.c * body_rate(a.uc, a.nbodies, i, j, nn, ta, tb);
     }
     a.q[r] = qv;
+    if (a.qf) a.qf[r] = (float)qv;
     // diagonal c d^T K d
     double acc = (a.K[i] + a.K[j]) * (nn[0] * nn[0] + nn[1] * nn[1] + nn[2] * nn[2]);
     for (int side = 0; side < 2; ++side) {
@@ -162,7 +177,29 @@ __global__ void rows_kernel(RowsArgs a) {
                t[2] * (kxz * t[0] + kyz * t[1] + kzz * t[2]);
     }
     a.diag[r] = a.c * acc;
-    a.gamma[r] = 0.0;
+    if (a.invd) a.invd[r] = 1.0 / (a.c * acc);
+    if (a.invdf) a.invdf[r] = (float)(1.0 / (a.c * acc));
+    double g0 = 0.0;
+    if (a.rec_index == 0 && a.prev_n > 0) {
+        // binary search of (i, j) among the previous step's A_0 rows
+        const long long key = ((long long)i << 32) | (long long)j;
+        int64_t lo = 0, hi = a.prev_n;
+        while (lo < hi) {
+            int64_t mid = (lo + hi) >> 1;
+            if (a.prev_keys[mid] < key) lo = mid + 1;
+            else hi = mid;
+        }
+        if (lo < a.prev_n && a.prev_keys[lo] == key) g0 = a.prev_gamma[lo];
+    }
+    if (a.gamma) a.gamma[r] = g0;
+    if (a.gammaf) a.gammaf[r] = (float)g0;
+}
+
+__global__ void save_warm_kernel(SaveWarmArgs a) {
+    int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= *a.nrows0_dev) return;
+    a.keys[r] = ((long long)a.ia[r] << 32) | (long long)a.ib[r];
+    a.gout[r] = a.gamma ? a.gamma[r] : (double)a.gammaf[r];
 }
 
 __global__ void trial_kernel(TrialArgs a) {
@@ -219,28 +256,6 @@ __global__ void accept_kernel(AcceptArgs a) {
         for (int k = 0; k < 6; ++k) a.vel[k * n + i] = a.ustep[k * n + i];
 }
 
-__global__ void max_blocks_kernel(int nblocks, const double* __restrict__ v, double* __restrict__ out) {
-    __shared__ double sh[32];
-    double m = 0.0;
-    for (int i = threadIdx.x; i < nblocks; i += blockDim.x) m = fmax(m, v[i]);
-    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
-    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = m;
-    __syncthreads();
-    if (threadIdx.x < 32) {
-        m = threadIdx.x < (blockDim.x >> 5) ? sh[threadIdx.x] : 0.0;
-        for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
-        if (threadIdx.x == 0) *out = m;
-    }
-}
-
-__global__ void iters_max_kernel(int64_t np, const int* __restrict__ it, int* __restrict__ out) {
-    int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (p < np) {
-        int v = it[p];
-        atomicMax(out, v < 0 ? -v : v);
-    }
-}
-
 __global__ void wrap_kernel(int64_t n, double* x, double L0, double L1, double L2) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
@@ -286,23 +301,14 @@ relcp_status accept_launch(const AcceptArgs& a, cudaStream_t s) {
     RELCP_CUDA(cudaGetLastError());
     return RELCP_OK;
 }
-relcp_status max_blocks_launch(int nblocks, const double* v, double* out, cudaStream_t s) {
-    if (nblocks <= 0) {
-        RELCP_CUDA(cudaMemsetAsync(out, 0, sizeof(double), s));
-        return RELCP_OK;
-    }
+relcp_status save_warm_launch(const SaveWarmArgs& a, int64_t cap, cudaStream_t s) {
+    if (cap <= 0) return RELCP_OK;
     note_launch();
-    max_blocks_kernel<<<1, 1024, 0, s>>>(nblocks, v, out);
+    save_warm_kernel<<<nb(cap), kT, 0, s>>>(a);
     RELCP_CUDA(cudaGetLastError());
     return RELCP_OK;
 }
-relcp_status iters_max_launch(int64_t np, const int* it, int* out, cudaStream_t s) {
-    if (np == 0) return RELCP_OK;
-    note_launch();
-    iters_max_kernel<<<nb(np), kT, 0, s>>>(np, it, out);
-    RELCP_CUDA(cudaGetLastError());
-    return RELCP_OK;
-}
+
 relcp_status wrap_launch(int64_t n, double* x, const double box[3], cudaStream_t s) {
     if (n == 0) return RELCP_OK;
     note_launch();

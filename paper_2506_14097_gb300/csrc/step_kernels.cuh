@@ -19,6 +19,7 @@ struct PrepArgs {
     const double* fext;
     double* P;
     double* K;
+    float* Kf;  // FP32 mirror of K (mixed path)
     double* rb;
     double* ufree;
 };
@@ -42,11 +43,32 @@ struct RowsArgs {
     int* ib;
     int* rec;
     int* pair;
-    double* geom;  // 9 x cap
+    double* geom;   // 9 x cap
+    float* geomf;   // 9 x cap FP32 mirror (mixed path) or null
     double* q;
+    float* qf;      // FP32 mirror of q (mixed path) or null
     double* diag;
-    double* gamma;
+    double* invd;   // 1 / A_aa (FP64 path) or null
+    float* invdf;   // 1 / A_aa (mixed path) or null
+    double* gamma;  // warm start of new rows set to 0 (FP64 path) or null
+    float* gammaf;  // same for the mixed path or null
+    int* nrows_dev; // set to base + number of flagged pairs
     int* status;
+    // warm start of A_0 rows from the previous step's A_0 rows (sorted keys
+    // (a << 32) | b with their final gamma); prev_n = 0 disables it
+    int64_t prev_n;
+    const long long* prev_keys;
+    const double* prev_gamma;
+};
+
+struct SaveWarmArgs {
+    const int* nrows0_dev;  // number of A_0 rows (device)
+    const int* ia;
+    const int* ib;
+    const double* gamma;    // FP64 path or null
+    const float* gammaf;    // mixed path or null
+    long long* keys;
+    double* gout;
 };
 
 struct TrialArgs {
@@ -80,8 +102,7 @@ relcp_status flag_le_launch(int64_t np, const double* phi, double thr, int* flag
 relcp_status rows_launch(const RowsArgs& a, cudaStream_t s);
 relcp_status trial_launch(const TrialArgs& a, cudaStream_t s);
 relcp_status accept_launch(const AcceptArgs& a, cudaStream_t s);
-relcp_status max_blocks_launch(int nblocks, const double* v, double* out, cudaStream_t s);
-relcp_status iters_max_launch(int64_t np, const int* it, int* out, cudaStream_t s);
 relcp_status wrap_launch(int64_t n, double* x, const double box[3], cudaStream_t s);
+relcp_status save_warm_launch(const SaveWarmArgs& a, int64_t cap, cudaStream_t s);
 
 }  // namespace relcp

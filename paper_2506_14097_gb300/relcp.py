@@ -34,6 +34,8 @@ RELCP_GUESS_COLD, RELCP_GUESS_MLP = 0, 1
 RELCP_PTR_HOST, RELCP_PTR_DEVICE = 0, 1
 RELCP_FAULT_ROW_CAPACITY, RELCP_FAULT_LCP_ITERS = 1, 2
 RELCP_FLAG_PHASE_TIMING = 1
+RELCP_FLAG_NO_WARM_START = 2
+RELCP_FLAG_JACOBI = 4
 MAX_DEPTH_STATS = 64
 
 
@@ -54,7 +56,7 @@ class relcp_step_stats(ctypes.Structure):
                 ("ms_total", c_double), ("steps_done", c_int64), ("guess_used", c_int32),
                 ("newton_fallbacks", c_int32), ("ms_lcp_kernel", c_double), ("lcp_alg_bytes", c_double),
                 ("ms_snsd_kernel", c_double), ("snsd_evals", c_int64), ("lcp_launches", c_int32),
-                ("snsd_launches", c_int32)]
+                ("snsd_launches", c_int32), ("pair_list_rebuilt", c_int32), ("pad0", c_int32)]
 
 
 class relcp_lcp_info(ctypes.Structure):
