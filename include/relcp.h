@@ -252,6 +252,35 @@ relcp_status relcp_lcp_solve(int64_t nrows, int64_t nbodies, const int32_t* ia, 
                              int32_t precision, double tol, int32_t max_iter, double* gamma, double* uc,
                              relcp_lcp_info* info, void* stream);
 
+/* ------------------------------------------------------------------ */
+/* Allocation-free variant                                              */
+/* ------------------------------------------------------------------ */
+
+/* The paper has no counterpart of this entry point: it is a library
+ * convenience.  relcp_snsd_eval_noalloc computes exactly what
+ * relcp_snsd_eval computes (same kernels, same arguments, same outputs), but
+ * allocates no device memory: its scratch (the per-body shape matrices and the
+ * device status word) is a fixed file-scope device array of
+ * RELCP_NOALLOC_SCRATCH_BYTES bytes that every GPU loading the library holds
+ * until the process exits.  It is for callers that cannot call cudaMalloc or
+ * cudaMallocAsync: a host framework whose caching allocator has reserved the
+ * device memory, a real-time loop where an allocation (which may synchronise
+ * the device) is not allowed, or a plugin that may allocate only at start-up.
+ *   - n must be <= RELCP_NOALLOC_MAX_BODIES, else RELCP_ERR_CAPACITY with a
+ *     message; nothing runs then.
+ *   - The first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress, with that device current) and caches it; make
+ *     that first call before any stream capture.
+ *   - Every call shares the array, which keeps the last call's contents; the
+ *     status word is cleared by each call.  Calls whose work overlaps on the
+ *     GPU race on the array: serialise them (one stream, one thread at a time).
+ *   - Synchronises `stream`.  Returns RELCP_ERR_NEWTON like relcp_snsd_eval. */
+#define RELCP_NOALLOC_MAX_BODIES 65536
+#define RELCP_NOALLOC_SCRATCH_BYTES (256 + 48 * RELCP_NOALLOC_MAX_BODIES)
+relcp_status relcp_snsd_eval_noalloc(int64_t npairs, const int32_t* pairs, int64_t n, const double* x,
+                                     const double* q, const double* axes, const double* box3, int32_t precision,
+                                     double* out, int32_t* iters, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

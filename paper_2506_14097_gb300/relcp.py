@@ -73,7 +73,8 @@ class RelcpError(RuntimeError):
 _lib = None
 EXPORTS = ["relcp_last_error", "relcp_kernel_launches", "relcp_version", "relcp_create", "relcp_set_config", "relcp_set_bodies",
            "relcp_step", "relcp_get_bodies", "relcp_get_box", "relcp_stats", "relcp_get_pairs", "relcp_get_rows",
-           "relcp_get_contact_velocity", "relcp_destroy", "relcp_broadphase", "relcp_snsd_eval", "relcp_lcp_solve"]
+           "relcp_get_contact_velocity", "relcp_destroy", "relcp_broadphase", "relcp_snsd_eval", "relcp_lcp_solve",
+           "relcp_snsd_eval_noalloc"]
 
 
 def library_path() -> str:
@@ -112,6 +113,8 @@ def load(build_if_needed: bool = True):
                             c_void_p, c_void_p],
         "relcp_lcp_solve": [c_int64, c_int64, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_double, c_int32,
                             c_double, c_int32, c_void_p, c_void_p, POINTER(relcp_lcp_info), c_void_p],
+        "relcp_snsd_eval_noalloc": [c_int64, c_void_p, c_int64, c_void_p, c_void_p, c_void_p, c_void_p, c_int32,
+                                    c_void_p, c_void_p, c_void_p],
     }
     for name, args in sigs.items():
         f = getattr(L, name)
@@ -302,6 +305,20 @@ def relcp_snsd_eval(pairs, x, q, axes, box, precision=RELCP_FP64, stream=None, a
                                 int(precision), _ptr(out), _ptr(iters), c_void_p(_stream(stream)))
     _check(st, "relcp_snsd_eval", allow)
     return out[:P], iters[:P]
+
+
+NOALLOC_MAX_BODIES = 65536
+
+
+def relcp_snsd_eval_noalloc(pairs, x, q, axes, box, out, iters=None, precision=RELCP_FP64, stream=None, allow=()):
+    """Allocation-free SNSD evaluation into caller-provided device buffers
+    `out` (P, 10) float64 and `iters` (P,) int32 (or None).  Same results as
+    relcp_snsd_eval; see include/relcp.h for the scratch rules."""
+    P = int(pairs.shape[0])
+    box_h = np.ascontiguousarray(box, dtype=np.float64)
+    st = load().relcp_snsd_eval_noalloc(P, _ptr(pairs), int(x.shape[0]), _ptr(x), _ptr(q), _ptr(axes), _ptr(box_h),
+                                        int(precision), _ptr(out), _ptr(iters), c_void_p(_stream(stream)))
+    return _check(st, "relcp_snsd_eval_noalloc", allow)
 
 
 def relcp_lcp_solve(ia, ib, geom, qv, K, c: float, gamma=None, precision=RELCP_FP64, tol=1e-12, max_iter=100000,
