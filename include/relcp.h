@@ -130,6 +130,7 @@ typedef struct relcp_step_stats {
     int32_t snsd_launches;
     int32_t pair_list_rebuilt;  /* 1 when the cached candidate list was rebuilt in this step */
     int32_t pad0;
+    int64_t newton_iters_c0;    /* Newton iterations summed over the pairs of the C^k evaluation */
 } relcp_step_stats;
 
 typedef struct relcp_ctx relcp_ctx;
@@ -251,6 +252,69 @@ relcp_status relcp_lcp_solve(int64_t nrows, int64_t nbodies, const int32_t* ia, 
                              const double* geom, const double* qv, const double* K, double c,
                              int32_t precision, double tol, int32_t max_iter, double* gamma, double* uc,
                              relcp_lcp_info* info, void* stream);
+
+/* ------------------------------------------------------------------ */
+/* Learned SNSD initial guess                                           */
+/* ------------------------------------------------------------------ */
+/* A small MLP proposes the Newton start of the SNSD solve at C^k; Newton on
+ * the sphere stays the judge of every result (a bad guess costs iterations,
+ * never accuracy).  The paper uses no learned component: this is the learned
+ * stand-in for the cold start.  Network: 16 inputs -> 128 -> 128 -> 128 -> 8
+ * outputs (5 used), ReLU, BF16 tensor-core kernels with FP32 accumulation.
+ * Parameters: one FP32 vector of RELCP_MLP_NPARAMS values, row-major
+ * W[out][in]: W1 (128x16), b1, W2 (128x128), b2, W3, b3, W4 (8x128), b4;
+ * padded outputs 5..7 must be zero.
+ * Features of pair (a, b): d = min-image c_b - c_a in a's frame divided by
+ * s = max semi-axis(a) + max semi-axis(b) (3); q_rel = conj(q_a) (x) q_b with
+ * non-negative scalar part (4); semi-axes of a (3) and of b (3); the analytic
+ * seed normalise((P_a + P_b)^-1 d) in a's frame (3).
+ * Outputs: correction from the seed to the shared normal in a's frame, times
+ * RELCP_MLP_CORR_SCALE (3), Phi / s, trust logit; the Newton start is
+ * normalise(seed + correction / RELCP_MLP_CORR_SCALE) where the logit is
+ * positive, the cold start elsewhere.  Training targets: RELCP_MLP_CORR_SCALE
+ * times (FP64 SNSD normal in a's frame - seed), and Phi / s. */
+#define RELCP_MLP_IN 16
+#define RELCP_MLP_HID 128
+#define RELCP_MLP_OUT 8
+#define RELCP_MLP_NPARAMS (128 * 16 + 128 + 128 * 128 + 128 + 128 * 128 + 128 + 8 * 128 + 8)
+/* the correction is learned scaled by this factor (outputs of order one stay
+ * far above the BF16 resolution of the last layer) */
+#define RELCP_MLP_CORR_SCALE 32.0f
+
+/* Features (npairs x 16 float, device) of listed pairs (device, as in
+ * relcp_snsd_eval); with snsd_out (npairs x 10 from relcp_snsd_eval) also the
+ * training targets (npairs x 4 float: RELCP_MLP_CORR_SCALE x (normal in a's
+ * frame minus the seed), Phi / s). */
+relcp_status relcp_mlp_features(int64_t npairs, const int32_t* pairs, int64_t n, const double* x, const double* q,
+                                const double* axes, const double* box3, const double* snsd_out, float* feat,
+                                float* targets, void* stream);
+
+/* Network outputs (npairs x 8 float) for features (npairs x 16); params device. */
+relcp_status relcp_mlp_forward(int64_t npairs, const float* params, const float* feat, float* out, void* stream);
+
+typedef struct relcp_mlp_train_config {
+    float lr;          /* Adam step; 0 = compute the loss and gradients only */
+    float beta1, beta2, eps;
+    float w_phi;       /* weight of (Phi/s - target)^2 */
+    float w_trust;     /* weight of the trust logit's cross-entropy */
+    float trust_tol;   /* trust label: squared error of the corrected seed below trust_tol times the
+                          squared error of the seed alone (1 = "the correction helps") */
+    int32_t step;      /* Adam step counter (>= 1 when lr > 0) */
+} relcp_mlp_train_config;
+
+/* One training step on a batch (device): loss = mean over samples of
+ * |o[0:3] - t[0:3]|^2 + w_phi (o[3] - t[3])^2 + w_trust BCE(o[4], label);
+ * forward and backward on the tensor cores; Adam on params (FP32 master) with
+ * moments adam_m, adam_v (NPARAMS each, device).  grad_out (device, NPARAMS)
+ * or NULL receives the gradient; *loss_out (host) the batch loss.  Allocates
+ * its scratch stream-ordered; synchronises `stream`. */
+relcp_status relcp_mlp_train_step(int64_t batch, float* params, float* adam_m, float* adam_v, const float* feat,
+                                  const float* targets, const relcp_mlp_train_config* cfg, float* grad_out,
+                                  double* loss_out, void* stream);
+
+/* Give a context the parameters (host or device, NPARAMS floats) used when
+ * its config has guess = RELCP_GUESS_MLP. */
+relcp_status relcp_load_mlp(relcp_ctx* ctx, const float* params, int32_t ptr_kind);
 
 /* ------------------------------------------------------------------ */
 /* Allocation-free variant                                              */

@@ -62,6 +62,7 @@ struct DevStep {
     int newton_max;     // largest Newton iteration count
     int nrows0;         // |A_0| (copied from nrows after the first LCP)
     unsigned long long maxov_bits;  // bits of the largest overlap at the last trial
+    unsigned long long iters0;      // Newton iterations summed over the pairs at C^k
     LcpDevResult lcp;   // iterations and residual of the last LCP
 };
 
@@ -315,6 +316,7 @@ relcp_status step_once(relcp_ctx* c) {
     sa.viol = nullptr;
     sa.maxov_bits = nullptr;
     sa.newton_max = &ds->newton_max;
+    sa.iters_sum = &ds->iters0;
     sa.status = &ds->status;
     {
         int e0 = tm.mark();
@@ -438,6 +440,7 @@ relcp_status step_once(relcp_ctx* c) {
         sb.eps = cfg.eps_ncp;
         sb.viol = c->flags.p;
         sb.maxov_bits = &ds->maxov_bits;
+        sb.iters_sum = nullptr;
         RELCP_CUDA(cudaMemsetAsync(&ds->maxov_bits, 0, sizeof(unsigned long long), s));
         {
             int e0 = tm.mark();
@@ -525,6 +528,7 @@ relcp_status step_once(relcp_ctx* c) {
     st.status = step_status;
     st.lcp_iters_total = lcp_iters_total;
     st.newton_iters_max = hs.newton_max;
+    st.newton_iters_c0 = (int64_t)hs.iters0;
     st.lcp_residual = hs.lcp.residual;
     st.max_overlap = __builtin_bit_cast(double, hs.maxov_bits);
     for (int k = 0; k < 3; ++k) st.box[k] = c->box[k];
@@ -799,6 +803,16 @@ relcp_status relcp_get_contact_velocity(relcp_ctx* c, double* uc, int32_t ptr_ki
     return RELCP_OK;
 }
 
+relcp_status relcp_load_mlp(relcp_ctx* c, const float* params, int32_t ptr_kind) {
+    if (!c || !params) return set_error("NULL argument"), RELCP_ERR_INVALID_ARG;
+    RELCP_TRY(c->mlp.params.ensure(RELCP_MLP_NPARAMS, c->s));
+    RELCP_CUDA(cudaMemcpyAsync(c->mlp.params.p, params, RELCP_MLP_NPARAMS * sizeof(float),
+                               ptr_kind == RELCP_PTR_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->s));
+    RELCP_CUDA(cudaStreamSynchronize(c->s));
+    c->mlp.loaded = true;
+    return RELCP_OK;
+}
+
 void relcp_destroy(relcp_ctx* c) {
     if (!c) return;
     cudaStream_t s = c->s;
@@ -897,6 +911,7 @@ relcp_status relcp_snsd_eval(int64_t npairs, const int32_t* pairs, int64_t n, co
     a.status = status.p;
     a.maxov_bits = nullptr;
     a.newton_max = nullptr;
+    a.iters_sum = nullptr;
     relcp_status st = snsd_launch(a, s);
     int bits = 0;
     if (st == RELCP_OK) {

@@ -1,14 +1,680 @@
+// Learned SNSD initial guess (the learned part of the method's Newton start;
+// Newton on the sphere remains the judge of every result).
+//
+// Network: features (16, 13 used) -> 128 -> 128 -> 128 -> outputs (8, 5 used),
+// ReLU, BF16 operands on the tensor cores (mma.sync.m16n8k16, FP32
+// accumulation).
+//   features : d = c_b - c_a (minimum image) in a's frame divided by
+//              s = max(a_a) + max(a_b); q_rel = conj(q_a) (x) q_b with s >= 0;
+//              a's and b's semi-axes; the analytic seed (P_a + P_b)^-1 d,
+//              normalised, in a's frame.
+//   outputs  : the correction from the seed to the shared normal (in a's
+//              frame, scaled by RELCP_MLP_CORR_SCALE), Phi / s, and a trust
+//              logit (positive: the corrected seed is the Newton start; else
+//              the cold start is used).
+// Inference is one fused kernel: the four weight matrices live in shared
+// memory (BF16, row = output unit), each warp carries 16 pairs through all four
+// layers in registers -- the FP32 accumulator fragment of one layer is exactly
+// the A-operand fragment of the next (same rows, same columns per thread), so
+// activations never leave the registers.
+// Training is layer by layer with a generic tensor-core GEMM
+// C = A B^T (both operands K-contiguous BF16), transposes, the loss, bias sums
+// and Adam (Kingma & Ba) on FP32 master parameters.
+#include <cuda_bf16.h>
+
+#include <vector>
+
 #include "mlp.cuh"
 
 namespace relcp {
 
-relcp_status mlp_guess(MlpState& m, int64_t, const int*, const int*, View<3, const double>, View<4, const double>,
-                       View<3, const double>, const double*, cudaStream_t) {
-    (void)m;
-    set_error("learned guess not loaded");
-    return RELCP_ERR_STATE;
+namespace {
+
+// ---------------------------------------------------------------------------
+// tensor-core primitives
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
+    __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<uint32_t*>(&v);
 }
 
-void mlp_release(MlpState& m, cudaStream_t s) { m.guess.release(s); }
+// D = A B + D with A 16x16 (row), B 16x8 (col), BF16 in, FP32 accumulate.
+// Fragment ownership (g = lane / 4, t = lane % 4):
+//   a0: A[g][2t..2t+1]   a1: A[g+8][2t..2t+1]   a2: A[g][2t+8..]   a3: A[g+8][2t+8..]
+//   b0: B[2t..2t+1][g]   b1: B[2t+8..2t+9][g]
+//   c0,c1: C[g][2t..2t+1]   c2,c3: C[g+8][2t..2t+1]
+__device__ __forceinline__ void mma_bf16(float c[4], const uint32_t a[4], uint32_t b0, uint32_t b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};\n"
+        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+// ---------------------------------------------------------------------------
+// features
+// ---------------------------------------------------------------------------
+__global__ void features_kernel(MlpFeatArgs a) {
+    int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= a.npairs) return;
+    const int i = a.pa[p * a.pstride], j = a.pb[p * a.pstride];
+    double d[3];
+    for (int k = 0; k < 3; ++k) d[k] = min_image(a.x(k, j) - a.x(k, i), a.box[k]);
+    double qa[4], qb[4];
+    double la = 0, lb = 0;
+    for (int k = 0; k < 4; ++k) {
+        qa[k] = a.q(k, i);
+        qb[k] = a.q(k, j);
+        la += qa[k] * qa[k];
+        lb += qb[k] * qb[k];
+    }
+    la = sqrt(la);
+    lb = sqrt(lb);
+    for (int k = 0; k < 4; ++k) {
+        qa[k] /= la;
+        qb[k] /= lb;
+    }
+    double R[9];
+    quat_to_R(qa[0], qa[1], qa[2], qa[3], R);
+    const double aa[3] = {a.axes(0, i), a.axes(1, i), a.axes(2, i)};
+    const double ab[3] = {a.axes(0, j), a.axes(1, j), a.axes(2, j)};
+    const double sc = fmax(aa[0], fmax(aa[1], aa[2])) + fmax(ab[0], fmax(ab[1], ab[2]));
+    float* f = a.feat + 16 * p;
+    for (int k = 0; k < 3; ++k) f[k] = (float)((R[k] * d[0] + R[3 + k] * d[1] + R[6 + k] * d[2]) / sc);
+    // q_rel = conj(q_a) (x) q_b
+    const double s1 = qa[0], x1 = -qa[1], y1 = -qa[2], z1 = -qa[3];
+    const double s2 = qb[0], x2 = qb[1], y2 = qb[2], z2 = qb[3];
+    double qr[4] = {s1 * s2 - (x1 * x2 + y1 * y2 + z1 * z2), s1 * x2 + s2 * x1 + (y1 * z2 - z1 * y2),
+                    s1 * y2 + s2 * y1 + (z1 * x2 - x1 * z2), s1 * z2 + s2 * z1 + (x1 * y2 - y1 * x2)};
+    const double sg = qr[0] < 0.0 ? -1.0 : 1.0;
+    for (int k = 0; k < 4; ++k) f[3 + k] = (float)(sg * qr[k]);
+    for (int k = 0; k < 3; ++k) {
+        f[7 + k] = (float)aa[k];
+        f[10 + k] = (float)ab[k];
+    }
+    // analytic seed (P_a + P_b)^-1 d (world), normalised, in a's frame: the
+    // network predicts the correction from this seed to the shared normal
+    double sd[3];
+    {
+        double Rb[9];
+        quat_to_R(qb[0], qb[1], qb[2], qb[3], Rb);
+        Sym3<double> Pa = rot_diag_rot(R, aa[0] * aa[0], aa[1] * aa[1], aa[2] * aa[2]);
+        Sym3<double> Pb = rot_diag_rot(Rb, ab[0] * ab[0], ab[1] * ab[1], ab[2] * ab[2]);
+        const double xx = Pa.xx + Pb.xx, yy = Pa.yy + Pb.yy, zz = Pa.zz + Pb.zz;
+        const double xy = Pa.xy + Pb.xy, xz = Pa.xz + Pb.xz, yz = Pa.yz + Pb.yz;
+        // adjugate of the symmetric sum times d (same direction as the inverse)
+        const double A00 = yy * zz - yz * yz, A11 = xx * zz - xz * xz, A22 = xx * yy - xy * xy;
+        const double A01 = xz * yz - xy * zz, A02 = xy * yz - yy * xz, A12 = xy * xz - xx * yz;
+        double w[3] = {A00 * d[0] + A01 * d[1] + A02 * d[2], A01 * d[0] + A11 * d[1] + A12 * d[2],
+                       A02 * d[0] + A12 * d[1] + A22 * d[2]};
+        double lw = sqrt(w[0] * w[0] + w[1] * w[1] + w[2] * w[2]);
+        if (!(lw > 0.0)) {
+            w[0] = 1.0;
+            w[1] = w[2] = 0.0;
+            lw = 1.0;
+        }
+        for (int k = 0; k < 3; ++k) sd[k] = (R[k] * w[0] + R[3 + k] * w[1] + R[6 + k] * w[2]) / lw;
+    }
+    for (int k = 0; k < 3; ++k) f[13 + k] = (float)sd[k];
+    if (a.targets && a.snsd) {
+        const double* o = a.snsd + p * a.snsd_s;
+        const double n[3] = {o[1 * a.snsd_c], o[2 * a.snsd_c], o[3 * a.snsd_c]};
+        float* t = a.targets + 4 * p;
+        for (int k = 0; k < 3; ++k)
+            t[k] = (float)(RELCP_MLP_CORR_SCALE * ((R[k] * n[0] + R[3 + k] * n[1] + R[6 + k] * n[2]) - sd[k]));
+        t[3] = (float)(o[0] / sc);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// fused inference
+// ---------------------------------------------------------------------------
+constexpr int kFwdWarps = 4;
+constexpr int kKs1 = kMlpIn + 8;   // padded row stride (BF16 elements) of W1
+constexpr int kKs = kMlpHid + 8;   // padded row stride of W2, W3, W4
+constexpr int kSmemW1 = kMlpHid * kKs1;
+constexpr int kSmemW = kMlpHid * kKs;
+constexpr int kSmemW4 = kMlpOut * kKs;
+constexpr size_t kFwdSmem = (size_t)(kSmemW1 + 2 * kSmemW + kSmemW4) * 2 + (3 * kMlpHid + kMlpOut) * 4;
+
+__device__ __forceinline__ uint32_t lds32(const __nv_bfloat16* p) { return *reinterpret_cast<const uint32_t*>(p); }
+
+// one hidden layer: acc (16 n-tiles) = A (8 k-tiles) x W^T, then bias + ReLU
+// and repack as the next layer's A fragments
+__device__ __forceinline__ void hidden_layer(uint32_t A[8][4], const __nv_bfloat16* W, const float* bias, int g, int t) {
+    float acc[16][4];
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+        acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.f;
+        const __nv_bfloat16* wr = W + (8 * j + g) * kKs + 2 * t;
+#pragma unroll
+        for (int kk = 0; kk < 8; ++kk) mma_bf16(acc[j], A[kk], lds32(wr + 16 * kk), lds32(wr + 16 * kk + 8));
+    }
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+        const float b0 = bias[8 * j + 2 * t], b1 = bias[8 * j + 2 * t + 1];
+        acc[j][0] = fmaxf(acc[j][0] + b0, 0.f);
+        acc[j][1] = fmaxf(acc[j][1] + b1, 0.f);
+        acc[j][2] = fmaxf(acc[j][2] + b0, 0.f);
+        acc[j][3] = fmaxf(acc[j][3] + b1, 0.f);
+    }
+#pragma unroll
+    for (int kk = 0; kk < 8; ++kk) {
+        A[kk][0] = pack_bf16(acc[2 * kk][0], acc[2 * kk][1]);
+        A[kk][1] = pack_bf16(acc[2 * kk][2], acc[2 * kk][3]);
+        A[kk][2] = pack_bf16(acc[2 * kk + 1][0], acc[2 * kk + 1][1]);
+        A[kk][3] = pack_bf16(acc[2 * kk + 1][2], acc[2 * kk + 1][3]);
+    }
+}
+
+__global__ void __launch_bounds__(kFwdWarps * 32) mlp_forward_kernel(int64_t npairs, const float* __restrict__ params,
+                                                                     const float* __restrict__ feat,
+                                                                     float* __restrict__ out) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __nv_bfloat16* W1 = reinterpret_cast<__nv_bfloat16*>(smem);
+    __nv_bfloat16* W2 = W1 + kSmemW1;
+    __nv_bfloat16* W3 = W2 + kSmemW;
+    __nv_bfloat16* W4 = W3 + kSmemW;
+    float* bias = reinterpret_cast<float*>(W4 + kSmemW4);  // b1 | b2 | b3 | b4
+    for (int e = threadIdx.x; e < kMlpHid * kMlpIn; e += blockDim.x)
+        W1[(e / kMlpIn) * kKs1 + e % kMlpIn] = __float2bfloat16_rn(params[kOffW1 + e]);
+    for (int e = threadIdx.x; e < kMlpHid * kMlpHid; e += blockDim.x) {
+        W2[(e / kMlpHid) * kKs + e % kMlpHid] = __float2bfloat16_rn(params[kOffW2 + e]);
+        W3[(e / kMlpHid) * kKs + e % kMlpHid] = __float2bfloat16_rn(params[kOffW3 + e]);
+    }
+    for (int e = threadIdx.x; e < kMlpOut * kMlpHid; e += blockDim.x)
+        W4[(e / kMlpHid) * kKs + e % kMlpHid] = __float2bfloat16_rn(params[kOffW4 + e]);
+    for (int e = threadIdx.x; e < kMlpHid; e += blockDim.x) {
+        bias[e] = params[kOffB1 + e];
+        bias[kMlpHid + e] = params[kOffB2 + e];
+        bias[2 * kMlpHid + e] = params[kOffB3 + e];
+    }
+    if (threadIdx.x < kMlpOut) bias[3 * kMlpHid + threadIdx.x] = params[kOffB4 + threadIdx.x];
+    __syncthreads();
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int g = lane >> 2, t = lane & 3;
+    const int64_t ntiles = (npairs + 16 * kFwdWarps - 1) / (16 * kFwdWarps);
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int64_t r0 = tile * 16 * kFwdWarps + 16 * warp + g, r1 = r0 + 8;
+        // layer 1: A = features (16 x 16)
+        uint32_t A[8][4];
+        {
+            float f0[4] = {0, 0, 0, 0}, f1[4] = {0, 0, 0, 0};
+            if (r0 < npairs) {
+                const float* fr = feat + 16 * r0;
+                f0[0] = fr[2 * t];
+                f0[1] = fr[2 * t + 1];
+                f0[2] = fr[2 * t + 8];
+                f0[3] = fr[2 * t + 9];
+            }
+            if (r1 < npairs) {
+                const float* fr = feat + 16 * r1;
+                f1[0] = fr[2 * t];
+                f1[1] = fr[2 * t + 1];
+                f1[2] = fr[2 * t + 8];
+                f1[3] = fr[2 * t + 9];
+            }
+            uint32_t X[4] = {pack_bf16(f0[0], f0[1]), pack_bf16(f1[0], f1[1]), pack_bf16(f0[2], f0[3]),
+                             pack_bf16(f1[2], f1[3])};
+            float acc[16][4];
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+                acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.f;
+                const __nv_bfloat16* wr = W1 + (8 * j + g) * kKs1 + 2 * t;
+                mma_bf16(acc[j], X, lds32(wr), lds32(wr + 8));
+                const float b0 = bias[8 * j + 2 * t], b1 = bias[8 * j + 2 * t + 1];
+                acc[j][0] = fmaxf(acc[j][0] + b0, 0.f);
+                acc[j][1] = fmaxf(acc[j][1] + b1, 0.f);
+                acc[j][2] = fmaxf(acc[j][2] + b0, 0.f);
+                acc[j][3] = fmaxf(acc[j][3] + b1, 0.f);
+            }
+#pragma unroll
+            for (int kk = 0; kk < 8; ++kk) {
+                A[kk][0] = pack_bf16(acc[2 * kk][0], acc[2 * kk][1]);
+                A[kk][1] = pack_bf16(acc[2 * kk][2], acc[2 * kk][3]);
+                A[kk][2] = pack_bf16(acc[2 * kk + 1][0], acc[2 * kk + 1][1]);
+                A[kk][3] = pack_bf16(acc[2 * kk + 1][2], acc[2 * kk + 1][3]);
+            }
+        }
+        hidden_layer(A, W2, bias + kMlpHid, g, t);
+        hidden_layer(A, W3, bias + 2 * kMlpHid, g, t);
+        // layer 4: 8 outputs
+        float o[4] = {0, 0, 0, 0};
+        const __nv_bfloat16* wr = W4 + g * kKs + 2 * t;
+#pragma unroll
+        for (int kk = 0; kk < 8; ++kk) mma_bf16(o, A[kk], lds32(wr + 16 * kk), lds32(wr + 16 * kk + 8));
+        const float b0 = bias[3 * kMlpHid + 2 * t], b1 = bias[3 * kMlpHid + 2 * t + 1];
+        if (r0 < npairs) {
+            out[8 * r0 + 2 * t] = o[0] + b0;
+            out[8 * r0 + 2 * t + 1] = o[1] + b1;
+        }
+        if (r1 < npairs) {
+            out[8 * r1 + 2 * t] = o[2] + b0;
+            out[8 * r1 + 2 * t + 1] = o[3] + b1;
+        }
+    }
+}
+
+// network output -> world-frame start normal (zero when the trust logit is
+// negative: the Newton solve then starts cold)
+__global__ void guess_kernel(int64_t npairs, const int* __restrict__ pa, View<4, const double> q,
+                             const float* __restrict__ feat, const float* __restrict__ out, View<3, double> guess) {
+    int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= npairs) return;
+    const float* o = out + 8 * p;
+    const float* f = feat + 16 * p;
+    const double inv = 1.0 / (double)RELCP_MLP_CORR_SCALE;
+    double n[3] = {(double)f[13] + inv * o[0], (double)f[14] + inv * o[1], (double)f[15] + inv * o[2]};
+    double l = sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
+    if (!(o[4] > 0.f) || !(l > 1e-6)) {
+        guess(0, p) = guess(1, p) = guess(2, p) = 0.0;
+        return;
+    }
+    const int i = pa[p];
+    double s = q(0, i), x = q(1, i), y = q(2, i), z = q(3, i);
+    double lq = sqrt(s * s + x * x + y * y + z * z);
+    double R[9];
+    quat_to_R(s / lq, x / lq, y / lq, z / lq, R);
+    for (int k = 0; k < 3; ++k) guess(k, p) = (R[3 * k] * n[0] + R[3 * k + 1] * n[1] + R[3 * k + 2] * n[2]) / l;
+}
+
+// ---------------------------------------------------------------------------
+// training: generic tensor-core GEMM C[M x N] (+)= A[M x K] B[N x K]^T
+// ---------------------------------------------------------------------------
+constexpr int kGT = 64;  // tile M and N
+__global__ void __launch_bounds__(128) gemm_nt_kernel(int M, int N, int K, const __nv_bfloat16* __restrict__ A, int lda,
+                                                      const __nv_bfloat16* __restrict__ B, int ldb, float* __restrict__ C,
+                                                      int ldc, int accumulate) {
+    __shared__ __align__(16) __nv_bfloat16 As[kGT][16 + 8];
+    __shared__ __align__(16) __nv_bfloat16 Bs[kGT][16 + 8];
+    const int m0 = blockIdx.y * kGT, n0 = blockIdx.x * kGT;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+    float acc[8][4];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.f;
+    const __nv_bfloat16 zero = __float2bfloat16_rn(0.f);
+    for (int k0 = 0; k0 < K; k0 += 16) {
+        for (int e = threadIdx.x; e < kGT * 16; e += blockDim.x) {
+            const int r = e / 16, c = e % 16;
+            const int gm = m0 + r, gn = n0 + r, gk = k0 + c;
+            As[r][c] = (gm < M && gk < K) ? A[(int64_t)gm * lda + gk] : zero;
+            Bs[r][c] = (gn < N && gk < K) ? B[(int64_t)gn * ldb + gk] : zero;
+        }
+        __syncthreads();
+        uint32_t a[4] = {lds32(&As[16 * warp + g][2 * t]), lds32(&As[16 * warp + g + 8][2 * t]),
+                         lds32(&As[16 * warp + g][2 * t + 8]), lds32(&As[16 * warp + g + 8][2 * t + 8])};
+#pragma unroll
+        for (int j = 0; j < 8; ++j) mma_bf16(acc[j], a, lds32(&Bs[8 * j + g][2 * t]), lds32(&Bs[8 * j + g][2 * t + 8]));
+        __syncthreads();
+    }
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        const int col = n0 + 8 * j + 2 * t;
+        const int row0 = m0 + 16 * warp + g, row1 = row0 + 8;
+        const float v[4] = {acc[j][0], acc[j][1], acc[j][2], acc[j][3]};
+        const int rr[4] = {row0, row0, row1, row1};
+        const int cc[4] = {col, col + 1, col, col + 1};
+#pragma unroll
+        for (int e = 0; e < 4; ++e)
+            if (rr[e] < M && cc[e] < N) {
+                float* d = C + (int64_t)rr[e] * ldc + cc[e];
+                *d = accumulate ? *d + v[e] : v[e];
+            }
+    }
+}
+
+// dst (BF16) [rows x cols] from src (FP32) [rows x cols] (ld = cols), optionally transposed
+__global__ void cast_kernel(int64_t rows, int cols, const float* __restrict__ src, __nv_bfloat16* __restrict__ dst,
+                            int transpose) {
+    int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= rows * cols) return;
+    const int64_t r = e / cols, c = e % cols;
+    const __nv_bfloat16 v = __float2bfloat16_rn(src[e]);
+    if (transpose) dst[c * rows + r] = v;
+    else dst[e] = v;
+}
+
+// H = relu(Z + b) in place on Z (FP32), plus the BF16 copy
+__global__ void bias_relu_kernel(int64_t rows, int cols, float* __restrict__ Z, const float* __restrict__ b, int relu) {
+    int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= rows * cols) return;
+    float v = Z[e] + b[e % cols];
+    Z[e] = relu ? fmaxf(v, 0.f) : v;
+}
+
+// dZ = dH * (H > 0)
+__global__ void relu_back_kernel(int64_t n, float* __restrict__ dH, const float* __restrict__ H) {
+    int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e < n && !(H[e] > 0.f)) dH[e] = 0.f;
+}
+
+struct LossCfg {
+    float w_phi, w_trust, trust_tol;
+};
+
+// loss of one sample and dL/dO (batch mean); partial loss sums per block
+__global__ void loss_kernel(int64_t B, const float* __restrict__ O, const float* __restrict__ T, LossCfg lc,
+                            float* __restrict__ dO, double* __restrict__ part) {
+    __shared__ double sh[256 / 32];
+    int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    double L = 0.0;
+    if (b < B) {
+        const float* o = O + 8 * b;
+        const float* t = T + 4 * b;
+        float* d = dO + 8 * b;
+        const float inv = 1.0f / (float)B;
+        float en = 0.f;
+        for (int k = 0; k < 3; ++k) {
+            const float r = o[k] - t[k];
+            en += r * r;
+            d[k] = 2.f * r * inv;
+        }
+        const float rp = o[3] - t[3];
+        d[3] = 2.f * lc.w_phi * rp * inv;
+        const float e0 = t[0] * t[0] + t[1] * t[1] + t[2] * t[2];  // squared error of the seed alone
+        const float y = en < lc.trust_tol * e0 ? 1.f : 0.f;
+        const float z = o[4];
+        const float p = 1.f / (1.f + expf(-z));
+        d[4] = lc.w_trust * (p - y) * inv;
+        d[5] = d[6] = d[7] = 0.f;
+        // BCE with logits, written stably
+        const float bce = fmaxf(z, 0.f) - z * y + log1pf(expf(-fabsf(z)));
+        L = (double)en + (double)lc.w_phi * rp * rp + (double)lc.w_trust * bce;
+    }
+    for (int o = 16; o > 0; o >>= 1) L += __shfl_xor_sync(0xffffffffu, L, o);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = L;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += sh[w];
+        part[blockIdx.x] = s;
+    }
+}
+
+// column sums of dZ [rows x cols] -> out[cols] (fixed order)
+__global__ void colsum_kernel(int64_t rows, int cols, const float* __restrict__ dZ, float* __restrict__ out) {
+    const int c = blockIdx.x;
+    __shared__ float sh[256];
+    float s = 0.f;
+    for (int64_t r = threadIdx.x; r < rows; r += blockDim.x) s += dZ[r * cols + c];
+    sh[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[c] = sh[0];
+}
+
+__global__ void adam_kernel(int n, float* __restrict__ p, float* __restrict__ m, float* __restrict__ v,
+                            const float* __restrict__ gr, float lr, float b1, float b2, float eps, float c1, float c2) {
+    int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n) return;
+    const float g = gr[e];
+    const float mm = b1 * m[e] + (1.f - b1) * g;
+    const float vv = b2 * v[e] + (1.f - b2) * g * g;
+    m[e] = mm;
+    v[e] = vv;
+    p[e] -= lr * (mm / c1) / (sqrtf(vv / c2) + eps);
+}
+
+// padded entries of the parameter vector are kept at zero
+__global__ void mask_grad_kernel(float* __restrict__ grad) {
+    int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e < kMlpOut * kMlpHid) {
+        if (e / kMlpHid >= 5) grad[kOffW4 + e] = 0.f;
+    }
+    if (e < kMlpOut && e >= 5) grad[kOffB4 + e] = 0.f;
+}
+
+inline unsigned nb(int64_t n, int t = 256) { return (unsigned)((n + t - 1) / t); }
+
+relcp_status gemm_nt(int M, int N, int K, const __nv_bfloat16* A, int lda, const __nv_bfloat16* B, int ldb, float* C,
+                     int ldc, bool accumulate, cudaStream_t s) {
+    dim3 grid((N + kGT - 1) / kGT, (M + kGT - 1) / kGT);
+    note_launch();
+    gemm_nt_kernel<<<grid, 128, 0, s>>>(M, N, K, A, lda, B, ldb, C, ldc, accumulate ? 1 : 0);
+    RELCP_CUDA(cudaGetLastError());
+    return RELCP_OK;
+}
+
+relcp_status cast(int64_t rows, int cols, const float* src, __nv_bfloat16* dst, bool transpose, cudaStream_t s) {
+    if (rows * cols == 0) return RELCP_OK;
+    note_launch();
+    cast_kernel<<<nb(rows * cols), 256, 0, s>>>(rows, cols, src, dst, transpose ? 1 : 0);
+    RELCP_CUDA(cudaGetLastError());
+    return RELCP_OK;
+}
+
+}  // namespace
+
+relcp_status mlp_features_launch(const MlpFeatArgs& a, cudaStream_t s) {
+    if (a.npairs == 0) return RELCP_OK;
+    note_launch();
+    features_kernel<<<nb(a.npairs), 256, 0, s>>>(a);
+    RELCP_CUDA(cudaGetLastError());
+    return RELCP_OK;
+}
+
+relcp_status mlp_forward_launch(int64_t npairs, const float* params, const float* feat, float* out, cudaStream_t s) {
+    if (npairs == 0) return RELCP_OK;
+    static bool attr_set[64] = {false};
+    int dev = 0;
+    RELCP_CUDA(cudaGetDevice(&dev));
+    if (dev >= 0 && dev < 64 && !attr_set[dev]) {
+        RELCP_CUDA(cudaFuncSetAttribute(mlp_forward_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFwdSmem));
+        attr_set[dev] = true;
+    }
+    const int64_t ntiles = (npairs + 16 * kFwdWarps - 1) / (16 * kFwdWarps);
+    const int sms = device_sm_count();
+    int64_t blocks = (int64_t)(sms > 0 ? sms : 1) * 2;
+    if (blocks > ntiles) blocks = ntiles;
+    note_launch();
+    mlp_forward_kernel<<<(unsigned)blocks, kFwdWarps * 32, kFwdSmem, s>>>(npairs, params, feat, out);
+    RELCP_CUDA(cudaGetLastError());
+    return RELCP_OK;
+}
+
+relcp_status mlp_guess(MlpState& m, int64_t npairs, const int* pa, const int* pb, View<3, const double> x,
+                       View<4, const double> q, View<3, const double> axes, const double box[3], cudaStream_t s) {
+    if (!m.loaded) {
+        set_error("learned guess not loaded");
+        return RELCP_ERR_STATE;
+    }
+    const int64_t na = npairs > 0 ? npairs : 1;
+    RELCP_TRY(m.feat.ensure((size_t)(16 * na), s));
+    RELCP_TRY(m.out.ensure((size_t)(8 * na), s));
+    RELCP_TRY(m.guess.ensure((size_t)(3 * na), s));
+    MlpFeatArgs fa{};
+    fa.npairs = npairs;
+    fa.pa = pa;
+    fa.pb = pb;
+    fa.pstride = 1;
+    fa.x = x;
+    fa.q = q;
+    fa.axes = axes;
+    for (int k = 0; k < 3; ++k) fa.box[k] = box[k];
+    fa.snsd = nullptr;
+    fa.feat = m.feat.p;
+    fa.targets = nullptr;
+    RELCP_TRY(mlp_features_launch(fa, s));
+    RELCP_TRY(mlp_forward_launch(npairs, m.params.p, m.feat.p, m.out.p, s));
+    if (npairs > 0) {
+        note_launch();
+        guess_kernel<<<nb(npairs), 256, 0, s>>>(npairs, pa, q, m.feat.p, m.out.p, View<3, double>::soa(m.guess.p, npairs));
+        RELCP_CUDA(cudaGetLastError());
+    }
+    return RELCP_OK;
+}
+
+void mlp_release(MlpState& m, cudaStream_t s) {
+    m.params.release(s);
+    m.feat.release(s);
+    m.out.release(s);
+    m.guess.release(s);
+    m.loaded = false;
+}
+
+// one training step (see relcp_mlp_train_step)
+relcp_status mlp_train_step(int64_t B, float* params, float* am, float* av, const float* feat, const float* targets,
+                            const relcp_mlp_train_config& tc, float* grad_out, double* loss_out, cudaStream_t s) {
+    if (B <= 0 || B > (1 << 24)) {
+        set_error("batch must be in [1, 2^24]");
+        return RELCP_ERR_INVALID_ARG;
+    }
+    const int H = kMlpHid;
+    DBuf<float> Z1, Z2, Z3, O, dO, dH, grad, dH2;
+    DBuf<__nv_bfloat16> Xb, H1b, H2b, H3b, Wb, Wtb, T1, T2;
+    DBuf<double> part;
+    relcp_status st = RELCP_OK;
+    auto R = [&](relcp_status e) {
+        if (st == RELCP_OK) st = e;
+        return st != RELCP_OK;
+    };
+    do {
+        if (R(Z1.ensure(B * H, s)) || R(Z2.ensure(B * H, s)) || R(Z3.ensure(B * H, s)) || R(O.ensure(B * 8, s)) ||
+            R(dO.ensure(B * 8, s)) || R(dH.ensure(B * H, s)) || R(dH2.ensure(B * H, s)) ||
+            R(grad.ensure(kMlpParams, s)) || R(Xb.ensure(B * 16, s)) || R(H1b.ensure(B * H, s)) ||
+            R(H2b.ensure(B * H, s)) || R(H3b.ensure(B * H, s)) || R(Wb.ensure(H * H, s)) ||
+            R(Wtb.ensure(H * H, s)) || R(T1.ensure(B * H, s)) || R(T2.ensure(B * H, s)) ||
+            R(part.ensure(nb(B), s)))
+            break;
+        cudaError_t ce = cudaMemsetAsync(grad.p, 0, kMlpParams * sizeof(float), s);
+        if (ce != cudaSuccess) {
+            set_error("%s", cudaGetErrorString(ce));
+            st = RELCP_ERR_CUDA;
+            break;
+        }
+        // ---- forward
+        if (R(cast(B, 16, feat, Xb.p, false, s))) break;
+        struct L {
+            int in, out, offw, offb;
+        };
+        const L layers[4] = {{16, H, kOffW1, kOffB1}, {H, H, kOffW2, kOffB2}, {H, H, kOffW3, kOffB3}, {H, 8, kOffW4, kOffB4}};
+        float* Zs[4] = {Z1.p, Z2.p, Z3.p, O.p};
+        const __nv_bfloat16* Ins[4] = {Xb.p, H1b.p, H2b.p, H3b.p};
+        __nv_bfloat16* Outs[3] = {H1b.p, H2b.p, H3b.p};
+        for (int l = 0; l < 4 && st == RELCP_OK; ++l) {
+            const L& ly = layers[l];
+            if (R(cast(ly.out, ly.in, params + ly.offw, Wb.p, false, s))) break;
+            if (R(gemm_nt((int)B, ly.out, ly.in, Ins[l], ly.in, Wb.p, ly.in, Zs[l], ly.out, false, s))) break;
+            note_launch();
+            bias_relu_kernel<<<nb(B * ly.out), 256, 0, s>>>(B, ly.out, Zs[l], params + ly.offb, l < 3 ? 1 : 0);
+            if (l < 3 && R(cast(B, ly.out, Zs[l], Outs[l], false, s))) break;
+        }
+        if (st != RELCP_OK) break;
+        // ---- loss and dO
+        LossCfg lc{tc.w_phi, tc.w_trust, tc.trust_tol};
+        note_launch();
+        loss_kernel<<<nb(B), 256, 0, s>>>(B, O.p, targets, lc, dO.p, part.p);
+        // ---- backward: for l = 3..0: dW_l = dZ_l^T H_{l-1}, db_l = colsum dZ_l, dH_{l-1} = dZ_l W_l
+        float* dZ = dO.p;  // dZ of layer 3 (output layer, no activation)
+        int dzcols = 8;
+        for (int l = 3; l >= 0 && st == RELCP_OK; --l) {
+            const L& ly = layers[l];
+            // transposes: dZ^T [out x B], H_{l-1}^T [in x B]
+            if (R(cast(B, dzcols, dZ, T1.p, true, s))) break;
+            const float* Hprev = l == 0 ? feat : Zs[l - 1];
+            if (R(cast(B, ly.in, Hprev, T2.p, true, s))) break;
+            if (R(gemm_nt(ly.out, ly.in, (int)B, T1.p, (int)B, T2.p, (int)B, grad.p + ly.offw, ly.in, false, s))) break;
+            note_launch();
+            colsum_kernel<<<ly.out, 256, 0, s>>>(B, dzcols, dZ, grad.p + ly.offb);
+            if (l == 0) break;
+            // dH_{l-1} [B x in] = dZ [B x out] W_l [out x in]: NT form with B-operand W^T [in x out]
+            // (T1 is free again: the dW GEMM that read it precedes this cast on the stream)
+            if (R(cast(B, dzcols, dZ, T1.p, false, s))) break;
+            const __nv_bfloat16* dZb = T1.p;
+            if (R(cast(ly.out, ly.in, params + ly.offw, Wtb.p, true, s))) break;
+            float* dHn = (l % 2 == 1) ? dH.p : dH2.p;
+            if (R(gemm_nt((int)B, ly.in, ly.out, dZb, ly.out, Wtb.p, ly.out, dHn, ly.in, false, s))) break;
+            note_launch();
+            relu_back_kernel<<<nb(B * ly.in), 256, 0, s>>>(B * ly.in, dHn, Zs[l - 1]);
+            dZ = dHn;
+            dzcols = ly.in;
+        }
+        if (st != RELCP_OK) break;
+        note_launch();
+        mask_grad_kernel<<<nb(kMlpHid * kMlpIn), 256, 0, s>>>(grad.p);
+        if (grad_out) {
+            ce = cudaMemcpyAsync(grad_out, grad.p, kMlpParams * sizeof(float), cudaMemcpyDeviceToDevice, s);
+            if (ce != cudaSuccess) {
+                set_error("%s", cudaGetErrorString(ce));
+                st = RELCP_ERR_CUDA;
+                break;
+            }
+        }
+        if (tc.lr > 0.f) {
+            const float c1 = 1.f - powf(tc.beta1, (float)tc.step), c2 = 1.f - powf(tc.beta2, (float)tc.step);
+            note_launch();
+            adam_kernel<<<nb(kMlpParams), 256, 0, s>>>(kMlpParams, params, am, av, grad.p, tc.lr, tc.beta1, tc.beta2,
+                                                       tc.eps, c1, c2);
+        }
+        std::vector<double> hp(nb(B));
+        ce = cudaMemcpyAsync(hp.data(), part.p, hp.size() * sizeof(double), cudaMemcpyDeviceToHost, s);
+        if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
+        if (ce != cudaSuccess) {
+            set_error("%s", cudaGetErrorString(ce));
+            st = RELCP_ERR_CUDA;
+            break;
+        }
+        double L = 0;
+        for (double v : hp) L += v;
+        if (loss_out) *loss_out = L / (double)B;
+    } while (0);
+    DBuf<float>* fb[] = {&Z1, &Z2, &Z3, &O, &dO, &dH, &grad, &dH2};
+    for (auto* b : fb) b->release(s);
+    DBuf<__nv_bfloat16>* bb[] = {&Xb, &H1b, &H2b, &H3b, &Wb, &Wtb, &T1, &T2};
+    for (auto* b : bb) b->release(s);
+    part.release(s);
+    return st;
+}
 
 }  // namespace relcp
+
+using namespace relcp;
+
+extern "C" relcp_status relcp_mlp_features(int64_t npairs, const int32_t* pairs, int64_t n, const double* x,
+                                           const double* q, const double* axes, const double* box3,
+                                           const double* snsd_out, float* feat, float* targets, void* stream) {
+    if (npairs < 0 || n < 0 || !box3 || (npairs > 0 && (!pairs || !x || !q || !axes || !feat)))
+        return set_error("bad argument"), RELCP_ERR_INVALID_ARG;
+    if (targets && !snsd_out) return set_error("targets need snsd_out"), RELCP_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    MlpFeatArgs a{};
+    a.npairs = npairs;
+    a.pa = pairs;
+    a.pb = pairs + 1;
+    a.pstride = 2;
+    a.x = View<3, const double>::aos(x, 3);
+    a.q = View<4, const double>::aos(q, 4);
+    a.axes = View<3, const double>::aos(axes, 3);
+    for (int k = 0; k < 3; ++k) a.box[k] = box3[k];
+    a.snsd = snsd_out;
+    a.snsd_s = 10;
+    a.snsd_c = 1;
+    a.feat = feat;
+    a.targets = targets;
+    RELCP_TRY(mlp_features_launch(a, s));
+    RELCP_CUDA(cudaStreamSynchronize(s));
+    return RELCP_OK;
+}
+
+extern "C" relcp_status relcp_mlp_forward(int64_t npairs, const float* params, const float* feat, float* out,
+                                          void* stream) {
+    if (npairs < 0 || !params || (npairs > 0 && (!feat || !out))) return set_error("bad argument"), RELCP_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    RELCP_TRY(mlp_forward_launch(npairs, params, feat, out, s));
+    RELCP_CUDA(cudaStreamSynchronize(s));
+    return RELCP_OK;
+}
+
+extern "C" relcp_status relcp_mlp_train_step(int64_t batch, float* params, float* adam_m, float* adam_v,
+                                             const float* feat, const float* targets,
+                                             const relcp_mlp_train_config* cfg, float* grad_out, double* loss_out,
+                                             void* stream) {
+    if (!params || !feat || !targets || !cfg) return set_error("bad argument"), RELCP_ERR_INVALID_ARG;
+    if (cfg->lr > 0.f && (!adam_m || !adam_v || cfg->step < 1))
+        return set_error("Adam needs m, v and step >= 1"), RELCP_ERR_INVALID_ARG;
+    return mlp_train_step(batch, params, adam_m, adam_v, feat, targets, *cfg, grad_out, loss_out, (cudaStream_t)stream);
+}

@@ -101,6 +101,7 @@ extern "C" relcp_status relcp_snsd_eval_noalloc(int64_t npairs, const int32_t* p
     a.status = status;
     a.maxov_bits = nullptr;
     a.newton_max = nullptr;
+    a.iters_sum = nullptr;
     RELCP_TRY(snsd_launch(a, s));
     int bits = 0;
     RELCP_CUDA(cudaMemcpyAsync(&bits, status, sizeof(int), cudaMemcpyDeviceToHost, s));

@@ -230,6 +230,7 @@ struct SnsdArgs {
     unsigned long long* maxov_bits;  // may be null: atomicMax of the bits of max(0, -Phi) (>= 0 doubles
                                      // order like their bit patterns)
     int* newton_max;                 // may be null: atomicMax of the Newton iteration counts
+    unsigned long long* iters_sum;   // may be null: sum of the Newton iteration counts
     int* status;                     // DEV_NEWTON
 };
 relcp_status snsd_launch(const SnsdArgs& a, cudaStream_t s);

@@ -264,25 +264,32 @@ __global__ void __launch_bounds__(kThreads) snsd_kernel(SnsdArgs a) {
     // one atomic per block for the largest overlap and iteration count
     __shared__ double sh_ov[kThreads / 32];
     __shared__ int sh_it[kThreads / 32];
+    __shared__ int sh_is[kThreads / 32];
     int itabs = iters_out < 0 ? -iters_out : iters_out;
+    int itsum = itabs;
     for (int o = 16; o > 0; o >>= 1) {
         maxov = fmax(maxov, __shfl_xor_sync(0xffffffffu, maxov, o));
         itabs = max(itabs, __shfl_xor_sync(0xffffffffu, itabs, o));
+        itsum += __shfl_xor_sync(0xffffffffu, itsum, o);
     }
     if ((threadIdx.x & 31) == 0) {
         sh_ov[threadIdx.x >> 5] = maxov;
         sh_it[threadIdx.x >> 5] = itabs;
+        sh_is[threadIdx.x >> 5] = itsum;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
         double m = 0.0;
         int mi = 0;
+        long long ms = 0;
         for (int w = 0; w < kThreads / 32; ++w) {
             m = fmax(m, sh_ov[w]);
             mi = max(mi, sh_it[w]);
+            ms += sh_is[w];
         }
         if (a.maxov_bits) atomicMax(a.maxov_bits, (unsigned long long)__double_as_longlong(m));
         if (a.newton_max) atomicMax(a.newton_max, mi);
+        if (a.iters_sum) atomicAdd(a.iters_sum, (unsigned long long)ms);
     }
 }
 

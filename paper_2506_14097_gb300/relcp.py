@@ -56,12 +56,24 @@ class relcp_step_stats(ctypes.Structure):
                 ("ms_total", c_double), ("steps_done", c_int64), ("guess_used", c_int32),
                 ("newton_fallbacks", c_int32), ("ms_lcp_kernel", c_double), ("lcp_alg_bytes", c_double),
                 ("ms_snsd_kernel", c_double), ("snsd_evals", c_int64), ("lcp_launches", c_int32),
-                ("snsd_launches", c_int32), ("pair_list_rebuilt", c_int32), ("pad0", c_int32)]
+                ("snsd_launches", c_int32), ("pair_list_rebuilt", c_int32), ("pad0", c_int32),
+                ("newton_iters_c0", c_int64)]
 
 
 class relcp_lcp_info(ctypes.Structure):
     _fields_ = [("iterations", c_int32), ("status", c_int32), ("residual", c_double), ("grid_blocks", c_int32),
                 ("pad", c_int32)]
+
+
+MLP_IN, MLP_HID, MLP_OUT = 16, 128, 8
+MLP_CORR_SCALE = 32.0
+MLP_NPARAMS = 128 * 16 + 128 + 128 * 128 + 128 + 128 * 128 + 128 + 8 * 128 + 8
+
+
+class relcp_mlp_train_config(ctypes.Structure):
+    _fields_ = [("lr", ctypes.c_float), ("beta1", ctypes.c_float), ("beta2", ctypes.c_float), ("eps", ctypes.c_float),
+                ("w_phi", ctypes.c_float), ("w_trust", ctypes.c_float), ("trust_tol", ctypes.c_float),
+                ("step", c_int32)]
 
 
 class RelcpError(RuntimeError):
@@ -74,7 +86,8 @@ _lib = None
 EXPORTS = ["relcp_last_error", "relcp_kernel_launches", "relcp_version", "relcp_create", "relcp_set_config", "relcp_set_bodies",
            "relcp_step", "relcp_get_bodies", "relcp_get_box", "relcp_stats", "relcp_get_pairs", "relcp_get_rows",
            "relcp_get_contact_velocity", "relcp_destroy", "relcp_broadphase", "relcp_snsd_eval", "relcp_lcp_solve",
-           "relcp_snsd_eval_noalloc"]
+           "relcp_snsd_eval_noalloc", "relcp_mlp_features", "relcp_mlp_forward", "relcp_mlp_train_step",
+           "relcp_load_mlp"]
 
 
 def library_path() -> str:
@@ -115,6 +128,12 @@ def load(build_if_needed: bool = True):
                             c_double, c_int32, c_void_p, c_void_p, POINTER(relcp_lcp_info), c_void_p],
         "relcp_snsd_eval_noalloc": [c_int64, c_void_p, c_int64, c_void_p, c_void_p, c_void_p, c_void_p, c_int32,
                                     c_void_p, c_void_p, c_void_p],
+        "relcp_mlp_features": [c_int64, c_void_p, c_int64, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
+                               c_void_p, c_void_p],
+        "relcp_mlp_forward": [c_int64, c_void_p, c_void_p, c_void_p, c_void_p],
+        "relcp_mlp_train_step": [c_int64, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
+                                 POINTER(relcp_mlp_train_config), c_void_p, POINTER(c_double), c_void_p],
+        "relcp_load_mlp": [c_void_p, c_void_p, c_int32],
     }
     for name, args in sigs.items():
         f = getattr(L, name)
@@ -340,6 +359,45 @@ def relcp_lcp_solve(ia, ib, geom, qv, K, c: float, gamma=None, precision=RELCP_F
                                 c_void_p(_stream(stream)))
     _check(st, "relcp_lcp_solve", allow)
     return gamma[:m], uc[:nb], info
+
+
+# ---------------------------------------------------------------------------
+# learned SNSD guess (device tensors)
+# ---------------------------------------------------------------------------
+def relcp_mlp_features(pairs, x, q, axes, box, snsd_out=None, stream=None):
+    """(feat (P, 16) float32, targets (P, 4) float32 or None) on the device."""
+    import torch
+
+    P = int(pairs.shape[0])
+    feat = torch.empty((max(P, 1), MLP_IN), dtype=torch.float32, device=x.device)
+    targets = torch.empty((max(P, 1), 4), dtype=torch.float32, device=x.device) if snsd_out is not None else None
+    box_h = np.ascontiguousarray(box, dtype=np.float64)
+    st = load().relcp_mlp_features(P, _ptr(pairs), int(x.shape[0]), _ptr(x), _ptr(q), _ptr(axes), _ptr(box_h),
+                                   _ptr(snsd_out), _ptr(feat), _ptr(targets), c_void_p(_stream(stream)))
+    _check(st, "relcp_mlp_features")
+    return feat[:P], (targets[:P] if targets is not None else None)
+
+
+def relcp_mlp_forward(params, feat, stream=None):
+    import torch
+
+    P = int(feat.shape[0])
+    out = torch.empty((max(P, 1), MLP_OUT), dtype=torch.float32, device=feat.device)
+    _check(load().relcp_mlp_forward(P, _ptr(params), _ptr(feat), _ptr(out), c_void_p(_stream(stream))),
+           "relcp_mlp_forward")
+    return out[:P]
+
+
+def relcp_mlp_train_step(params, m, v, feat, targets, cfg: relcp_mlp_train_config, grad=None, stream=None) -> float:
+    loss = c_double(0.0)
+    st = load().relcp_mlp_train_step(int(feat.shape[0]), _ptr(params), _ptr(m), _ptr(v), _ptr(feat), _ptr(targets),
+                                     byref(cfg), _ptr(grad), byref(loss), c_void_p(_stream(stream)))
+    _check(st, "relcp_mlp_train_step")
+    return float(loss.value)
+
+
+def relcp_load_mlp(ctx, params):
+    _check(load().relcp_load_mlp(ctx, _ptr(params), _kind(params)), "relcp_load_mlp")
 
 
 # ---------------------------------------------------------------------------
