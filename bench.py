@@ -113,17 +113,24 @@ class Clocks:
                 "samples": len(sm)}
 
 
-def run_gpu_arm(R, torch, sc, precision, guess, steps, warmup, flush, stream, nvtx_from=None):
+def new_sim(R, sc, precision, guess, timing, stream, mlp_params):
+    sim = R.Simulation(make_cfg(R, sc, precision, guess, timing=timing), stream)
+    if guess == R.RELCP_GUESS_MLP:
+        R.relcp_load_mlp(sim.ctx, mlp_params)
+    return sim
+
+
+def run_gpu_arm(R, torch, sc, precision, guess, steps, warmup, flush, stream, nvtx_from=None, mlp_params=None):
     """W warm-up steps on one context, then `steps` timed steps from the initial
     state on a fresh context.  Returns per-step times and accumulated stats."""
     x, q, axes = (np.ascontiguousarray(a) for a in (sc.x, sc.q, sc.axes))
     if warmup > 0:
-        sim = R.Simulation(make_cfg(R, sc, precision, guess, timing=False), stream.cuda_stream)
+        sim = new_sim(R, sc, precision, guess, False, stream.cuda_stream, mlp_params)
         sim.set_bodies(x, q, axes)
         for _ in range(warmup):
             sim.step(1, allow=(R.RELCP_ERR_NOT_CONVERGED,))
         sim.close()
-    sim = R.Simulation(make_cfg(R, sc, precision, guess, timing=True), stream.cuda_stream)
+    sim = new_sim(R, sc, precision, guess, True, stream.cuda_stream, mlp_params)
     sim.set_bodies(x, q, axes)
     torch.cuda.synchronize()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
@@ -159,6 +166,8 @@ def run_gpu_arm(R, torch, sc, precision, guess, steps, warmup, flush, stream, nv
             acc["ms_other"] += s.ms_augment
             acc["ms_step_events"] += s.ms_total
             acc["rebuilds"] += s.pair_list_rebuilt
+            acc["newton_c0"] = acc.get("newton_c0", 0) + s.newton_iters_c0
+            acc["pairs_total"] = acc.get("pairs_total", 0) + s.n_pairs
     torch.cuda.synchronize()
     if nvtx_from is not None and nvtx_from < steps:
         torch.cuda.nvtx.range_pop()
@@ -170,7 +179,7 @@ def run_gpu_arm(R, torch, sc, precision, guess, steps, warmup, flush, stream, nv
     return times, acc
 
 
-def run_e2e(R, torch, sc, precision, guess, steps):
+def run_e2e(R, torch, sc, precision, guess, steps, mlp_params=None):
     """The same steps through the public C ABI with host buffers: every step
     copies the body state in (set_bodies: x, q, semi-axes) and the result out
     (get_bodies: x, q and the step velocity).  The workload has no background
@@ -180,6 +189,8 @@ def run_e2e(R, torch, sc, precision, guess, steps):
     u = np.zeros((n, 6))
     cfg = make_cfg(R, sc, precision, guess, timing=False)
     sim = R.Simulation(cfg)
+    if guess == R.RELCP_GUESS_MLP:
+        R.relcp_load_mlp(sim.ctx, mlp_params)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     box = np.asarray(sc.box, dtype=np.float64)
@@ -280,6 +291,7 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     ap.add_argument("--ref-budget", type=float, default=150.0)
     ap.add_argument("--jacobi", type=int, default=0, help="1: Jacobi-scaled projected-gradient steps")
+    ap.add_argument("--cold", action="store_true", help="cold SNSD start only (no learned guess)")
     ap.add_argument("--nvtx-from", type=int, default=None,
                     help="profiling aid: wrap timed steps >= this index in the NVTX range relcp_profile")
     args = ap.parse_args()
@@ -315,14 +327,29 @@ def main():
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 
     precision = R.RELCP_MIXED
+    # learned SNSD guess: trained before the timed region on pairs the method
+    # generates in a separate, smaller compaction (another seed)
+    mlp_params, learned_info = None, None
     guess = R.RELCP_GUESS_COLD
+    if not args.cold:
+        from paper_2506_14097_gb300 import learned
+
+        t_tr = time.perf_counter()
+        feat, targ = learned.harvest_compaction(n=4096, seed=11, steps=300, every=10)
+        mlp_params, losses = learned.train(feat, targ, epochs=20, batch=4096, lr=2e-3, seed=0)
+        torch.cuda.synchronize()
+        learned_info = {"train_samples": int(feat.shape[0]), "epochs": 20, "loss_first": losses[0],
+                        "loss_last": losses[-1], "train_s": time.perf_counter() - t_tr,
+                        "harvest": "4,096-body compaction, seed 11, every 10th of 300 steps, FP64 SNSD targets"}
+        guess = R.RELCP_GUESS_MLP
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
     clocks = Clocks(local)
     clocks.start()
     t_wall0 = time.perf_counter()
-    times, acc = run_gpu_arm(R, torch, sc, precision, guess, args.steps, args.warmup, flush, stream, args.nvtx_from)
+    times, acc = run_gpu_arm(R, torch, sc, precision, guess, args.steps, args.warmup, flush, stream, args.nvtx_from,
+                             mlp_params)
     t_wall = time.perf_counter() - t_wall0
     clk = clocks.stop()
     total_ms = float(sum(times))
@@ -331,6 +358,15 @@ def main():
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         total_ms = float(t.item())
     value = world * sc.n * args.steps / (total_ms / 1e3)
+
+    cold = None
+    if guess == R.RELCP_GUESS_MLP and not args.no_fp64:
+        times_c, acc_c = run_gpu_arm(R, torch, sc, precision, R.RELCP_GUESS_COLD, args.steps, args.warmup, flush,
+                                     stream)
+        tc = float(sum(times_c))
+        cold = {"value": sc.n * args.steps / (tc / 1e3), "unit": UNIT, "ms_per_step": tc / args.steps,
+                "newton_iters_per_pair_c0": acc_c.get("newton_c0", 0) / max(acc_c.get("pairs_total", 1), 1),
+                "max_overlap": acc_c["max_overlap"]}
 
     fp64 = None
     if not args.no_fp64:
@@ -343,7 +379,7 @@ def main():
 
     e2e_steps = args.steps if args.e2e_steps is None else args.e2e_steps
     if e2e_steps > 0:
-        e2e_t, h2d, d2h = run_e2e(R, torch, sc, precision, guess, e2e_steps)
+        e2e_t, h2d, d2h = run_e2e(R, torch, sc, precision, guess, e2e_steps, mlp_params)
         e2e_value = world * sc.n * e2e_steps / e2e_t
     else:
         e2e_value, h2d, d2h = None, 0, 0
@@ -358,7 +394,8 @@ def main():
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "bodies": sc.n, "precision": "mixed (FP32 bulk, FP64 checks)",
-                       "guess": "cold", "lcp_steps": "jacobi-scaled BB" if args.jacobi else "BB",
+                       "guess": "learned" if guess == R.RELCP_GUESS_MLP else "cold",
+                       "lcp_steps": "jacobi-scaled BB" if args.jacobi else "BB",
                        "l2": "flushed between steps (256 MiB write)",
                        "parallelism": "replicas" if world > 1 else "single"},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
@@ -375,6 +412,8 @@ def main():
             "clocks": clk,
             "fp64_gpu": fp64,
             "speedup_vs_fp64": (value / fp64["value"]) if fp64 else None,
+            "mixed_cold": cold,
+            "learned": learned_info,
             "stats": {"depth_max": acc["depth_max"], "depth_mean": acc["depth_sum"] / args.steps,
                       "rows_max": acc["rows_max"], "pairs_max": acc["pairs_max"],
                       "lcp_iters_total": acc["lcp_iters"], "max_overlap": acc["max_overlap"],
@@ -385,6 +424,7 @@ def main():
                                    "lcp_incl_csr": acc["ms_lcp_phase"], "rest": acc["ms_other"],
                                    "to_last_sync": acc["ms_step_events"]},
                       "pair_list_rebuilds": acc["rebuilds"],
+                      "newton_iters_per_pair_c0": acc.get("newton_c0", 0) / max(acc.get("pairs_total", 1), 1),
                       "phi_final": sc.meta["volume"] / float(np.prod(acc["box_final"]))},
         }
         print(json.dumps(line), flush=True)

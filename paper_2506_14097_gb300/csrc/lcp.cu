@@ -29,9 +29,41 @@ namespace relcp {
 
 namespace {
 
-constexpr int kThreads = 768;
+#ifndef RELCP_LCP_THREADS
+#define RELCP_LCP_THREADS 640
+#endif
+#ifndef RELCP_LCP_INC_PER_LANE
+#define RELCP_LCP_INC_PER_LANE 5
+#endif
+// 640 threads leave 96 registers per thread at one CTA per SM: the row and
+// body slots and the 10 register-resident incidences per body fit unspilled
+constexpr int kThreads = RELCP_LCP_THREADS;
 constexpr int kMaxCtasPerSm = 1;
 constexpr int kMixedCheckEvery = 4;  // mixed path: FP64 termination residual every 4th iteration
+
+#ifdef RELCP_LCP_TRACE
+// optional phase timing of block 0 (nanoseconds summed over iterations):
+// [0] scatter, [1] barrier 1, [2] gather, [3] block reduction + partials,
+// [4] barrier 2, [5] grid reduction + step length, [6] iterations
+__device__ unsigned long long g_lcp_trace[8];
+__device__ __forceinline__ unsigned long long gtimer() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+#define TRACE_MARK(k)                                                            \
+    do {                                                                         \
+        if (blockIdx.x == 0 && threadIdx.x == 0) {                               \
+            unsigned long long t_ = gtimer();                                    \
+            g_lcp_trace[k] += t_ - t_prev;                                       \
+            t_prev = t_;                                                         \
+        }                                                                        \
+    } while (0)
+#else
+#define TRACE_MARK(k) \
+    do {              \
+    } while (0)
+#endif
 constexpr int kNred = 4;  // ss, sy, yy, residual-or-maxdiag
 constexpr long long kSpinLimit = 1ll << 26;
 
@@ -67,7 +99,7 @@ struct KArgs {
     double c, tol;
     int max_iter;
     int check_every;  // FP64 residual on every check_every-th iteration (and the first)
-    double* partials;
+    unsigned long long* partials;  // kNred words per block (see block_partials)
     unsigned* bar;
     int* status;
     LcpDevResult* result;
@@ -76,31 +108,31 @@ struct KArgs {
 __device__ __forceinline__ double ldcg(const double* p) { return __ldcg(p); }
 __device__ __forceinline__ float ldcg(const float* p) { return __ldcg(p); }
 
-__device__ __forceinline__ void red_add_relaxed(unsigned* p, unsigned v) {
-    asm volatile("red.relaxed.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+__device__ __forceinline__ void red_add_release(unsigned* p, unsigned v) {
+    asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
-__device__ __forceinline__ unsigned ld_relaxed(const unsigned* p) {
+__device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
     unsigned v;
-    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
     return v;
 }
 
 // Bounded grid barrier on a monotonic arrival counter (zeroed before the
 // launch): barrier number e of the launch completes when the counter reaches
-// e * gridDim.x.  Thread 0 of each block publishes the block's writes (fence,
-// then a relaxed add), polls with relaxed loads (no cache invalidation per
-// poll) and fences once when the count is reached.  It sleeps only after a
-// short busy spin and gives up after kSpinLimit polls (DEV_TIMEOUT).
+// e * gridDim.x.  After a __syncthreads, thread 0 of each block arrives with
+// a release add (which publishes every write the block made before the
+// __syncthreads) and polls with acquire loads (the block's later reads see
+// every block's published writes).  It sleeps only after a short busy spin
+// and gives up after kSpinLimit polls (DEV_TIMEOUT).
 __device__ bool grid_barrier(unsigned* count, unsigned* epoch, int* status) {
     __shared__ int timed_out;
     __syncthreads();
     if (threadIdx.x == 0) {
         timed_out = 0;
         const unsigned target = (++(*epoch)) * gridDim.x;
-        __threadfence();
-        red_add_relaxed(count, 1u);
+        red_add_release(count, 1u);
         long long spins = 0;
-        while (ld_relaxed(count) < target) {
+        while (ld_acquire(count) < target) {
             if (++spins > kSpinLimit) {
                 atomicOr(status, DEV_TIMEOUT);
                 timed_out = 1;
@@ -108,7 +140,6 @@ __device__ bool grid_barrier(unsigned* count, unsigned* epoch, int* status) {
             }
             if (spins > 256) __nanosleep(16);
         }
-        __threadfence();
     }
     __syncthreads();
     return timed_out == 0;
@@ -141,33 +172,93 @@ __device__ void block_reduce_store(const A v[kNred], unsigned maxmask, double* o
     __syncthreads();
 }
 
-// every block: reduce all blocks' partials in a fixed order
-__device__ void grid_reduce(const double* partials, unsigned maxmask, double tot[kNred]) {
-    __shared__ double res[kNred];
+// Partials are 64-bit words, kNred per block.  A sum slot holds the bits of a
+// value in the solve precision R (the mixed path sums in FP32: FP64 runs at a
+// small fraction of the FP32 rate on this part); a max slot holds the bits of a
+// non-negative double, whose maximum is the unsigned maximum of the bit
+// patterns.  The integer max needs no FP64 unit, and a NaN residual (bits
+// above +inf) survives it and fails the convergence test, where fmax would
+// drop it.
+__device__ __forceinline__ unsigned long long to_word(float x) { return (unsigned long long)__float_as_uint(x); }
+__device__ __forceinline__ unsigned long long to_word(double x) {
+    return (unsigned long long)__double_as_longlong(x);
+}
+template <class R>
+__device__ __forceinline__ R from_word(unsigned long long w);
+template <>
+__device__ __forceinline__ float from_word<float>(unsigned long long w) {
+    return __uint_as_float((unsigned)w);
+}
+template <>
+__device__ __forceinline__ double from_word<double>(unsigned long long w) {
+    return __longlong_as_double((long long)w);
+}
+__device__ __forceinline__ unsigned long long umax64(unsigned long long x, unsigned long long y) {
+    return x > y ? x : y;
+}
+
+// every block: reduce all blocks' partials in a fixed order.  All partials
+// are fetched at once (one L2 round trip, one word per thread) into shared
+// memory; warp 0 then folds them block by block.  The reduced words are valid
+// in thread 0 only; the caller ends the step with a __syncthreads.
+constexpr int kMaxBlocks = 256;
+template <class R>
+__device__ void grid_reduce_t0(const unsigned long long* partials, unsigned maxmask,
+                               unsigned long long tot[kNred]) {
+    __shared__ unsigned long long buf[kMaxBlocks * kNred];
+    const int n = gridDim.x * kNred;
+    for (int t = threadIdx.x; t < n; t += blockDim.x) buf[t] = __ldcg(partials + t);
+    __syncthreads();
     if (threadIdx.x < 32) {
         const int lane = threadIdx.x;
-        double acc[kNred] = {0, 0, 0, 0};
-        for (int b = lane; b < (int)gridDim.x; b += 32) {
-#pragma unroll
-            for (int k = 0; k < kNred; ++k) {
-                double x = __ldcg(partials + (size_t)b * kNred + k);
-                acc[k] = ((maxmask >> k) & 1u) ? fmax(acc[k], x) : acc[k] + x;
-            }
-        }
 #pragma unroll
         for (int k = 0; k < kNred; ++k) {
-            double x = acc[k];
-            for (int o = 16; o > 0; o >>= 1) {
-                double y = __shfl_down_sync(0xffffffffu, x, o);
-                x = ((maxmask >> k) & 1u) ? fmax(x, y) : x + y;
+            if ((maxmask >> k) & 1u) {
+                unsigned long long m = 0;
+                for (int b = lane; b < (int)gridDim.x; b += 32) m = umax64(m, buf[b * kNred + k]);
+                for (int o = 16; o > 0; o >>= 1) m = umax64(m, __shfl_down_sync(0xffffffffu, m, o));
+                tot[k] = m;
+            } else {
+                R x = R(0);
+                for (int b = lane; b < (int)gridDim.x; b += 32) x += from_word<R>(buf[b * kNred + k]);
+                for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+                tot[k] = to_word(x);
             }
-            if (lane == 0) res[k] = x;
         }
     }
-    __syncthreads();
+}
+
+// per-block partials of an iteration: the three BB products (sums in the
+// solve precision) and, on check iterations, the FP64 residual (a max);
+// threads 0..3 write the block's words
+template <class R>
+__device__ void block_partials(const R v[3], double res, bool with_res, unsigned long long* out) {
+    __shared__ R sh[kThreads / 32][3];
+    __shared__ unsigned long long shr[kThreads / 32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
-    for (int k = 0; k < kNred; ++k) tot[k] = res[k];
+    for (int k = 0; k < 3; ++k) {
+        R x = v[k];
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+        if (lane == 0) sh[wid][k] = x;
+    }
+    if (with_res) {
+        unsigned long long m = (unsigned long long)__double_as_longlong(res);
+        for (int o = 16; o > 0; o >>= 1) m = umax64(m, __shfl_down_sync(0xffffffffu, m, o));
+        if (lane == 0) shr[wid] = m;
+    }
     __syncthreads();
+    if (threadIdx.x < 3) {
+        const int k = threadIdx.x;
+        R x = sh[0][k];
+        for (int w = 1; w < kThreads / 32; ++w) x += sh[w][k];
+        out[k] = to_word(x);
+    } else if (threadIdx.x == 3) {
+        unsigned long long m = 0;
+        if (with_res)
+            for (int w = 0; w < kThreads / 32; ++w) m = umax64(m, shr[w]);
+        out[3] = m;
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -184,14 +275,14 @@ __device__ void grid_reduce(const double* partials, unsigned maxmask, double tot
 //   ucp[8 b .. 8 b + 5] = K D gamma of b one 32-byte (FP32) / 64-byte record
 // ---------------------------------------------------------------------------
 constexpr int kLanesPerBody = 2;
-constexpr int kIncPerLane = 4;
+constexpr int kIncPerLane = RELCP_LCP_INC_PER_LANE;
 
 template <class R>
 struct BodySlot {
     int b;                   // body, or >= nbodies for none
     int e0, e1;              // CSR range of the body
     int code[kIncPerLane];   // (row << 1) | side, or -1
-    R c[kIncPerLane][6];     // signed coefficients: side a (-n, -r_a x n), side b (n, r_b x n)
+    R c[kIncPerLane][6];     // K times the signed row coefficients: side a (-n, -r_a x n), side b (n, r_b x n)
 };
 
 template <class R>
@@ -200,6 +291,7 @@ struct RowSlot {
     int i, j;
     R g[9];
     R q, invd;
+    R gm, gv;                // (gamma, g) of the current iterate, carried between iterations
 };
 
 template <class R>
@@ -217,6 +309,29 @@ __device__ __forceinline__ void load_coefs(const KArgs<R>& a, int code, R c[6]) 
 }
 
 template <class R>
+__device__ __forceinline__ void load_K(const KArgs<R>& a, int b, R K[7]) {
+#pragma unroll
+    for (int kk = 0; kk < 7; ++kk) K[kk] = a.K[kk][b];
+}
+
+// c <- K c: the body operator applied to one row's coefficients, so that the
+// body's contact velocity Uc = K sum_a c_a gamma_a is the plain sum of the
+// premultiplied coefficients weighted by gamma (K is symmetric:
+// K[0] scalar translation, rotation block (K1 K4 K5; K4 K2 K6; K5 K6 K3))
+template <class R>
+__device__ __forceinline__ void apply_K(const R K[7], R c[6]) {
+    const R r3 = K[1] * c[3] + K[4] * c[4] + K[5] * c[5];
+    const R r4 = K[4] * c[3] + K[2] * c[4] + K[6] * c[5];
+    const R r5 = K[5] * c[3] + K[6] * c[4] + K[3] * c[5];
+    c[0] *= K[0];
+    c[1] *= K[0];
+    c[2] *= K[0];
+    c[3] = r3;
+    c[4] = r4;
+    c[5] = r5;
+}
+
+template <class R>
 __device__ void load_body_slot(const KArgs<R>& a, int b, int lane, BodySlot<R>& S) {
     S.b = b;
     S.e0 = S.e1 = 0;
@@ -225,12 +340,15 @@ __device__ void load_body_slot(const KArgs<R>& a, int b, int lane, BodySlot<R>& 
     if (b >= a.nbodies) return;
     S.e0 = a.inc_off[b];
     S.e1 = a.inc_off[b + 1];
+    R K[7];
+    load_K(a, b, K);
 #pragma unroll
     for (int k = 0; k < kIncPerLane; ++k) {
         const int e = S.e0 + lane + kLanesPerBody * k;
         if (e < S.e1) {
             S.code[k] = a.inc[e];
             load_coefs(a, S.code[k], S.c[k]);
+            apply_K(K, S.c[k]);
         }
     }
 }
@@ -245,6 +363,20 @@ __device__ void load_row_slot(const KArgs<R>& a, int r, int nrows, RowSlot<R>& S
     for (int k = 0; k < 9; ++k) S.g[k] = a.geom[k][r];
     S.q = a.qr[r];
     S.invd = a.invd ? a.invd[r] : R(1);
+    S.gm = a.gamma_io[r];
+    S.gv = R(0);
+}
+
+// the projected step of one row, gamma' = max(0, gamma - alpha g / A_aa), with
+// explicit roundings: the body threads of the scatter and the row's own thread
+// evaluate it on the same inputs and must agree bit for bit
+__device__ __forceinline__ float proj_step(float gm, float g, float invd, float alpha) {
+    const float v = __fmaf_rn(-alpha, __fmul_rn(g, invd), gm);
+    return v > 0.f ? v : 0.f;
+}
+__device__ __forceinline__ double proj_step(double gm, double g, double invd, double alpha) {
+    const double v = __fma_rn(-alpha, __dmul_rn(g, invd), gm);
+    return v > 0.0 ? v : 0.0;
 }
 
 template <class R>
@@ -252,19 +384,19 @@ __device__ __forceinline__ typename Vec2<R>::T ld_pair(const typename Vec2<R>::T
     return __ldcg(p);
 }
 
-// one incidence: gamma' = P(gamma - alpha g/A_aa) (or gamma), accumulated wrench
+// one incidence: gamma' = P(gamma - alpha g/A_aa) (or gamma), accumulated
+// wrench.  A row inside the row slots (r < threads in the grid) gets gamma'
+// from its own thread; the side-a body thread stores it for the others.
 template <class R>
 __device__ __forceinline__ void incidence(const KArgs<R>& a, int code, const R c[6], int src, bool project,
-                                          R alpha_r, R w[6]) {
+                                          R alpha_r, int nslots, R w[6]) {
     const int r = code >> 1;
     const typename Vec2<R>::T p = ld_pair<R>(a.gg[src] + r);
     R gm = p.x;
     if (project) {
-        R gs = p.y;
-        if (a.invd) gs *= a.invd[r];
-        const R v = gm - alpha_r * gs;
-        gm = v > R(0) ? v : R(0);
-        if (!(code & 1)) a.gg[1 - src][r].x = gm;
+        const R inv = a.invd ? a.invd[r] : R(1);
+        gm = proj_step(gm, p.y, inv, alpha_r);
+        if (!(code & 1) && r >= nslots) a.gg[1 - src][r].x = gm;
     }
 #pragma unroll
     for (int k = 0; k < 6; ++k) w[k] += gm * c[k];
@@ -293,21 +425,6 @@ __device__ __forceinline__ void store_rec(double* p, const double u[6]) {
 }
 
 template <class R>
-__device__ __forceinline__ void store_uc(const KArgs<R>& a, int b, const R w[6]) {
-    R K[7];
-#pragma unroll
-    for (int kk = 0; kk < 7; ++kk) K[kk] = a.K[kk][b];
-    R o[6];
-    o[0] = K[0] * w[0];
-    o[1] = K[0] * w[1];
-    o[2] = K[0] * w[2];
-    o[3] = K[1] * w[3] + K[4] * w[4] + K[5] * w[5];
-    o[4] = K[4] * w[3] + K[2] * w[4] + K[6] * w[5];
-    o[5] = K[5] * w[3] + K[6] * w[4] + K[3] * w[5];
-    store_rec(a.ucp + 8 * (int64_t)b, o);
-}
-
-template <class R>
 __device__ __forceinline__ void reduce_lanes(R w[6]) {
 #pragma unroll
     for (int sh = kLanesPerBody / 2; sh > 0; sh >>= 1)
@@ -316,93 +433,147 @@ __device__ __forceinline__ void reduce_lanes(R w[6]) {
 }
 
 // phase 1: contact velocity Uc = K D gamma' for every body; gamma' read from
-// buffer src (projected step when `project`), written to buffer 1 - src
+// buffer src (projected step when `project`), written to buffer 1 - src for
+// rows outside the row slots.  The slot's coefficients already carry K;
+// incidences read from memory are premultiplied on the fly.
 template <class R>
 __device__ void scatter_phase(const KArgs<R>& a, const BodySlot<R>& S, int src, bool project, R alpha_r) {
     const int lane = threadIdx.x & (kLanesPerBody - 1);
+    const int nslots = gridDim.x * blockDim.x;
     {
         R w[6] = {0, 0, 0, 0, 0, 0};
 #pragma unroll
         for (int k = 0; k < kIncPerLane; ++k)
-            if (S.code[k] >= 0) incidence(a, S.code[k], S.c[k], src, project, alpha_r, w);
-        for (int e = S.e0 + kLanesPerBody * kIncPerLane + lane; e < S.e1; e += kLanesPerBody) {
-            const int code = a.inc[e];
-            R c[6];
-            load_coefs(a, code, c);
-            incidence(a, code, c, src, project, alpha_r, w);
+            if (S.code[k] >= 0) incidence(a, S.code[k], S.c[k], src, project, alpha_r, nslots, w);
+        const int e_over = S.e0 + kLanesPerBody * kIncPerLane + lane;
+        if (e_over < S.e1) {
+            R K[7];
+            load_K(a, S.b, K);
+            for (int e = e_over; e < S.e1; e += kLanesPerBody) {
+                const int code = a.inc[e];
+                R c[6];
+                load_coefs(a, code, c);
+                apply_K(K, c);
+                incidence(a, code, c, src, project, alpha_r, nslots, w);
+            }
         }
         reduce_lanes(w);
-        if (S.b < a.nbodies && lane == 0) store_uc(a, S.b, w);
+        if (S.b < a.nbodies && lane == 0) store_rec(a.ucp + 8 * (int64_t)S.b, w);
     }
     // bodies beyond one slot per thread
-    const int groups_total = (gridDim.x * blockDim.x) / kLanesPerBody;
+    const int groups_total = nslots / kLanesPerBody;
     const int gid = (blockIdx.x * blockDim.x + threadIdx.x) / kLanesPerBody;
     const int warp_first = gid & ~(32 / kLanesPerBody - 1);
     for (int k = 1; warp_first + k * groups_total < a.nbodies; ++k) {
         const int b = gid + k * groups_total;
         R w[6] = {0, 0, 0, 0, 0, 0};
         if (b < a.nbodies) {
+            R K[7];
+            load_K(a, b, K);
             const int e0 = a.inc_off[b], e1 = a.inc_off[b + 1];
             for (int e = e0 + lane; e < e1; e += kLanesPerBody) {
                 const int code = a.inc[e];
                 R c[6];
                 load_coefs(a, code, c);
-                incidence(a, code, c, src, project, alpha_r, w);
+                apply_K(K, c);
+                incidence(a, code, c, src, project, alpha_r, nslots, w);
             }
         }
         reduce_lanes(w);
-        if (b < a.nbodies && lane == 0) store_uc(a, b, w);
+        if (b < a.nbodies && lane == 0) store_rec(a.ucp + 8 * (int64_t)b, w);
     }
 }
 
-// phase 2 for one row: g' in the solve precision into buffer nw, BB products
-// against buffer old (if any), FP64 residual on check iterations
+// phase 2 for one row: g' = q + c d^T Uc in the solve precision, the BB
+// products of s = gamma' - gamma, y = g' - g, and the FP64 natural residual on
+// check iterations.  Every load is issued before the row's store.
 template <class R>
-__device__ __forceinline__ void row_update(const KArgs<R>& a, int r, int i, int j, const R g9[9], R q, R invd, int nw,
-                                           int old, bool check, R acc[3], double& res) {
-    R ui[6], uj[6];
-    load_rec(a.ucp + 8 * (int64_t)i, ui);
-    load_rec(a.ucp + 8 * (int64_t)j, uj);
+__device__ __forceinline__ R row_rate(const R g9[9], const R ui[6], const R uj[6]) {
     R rate = g9[0] * (uj[0] - ui[0]) + g9[1] * (uj[1] - ui[1]) + g9[2] * (uj[2] - ui[2]);
     rate += g9[6] * uj[3] + g9[7] * uj[4] + g9[8] * uj[5];
     rate -= g9[3] * ui[3] + g9[4] * ui[4] + g9[5] * ui[5];
-    const R g = q + (R)a.c * rate;
-    const R gm = ldcg(&a.gg[nw][r].x);
-    a.gg[nw][r].y = g;
-    if (old >= 0) {
-        const typename Vec2<R>::T po = ld_pair<R>(a.gg[old] + r);
-        const R s = gm - po.x;
-        const R y = g - po.y;
-        if (a.invd) {
-            // metric diag(A): s^T D s, s^T y, y^T D^-1 y
-            acc[0] += s * s / invd;
-            acc[1] += s * y;
-            acc[2] += y * y * invd;
-        } else {
-            acc[0] += s * s;
-            acc[1] += s * y;
-            acc[2] += y * y;
-        }
-    }
-    if (check) {
-        const double gd = a.q[r] + a.c * (double)rate;
-        res = fmax(res, fabs(fmin(a.diag[r] * (double)gm, gd)));
-    }
+    return rate;
 }
 
 template <class R>
-__device__ void gather_phase(const KArgs<R>& a, const RowSlot<R>& S, const int nrows, int nw, int old, bool check,
-                             R v[3], double* resid) {
+__device__ __forceinline__ void bb_accumulate(const KArgs<R>& a, R s, R y, R invd, R acc[3]) {
+    if (a.invd) {
+        // metric diag(A): s^T D s, s^T y, y^T D^-1 y
+        acc[0] += s * s / invd;
+        acc[1] += s * y;
+        acc[2] += y * y * invd;
+    } else {
+        acc[0] += s * s;
+        acc[1] += s * y;
+        acc[2] += y * y;
+    }
+}
+
+// a row outside the row slots: everything from memory; gamma' was stored by
+// the side-a body thread of the scatter
+template <class R>
+__device__ __forceinline__ void row_update_mem(const KArgs<R>& a, int r, int nw, int old, bool check, R acc[3],
+                                               double& res) {
+    const int i = a.ia[r], j = a.ib[r];
+    R g9[9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) g9[k] = a.geom[k][r];
+    const R q = a.qr[r];
+    const R invd = a.invd ? a.invd[r] : R(1);
+    R ui[6], uj[6];
+    load_rec(a.ucp + 8 * (int64_t)i, ui);
+    load_rec(a.ucp + 8 * (int64_t)j, uj);
+    const R gm = ldcg(&a.gg[nw][r].x);
+    typename Vec2<R>::T po;
+    if (old >= 0) po = ld_pair<R>(a.gg[old] + r);
+    double qd = 0.0, dg = 0.0;
+    if (check) {
+        qd = a.q[r];
+        dg = a.diag[r];
+    }
+    const R rate = row_rate(g9, ui, uj);
+    const R g = q + (R)a.c * rate;
+    a.gg[nw][r].y = g;
+    if (old >= 0) bb_accumulate(a, gm - po.x, g - po.y, invd, acc);
+    if (check) res = fmax(res, fabs(fmin(dg * (double)gm, qd + a.c * (double)rate)));
+}
+
+// the thread's own row: (gamma, g) of the current iterate are in registers,
+// gamma' is recomputed here with the scatter's projected step, and the new
+// pair is written with one store
+template <class R>
+__device__ __forceinline__ void row_update_slot(const KArgs<R>& a, RowSlot<R>& S, int nw, bool first, bool check,
+                                                R alpha_r, R acc[3], double& res) {
+    R ui[6], uj[6];
+    load_rec(a.ucp + 8 * (int64_t)S.i, ui);
+    load_rec(a.ucp + 8 * (int64_t)S.j, uj);
+    double qd = 0.0, dg = 0.0;
+    if (check) {
+        qd = a.q[S.r];
+        dg = a.diag[S.r];
+    }
+    const R gm = first ? S.gm : proj_step(S.gm, S.gv, S.invd, alpha_r);
+    const R rate = row_rate(S.g, ui, uj);
+    const R g = S.q + (R)a.c * rate;
+    typename Vec2<R>::T p;
+    p.x = gm;
+    p.y = g;
+    a.gg[nw][S.r] = p;
+    if (!first) bb_accumulate(a, gm - S.gm, g - S.gv, S.invd, acc);
+    if (check) res = fmax(res, fabs(fmin(dg * (double)gm, qd + a.c * (double)rate)));
+    S.gm = gm;
+    S.gv = g;
+}
+
+template <class R>
+__device__ void gather_phase(const KArgs<R>& a, RowSlot<R>& S, const int nrows, int nw, int old, bool check,
+                             R alpha_r, R v[3], double* resid) {
     R acc[3] = {0, 0, 0};
     double res = 0.0;
-    if (S.r >= 0) row_update(a, S.r, S.i, S.j, S.g, S.q, S.invd, nw, old, check, acc, res);
+    if (S.r >= 0) row_update_slot(a, S, nw, old < 0, check, alpha_r, acc, res);
     const int stride = gridDim.x * blockDim.x;
-    for (int r = blockIdx.x * blockDim.x + threadIdx.x + stride; r < nrows; r += stride) {
-        R g9[9];
-#pragma unroll
-        for (int k = 0; k < 9; ++k) g9[k] = a.geom[k][r];
-        row_update(a, r, a.ia[r], a.ib[r], g9, a.qr[r], a.invd ? a.invd[r] : R(1), nw, old, check, acc, res);
-    }
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x + stride; r < nrows; r += stride)
+        row_update_mem(a, r, nw, old, check, acc, res);
     v[0] = acc[0];
     v[1] = acc[1];
     v[2] = acc[2];
@@ -416,7 +587,7 @@ __global__ void __launch_bounds__(kThreads) lcp_kernel(KArgs<R> a) {
     unsigned epoch = 0;  // used by thread 0 only
     R v[3];
     double res_t;
-    double tot[kNred];
+    unsigned long long tot[kNred];
     const int tid = blockIdx.x * blockDim.x + threadIdx.x;
     const int stride = gridDim.x * blockDim.x;
     // warm start into the packed buffer
@@ -429,30 +600,35 @@ __global__ void __launch_bounds__(kThreads) lcp_kernel(KArgs<R> a) {
     // ---- init: Uc = K D gamma0, g0, residual, max diagonal
     scatter_phase(a, bs, 0, false, R(0));
     if (!grid_barrier(a.bar, &epoch, a.status)) return;
-    gather_phase(a, rs, nrows, 0, -1, true, v, &res_t);
+    gather_phase(a, rs, nrows, 0, -1, true, R(0), v, &res_t);
     {
         // init reduces two maxima: slot 0 = largest A_aa, slot 3 = residual
         double md = 0.0;
         for (int r = tid; r < nrows; r += stride) md = fmax(md, a.diag[r]);
         double w[kNred] = {md, 0.0, 0.0, res_t};
         block_reduce_store<double>(w, 0x9u, part);
-        if (threadIdx.x == 0)
-            for (int k = 0; k < kNred; ++k) a.partials[(size_t)blockIdx.x * kNred + k] = part[k];
+        if (threadIdx.x == 0) {
+            unsigned long long* o = a.partials + (size_t)blockIdx.x * kNred;
+            o[0] = to_word(part[0]);
+            o[1] = to_word(R(0));
+            o[2] = to_word(R(0));
+            o[3] = to_word(part[3]);
+        }
     }
     if (!grid_barrier(a.bar, &epoch, a.status)) return;
-    grid_reduce(a.partials, 0x9u, tot);
+    grid_reduce_t0<R>(a.partials, 0x9u, tot);
     // the step length, the residual and the stop decision are computed by
     // thread 0 of each block (identically in every block: same reduced values)
     // and broadcast through shared memory, so FP64 scalar work is not repeated
     // by every thread
-    __shared__ double sh_alpha, sh_resid;
+    __shared__ double sh_resid;
     __shared__ R sh_alpha_r;
     __shared__ int sh_stop;
     double resid = 0.0;
     if (threadIdx.x == 0) {
-        resid = tot[3];
-        const double alpha = a.invd ? 1.0 : (tot[0] > 0.0 ? 1.0 / tot[0] : 1.0);
-        sh_alpha = alpha;
+        resid = from_word<double>(tot[3]);
+        const double md = from_word<double>(tot[0]);
+        const double alpha = a.invd ? 1.0 : (md > 0.0 ? 1.0 / md : 1.0);
         sh_alpha_r = (R)alpha;
         sh_resid = resid;
         sh_stop = resid <= a.tol;
@@ -461,44 +637,47 @@ __global__ void __launch_bounds__(kThreads) lcp_kernel(KArgs<R> a) {
     R alpha_r = sh_alpha_r;
     int cur = 0, it = 0;
     if (!sh_stop) {
+#ifdef RELCP_LCP_TRACE
+        unsigned long long t_prev = gtimer();
+#endif
         for (it = 1; it <= a.max_iter; ++it) {
             // all blocks have read partials before any block rewrites them:
             // the barrier after phase 1 separates the reads from the writes
             const bool check = (it % a.check_every) == 0 || it == a.max_iter;
             scatter_phase(a, bs, cur, true, alpha_r);
+            TRACE_MARK(0);
             if (!grid_barrier(a.bar, &epoch, a.status)) return;
-            gather_phase(a, rs, nrows, 1 - cur, cur, check, v, &res_t);
-            {
-                R w[kNred] = {v[0], v[1], v[2], R(0)};
-                block_reduce_store<R>(w, 0x0u, part);
-                if (check) {
-                    double wr[kNred] = {0.0, 0.0, 0.0, res_t};
-                    __shared__ double part_r[kNred];
-                    block_reduce_store<double>(wr, 0x8u, part_r);
-                    if (threadIdx.x == 0) part[3] = part_r[3];
-                }
-            }
-            if (threadIdx.x == 0)
-                for (int k = 0; k < kNred; ++k) a.partials[(size_t)blockIdx.x * kNred + k] = part[k];
+            TRACE_MARK(1);
+            gather_phase(a, rs, nrows, 1 - cur, cur, check, alpha_r, v, &res_t);
+            TRACE_MARK(2);
+            block_partials<R>(v, res_t, check, a.partials + (size_t)blockIdx.x * kNred);
+            TRACE_MARK(3);
             if (!grid_barrier(a.bar, &epoch, a.status)) return;
-            grid_reduce(a.partials, 0x8u, tot);
+            TRACE_MARK(4);
+            grid_reduce_t0<R>(a.partials, 0x8u, tot);
             cur = 1 - cur;
             if (threadIdx.x == 0) {
                 int stop = 0;
                 if (check) {
-                    sh_resid = tot[3];
-                    stop = tot[3] <= a.tol;
+                    const double rs = from_word<double>(tot[3]);
+                    sh_resid = rs;
+                    stop = rs <= a.tol;
                 }
-                const double ss = tot[0], sy = tot[1], yy = tot[2];
-                double na;
-                if (it & 1) na = (sy > 0.0) ? ss / sy : sh_alpha;
-                else na = (yy > 0.0 && sy > 0.0) ? sy / yy : sh_alpha;
-                if (isfinite(na) && na > 0.0) sh_alpha = na;
-                sh_alpha_r = (R)sh_alpha;
+                // BB1 / BB2 in the solve precision; a non-positive or
+                // non-finite ratio keeps the previous step
+                const R ss = from_word<R>(tot[0]), sy = from_word<R>(tot[1]), yy = from_word<R>(tot[2]);
+                R na;
+                if (it & 1) na = (sy > R(0)) ? ss / sy : sh_alpha_r;
+                else na = (yy > R(0) && sy > R(0)) ? sy / yy : sh_alpha_r;
+                if (isfinite(na) && na > R(0)) sh_alpha_r = na;
                 sh_stop = stop;
             }
             __syncthreads();
             alpha_r = sh_alpha_r;
+            TRACE_MARK(5);
+#ifdef RELCP_LCP_TRACE
+            if (blockIdx.x == 0 && threadIdx.x == 0) g_lcp_trace[6] += 1;
+#endif
             if (sh_stop) break;
         }
         if (it > a.max_iter) it = a.max_iter;
@@ -592,9 +771,10 @@ relcp_status launch_lcp(KArgs<R>& ka, int64_t work, LcpScratch& sc, cudaStream_t
     int64_t want = (work + kThreads - 1) / kThreads;
     // one CTA per SM: fewest arrivals per grid barrier
     int64_t maxb = (int64_t)sms * (per_sm < kMaxCtasPerSm ? per_sm : kMaxCtasPerSm);
+    if (maxb > kMaxBlocks) maxb = kMaxBlocks;  // the grid reduction stages kMaxBlocks blocks' partials
     int blocks = (int)(want < 1 ? 1 : (want > maxb ? maxb : want));
     RELCP_TRY(sc.partials.ensure((size_t)blocks * kNred, s));
-    ka.partials = sc.partials.p;
+    ka.partials = reinterpret_cast<unsigned long long*>(sc.partials.p);
     void* args[] = {&ka};
     if (ev0) RELCP_CUDA(cudaEventRecord(ev0, s));
     note_launch();
@@ -698,3 +878,14 @@ void release(LcpScratch& sc, cudaStream_t s) {
 }
 
 }  // namespace relcp
+
+#ifdef RELCP_LCP_TRACE
+extern "C" int relcp_debug_lcp_trace(unsigned long long* out, int reset) {
+    if (cudaMemcpyFromSymbol(out, relcp::g_lcp_trace, 8 * sizeof(unsigned long long)) != cudaSuccess) return 1;
+    if (reset) {
+        unsigned long long z[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+        if (cudaMemcpyToSymbol(relcp::g_lcp_trace, z, sizeof(z)) != cudaSuccess) return 1;
+    }
+    return 0;
+}
+#endif
