@@ -718,19 +718,20 @@ __global__ void inc_fill(const int* __restrict__ nrows_dev, const int* __restric
     inc[off[b] + atomicAdd(&cursor[b], 1)] = (int)(r << 1) | 1;
 }
 
-__global__ void inc_sort(int64_t nbodies, const int* __restrict__ off, int* __restrict__ inc) {
-    int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (b >= nbodies) return;
-    int e0 = off[b], e1 = off[b + 1];
-    for (int k = e0 + 1; k < e1; ++k) {
-        int v = inc[k];
-        int m = k - 1;
-        while (m >= e0 && inc[m] > v) {
-            inc[m + 1] = inc[m];
-            --m;
-        }
-        inc[m + 1] = v;
-    }
+// deterministic order inside each body's segment: incidence codes sorted
+// ascending (row order), each placed at its rank among its body's codes
+// (the atomic fill above leaves the order of a segment to the scheduler)
+__global__ void inc_rank(const int* __restrict__ nrows_dev, const int* __restrict__ ia, const int* __restrict__ ib,
+                         const int* __restrict__ off, const int* __restrict__ unsorted, int* __restrict__ inc) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= 2 * (int64_t)*nrows_dev) return;
+    const int v = unsorted[e];
+    const int r = v >> 1;
+    const int b = (v & 1) ? ib[r] : ia[r];
+    const int e0 = off[b], e1 = off[b + 1];
+    int rank = 0;
+    for (int k = e0; k < e1; ++k) rank += unsorted[k] < v;
+    inc[e0 + rank] = v;
 }
 
 __global__ void diag_kernel(int64_t nrows, const int* __restrict__ ia, const int* __restrict__ ib,
@@ -814,7 +815,7 @@ relcp_status solve_typed(const LcpProblem& pr, LcpScratch& sc, DBuf<R>& pack, in
     ka.tol = pr.tol;
     ka.max_iter = pr.max_iter;
     ka.check_every = sizeof(R) == sizeof(double) ? 1 : kMixedCheckEvery;
-    ka.bar = sc.barrier.p;
+    ka.bar = reinterpret_cast<unsigned*>(sc.inc_count.p + 2 * (nb > 0 ? nb : 1));  // zeroed with the counts
     ka.status = pr.status;
     ka.result = pr.result;
     int64_t work = pr.m_cap > kLanesPerBody * nb ? pr.m_cap : kLanesPerBody * nb;
@@ -841,26 +842,24 @@ relcp_status lcp_solve(const LcpProblem& pr, LcpScratch& sc, int* blocks, float*
     const int64_t mc = pr.m_cap > 0 ? pr.m_cap : 1, nb = pr.nbodies;
     if (pr.m_cap > (int64_t)1 << 29 || nb > (int64_t)1 << 30) return RELCP_ERR_INVALID_ARG;
     const int64_t nba = nb > 0 ? nb : 1;
-    RELCP_TRY(sc.inc_count.ensure((size_t)nba, s));
-    RELCP_TRY(sc.inc_cursor.ensure((size_t)nba, s));
+    // one zeroed block: counts [0, nb), fill cursors [nb, 2 nb), barrier counters [2 nb, 2 nb + 2)
+    RELCP_TRY(sc.inc_count.ensure((size_t)(2 * nba + 2), s));
     RELCP_TRY(sc.inc_off.ensure((size_t)nba + 1, s));
+    RELCP_TRY(sc.inc_tmp.ensure((size_t)(2 * mc), s));
     RELCP_TRY(sc.inc.ensure((size_t)(2 * mc), s));
-    RELCP_TRY(sc.barrier.ensure(2, s));
-    RELCP_CUDA(cudaMemsetAsync(sc.inc_count.p, 0, nba * sizeof(int), s));
-    RELCP_CUDA(cudaMemsetAsync(sc.inc_cursor.p, 0, nba * sizeof(int), s));
-    RELCP_CUDA(cudaMemsetAsync(sc.barrier.p, 0, 2 * sizeof(unsigned), s));
+    int* cnt = sc.inc_count.p;
+    int* cursor = cnt + nba;
+    RELCP_CUDA(cudaMemsetAsync(cnt, 0, (2 * nba + 2) * sizeof(int), s));
     note_launch();
-    inc_count<<<nblk(mc), 256, 0, s>>>(pr.nrows_dev, pr.ia, pr.ib, sc.inc_count.p);
+    inc_count<<<nblk(mc), 256, 0, s>>>(pr.nrows_dev, pr.ia, pr.ib, cnt);
     RELCP_CUDA(cudaGetLastError());
-    RELCP_TRY(exclusive_scan(sc.inc_count.p, sc.inc_off.p, nb, sc.scan, s));
+    RELCP_TRY(exclusive_scan(cnt, sc.inc_off.p, nb, sc.scan, s));
     note_launch();
-    inc_fill<<<nblk(mc), 256, 0, s>>>(pr.nrows_dev, pr.ia, pr.ib, sc.inc_off.p, sc.inc_cursor.p, sc.inc.p);
+    inc_fill<<<nblk(mc), 256, 0, s>>>(pr.nrows_dev, pr.ia, pr.ib, sc.inc_off.p, cursor, sc.inc_tmp.p);
     RELCP_CUDA(cudaGetLastError());
-    if (nb > 0) {
-        note_launch();
-        inc_sort<<<nblk(nb), 256, 0, s>>>(nb, sc.inc_off.p, sc.inc.p);
-        RELCP_CUDA(cudaGetLastError());
-    }
+    note_launch();
+    inc_rank<<<nblk(2 * mc), 256, 0, s>>>(pr.nrows_dev, pr.ia, pr.ib, sc.inc_off.p, sc.inc_tmp.p, sc.inc.p);
+    RELCP_CUDA(cudaGetLastError());
     if (pr.mixed) return solve_typed<float>(pr, sc, sc.packf, blocks, kernel_ms, s);
     return solve_typed<double>(pr, sc, sc.packd, blocks, kernel_ms, s);
 }
@@ -868,12 +867,11 @@ relcp_status lcp_solve(const LcpProblem& pr, LcpScratch& sc, int* blocks, float*
 void release(LcpScratch& sc, cudaStream_t s) {
     sc.inc_count.release(s);
     sc.inc_off.release(s);
-    sc.inc_cursor.release(s);
+    sc.inc_tmp.release(s);
     sc.inc.release(s);
     sc.packd.release(s);
     sc.packf.release(s);
     sc.partials.release(s);
-    sc.barrier.release(s);
     sc.scan.partial.release(s);
 }
 

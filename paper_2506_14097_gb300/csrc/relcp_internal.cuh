@@ -243,11 +243,11 @@ relcp_status shape_launch(int64_t n, View<4, const double> q, View<3, const doub
 // LCP (lcp.cu)
 // ---------------------------------------------------------------------------
 struct LcpScratch {
-    DBuf<int> inc_count, inc_off, inc_cursor, inc;
+    DBuf<int> inc_count;  // per body: incidence count, fill cursor; then the two grid-barrier counters
+    DBuf<int> inc_off, inc_tmp, inc;
     DBuf<double> packd;              // FP64: packed (gamma, g) pairs x 2 buffers + contact-velocity records
     DBuf<float> packf;               // mixed: the same in FP32
     DBuf<double> partials;
-    DBuf<unsigned> barrier;
     ScanScratch scan;
 };
 // Filled by the persistent kernel; read by the caller whenever it synchronises.

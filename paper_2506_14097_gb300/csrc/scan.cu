@@ -1,5 +1,6 @@
-// Device-wide exclusive prefix sum of int32 counts (three passes: tile sums,
-// scan of tile sums in one block, tile scan plus offset).  Used to turn
+// Device-wide exclusive prefix sum of int32 counts (two passes: tile sums,
+// then a tile scan in which every block first adds up the sums of the tiles
+// before it -- one load per thread -- so no separate pass scans the tile sums).  Used to turn
 // per-item counts or 0/1 flags into output positions (pair lists, constraint
 // compaction, incidence CSR) without atomics, so that every list the library
 // builds has a deterministic order.
@@ -54,22 +55,14 @@ __global__ void tile_sums(const int* __restrict__ in, int64_t n, int* __restrict
     if (threadIdx.x == 0) partial[blockIdx.x] = tot;
 }
 
-// single block: exclusive scan of nparts tile sums (in place), last entry total
-__global__ void scan_partials(int* __restrict__ partial, int nparts, int* __restrict__ total_out) {
-    int carry = 0;
-    for (int base = 0; base < nparts; base += kScanThreads) {
-        int i = base + threadIdx.x;
-        int v = i < nparts ? partial[i] : 0;
-        int tot;
-        int inc = block_inclusive_scan(v, &tot);
-        if (i < nparts) partial[i] = carry + inc - v;
-        carry += tot;
-    }
-    if (threadIdx.x == 0) *total_out = carry;
-}
-
+// tile scan plus offset; the offset of tile t is the sum of tile sums 0..t-1,
+// reduced by this block; the last block writes the total to out[n]
 __global__ void tile_scan(const int* __restrict__ in, int64_t n, const int* __restrict__ partial,
                           int* __restrict__ out) {
+    int before = 0;
+    for (int t = threadIdx.x; t < (int)blockIdx.x; t += blockDim.x) before += partial[t];
+    int offset;
+    block_inclusive_scan(before, &offset);
     int64_t base = (int64_t)blockIdx.x * kTile + (int64_t)threadIdx.x * kScanItems;
     int v[kScanItems];
     int s = 0;
@@ -80,36 +73,31 @@ __global__ void tile_scan(const int* __restrict__ in, int64_t n, const int* __re
     }
     int tot;
     int inc = block_inclusive_scan(s, &tot);
-    int run = partial[blockIdx.x] + inc - s;
+    int run = offset + inc - s;
 #pragma unroll
     for (int k = 0; k < kScanItems; ++k) {
         if (base + k < n) out[base + k] = run;
         run += v[k];
     }
+    if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) out[n] = offset + tot;
 }
 
 }  // namespace
 
 relcp_status exclusive_scan(const int* in, int* out, int64_t n, ScanScratch& sc, cudaStream_t s) {
     if (n < 0) return RELCP_ERR_INVALID_ARG;
-    int64_t nparts = (n + kTile - 1) / kTile;
-    if (nparts < 1) nparts = 1;
+    if (n == 0) {
+        RELCP_CUDA(cudaMemsetAsync(out, 0, sizeof(int), s));
+        return RELCP_OK;
+    }
+    const int64_t nparts = (n + kTile - 1) / kTile;
     RELCP_TRY(sc.partial.ensure((size_t)nparts, s));
-    if (n > 0) {
-        note_launch();
-        tile_sums<<<(unsigned)nparts, kScanThreads, 0, s>>>(in, n, sc.partial.p);
-        RELCP_CUDA(cudaGetLastError());
-    } else {
-        RELCP_CUDA(cudaMemsetAsync(sc.partial.p, 0, sizeof(int), s));
-    }
     note_launch();
-    scan_partials<<<1, kScanThreads, 0, s>>>(sc.partial.p, (int)nparts, out + n);
+    tile_sums<<<(unsigned)nparts, kScanThreads, 0, s>>>(in, n, sc.partial.p);
     RELCP_CUDA(cudaGetLastError());
-    if (n > 0) {
-        note_launch();
-        tile_scan<<<(unsigned)nparts, kScanThreads, 0, s>>>(in, n, sc.partial.p, out);
-        RELCP_CUDA(cudaGetLastError());
-    }
+    note_launch();
+    tile_scan<<<(unsigned)nparts, kScanThreads, 0, s>>>(in, n, sc.partial.p, out);
+    RELCP_CUDA(cudaGetLastError());
     return RELCP_OK;
 }
 

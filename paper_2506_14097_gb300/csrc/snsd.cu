@@ -84,32 +84,36 @@ __device__ __forceinline__ void adj_solve(const Sym3<T>& P, const T* v, T* o) {
 
 template <class T>
 __device__ void cold_start(const T* d, const Sym3<T>& Pa, const Sym3<T>& Pb, T* n) {
-    T cand[4][3];
     T l = sqrt(dot3(d, d));
-    if (!(l > 0)) {
-        n[0] = 1;
-        n[1] = 0;
-        n[2] = 0;
-        return;
-    }
-    for (int k = 0; k < 3; ++k) cand[0][k] = d[k] / l;
-    adj_solve(Pa, d, cand[1]);
-    adj_solve(Pb, d, cand[2]);
-    Sym3<T> S{Pa.xx + Pb.xx, Pa.yy + Pb.yy, Pa.zz + Pb.zz, Pa.xy + Pb.xy, Pa.xz + Pb.xz, Pa.yz + Pb.yz};
-    adj_solve(S, d, cand[3]);
+    n[0] = 1;
+    n[1] = 0;
+    n[2] = 0;
+    if (!(l > 0)) return;
+    const Sym3<T> S{Pa.xx + Pb.xx, Pa.yy + Pb.yy, Pa.zz + Pb.zz, Pa.xy + Pb.xy, Pa.xz + Pb.xz, Pa.yz + Pb.yz};
     T best = -INFINITY;
-    int arg = 0;
+    // seeds d, Pa^-1 d, Pb^-1 d, (Pa + Pb)^-1 d, each normalised; the best G wins
+    // (unrolled: the candidate stays in registers)
+#pragma unroll
     for (int c = 0; c < 4; ++c) {
-        T lc = sqrt(dot3(cand[c], cand[c]));
+        T v[3];
+        if (c == 0) {
+            v[0] = d[0];
+            v[1] = d[1];
+            v[2] = d[2];
+        } else {
+            adj_solve(c == 1 ? Pa : (c == 2 ? Pb : S), d, v);
+        }
+        const T lc = sqrt(dot3(v, v));
         if (!(lc > 0)) continue;
-        for (int k = 0; k < 3; ++k) cand[c][k] /= lc;
-        T g = g_value(cand[c], d, Pa, Pb);
+        for (int k = 0; k < 3; ++k) v[k] /= lc;
+        const T g = g_value(v, d, Pa, Pb);
         if (g > best) {
             best = g;
-            arg = c;
+            n[0] = v[0];
+            n[1] = v[1];
+            n[2] = v[2];
         }
     }
-    for (int k = 0; k < 3; ++k) n[k] = cand[arg][k];
 }
 
 // Newton ascent of G on the unit sphere from n (updated in place).
@@ -195,47 +199,82 @@ __global__ void __launch_bounds__(kThreads) snsd_kernel(SnsdArgs a) {
         double d[3];
         for (int k = 0; k < 3; ++k) d[k] = min_image(a.x(k, j) - a.x(k, i), a.box[k]);
         Sym3<double> Pa = load_P(a.P, i), Pb = load_P(a.P, j);
-        double scale = 1.0 + sqrt(dot3(d, d));
         double n[3];
         int iters = 0;
-        bool have = false;
-        if (a.guess.c[0]) {
-            n[0] = a.guess(0, p);
-            n[1] = a.guess(1, p);
-            n[2] = a.guess(2, p);
-            double l = sqrt(dot3(n, n));
-            if (l > 0.5 && l < 2.0) {
-                normalize3(n);
-                have = true;
-            }
-        }
         double G = 0.0;
         int r;
+        double va[3], vb[3], sa, sb;
+        float raf[3], rbf[3];
+        bool arms_f = false;  // lever arms from the FP32 phase
         if (a.mixed) {
+            // FP32 iterations.  FP64 runs at a small fraction of the FP32 rate
+            // on this part, so everything but the polish (G in FP64 at the FP32
+            // maximiser) stays in FP32: the start, the Newton steps, the scale
+            // of the stopping test and the lever arms.
             float df[3] = {(float)d[0], (float)d[1], (float)d[2]};
             Sym3<float> Pfa{(float)Pa.xx, (float)Pa.yy, (float)Pa.zz, (float)Pa.xy, (float)Pa.xz, (float)Pa.yz};
             Sym3<float> Pfb{(float)Pb.xx, (float)Pb.yy, (float)Pb.zz, (float)Pb.xy, (float)Pb.xz, (float)Pb.yz};
+            const float scalef = 1.f + sqrtf(dot3(df, df));
             float nf[3];
-            if (have) {
-                nf[0] = (float)n[0];
-                nf[1] = (float)n[1];
-                nf[2] = (float)n[2];
-            } else {
-                cold_start(df, Pfa, Pfb, nf);
+            bool have = false;
+            if (a.guess.c[0]) {
+                nf[0] = (float)a.guess(0, p);
+                nf[1] = (float)a.guess(1, p);
+                nf[2] = (float)a.guess(2, p);
+                const float l = sqrtf(dot3(nf, nf));
+                if (l > 0.5f && l < 2.f) {
+                    normalize3(nf);
+                    have = true;
+                }
             }
+            if (!have) cold_start(df, Pfa, Pfb, nf);
             float Gf;
-            int rf = newton_sphere(nf, df, Pfa, Pfb, (float)scale, 30, &Gf);
+            int rf = newton_sphere(nf, df, Pfa, Pfb, scalef, 30, &Gf);
             iters = rf >= 0 ? rf : -rf;
             n[0] = nf[0];
             n[1] = nf[1];
             n[2] = nf[2];
-            normalize3(n);
-            // FP64 polish.  At the FP32 maximiser the tangent gradient is
-            // below 2e-6 (1 + |d|), so by stationarity G evaluated there in FP64
-            // is within O(1e-12) of the maximum: that evaluation (below) is the
-            // polish.  Only when the FP32 phase failed does FP64 Newton run.
-            r = rf >= 0 ? 0 : newton_sphere(n, d, Pa, Pb, scale, 50, &G);
+            const double e = dot3(n, n) - 1.0;
+            if (rf >= 0 && fabs(e) < 1e-4) {
+                // FP64 polish.  At the FP32 maximiser the tangent gradient is
+                // below 2e-6 (1 + |d|), so by stationarity G evaluated there in
+                // FP64 is within O(1e-12) of the maximum: that evaluation (below)
+                // is the polish.  n is brought to unit length in FP64 with
+                // 1/sqrt(1 + e) = 1 - e/2 + 3e^2/8 + O(e^3), exact to rounding
+                // for |e| ~ 1e-7 (FP32 normalisation).
+                const double f = 1.0 + e * (-0.5 + 0.375 * e);
+                n[0] *= f;
+                n[1] *= f;
+                n[2] *= f;
+                r = 0;
+                float vaf[3], vbf[3];
+                symv(Pfa, nf, vaf);
+                symv(Pfb, nf, vbf);
+                const float ia = 1.f / sqrtf(dot3(nf, vaf)), ib = 1.f / sqrtf(dot3(nf, vbf));
+                for (int k = 0; k < 3; ++k) {
+                    raf[k] = vaf[k] * ia;
+                    rbf[k] = -vbf[k] * ib;
+                }
+                arms_f = true;
+            } else {
+                // the FP32 phase failed: FP64 Newton from its last iterate
+                normalize3(n);
+                const double scale = 1.0 + sqrt(dot3(d, d));
+                r = newton_sphere(n, d, Pa, Pb, scale, 50, &G);
+            }
         } else {
+            const double scale = 1.0 + sqrt(dot3(d, d));
+            bool have = false;
+            if (a.guess.c[0]) {
+                n[0] = a.guess(0, p);
+                n[1] = a.guess(1, p);
+                n[2] = a.guess(2, p);
+                const double l = sqrt(dot3(n, n));
+                if (l > 0.5 && l < 2.0) {
+                    normalize3(n);
+                    have = true;
+                }
+            }
             if (!have) cold_start(d, Pa, Pb, n);
             r = newton_sphere(n, d, Pa, Pb, scale, 50, &G);
         }
@@ -245,16 +284,25 @@ __global__ void __launch_bounds__(kThreads) snsd_kernel(SnsdArgs a) {
         } else {
             iters += r;
         }
-        double va[3], vb[3];
         symv(Pa, n, va);
         symv(Pb, n, vb);
-        double sa = sqrt(dot3(n, va)), sb = sqrt(dot3(n, vb));
+        sa = sqrt(dot3(n, va));
+        sb = sqrt(dot3(n, vb));
         G = dot3(n, d) - sa - sb;
         a.out.phi[p * a.out.phi_s] = G;
-        for (int k = 0; k < 3; ++k) {
-            a.out.n(k, p) = n[k];
-            a.out.ra(k, p) = va[k] / sa;
-            a.out.rb(k, p) = -vb[k] / sb;
+        if (arms_f) {
+            for (int k = 0; k < 3; ++k) {
+                a.out.n(k, p) = n[k];
+                a.out.ra(k, p) = (double)raf[k];
+                a.out.rb(k, p) = (double)rbf[k];
+            }
+        } else {
+            const double ia = 1.0 / sa, ib = 1.0 / sb;
+            for (int k = 0; k < 3; ++k) {
+                a.out.n(k, p) = n[k];
+                a.out.ra(k, p) = va[k] * ia;
+                a.out.rb(k, p) = -vb[k] * ib;
+            }
         }
         if (a.out.iters) a.out.iters[p] = iters;
         iters_out = iters;
