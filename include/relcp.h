@@ -94,8 +94,13 @@ enum {
     RELCP_FLAG_PHASE_TIMING = 1u,  /* record per-phase CUDA-event timings in relcp_step_stats */
     RELCP_FLAG_NO_WARM_START = 2u, /* start every LCP_0 from gamma = 0 instead of the previous step's
                                       gamma of the same pair (the solution is the same within lcp_tol) */
-    RELCP_FLAG_JACOBI = 4u         /* projected-gradient steps scaled by 1 / A_aa, BB lengths in the
+    RELCP_FLAG_JACOBI = 4u,        /* projected-gradient steps scaled by 1 / A_aa, BB lengths in the
                                       matching metric (same solution, fewer iterations on uneven rows) */
+    RELCP_FLAG_NO_SNSD_REUSE = 8u  /* evaluate the SNSD of every candidate pair at C^k.  By default a
+                                      pair that was a candidate in the previous step takes its C^k
+                                      values from that step's last overlap test, which evaluated it at
+                                      the configuration the step accepted (= this step's C^k); only
+                                      new pairs are evaluated (and given the learned guess) */
 };
 
 #define RELCP_MAX_DEPTH_STATS 64
@@ -131,6 +136,8 @@ typedef struct relcp_step_stats {
     int32_t pair_list_rebuilt;  /* 1 when the cached candidate list was rebuilt in this step */
     int32_t pad0;
     int64_t newton_iters_c0;    /* Newton iterations summed over the pairs of the C^k evaluation */
+    int64_t snsd_c0_evaluated;  /* pairs evaluated at C^k (the rest reused the previous step's last
+                                   overlap test; see RELCP_FLAG_NO_SNSD_REUSE) */
 } relcp_step_stats;
 
 typedef struct relcp_ctx relcp_ctx;
@@ -284,7 +291,9 @@ relcp_status relcp_lcp_solve(int64_t nrows, int64_t nbodies, const int32_t* ia, 
 /* Features (npairs x 16 float, device) of listed pairs (device, as in
  * relcp_snsd_eval); with snsd_out (npairs x 10 from relcp_snsd_eval) also the
  * training targets (npairs x 4 float: RELCP_MLP_CORR_SCALE x (normal in a's
- * frame minus the seed), Phi / s). */
+ * frame minus the seed), Phi / s).  With targets the arithmetic is FP64 (the
+ * targets resolve the FP64 SNSD normal); without, FP32 as in the step's own
+ * inference (the features agree to FP32 rounding). */
 relcp_status relcp_mlp_features(int64_t npairs, const int32_t* pairs, int64_t n, const double* x, const double* q,
                                 const double* axes, const double* box3, const double* snsd_out, float* feat,
                                 float* targets, void* stream);

@@ -64,6 +64,8 @@ struct DevStep {
     unsigned long long maxov_bits;  // bits of the largest overlap at the last trial
     unsigned long long iters0;      // Newton iterations summed over the pairs at C^k
     LcpDevResult lcp;   // iterations and residual of the last LCP
+    int c0_evals;       // pairs evaluated at C^k (the others reused the previous step's values)
+    int pad;
 };
 
 struct relcp_ctx {
@@ -93,12 +95,16 @@ struct relcp_ctx {
     relcp_step_stats stats{};
     int64_t steps_done = 0;
     std::vector<cudaEvent_t> events;  // phase-timing event pool
-    // warm start: the previous step's A_0 rows (sorted pair keys) and gamma
-    DBuf<long long> prev_keys;
-    DBuf<double> prev_gamma;
-    int64_t prev_n = 0;
-    DBuf<long long> next_keys;
-    DBuf<double> next_gamma;
+    // carried between steps: the last overlap test's SNSD output at the
+    // accepted configuration (= the next C^k) and the per-pair memo of the
+    // cached candidate list (bp.memo), stamped with the step number
+    DBuf<double> s1prev;
+    int64_t nprev = 0;
+    int stamp = 0;         // stamp written by the last completed step
+    bool memo_ok = false;  // memo and s1prev describe the current state
+    bool snsd_ok = false;  // s1prev may stand in for the SNSD at C^k
+    DBuf<double> gamma0;   // per pair: warm start of its A_0 row
+    DBuf<int> need, needscan, idx, rowof;
 };
 
 namespace {
@@ -293,7 +299,38 @@ relcp_status step_once(relcp_ctx* c) {
         return so;
     };
 
-    // SNSD at C^k
+    // C^k values a pair keeps from the previous step (the SNSD of its last
+    // overlap test, evaluated at this very configuration, and the final gamma
+    // of its A_0 row); need[] marks the pairs still to evaluate, idx lists them
+    RELCP_TRY(c->gamma0.ensure(npa, s));
+    RELCP_TRY(c->need.ensure(npa, s));
+    RELCP_TRY(c->needscan.ensure(npa + 1, s));
+    RELCP_TRY(c->idx.ensure(npa, s));
+    RELCP_TRY(c->rowof.ensure(npa, s));
+    const bool memo_ok = c->memo_ok;
+    c->memo_ok = false;  // set again once this step has saved its memo
+    const int* count_dev = c->needscan.p + np;
+    if (np > 0) {
+        ReuseArgs ru{};
+        ru.npairs = np;
+        ru.pv = c->bp.pv.p;
+        ru.memo = c->bp.memo.p;
+        ru.stamp_prev = memo_ok ? c->stamp : -1;
+        ru.reuse_snsd = c->snsd_ok && !(cfg.flags & RELCP_FLAG_NO_SNSD_REUSE);
+        ru.use_gamma = !(cfg.flags & RELCP_FLAG_NO_WARM_START);
+        ru.sprev = c->s1prev.p;
+        ru.nprev = c->nprev;
+        ru.s0 = c->s0.p;
+        ru.it0 = c->it0.p;
+        ru.gamma0 = c->gamma0.p;
+        ru.need = c->need.p;
+        RELCP_TRY(reuse_launch(ru, s));
+        RELCP_TRY(exclusive_scan(c->need.p, c->needscan.p, np, c->scan, s));
+        RELCP_TRY(index_compact_launch(np, c->need.p, c->needscan.p, c->idx.p, s));
+        RELCP_CUDA(cudaMemcpyAsync(&ds->c0_evals, count_dev, sizeof(int), cudaMemcpyDeviceToDevice, s));
+    }
+
+    // SNSD at C^k for the listed pairs
     SnsdArgs sa{};
     sa.npairs = np;
     sa.pa = c->pa.p;
@@ -304,9 +341,11 @@ relcp_status step_once(relcp_ctx* c) {
     for (int k = 0; k < 3; ++k) sa.box[k] = box0[k];
     sa.guess.c[0] = sa.guess.c[1] = sa.guess.c[2] = nullptr;
     sa.guess.s = 1;
+    sa.idx = c->idx.p;
+    sa.count_dev = count_dev;
     if (cfg.guess == RELCP_GUESS_MLP && c->mlp.loaded && np > 0) {
         RELCP_TRY(mlp_guess(c->mlp, np, c->pa.p, c->pb.p, xv, View<4, const double>::soa(c->q.p, n),
-                            View<3, const double>::soa(c->axes.p, n), box0, s));
+                            View<3, const double>::soa(c->axes.p, n), box0, s, c->idx.p, count_dev, &ds->status));
         sa.guess = View<3, const double>::soa(c->mlp.guess.p, np);
         st.guess_used = 1;
     }
@@ -345,10 +384,8 @@ relcp_status step_once(relcp_ctx* c) {
     ra.K = c->K.p;
     ra.nrows_dev = &ds->nrows;
     ra.status = &ds->status;
-    const bool warm = !(cfg.flags & RELCP_FLAG_NO_WARM_START) && c->prev_n > 0;
-    ra.prev_n = warm ? c->prev_n : 0;
-    ra.prev_keys = c->prev_keys.p;
-    ra.prev_gamma = c->prev_gamma.p;
+    ra.gamma0 = c->gamma0.p;
+    ra.rowof = c->rowof.p;
     auto bind_rows = [&](RowsArgs& r) {
         r.cap = c->rcap;
         r.ia = c->r_ia.p;
@@ -432,6 +469,8 @@ relcp_status step_once(relcp_ctx* c) {
         ta.ustep = c->ustep.p;
         RELCP_TRY(trial_launch(ta, s));
         SnsdArgs sb = sa;
+        sb.idx = nullptr;
+        sb.count_dev = nullptr;
         sb.x = View<3, const double>::soa(c->xt.p, n);
         sb.P = View<6, const double>::soa(c->Pt.p, n);
         for (int k = 0; k < 3; ++k) sb.box[k] = box1[k];
@@ -480,7 +519,8 @@ relcp_status step_once(relcp_ctx* c) {
         ++depth;
         RELCP_TRY(grow_rows(c, c->nrows + nv));
         RowsArgs rb2 = ra;
-        rb2.prev_n = 0;
+        rb2.gamma0 = nullptr;
+        rb2.rowof = nullptr;
         bind_rows(rb2);
         rb2.snsd = c->s1.p;
         rb2.base = c->nrows;
@@ -489,23 +529,25 @@ relcp_status step_once(relcp_ctx* c) {
         m_bound = c->nrows + nv;
     }
 
-    // keep the A_0 rows' final gamma for the next step's warm start
-    {
-        RELCP_TRY(c->next_keys.ensure((size_t)(c->nrows0 > 0 ? c->nrows0 : 1), s));
-        RELCP_TRY(c->next_gamma.ensure((size_t)(c->nrows0 > 0 ? c->nrows0 : 1), s));
-        SaveWarmArgs sw{};
-        sw.nrows0_dev = &ds->nrows0;  // |A_0|, copied on the device after the A_0 row kernel
-        sw.ia = c->r_ia.p;
-        sw.ib = c->r_ib.p;
-        sw.gamma = mixed ? nullptr : c->r_gamma.p;
-        sw.gammaf = mixed ? c->r_gammaf.p : nullptr;
-        sw.keys = c->next_keys.p;
-        sw.gout = c->next_gamma.p;
-        RELCP_TRY(save_warm_launch(sw, c->nrows0, s));
-        std::swap(c->prev_keys, c->next_keys);
-        std::swap(c->prev_gamma, c->next_gamma);
-        c->prev_n = c->nrows0;
+    // memo for the next step: every candidate pair's final A_0 gamma (0 without
+    // a row) and its index in this step's last overlap test, whose SNSD output
+    // (s1, at the configuration accepted below) becomes s1prev
+    if (np > 0) {
+        MemoSaveArgs ms{};
+        ms.npairs = np;
+        ms.pv = c->bp.pv.p;
+        ms.rowof = c->rowof.p;
+        ms.gamma = mixed ? nullptr : c->r_gamma.p;
+        ms.gammaf = mixed ? c->r_gammaf.p : nullptr;
+        ms.stamp = (c->stamp + 1) & 0x3fffffff;
+        ms.memo = c->bp.memo.p;
+        RELCP_TRY(memo_save_launch(ms, s));
     }
+    std::swap(c->s1, c->s1prev);
+    c->nprev = np;
+    c->stamp = (c->stamp + 1) & 0x3fffffff;
+    c->memo_ok = true;
+    c->snsd_ok = true;
 
     // accept C^{k+1} (no synchronisation: the next call queues behind it)
     AcceptArgs aa{};
@@ -529,16 +571,17 @@ relcp_status step_once(relcp_ctx* c) {
     st.lcp_iters_total = lcp_iters_total;
     st.newton_iters_max = hs.newton_max;
     st.newton_iters_c0 = (int64_t)hs.iters0;
+    st.snsd_c0_evaluated = hs.c0_evals;
     st.lcp_residual = hs.lcp.residual;
     st.max_overlap = __builtin_bit_cast(double, hs.maxov_bits);
     for (int k = 0; k < 3; ++k) st.box[k] = c->box[k];
     if (tm.on) {
         st.ms_broadphase = tm.ms(t_begin, t_bp);
         st.ms_total = tm.ms(t_begin, t_last);
-        for (auto& mk : snsd_marks) {
-            st.ms_snsd_kernel += tm.ms(mk.first, mk.second);
+        for (size_t m = 0; m < snsd_marks.size(); ++m) {
+            st.ms_snsd_kernel += tm.ms(snsd_marks[m].first, snsd_marks[m].second);
             st.snsd_launches += 1;
-            st.snsd_evals += np;
+            st.snsd_evals += m == 0 ? hs.c0_evals : np;  // the first launch is the C^k evaluation
         }
         st.ms_snsd = st.ms_snsd_kernel;
         for (auto& mk : lcp_marks) st.ms_lcp += tm.ms(mk.first, mk.second);
@@ -597,6 +640,10 @@ relcp_status relcp_create(const relcp_config* cfg, void* cuda_stream, relcp_ctx*
 relcp_status relcp_set_config(relcp_ctx* c, const relcp_config* cfg) {
     if (!c) return set_error("ctx is NULL"), RELCP_ERR_INVALID_ARG;
     RELCP_TRY(check_config(cfg));
+    // the carried SNSD values hold for the current box and precision only
+    for (int k = 0; k < 3; ++k)
+        if (cfg->box[k] != c->box[k]) c->snsd_ok = false;
+    if (cfg->precision != c->cfg.precision || cfg->skin != c->cfg.skin) c->snsd_ok = false;
     c->cfg = *cfg;
     for (int k = 0; k < 3; ++k) c->box[k] = cfg->box[k];
     return RELCP_OK;
@@ -671,7 +718,8 @@ relcp_status relcp_set_bodies(relcp_ctx* c, int64_t n, const int32_t* scene_offs
         RELCP_TRY(wrap_launch(n, c->x.p, c->box, s));
         RELCP_CUDA(cudaStreamSynchronize(s));  // host staging buffers go out of scope
     }
-    c->prev_n = 0;
+    c->memo_ok = false;
+    c->snsd_ok = false;
     c->bp.valid = false;
     c->rb_max = 0.0;
     for (size_t i = 0; i < ha.size(); ++i) c->rb_max = ha[i] > c->rb_max ? ha[i] : c->rb_max;
@@ -808,6 +856,8 @@ relcp_status relcp_load_mlp(relcp_ctx* c, const float* params, int32_t ptr_kind)
     RELCP_TRY(c->mlp.params.ensure(RELCP_MLP_NPARAMS, c->s));
     RELCP_CUDA(cudaMemcpyAsync(c->mlp.params.p, params, RELCP_MLP_NPARAMS * sizeof(float),
                                ptr_kind == RELCP_PTR_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->s));
+    RELCP_TRY(c->mlp.image.ensure(mlp_image_bytes(), c->s));
+    RELCP_TRY(mlp_pack_launch(c->mlp.params.p, c->mlp.image.p, c->s));
     RELCP_CUDA(cudaStreamSynchronize(c->s));
     c->mlp.loaded = true;
     return RELCP_OK;
@@ -834,10 +884,17 @@ void relcp_destroy(relcp_ctx* c) {
     c->dstep.release(s);
     c->bp.xb.release(s);
     c->bp.dmax.release(s);
-    c->prev_keys.release(s);
-    c->next_keys.release(s);
-    c->prev_gamma.release(s);
-    c->next_gamma.release(s);
+    c->s1prev.release(s);
+    c->gamma0.release(s);
+    c->need.release(s);
+    c->needscan.release(s);
+    c->idx.release(s);
+    c->rowof.release(s);
+    c->bp.memo.release(s);
+    c->bp.memo_old.release(s);
+    c->bp.vpa_old.release(s);
+    c->bp.vpb_old.release(s);
+    c->bp.pv.release(s);
     release(c->lcp, s);
     mlp_release(c->mlp, s);
     cudaStreamSynchronize(s);

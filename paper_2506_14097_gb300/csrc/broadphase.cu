@@ -12,6 +12,8 @@
 //
 // The distance test is a fixed sequence of separately rounded FP64
 // operations (no contraction), so the decision is reproducible bit for bit.
+#include <utility>
+
 #include "relcp_internal.cuh"
 
 namespace relcp {
@@ -183,11 +185,35 @@ __global__ void filter_kernel(int64_t nv, const int* __restrict__ vpa, const int
 
 __global__ void compact_kernel(int64_t nv, const int* __restrict__ vpa, const int* __restrict__ vpb,
                                const int* __restrict__ flag, const int* __restrict__ pos, int* __restrict__ pa,
-                               int* __restrict__ pb) {
-    int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= nv || !flag[p]) return;
-    pa[pos[p]] = vpa[p];
-    pb[pos[p]] = vpb[p];
+                               int* __restrict__ pb, int* __restrict__ pv) {
+    int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= nv || !flag[v]) return;
+    pa[pos[v]] = vpa[v];
+    pb[pos[v]] = vpb[v];
+    pv[pos[v]] = (int)v;
+}
+
+// carry the memo of every pair that is in both the old and the new cached
+// list (both sorted by (i, j)) to its new entry; new pairs get stamp -1
+__global__ void memo_remap_kernel(int64_t nv, const int* __restrict__ vpa, const int* __restrict__ vpb,
+                                  int64_t nold, const int* __restrict__ opa, const int* __restrict__ opb,
+                                  const PairMemo* __restrict__ omemo, PairMemo* __restrict__ memo) {
+    int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= nv) return;
+    const long long key = ((long long)vpa[v] << 32) | (long long)(unsigned)vpb[v];
+    int64_t lo = 0, hi = nold;
+    while (lo < hi) {
+        const int64_t mid = (lo + hi) >> 1;
+        const long long km = ((long long)opa[mid] << 32) | (long long)(unsigned)opb[mid];
+        if (km < key) lo = mid + 1;
+        else hi = mid;
+    }
+    PairMemo m;
+    m.stamp = -1;
+    m.pidx = -1;
+    m.gamma = 0.0;
+    if (lo < nold && opa[lo] == vpa[v] && opb[lo] == vpb[v]) m = omemo[lo];
+    memo[v] = m;
 }
 
 }  // namespace
@@ -296,11 +322,23 @@ relcp_status broadphase_cached(int64_t n, const double* x_soa, const double* rb,
             else if (box[k] > 0) sfac[k] = box[k] / sc.Lb[k];
         }
         if (!geom_ok) {
-            // rebuild: candidates within R_i + R_j + skin + delta at the current positions
+            // rebuild: candidates within R_i + R_j + skin + delta at the current
+            // positions; the memo follows the pairs that stay in the list
+            const int64_t nold = (sc.vn_bodies == n) ? sc.vn : 0;
+            std::swap(sc.vpa, sc.vpa_old);
+            std::swap(sc.vpb, sc.vpb_old);
+            std::swap(sc.memo, sc.memo_old);
             sc.delta = 0.15 * cutmax;
             int64_t nv = 0;
             RELCP_TRY(broadphase(n, xv, rb, rbmax, box, skin + sc.delta, sc.vpa, sc.vpb, &nv, sc, s));
             sc.vn = nv;
+            RELCP_TRY(sc.memo.ensure((size_t)(nv > 0 ? nv : 1), s));
+            if (nv > 0) {
+                note_launch();
+                memo_remap_kernel<<<(unsigned)((nv + kThreads - 1) / kThreads), kThreads, 0, s>>>(
+                    nv, sc.vpa.p, sc.vpb.p, nold, sc.vpa_old.p, sc.vpb_old.p, sc.memo_old.p, sc.memo.p);
+                RELCP_CUDA(cudaGetLastError());
+            }
             RELCP_TRY(sc.xb.ensure((size_t)(3 * n), s));
             RELCP_CUDA(cudaMemcpyAsync(sc.xb.p, x_soa, 3 * n * sizeof(double), cudaMemcpyDeviceToDevice, s));
             for (int k = 0; k < 3; ++k) sc.Lb[k] = box[k];
@@ -350,10 +388,11 @@ relcp_status broadphase_cached(int64_t n, const double* x_soa, const double* rb,
         if (total > 0) {
             RELCP_TRY(pa.ensure((size_t)total, s));
             RELCP_TRY(pb.ensure((size_t)total, s));
+            RELCP_TRY(sc.pv.ensure((size_t)total, s));
             note_launch();
             compact_kernel<<<(unsigned)((nv + kThreads - 1) / kThreads), kThreads, 0, s>>>(nv, sc.vpa.p, sc.vpb.p,
                                                                                           sc.vflag.p, sc.vscan.p,
-                                                                                          pa.p, pb.p);
+                                                                                          pa.p, pb.p, sc.pv.p);
             RELCP_CUDA(cudaGetLastError());
         }
         return RELCP_OK;

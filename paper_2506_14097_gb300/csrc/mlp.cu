@@ -54,17 +54,23 @@ __device__ __forceinline__ void mma_bf16(float c[4], const uint32_t a[4], uint32
 // ---------------------------------------------------------------------------
 // features
 // ---------------------------------------------------------------------------
+// T = double when training targets are written (the targets resolve the SNSD
+// normal to FP64 accuracy); T = float for inference, whose outputs are FP32
+// features (FP64 runs at a small fraction of the FP32 rate on this part).  The
+// minimum image of the centres is always taken in FP64 (exact, like the SNSD).
+template <class T>
 __global__ void features_kernel(MlpFeatArgs a) {
-    int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= a.npairs) return;
+    const int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (row >= (a.count_dev ? (int64_t)*a.count_dev : a.npairs)) return;
+    const int64_t p = a.idx ? (int64_t)a.idx[row] : row;
     const int i = a.pa[p * a.pstride], j = a.pb[p * a.pstride];
-    double d[3];
-    for (int k = 0; k < 3; ++k) d[k] = min_image(a.x(k, j) - a.x(k, i), a.box[k]);
-    double qa[4], qb[4];
-    double la = 0, lb = 0;
+    T d[3];
+    for (int k = 0; k < 3; ++k) d[k] = (T)min_image(a.x(k, j) - a.x(k, i), a.box[k]);
+    T qa[4], qb[4];
+    T la = 0, lb = 0;
     for (int k = 0; k < 4; ++k) {
-        qa[k] = a.q(k, i);
-        qb[k] = a.q(k, j);
+        qa[k] = (T)a.q(k, i);
+        qb[k] = (T)a.q(k, j);
         la += qa[k] * qa[k];
         lb += qb[k] * qb[k];
     }
@@ -74,19 +80,19 @@ __global__ void features_kernel(MlpFeatArgs a) {
         qa[k] /= la;
         qb[k] /= lb;
     }
-    double R[9];
+    T R[9];
     quat_to_R(qa[0], qa[1], qa[2], qa[3], R);
-    const double aa[3] = {a.axes(0, i), a.axes(1, i), a.axes(2, i)};
-    const double ab[3] = {a.axes(0, j), a.axes(1, j), a.axes(2, j)};
-    const double sc = fmax(aa[0], fmax(aa[1], aa[2])) + fmax(ab[0], fmax(ab[1], ab[2]));
-    float* f = a.feat + 16 * p;
+    const T aa[3] = {(T)a.axes(0, i), (T)a.axes(1, i), (T)a.axes(2, i)};
+    const T ab[3] = {(T)a.axes(0, j), (T)a.axes(1, j), (T)a.axes(2, j)};
+    const T sc = fmax(aa[0], fmax(aa[1], aa[2])) + fmax(ab[0], fmax(ab[1], ab[2]));
+    float* f = a.feat + 16 * row;
     for (int k = 0; k < 3; ++k) f[k] = (float)((R[k] * d[0] + R[3 + k] * d[1] + R[6 + k] * d[2]) / sc);
     // q_rel = conj(q_a) (x) q_b
-    const double s1 = qa[0], x1 = -qa[1], y1 = -qa[2], z1 = -qa[3];
-    const double s2 = qb[0], x2 = qb[1], y2 = qb[2], z2 = qb[3];
-    double qr[4] = {s1 * s2 - (x1 * x2 + y1 * y2 + z1 * z2), s1 * x2 + s2 * x1 + (y1 * z2 - z1 * y2),
-                    s1 * y2 + s2 * y1 + (z1 * x2 - x1 * z2), s1 * z2 + s2 * z1 + (x1 * y2 - y1 * x2)};
-    const double sg = qr[0] < 0.0 ? -1.0 : 1.0;
+    const T s1 = qa[0], x1 = -qa[1], y1 = -qa[2], z1 = -qa[3];
+    const T s2 = qb[0], x2 = qb[1], y2 = qb[2], z2 = qb[3];
+    T qr[4] = {s1 * s2 - (x1 * x2 + y1 * y2 + z1 * z2), s1 * x2 + s2 * x1 + (y1 * z2 - z1 * y2),
+               s1 * y2 + s2 * y1 + (z1 * x2 - x1 * z2), s1 * z2 + s2 * z1 + (x1 * y2 - y1 * x2)};
+    const T sg = qr[0] < T(0) ? T(-1) : T(1);
     for (int k = 0; k < 4; ++k) f[3 + k] = (float)(sg * qr[k]);
     for (int k = 0; k < 3; ++k) {
         f[7 + k] = (float)aa[k];
@@ -94,35 +100,35 @@ __global__ void features_kernel(MlpFeatArgs a) {
     }
     // analytic seed (P_a + P_b)^-1 d (world), normalised, in a's frame: the
     // network predicts the correction from this seed to the shared normal
-    double sd[3];
+    T sd[3];
     {
-        double Rb[9];
+        T Rb[9];
         quat_to_R(qb[0], qb[1], qb[2], qb[3], Rb);
-        Sym3<double> Pa = rot_diag_rot(R, aa[0] * aa[0], aa[1] * aa[1], aa[2] * aa[2]);
-        Sym3<double> Pb = rot_diag_rot(Rb, ab[0] * ab[0], ab[1] * ab[1], ab[2] * ab[2]);
-        const double xx = Pa.xx + Pb.xx, yy = Pa.yy + Pb.yy, zz = Pa.zz + Pb.zz;
-        const double xy = Pa.xy + Pb.xy, xz = Pa.xz + Pb.xz, yz = Pa.yz + Pb.yz;
+        Sym3<T> Pa = rot_diag_rot(R, aa[0] * aa[0], aa[1] * aa[1], aa[2] * aa[2]);
+        Sym3<T> Pb = rot_diag_rot(Rb, ab[0] * ab[0], ab[1] * ab[1], ab[2] * ab[2]);
+        const T xx = Pa.xx + Pb.xx, yy = Pa.yy + Pb.yy, zz = Pa.zz + Pb.zz;
+        const T xy = Pa.xy + Pb.xy, xz = Pa.xz + Pb.xz, yz = Pa.yz + Pb.yz;
         // adjugate of the symmetric sum times d (same direction as the inverse)
-        const double A00 = yy * zz - yz * yz, A11 = xx * zz - xz * xz, A22 = xx * yy - xy * xy;
-        const double A01 = xz * yz - xy * zz, A02 = xy * yz - yy * xz, A12 = xy * xz - xx * yz;
-        double w[3] = {A00 * d[0] + A01 * d[1] + A02 * d[2], A01 * d[0] + A11 * d[1] + A12 * d[2],
-                       A02 * d[0] + A12 * d[1] + A22 * d[2]};
-        double lw = sqrt(w[0] * w[0] + w[1] * w[1] + w[2] * w[2]);
-        if (!(lw > 0.0)) {
-            w[0] = 1.0;
-            w[1] = w[2] = 0.0;
-            lw = 1.0;
+        const T A00 = yy * zz - yz * yz, A11 = xx * zz - xz * xz, A22 = xx * yy - xy * xy;
+        const T A01 = xz * yz - xy * zz, A02 = xy * yz - yy * xz, A12 = xy * xz - xx * yz;
+        T w[3] = {A00 * d[0] + A01 * d[1] + A02 * d[2], A01 * d[0] + A11 * d[1] + A12 * d[2],
+                  A02 * d[0] + A12 * d[1] + A22 * d[2]};
+        T lw = sqrt(w[0] * w[0] + w[1] * w[1] + w[2] * w[2]);
+        if (!(lw > T(0))) {
+            w[0] = 1;
+            w[1] = w[2] = 0;
+            lw = 1;
         }
         for (int k = 0; k < 3; ++k) sd[k] = (R[k] * w[0] + R[3 + k] * w[1] + R[6 + k] * w[2]) / lw;
     }
     for (int k = 0; k < 3; ++k) f[13 + k] = (float)sd[k];
     if (a.targets && a.snsd) {
         const double* o = a.snsd + p * a.snsd_s;
-        const double n[3] = {o[1 * a.snsd_c], o[2 * a.snsd_c], o[3 * a.snsd_c]};
-        float* t = a.targets + 4 * p;
+        const T n[3] = {(T)o[1 * a.snsd_c], (T)o[2 * a.snsd_c], (T)o[3 * a.snsd_c]};
+        float* t = a.targets + 4 * row;
         for (int k = 0; k < 3; ++k)
-            t[k] = (float)(RELCP_MLP_CORR_SCALE * ((R[k] * n[0] + R[3 + k] * n[1] + R[6 + k] * n[2]) - sd[k]));
-        t[3] = (float)(o[0] / sc);
+            t[k] = (float)(T(RELCP_MLP_CORR_SCALE) * ((R[k] * n[0] + R[3 + k] * n[1] + R[6 + k] * n[2]) - sd[k]));
+        t[3] = (float)((T)o[0] / sc);
     }
 }
 
@@ -138,6 +144,81 @@ constexpr int kSmemW4 = kMlpOut * kKs;
 constexpr size_t kFwdSmem = (size_t)(kSmemW1 + 2 * kSmemW + kSmemW4) * 2 + (3 * kMlpHid + kMlpOut) * 4;
 
 __device__ __forceinline__ uint32_t lds32(const __nv_bfloat16* p) { return *reinterpret_cast<const uint32_t*>(p); }
+
+// The forward kernel's shared-memory image of the network, built once per
+// parameter set: BF16 weight rows padded to the strides above, then the FP32
+// biases b1 | b2 | b3 | b4.  kFwdSmem is a multiple of 16 bytes (bulk copies).
+static_assert(kFwdSmem % 16 == 0, "image size must be a multiple of 16 bytes");
+constexpr unsigned kBulkChunk = 16384;
+constexpr long long kBulkWaitLimit = 1ll << 22;
+
+__global__ void mlp_pack_kernel(const float* __restrict__ params, unsigned char* __restrict__ image) {
+    __nv_bfloat16* W1 = reinterpret_cast<__nv_bfloat16*>(image);
+    __nv_bfloat16* W2 = W1 + kSmemW1;
+    __nv_bfloat16* W3 = W2 + kSmemW;
+    __nv_bfloat16* W4 = W3 + kSmemW;
+    float* bias = reinterpret_cast<float*>(W4 + kSmemW4);
+    const int stride = gridDim.x * blockDim.x;
+    const int t0 = blockIdx.x * blockDim.x + threadIdx.x;
+    for (int e = t0; e < kSmemW1; e += stride) {
+        const int r = e / kKs1, c = e % kKs1;
+        W1[e] = __float2bfloat16_rn(c < kMlpIn ? params[kOffW1 + r * kMlpIn + c] : 0.f);
+    }
+    for (int e = t0; e < kSmemW; e += stride) {
+        const int r = e / kKs, c = e % kKs;
+        W2[e] = __float2bfloat16_rn(c < kMlpHid ? params[kOffW2 + r * kMlpHid + c] : 0.f);
+        W3[e] = __float2bfloat16_rn(c < kMlpHid ? params[kOffW3 + r * kMlpHid + c] : 0.f);
+    }
+    for (int e = t0; e < kSmemW4; e += stride) {
+        const int r = e / kKs, c = e % kKs;
+        W4[e] = __float2bfloat16_rn(c < kMlpHid ? params[kOffW4 + r * kMlpHid + c] : 0.f);
+    }
+    for (int e = t0; e < kMlpHid; e += stride) {
+        bias[e] = params[kOffB1 + e];
+        bias[kMlpHid + e] = params[kOffB2 + e];
+        bias[2 * kMlpHid + e] = params[kOffB3 + e];
+    }
+    if (t0 < kMlpOut) bias[3 * kMlpHid + t0] = params[kOffB4 + t0];
+}
+
+// Copy `bytes` (multiple of 16) from global memory into this block's shared
+// memory with the bulk asynchronous copy engine (cp.async.bulk), completion
+// tracked by an mbarrier.  Every thread waits a bounded number of polls; on
+// a timeout the block records DEV_TIMEOUT, waits once more (bounded) for its
+// copies and returns false.
+__device__ bool bulk_copy_to_smem(unsigned char* dst, const unsigned char* src, unsigned bytes,
+                                  unsigned long long* mbar, int* status) {
+    const unsigned bar = (unsigned)__cvta_generic_to_shared(mbar);
+    const unsigned dsts = (unsigned)__cvta_generic_to_shared(dst);
+    if (threadIdx.x == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+        for (unsigned off = 0; off < bytes; off += kBulkChunk) {
+            const unsigned sz = bytes - off < kBulkChunk ? bytes - off : kBulkChunk;
+            asm volatile(
+                "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                    dsts + off),
+                "l"(src + off), "r"(sz), "r"(bar)
+                : "memory");
+        }
+    }
+    __syncthreads();  // the barrier is initialised before anyone polls it
+    auto wait = [&]() {
+        unsigned done = 0;
+        for (long long it = 0; it < kBulkWaitLimit && !done; ++it)
+            asm volatile(
+                "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n selp.u32 %0, 1, 0, p;\n}"
+                : "=r"(done)
+                : "r"(bar)
+                : "memory");
+        return done != 0;
+    };
+    if (wait()) return true;
+    if (status) atomicOr(status, DEV_TIMEOUT);
+    wait();
+    return false;
+}
 
 // one hidden layer: acc (16 n-tiles) = A (8 k-tiles) x W^T, then bias + ReLU
 // and repack as the next layer's A fragments
@@ -167,30 +248,24 @@ __device__ __forceinline__ void hidden_layer(uint32_t A[8][4], const __nv_bfloat
     }
 }
 
-__global__ void __launch_bounds__(kFwdWarps * 32) mlp_forward_kernel(int64_t npairs, const float* __restrict__ params,
+__global__ void __launch_bounds__(kFwdWarps * 32) mlp_forward_kernel(int64_t nmax, const unsigned char* __restrict__ image,
                                                                      const float* __restrict__ feat,
-                                                                     float* __restrict__ out) {
+                                                                     float* __restrict__ out,
+                                                                     const int* __restrict__ count_dev,
+                                                                     int* __restrict__ status) {
+    const int64_t npairs = count_dev ? (int64_t)*count_dev : nmax;
+    if ((int64_t)blockIdx.x * 16 * kFwdWarps >= npairs) return;  // no tile for this block
     extern __shared__ __align__(16) unsigned char smem[];
-    __nv_bfloat16* W1 = reinterpret_cast<__nv_bfloat16*>(smem);
-    __nv_bfloat16* W2 = W1 + kSmemW1;
-    __nv_bfloat16* W3 = W2 + kSmemW;
-    __nv_bfloat16* W4 = W3 + kSmemW;
-    float* bias = reinterpret_cast<float*>(W4 + kSmemW4);  // b1 | b2 | b3 | b4
-    for (int e = threadIdx.x; e < kMlpHid * kMlpIn; e += blockDim.x)
-        W1[(e / kMlpIn) * kKs1 + e % kMlpIn] = __float2bfloat16_rn(params[kOffW1 + e]);
-    for (int e = threadIdx.x; e < kMlpHid * kMlpHid; e += blockDim.x) {
-        W2[(e / kMlpHid) * kKs + e % kMlpHid] = __float2bfloat16_rn(params[kOffW2 + e]);
-        W3[(e / kMlpHid) * kKs + e % kMlpHid] = __float2bfloat16_rn(params[kOffW3 + e]);
-    }
-    for (int e = threadIdx.x; e < kMlpOut * kMlpHid; e += blockDim.x)
-        W4[(e / kMlpHid) * kKs + e % kMlpHid] = __float2bfloat16_rn(params[kOffW4 + e]);
-    for (int e = threadIdx.x; e < kMlpHid; e += blockDim.x) {
-        bias[e] = params[kOffB1 + e];
-        bias[kMlpHid + e] = params[kOffB2 + e];
-        bias[2 * kMlpHid + e] = params[kOffB3 + e];
-    }
-    if (threadIdx.x < kMlpOut) bias[3 * kMlpHid + threadIdx.x] = params[kOffB4 + threadIdx.x];
-    __syncthreads();
+    // the packed network (weights and biases) in one bulk copy; the mbarrier
+    // sits right after it
+    if (!bulk_copy_to_smem(smem, image, (unsigned)kFwdSmem, reinterpret_cast<unsigned long long*>(smem + kFwdSmem),
+                           status))
+        return;
+    const __nv_bfloat16* W1 = reinterpret_cast<const __nv_bfloat16*>(smem);
+    const __nv_bfloat16* W2 = W1 + kSmemW1;
+    const __nv_bfloat16* W3 = W2 + kSmemW;
+    const __nv_bfloat16* W4 = W3 + kSmemW;
+    const float* bias = reinterpret_cast<const float*>(W4 + kSmemW4);  // b1 | b2 | b3 | b4
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int g = lane >> 2, t = lane & 3;
@@ -257,26 +332,30 @@ __global__ void __launch_bounds__(kFwdWarps * 32) mlp_forward_kernel(int64_t npa
 }
 
 // network output -> world-frame start normal (zero when the trust logit is
-// negative: the Newton solve then starts cold)
+// negative: the Newton solve then starts cold).  FP32: it only seeds the FP32
+// Newton iterations.
 __global__ void guess_kernel(int64_t npairs, const int* __restrict__ pa, View<4, const double> q,
-                             const float* __restrict__ feat, const float* __restrict__ out, View<3, double> guess) {
-    int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= npairs) return;
+                             const float* __restrict__ feat, const float* __restrict__ out, View<3, double> guess,
+                             const int* __restrict__ idx, const int* __restrict__ count_dev) {
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;  // row of feat / out / guess
+    if (p >= (count_dev ? (int64_t)*count_dev : npairs)) return;
+    const int64_t pair = idx ? (int64_t)idx[p] : p;
     const float* o = out + 8 * p;
     const float* f = feat + 16 * p;
-    const double inv = 1.0 / (double)RELCP_MLP_CORR_SCALE;
-    double n[3] = {(double)f[13] + inv * o[0], (double)f[14] + inv * o[1], (double)f[15] + inv * o[2]};
-    double l = sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
-    if (!(o[4] > 0.f) || !(l > 1e-6)) {
+    const float inv = 1.f / (float)RELCP_MLP_CORR_SCALE;
+    const float n[3] = {f[13] + inv * o[0], f[14] + inv * o[1], f[15] + inv * o[2]};
+    const float l = sqrtf(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
+    if (!(o[4] > 0.f) || !(l > 1e-6f)) {
         guess(0, p) = guess(1, p) = guess(2, p) = 0.0;
         return;
     }
-    const int i = pa[p];
-    double s = q(0, i), x = q(1, i), y = q(2, i), z = q(3, i);
-    double lq = sqrt(s * s + x * x + y * y + z * z);
-    double R[9];
+    const int i = pa[pair];
+    const float s = (float)q(0, i), x = (float)q(1, i), y = (float)q(2, i), z = (float)q(3, i);
+    const float lq = sqrtf(s * s + x * x + y * y + z * z);
+    float R[9];
     quat_to_R(s / lq, x / lq, y / lq, z / lq, R);
-    for (int k = 0; k < 3; ++k) guess(k, p) = (R[3 * k] * n[0] + R[3 * k + 1] * n[1] + R[3 * k + 2] * n[2]) / l;
+    for (int k = 0; k < 3; ++k)
+        guess(k, p) = (double)((R[3 * k] * n[0] + R[3 * k + 1] * n[1] + R[3 * k + 2] * n[2]) / l);
 }
 
 // ---------------------------------------------------------------------------
@@ -452,18 +531,31 @@ relcp_status cast(int64_t rows, int cols, const float* src, __nv_bfloat16* dst, 
 relcp_status mlp_features_launch(const MlpFeatArgs& a, cudaStream_t s) {
     if (a.npairs == 0) return RELCP_OK;
     note_launch();
-    features_kernel<<<nb(a.npairs), 256, 0, s>>>(a);
+    // small blocks: a short pair list still spreads over many SMs
+    if (a.targets) features_kernel<double><<<nb(a.npairs, 64), 64, 0, s>>>(a);
+    else features_kernel<float><<<nb(a.npairs, 64), 64, 0, s>>>(a);
     RELCP_CUDA(cudaGetLastError());
     return RELCP_OK;
 }
 
-relcp_status mlp_forward_launch(int64_t npairs, const float* params, const float* feat, float* out, cudaStream_t s) {
+size_t mlp_image_bytes() { return kFwdSmem; }
+
+relcp_status mlp_pack_launch(const float* params, unsigned char* image, cudaStream_t s) {
+    note_launch();
+    mlp_pack_kernel<<<64, 256, 0, s>>>(params, image);
+    RELCP_CUDA(cudaGetLastError());
+    return RELCP_OK;
+}
+
+relcp_status mlp_forward_launch(int64_t npairs, const unsigned char* image, const float* feat, float* out,
+                                cudaStream_t s, const int* count_dev, int* status) {
     if (npairs == 0) return RELCP_OK;
+    constexpr size_t smem = kFwdSmem + 16;  // image + mbarrier
     static bool attr_set[64] = {false};
     int dev = 0;
     RELCP_CUDA(cudaGetDevice(&dev));
     if (dev >= 0 && dev < 64 && !attr_set[dev]) {
-        RELCP_CUDA(cudaFuncSetAttribute(mlp_forward_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFwdSmem));
+        RELCP_CUDA(cudaFuncSetAttribute(mlp_forward_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         attr_set[dev] = true;
     }
     const int64_t ntiles = (npairs + 16 * kFwdWarps - 1) / (16 * kFwdWarps);
@@ -471,13 +563,14 @@ relcp_status mlp_forward_launch(int64_t npairs, const float* params, const float
     int64_t blocks = (int64_t)(sms > 0 ? sms : 1) * 2;
     if (blocks > ntiles) blocks = ntiles;
     note_launch();
-    mlp_forward_kernel<<<(unsigned)blocks, kFwdWarps * 32, kFwdSmem, s>>>(npairs, params, feat, out);
+    mlp_forward_kernel<<<(unsigned)blocks, kFwdWarps * 32, smem, s>>>(npairs, image, feat, out, count_dev, status);
     RELCP_CUDA(cudaGetLastError());
     return RELCP_OK;
 }
 
 relcp_status mlp_guess(MlpState& m, int64_t npairs, const int* pa, const int* pb, View<3, const double> x,
-                       View<4, const double> q, View<3, const double> axes, const double box[3], cudaStream_t s) {
+                       View<4, const double> q, View<3, const double> axes, const double box[3], cudaStream_t s,
+                       const int* idx, const int* count_dev, int* status) {
     if (!m.loaded) {
         set_error("learned guess not loaded");
         return RELCP_ERR_STATE;
@@ -498,11 +591,14 @@ relcp_status mlp_guess(MlpState& m, int64_t npairs, const int* pa, const int* pb
     fa.snsd = nullptr;
     fa.feat = m.feat.p;
     fa.targets = nullptr;
+    fa.idx = idx;
+    fa.count_dev = count_dev;
     RELCP_TRY(mlp_features_launch(fa, s));
-    RELCP_TRY(mlp_forward_launch(npairs, m.params.p, m.feat.p, m.out.p, s));
+    RELCP_TRY(mlp_forward_launch(npairs, m.image.p, m.feat.p, m.out.p, s, count_dev, status));
     if (npairs > 0) {
         note_launch();
-        guess_kernel<<<nb(npairs), 256, 0, s>>>(npairs, pa, q, m.feat.p, m.out.p, View<3, double>::soa(m.guess.p, npairs));
+        guess_kernel<<<nb(npairs), 256, 0, s>>>(npairs, pa, q, m.feat.p, m.out.p, View<3, double>::soa(m.guess.p, npairs),
+                                                 idx, count_dev);
         RELCP_CUDA(cudaGetLastError());
     }
     return RELCP_OK;
@@ -510,6 +606,7 @@ relcp_status mlp_guess(MlpState& m, int64_t npairs, const int* pa, const int* pb
 
 void mlp_release(MlpState& m, cudaStream_t s) {
     m.params.release(s);
+    m.image.release(s);
     m.feat.release(s);
     m.out.release(s);
     m.guess.release(s);
@@ -664,9 +761,22 @@ extern "C" relcp_status relcp_mlp_forward(int64_t npairs, const float* params, c
                                           void* stream) {
     if (npairs < 0 || !params || (npairs > 0 && (!feat || !out))) return set_error("bad argument"), RELCP_ERR_INVALID_ARG;
     cudaStream_t s = (cudaStream_t)stream;
-    RELCP_TRY(mlp_forward_launch(npairs, params, feat, out, s));
-    RELCP_CUDA(cudaStreamSynchronize(s));
-    return RELCP_OK;
+    if (npairs == 0) return RELCP_OK;
+    DBuf<unsigned char> image;
+    DBuf<int> status;
+    relcp_status st = image.ensure(kFwdSmem, s);
+    if (st == RELCP_OK) st = status.ensure(1, s);
+    if (st == RELCP_OK && cudaMemsetAsync(status.p, 0, sizeof(int), s) != cudaSuccess) st = RELCP_ERR_CUDA;
+    if (st == RELCP_OK) st = mlp_pack_launch(params, image.p, s);
+    if (st == RELCP_OK) st = mlp_forward_launch(npairs, image.p, feat, out, s, nullptr, status.p);
+    int bits = 0;
+    if (st == RELCP_OK && cudaMemcpyAsync(&bits, status.p, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+        st = RELCP_ERR_CUDA;
+    image.release(s);
+    status.release(s);
+    if (cudaStreamSynchronize(s) != cudaSuccess && st == RELCP_OK) st = RELCP_ERR_CUDA;
+    if (st == RELCP_OK) st = status_from_device(bits);
+    return st;
 }
 
 extern "C" relcp_status relcp_mlp_train_step(int64_t batch, float* params, float* adam_m, float* adam_v,

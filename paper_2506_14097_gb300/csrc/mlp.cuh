@@ -26,6 +26,7 @@ static_assert(kOffB4 + kMlpOut == kMlpParams, "parameter layout");
 struct MlpState {
     bool loaded = false;
     DBuf<float> params;  // FP32 parameters
+    DBuf<unsigned char> image;  // the forward kernel's shared-memory image of params (mlp_pack_launch)
     DBuf<float> feat;    // npairs x 16
     DBuf<float> out;     // npairs x 8
     DBuf<double> guess;  // 3 x npairs start normals (world frame; zero = no guess)
@@ -45,15 +46,27 @@ struct MlpFeatArgs {
     int64_t snsd_s, snsd_c;  // pair stride and component stride of `snsd`
     float* feat;         // npairs x 16
     float* targets;      // npairs x 4 (n in a's frame, phi / scale) or null
+    // optional subset: row k < *count_dev holds pair idx[k] (idx == nullptr: row p = pair p)
+    const int* idx;
+    const int* count_dev;
 };
 relcp_status mlp_features_launch(const MlpFeatArgs& a, cudaStream_t s);
-relcp_status mlp_forward_launch(int64_t npairs, const float* params, const float* feat, float* out, cudaStream_t s);
+// the forward kernel's packed network image (RELCP_MLP image bytes) from FP32 params
+relcp_status mlp_pack_launch(const float* params, unsigned char* image, cudaStream_t s);
+// rows: npairs, or *count_dev (<= npairs) when count_dev is given; a failed
+// weight copy sets DEV_TIMEOUT in *status (may be null)
+relcp_status mlp_forward_launch(int64_t npairs, const unsigned char* image, const float* feat, float* out,
+                                cudaStream_t s, const int* count_dev = nullptr, int* status = nullptr);
+size_t mlp_image_bytes();
 
 relcp_status mlp_train_step(int64_t B, float* params, float* am, float* av, const float* feat, const float* targets,
                             const relcp_mlp_train_config& tc, float* grad_out, double* loss_out, cudaStream_t s);
 
+// start normals guess(., k) for the pairs idx[k], k < *count_dev (idx == nullptr:
+// all npairs pairs); npairs bounds the count
 relcp_status mlp_guess(MlpState& m, int64_t npairs, const int* pa, const int* pb, View<3, const double> x,
-                       View<4, const double> q, View<3, const double> axes, const double box[3], cudaStream_t s);
+                       View<4, const double> q, View<3, const double> axes, const double box[3], cudaStream_t s,
+                       const int* idx = nullptr, const int* count_dev = nullptr, int* status = nullptr);
 void mlp_release(MlpState& m, cudaStream_t s);
 
 }  // namespace relcp

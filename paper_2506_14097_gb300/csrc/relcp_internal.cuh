@@ -121,21 +121,23 @@ __device__ __forceinline__ void cross3(const T* a, const T* b, T* c) {
 }
 
 // Rotation of the normalised quaternion (s, w), Hamilton, body -> world.
-__device__ __forceinline__ void quat_to_R(double s, double x, double y, double z, double* R) {
-    R[0] = 1.0 - 2.0 * (y * y + z * z);
-    R[1] = 2.0 * (x * y - s * z);
-    R[2] = 2.0 * (x * z + s * y);
-    R[3] = 2.0 * (x * y + s * z);
-    R[4] = 1.0 - 2.0 * (x * x + z * z);
-    R[5] = 2.0 * (y * z - s * x);
-    R[6] = 2.0 * (x * z - s * y);
-    R[7] = 2.0 * (y * z + s * x);
-    R[8] = 1.0 - 2.0 * (x * x + y * y);
+template <class T>
+__device__ __forceinline__ void quat_to_R(T s, T x, T y, T z, T* R) {
+    R[0] = T(1) - T(2) * (y * y + z * z);
+    R[1] = T(2) * (x * y - s * z);
+    R[2] = T(2) * (x * z + s * y);
+    R[3] = T(2) * (x * y + s * z);
+    R[4] = T(1) - T(2) * (x * x + z * z);
+    R[5] = T(2) * (y * z - s * x);
+    R[6] = T(2) * (x * z - s * y);
+    R[7] = T(2) * (y * z + s * x);
+    R[8] = T(1) - T(2) * (x * x + y * y);
 }
 
 // R diag(w) R^T as a symmetric matrix
-__device__ __forceinline__ Sym3<double> rot_diag_rot(const double* R, double w0, double w1, double w2) {
-    Sym3<double> P;
+template <class T>
+__device__ __forceinline__ Sym3<T> rot_diag_rot(const T* R, T w0, T w1, T w2) {
+    Sym3<T> P;
     P.xx = R[0] * R[0] * w0 + R[1] * R[1] * w1 + R[2] * R[2] * w2;
     P.yy = R[3] * R[3] * w0 + R[4] * R[4] * w1 + R[5] * R[5] * w2;
     P.zz = R[6] * R[6] * w0 + R[7] * R[7] * w1 + R[8] * R[8] * w2;
@@ -179,12 +181,27 @@ relcp_status exclusive_scan(const int* in, int* out, int64_t n, ScanScratch& sc,
 // ---------------------------------------------------------------------------
 // broad phase (broadphase.cu)
 // ---------------------------------------------------------------------------
+// What a step leaves for the next one about a pair of the cached candidate
+// list: the step number, the pair's index in that step (its row of the SNSD
+// output of the step's last overlap test) and the final gamma of its A_0 row
+// (0 when it had none).
+struct PairMemo {
+    int stamp;
+    int pidx;
+    double gamma;
+};
+
 struct BroadphaseScratch {
     DBuf<int> cell_of, cell_count, cell_start, cell_cursor, cell_body, pair_count, pair_off;
     ScanScratch scan;
     // Verlet candidate list (context use): pairs within R_i + R_j + skin + delta
-    // at the build positions xb in the build box Lb
+    // at the build positions xb in the build box Lb, sorted by (i, j)
     DBuf<int> vpa, vpb, vflag, vscan;
+    // per-entry memo, carried to the new list (by pair key) when it is rebuilt
+    DBuf<PairMemo> memo;
+    DBuf<int> vpa_old, vpb_old;
+    DBuf<PairMemo> memo_old;
+    DBuf<int> pv;  // candidate pair p -> its entry of the cached list
     DBuf<double> xb;
     DBuf<unsigned long long> dmax;  // bits of the largest displacement since the build
     int64_t vn = 0, vn_bodies = -1;
@@ -199,7 +216,8 @@ relcp_status broadphase(int64_t n, View<3, const double> x, const double* rb, do
                         double skin, DBuf<int>& pa, DBuf<int>& pb, int64_t* npairs, BroadphaseScratch& sc,
                         cudaStream_t s);
 // The same pair list through a cached Verlet list (x in SoA layout, n bodies,
-// rbmax known).  Rebuilds the cache when the displacement bound requires it.
+// rbmax known).  Rebuilds the cache when the displacement bound requires it;
+// sc.pv maps each pair to its list entry, sc.memo is indexed by entry.
 relcp_status broadphase_cached(int64_t n, const double* x_soa, const double* rb, double rbmax, const double box[3],
                                double skin, DBuf<int>& pa, DBuf<int>& pb, int64_t* npairs, BroadphaseScratch& sc,
                                cudaStream_t s);
@@ -222,6 +240,10 @@ struct SnsdArgs {
     View<6, const double> P;         // shape matrices
     double box[3];
     View<3, const double> guess;     // per-pair start normal (c[0] == nullptr: cold start)
+    // optional pair subset: thread k < *count_dev evaluates pair idx[k] (its
+    // start normal is guess(., k)); idx == nullptr: thread p evaluates pair p
+    const int* idx;
+    const int* count_dev;
     int mixed;                       // FP32 iterations + FP64 polish
     SnsdOut out;
     // optional overlap test (Phi < -eps): violator flags and the largest overlap

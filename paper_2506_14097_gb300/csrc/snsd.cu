@@ -190,10 +190,13 @@ __device__ __forceinline__ Sym3<double> load_P(View<6, const double> P, int64_t 
 }
 
 __global__ void __launch_bounds__(kThreads) snsd_kernel(SnsdArgs a) {
-    int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t k_thr = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t count = a.count_dev ? (int64_t)*a.count_dev : a.npairs;
     double maxov = 0.0;
     int iters_out = 0;
-    if (p < a.npairs) {
+    if (k_thr < count) {
+        const int64_t p = a.idx ? (int64_t)a.idx[k_thr] : k_thr;  // the pair
+        const int64_t gk = k_thr;                                  // its start-normal slot
         int i = a.pa[p * a.pstride];
         int j = a.pb[p * a.pstride];
         double d[3];
@@ -218,9 +221,9 @@ __global__ void __launch_bounds__(kThreads) snsd_kernel(SnsdArgs a) {
             float nf[3];
             bool have = false;
             if (a.guess.c[0]) {
-                nf[0] = (float)a.guess(0, p);
-                nf[1] = (float)a.guess(1, p);
-                nf[2] = (float)a.guess(2, p);
+                nf[0] = (float)a.guess(0, gk);
+                nf[1] = (float)a.guess(1, gk);
+                nf[2] = (float)a.guess(2, gk);
                 const float l = sqrtf(dot3(nf, nf));
                 if (l > 0.5f && l < 2.f) {
                     normalize3(nf);
@@ -266,9 +269,9 @@ __global__ void __launch_bounds__(kThreads) snsd_kernel(SnsdArgs a) {
             const double scale = 1.0 + sqrt(dot3(d, d));
             bool have = false;
             if (a.guess.c[0]) {
-                n[0] = a.guess(0, p);
-                n[1] = a.guess(1, p);
-                n[2] = a.guess(2, p);
+                n[0] = a.guess(0, gk);
+                n[1] = a.guess(1, gk);
+                n[2] = a.guess(2, gk);
                 const double l = sqrt(dot3(n, n));
                 if (l > 0.5 && l < 2.0) {
                     normalize3(n);

@@ -114,12 +114,14 @@ __global__ void rows_kernel(RowsArgs a) {
         int64_t total = a.base + a.scan[a.npairs];
         *a.nrows_dev = (int)(total < a.cap ? total : a.cap);
     }
-    if (p >= a.npairs || !a.flags[p]) return;
-    int64_t r = a.base + a.scan[p];
+    if (p >= a.npairs) return;
+    int64_t r = a.flags[p] ? a.base + a.scan[p] : -1;
     if (r >= a.cap) {
         atomicOr(a.status, DEV_CAPACITY);
-        return;
+        r = -1;
     }
+    if (a.rowof) a.rowof[p] = (int)r;
+    if (r < 0) return;
     int i = a.pa[p], j = a.pb[p];
     const int64_t P = a.npairs;
     double nn[3], ra[3], rb[3], ta[3], tb[3];
@@ -179,27 +181,43 @@ __global__ void rows_kernel(RowsArgs a) {
     a.diag[r] = a.c * acc;
     if (a.invd) a.invd[r] = 1.0 / (a.c * acc);
     if (a.invdf) a.invdf[r] = (float)(1.0 / (a.c * acc));
-    double g0 = 0.0;
-    if (a.rec_index == 0 && a.prev_n > 0) {
-        // binary search of (i, j) among the previous step's A_0 rows
-        const long long key = ((long long)i << 32) | (long long)j;
-        int64_t lo = 0, hi = a.prev_n;
-        while (lo < hi) {
-            int64_t mid = (lo + hi) >> 1;
-            if (a.prev_keys[mid] < key) lo = mid + 1;
-            else hi = mid;
-        }
-        if (lo < a.prev_n && a.prev_keys[lo] == key) g0 = a.prev_gamma[lo];
-    }
+    const double g0 = (a.rec_index == 0 && a.gamma0) ? a.gamma0[p] : 0.0;
     if (a.gamma) a.gamma[r] = g0;
     if (a.gammaf) a.gammaf[r] = (float)g0;
 }
 
-__global__ void save_warm_kernel(SaveWarmArgs a) {
-    int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= *a.nrows0_dev) return;
-    a.keys[r] = ((long long)a.ia[r] << 32) | (long long)a.ib[r];
-    a.gout[r] = a.gamma ? a.gamma[r] : (double)a.gammaf[r];
+__global__ void reuse_kernel(ReuseArgs a) {
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= a.npairs) return;
+    const PairMemo m = a.memo[a.pv[p]];
+    const bool hit = a.stamp_prev >= 0 && m.stamp == a.stamp_prev && m.pidx >= 0 && m.pidx < a.nprev;
+    a.gamma0[p] = (hit && a.use_gamma) ? m.gamma : 0.0;
+    const bool take = hit && a.reuse_snsd;
+    if (take) {
+#pragma unroll
+        for (int k = 0; k < 10; ++k) a.s0[k * a.npairs + p] = a.sprev[k * a.nprev + m.pidx];
+        a.it0[p] = 0;
+    }
+    a.need[p] = take ? 0 : 1;
+}
+
+__global__ void index_compact_kernel(int64_t np, const int* __restrict__ flags, const int* __restrict__ scan,
+                                     int* __restrict__ idx) {
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p < np && flags[p]) idx[scan[p]] = (int)p;
+}
+
+__global__ void memo_save_kernel(MemoSaveArgs a) {
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= a.npairs) return;
+    const int r = a.rowof[p];
+    double g = 0.0;
+    if (r >= 0) g = a.gamma ? a.gamma[r] : (double)a.gammaf[r];
+    PairMemo m;
+    m.stamp = a.stamp;
+    m.pidx = (int)p;
+    m.gamma = g;
+    a.memo[a.pv[p]] = m;
 }
 
 __global__ void trial_kernel(TrialArgs a) {
@@ -301,10 +319,24 @@ relcp_status accept_launch(const AcceptArgs& a, cudaStream_t s) {
     RELCP_CUDA(cudaGetLastError());
     return RELCP_OK;
 }
-relcp_status save_warm_launch(const SaveWarmArgs& a, int64_t cap, cudaStream_t s) {
-    if (cap <= 0) return RELCP_OK;
+relcp_status reuse_launch(const ReuseArgs& a, cudaStream_t s) {
+    if (a.npairs == 0) return RELCP_OK;
     note_launch();
-    save_warm_kernel<<<nb(cap), kT, 0, s>>>(a);
+    reuse_kernel<<<nb(a.npairs), kT, 0, s>>>(a);
+    RELCP_CUDA(cudaGetLastError());
+    return RELCP_OK;
+}
+relcp_status index_compact_launch(int64_t np, const int* flags, const int* scan, int* idx, cudaStream_t s) {
+    if (np == 0) return RELCP_OK;
+    note_launch();
+    index_compact_kernel<<<nb(np), kT, 0, s>>>(np, flags, scan, idx);
+    RELCP_CUDA(cudaGetLastError());
+    return RELCP_OK;
+}
+relcp_status memo_save_launch(const MemoSaveArgs& a, cudaStream_t s) {
+    if (a.npairs == 0) return RELCP_OK;
+    note_launch();
+    memo_save_kernel<<<nb(a.npairs), kT, 0, s>>>(a);
     RELCP_CUDA(cudaGetLastError());
     return RELCP_OK;
 }

@@ -54,21 +54,37 @@ struct RowsArgs {
     float* gammaf;  // same for the mixed path or null
     int* nrows_dev; // set to base + number of flagged pairs
     int* status;
-    // warm start of A_0 rows from the previous step's A_0 rows (sorted keys
-    // (a << 32) | b with their final gamma); prev_n = 0 disables it
-    int64_t prev_n;
-    const long long* prev_keys;
-    const double* prev_gamma;
+    // A_0 only: warm start per pair (null: 0) and the pair -> row map (-1: no row)
+    const double* gamma0;
+    int* rowof;
 };
 
-struct SaveWarmArgs {
-    const int* nrows0_dev;  // number of A_0 rows (device)
-    const int* ia;
-    const int* ib;
+// C^k values of the pairs that were candidates in the previous step: the SNSD
+// result of that step's last overlap test (same configuration) and the final
+// gamma of the pair's A_0 row; need[p] = 1 for the pairs still to evaluate
+struct ReuseArgs {
+    int64_t npairs;
+    const int* pv;          // pair -> cached-list entry
+    const PairMemo* memo;   // per entry
+    int stamp_prev;         // stamp of the previous step (no memo matches a negative stamp)
+    int reuse_snsd;
+    int use_gamma;
+    const double* sprev;    // previous step's last trial SNSD output, 10 x nprev (SoA)
+    int64_t nprev;
+    double* s0;             // SNSD output at C^k, 10 x npairs (SoA)
+    int* it0;               // Newton iterations at C^k (0 for reused pairs)
+    double* gamma0;         // per pair
+    int* need;              // per pair
+};
+
+struct MemoSaveArgs {
+    int64_t npairs;
+    const int* pv;
+    const int* rowof;
     const double* gamma;    // FP64 path or null
     const float* gammaf;    // mixed path or null
-    long long* keys;
-    double* gout;
+    int stamp;
+    PairMemo* memo;
 };
 
 struct TrialArgs {
@@ -103,6 +119,9 @@ relcp_status rows_launch(const RowsArgs& a, cudaStream_t s);
 relcp_status trial_launch(const TrialArgs& a, cudaStream_t s);
 relcp_status accept_launch(const AcceptArgs& a, cudaStream_t s);
 relcp_status wrap_launch(int64_t n, double* x, const double box[3], cudaStream_t s);
-relcp_status save_warm_launch(const SaveWarmArgs& a, int64_t cap, cudaStream_t s);
+relcp_status reuse_launch(const ReuseArgs& a, cudaStream_t s);
+// idx[scan[p]] = p for the flagged pairs
+relcp_status index_compact_launch(int64_t np, const int* flags, const int* scan, int* idx, cudaStream_t s);
+relcp_status memo_save_launch(const MemoSaveArgs& a, cudaStream_t s);
 
 }  // namespace relcp

@@ -36,6 +36,7 @@ RELCP_FAULT_ROW_CAPACITY, RELCP_FAULT_LCP_ITERS = 1, 2
 RELCP_FLAG_PHASE_TIMING = 1
 RELCP_FLAG_NO_WARM_START = 2
 RELCP_FLAG_JACOBI = 4
+RELCP_FLAG_NO_SNSD_REUSE = 8
 MAX_DEPTH_STATS = 64
 
 
@@ -57,7 +58,7 @@ class relcp_step_stats(ctypes.Structure):
                 ("newton_fallbacks", c_int32), ("ms_lcp_kernel", c_double), ("lcp_alg_bytes", c_double),
                 ("ms_snsd_kernel", c_double), ("snsd_evals", c_int64), ("lcp_launches", c_int32),
                 ("snsd_launches", c_int32), ("pair_list_rebuilt", c_int32), ("pad0", c_int32),
-                ("newton_iters_c0", c_int64)]
+                ("newton_iters_c0", c_int64), ("snsd_c0_evaluated", c_int64)]
 
 
 class relcp_lcp_info(ctypes.Structure):

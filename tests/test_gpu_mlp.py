@@ -38,6 +38,10 @@ def test_features_and_targets_match_reference(relcp_gpu, orc):
     fr, tr = M.features(pairs, x, q, axes, box, out.cpu().numpy())
     assert np.abs(f.cpu().numpy() - fr).max() < 2e-6
     assert np.abs(t.cpu().numpy() - tr).max() < 2e-6
+    # inference features (no targets) are computed in FP32: same values to FP32 rounding
+    f32, t32 = R.relcp_mlp_features(dev(pairs, torch.int32), dev(x), dev(q), dev(axes), box, None)
+    assert t32 is None
+    assert np.abs(f32.cpu().numpy() - fr).max() < 2e-5
 
 
 def test_forward_matches_fp64(relcp_gpu):

@@ -372,3 +372,51 @@ def test_deterministic_bitwise(relcp_gpu):
         sim.close()
     for a, b in zip(outs[0], outs[1]):
         assert np.array_equal(a, b)
+
+
+def test_carried_c0_values_match_fresh_evaluation(relcp_gpu):
+    """From the second step on a pair that was a candidate in the previous step
+    takes its SNSD at C^k from that step's last overlap test, which evaluated
+    it at the configuration the step accepted, and its warm-start gamma from
+    the memo of the cached candidate list (carried across list rebuilds).
+    Against evaluating every pair afresh (RELCP_FLAG_NO_SNSD_REUSE) the
+    trajectory, the pair lists and the C^k signed distances agree within each
+    path's tolerance; the warm start cuts the LCP iterations."""
+    R = relcp_gpu
+    sc = scenes.suspension_scene(seed=5, n=2048, phi=0.1, phi_final=0.45, steps=60, dt=5e-3)
+    amin = float(sc.axes.min())
+    # mixed: the relative 1e-5 of that path, on lengths scaled by the smallest semi-axis
+    for prec, xtol, ptol in ((R.RELCP_FP64, 1e-9, 1e-10), (R.RELCP_MIXED, 1e-5 * amin, 1e-5 * amin)):
+        outs = {}
+        for flags in (0, R.RELCP_FLAG_NO_SNSD_REUSE, R.RELCP_FLAG_NO_WARM_START):
+            cfg = R.make_config(dynamics=R.RELCP_OVERDAMPED, precision=prec, dt=sc.dt, eps_ncp=1e-3 * amin,
+                                box=tuple(sc.box), skin=0.1 * amin, strain_rate=sc.meta["strain_rate"],
+                                length_scale=amin, flags=flags)
+            sim = R.Simulation(cfg)
+            sim.set_bodies(sc.x, sc.q, sc.axes)
+            ev, rebuilt, iters = [], 0, 0
+            for _ in range(40):
+                sim.step(1, allow=(R.RELCP_ERR_NOT_CONVERGED,))
+                st = sim.stats()
+                ev.append((st.snsd_c0_evaluated, st.n_pairs))
+                rebuilt += st.pair_list_rebuilt
+                iters += st.lcp_iters_total
+            x, q, v = sim.bodies()
+            box = np.asarray(R.relcp_get_box(sim.ctx))
+            pairs, phi0 = R.relcp_get_pairs(sim.ctx)
+            outs[flags] = (x, q, ev, rebuilt, iters, pairs, phi0)
+            sim.close()
+        (x0, q0, ev0, rb0, it0, p0, f0) = outs[0]
+        (x1, q1, ev1, rb1, it1, p1, f1) = outs[R.RELCP_FLAG_NO_SNSD_REUSE]
+        assert ev0[0][0] == ev0[0][1] and all(e == n for e, n in ev1)
+        assert sum(e for e, _ in ev0[1:]) < 0.2 * sum(n for _, n in ev0[1:])
+        assert rb0 >= 1  # the memo crossed at least one rebuild of the cached list
+        dx = x0 - x1
+        dx -= box * np.round(dx / box)
+        assert np.abs(dx).max() <= xtol and np.abs(q0 - q1).max() <= xtol
+        k0 = {tuple(p): f for p, f in zip(p0, f0)}
+        common = [(k0[tuple(p)], f) for p, f in zip(p1, f1) if tuple(p) in k0]
+        assert len(common) >= 0.99 * max(len(p0), len(p1))
+        a, b = np.array(common).T
+        assert np.abs(a - b).max() <= ptol
+        assert it0 < outs[R.RELCP_FLAG_NO_WARM_START][4]
