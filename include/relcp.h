@@ -326,6 +326,79 @@ relcp_status relcp_mlp_train_step(int64_t batch, float* params, float* adam_m, f
 relcp_status relcp_load_mlp(relcp_ctx* ctx, const float* params, int32_t ptr_kind);
 
 /* ------------------------------------------------------------------ */
+/* Batched scenes                                                       */
+/* ------------------------------------------------------------------ */
+
+/* Many independent periodic scenes of up to RELCP_BATCH_MAX_BODIES bodies,
+ * each stepped by the whole of Algorithm 1 (broad phase, SNSD, A_0, the
+ * recursive LCP with the overlap test and augmentation, accept) inside ONE
+ * persistent kernel launch per relcp_batch_step call: a CTA takes a scene from
+ * a device work queue (largest scenes first) and runs all requested steps of
+ * it with CTA barriers only.  The launch is captured in a CUDA graph and
+ * replayed.  The block size comes from relcp_batch_autotune (timed on the
+ * loaded scenes, cached in a JSON file) or relcp_batch_set_threads.
+ *   Dynamics, precision (FP64 or MIXED), drag_xi, density, lcp_max_iter and
+ *   max_recursion come from the relcp_config given to relcp_batch_create; box,
+ *   dt, eps_ncp, skin, lcp_tol and phi_skin are per scene.  guess and
+ *   strain_rate must be RELCP_GUESS_COLD and 0.  Bodies of different scenes
+ *   never interact. */
+#define RELCP_BATCH_MAX_BODIES 1024
+#define RELCP_SCENE_PARAMS 8 /* box x, y, z; dt; eps_ncp; skin; lcp_tol; phi_skin */
+
+typedef struct relcp_batch relcp_batch;
+
+typedef struct {
+    int32_t status;       /* relcp_status of the scene (worst over its steps) */
+    int32_t status_bits;  /* internal device bits (diagnostics) */
+    int32_t steps_done;   /* steps completed since relcp_batch_set_scenes */
+    int32_t depth_max;    /* deepest recursion of those steps */
+    int32_t lcp_iters;    /* projected-gradient iterations, summed over those steps */
+    int32_t n_pairs;      /* candidate pairs of the last step */
+    int32_t n_rows;       /* constraint rows of the last step */
+    int32_t pad;
+    double max_overlap;   /* largest overlap after the last step */
+    double lcp_residual;  /* natural residual of the last LCP */
+} relcp_scene_stats;
+
+/* Create an empty batch on the current device; the stream as in relcp_create. */
+relcp_status relcp_batch_create(const relcp_config* cfg, void* cuda_stream, relcp_batch** out);
+
+/* Load the scenes: scene s owns bodies scene_offsets[s] .. scene_offsets[s+1]-1
+ * (0 = offsets[0] <= ... , at most RELCP_BATCH_MAX_BODIES per scene; n = 
+ * offsets[n_scenes]).  x, q, semi_axes, vel (NULL = 0), f_ext (NULL = 0) as in
+ * relcp_set_bodies, n rows each; scene_params: n_scenes x RELCP_SCENE_PARAMS
+ * (box sides > 0 for a periodic axis, 0 for an open one; dt, eps_ncp, lcp_tol
+ * > 0; skin, phi_skin >= 0).  Positions are wrapped into the scene's box.
+ * Resets the per-scene statistics and warm starts. */
+relcp_status relcp_batch_set_scenes(relcp_batch* b, int32_t n_scenes, const int32_t* scene_offsets,
+                                    const double* x, const double* q, const double* semi_axes, const double* vel,
+                                    const double* f_ext, const double* scene_params, int32_t ptr_kind);
+
+/* Advance every scene by nsteps steps in one launch (synchronises the stream).
+ * Returns the worst status over the scenes; a scene that runs out of pair or
+ * row capacity (RELCP_ERR_CAPACITY) keeps its last accepted state. */
+relcp_status relcp_batch_step(relcp_batch* b, int32_t nsteps);
+
+/* Bodies in the order of relcp_batch_set_scenes (x, q: any may be NULL; vel:
+ * n x 6 step velocities). */
+relcp_status relcp_batch_get_bodies(relcp_batch* b, double* x, double* q, double* vel, int32_t ptr_kind);
+
+/* Per-scene statistics (host array of n_scenes). */
+relcp_status relcp_batch_scene_stats(relcp_batch* b, relcp_scene_stats* out);
+
+/* Time the candidate block sizes (64, 128, 256, 512 threads) on two steps of
+ * the loaded scenes (the scenes' state is restored afterwards) and keep the
+ * fastest.  cache_path (may be NULL): a JSON file of earlier choices, keyed by
+ * device, precision and the scenes' size histogram; a hit skips the timing, a
+ * miss adds the result.  *threads_out (may be NULL) receives the choice. */
+relcp_status relcp_batch_autotune(relcp_batch* b, const char* cache_path, int32_t* threads_out);
+
+/* Fix the block size (a multiple of 32 in [32, 1024]); 0 = untuned default. */
+relcp_status relcp_batch_set_threads(relcp_batch* b, int32_t threads);
+
+void relcp_batch_destroy(relcp_batch* b);
+
+/* ------------------------------------------------------------------ */
 /* Allocation-free variant                                              */
 /* ------------------------------------------------------------------ */
 

@@ -24,12 +24,7 @@ constexpr int kThreads = 256;
 
 __device__ __forceinline__ bool near_pair(View<3, const double> x, const double* __restrict__ rb, int64_t i,
                                           int64_t j, double L0, double L1, double L2, double skin) {
-    double dx = min_image(__dsub_rn(x(0, j), x(0, i)), L0);
-    double dy = min_image(__dsub_rn(x(1, j), x(1, i)), L1);
-    double dz = min_image(__dsub_rn(x(2, j), x(2, i)), L2);
-    double d2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
-    double s = __dadd_rn(__dadd_rn(rb[i], rb[j]), skin);
-    return d2 <= __dmul_rn(s, s);
+    return near_pair_exact(x(0, i), x(1, i), x(2, i), x(0, j), x(1, j), x(2, j), rb[i], rb[j], L0, L1, L2, skin);
 }
 
 __global__ void brute_count(int64_t n, View<3, const double> x, const double* __restrict__ rb, double L0,

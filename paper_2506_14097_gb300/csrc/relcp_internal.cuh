@@ -28,6 +28,7 @@ enum : int {
     DEV_NEWTON = 2,
     DEV_TIMEOUT = 4,
     DEV_CAPACITY = 8,
+    DEV_RECURSION = 16,  // recursion limit reached with violators left (batched scenes)
 };
 
 void set_error(const char* fmt, ...);
@@ -167,6 +168,20 @@ __device__ __forceinline__ double min_image(double d, double L) {
         k = rint(__ddiv_rn(d, L));
     }
     return __dsub_rn(d, __dmul_rn(L, k));
+}
+
+// The candidate test of the broad phase: |min_image(x_j - x_i)|^2 <=
+// (rb_i + rb_j + skin)^2 as a fixed sequence of separately rounded FP64
+// operations (no contraction), so the decision is reproducible bit for bit.
+__device__ __forceinline__ bool near_pair_exact(double xi0, double xi1, double xi2, double xj0, double xj1,
+                                                double xj2, double rbi, double rbj, double L0, double L1, double L2,
+                                                double skin) {
+    const double dx = min_image(__dsub_rn(xj0, xi0), L0);
+    const double dy = min_image(__dsub_rn(xj1, xi1), L1);
+    const double dz = min_image(__dsub_rn(xj2, xi2), L2);
+    const double d2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+    const double s = __dadd_rn(__dadd_rn(rbi, rbj), skin);
+    return d2 <= __dmul_rn(s, s);
 }
 
 // ---------------------------------------------------------------------------

@@ -19,6 +19,7 @@
 //   accept    : C^{k+1} = the last trial, positions wrapped into the box.
 #include "relcp_internal.cuh"
 #include "step_kernels.cuh"
+#include "step_math.cuh"
 
 namespace relcp {
 
@@ -30,69 +31,31 @@ inline unsigned nb(int64_t n) { return (unsigned)((n + kT - 1) / kT); }
 __global__ void prep_kernel(PrepArgs a) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= a.n) return;
-    double s = a.q[i], x = a.q[a.n + i], y = a.q[2 * a.n + i], z = a.q[3 * a.n + i];
-    double l = sqrt(s * s + x * x + y * y + z * z);
-    s /= l;
-    x /= l;
-    y /= l;
-    z /= l;
-    a.q[i] = s;
-    a.q[a.n + i] = x;
-    a.q[2 * a.n + i] = y;
-    a.q[3 * a.n + i] = z;
-    double R[9];
-    quat_to_R(s, x, y, z, R);
-    double a0 = a.axes[i], a1 = a.axes[a.n + i], a2 = a.axes[2 * a.n + i];
-    Sym3<double> P = rot_diag_rot(R, a0 * a0, a1 * a1, a2 * a2);
-    a.P[i] = P.xx;
-    a.P[a.n + i] = P.yy;
-    a.P[2 * a.n + i] = P.zz;
-    a.P[3 * a.n + i] = P.xy;
-    a.P[4 * a.n + i] = P.xz;
-    a.P[5 * a.n + i] = P.yz;
-    double amax = fmax(a0, fmax(a1, a2));
-    a.rb[i] = amax;
-    double kt;
-    Sym3<double> Kr;
-    if (a.dynamics == RELCP_OVERDAMPED) {
-        double L = 2.0 * amax;
-        kt = 1.0 / (a.drag_xi * L);
-        double kr = 12.0 / (a.drag_xi * L * L * L);
-        Kr = Sym3<double>{kr, kr, kr, 0.0, 0.0, 0.0};
-    } else {
-        const double pi = 3.14159265358979323846;
-        double m = a.density * 4.0 / 3.0 * pi * a0 * a1 * a2;
-        double I0 = m / 5.0 * (a1 * a1 + a2 * a2), I1 = m / 5.0 * (a0 * a0 + a2 * a2), I2 = m / 5.0 * (a0 * a0 + a1 * a1);
-        kt = a.dt / m;
-        Kr = rot_diag_rot(R, a.dt / I0, a.dt / I1, a.dt / I2);
+    const int64_t n = a.n;
+    double qin[4], ax[3], vel[6], f[6], x[3];
+    for (int k = 0; k < 4; ++k) qin[k] = a.q[k * n + i];
+    for (int k = 0; k < 3; ++k) {
+        ax[k] = a.axes[k * n + i];
+        x[k] = a.x[k * n + i];
     }
-    a.K[i] = kt;
-    a.K[a.n + i] = Kr.xx;
-    a.K[2 * a.n + i] = Kr.yy;
-    a.K[3 * a.n + i] = Kr.zz;
-    a.K[4 * a.n + i] = Kr.xy;
-    a.K[5 * a.n + i] = Kr.xz;
-    a.K[6 * a.n + i] = Kr.yz;
-    if (a.Kf) {
-        const double kv[7] = {kt, Kr.xx, Kr.yy, Kr.zz, Kr.xy, Kr.xz, Kr.yz};
-        for (int k = 0; k < 7; ++k) a.Kf[k * a.n + i] = (float)kv[k];
-    }
-    // U_free = vel + K F_ext (+ affine background velocity)
-    double f[6], u[6];
     for (int k = 0; k < 6; ++k) {
-        f[k] = a.fext[k * a.n + i];
-        u[k] = a.vel[k * a.n + i];
+        vel[k] = a.vel[k * n + i];
+        f[k] = a.fext[k * n + i];
     }
-    u[0] += kt * f[0];
-    u[1] += kt * f[1];
-    u[2] += kt * f[2];
-    u[3] += Kr.xx * f[3] + Kr.xy * f[4] + Kr.xz * f[5];
-    u[4] += Kr.xy * f[3] + Kr.yy * f[4] + Kr.yz * f[5];
-    u[5] += Kr.xz * f[3] + Kr.yz * f[4] + Kr.zz * f[5];
-    if (a.strain_rate != 0.0)
-        for (int k = 0; k < 3; ++k)
-            if (a.box[k] > 0.0) u[k] += a.strain_rate * (a.x[k * a.n + i] - 0.5 * a.box[k]);
-    for (int k = 0; k < 6; ++k) a.ufree[k * a.n + i] = u[k];
+    step_math::BodyPrep b;
+    step_math::prep_body(qin, ax, vel, f, x, a.dynamics, a.dt, a.drag_xi, a.density, a.strain_rate, a.box, b);
+    for (int k = 0; k < 4; ++k) a.q[k * n + i] = b.q[k];
+    a.P[i] = b.P.xx;
+    a.P[n + i] = b.P.yy;
+    a.P[2 * n + i] = b.P.zz;
+    a.P[3 * n + i] = b.P.xy;
+    a.P[4 * n + i] = b.P.xz;
+    a.P[5 * n + i] = b.P.yz;
+    a.rb[i] = b.rb;
+    for (int k = 0; k < 7; ++k) a.K[k * n + i] = b.K[k];
+    if (a.Kf)
+        for (int k = 0; k < 7; ++k) a.Kf[k * n + i] = (float)b.K[k];
+    for (int k = 0; k < 6; ++k) a.ufree[k * n + i] = b.ufree[k];
 }
 
 __global__ void flag_le_kernel(int64_t np, const double* __restrict__ phi, double thr, int* __restrict__ flags) {
@@ -102,10 +65,12 @@ __global__ void flag_le_kernel(int64_t np, const double* __restrict__ phi, doubl
 
 __device__ __forceinline__ double body_rate(const double* U, int64_t n, int i, int j, const double* nn,
                                             const double* ta, const double* tb) {
-    double r = 0.0;
-    for (int k = 0; k < 3; ++k) r += nn[k] * (U[k * n + j] - U[k * n + i]);
-    for (int k = 0; k < 3; ++k) r += tb[k] * U[(3 + k) * n + j] - ta[k] * U[(3 + k) * n + i];
-    return r;
+    double Ui[6], Uj[6];
+    for (int k = 0; k < 6; ++k) {
+        Ui[k] = U[k * n + i];
+        Uj[k] = U[k * n + j];
+    }
+    return step_math::row_rate(Ui, Uj, nn, ta, tb);
 }
 
 __global__ void rows_kernel(RowsArgs a) {
@@ -131,8 +96,7 @@ __global__ void rows_kernel(RowsArgs a) {
         rb[k] = a.snsd[(7 + k) * P + p];
     }
     double phi = a.snsd[p];
-    cross3(ra, nn, ta);
-    cross3(rb, nn, tb);
+    step_math::row_torques(nn, ra, rb, ta, tb);
     const int64_t C = a.cap;
     a.ia[r] = i;
     a.ib[r] = j;
@@ -154,12 +118,12 @@ __global__ void rows_kernel(RowsArgs a) {
     if (a.rec_index == 0) {
         double rate = body_rate(a.ufree, a.nbodies, i, j, nn, ta, tb);
         if (a.strain_rate != 0.0) {
-            double corr = 0.0;
+            double xi[3], xj[3];
             for (int k = 0; k < 3; ++k) {
-                double raw = a.x[k * a.nbodies + j] - a.x[k * a.nbodies + i];
-                corr += nn[k] * (min_image(raw, a.box[k]) - raw);
+                xi[k] = a.x[k * a.nbodies + i];
+                xj[k] = a.x[k * a.nbodies + j];
             }
-            rate += a.strain_rate * corr;
+            rate += a.strain_rate * step_math::affine_image_corr(xi, xj, nn, a.box);
         }
         qv = phi + a.c * rate;
     } else {
@@ -168,16 +132,12 @@ __global__ void rows_kernel(RowsArgs a) {
     a.q[r] = qv;
     if (a.qf) a.qf[r] = (float)qv;
     // diagonal c d^T K d
-    double acc = (a.K[i] + a.K[j]) * (nn[0] * nn[0] + nn[1] * nn[1] + nn[2] * nn[2]);
-    for (int side = 0; side < 2; ++side) {
-        int b = side ? j : i;
-        const double* t = side ? tb : ta;
-        const int64_t n = a.nbodies;
-        double kxx = a.K[n + b], kyy = a.K[2 * n + b], kzz = a.K[3 * n + b];
-        double kxy = a.K[4 * n + b], kxz = a.K[5 * n + b], kyz = a.K[6 * n + b];
-        acc += t[0] * (kxx * t[0] + kxy * t[1] + kxz * t[2]) + t[1] * (kxy * t[0] + kyy * t[1] + kyz * t[2]) +
-               t[2] * (kxz * t[0] + kyz * t[1] + kzz * t[2]);
+    double Ki[7], Kj[7];
+    for (int k = 0; k < 7; ++k) {
+        Ki[k] = a.K[k * a.nbodies + i];
+        Kj[k] = a.K[k * a.nbodies + j];
     }
+    const double acc = step_math::row_dKd(Ki, Kj, nn, ta, tb);
     a.diag[r] = a.c * acc;
     if (a.invd) a.invd[r] = 1.0 / (a.c * acc);
     if (a.invdf) a.invdf[r] = (float)(1.0 / (a.c * acc));
@@ -224,33 +184,20 @@ __global__ void trial_kernel(TrialArgs a) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= a.n) return;
     const int64_t n = a.n;
-    double U[6];
+    double U[6], x[3], q[4], ax[3], xt[3], qt[4];
     for (int k = 0; k < 6; ++k) {
         U[k] = a.ufree[k * n + i] + a.uc[k * n + i];
         a.ustep[k * n + i] = U[k];
     }
-    for (int k = 0; k < 3; ++k) a.xt[k * n + i] = a.x[k * n + i] + a.dt * U[k];
-    double s = a.q[i], x = a.q[n + i], y = a.q[2 * n + i], z = a.q[3 * n + i];
-    // q + dt/2 (0, w) (x) q
-    double h = 0.5 * a.dt;
-    double w0 = U[3], w1 = U[4], w2 = U[5];
-    double ns = s - h * (w0 * x + w1 * y + w2 * z);
-    double nx = x + h * (s * w0 + (w1 * z - w2 * y));
-    double ny = y + h * (s * w1 + (w2 * x - w0 * z));
-    double nz = z + h * (s * w2 + (w0 * y - w1 * x));
-    double l = sqrt(ns * ns + nx * nx + ny * ny + nz * nz);
-    ns /= l;
-    nx /= l;
-    ny /= l;
-    nz /= l;
-    a.qt[i] = ns;
-    a.qt[n + i] = nx;
-    a.qt[2 * n + i] = ny;
-    a.qt[3 * n + i] = nz;
-    double R[9];
-    quat_to_R(ns, nx, ny, nz, R);
-    double a0 = a.axes[i], a1 = a.axes[n + i], a2 = a.axes[2 * n + i];
-    Sym3<double> P = rot_diag_rot(R, a0 * a0, a1 * a1, a2 * a2);
+    for (int k = 0; k < 3; ++k) {
+        x[k] = a.x[k * n + i];
+        ax[k] = a.axes[k * n + i];
+    }
+    for (int k = 0; k < 4; ++k) q[k] = a.q[k * n + i];
+    Sym3<double> P;
+    step_math::trial_body(x, q, U, ax, a.dt, xt, qt, P);
+    for (int k = 0; k < 3; ++k) a.xt[k * n + i] = xt[k];
+    for (int k = 0; k < 4; ++k) a.qt[k * n + i] = qt[k];
     a.Pt[i] = P.xx;
     a.Pt[n + i] = P.yy;
     a.Pt[2 * n + i] = P.zz;
@@ -263,12 +210,7 @@ __global__ void accept_kernel(AcceptArgs a) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= a.n) return;
     const int64_t n = a.n;
-    for (int k = 0; k < 3; ++k) {
-        double v = a.xt[k * n + i];
-        double L = a.box[k];
-        if (L > 0.0) v = v - L * floor(v / L);
-        a.x[k * n + i] = v;
-    }
+    for (int k = 0; k < 3; ++k) a.x[k * n + i] = step_math::wrap_coord(a.xt[k * n + i], a.box[k]);
     for (int k = 0; k < 4; ++k) a.q[k * n + i] = a.qt[k * n + i];
     if (a.inertial)
         for (int k = 0; k < 6; ++k) a.vel[k * n + i] = a.ustep[k * n + i];
@@ -277,9 +219,8 @@ __global__ void accept_kernel(AcceptArgs a) {
 __global__ void wrap_kernel(int64_t n, double* x, double L0, double L1, double L2) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    double L[3] = {L0, L1, L2};
-    for (int k = 0; k < 3; ++k)
-        if (L[k] > 0.0) x[k * n + i] = x[k * n + i] - L[k] * floor(x[k * n + i] / L[k]);
+    const double L[3] = {L0, L1, L2};
+    for (int k = 0; k < 3; ++k) x[k * n + i] = step_math::wrap_coord(x[k * n + i], L[k]);
 }
 
 }  // namespace

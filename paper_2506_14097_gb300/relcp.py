@@ -88,7 +88,9 @@ EXPORTS = ["relcp_last_error", "relcp_kernel_launches", "relcp_version", "relcp_
            "relcp_step", "relcp_get_bodies", "relcp_get_box", "relcp_stats", "relcp_get_pairs", "relcp_get_rows",
            "relcp_get_contact_velocity", "relcp_destroy", "relcp_broadphase", "relcp_snsd_eval", "relcp_lcp_solve",
            "relcp_snsd_eval_noalloc", "relcp_mlp_features", "relcp_mlp_forward", "relcp_mlp_train_step",
-           "relcp_load_mlp"]
+           "relcp_load_mlp", "relcp_batch_create", "relcp_batch_set_scenes", "relcp_batch_step",
+           "relcp_batch_get_bodies", "relcp_batch_scene_stats", "relcp_batch_autotune", "relcp_batch_set_threads",
+           "relcp_batch_destroy"]
 
 
 def library_path() -> str:
@@ -135,6 +137,14 @@ def load(build_if_needed: bool = True):
         "relcp_mlp_train_step": [c_int64, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
                                  POINTER(relcp_mlp_train_config), c_void_p, POINTER(c_double), c_void_p],
         "relcp_load_mlp": [c_void_p, c_void_p, c_int32],
+        "relcp_batch_create": [POINTER(relcp_config), c_void_p, POINTER(c_void_p)],
+        "relcp_batch_set_scenes": [c_void_p, c_int32, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
+                                   c_void_p, c_int32],
+        "relcp_batch_step": [c_void_p, c_int32],
+        "relcp_batch_get_bodies": [c_void_p, c_void_p, c_void_p, c_void_p, c_int32],
+        "relcp_batch_scene_stats": [c_void_p, c_void_p],
+        "relcp_batch_autotune": [c_void_p, c_char_p, POINTER(c_int32)],
+        "relcp_batch_set_threads": [c_void_p, c_int32],
     }
     for name, args in sigs.items():
         f = getattr(L, name)
@@ -142,6 +152,8 @@ def load(build_if_needed: bool = True):
         f.restype = c_int32
     L.relcp_destroy.argtypes = [c_void_p]
     L.relcp_destroy.restype = None
+    L.relcp_batch_destroy.argtypes = [c_void_p]
+    L.relcp_batch_destroy.restype = None
     L.relcp_kernel_launches.argtypes = []
     L.relcp_kernel_launches.restype = c_int64
     _lib = L
@@ -433,6 +445,106 @@ class Simulation:
         if self.ctx:
             relcp_destroy(self.ctx)
             self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ---------------------------------------------------------------------------
+# batched scenes
+# ---------------------------------------------------------------------------
+BATCH_MAX_BODIES = 1024
+SCENE_PARAMS = 8
+
+
+class relcp_scene_stats(ctypes.Structure):
+    _fields_ = [("status", c_int32), ("status_bits", c_int32), ("steps_done", c_int32), ("depth_max", c_int32),
+                ("lcp_iters", c_int32), ("n_pairs", c_int32), ("n_rows", c_int32), ("pad", c_int32),
+                ("max_overlap", c_double), ("lcp_residual", c_double)]
+
+
+def relcp_batch_create(cfg: relcp_config, stream=None):
+    h = c_void_p()
+    _check(load().relcp_batch_create(byref(cfg), c_void_p(_stream(stream)), byref(h)), "relcp_batch_create")
+    return h
+
+
+def relcp_batch_set_scenes(b, offsets, x, q, axes, vel, fext, params):
+    offsets = np.ascontiguousarray(offsets, dtype=np.int32)
+    x, q, axes, params = (np.ascontiguousarray(a, dtype=np.float64) for a in (x, q, axes, params))
+    vel = None if vel is None else np.ascontiguousarray(vel, dtype=np.float64)
+    fext = None if fext is None else np.ascontiguousarray(fext, dtype=np.float64)
+    _check(load().relcp_batch_set_scenes(b, int(offsets.shape[0] - 1), _ptr(offsets), _ptr(x), _ptr(q), _ptr(axes),
+                                         _ptr(vel), _ptr(fext), _ptr(params), RELCP_PTR_HOST),
+           "relcp_batch_set_scenes")
+
+
+def relcp_batch_step(b, nsteps=1, allow=()):
+    return _check(load().relcp_batch_step(b, int(nsteps)), "relcp_batch_step", allow)
+
+
+def relcp_batch_get_bodies(b, x, q, vel):
+    _check(load().relcp_batch_get_bodies(b, _ptr(x), _ptr(q), _ptr(vel), RELCP_PTR_HOST), "relcp_batch_get_bodies")
+
+
+def relcp_batch_scene_stats(b, n_scenes):
+    out = (relcp_scene_stats * n_scenes)()
+    _check(load().relcp_batch_scene_stats(b, ctypes.cast(out, c_void_p)), "relcp_batch_scene_stats")
+    return list(out)
+
+
+def relcp_batch_autotune(b, cache_path=None):
+    t = c_int32(0)
+    path = None if cache_path is None else os.fsencode(cache_path)
+    _check(load().relcp_batch_autotune(b, path, byref(t)), "relcp_batch_autotune")
+    return int(t.value)
+
+
+def relcp_batch_set_threads(b, threads):
+    _check(load().relcp_batch_set_threads(b, int(threads)), "relcp_batch_set_threads")
+
+
+def relcp_batch_destroy(b):
+    load().relcp_batch_destroy(b)
+
+
+class Batch:
+    """Many independent scenes stepped by one persistent launch."""
+
+    def __init__(self, cfg: relcp_config, stream=None):
+        self.cfg = cfg
+        self.h = relcp_batch_create(cfg, stream)
+        self.offsets = None
+
+    def set_scenes(self, offsets, x, q, axes, params, vel=None, fext=None):
+        self.offsets = np.ascontiguousarray(offsets, dtype=np.int32)
+        relcp_batch_set_scenes(self.h, self.offsets, x, q, axes, vel, fext, params)
+
+    def step(self, nsteps=1, allow=()):
+        return relcp_batch_step(self.h, nsteps, allow)
+
+    def bodies(self):
+        n = int(self.offsets[-1])
+        x, q, v = np.zeros((n, 3)), np.zeros((n, 4)), np.zeros((n, 6))
+        relcp_batch_get_bodies(self.h, x, q, v)
+        return x, q, v
+
+    def scene_stats(self):
+        return relcp_batch_scene_stats(self.h, len(self.offsets) - 1)
+
+    def autotune(self, cache_path=None):
+        return relcp_batch_autotune(self.h, cache_path)
+
+    def set_threads(self, threads):
+        relcp_batch_set_threads(self.h, threads)
+
+    def close(self):
+        if self.h:
+            relcp_batch_destroy(self.h)
+            self.h = None
 
     def __del__(self):
         try:

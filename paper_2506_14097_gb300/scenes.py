@@ -163,6 +163,27 @@ def batched_scenes(n_scenes: int = 2048, seed0: int = 1000, nmin: int = 2, nmax:
     return out
 
 
+def pack_scenes(scenes: list, precision_fp64: bool = False, eps_factor: float = 1e-3, skin_factor: float = 0.1):
+    """Concatenate scenes for the batched entry points: (offsets, x, q, axes,
+    vel, params) with params[s] = (box x, y, z, dt, eps_ncp, skin, lcp_tol,
+    phi_skin).  Per scene, with a_min its smallest semi-axis: eps_ncp =
+    eps_factor a_min, skin = phi_skin = skin_factor a_min, lcp_tol = 1e-12
+    (FP64) or 1e-7 (mixed) times a_min."""
+    offsets = np.zeros(len(scenes) + 1, dtype=np.int32)
+    params = np.zeros((len(scenes), 8))
+    for s, sc in enumerate(scenes):
+        offsets[s + 1] = offsets[s] + sc.n
+        amin = float(sc.axes.min()) if sc.n else 1.0
+        params[s, 0:3] = sc.box
+        params[s, 3] = sc.dt
+        params[s, 4] = eps_factor * amin
+        params[s, 5] = skin_factor * amin
+        params[s, 6] = (1e-12 if precision_fp64 else 1e-7) * amin
+        params[s, 7] = skin_factor * amin
+    cat = lambda f, w: (np.concatenate([getattr(sc, f) for sc in scenes if sc.n]) if offsets[-1] else np.zeros((0, w)))
+    return offsets, cat("x", 3), cat("q", 4), cat("axes", 3), cat("vel", 6), params
+
+
 def two_ellipsoid_scene(offset_y: float = 2.5, force: float = 1.0) -> Scene:
     """Two identical ellipsoids with radii (1, 1, 2) rotated so that the long
     axis lies in the x-y plane at 45 degrees, centres one unit apart in x and
