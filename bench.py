@@ -54,12 +54,16 @@ def build_scene(n, seed=1, steps=2000):
 EXTRA_FLAGS = 0
 
 
-def make_cfg(R, sc, precision, guess, timing=True):
+def make_cfg(R, sc, precision, guess, timing="lcp"):
+    """timing: None, "lcp" (CUDA events around the LCP launches only, for the
+    roofline; what the timed runs use) or "phases" (events between all phases,
+    ~2 us of host time each: a separate breakdown run)."""
     amin = float(sc.axes.min())
+    tf = {None: 0, False: 0, "lcp": R.RELCP_FLAG_LCP_TIMING, "phases": R.RELCP_FLAG_PHASE_TIMING}[timing]
     return R.make_config(dynamics=R.RELCP_OVERDAMPED, precision=precision, guess=guess, dt=sc.dt,
                          eps_ncp=1e-3 * amin, box=tuple(sc.box), skin=0.1 * amin,
                          strain_rate=sc.meta["strain_rate"], length_scale=amin, lcp_max_iter=20000,
-                         flags=(R.RELCP_FLAG_PHASE_TIMING if timing else 0) | EXTRA_FLAGS)
+                         flags=tf | EXTRA_FLAGS)
 
 
 class Clocks:
@@ -168,17 +172,18 @@ def new_sim(R, sc, precision, guess, timing, stream, mlp_params):
     return sim
 
 
-def run_gpu_arm(R, torch, sc, precision, guess, steps, warmup, flush, stream, nvtx_from=None, mlp_params=None):
+def run_gpu_arm(R, torch, sc, precision, guess, steps, warmup, flush, stream, nvtx_from=None, mlp_params=None,
+                timing="lcp"):
     """W warm-up steps on one context, then `steps` timed steps from the initial
     state on a fresh context.  Returns per-step times and accumulated stats."""
     x, q, axes = (np.ascontiguousarray(a) for a in (sc.x, sc.q, sc.axes))
     if warmup > 0:
-        sim = new_sim(R, sc, precision, guess, False, stream.cuda_stream, mlp_params)
+        sim = new_sim(R, sc, precision, guess, None, stream.cuda_stream, mlp_params)
         sim.set_bodies(x, q, axes)
         for _ in range(warmup):
             sim.step(1, allow=(R.RELCP_ERR_NOT_CONVERGED,))
         sim.close()
-    sim = new_sim(R, sc, precision, guess, True, stream.cuda_stream, mlp_params)
+    sim = new_sim(R, sc, precision, guess, timing, stream.cuda_stream, mlp_params)
     sim.set_bodies(x, q, axes)
     torch.cuda.synchronize()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
@@ -235,7 +240,7 @@ def run_e2e(R, torch, sc, precision, guess, steps, mlp_params=None):
     n = sc.n
     x, q, axes = (np.ascontiguousarray(a) for a in (sc.x, sc.q, sc.axes))
     u = np.zeros((n, 6))
-    cfg = make_cfg(R, sc, precision, guess, timing=False)
+    cfg = make_cfg(R, sc, precision, guess, timing=None)
     sim = R.Simulation(cfg)
     if guess == R.RELCP_GUESS_MLP:
         R.relcp_load_mlp(sim.ctx, mlp_params)
@@ -340,6 +345,7 @@ def main():
     ap.add_argument("--ref-budget", type=float, default=150.0)
     ap.add_argument("--jacobi", type=int, default=0, help="1: Jacobi-scaled projected-gradient steps")
     ap.add_argument("--cold", action="store_true", help="cold SNSD start only (no learned guess)")
+    ap.add_argument("--phase-breakdown", type=int, default=1, help="1: extra run with per-phase events")
     ap.add_argument("--batched-scenes", type=int, default=2048,
                     help="scenes of the batched-scene measurement (0 skips it)")
     ap.add_argument("--nvtx-from", type=int, default=None,
@@ -437,6 +443,17 @@ def main():
     batched = (run_batched(R, torch, args.batched_scenes, rank=rank, world=world, dist=dist)
                if args.batched_scenes > 0 else None)
 
+    # phase breakdown: a separate run of the headline configuration with events
+    # between all phases (their host cost inflates its step times, so it is not
+    # the timed run)
+    phases, accp = None, None
+    if args.phase_breakdown and rank == 0:
+        _, accp = run_gpu_arm(R, torch, sc, precision, guess, args.steps, args.warmup, flush, stream, None, mlp_params,
+                              timing="phases")
+        phases = {"broadphase": accp["ms_broadphase"], "snsd_kernels": accp["snsd_ms"],
+                  "lcp_incl_csr": accp["ms_lcp_phase"], "rest": accp["ms_other"],
+                  "to_last_sync": accp["ms_step_events"], "note": "separate run with per-phase CUDA events"}
+
     hbm, peak_kind = peaks()
     lcp_gbs = acc["lcp_bytes"] / (acc["lcp_ms"] / 1e3) / 1e9 if acc["lcp_ms"] > 0 else 0.0
     line = None
@@ -472,11 +489,10 @@ def main():
                       "rows_max": acc["rows_max"], "pairs_max": acc["pairs_max"],
                       "lcp_iters_total": acc["lcp_iters"], "max_overlap": acc["max_overlap"],
                       "eps_ncp": 1e-3 * float(sc.axes.min()), "status": acc["status"],
-                      "snsd_kernel_ms": acc["snsd_ms"], "snsd_evals": acc["snsd_evals"],
+                      "snsd_kernel_ms": accp["snsd_ms"] if accp else None,
+                      "snsd_evals": accp["snsd_evals"] if accp else None,
                       "lcp_kernel_ms": acc["lcp_ms"], "wall_s": t_wall,
-                      "phase_ms": {"broadphase": acc["ms_broadphase"], "snsd": acc["snsd_ms"],
-                                   "lcp_incl_csr": acc["ms_lcp_phase"], "rest": acc["ms_other"],
-                                   "to_last_sync": acc["ms_step_events"]},
+                      "phase_ms": phases,
                       "pair_list_rebuilds": acc["rebuilds"],
                       "newton_iters_per_pair_c0": acc.get("newton_c0", 0) / max(acc.get("pairs_total", 1), 1),
                       "phi_final": sc.meta["volume"] / float(np.prod(acc["box_final"]))},

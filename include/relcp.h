@@ -96,6 +96,9 @@ enum {
                                       gamma of the same pair (the solution is the same within lcp_tol) */
     RELCP_FLAG_JACOBI = 4u,        /* projected-gradient steps scaled by 1 / A_aa, BB lengths in the
                                       matching metric (same solution, fewer iterations on uneven rows) */
+    RELCP_FLAG_LCP_TIMING = 16u,   /* CUDA events around the LCP kernel launches only (ms_lcp_kernel,
+                                      lcp_alg_bytes), without the per-phase events; an event record costs the
+                                      host ~2 us on this hardware */
     RELCP_FLAG_NO_SNSD_REUSE = 8u  /* evaluate the SNSD of every candidate pair at C^k.  By default a
                                       pair that was a candidate in the previous step takes its C^k
                                       values from that step's last overlap test, which evaluated it at

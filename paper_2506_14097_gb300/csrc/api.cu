@@ -65,7 +65,8 @@ struct DevStep {
     unsigned long long iters0;      // Newton iterations summed over the pairs at C^k
     LcpDevResult lcp;   // iterations and residual of the last LCP
     int c0_evals;       // pairs evaluated at C^k (the others reused the previous step's values)
-    int pad;
+    int np;             // candidate pairs of the step
+    unsigned long long la_dmax;  // bits of the largest displacement of the trial positions since the list build
 };
 
 struct relcp_ctx {
@@ -99,12 +100,17 @@ struct relcp_ctx {
     // accepted configuration (= the next C^k) and the per-pair memo of the
     // cached candidate list (bp.memo), stamped with the step number
     DBuf<double> s1prev;
-    int64_t nprev = 0;
+    int64_t nprev = 0, sprev_stride = 0;
+    // the previous step checked the cached pair list against the positions it
+    // accepted (= this step's C^k): la_ok says the check is current, la_rebuild
+    // whether the list must be rebuilt; with la_ok && !la_rebuild the broad
+    // phase needs no host round trip
+    bool la_ok = false, la_rebuild = true;
     int stamp = 0;         // stamp written by the last completed step
     bool memo_ok = false;  // memo and s1prev describe the current state
     bool snsd_ok = false;  // s1prev may stand in for the SNSD at C^k
     DBuf<double> gamma0;   // per pair: warm start of its A_0 row
-    DBuf<int> need, needscan, idx, rowof;
+    DBuf<int> idx, rowof;  // pairs to evaluate at C^k (unordered); pair -> A_0 row
 };
 
 namespace {
@@ -177,47 +183,55 @@ relcp_status grow_rows(relcp_ctx* c, int64_t need) {
 // CUDA events of the optional per-phase timing, recorded on the context
 // stream and read only after a stream synchronisation.  Events come from a
 // per-context pool, created once.
+// CUDA-event timing of a step: per-phase marks (RELCP_FLAG_PHASE_TIMING) and/or
+// events around the LCP kernel launches only (take(), also with
+// RELCP_FLAG_LCP_TIMING)
 struct PhaseTimer {
     std::vector<cudaEvent_t>* pool = nullptr;
-    bool on = false;
+    bool on = false;       // per-phase marks
+    bool kernels = false;  // kernel events (take)
     cudaStream_t s{};
     int k = 0;
-    relcp_status start(bool enable, cudaStream_t st, std::vector<cudaEvent_t>* p) {
-        on = enable;
+    relcp_status start(bool phases, bool lcp_only, cudaStream_t st, std::vector<cudaEvent_t>* p) {
+        on = phases;
+        kernels = phases || lcp_only;
         s = st;
         k = 0;
         pool = p;
         return RELCP_OK;
     }
-    int mark() {
-        if (!on) return -1;
-        if (k >= (int)pool->size()) {
-            cudaEvent_t e;
-            if (cudaEventCreate(&e) != cudaSuccess) return -1;
-            pool->push_back(e);
-        }
-        cudaEventRecord((*pool)[k], s);
-        return k++;
-    }
-    // both events must have completed (call after a stream synchronisation)
-    float ms(int a, int b) {
-        float t = 0.f;
-        if (on && a >= 0 && b >= 0) cudaEventElapsedTime(&t, (*pool)[a], (*pool)[b]);
-        return t;
-    }
-    // an unrecorded event for a callee to record (index returned in *idx)
-    cudaEvent_t take(int* idx) {
-        *idx = -1;
-        if (!on) return nullptr;
+    cudaEvent_t next() {
         if (k >= (int)pool->size()) {
             cudaEvent_t e;
             if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
             pool->push_back(e);
         }
-        *idx = k;
-        return (*pool)[k++];
+        return (*pool)[k];
     }
-    void stop() { on = false; }
+    int mark() {
+        if (!on) return -1;
+        cudaEvent_t e = next();
+        if (!e) return -1;
+        cudaEventRecord(e, s);
+        return k++;
+    }
+    // both events must have completed (call after a stream synchronisation)
+    float ms(int a, int b) {
+        float t = 0.f;
+        if (kernels && a >= 0 && b >= 0) cudaEventElapsedTime(&t, (*pool)[a], (*pool)[b]);
+        return t;
+    }
+    // an unrecorded event for a callee to record (index returned in *idx)
+    cudaEvent_t take(int* idx) {
+        *idx = -1;
+        if (!kernels) return nullptr;
+        cudaEvent_t e = next();
+        if (!e) return nullptr;
+        *idx = k;
+        ++k;
+        return e;
+    }
+    void stop() { on = kernels = false; }
 };
 
 relcp_status step_once(relcp_ctx* c) {
@@ -234,7 +248,8 @@ relcp_status step_once(relcp_ctx* c) {
     }
     const bool mixed = cfg.precision == RELCP_MIXED;
     PhaseTimer tm;
-    RELCP_TRY(tm.start((cfg.flags & RELCP_FLAG_PHASE_TIMING) != 0, s, &c->events));
+    RELCP_TRY(tm.start((cfg.flags & RELCP_FLAG_PHASE_TIMING) != 0, (cfg.flags & RELCP_FLAG_LCP_TIMING) != 0, s,
+                       &c->events));
     std::vector<std::pair<int, int>> snsd_marks, lcp_marks, lcpk_marks;
     int t_begin = tm.mark();
     RELCP_CUDA(cudaMemsetAsync(c->dstep.p, 0, sizeof(DevStep), s));
@@ -265,13 +280,27 @@ relcp_status step_once(relcp_ctx* c) {
     pa.ufree = c->ufree.p;
     RELCP_TRY(prep_launch(pa, s));
 
-    // broad phase (synchronises once for the pair count)
+    // broad phase.  When the previous step's look-ahead showed the cached list
+    // complete for these positions, the exact filter and compaction run with
+    // the pair count left on the device; otherwise the synchronous path checks
+    // the bound and rebuilds the list if needed.  Per-pair work below runs over
+    // the list's capacity PC (also the SoA stride of pair arrays) and stops at
+    // the device count.
     View<3, const double> xv = View<3, const double>::soa(c->x.p, n);
     const int rebuilds_before = c->bp.rebuilds;
-    RELCP_TRY(broadphase_cached(n, c->x.p, c->rb.p, c->rb_max, box0, cfg.skin, c->pa, c->pb, &c->npairs, c->bp, s));
+    const bool fast_bp = c->la_ok && !c->la_rebuild && n >= 2 &&
+                         verlet_bound_holds(c->bp, n, box0, c->rb_max, cfg.skin, 0.0);
+    c->la_ok = false;  // set again when this step completes
+    if (fast_bp) {
+        RELCP_TRY(broadphase_filter_async(n, c->x.p, c->rb.p, box0, cfg.skin, c->pa, c->pb, c->bp, s));
+    } else {
+        int64_t np_host = 0;
+        RELCP_TRY(broadphase_cached(n, c->x.p, c->rb.p, c->rb_max, box0, cfg.skin, c->pa, c->pb, &np_host, c->bp, s));
+    }
     st.pair_list_rebuilt = c->bp.rebuilds != rebuilds_before;
-    const int64_t np = c->npairs;
-    st.n_pairs = np;
+    const int64_t PC = (n >= 2) ? c->bp.vn : 0;  // pair capacity and SoA stride
+    const int* npd = PC > 0 ? c->bp.vscan.p + PC : nullptr;  // device pair count
+    const int64_t np = PC;  // grid sizes and strides of the per-pair work
     int t_bp = tm.mark();
     const int64_t npa = np > 0 ? np : 1;
     RELCP_TRY(c->s0.ensure(10 * npa, s));
@@ -287,6 +316,7 @@ relcp_status step_once(relcp_ctx* c) {
         return RELCP_ERR_CAPACITY;
     }
     RELCP_TRY(grow_rows(c, npa));
+    if (npd) RELCP_CUDA(cudaMemcpyAsync(&ds->np, npd, sizeof(int), cudaMemcpyDeviceToDevice, s));
 
     auto snsd_out = [&](DBuf<double>& o, DBuf<int>& it) {
         SnsdOut so;
@@ -301,33 +331,31 @@ relcp_status step_once(relcp_ctx* c) {
 
     // C^k values a pair keeps from the previous step (the SNSD of its last
     // overlap test, evaluated at this very configuration, and the final gamma
-    // of its A_0 row); need[] marks the pairs still to evaluate, idx lists them
+    // of its A_0 row); idx lists the pairs still to evaluate
     RELCP_TRY(c->gamma0.ensure(npa, s));
-    RELCP_TRY(c->need.ensure(npa, s));
-    RELCP_TRY(c->needscan.ensure(npa + 1, s));
     RELCP_TRY(c->idx.ensure(npa, s));
     RELCP_TRY(c->rowof.ensure(npa, s));
     const bool memo_ok = c->memo_ok;
     c->memo_ok = false;  // set again once this step has saved its memo
-    const int* count_dev = c->needscan.p + np;
+    const int* count_dev = &ds->c0_evals;
     if (np > 0) {
         ReuseArgs ru{};
         ru.npairs = np;
+        ru.np_dev = npd;
         ru.pv = c->bp.pv.p;
         ru.memo = c->bp.memo.p;
         ru.stamp_prev = memo_ok ? c->stamp : -1;
         ru.reuse_snsd = c->snsd_ok && !(cfg.flags & RELCP_FLAG_NO_SNSD_REUSE);
         ru.use_gamma = !(cfg.flags & RELCP_FLAG_NO_WARM_START);
         ru.sprev = c->s1prev.p;
+        ru.sprev_stride = c->sprev_stride;
         ru.nprev = c->nprev;
         ru.s0 = c->s0.p;
         ru.it0 = c->it0.p;
         ru.gamma0 = c->gamma0.p;
-        ru.need = c->need.p;
+        ru.list = c->idx.p;
+        ru.count = &ds->c0_evals;  // zeroed with the rest of DevStep at the start of the step
         RELCP_TRY(reuse_launch(ru, s));
-        RELCP_TRY(exclusive_scan(c->need.p, c->needscan.p, np, c->scan, s));
-        RELCP_TRY(index_compact_launch(np, c->need.p, c->needscan.p, c->idx.p, s));
-        RELCP_CUDA(cudaMemcpyAsync(&ds->c0_evals, count_dev, sizeof(int), cudaMemcpyDeviceToDevice, s));
     }
 
     // SNSD at C^k for the listed pairs
@@ -397,14 +425,15 @@ relcp_status step_once(relcp_ctx* c) {
         r.q = c->r_q.p;
         r.qf = mixed ? c->r_qf.p : nullptr;
         r.diag = c->r_diag.p;
-        r.invd = mixed ? nullptr : c->r_invd.p;
-        r.invdf = mixed ? c->r_invdf.p : nullptr;
+        const bool jac = (cfg.flags & RELCP_FLAG_JACOBI) != 0;  // 1 / A_aa is only used by the Jacobi metric
+        r.invd = (!mixed && jac) ? c->r_invd.p : nullptr;
+        r.invdf = (mixed && jac) ? c->r_invdf.p : nullptr;
         r.gamma = mixed ? nullptr : c->r_gamma.p;
         r.gammaf = mixed ? c->r_gammaf.p : nullptr;
     };
     bind_rows(ra);
     if (np > 0) {
-        RELCP_TRY(flag_le_launch(np, c->s0.p, cfg.phi_skin, c->flags.p, s));
+        RELCP_TRY(flag_le_launch(np, npd, c->s0.p, cfg.phi_skin, c->flags.p, s));
         RELCP_TRY(exclusive_scan(c->flags.p, c->fscan.p, np, c->scan, s));
         RELCP_TRY(rows_launch(ra, s));
         RELCP_CUDA(cudaMemcpyAsync(&ds->nrows0, &ds->nrows, sizeof(int), cudaMemcpyDeviceToDevice, s));
@@ -470,7 +499,7 @@ relcp_status step_once(relcp_ctx* c) {
         RELCP_TRY(trial_launch(ta, s));
         SnsdArgs sb = sa;
         sb.idx = nullptr;
-        sb.count_dev = nullptr;
+        sb.count_dev = npd;
         sb.x = View<3, const double>::soa(c->xt.p, n);
         sb.P = View<6, const double>::soa(c->Pt.p, n);
         for (int k = 0; k < 3; ++k) sb.box[k] = box1[k];
@@ -491,9 +520,14 @@ relcp_status step_once(relcp_ctx* c) {
             RELCP_TRY(exclusive_scan(c->flags.p, c->fscan.p, np, c->scan, s));
             RELCP_CUDA(cudaMemcpyAsync(&nv, c->fscan.p + np, sizeof(int), cudaMemcpyDeviceToHost, s));
         }
+        // look-ahead for the next step: the cached list against these trial
+        // positions (accepted if the recursion stops here) in the next box
+        RELCP_CUDA(cudaMemsetAsync(&ds->la_dmax, 0, sizeof(unsigned long long), s));
+        RELCP_TRY(broadphase_lookahead(n, c->xt.p, box1, c->bp, &ds->la_dmax, s));
         RELCP_CUDA(cudaMemcpyAsync(&hs, ds, sizeof(DevStep), cudaMemcpyDeviceToHost, s));
         t_last = tm.mark();
         RELCP_CUDA(cudaStreamSynchronize(s));
+        c->npairs = hs.np;
         c->nrows = hs.nrows;
         if (depth == 0) c->nrows0 = hs.nrows;
         if (depth < RELCP_MAX_DEPTH_STATS) {
@@ -501,7 +535,7 @@ relcp_status step_once(relcp_ctx* c) {
             st.rows_per_rec[depth] = hs.nrows;
         }
         lcp_iters_total += (int)hs.lcp.iterations;
-        if (tm.on && hs.nrows > 0) {
+        if (tm.kernels && hs.nrows > 0) {
             st.ms_lcp_kernel += tm.ms(k0, k1);
             st.lcp_alg_bytes += lcp_bytes_per_iter(hs.nrows, n, mixed) * (hs.lcp.iterations + 1);
             st.lcp_launches += 1;
@@ -535,6 +569,7 @@ relcp_status step_once(relcp_ctx* c) {
     if (np > 0) {
         MemoSaveArgs ms{};
         ms.npairs = np;
+        ms.np_dev = npd;
         ms.pv = c->bp.pv.p;
         ms.rowof = c->rowof.p;
         ms.gamma = mixed ? nullptr : c->r_gamma.p;
@@ -544,10 +579,14 @@ relcp_status step_once(relcp_ctx* c) {
         RELCP_TRY(memo_save_launch(ms, s));
     }
     std::swap(c->s1, c->s1prev);
-    c->nprev = np;
+    c->sprev_stride = np;
+    c->nprev = hs.np;
     c->stamp = (c->stamp + 1) & 0x3fffffff;
     c->memo_ok = true;
     c->snsd_ok = true;
+    // the last look-ahead was taken at the configuration accepted below
+    c->la_ok = true;
+    c->la_rebuild = !verlet_bound_holds(c->bp, n, box1, c->rb_max, cfg.skin, __builtin_bit_cast(double, hs.la_dmax));
 
     // accept C^{k+1} (no synchronisation: the next call queues behind it)
     AcceptArgs aa{};
@@ -571,6 +610,7 @@ relcp_status step_once(relcp_ctx* c) {
     st.lcp_iters_total = lcp_iters_total;
     st.newton_iters_max = hs.newton_max;
     st.newton_iters_c0 = (int64_t)hs.iters0;
+    st.n_pairs = hs.np;
     st.snsd_c0_evaluated = hs.c0_evals;
     st.lcp_residual = hs.lcp.residual;
     st.max_overlap = __builtin_bit_cast(double, hs.maxov_bits);
@@ -581,7 +621,7 @@ relcp_status step_once(relcp_ctx* c) {
         for (size_t m = 0; m < snsd_marks.size(); ++m) {
             st.ms_snsd_kernel += tm.ms(snsd_marks[m].first, snsd_marks[m].second);
             st.snsd_launches += 1;
-            st.snsd_evals += m == 0 ? hs.c0_evals : np;  // the first launch is the C^k evaluation
+            st.snsd_evals += m == 0 ? hs.c0_evals : hs.np;  // the first launch is the C^k evaluation
         }
         st.ms_snsd = st.ms_snsd_kernel;
         for (auto& mk : lcp_marks) st.ms_lcp += tm.ms(mk.first, mk.second);
@@ -644,6 +684,7 @@ relcp_status relcp_set_config(relcp_ctx* c, const relcp_config* cfg) {
     for (int k = 0; k < 3; ++k)
         if (cfg->box[k] != c->box[k]) c->snsd_ok = false;
     if (cfg->precision != c->cfg.precision || cfg->skin != c->cfg.skin) c->snsd_ok = false;
+    c->la_ok = false;  // the broad phase checks its cached list again
     c->cfg = *cfg;
     for (int k = 0; k < 3; ++k) c->box[k] = cfg->box[k];
     return RELCP_OK;
@@ -720,6 +761,7 @@ relcp_status relcp_set_bodies(relcp_ctx* c, int64_t n, const int32_t* scene_offs
     }
     c->memo_ok = false;
     c->snsd_ok = false;
+    c->la_ok = false;
     c->bp.valid = false;
     c->rb_max = 0.0;
     for (size_t i = 0; i < ha.size(); ++i) c->rb_max = ha[i] > c->rb_max ? ha[i] : c->rb_max;
@@ -886,8 +928,6 @@ void relcp_destroy(relcp_ctx* c) {
     c->bp.dmax.release(s);
     c->s1prev.release(s);
     c->gamma0.release(s);
-    c->need.release(s);
-    c->needscan.release(s);
     c->idx.release(s);
     c->rowof.release(s);
     c->bp.memo.release(s);

@@ -380,10 +380,12 @@ relcp_status broadphase_cached(int64_t n, const double* x_soa, const double* rb,
             continue;
         }
         *npairs = total;
+        // pair buffers hold the whole cached list, so that later steps can
+        // compact into them without learning the count on the host
+        RELCP_TRY(pa.ensure((size_t)nva, s));
+        RELCP_TRY(pb.ensure((size_t)nva, s));
+        RELCP_TRY(sc.pv.ensure((size_t)nva, s));
         if (total > 0) {
-            RELCP_TRY(pa.ensure((size_t)total, s));
-            RELCP_TRY(pb.ensure((size_t)total, s));
-            RELCP_TRY(sc.pv.ensure((size_t)total, s));
             note_launch();
             compact_kernel<<<(unsigned)((nv + kThreads - 1) / kThreads), kThreads, 0, s>>>(nv, sc.vpa.p, sc.vpb.p,
                                                                                           sc.vflag.p, sc.vscan.p,
@@ -394,6 +396,57 @@ relcp_status broadphase_cached(int64_t n, const double* x_soa, const double* rb,
     }
     set_error("Verlet list rebuilt but the displacement bound still fails");
     return RELCP_ERR_CUDA;
+}
+
+}  // namespace relcp
+
+namespace relcp {
+
+bool verlet_bound_holds(const BroadphaseScratch& sc, int64_t n, const double box[3], double rbmax, double skin,
+                        double dmax) {
+    if (!sc.valid || sc.vn_bodies != n || sc.skin_b != skin) return false;
+    double smin = 1.0, grow = 0.0;
+    for (int k = 0; k < 3; ++k) {
+        if ((box[k] > 0) != (sc.Lb[k] > 0)) return false;
+        const double f = box[k] > 0 ? box[k] / sc.Lb[k] : 1.0;
+        smin = fmin(smin, f);
+        grow = fmax(grow, fabs(1.0 / f - 1.0));
+    }
+    const double cutmax = 2.0 * rbmax + skin;
+    return cutmax * grow + 2.0 * dmax / smin <= 0.9 * sc.delta;
+}
+
+relcp_status broadphase_lookahead(int64_t n, const double* x_soa, const double box[3], BroadphaseScratch& sc,
+                                  unsigned long long* dmax_dev, cudaStream_t s) {
+    if (!sc.valid || sc.vn_bodies != n || n < 2) return RELCP_OK;
+    double sfac[3];
+    for (int k = 0; k < 3; ++k) sfac[k] = (box[k] > 0 && sc.Lb[k] > 0) ? box[k] / sc.Lb[k] : 1.0;
+    note_launch();
+    disp_kernel<<<(unsigned)((n + kThreads - 1) / kThreads), kThreads, 0, s>>>(n, x_soa, sc.xb.p, sfac[0], sfac[1],
+                                                                                  sfac[2], box[0], box[1], box[2],
+                                                                                  dmax_dev);
+    RELCP_CUDA(cudaGetLastError());
+    return RELCP_OK;
+}
+
+relcp_status broadphase_filter_async(int64_t n, const double* x_soa, const double* rb, const double box[3],
+                                     double skin, DBuf<int>& pa, DBuf<int>& pb, BroadphaseScratch& sc,
+                                     cudaStream_t s) {
+    const int64_t nv = sc.vn;
+    if (n < 2 || nv == 0) return RELCP_OK;
+    View<3, const double> xv = View<3, const double>::soa(x_soa, n);
+    note_launch();
+    filter_kernel<<<(unsigned)((nv + kThreads - 1) / kThreads), kThreads, 0, s>>>(nv, sc.vpa.p, sc.vpb.p, xv, rb,
+                                                                                  box[0], box[1], box[2], skin,
+                                                                                  sc.vflag.p);
+    RELCP_CUDA(cudaGetLastError());
+    RELCP_TRY(exclusive_scan(sc.vflag.p, sc.vscan.p, nv, sc.scan, s));
+    note_launch();
+    compact_kernel<<<(unsigned)((nv + kThreads - 1) / kThreads), kThreads, 0, s>>>(nv, sc.vpa.p, sc.vpb.p,
+                                                                                  sc.vflag.p, sc.vscan.p, pa.p, pb.p,
+                                                                                  sc.pv.p);
+    RELCP_CUDA(cudaGetLastError());
+    return RELCP_OK;
 }
 
 }  // namespace relcp

@@ -236,6 +236,20 @@ relcp_status broadphase(int64_t n, View<3, const double> x, const double* rb, do
 relcp_status broadphase_cached(int64_t n, const double* x_soa, const double* rb, double rbmax, const double box[3],
                                double skin, DBuf<int>& pa, DBuf<int>& pb, int64_t* npairs, BroadphaseScratch& sc,
                                cudaStream_t s);
+// Whether the cached list is complete for positions whose largest displacement
+// since the build is dmax, in the box `box` (the bound of broadphase_cached).
+bool verlet_bound_holds(const BroadphaseScratch& sc, int64_t n, const double box[3], double rbmax, double skin,
+                        double dmax);
+// atomicMax of the bits of that displacement for positions x_soa in `box` into
+// *dmax_dev (zeroed by the caller); nothing when the cache is not valid
+relcp_status broadphase_lookahead(int64_t n, const double* x_soa, const double box[3], BroadphaseScratch& sc,
+                                  unsigned long long* dmax_dev, cudaStream_t s);
+// The cached list's exact filter and compaction without a host round trip:
+// pairs into pa, pb, sc.pv (capacity sc.vn), their count at sc.vscan.p[sc.vn].
+// Valid only when the bound held for these positions (checked beforehand).
+relcp_status broadphase_filter_async(int64_t n, const double* x_soa, const double* rb, const double box[3],
+                                     double skin, DBuf<int>& pa, DBuf<int>& pb, BroadphaseScratch& sc,
+                                     cudaStream_t s);
 
 // ---------------------------------------------------------------------------
 // SNSD (snsd.cu)

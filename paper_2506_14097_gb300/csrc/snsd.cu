@@ -37,6 +37,8 @@ __global__ void __launch_bounds__(kThreads) snsd_kernel(SnsdArgs a) {
     const int64_t count = a.count_dev ? (int64_t)*a.count_dev : a.npairs;
     double maxov = 0.0;
     int iters_out = 0;
+    // pairs past the count of a capacity-sized launch: no violation
+    if (a.viol && !a.idx && k_thr >= count && k_thr < a.npairs) a.viol[k_thr] = 0;
     if (k_thr < count) {
         const int64_t p = a.idx ? (int64_t)a.idx[k_thr] : k_thr;  // the pair
         const int64_t gk = k_thr;                                  // its start-normal slot

@@ -58,9 +58,10 @@ __global__ void prep_kernel(PrepArgs a) {
     for (int k = 0; k < 6; ++k) a.ufree[k * n + i] = b.ufree[k];
 }
 
-__global__ void flag_le_kernel(int64_t np, const double* __restrict__ phi, double thr, int* __restrict__ flags) {
+__global__ void flag_le_kernel(int64_t cap, const int* __restrict__ np_dev, const double* __restrict__ phi, double thr,
+                               int* __restrict__ flags) {
     int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (p < np) flags[p] = phi[p] <= thr ? 1 : 0;
+    if (p < cap) flags[p] = (p < *np_dev && phi[p] <= thr) ? 1 : 0;
 }
 
 __device__ __forceinline__ double body_rate(const double* U, int64_t n, int i, int j, const double* nn,
@@ -148,28 +149,33 @@ __global__ void rows_kernel(RowsArgs a) {
 
 __global__ void reuse_kernel(ReuseArgs a) {
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= a.npairs) return;
-    const PairMemo m = a.memo[a.pv[p]];
-    const bool hit = a.stamp_prev >= 0 && m.stamp == a.stamp_prev && m.pidx >= 0 && m.pidx < a.nprev;
-    a.gamma0[p] = (hit && a.use_gamma) ? m.gamma : 0.0;
-    const bool take = hit && a.reuse_snsd;
-    if (take) {
+    bool need = false;
+    if (p < a.npairs && p < *a.np_dev) {
+        const PairMemo m = a.memo[a.pv[p]];
+        const bool hit = a.stamp_prev >= 0 && m.stamp == a.stamp_prev && m.pidx >= 0 && m.pidx < a.nprev;
+        a.gamma0[p] = (hit && a.use_gamma) ? m.gamma : 0.0;
+        const bool take = hit && a.reuse_snsd;
+        if (take) {
 #pragma unroll
-        for (int k = 0; k < 10; ++k) a.s0[k * a.npairs + p] = a.sprev[k * a.nprev + m.pidx];
-        a.it0[p] = 0;
+            for (int k = 0; k < 10; ++k) a.s0[k * a.npairs + p] = a.sprev[k * a.sprev_stride + m.pidx];
+            a.it0[p] = 0;
+        }
+        need = !take;
     }
-    a.need[p] = take ? 0 : 1;
-}
-
-__global__ void index_compact_kernel(int64_t np, const int* __restrict__ flags, const int* __restrict__ scan,
-                                     int* __restrict__ idx) {
-    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (p < np && flags[p]) idx[scan[p]] = (int)p;
+    // warp-aggregated append to the list of pairs to evaluate
+    const unsigned mask = __ballot_sync(0xffffffffu, need);
+    if (mask) {
+        const int lane = threadIdx.x & 31, leader = __ffs(mask) - 1;
+        int base = 0;
+        if (lane == leader) base = atomicAdd(a.count, __popc(mask));
+        base = __shfl_sync(0xffffffffu, base, leader);
+        if (need) a.list[base + __popc(mask & ((1u << lane) - 1u))] = (int)p;
+    }
 }
 
 __global__ void memo_save_kernel(MemoSaveArgs a) {
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= a.npairs) return;
+    if (p >= a.npairs || p >= *a.np_dev) return;
     const int r = a.rowof[p];
     double g = 0.0;
     if (r >= 0) g = a.gamma ? a.gamma[r] : (double)a.gammaf[r];
@@ -232,10 +238,10 @@ relcp_status prep_launch(const PrepArgs& a, cudaStream_t s) {
     RELCP_CUDA(cudaGetLastError());
     return RELCP_OK;
 }
-relcp_status flag_le_launch(int64_t np, const double* phi, double thr, int* flags, cudaStream_t s) {
-    if (np == 0) return RELCP_OK;
+relcp_status flag_le_launch(int64_t cap, const int* np_dev, const double* phi, double thr, int* flags, cudaStream_t s) {
+    if (cap == 0) return RELCP_OK;
     note_launch();
-    flag_le_kernel<<<nb(np), kT, 0, s>>>(np, phi, thr, flags);
+    flag_le_kernel<<<nb(cap), kT, 0, s>>>(cap, np_dev, phi, thr, flags);
     RELCP_CUDA(cudaGetLastError());
     return RELCP_OK;
 }
@@ -264,13 +270,6 @@ relcp_status reuse_launch(const ReuseArgs& a, cudaStream_t s) {
     if (a.npairs == 0) return RELCP_OK;
     note_launch();
     reuse_kernel<<<nb(a.npairs), kT, 0, s>>>(a);
-    RELCP_CUDA(cudaGetLastError());
-    return RELCP_OK;
-}
-relcp_status index_compact_launch(int64_t np, const int* flags, const int* scan, int* idx, cudaStream_t s) {
-    if (np == 0) return RELCP_OK;
-    note_launch();
-    index_compact_kernel<<<nb(np), kT, 0, s>>>(np, flags, scan, idx);
     RELCP_CUDA(cudaGetLastError());
     return RELCP_OK;
 }

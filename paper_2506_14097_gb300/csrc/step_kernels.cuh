@@ -63,22 +63,27 @@ struct RowsArgs {
 // result of that step's last overlap test (same configuration) and the final
 // gamma of the pair's A_0 row; need[p] = 1 for the pairs still to evaluate
 struct ReuseArgs {
-    int64_t npairs;
+    int64_t npairs;         // capacity (SoA stride of s0, gamma0)
+    const int* np_dev;      // number of pairs (device)
     const int* pv;          // pair -> cached-list entry
     const PairMemo* memo;   // per entry
     int stamp_prev;         // stamp of the previous step (no memo matches a negative stamp)
     int reuse_snsd;
     int use_gamma;
-    const double* sprev;    // previous step's last trial SNSD output, 10 x nprev (SoA)
-    int64_t nprev;
+    const double* sprev;    // previous step's last trial SNSD output, 10 x sprev_stride (SoA)
+    int64_t sprev_stride;
+    int64_t nprev;          // pairs of the previous step
     double* s0;             // SNSD output at C^k, 10 x npairs (SoA)
     int* it0;               // Newton iterations at C^k (0 for reused pairs)
     double* gamma0;         // per pair
-    int* need;              // per pair
+    int* list;              // pairs to evaluate, in no particular order (each pair's result does not
+                            // depend on its position in the list)
+    int* count;             // their number (zeroed before the launch)
 };
 
 struct MemoSaveArgs {
-    int64_t npairs;
+    int64_t npairs;         // capacity
+    const int* np_dev;      // number of pairs (device)
     const int* pv;
     const int* rowof;
     const double* gamma;    // FP64 path or null
@@ -114,14 +119,13 @@ struct AcceptArgs {
 };
 
 relcp_status prep_launch(const PrepArgs& a, cudaStream_t s);
-relcp_status flag_le_launch(int64_t np, const double* phi, double thr, int* flags, cudaStream_t s);
+// flags[p] = (p < *np_dev && phi[p] <= thr) for p < cap (zeros past the count)
+relcp_status flag_le_launch(int64_t cap, const int* np_dev, const double* phi, double thr, int* flags, cudaStream_t s);
 relcp_status rows_launch(const RowsArgs& a, cudaStream_t s);
 relcp_status trial_launch(const TrialArgs& a, cudaStream_t s);
 relcp_status accept_launch(const AcceptArgs& a, cudaStream_t s);
 relcp_status wrap_launch(int64_t n, double* x, const double box[3], cudaStream_t s);
 relcp_status reuse_launch(const ReuseArgs& a, cudaStream_t s);
-// idx[scan[p]] = p for the flagged pairs
-relcp_status index_compact_launch(int64_t np, const int* flags, const int* scan, int* idx, cudaStream_t s);
 relcp_status memo_save_launch(const MemoSaveArgs& a, cudaStream_t s);
 
 }  // namespace relcp

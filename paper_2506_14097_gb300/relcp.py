@@ -37,6 +37,7 @@ RELCP_FLAG_PHASE_TIMING = 1
 RELCP_FLAG_NO_WARM_START = 2
 RELCP_FLAG_JACOBI = 4
 RELCP_FLAG_NO_SNSD_REUSE = 8
+RELCP_FLAG_LCP_TIMING = 16
 MAX_DEPTH_STATS = 64
 
 
