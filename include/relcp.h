@@ -141,6 +141,8 @@ typedef struct relcp_step_stats {
     int64_t newton_iters_c0;    /* Newton iterations summed over the pairs of the C^k evaluation */
     int64_t snsd_c0_evaluated;  /* pairs evaluated at C^k (the rest reused the previous step's last
                                    overlap test; see RELCP_FLAG_NO_SNSD_REUSE) */
+    double host_ms;             /* host time of the step call */
+    double host_wait_ms;        /* of which waiting for the device (stream synchronisations) */
 } relcp_step_stats;
 
 typedef struct relcp_ctx relcp_ctx;

@@ -11,6 +11,7 @@
 // The host reads three counts per recursion (pairs, rows, violators) to size
 // buffers and decide the loop; everything else stays on the device.
 #include <atomic>
+#include <chrono>
 #include <cstdarg>
 #include <cstring>
 #include <string>
@@ -66,6 +67,7 @@ struct DevStep {
     LcpDevResult lcp;   // iterations and residual of the last LCP
     int c0_evals;       // pairs evaluated at C^k (the others reused the previous step's values)
     int np;             // candidate pairs of the step
+    int nviol;          // violators of the last overlap test
     unsigned long long la_dmax;  // bits of the largest displacement of the trial positions since the list build
 };
 
@@ -84,6 +86,7 @@ struct relcp_ctx {
     DBuf<double> s0, s1;  // SNSD outputs at C^k and at the trial (10 x npairs)
     DBuf<int> it0, it1, flags, fscan;
     DBuf<DevStep> dstep;
+    DevStep* hstep = nullptr;  // pinned host copy (asynchronous readback)
     // rows (capacity rcap, SoA)
     int64_t nrows = 0, nrows0 = 0, rcap = 0;
     DBuf<int> r_ia, r_ib, r_rec, r_pair;
@@ -106,6 +109,7 @@ struct relcp_ctx {
     // whether the list must be rebuilt; with la_ok && !la_rebuild the broad
     // phase needs no host round trip
     bool la_ok = false, la_rebuild = true;
+    bool prepped = false;  // the last accept pass also ran the next step's prep
     int stamp = 0;         // stamp written by the last completed step
     bool memo_ok = false;  // memo and s1prev describe the current state
     bool snsd_ok = false;  // s1prev may stand in for the SNSD at C^k
@@ -235,6 +239,8 @@ struct PhaseTimer {
 };
 
 relcp_status step_once(relcp_ctx* c) {
+    const auto h0 = std::chrono::steady_clock::now();
+    double wait_ms = 0.0;
     cudaStream_t s = c->s;
     const relcp_config& cfg = c->cfg;
     const int64_t n = c->n;
@@ -278,7 +284,9 @@ relcp_status step_once(relcp_ctx* c) {
     }
     pa.rb = c->rb.p;
     pa.ufree = c->ufree.p;
-    RELCP_TRY(prep_launch(pa, s));
+    // the previous step's accept pass already prepared this state
+    if (!c->prepped) RELCP_TRY(prep_launch(pa, s));
+    c->prepped = false;
 
     // broad phase.  When the previous step's look-ahead showed the cached list
     // complete for these positions, the exact filter and compaction run with
@@ -496,6 +504,16 @@ relcp_status step_once(relcp_ctx* c) {
         ta.qt = c->qt.p;
         ta.Pt = c->Pt.p;
         ta.ustep = c->ustep.p;
+        // look-ahead for the next step, folded into the trial pass: the cached
+        // list against these trial positions (accepted if the recursion stops
+        // here) in the next box
+        RELCP_CUDA(cudaMemsetAsync(&ds->la_dmax, 0, sizeof(unsigned long long), s));
+        ta.xb = nullptr;
+        if (broadphase_lookahead_params(c->bp, n, box1, ta.sfac)) {
+            ta.xb = c->bp.xb.p;
+            for (int k = 0; k < 3; ++k) ta.la_box[k] = box1[k];
+            ta.la_dmax = &ds->la_dmax;
+        }
         RELCP_TRY(trial_launch(ta, s));
         SnsdArgs sb = sa;
         sb.idx = nullptr;
@@ -515,18 +533,19 @@ relcp_status step_once(relcp_ctx* c) {
             RELCP_TRY(snsd_launch(sb, s));
             snsd_marks.push_back({e0, tm.mark()});
         }
-        int nv = 0;
         if (np > 0) {
             RELCP_TRY(exclusive_scan(c->flags.p, c->fscan.p, np, c->scan, s));
-            RELCP_CUDA(cudaMemcpyAsync(&nv, c->fscan.p + np, sizeof(int), cudaMemcpyDeviceToHost, s));
+            RELCP_CUDA(cudaMemcpyAsync(&ds->nviol, c->fscan.p + np, sizeof(int), cudaMemcpyDeviceToDevice, s));
         }
-        // look-ahead for the next step: the cached list against these trial
-        // positions (accepted if the recursion stops here) in the next box
-        RELCP_CUDA(cudaMemsetAsync(&ds->la_dmax, 0, sizeof(unsigned long long), s));
-        RELCP_TRY(broadphase_lookahead(n, c->xt.p, box1, c->bp, &ds->la_dmax, s));
-        RELCP_CUDA(cudaMemcpyAsync(&hs, ds, sizeof(DevStep), cudaMemcpyDeviceToHost, s));
+        RELCP_CUDA(cudaMemcpyAsync(c->hstep, ds, sizeof(DevStep), cudaMemcpyDeviceToHost, s));
         t_last = tm.mark();
-        RELCP_CUDA(cudaStreamSynchronize(s));
+        {
+            const auto w0 = std::chrono::steady_clock::now();
+            RELCP_CUDA(cudaStreamSynchronize(s));
+            wait_ms += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - w0).count();
+        }
+        hs = *c->hstep;
+        const int nv = np > 0 ? hs.nviol : 0;
         c->npairs = hs.np;
         c->nrows = hs.nrows;
         if (depth == 0) c->nrows0 = hs.nrows;
@@ -599,7 +618,11 @@ relcp_status step_once(relcp_ctx* c) {
     aa.x = c->x.p;
     aa.q = c->q.p;
     aa.vel = c->vel.p;
+    // the next step's prep in the same pass, on the accepted state in the next box
+    aa.next = pa;
+    for (int k = 0; k < 3; ++k) aa.next.box[k] = box1[k];
     RELCP_TRY(accept_launch(aa, s));
+    c->prepped = true;
     for (int k = 0; k < 3; ++k) c->box[k] = box1[k];
     relcp_status dstat = status_from_device(hs.status);
     if (step_status == RELCP_OK) step_status = dstat;
@@ -630,6 +653,8 @@ relcp_status step_once(relcp_ctx* c) {
     tm.stop();
     c->steps_done += 1;
     st.steps_done = c->steps_done;
+    st.host_wait_ms = wait_ms;
+    st.host_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - h0).count();
     c->stats = st;
     return step_status;
 }
@@ -669,7 +694,16 @@ relcp_status relcp_create(const relcp_config* cfg, void* cuda_stream, relcp_ctx*
     c->s = (cudaStream_t)cuda_stream;
     for (int k = 0; k < 3; ++k) c->box[k] = cfg->box[k];
     relcp_status st = c->dstep.ensure(1, c->s);
+    if (st == RELCP_OK && cudaMallocHost((void**)&c->hstep, sizeof(DevStep)) != cudaSuccess) {
+        set_error("pinned allocation failed");
+        st = RELCP_ERR_CUDA;
+    }
+    if (st == RELCP_OK) {
+        // the context's prefix sums report a look-back timeout in the step's status word
+        c->scan.status = c->bp.scan.status = c->lcp.scan.status = &c->dstep.p->status;
+    }
     if (st != RELCP_OK) {
+        c->dstep.release(c->s);
         delete c;
         return st;
     }
@@ -685,6 +719,7 @@ relcp_status relcp_set_config(relcp_ctx* c, const relcp_config* cfg) {
         if (cfg->box[k] != c->box[k]) c->snsd_ok = false;
     if (cfg->precision != c->cfg.precision || cfg->skin != c->cfg.skin) c->snsd_ok = false;
     c->la_ok = false;  // the broad phase checks its cached list again
+    c->prepped = false;
     c->cfg = *cfg;
     for (int k = 0; k < 3; ++k) c->box[k] = cfg->box[k];
     return RELCP_OK;
@@ -762,6 +797,7 @@ relcp_status relcp_set_bodies(relcp_ctx* c, int64_t n, const int32_t* scene_offs
     c->memo_ok = false;
     c->snsd_ok = false;
     c->la_ok = false;
+    c->prepped = false;
     c->bp.valid = false;
     c->rb_max = 0.0;
     for (size_t i = 0; i < ha.size(); ++i) c->rb_max = ha[i] > c->rb_max ? ha[i] : c->rb_max;
@@ -914,8 +950,7 @@ void relcp_destroy(relcp_ctx* c) {
     for (auto* b : dbs) b->release(s);
     DBuf<int>* ibs[] = {&c->pa, &c->pb, &c->it0, &c->it1, &c->flags, &c->fscan, &c->r_ia, &c->r_ib, &c->r_rec,
                         &c->r_pair, &c->bp.cell_of, &c->bp.cell_count, &c->bp.cell_start, &c->bp.cell_cursor,
-                        &c->bp.cell_body, &c->bp.pair_count, &c->bp.pair_off, &c->bp.scan.partial,
-                        &c->scan.partial, &c->bp.vpa, &c->bp.vpb, &c->bp.vflag, &c->bp.vscan};
+                        &c->bp.cell_body, &c->bp.pair_count, &c->bp.pair_off, &c->bp.vpa, &c->bp.vpb, &c->bp.vflag, &c->bp.vscan};
     for (auto* b : ibs) b->release(s);
     c->r_geomf.release(s);
     c->r_gammaf.release(s);
@@ -936,9 +971,12 @@ void relcp_destroy(relcp_ctx* c) {
     c->bp.vpb_old.release(s);
     c->bp.pv.release(s);
     release(c->lcp, s);
+    release(c->scan, s);
+    release(c->bp.scan, s);
     mlp_release(c->mlp, s);
     cudaStreamSynchronize(s);
     for (cudaEvent_t e : c->events) cudaEventDestroy(e);
+    if (c->hstep) cudaFreeHost(c->hstep);
     delete c;
 }
 
@@ -954,6 +992,7 @@ relcp_status relcp_broadphase(int64_t n, const double* x, const double* rb, cons
     DBuf<int> pa, pb;
     int64_t np = 0;
     relcp_status st = broadphase(n, View<3, const double>::aos(x, 3), rb, 0.0, box3, skin, pa, pb, &np, sc, s);
+    if (st == RELCP_OK) st = scan_error(sc.scan, s);
     *n_out = np;
     if (st == RELCP_OK && np > cap) st = RELCP_ERR_CAPACITY;
     if (st == RELCP_OK && np > 0) {
@@ -967,8 +1006,9 @@ relcp_status relcp_broadphase(int64_t n, const double* x, const double* rb, cons
         }
     }
     DBuf<int>* bufs[] = {&pa, &pb, &sc.cell_of, &sc.cell_count, &sc.cell_start, &sc.cell_cursor, &sc.cell_body,
-                         &sc.pair_count, &sc.pair_off, &sc.scan.partial};
+                         &sc.pair_count, &sc.pair_off};
     for (auto* b : bufs) b->release(s);
+    release(sc.scan, s);
     if (cudaStreamSynchronize(s) != cudaSuccess && st == RELCP_OK) st = RELCP_ERR_CUDA;
     return st;
 }
@@ -1136,6 +1176,7 @@ relcp_status relcp_lcp_solve(int64_t nrows, int64_t nbodies, const int32_t* ia, 
         pr.result = res.p;
         pr.status = dst.p;
         pr.ev_before = pr.ev_after = nullptr;
+        sc.scan.status = dst.p;  // a prefix-sum timeout is reported like the solver's own
         int blocks = 0;
         float kms = 0.f;
         if (fail(lcp_solve(pr, sc, &blocks, &kms, s))) break;

@@ -280,6 +280,10 @@ relcp_status broadphase(int64_t n, View<3, const double> x, const double* rb, do
     int total = 0;
     RELCP_CUDA(cudaMemcpyAsync(&total, sc.pair_off.p + n, sizeof(int), cudaMemcpyDeviceToHost, s));
     RELCP_CUDA(cudaStreamSynchronize(s));
+    if (total < 0 || (int64_t)total > n * (n - 1) / 2) {
+        set_error("broad phase: inconsistent pair count %d", total);
+        return RELCP_ERR_TIMEOUT;
+    }
     *npairs = total;
     if (total == 0) return RELCP_OK;
     RELCP_TRY(pa.ensure((size_t)total, s));
@@ -414,6 +418,12 @@ bool verlet_bound_holds(const BroadphaseScratch& sc, int64_t n, const double box
     }
     const double cutmax = 2.0 * rbmax + skin;
     return cutmax * grow + 2.0 * dmax / smin <= 0.9 * sc.delta;
+}
+
+bool broadphase_lookahead_params(const BroadphaseScratch& sc, int64_t n, const double box[3], double sfac[3]) {
+    if (!sc.valid || sc.vn_bodies != n || n < 2) return false;
+    for (int k = 0; k < 3; ++k) sfac[k] = (box[k] > 0 && sc.Lb[k] > 0) ? box[k] / sc.Lb[k] : 1.0;
+    return true;
 }
 
 relcp_status broadphase_lookahead(int64_t n, const double* x_soa, const double box[3], BroadphaseScratch& sc,

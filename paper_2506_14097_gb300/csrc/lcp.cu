@@ -872,7 +872,7 @@ void release(LcpScratch& sc, cudaStream_t s) {
     sc.packd.release(s);
     sc.packf.release(s);
     sc.partials.release(s);
-    sc.scan.partial.release(s);
+    release(sc.scan, s);
 }
 
 }  // namespace relcp

@@ -188,10 +188,19 @@ __device__ __forceinline__ bool near_pair_exact(double xi0, double xi1, double x
 // device-wide exclusive scan (int32) and helpers (scan.cu)
 // ---------------------------------------------------------------------------
 struct ScanScratch {
-    DBuf<int> partial;
+    DBuf<unsigned long long> tiles;  // per-tile look-back words (left cleared by every call)
+    DBuf<int> ctr;                   // ticket, finished blocks, own error word
+    int* status = nullptr;           // DEV_TIMEOUT goes here if set (else into ctr[2])
 };
 // out[i] = sum_{j<i} in[i]; out[n] = total.  `out` has n+1 entries.
 relcp_status exclusive_scan(const int* in, int* out, int64_t n, ScanScratch& sc, cudaStream_t s);
+// RELCP_ERR_TIMEOUT if a scan on this scratch (without a status word) timed
+// out; synchronises s
+relcp_status scan_error(ScanScratch& sc, cudaStream_t s);
+inline void release(ScanScratch& sc, cudaStream_t s) {
+    sc.tiles.release(s);
+    sc.ctr.release(s);
+}
 
 // ---------------------------------------------------------------------------
 // broad phase (broadphase.cu)
@@ -244,6 +253,9 @@ bool verlet_bound_holds(const BroadphaseScratch& sc, int64_t n, const double box
 // *dmax_dev (zeroed by the caller); nothing when the cache is not valid
 relcp_status broadphase_lookahead(int64_t n, const double* x_soa, const double box[3], BroadphaseScratch& sc,
                                   unsigned long long* dmax_dev, cudaStream_t s);
+// the scale factors of that check (false: no valid cached list), for kernels
+// that fold the check into their own pass over the bodies
+bool broadphase_lookahead_params(const BroadphaseScratch& sc, int64_t n, const double box[3], double sfac[3]);
 // The cached list's exact filter and compaction without a host round trip:
 // pairs into pa, pb, sc.pv (capacity sc.vn), their count at sc.vscan.p[sc.vn].
 // Valid only when the bound held for these positions (checked beforehand).

@@ -1,18 +1,29 @@
-// Device-wide exclusive prefix sum of int32 counts (two passes: tile sums,
-// then a tile scan in which every block first adds up the sums of the tiles
-// before it -- one load per thread -- so no separate pass scans the tile sums).  Used to turn
-// per-item counts or 0/1 flags into output positions (pair lists, constraint
-// compaction, incidence CSR) without atomics, so that every list the library
-// builds has a deterministic order.
+// Device-wide exclusive prefix sum of int32 counts in ONE pass (decoupled
+// look-back).  Used to turn per-item counts or 0/1 flags into output positions
+// (pair lists, constraint compaction, incidence CSR) without atomics on the
+// positions, so that every list the library builds has a deterministic order.
+//
+// Each block takes a tile ticket from a counter, so tile t is only ever
+// processed by a block that started after the blocks of tiles 0..t-1: those
+// are resident and never wait on later tiles, hence every wait below ends.
+// A tile publishes its aggregate, then its inclusive prefix, as one 64-bit
+// word (status in the high half, value in the low half); thread 0 walks back
+// over the predecessors, adding aggregates until it meets an inclusive prefix.
+// The spin on a predecessor is bounded: past the limit the block records
+// DEV_TIMEOUT in the caller's status word (or the scratch's own) and goes on.
+// The last block to finish clears the tile words and the counters, so the next
+// call needs no memset (and the launch can be replayed inside a CUDA graph).
 #include "relcp_internal.cuh"
 
 namespace relcp {
 
 namespace {
 
-constexpr int kScanThreads = 1024;
-constexpr int kScanItems = 4;
+constexpr int kScanThreads = 256;
+constexpr int kScanItems = 8;
 constexpr int kTile = kScanThreads * kScanItems;
+constexpr long long kLookbackLimit = 1ll << 22;
+constexpr unsigned long long kAggregate = 1ull << 32, kInclusive = 2ull << 32;
 
 // inclusive scan of one value per thread across the block; returns the
 // inclusive prefix, *total gets the block total
@@ -44,26 +55,25 @@ __device__ int block_inclusive_scan(int v, int* total) {
     return r;
 }
 
-__global__ void tile_sums(const int* __restrict__ in, int64_t n, int* __restrict__ partial) {
-    int64_t base = (int64_t)blockIdx.x * kTile + (int64_t)threadIdx.x * kScanItems;
-    int s = 0;
-#pragma unroll
-    for (int k = 0; k < kScanItems; ++k)
-        if (base + k < n) s += in[base + k];
-    int tot;
-    block_inclusive_scan(s, &tot);
-    if (threadIdx.x == 0) partial[blockIdx.x] = tot;
+__device__ __forceinline__ void st_relaxed64(unsigned long long* p, unsigned long long v) {
+    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ unsigned long long ld_relaxed64(const unsigned long long* p) {
+    unsigned long long v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
 }
 
-// tile scan plus offset; the offset of tile t is the sum of tile sums 0..t-1,
-// reduced by this block; the last block writes the total to out[n]
-__global__ void tile_scan(const int* __restrict__ in, int64_t n, const int* __restrict__ partial,
-                          int* __restrict__ out) {
-    int before = 0;
-    for (int t = threadIdx.x; t < (int)blockIdx.x; t += blockDim.x) before += partial[t];
-    int offset;
-    block_inclusive_scan(before, &offset);
-    int64_t base = (int64_t)blockIdx.x * kTile + (int64_t)threadIdx.x * kScanItems;
+// ctr[0]: tile ticket, ctr[1]: finished blocks
+__global__ void __launch_bounds__(kScanThreads) scan_lookback_kernel(const int* __restrict__ in, int64_t n,
+                                                                     int* __restrict__ out,
+                                                                     unsigned long long* tiles, int* ctr,
+                                                                     int* status) {
+    __shared__ int sh_tile, sh_excl;
+    if (threadIdx.x == 0) sh_tile = atomicAdd(&ctr[0], 1);
+    __syncthreads();
+    const int t = sh_tile;
+    const int64_t base = (int64_t)t * kTile + (int64_t)threadIdx.x * kScanItems;
     int v[kScanItems];
     int s = 0;
 #pragma unroll
@@ -72,14 +82,52 @@ __global__ void tile_scan(const int* __restrict__ in, int64_t n, const int* __re
         s += v[k];
     }
     int tot;
-    int inc = block_inclusive_scan(s, &tot);
-    int run = offset + inc - s;
+    const int inc = block_inclusive_scan(s, &tot);
+    if (threadIdx.x == 0) {
+        int excl = 0;
+        if (t == 0) {
+            st_relaxed64(tiles, kInclusive | (unsigned)tot);
+        } else {
+            st_relaxed64(tiles + t, kAggregate | (unsigned)tot);
+            long long spins = 0;
+            for (int j = t - 1; j >= 0;) {
+                const unsigned long long w = ld_relaxed64(tiles + j);
+                const unsigned long long st = w & (3ull << 32);
+                if (st == 0) {
+                    if (++spins > kLookbackLimit) {
+                        atomicOr(status, DEV_TIMEOUT);
+                        break;
+                    }
+                    if (spins > 64) __nanosleep(32);
+                    continue;
+                }
+                excl += (int)(unsigned)(w & 0xffffffffull);
+                if (st == kInclusive) break;
+                --j;
+            }
+            st_relaxed64(tiles + t, kInclusive | (unsigned)(excl + tot));
+        }
+        sh_excl = excl;
+    }
+    __syncthreads();
+    int run = sh_excl + inc - s;
 #pragma unroll
     for (int k = 0; k < kScanItems; ++k) {
         if (base + k < n) out[base + k] = run;
         run += v[k];
     }
-    if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) out[n] = offset + tot;
+    if (t == (int)gridDim.x - 1 && threadIdx.x == 0) out[n] = sh_excl + tot;
+    // the last block to finish clears the tiles and counters for the next call
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        if (atomicAdd(&ctr[1], 1) == (int)gridDim.x - 1) {
+            for (unsigned j = 0; j < gridDim.x; ++j) st_relaxed64(tiles + j, 0ull);
+            ctr[0] = 0;
+            ctr[1] = 0;
+            __threadfence();
+        }
+    }
 }
 
 }  // namespace
@@ -90,14 +138,31 @@ relcp_status exclusive_scan(const int* in, int* out, int64_t n, ScanScratch& sc,
         RELCP_CUDA(cudaMemsetAsync(out, 0, sizeof(int), s));
         return RELCP_OK;
     }
-    const int64_t nparts = (n + kTile - 1) / kTile;
-    RELCP_TRY(sc.partial.ensure((size_t)nparts, s));
+    const int64_t ntiles = (n + kTile - 1) / kTile;
+    if (ntiles > (int64_t)1 << 30) return RELCP_ERR_INVALID_ARG;
+    if (sc.tiles.cap < (size_t)ntiles || !sc.ctr.p) {
+        // fresh words must start cleared; afterwards every call leaves them cleared
+        RELCP_TRY(sc.tiles.ensure((size_t)ntiles, s));
+        RELCP_TRY(sc.ctr.ensure(4, s));
+        RELCP_CUDA(cudaMemsetAsync(sc.tiles.p, 0, sc.tiles.cap * sizeof(unsigned long long), s));
+        RELCP_CUDA(cudaMemsetAsync(sc.ctr.p, 0, 4 * sizeof(int), s));
+    }
+    int* status = sc.status ? sc.status : sc.ctr.p + 2;  // ctr[2]: the scratch's own error word
     note_launch();
-    tile_sums<<<(unsigned)nparts, kScanThreads, 0, s>>>(in, n, sc.partial.p);
+    scan_lookback_kernel<<<(unsigned)ntiles, kScanThreads, 0, s>>>(in, n, out, sc.tiles.p, sc.ctr.p, status);
     RELCP_CUDA(cudaGetLastError());
-    note_launch();
-    tile_scan<<<(unsigned)nparts, kScanThreads, 0, s>>>(in, n, sc.partial.p, out);
-    RELCP_CUDA(cudaGetLastError());
+    return RELCP_OK;
+}
+
+relcp_status scan_error(ScanScratch& sc, cudaStream_t s) {
+    if (sc.status || !sc.ctr.p) return RELCP_OK;
+    int bits = 0;
+    RELCP_CUDA(cudaMemcpyAsync(&bits, sc.ctr.p + 2, sizeof(int), cudaMemcpyDeviceToHost, s));
+    RELCP_CUDA(cudaStreamSynchronize(s));
+    if (bits & DEV_TIMEOUT) {
+        set_error("prefix-sum look-back timed out");
+        return RELCP_ERR_TIMEOUT;
+    }
     return RELCP_OK;
 }
 

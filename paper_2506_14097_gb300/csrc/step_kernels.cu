@@ -28,9 +28,7 @@ namespace {
 constexpr int kT = 256;
 inline unsigned nb(int64_t n) { return (unsigned)((n + kT - 1) / kT); }
 
-__global__ void prep_kernel(PrepArgs a) {
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= a.n) return;
+__device__ __forceinline__ void prep_one(const PrepArgs& a, int64_t i) {
     const int64_t n = a.n;
     double qin[4], ax[3], vel[6], f[6], x[3];
     for (int k = 0; k < 4; ++k) qin[k] = a.q[k * n + i];
@@ -56,6 +54,11 @@ __global__ void prep_kernel(PrepArgs a) {
     if (a.Kf)
         for (int k = 0; k < 7; ++k) a.Kf[k * n + i] = (float)b.K[k];
     for (int k = 0; k < 6; ++k) a.ufree[k * n + i] = b.ufree[k];
+}
+
+__global__ void prep_kernel(PrepArgs a) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < a.n) prep_one(a, i);
 }
 
 __global__ void flag_le_kernel(int64_t cap, const int* __restrict__ np_dev, const double* __restrict__ phi, double thr,
@@ -188,7 +191,8 @@ __global__ void memo_save_kernel(MemoSaveArgs a) {
 
 __global__ void trial_kernel(TrialArgs a) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= a.n) return;
+    double dlen = 0.0;  // look-ahead displacement of this body
+    if (i < a.n) {
     const int64_t n = a.n;
     double U[6], x[3], q[4], ax[3], xt[3], qt[4];
     for (int k = 0; k < 6; ++k) {
@@ -210,6 +214,20 @@ __global__ void trial_kernel(TrialArgs a) {
     a.Pt[3 * n + i] = P.xy;
     a.Pt[4 * n + i] = P.xz;
     a.Pt[5 * n + i] = P.yz;
+    if (a.xb) {
+        // the same arithmetic as the broad phase's displacement check
+        double d2 = 0.0;
+        for (int k = 0; k < 3; ++k) {
+            const double d = min_image(xt[k] - a.sfac[k] * a.xb[k * n + i], a.la_box[k]);
+            d2 += d * d;
+        }
+        dlen = sqrt(d2);
+    }
+    }
+    if (a.xb) {
+        for (int o = 16; o > 0; o >>= 1) dlen = fmax(dlen, __shfl_xor_sync(0xffffffffu, dlen, o));
+        if ((threadIdx.x & 31) == 0 && dlen > 0.0) atomicMax(a.la_dmax, (unsigned long long)__double_as_longlong(dlen));
+    }
 }
 
 __global__ void accept_kernel(AcceptArgs a) {
@@ -220,6 +238,7 @@ __global__ void accept_kernel(AcceptArgs a) {
     for (int k = 0; k < 4; ++k) a.q[k * n + i] = a.qt[k * n + i];
     if (a.inertial)
         for (int k = 0; k < 6; ++k) a.vel[k * n + i] = a.ustep[k * n + i];
+    if (a.next.n == n) prep_one(a.next, i);  // reads back this thread's own writes
 }
 
 __global__ void wrap_kernel(int64_t n, double* x, double L0, double L1, double L2) {

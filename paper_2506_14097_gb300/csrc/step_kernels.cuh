@@ -95,6 +95,11 @@ struct MemoSaveArgs {
 struct TrialArgs {
     int64_t n;
     double dt;
+    // optional look-ahead of the cached pair list (xb == nullptr: none): the
+    // largest |min_image(x_t - sfac xb)| in box `la_box`, atomicMax of its bits
+    const double* xb;
+    double sfac[3], la_box[3];
+    unsigned long long* la_dmax;
     const double* x;
     const double* q;
     const double* axes;
@@ -110,6 +115,9 @@ struct AcceptArgs {
     int64_t n;
     int inertial;
     double box[3];
+    // optional: the next step's prep on the accepted state, in the same pass
+    // (next.n == 0: none)
+    PrepArgs next;
     const double* xt;
     const double* qt;
     const double* ustep;

@@ -59,7 +59,8 @@ class relcp_step_stats(ctypes.Structure):
                 ("newton_fallbacks", c_int32), ("ms_lcp_kernel", c_double), ("lcp_alg_bytes", c_double),
                 ("ms_snsd_kernel", c_double), ("snsd_evals", c_int64), ("lcp_launches", c_int32),
                 ("snsd_launches", c_int32), ("pair_list_rebuilt", c_int32), ("pad0", c_int32),
-                ("newton_iters_c0", c_int64), ("snsd_c0_evaluated", c_int64)]
+                ("newton_iters_c0", c_int64), ("snsd_c0_evaluated", c_int64),
+                ("host_ms", c_double), ("host_wait_ms", c_double)]
 
 
 class relcp_lcp_info(ctypes.Structure):
