@@ -62,13 +62,15 @@ struct DevStep {
     int status;         // DEV_* bits
     int newton_max;     // largest Newton iteration count
     int nrows0;         // |A_0| (copied from nrows after the first LCP)
-    unsigned long long maxov_bits;  // bits of the largest overlap at the last trial
     unsigned long long iters0;      // Newton iterations summed over the pairs at C^k
     LcpDevResult lcp;   // iterations and residual of the last LCP
     int c0_evals;       // pairs evaluated at C^k (the others reused the previous step's values)
     int np;             // candidate pairs of the step
-    int nviol;          // violators of the last overlap test
-    unsigned long long la_dmax;  // bits of the largest displacement of the trial positions since the list build
+    // per recursion level (cleared together before each trial)
+    unsigned long long maxov_bits;  // bits of the largest overlap at the last trial
+    unsigned long long la_dmax;     // bits of the largest displacement of the trial positions since the list build
+    int nviol;                      // violators of the last overlap test
+    int pad;
 };
 
 struct relcp_ctx {
@@ -507,7 +509,8 @@ relcp_status step_once(relcp_ctx* c) {
         // look-ahead for the next step, folded into the trial pass: the cached
         // list against these trial positions (accepted if the recursion stops
         // here) in the next box
-        RELCP_CUDA(cudaMemsetAsync(&ds->la_dmax, 0, sizeof(unsigned long long), s));
+        // the per-level fields (largest overlap, look-ahead displacement, violator count)
+        RELCP_CUDA(cudaMemsetAsync(&ds->maxov_bits, 0, 2 * sizeof(unsigned long long) + 2 * sizeof(int), s));
         ta.xb = nullptr;
         if (broadphase_lookahead_params(c->bp, n, box1, ta.sfac)) {
             ta.xb = c->bp.xb.p;
@@ -526,16 +529,12 @@ relcp_status step_once(relcp_ctx* c) {
         sb.eps = cfg.eps_ncp;
         sb.viol = c->flags.p;
         sb.maxov_bits = &ds->maxov_bits;
+        sb.nviol = &ds->nviol;
         sb.iters_sum = nullptr;
-        RELCP_CUDA(cudaMemsetAsync(&ds->maxov_bits, 0, sizeof(unsigned long long), s));
         {
             int e0 = tm.mark();
             RELCP_TRY(snsd_launch(sb, s));
             snsd_marks.push_back({e0, tm.mark()});
-        }
-        if (np > 0) {
-            RELCP_TRY(exclusive_scan(c->flags.p, c->fscan.p, np, c->scan, s));
-            RELCP_CUDA(cudaMemcpyAsync(&ds->nviol, c->fscan.p + np, sizeof(int), cudaMemcpyDeviceToDevice, s));
         }
         RELCP_CUDA(cudaMemcpyAsync(c->hstep, ds, sizeof(DevStep), cudaMemcpyDeviceToHost, s));
         t_last = tm.mark();
@@ -570,6 +569,8 @@ relcp_status step_once(relcp_ctx* c) {
             break;
         }
         ++depth;
+        // positions of the appended rows (the violator flags of the last test)
+        RELCP_TRY(exclusive_scan(c->flags.p, c->fscan.p, np, c->scan, s));
         RELCP_TRY(grow_rows(c, c->nrows + nv));
         RowsArgs rb2 = ra;
         rb2.gamma0 = nullptr;

@@ -12,11 +12,14 @@
 //              frame, scaled by RELCP_MLP_CORR_SCALE), Phi / s, and a trust
 //              logit (positive: the corrected seed is the Newton start; else
 //              the cold start is used).
-// Inference is one fused kernel: the four weight matrices live in shared
-// memory (BF16, row = output unit), each warp carries 16 pairs through all four
-// layers in registers -- the FP32 accumulator fragment of one layer is exactly
-// the A-operand fragment of the next (same rows, same columns per thread), so
-// activations never leave the registers.
+// Inference: the four weight matrices live in shared memory (BF16, row =
+// output unit, packed once per parameter set and bulk-copied in per CTA), each
+// warp carries 16 pairs through all four layers in registers -- the FP32
+// accumulator fragment of one layer is exactly the A-operand fragment of the
+// next (same rows, same columns per thread), so activations never leave the
+// registers.  Inside a step one kernel does the whole start for a list of
+// pairs (features, network, rotated normal); relcp_mlp_forward runs the
+// network alone on given features.
 // Training is layer by layer with a generic tensor-core GEMM
 // C = A B^T (both operands K-contiguous BF16), transposes, the loss, bias sums
 // and Adam (Kingma & Ba) on FP32 master parameters.
@@ -59,10 +62,7 @@ __device__ __forceinline__ void mma_bf16(float c[4], const uint32_t a[4], uint32
 // features (FP64 runs at a small fraction of the FP32 rate on this part).  The
 // minimum image of the centres is always taken in FP64 (exact, like the SNSD).
 template <class T>
-__global__ void features_kernel(MlpFeatArgs a) {
-    const int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (row >= (a.count_dev ? (int64_t)*a.count_dev : a.npairs)) return;
-    const int64_t p = a.idx ? (int64_t)a.idx[row] : row;
+__device__ void compute_features(const MlpFeatArgs& a, int64_t row, int64_t p, float* f, float* targ) {
     const int i = a.pa[p * a.pstride], j = a.pb[p * a.pstride];
     T d[3];
     for (int k = 0; k < 3; ++k) d[k] = (T)min_image(a.x(k, j) - a.x(k, i), a.box[k]);
@@ -85,7 +85,6 @@ __global__ void features_kernel(MlpFeatArgs a) {
     const T aa[3] = {(T)a.axes(0, i), (T)a.axes(1, i), (T)a.axes(2, i)};
     const T ab[3] = {(T)a.axes(0, j), (T)a.axes(1, j), (T)a.axes(2, j)};
     const T sc = fmax(aa[0], fmax(aa[1], aa[2])) + fmax(ab[0], fmax(ab[1], ab[2]));
-    float* f = a.feat + 16 * row;
     for (int k = 0; k < 3; ++k) f[k] = (float)((R[k] * d[0] + R[3 + k] * d[1] + R[6 + k] * d[2]) / sc);
     // q_rel = conj(q_a) (x) q_b
     const T s1 = qa[0], x1 = -qa[1], y1 = -qa[2], z1 = -qa[3];
@@ -122,14 +121,22 @@ __global__ void features_kernel(MlpFeatArgs a) {
         for (int k = 0; k < 3; ++k) sd[k] = (R[k] * w[0] + R[3 + k] * w[1] + R[6 + k] * w[2]) / lw;
     }
     for (int k = 0; k < 3; ++k) f[13 + k] = (float)sd[k];
-    if (a.targets && a.snsd) {
+    if (targ && a.snsd) {
         const double* o = a.snsd + p * a.snsd_s;
         const T n[3] = {(T)o[1 * a.snsd_c], (T)o[2 * a.snsd_c], (T)o[3 * a.snsd_c]};
-        float* t = a.targets + 4 * row;
+        float* t = targ;
         for (int k = 0; k < 3; ++k)
             t[k] = (float)(T(RELCP_MLP_CORR_SCALE) * ((R[k] * n[0] + R[3 + k] * n[1] + R[6 + k] * n[2]) - sd[k]));
         t[3] = (float)((T)o[0] / sc);
     }
+}
+
+template <class T>
+__global__ void features_kernel(MlpFeatArgs a) {
+    const int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (row >= (a.count_dev ? (int64_t)*a.count_dev : a.npairs)) return;
+    const int64_t p = a.idx ? (int64_t)a.idx[row] : row;
+    compute_features<T>(a, row, p, a.feat + 16 * row, a.targets ? a.targets + 4 * row : nullptr);
 }
 
 // ---------------------------------------------------------------------------
@@ -248,6 +255,76 @@ __device__ __forceinline__ void hidden_layer(uint32_t A[8][4], const __nv_bfloat
     }
 }
 
+// One warp carries 16 rows through the network: rows g and g + 8 of the warp
+// (g = lane / 4) come from feature rows f0 and f1 (16 floats each, null: a
+// zero row) and their 8 outputs go to o0 and o1 (null: dropped); each thread
+// writes outputs 2t and 2t + 1 (t = lane % 4).  `img` is the network image in
+// shared memory.
+__device__ __forceinline__ void mlp_warp_rows(const unsigned char* img, const float* f0p, const float* f1p, float* o0,
+                                              float* o1) {
+    const __nv_bfloat16* W1 = reinterpret_cast<const __nv_bfloat16*>(img);
+    const __nv_bfloat16* W2 = W1 + kSmemW1;
+    const __nv_bfloat16* W3 = W2 + kSmemW;
+    const __nv_bfloat16* W4 = W3 + kSmemW;
+    const float* bias = reinterpret_cast<const float*>(W4 + kSmemW4);  // b1 | b2 | b3 | b4
+    const int lane = threadIdx.x & 31;
+    const int g = lane >> 2, t = lane & 3;
+    // layer 1: A = features (16 x 16)
+    uint32_t A[8][4];
+    {
+        float f0[4] = {0, 0, 0, 0}, f1[4] = {0, 0, 0, 0};
+        if (f0p) {
+            f0[0] = f0p[2 * t];
+            f0[1] = f0p[2 * t + 1];
+            f0[2] = f0p[2 * t + 8];
+            f0[3] = f0p[2 * t + 9];
+        }
+        if (f1p) {
+            f1[0] = f1p[2 * t];
+            f1[1] = f1p[2 * t + 1];
+            f1[2] = f1p[2 * t + 8];
+            f1[3] = f1p[2 * t + 9];
+        }
+        uint32_t X[4] = {pack_bf16(f0[0], f0[1]), pack_bf16(f1[0], f1[1]), pack_bf16(f0[2], f0[3]),
+                         pack_bf16(f1[2], f1[3])};
+        float acc[16][4];
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+            acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.f;
+            const __nv_bfloat16* wr = W1 + (8 * j + g) * kKs1 + 2 * t;
+            mma_bf16(acc[j], X, lds32(wr), lds32(wr + 8));
+            const float b0 = bias[8 * j + 2 * t], b1 = bias[8 * j + 2 * t + 1];
+            acc[j][0] = fmaxf(acc[j][0] + b0, 0.f);
+            acc[j][1] = fmaxf(acc[j][1] + b1, 0.f);
+            acc[j][2] = fmaxf(acc[j][2] + b0, 0.f);
+            acc[j][3] = fmaxf(acc[j][3] + b1, 0.f);
+        }
+#pragma unroll
+        for (int kk = 0; kk < 8; ++kk) {
+            A[kk][0] = pack_bf16(acc[2 * kk][0], acc[2 * kk][1]);
+            A[kk][1] = pack_bf16(acc[2 * kk][2], acc[2 * kk][3]);
+            A[kk][2] = pack_bf16(acc[2 * kk + 1][0], acc[2 * kk + 1][1]);
+            A[kk][3] = pack_bf16(acc[2 * kk + 1][2], acc[2 * kk + 1][3]);
+        }
+    }
+    hidden_layer(A, W2, bias + kMlpHid, g, t);
+    hidden_layer(A, W3, bias + 2 * kMlpHid, g, t);
+    // layer 4: 8 outputs
+    float o[4] = {0, 0, 0, 0};
+    const __nv_bfloat16* wr = W4 + g * kKs + 2 * t;
+#pragma unroll
+    for (int kk = 0; kk < 8; ++kk) mma_bf16(o, A[kk], lds32(wr + 16 * kk), lds32(wr + 16 * kk + 8));
+    const float b0 = bias[3 * kMlpHid + 2 * t], b1 = bias[3 * kMlpHid + 2 * t + 1];
+    if (o0) {
+        o0[2 * t] = o[0] + b0;
+        o0[2 * t + 1] = o[1] + b1;
+    }
+    if (o1) {
+        o1[2 * t] = o[2] + b0;
+        o1[2 * t + 1] = o[3] + b1;
+    }
+}
+
 __global__ void __launch_bounds__(kFwdWarps * 32) mlp_forward_kernel(int64_t nmax, const unsigned char* __restrict__ image,
                                                                      const float* __restrict__ feat,
                                                                      float* __restrict__ out,
@@ -261,101 +338,75 @@ __global__ void __launch_bounds__(kFwdWarps * 32) mlp_forward_kernel(int64_t nma
     if (!bulk_copy_to_smem(smem, image, (unsigned)kFwdSmem, reinterpret_cast<unsigned long long*>(smem + kFwdSmem),
                            status))
         return;
-    const __nv_bfloat16* W1 = reinterpret_cast<const __nv_bfloat16*>(smem);
-    const __nv_bfloat16* W2 = W1 + kSmemW1;
-    const __nv_bfloat16* W3 = W2 + kSmemW;
-    const __nv_bfloat16* W4 = W3 + kSmemW;
-    const float* bias = reinterpret_cast<const float*>(W4 + kSmemW4);  // b1 | b2 | b3 | b4
-
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int g = lane >> 2, t = lane & 3;
     const int64_t ntiles = (npairs + 16 * kFwdWarps - 1) / (16 * kFwdWarps);
     for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        const int64_t r0 = tile * 16 * kFwdWarps + 16 * warp + g, r1 = r0 + 8;
-        // layer 1: A = features (16 x 16)
-        uint32_t A[8][4];
-        {
-            float f0[4] = {0, 0, 0, 0}, f1[4] = {0, 0, 0, 0};
-            if (r0 < npairs) {
-                const float* fr = feat + 16 * r0;
-                f0[0] = fr[2 * t];
-                f0[1] = fr[2 * t + 1];
-                f0[2] = fr[2 * t + 8];
-                f0[3] = fr[2 * t + 9];
-            }
-            if (r1 < npairs) {
-                const float* fr = feat + 16 * r1;
-                f1[0] = fr[2 * t];
-                f1[1] = fr[2 * t + 1];
-                f1[2] = fr[2 * t + 8];
-                f1[3] = fr[2 * t + 9];
-            }
-            uint32_t X[4] = {pack_bf16(f0[0], f0[1]), pack_bf16(f1[0], f1[1]), pack_bf16(f0[2], f0[3]),
-                             pack_bf16(f1[2], f1[3])};
-            float acc[16][4];
-#pragma unroll
-            for (int j = 0; j < 16; ++j) {
-                acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.f;
-                const __nv_bfloat16* wr = W1 + (8 * j + g) * kKs1 + 2 * t;
-                mma_bf16(acc[j], X, lds32(wr), lds32(wr + 8));
-                const float b0 = bias[8 * j + 2 * t], b1 = bias[8 * j + 2 * t + 1];
-                acc[j][0] = fmaxf(acc[j][0] + b0, 0.f);
-                acc[j][1] = fmaxf(acc[j][1] + b1, 0.f);
-                acc[j][2] = fmaxf(acc[j][2] + b0, 0.f);
-                acc[j][3] = fmaxf(acc[j][3] + b1, 0.f);
-            }
-#pragma unroll
-            for (int kk = 0; kk < 8; ++kk) {
-                A[kk][0] = pack_bf16(acc[2 * kk][0], acc[2 * kk][1]);
-                A[kk][1] = pack_bf16(acc[2 * kk][2], acc[2 * kk][3]);
-                A[kk][2] = pack_bf16(acc[2 * kk + 1][0], acc[2 * kk + 1][1]);
-                A[kk][3] = pack_bf16(acc[2 * kk + 1][2], acc[2 * kk + 1][3]);
-            }
-        }
-        hidden_layer(A, W2, bias + kMlpHid, g, t);
-        hidden_layer(A, W3, bias + 2 * kMlpHid, g, t);
-        // layer 4: 8 outputs
-        float o[4] = {0, 0, 0, 0};
-        const __nv_bfloat16* wr = W4 + g * kKs + 2 * t;
-#pragma unroll
-        for (int kk = 0; kk < 8; ++kk) mma_bf16(o, A[kk], lds32(wr + 16 * kk), lds32(wr + 16 * kk + 8));
-        const float b0 = bias[3 * kMlpHid + 2 * t], b1 = bias[3 * kMlpHid + 2 * t + 1];
-        if (r0 < npairs) {
-            out[8 * r0 + 2 * t] = o[0] + b0;
-            out[8 * r0 + 2 * t + 1] = o[1] + b1;
-        }
-        if (r1 < npairs) {
-            out[8 * r1 + 2 * t] = o[2] + b0;
-            out[8 * r1 + 2 * t + 1] = o[3] + b1;
-        }
+        const int64_t r0 = tile * 16 * kFwdWarps + 16 * warp + (lane >> 2), r1 = r0 + 8;
+        mlp_warp_rows(smem, r0 < npairs ? feat + 16 * r0 : nullptr, r1 < npairs ? feat + 16 * r1 : nullptr,
+                      r0 < npairs ? out + 8 * r0 : nullptr, r1 < npairs ? out + 8 * r1 : nullptr);
     }
 }
 
 // network output -> world-frame start normal (zero when the trust logit is
 // negative: the Newton solve then starts cold).  FP32: it only seeds the FP32
 // Newton iterations.
-__global__ void guess_kernel(int64_t npairs, const int* __restrict__ pa, View<4, const double> q,
-                             const float* __restrict__ feat, const float* __restrict__ out, View<3, double> guess,
-                             const int* __restrict__ idx, const int* __restrict__ count_dev) {
-    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;  // row of feat / out / guess
-    if (p >= (count_dev ? (int64_t)*count_dev : npairs)) return;
-    const int64_t pair = idx ? (int64_t)idx[p] : p;
-    const float* o = out + 8 * p;
-    const float* f = feat + 16 * p;
+__device__ __forceinline__ void guess_from(const float* f, const float* o, float s, float x, float y, float z,
+                                           double g[3]) {
     const float inv = 1.f / (float)RELCP_MLP_CORR_SCALE;
     const float n[3] = {f[13] + inv * o[0], f[14] + inv * o[1], f[15] + inv * o[2]};
     const float l = sqrtf(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
     if (!(o[4] > 0.f) || !(l > 1e-6f)) {
-        guess(0, p) = guess(1, p) = guess(2, p) = 0.0;
+        g[0] = g[1] = g[2] = 0.0;
         return;
     }
-    const int i = pa[pair];
-    const float s = (float)q(0, i), x = (float)q(1, i), y = (float)q(2, i), z = (float)q(3, i);
     const float lq = sqrtf(s * s + x * x + y * y + z * z);
     float R[9];
     quat_to_R(s / lq, x / lq, y / lq, z / lq, R);
-    for (int k = 0; k < 3; ++k)
-        guess(k, p) = (double)((R[3 * k] * n[0] + R[3 * k + 1] * n[1] + R[3 * k + 2] * n[2]) / l);
+    for (int k = 0; k < 3; ++k) g[k] = (double)((R[3 * k] * n[0] + R[3 * k + 1] * n[1] + R[3 * k + 2] * n[2]) / l);
+}
+
+// The learned start in one kernel for a list of pairs: per tile of 64 pairs,
+// FP32 features into shared memory, the BF16 network on the tensor cores (one
+// warp per 16 pairs, weights bulk-copied into shared memory once per CTA),
+// the outputs back into shared memory, then the rotated start normals.
+constexpr int kGuessTile = 16 * kFwdWarps;
+constexpr size_t kGuessSmem = kFwdSmem + 16 + (size_t)kGuessTile * (16 + 8) * sizeof(float);
+
+__global__ void __launch_bounds__(kFwdWarps * 32) mlp_guess_kernel(MlpFeatArgs fa, const unsigned char* __restrict__ image,
+                                                                   View<3, double> guess, int* __restrict__ status) {
+    const int64_t count = fa.count_dev ? (int64_t)*fa.count_dev : fa.npairs;
+    if ((int64_t)blockIdx.x * kGuessTile >= count) return;  // no tile for this block
+    extern __shared__ __align__(16) unsigned char smem[];
+    if (!bulk_copy_to_smem(smem, image, (unsigned)kFwdSmem, reinterpret_cast<unsigned long long*>(smem + kFwdSmem),
+                           status))
+        return;
+    float* feat = reinterpret_cast<float*>(smem + kFwdSmem + 16);  // kGuessTile x 16
+    float* outs = feat + kGuessTile * 16;                          // kGuessTile x 8
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t ntiles = (count + kGuessTile - 1) / kGuessTile;
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int64_t row0 = tile * kGuessTile;
+        const int r = threadIdx.x;  // one pair per thread (kGuessTile <= blockDim.x)
+        int64_t pair = -1;
+        if (r < kGuessTile && row0 + r < count) {
+            pair = fa.idx ? (int64_t)fa.idx[row0 + r] : row0 + r;
+            compute_features<float>(fa, row0 + r, pair, feat + 16 * r, nullptr);
+        }
+        __syncthreads();
+        const int rr = 16 * warp + (lane >> 2);
+        mlp_warp_rows(smem, row0 + rr < count ? feat + 16 * rr : nullptr,
+                      row0 + rr + 8 < count ? feat + 16 * (rr + 8) : nullptr,
+                      row0 + rr < count ? outs + 8 * rr : nullptr, row0 + rr + 8 < count ? outs + 8 * (rr + 8) : nullptr);
+        __syncthreads();
+        if (pair >= 0) {
+            const int i = fa.pa[pair * fa.pstride];
+            double g[3];
+            guess_from(feat + 16 * r, outs + 8 * r, (float)fa.q(0, i), (float)fa.q(1, i), (float)fa.q(2, i),
+                       (float)fa.q(3, i), g);
+            for (int k = 0; k < 3; ++k) guess(k, row0 + r) = g[k];
+        }
+        __syncthreads();
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -575,10 +626,8 @@ relcp_status mlp_guess(MlpState& m, int64_t npairs, const int* pa, const int* pb
         set_error("learned guess not loaded");
         return RELCP_ERR_STATE;
     }
-    const int64_t na = npairs > 0 ? npairs : 1;
-    RELCP_TRY(m.feat.ensure((size_t)(16 * na), s));
-    RELCP_TRY(m.out.ensure((size_t)(8 * na), s));
-    RELCP_TRY(m.guess.ensure((size_t)(3 * na), s));
+    if (npairs == 0) return RELCP_OK;
+    RELCP_TRY(m.guess.ensure((size_t)(3 * npairs), s));
     MlpFeatArgs fa{};
     fa.npairs = npairs;
     fa.pa = pa;
@@ -589,26 +638,32 @@ relcp_status mlp_guess(MlpState& m, int64_t npairs, const int* pa, const int* pb
     fa.axes = axes;
     for (int k = 0; k < 3; ++k) fa.box[k] = box[k];
     fa.snsd = nullptr;
-    fa.feat = m.feat.p;
+    fa.feat = nullptr;
     fa.targets = nullptr;
     fa.idx = idx;
     fa.count_dev = count_dev;
-    RELCP_TRY(mlp_features_launch(fa, s));
-    RELCP_TRY(mlp_forward_launch(npairs, m.image.p, m.feat.p, m.out.p, s, count_dev, status));
-    if (npairs > 0) {
-        note_launch();
-        guess_kernel<<<nb(npairs), 256, 0, s>>>(npairs, pa, q, m.feat.p, m.out.p, View<3, double>::soa(m.guess.p, npairs),
-                                                 idx, count_dev);
-        RELCP_CUDA(cudaGetLastError());
+    static bool attr_set[64] = {false};
+    int dev = 0;
+    RELCP_CUDA(cudaGetDevice(&dev));
+    if (dev >= 0 && dev < 64 && !attr_set[dev]) {
+        RELCP_CUDA(cudaFuncSetAttribute(mlp_guess_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kGuessSmem));
+        attr_set[dev] = true;
     }
+    const int64_t ntiles = (npairs + kGuessTile - 1) / kGuessTile;
+    const int sms = device_sm_count();
+    int64_t blocks = (int64_t)(sms > 0 ? sms : 1) * 2;
+    if (blocks > ntiles) blocks = ntiles;
+    note_launch();
+    mlp_guess_kernel<<<(unsigned)blocks, kFwdWarps * 32, kGuessSmem, s>>>(fa, m.image.p,
+                                                                          View<3, double>::soa(m.guess.p, npairs),
+                                                                          status);
+    RELCP_CUDA(cudaGetLastError());
     return RELCP_OK;
 }
 
 void mlp_release(MlpState& m, cudaStream_t s) {
     m.params.release(s);
     m.image.release(s);
-    m.feat.release(s);
-    m.out.release(s);
     m.guess.release(s);
     m.loaded = false;
 }

@@ -27,8 +27,6 @@ struct MlpState {
     bool loaded = false;
     DBuf<float> params;  // FP32 parameters
     DBuf<unsigned char> image;  // the forward kernel's shared-memory image of params (mlp_pack_launch)
-    DBuf<float> feat;    // npairs x 16
-    DBuf<float> out;     // npairs x 8
     DBuf<double> guess;  // 3 x npairs start normals (world frame; zero = no guess)
 };
 

@@ -292,6 +292,7 @@ struct SnsdArgs {
     int32_t* viol;                   // may be null
     unsigned long long* maxov_bits;  // may be null: atomicMax of the bits of max(0, -Phi) (>= 0 doubles
                                      // order like their bit patterns)
+    int* nviol;                      // may be null: atomicAdd of the number of violators
     int* newton_max;                 // may be null: atomicMax of the Newton iteration counts
     unsigned long long* iters_sum;   // may be null: sum of the Newton iteration counts
     int* status;                     // DEV_NEWTON

@@ -37,6 +37,7 @@ __global__ void __launch_bounds__(kThreads) snsd_kernel(SnsdArgs a) {
     const int64_t count = a.count_dev ? (int64_t)*a.count_dev : a.npairs;
     double maxov = 0.0;
     int iters_out = 0;
+    bool viol_here = false;
     // pairs past the count of a capacity-sized launch: no violation
     if (a.viol && !a.idx && k_thr >= count && k_thr < a.npairs) a.viol[k_thr] = 0;
     if (k_thr < count) {
@@ -62,38 +63,49 @@ __global__ void __launch_bounds__(kThreads) snsd_kernel(SnsdArgs a) {
         }
         if (a.out.iters) a.out.iters[p] = iters;
         iters_out = iters;
-        if (a.viol) a.viol[p] = (G < -a.eps) ? 1 : 0;
+        viol_here = G < -a.eps;
+        if (a.viol) a.viol[p] = viol_here ? 1 : 0;
         maxov = G < 0.0 ? -G : 0.0;
     }
-    // one atomic per block for the largest overlap and iteration count
-    __shared__ double sh_ov[kThreads / 32];
+    // one atomic per block for the largest overlap, the iteration counts and
+    // the violators; the overlap maximum is taken on the bits of non-negative
+    // doubles (integer max, no FP64 unit)
+    __shared__ unsigned long long sh_ov[kThreads / 32];
     __shared__ int sh_it[kThreads / 32];
     __shared__ int sh_is[kThreads / 32];
+    __shared__ int sh_nv[kThreads / 32];
+    unsigned long long ovb = (unsigned long long)__double_as_longlong(maxov);
     int itabs = iters_out < 0 ? -iters_out : iters_out;
     int itsum = itabs;
+    int nvl = viol_here ? 1 : 0;
     for (int o = 16; o > 0; o >>= 1) {
-        maxov = fmax(maxov, __shfl_xor_sync(0xffffffffu, maxov, o));
+        const unsigned long long y = __shfl_xor_sync(0xffffffffu, ovb, o);
+        ovb = y > ovb ? y : ovb;
         itabs = max(itabs, __shfl_xor_sync(0xffffffffu, itabs, o));
         itsum += __shfl_xor_sync(0xffffffffu, itsum, o);
+        nvl += __shfl_xor_sync(0xffffffffu, nvl, o);
     }
     if ((threadIdx.x & 31) == 0) {
-        sh_ov[threadIdx.x >> 5] = maxov;
+        sh_ov[threadIdx.x >> 5] = ovb;
         sh_it[threadIdx.x >> 5] = itabs;
         sh_is[threadIdx.x >> 5] = itsum;
+        sh_nv[threadIdx.x >> 5] = nvl;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-        double m = 0.0;
-        int mi = 0;
+        unsigned long long m = 0;
+        int mi = 0, nv = 0;
         long long ms = 0;
         for (int w = 0; w < kThreads / 32; ++w) {
-            m = fmax(m, sh_ov[w]);
+            m = sh_ov[w] > m ? sh_ov[w] : m;
             mi = max(mi, sh_it[w]);
             ms += sh_is[w];
+            nv += sh_nv[w];
         }
-        if (a.maxov_bits) atomicMax(a.maxov_bits, (unsigned long long)__double_as_longlong(m));
+        if (a.maxov_bits && m) atomicMax(a.maxov_bits, m);
         if (a.newton_max) atomicMax(a.newton_max, mi);
         if (a.iters_sum) atomicAdd(a.iters_sum, (unsigned long long)ms);
+        if (a.nviol && nv) atomicAdd(a.nviol, nv);
     }
 }
 
