@@ -96,6 +96,10 @@ enum {
                                       gamma of the same pair (the solution is the same within lcp_tol) */
     RELCP_FLAG_JACOBI = 4u,        /* projected-gradient steps scaled by 1 / A_aa, BB lengths in the
                                       matching metric (same solution, fewer iterations on uneven rows) */
+    RELCP_FLAG_GRAPH = 32u,        /* replay the step's first level (broad-phase filter to overlap test, the
+                                      LCP launched between the two graphs) from CUDA graphs captured per
+                                      configuration; pays off only while the cached pair list is not rebuilt
+                                      (every rebuild changes the configuration and costs a new capture) */
     RELCP_FLAG_LCP_TIMING = 16u,   /* CUDA events around the LCP kernel launches only (ms_lcp_kernel,
                                       lcp_alg_bytes), without the per-phase events; an event record costs the
                                       host ~2 us on this hardware */
@@ -137,7 +141,7 @@ typedef struct relcp_step_stats {
     int32_t lcp_launches;
     int32_t snsd_launches;
     int32_t pair_list_rebuilt;  /* 1 when the cached candidate list was rebuilt in this step */
-    int32_t pad0;
+    int32_t graph_replayed;     /* 1 when the step's first level ran as a replayed CUDA graph */
     int64_t newton_iters_c0;    /* Newton iterations summed over the pairs of the C^k evaluation */
     int64_t snsd_c0_evaluated;  /* pairs evaluated at C^k (the rest reused the previous step's last
                                    overlap test; see RELCP_FLAG_NO_SNSD_REUSE) */

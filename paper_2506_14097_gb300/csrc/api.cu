@@ -12,6 +12,7 @@
 // buffers and decide the loop; everything else stays on the device.
 #include <atomic>
 #include <chrono>
+#include <functional>
 #include <cstdarg>
 #include <cstring>
 #include <string>
@@ -28,6 +29,7 @@ static thread_local char g_err[1024] = "";
 static std::atomic<long long> g_launches{0};
 
 void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+void note_launches(long long k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
 
 void set_error(const char* fmt, ...) {
     va_list ap;
@@ -73,6 +75,14 @@ struct DevStep {
     int pad;
 };
 
+// a captured first level of a step (see step_once)
+struct StepGraph {
+    std::vector<uintptr_t> key;
+    bool uncapturable = false;
+    cudaGraphExec_t pre = nullptr, post = nullptr;  // before and after the LCP launch
+    long long nkernels = 0;
+};
+
 struct relcp_ctx {
     relcp_config cfg{};
     cudaStream_t s = nullptr;
@@ -112,6 +122,9 @@ struct relcp_ctx {
     // phase needs no host round trip
     bool la_ok = false, la_rebuild = true;
     bool prepped = false;  // the last accept pass also ran the next step's prep
+    DBuf<StepConst> skd;      // per-step scalars on the device
+    StepConst* skh = nullptr; // their pinned host staging copy
+    std::vector<StepGraph> graphs;
     int stamp = 0;         // stamp written by the last completed step
     bool memo_ok = false;  // memo and s1prev describe the current state
     bool snsd_ok = false;  // s1prev may stand in for the SNSD at C^k
@@ -240,6 +253,42 @@ struct PhaseTimer {
     void stop() { on = kernels = false; }
 };
 
+// Key of a captured step graph: everything the level-0 launches depend on
+// (buffer addresses, capacities, modes).  A step whose key was seen before runs
+// the graph of that key; the second sighting captures it.
+static void step_key(relcp_ctx* c, int64_t PC, std::vector<uintptr_t>& key) {
+    key.clear();
+    auto add = [&](const void* p) { key.push_back((uintptr_t)p); };
+    key.push_back((uintptr_t)PC);
+    key.push_back((uintptr_t)c->n);
+    key.push_back((uintptr_t)c->rcap);
+    key.push_back((uintptr_t)c->sprev_stride);
+    key.push_back((uintptr_t)(c->memo_ok ? 1 : 0) | (uintptr_t)(c->snsd_ok ? 2 : 0) | (uintptr_t)(c->mlp.loaded ? 4 : 0));
+    const void* ptrs[] = {c->x.p, c->q.p, c->axes.p, c->vel.p, c->fext.p, c->P.p, c->K.p, c->Kf.p, c->rb.p,
+                          c->ufree.p, c->uc.p, c->ustep.p, c->xt.p, c->qt.p, c->Pt.p, c->s0.p, c->s1.p, c->s1prev.p,
+                          c->it0.p, c->it1.p, c->flags.p, c->fscan.p, c->gamma0.p, c->idx.p, c->rowof.p, c->pa.p,
+                          c->pb.p, c->bp.pv.p, c->bp.memo.p, c->bp.vpa.p, c->bp.vpb.p, c->bp.vflag.p, c->bp.vscan.p,
+                          c->bp.xb.p, c->r_ia.p, c->r_ib.p, c->r_rec.p, c->r_pair.p, c->r_geom.p, c->r_geomf.p,
+                          c->r_q.p, c->r_qf.p, c->r_diag.p, c->r_gamma.p, c->r_gammaf.p, c->r_invd.p, c->r_invdf.p,
+                          c->lcp.inc_count.p, c->lcp.inc_off.p, c->lcp.inc_tmp.p, c->lcp.inc.p, c->lcp.packf.p,
+                          c->lcp.packd.p, c->lcp.partials.p, c->scan.tiles.p, c->scan.ctr.p, c->bp.scan.tiles.p,
+                          c->bp.scan.ctr.p, c->lcp.scan.tiles.p, c->lcp.scan.ctr.p, c->mlp.image.p, c->mlp.guess.p,
+                          c->dstep.p, c->hstep, c->skd.p, c->skh};
+    for (const void* q : ptrs) add(q);
+    for (size_t k = 0; k < 2 && k < c->events.size(); ++k) add(c->events[k]);
+}
+
+static void destroy_graph(StepGraph& g) {
+    if (g.pre) cudaGraphExecDestroy(g.pre);
+    if (g.post) cudaGraphExecDestroy(g.post);
+    g.pre = g.post = nullptr;
+}
+
+void drop_graphs(relcp_ctx* c) {
+    for (auto& g : c->graphs) destroy_graph(g);
+    c->graphs.clear();
+}
+
 relcp_status step_once(relcp_ctx* c) {
     const auto h0 = std::chrono::steady_clock::now();
     double wait_ms = 0.0;
@@ -259,9 +308,22 @@ relcp_status step_once(relcp_ctx* c) {
     RELCP_TRY(tm.start((cfg.flags & RELCP_FLAG_PHASE_TIMING) != 0, (cfg.flags & RELCP_FLAG_LCP_TIMING) != 0, s,
                        &c->events));
     std::vector<std::pair<int, int>> snsd_marks, lcp_marks, lcpk_marks;
-    int t_begin = tm.mark();
-    RELCP_CUDA(cudaMemsetAsync(c->dstep.p, 0, sizeof(DevStep), s));
     DevStep* ds = c->dstep.p;
+    const bool memo_ok = c->memo_ok;
+    const bool prepped = c->prepped;
+
+    // per-step scalars, read by the kernels from device memory
+    StepConst& sk = *c->skh;
+    for (int k = 0; k < 3; ++k) {
+        sk.box0[k] = box0[k];
+        sk.box1[k] = box1[k];
+    }
+    if (!broadphase_lookahead_params(c->bp, n, box1, sk.sfac))
+        for (int k = 0; k < 3; ++k) sk.sfac[k] = 1.0;
+    sk.stamp_prev = memo_ok ? c->stamp : -1;
+    sk.pad = 0;
+    const double* box0_dev = c->skd.p->box0;
+    const double* box1_dev = c->skd.p->box1;
 
     // bodies: normalised q, P, K, rb, U_free
     PrepArgs pa{};
@@ -286,47 +348,69 @@ relcp_status step_once(relcp_ctx* c) {
     }
     pa.rb = c->rb.p;
     pa.ufree = c->ufree.p;
-    // the previous step's accept pass already prepared this state
-    if (!c->prepped) RELCP_TRY(prep_launch(pa, s));
     c->prepped = false;
-
-    // broad phase.  When the previous step's look-ahead showed the cached list
-    // complete for these positions, the exact filter and compaction run with
-    // the pair count left on the device; otherwise the synchronous path checks
-    // the bound and rebuilds the list if needed.  Per-pair work below runs over
-    // the list's capacity PC (also the SoA stride of pair arrays) and stops at
-    // the device count.
-    View<3, const double> xv = View<3, const double>::soa(c->x.p, n);
-    const int rebuilds_before = c->bp.rebuilds;
-    const bool fast_bp = c->la_ok && !c->la_rebuild && n >= 2 &&
-                         verlet_bound_holds(c->bp, n, box0, c->rb_max, cfg.skin, 0.0);
-    c->la_ok = false;  // set again when this step completes
-    if (fast_bp) {
-        RELCP_TRY(broadphase_filter_async(n, c->x.p, c->rb.p, box0, cfg.skin, c->pa, c->pb, c->bp, s));
-    } else {
-        int64_t np_host = 0;
-        RELCP_TRY(broadphase_cached(n, c->x.p, c->rb.p, c->rb_max, box0, cfg.skin, c->pa, c->pb, &np_host, c->bp, s));
-    }
-    st.pair_list_rebuilt = c->bp.rebuilds != rebuilds_before;
-    const int64_t PC = (n >= 2) ? c->bp.vn : 0;  // pair capacity and SoA stride
-    const int* npd = PC > 0 ? c->bp.vscan.p + PC : nullptr;  // device pair count
-    const int64_t np = PC;  // grid sizes and strides of the per-pair work
-    int t_bp = tm.mark();
-    const int64_t npa = np > 0 ? np : 1;
-    RELCP_TRY(c->s0.ensure(10 * npa, s));
-    RELCP_TRY(c->s1.ensure(10 * npa, s));
-    RELCP_TRY(c->it0.ensure(npa, s));
-    RELCP_TRY(c->it1.ensure(npa, s));
-    RELCP_TRY(c->flags.ensure(npa, s));
-    RELCP_TRY(c->fscan.ensure(npa + 1, s));
-    c->nrows = 0;
     if (cfg.fault_inject & RELCP_FAULT_ROW_CAPACITY) {
         set_error("row capacity exhausted (injected fault)");
         tm.stop();
         return RELCP_ERR_CAPACITY;
     }
-    RELCP_TRY(grow_rows(c, npa));
-    if (npd) RELCP_CUDA(cudaMemcpyAsync(&ds->np, npd, sizeof(int), cudaMemcpyDeviceToDevice, s));
+
+    // broad phase.  When the previous step's look-ahead showed the cached list
+    // complete for these positions, the exact filter and compaction run with
+    // the pair count left on the device (and the whole first level of the
+    // step can be a replayed CUDA graph); otherwise the synchronous path
+    // checks the bound and rebuilds the list if needed.  Per-pair work runs
+    // over the list's capacity PC (also the SoA stride of pair arrays) and
+    // stops at the device count.
+    View<3, const double> xv = View<3, const double>::soa(c->x.p, n);
+    const int rebuilds_before = c->bp.rebuilds;
+    const bool fast_bp = c->la_ok && !c->la_rebuild && n >= 2 &&
+                         verlet_bound_holds(c->bp, n, box0, c->rb_max, cfg.skin, 0.0);
+    c->la_ok = false;  // set again when this step completes
+    int t_begin = -1, t_bp = -1;
+    // every buffer of the step sized before any launch (nothing allocates
+    // inside a captured region)
+    auto reserve = [&](int64_t PC) -> relcp_status {
+        const int64_t npa = PC > 0 ? PC : 1;
+        RELCP_TRY(c->s0.ensure(10 * npa, s));
+        RELCP_TRY(c->s1.ensure(10 * npa, s));
+        RELCP_TRY(c->it0.ensure(npa, s));
+        RELCP_TRY(c->it1.ensure(npa, s));
+        RELCP_TRY(c->flags.ensure(npa, s));
+        RELCP_TRY(c->fscan.ensure(npa + 1, s));
+        RELCP_TRY(c->gamma0.ensure(npa, s));
+        RELCP_TRY(c->idx.ensure(npa, s));
+        RELCP_TRY(c->rowof.ensure(npa, s));
+        c->nrows = 0;
+        RELCP_TRY(grow_rows(c, npa));
+        if (cfg.guess == RELCP_GUESS_MLP && c->mlp.loaded) RELCP_TRY(c->mlp.guess.ensure((size_t)(3 * npa), s));
+        RELCP_TRY(lcp_reserve(c->lcp, npa, n, mixed, s));
+        RELCP_TRY(scan_reserve(c->scan, npa, s));
+        RELCP_TRY(scan_reserve(c->bp.scan, c->bp.vn > 0 ? c->bp.vn : 1, s));
+        return RELCP_OK;
+    };
+    auto head = [&]() -> relcp_status {
+        RELCP_CUDA(cudaMemsetAsync(ds, 0, sizeof(DevStep), s));
+        RELCP_CUDA(cudaMemcpyAsync(c->skd.p, c->skh, sizeof(StepConst), cudaMemcpyHostToDevice, s));
+        if (!prepped) RELCP_TRY(prep_launch(pa, s));
+        return RELCP_OK;
+    };
+    int64_t PC = 0;
+    if (fast_bp) {
+        PC = c->bp.vn;
+        RELCP_TRY(reserve(PC));
+    } else {
+        t_begin = tm.mark();
+        RELCP_TRY(head());
+        int64_t np_host = 0;
+        RELCP_TRY(broadphase_cached(n, c->x.p, c->rb.p, c->rb_max, box0, cfg.skin, c->pa, c->pb, &np_host, c->bp, s));
+        PC = (n >= 2) ? c->bp.vn : 0;
+        RELCP_TRY(reserve(PC));
+        t_bp = tm.mark();
+    }
+    st.pair_list_rebuilt = c->bp.rebuilds != rebuilds_before;
+    const int* npd = PC > 0 ? c->bp.vscan.p + PC : nullptr;  // device pair count
+    const int64_t np = PC;  // grid sizes and strides of the per-pair work
 
     auto snsd_out = [&](DBuf<double>& o, DBuf<int>& it) {
         SnsdOut so;
@@ -342,33 +426,28 @@ relcp_status step_once(relcp_ctx* c) {
     // C^k values a pair keeps from the previous step (the SNSD of its last
     // overlap test, evaluated at this very configuration, and the final gamma
     // of its A_0 row); idx lists the pairs still to evaluate
-    RELCP_TRY(c->gamma0.ensure(npa, s));
-    RELCP_TRY(c->idx.ensure(npa, s));
-    RELCP_TRY(c->rowof.ensure(npa, s));
-    const bool memo_ok = c->memo_ok;
     c->memo_ok = false;  // set again once this step has saved its memo
     const int* count_dev = &ds->c0_evals;
-    if (np > 0) {
-        ReuseArgs ru{};
-        ru.npairs = np;
-        ru.np_dev = npd;
-        ru.pv = c->bp.pv.p;
-        ru.memo = c->bp.memo.p;
-        ru.stamp_prev = memo_ok ? c->stamp : -1;
-        ru.reuse_snsd = c->snsd_ok && !(cfg.flags & RELCP_FLAG_NO_SNSD_REUSE);
-        ru.use_gamma = !(cfg.flags & RELCP_FLAG_NO_WARM_START);
-        ru.sprev = c->s1prev.p;
-        ru.sprev_stride = c->sprev_stride;
-        ru.nprev = c->nprev;
-        ru.s0 = c->s0.p;
-        ru.it0 = c->it0.p;
-        ru.gamma0 = c->gamma0.p;
-        ru.list = c->idx.p;
-        ru.count = &ds->c0_evals;  // zeroed with the rest of DevStep at the start of the step
-        RELCP_TRY(reuse_launch(ru, s));
-    }
+    ReuseArgs ru{};
+    ru.npairs = np;
+    ru.np_dev = npd;
+    ru.pv = c->bp.pv.p;
+    ru.memo = c->bp.memo.p;
+    ru.stamp_prev = sk.stamp_prev;
+    ru.stamp_prev_dev = &c->skd.p->stamp_prev;
+    ru.reuse_snsd = c->snsd_ok && !(cfg.flags & RELCP_FLAG_NO_SNSD_REUSE);
+    ru.use_gamma = !(cfg.flags & RELCP_FLAG_NO_WARM_START);
+    ru.sprev = c->s1prev.p;
+    ru.sprev_stride = c->sprev_stride;
+    ru.nprev = c->nprev;
+    ru.s0 = c->s0.p;
+    ru.it0 = c->it0.p;
+    ru.gamma0 = c->gamma0.p;
+    ru.list = c->idx.p;
+    ru.count = &ds->c0_evals;  // zeroed with the rest of DevStep at the start of the step
 
     // SNSD at C^k for the listed pairs
+    const bool learned = cfg.guess == RELCP_GUESS_MLP && c->mlp.loaded && np > 0;
     SnsdArgs sa{};
     sa.npairs = np;
     sa.pa = c->pa.p;
@@ -377,13 +456,12 @@ relcp_status step_once(relcp_ctx* c) {
     sa.x = xv;
     sa.P = View<6, const double>::soa(c->P.p, n);
     for (int k = 0; k < 3; ++k) sa.box[k] = box0[k];
+    sa.box_dev = box0_dev;
     sa.guess.c[0] = sa.guess.c[1] = sa.guess.c[2] = nullptr;
     sa.guess.s = 1;
     sa.idx = c->idx.p;
     sa.count_dev = count_dev;
-    if (cfg.guess == RELCP_GUESS_MLP && c->mlp.loaded && np > 0) {
-        RELCP_TRY(mlp_guess(c->mlp, np, c->pa.p, c->pb.p, xv, View<4, const double>::soa(c->q.p, n),
-                            View<3, const double>::soa(c->axes.p, n), box0, s, c->idx.p, count_dev, &ds->status));
+    if (learned) {
         sa.guess = View<3, const double>::soa(c->mlp.guess.p, np);
         st.guess_used = 1;
     }
@@ -395,11 +473,6 @@ relcp_status step_once(relcp_ctx* c) {
     sa.newton_max = &ds->newton_max;
     sa.iters_sum = &ds->iters0;
     sa.status = &ds->status;
-    {
-        int e0 = tm.mark();
-        RELCP_TRY(snsd_launch(sa, s));
-        snsd_marks.push_back({e0, tm.mark()});
-    }
 
     // A_0: rows for the pairs with Phi(C^k) <= phi_skin
     RowsArgs ra{};
@@ -411,11 +484,11 @@ relcp_status step_once(relcp_ctx* c) {
     ra.scan = c->fscan.p;
     ra.snsd = c->s0.p;
     ra.base = 0;
-    ra.cap = c->rcap;
     ra.rec_index = 0;
     ra.c = dt;
     ra.strain_rate = cfg.strain_rate;
     for (int k = 0; k < 3; ++k) ra.box[k] = box0[k];
+    ra.box_dev = box0_dev;
     ra.x = c->x.p;
     ra.ufree = c->ufree.p;
     ra.uc = c->uc.p;
@@ -442,22 +515,11 @@ relcp_status step_once(relcp_ctx* c) {
         r.gammaf = mixed ? c->r_gammaf.p : nullptr;
     };
     bind_rows(ra);
-    if (np > 0) {
-        RELCP_TRY(flag_le_launch(np, npd, c->s0.p, cfg.phi_skin, c->flags.p, s));
-        RELCP_TRY(exclusive_scan(c->flags.p, c->fscan.p, np, c->scan, s));
-        RELCP_TRY(rows_launch(ra, s));
-        RELCP_CUDA(cudaMemcpyAsync(&ds->nrows0, &ds->nrows, sizeof(int), cudaMemcpyDeviceToDevice, s));
-    }
     int64_t m_bound = np;  // rows <= m_bound until the host learns the count
 
-    int depth = 0;
-    int lcp_iters_total = 0;
-    relcp_status step_status = RELCP_OK;
-    DevStep hs{};
-    int t_last = -1;
-    for (;;) {
-        // LCP on the current rows
-        LcpProblem pr{};
+    // LCP on the current rows (row buffers may move when rows are appended)
+    auto make_pr = [&](LcpProblem& pr) {
+        pr = LcpProblem{};
         pr.m_cap = m_bound;
         pr.nrows_dev = &ds->nrows;
         pr.nbodies = n;
@@ -482,62 +544,199 @@ relcp_status step_once(relcp_ctx* c) {
         for (int k = 0; k < 6; ++k) pr.uc[k] = c->uc.p + k * n;
         pr.result = &ds->lcp;
         pr.status = &ds->status;
-        int k0 = -1, k1 = -1;
+    };
+
+    // trial configuration and overlap test (the list look-ahead for the next
+    // step folded into the trial pass: the cached list against these trial
+    // positions, accepted if the recursion stops here, in the next box)
+    TrialArgs ta{};
+    ta.n = n;
+    ta.dt = dt;
+    ta.x = c->x.p;
+    ta.q = c->q.p;
+    ta.axes = c->axes.p;
+    ta.ufree = c->ufree.p;
+    ta.uc = c->uc.p;
+    ta.xt = c->xt.p;
+    ta.qt = c->qt.p;
+    ta.Pt = c->Pt.p;
+    ta.ustep = c->ustep.p;
+    ta.xb = nullptr;
+    if (broadphase_lookahead_params(c->bp, n, box1, ta.sfac)) {
+        ta.xb = c->bp.xb.p;
+        for (int k = 0; k < 3; ++k) ta.la_box[k] = box1[k];
+        ta.sfac_dev = c->skd.p->sfac;
+        ta.la_box_dev = box1_dev;
+        ta.la_dmax = &ds->la_dmax;
+    }
+    SnsdArgs sb = sa;
+    sb.idx = nullptr;
+    sb.count_dev = npd;
+    sb.x = View<3, const double>::soa(c->xt.p, n);
+    sb.P = View<6, const double>::soa(c->Pt.p, n);
+    for (int k = 0; k < 3; ++k) sb.box[k] = box1[k];
+    sb.box_dev = box1_dev;
+    sb.guess = View<3, const double>::soa(c->s0.p + np, np);  // warm start: normals at C^k
+    sb.out = snsd_out(c->s1, c->it1);
+    sb.eps = cfg.eps_ncp;
+    sb.viol = c->flags.p;
+    sb.maxov_bits = &ds->maxov_bits;
+    sb.nviol = &ds->nviol;
+    sb.iters_sum = nullptr;
+    sb.newton_max = &ds->newton_max;
+
+    int k0 = -1, k1 = -1, lcp_l0 = -1;
+    LcpProblem pr;
+    // the persistent LCP launch between its timing events
+    auto lcp_mid = [&]() -> relcp_status {
         pr.ev_before = tm.take(&k0);
         pr.ev_after = tm.take(&k1);
         int blocks = 0;
-        float kms = 0.f;
-        int l0 = tm.mark();
-        RELCP_TRY(lcp_solve(pr, c->lcp, &blocks, &kms, s));
-        int l1 = tm.mark();
-        lcp_marks.push_back({l0, l1});
+        RELCP_TRY(lcp_run(pr, c->lcp, &blocks, s));
         lcpk_marks.push_back({k0, k1});
-
-        // trial configuration and overlap test
-        TrialArgs ta{};
-        ta.n = n;
-        ta.dt = dt;
-        ta.x = c->x.p;
-        ta.q = c->q.p;
-        ta.axes = c->axes.p;
-        ta.ufree = c->ufree.p;
-        ta.uc = c->uc.p;
-        ta.xt = c->xt.p;
-        ta.qt = c->qt.p;
-        ta.Pt = c->Pt.p;
-        ta.ustep = c->ustep.p;
-        // look-ahead for the next step, folded into the trial pass: the cached
-        // list against these trial positions (accepted if the recursion stops
-        // here) in the next box
+        return RELCP_OK;
+    };
+    // after the LCP: trial, overlap test, readback
+    auto post_lcp = [&]() -> relcp_status {
         // the per-level fields (largest overlap, look-ahead displacement, violator count)
         RELCP_CUDA(cudaMemsetAsync(&ds->maxov_bits, 0, 2 * sizeof(unsigned long long) + 2 * sizeof(int), s));
-        ta.xb = nullptr;
-        if (broadphase_lookahead_params(c->bp, n, box1, ta.sfac)) {
-            ta.xb = c->bp.xb.p;
-            for (int k = 0; k < 3; ++k) ta.la_box[k] = box1[k];
-            ta.la_dmax = &ds->la_dmax;
-        }
         RELCP_TRY(trial_launch(ta, s));
-        SnsdArgs sb = sa;
-        sb.idx = nullptr;
-        sb.count_dev = npd;
-        sb.x = View<3, const double>::soa(c->xt.p, n);
-        sb.P = View<6, const double>::soa(c->Pt.p, n);
-        for (int k = 0; k < 3; ++k) sb.box[k] = box1[k];
-        sb.guess = View<3, const double>::soa(c->s0.p + np, np);  // warm start: normals at C^k
-        sb.out = snsd_out(c->s1, c->it1);
-        sb.eps = cfg.eps_ncp;
-        sb.viol = c->flags.p;
-        sb.maxov_bits = &ds->maxov_bits;
-        sb.nviol = &ds->nviol;
-        sb.iters_sum = nullptr;
         {
             int e0 = tm.mark();
             RELCP_TRY(snsd_launch(sb, s));
             snsd_marks.push_back({e0, tm.mark()});
         }
         RELCP_CUDA(cudaMemcpyAsync(c->hstep, ds, sizeof(DevStep), cudaMemcpyDeviceToHost, s));
-        t_last = tm.mark();
+        return RELCP_OK;
+    };
+    // one recursion level from the LCP to the readback
+    auto level_tail = [&]() -> relcp_status {
+        make_pr(pr);
+        int l0 = tm.mark();
+        RELCP_TRY(lcp_build_csr(pr, c->lcp, s));
+        RELCP_TRY(lcp_mid());
+        lcp_marks.push_back({l0, tm.mark()});
+        return post_lcp();
+    };
+    // level 0 after the broad phase, up to the LCP's incidence CSR
+    auto level0_pre = [&]() -> relcp_status {
+        if (np > 0) {
+            RELCP_CUDA(cudaMemcpyAsync(&ds->np, npd, sizeof(int), cudaMemcpyDeviceToDevice, s));
+            RELCP_TRY(reuse_launch(ru, s));
+            if (learned)
+                RELCP_TRY(mlp_guess(c->mlp, np, c->pa.p, c->pb.p, xv, View<4, const double>::soa(c->q.p, n),
+                                    View<3, const double>::soa(c->axes.p, n), box0, s, c->idx.p, count_dev,
+                                    &ds->status, box0_dev));
+        }
+        {
+            int e0 = tm.mark();
+            RELCP_TRY(snsd_launch(sa, s));
+            snsd_marks.push_back({e0, tm.mark()});
+        }
+        if (np > 0) {
+            RELCP_TRY(flag_le_launch(np, npd, c->s0.p, cfg.phi_skin, c->flags.p, s));
+            RELCP_TRY(exclusive_scan(c->flags.p, c->fscan.p, np, c->scan, s));
+            RELCP_TRY(rows_launch(ra, s));
+            RELCP_CUDA(cudaMemcpyAsync(&ds->nrows0, &ds->nrows, sizeof(int), cudaMemcpyDeviceToDevice, s));
+        }
+        make_pr(pr);
+        lcp_l0 = tm.mark();
+        return lcp_build_csr(pr, c->lcp, s);
+    };
+    // the first level with the fast broad phase, up to the LCP's CSR
+    auto level0_fast_pre = [&]() -> relcp_status {
+        t_begin = tm.mark();
+        RELCP_TRY(head());
+        RELCP_TRY(broadphase_filter_async(n, c->x.p, c->rb.p, box0, box0_dev, cfg.skin, c->pa, c->pb, c->bp, s));
+        t_bp = tm.mark();
+        return level0_pre();
+    };
+    auto run_direct = [&](bool fast) -> relcp_status {
+        RELCP_TRY(fast ? level0_fast_pre() : level0_pre());
+        RELCP_TRY(lcp_mid());
+        lcp_marks.push_back({lcp_l0, tm.mark()});
+        return post_lcp();
+    };
+    // capture fn into *out; false when the stream cannot be captured or the
+    // capture fails (nothing of fn has run then)
+    auto capture = [&](const std::function<relcp_status()>& fn, cudaGraphExec_t* out, long long* nk) -> bool {
+        *out = nullptr;
+        const long long l_before = relcp_kernel_launches();
+        if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+            (void)cudaGetLastError();
+            return false;
+        }
+        const relcp_status r = fn();
+        cudaGraph_t graph = nullptr;
+        const cudaError_t e = cudaStreamEndCapture(s, &graph);
+        *nk += relcp_kernel_launches() - l_before;
+        note_launches(-(relcp_kernel_launches() - l_before));  // captured, not run
+        bool ok = r == RELCP_OK && e == cudaSuccess && graph && cudaGraphInstantiate(out, graph, 0) == cudaSuccess;
+        if (graph) cudaGraphDestroy(graph);
+        if (!ok) {
+            *out = nullptr;
+            (void)cudaGetLastError();
+        }
+        return ok;
+    };
+    if (!fast_bp) {
+        RELCP_TRY(run_direct(false));
+    } else if (!(cfg.flags & RELCP_FLAG_GRAPH) || (cfg.flags & RELCP_FLAG_PHASE_TIMING) || !prepped ||
+               s == nullptr || s == cudaStreamLegacy) {
+        // (the legacy default stream cannot be captured)
+        RELCP_TRY(run_direct(true));
+    } else {
+        // replay the captured graphs of this configuration (before and after
+        // the LCP launch, which stays between its timing events), capture them
+        // on the configuration's second sighting, run directly on the first
+        std::vector<uintptr_t> key;
+        step_key(c, PC, key);
+        StepGraph* g = nullptr;
+        for (auto& e : c->graphs)
+            if (e.key == key) g = &e;
+        if (!g) {
+            if (c->graphs.size() >= 4) {
+                destroy_graph(c->graphs.front());
+                c->graphs.erase(c->graphs.begin());
+            }
+            c->graphs.push_back(StepGraph{key, false, nullptr, nullptr, 0});
+            RELCP_TRY(run_direct(true));
+        } else if (g->uncapturable) {
+            RELCP_TRY(run_direct(true));
+        } else {
+            if (!g->pre) {
+                long long nk = 0;
+                bool ok = capture(level0_fast_pre, &g->pre, &nk);
+                if (ok) ok = capture(post_lcp, &g->post, &nk);
+                if (ok) {
+                    g->nkernels = nk;
+                } else {
+                    destroy_graph(*g);
+                    g->uncapturable = true;
+                }
+                snsd_marks.clear();
+                lcp_marks.clear();
+                lcpk_marks.clear();
+            }
+            if (g->pre) {
+                make_pr(pr);
+                st.graph_replayed = 1;
+                RELCP_CUDA(cudaGraphLaunch(g->pre, s));
+                RELCP_TRY(lcp_mid());
+                RELCP_CUDA(cudaGraphLaunch(g->post, s));
+                note_launches(g->nkernels);
+            } else {
+                RELCP_TRY(run_direct(true));
+            }
+        }
+    }
+
+    int depth = 0;
+    int lcp_iters_total = 0;
+    relcp_status step_status = RELCP_OK;
+    DevStep hs{};
+    int t_last = tm.mark();
+    for (;;) {
         {
             const auto w0 = std::chrono::steady_clock::now();
             RELCP_CUDA(cudaStreamSynchronize(s));
@@ -559,7 +758,7 @@ relcp_status step_once(relcp_ctx* c) {
             st.lcp_launches += 1;
         }
         if (hs.status & DEV_TIMEOUT) {
-            set_error("LCP grid barrier timed out");
+            set_error("a device wait timed out (LCP grid barrier or prefix-sum look-back)");
             tm.stop();
             return RELCP_ERR_TIMEOUT;
         }
@@ -581,6 +780,8 @@ relcp_status step_once(relcp_ctx* c) {
         rb2.rec_index = depth;
         RELCP_TRY(rows_launch(rb2, s));
         m_bound = c->nrows + nv;
+        RELCP_TRY(level_tail());
+        t_last = tm.mark();
     }
 
     // memo for the next step: every candidate pair's final A_0 gamma (0 without
@@ -699,6 +900,11 @@ relcp_status relcp_create(const relcp_config* cfg, void* cuda_stream, relcp_ctx*
         set_error("pinned allocation failed");
         st = RELCP_ERR_CUDA;
     }
+    if (st == RELCP_OK) st = c->skd.ensure(1, c->s);
+    if (st == RELCP_OK && cudaMallocHost((void**)&c->skh, sizeof(StepConst)) != cudaSuccess) {
+        set_error("pinned allocation failed");
+        st = RELCP_ERR_CUDA;
+    }
     if (st == RELCP_OK) {
         // the context's prefix sums report a look-back timeout in the step's status word
         c->scan.status = c->bp.scan.status = c->lcp.scan.status = &c->dstep.p->status;
@@ -721,6 +927,7 @@ relcp_status relcp_set_config(relcp_ctx* c, const relcp_config* cfg) {
     if (cfg->precision != c->cfg.precision || cfg->skin != c->cfg.skin) c->snsd_ok = false;
     c->la_ok = false;  // the broad phase checks its cached list again
     c->prepped = false;
+    drop_graphs(c);
     c->cfg = *cfg;
     for (int k = 0; k < 3; ++k) c->box[k] = cfg->box[k];
     return RELCP_OK;
@@ -799,6 +1006,7 @@ relcp_status relcp_set_bodies(relcp_ctx* c, int64_t n, const int32_t* scene_offs
     c->snsd_ok = false;
     c->la_ok = false;
     c->prepped = false;
+    drop_graphs(c);
     c->bp.valid = false;
     c->rb_max = 0.0;
     for (size_t i = 0; i < ha.size(); ++i) c->rb_max = ha[i] > c->rb_max ? ha[i] : c->rb_max;
@@ -945,6 +1153,8 @@ relcp_status relcp_load_mlp(relcp_ctx* c, const float* params, int32_t ptr_kind)
 void relcp_destroy(relcp_ctx* c) {
     if (!c) return;
     cudaStream_t s = c->s;
+    cudaStreamSynchronize(s);
+    drop_graphs(c);
     DBuf<double>* dbs[] = {&c->x, &c->q, &c->axes, &c->vel, &c->fext, &c->P, &c->K, &c->rb, &c->ufree, &c->uc,
                            &c->ustep, &c->xt, &c->qt, &c->Pt, &c->s0, &c->s1, &c->r_geom, &c->r_q, &c->r_diag,
                            &c->r_gamma};
@@ -960,6 +1170,7 @@ void relcp_destroy(relcp_ctx* c) {
     c->r_invd.release(s);
     c->r_invdf.release(s);
     c->dstep.release(s);
+    c->skd.release(s);
     c->bp.xb.release(s);
     c->bp.dmax.release(s);
     c->s1prev.release(s);
@@ -978,6 +1189,7 @@ void relcp_destroy(relcp_ctx* c) {
     cudaStreamSynchronize(s);
     for (cudaEvent_t e : c->events) cudaEventDestroy(e);
     if (c->hstep) cudaFreeHost(c->hstep);
+    if (c->skh) cudaFreeHost(c->skh);
     delete c;
 }
 

@@ -172,9 +172,14 @@ __global__ void disp_kernel(int64_t n, const double* __restrict__ x, const doubl
 // exact candidate test on the cached list (same operations as near_pair)
 __global__ void filter_kernel(int64_t nv, const int* __restrict__ vpa, const int* __restrict__ vpb,
                               View<3, const double> x, const double* __restrict__ rb, double L0, double L1,
-                              double L2, double skin, int* __restrict__ flag) {
+                              double L2, const double* __restrict__ Ldev, double skin, int* __restrict__ flag) {
     int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= nv) return;
+    if (Ldev) {
+        L0 = Ldev[0];
+        L1 = Ldev[1];
+        L2 = Ldev[2];
+    }
     flag[p] = near_pair(x, rb, vpa[p], vpb[p], L0, L1, L2, skin) ? 1 : 0;
 }
 
@@ -360,7 +365,7 @@ relcp_status broadphase_cached(int64_t n, const double* x_soa, const double* rb,
         if (nv > 0) {
             note_launch();
             filter_kernel<<<(unsigned)((nv + kThreads - 1) / kThreads), kThreads, 0, s>>>(
-                nv, sc.vpa.p, sc.vpb.p, xv, rb, box[0], box[1], box[2], skin, sc.vflag.p);
+                nv, sc.vpa.p, sc.vpb.p, xv, rb, box[0], box[1], box[2], nullptr, skin, sc.vflag.p);
             RELCP_CUDA(cudaGetLastError());
         }
         RELCP_TRY(exclusive_scan(sc.vflag.p, sc.vscan.p, nv, sc.scan, s));
@@ -440,15 +445,15 @@ relcp_status broadphase_lookahead(int64_t n, const double* x_soa, const double b
 }
 
 relcp_status broadphase_filter_async(int64_t n, const double* x_soa, const double* rb, const double box[3],
-                                     double skin, DBuf<int>& pa, DBuf<int>& pb, BroadphaseScratch& sc,
-                                     cudaStream_t s) {
+                                     const double* box_dev, double skin, DBuf<int>& pa, DBuf<int>& pb,
+                                     BroadphaseScratch& sc, cudaStream_t s) {
     const int64_t nv = sc.vn;
     if (n < 2 || nv == 0) return RELCP_OK;
     View<3, const double> xv = View<3, const double>::soa(x_soa, n);
     note_launch();
     filter_kernel<<<(unsigned)((nv + kThreads - 1) / kThreads), kThreads, 0, s>>>(nv, sc.vpa.p, sc.vpb.p, xv, rb,
-                                                                                  box[0], box[1], box[2], skin,
-                                                                                  sc.vflag.p);
+                                                                                  box[0], box[1], box[2], box_dev,
+                                                                                  skin, sc.vflag.p);
     RELCP_CUDA(cudaGetLastError());
     RELCP_TRY(exclusive_scan(sc.vflag.p, sc.vscan.p, nv, sc.scan, s));
     note_launch();

@@ -834,11 +834,25 @@ relcp_status lcp_diag_launch(int64_t nrows, const int32_t* ia, const int32_t* ib
     return RELCP_OK;
 }
 
+// Every buffer lcp_solve uses for up to m_cap rows and nb bodies, so that a
+// later solve of that size allocates nothing.
+relcp_status lcp_reserve(LcpScratch& sc, int64_t m_cap, int64_t nb, bool mixed, cudaStream_t s) {
+    const int64_t mc = m_cap > 0 ? m_cap : 1, nba = nb > 0 ? nb : 1;
+    RELCP_TRY(sc.inc_count.ensure((size_t)(2 * nba + 2), s));
+    RELCP_TRY(sc.inc_off.ensure((size_t)nba + 1, s));
+    RELCP_TRY(sc.inc_tmp.ensure((size_t)(2 * mc), s));
+    RELCP_TRY(sc.inc.ensure((size_t)(2 * mc), s));
+    const size_t pack = (size_t)(2 * mc) * 2 + (size_t)(8 * nba);
+    if (mixed) RELCP_TRY(sc.packf.ensure(pack, s));
+    else RELCP_TRY(sc.packd.ensure(pack, s));
+    RELCP_TRY(sc.partials.ensure((size_t)kMaxBlocks * kNred, s));
+    RELCP_TRY(scan_reserve(sc.scan, nba, s));
+    return RELCP_OK;
+}
+
 // Incidence CSR of the current rows (device row count), then the persistent
 // solve.  Nothing here synchronises the stream.
-relcp_status lcp_solve(const LcpProblem& pr, LcpScratch& sc, int* blocks, float* kernel_ms, cudaStream_t s) {
-    *blocks = 0;
-    *kernel_ms = 0.f;
+relcp_status lcp_build_csr(const LcpProblem& pr, LcpScratch& sc, cudaStream_t s) {
     const int64_t mc = pr.m_cap > 0 ? pr.m_cap : 1, nb = pr.nbodies;
     if (pr.m_cap > (int64_t)1 << 29 || nb > (int64_t)1 << 30) return RELCP_ERR_INVALID_ARG;
     const int64_t nba = nb > 0 ? nb : 1;
@@ -860,8 +874,20 @@ relcp_status lcp_solve(const LcpProblem& pr, LcpScratch& sc, int* blocks, float*
     note_launch();
     inc_rank<<<nblk(2 * mc), 256, 0, s>>>(pr.nrows_dev, pr.ia, pr.ib, sc.inc_off.p, sc.inc_tmp.p, sc.inc.p);
     RELCP_CUDA(cudaGetLastError());
-    if (pr.mixed) return solve_typed<float>(pr, sc, sc.packf, blocks, kernel_ms, s);
-    return solve_typed<double>(pr, sc, sc.packd, blocks, kernel_ms, s);
+    return RELCP_OK;
+}
+
+relcp_status lcp_run(const LcpProblem& pr, LcpScratch& sc, int* blocks, cudaStream_t s) {
+    *blocks = 0;
+    float kernel_ms = 0.f;
+    if (pr.mixed) return solve_typed<float>(pr, sc, sc.packf, blocks, &kernel_ms, s);
+    return solve_typed<double>(pr, sc, sc.packd, blocks, &kernel_ms, s);
+}
+
+relcp_status lcp_solve(const LcpProblem& pr, LcpScratch& sc, int* blocks, float* kernel_ms, cudaStream_t s) {
+    *kernel_ms = 0.f;
+    RELCP_TRY(lcp_build_csr(pr, sc, s));
+    return lcp_run(pr, sc, blocks, s);
 }
 
 void release(LcpScratch& sc, cudaStream_t s) {

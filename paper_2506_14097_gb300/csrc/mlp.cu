@@ -65,7 +65,7 @@ template <class T>
 __device__ void compute_features(const MlpFeatArgs& a, int64_t row, int64_t p, float* f, float* targ) {
     const int i = a.pa[p * a.pstride], j = a.pb[p * a.pstride];
     T d[3];
-    for (int k = 0; k < 3; ++k) d[k] = (T)min_image(a.x(k, j) - a.x(k, i), a.box[k]);
+    for (int k = 0; k < 3; ++k) d[k] = (T)min_image(a.x(k, j) - a.x(k, i), a.box_dev ? a.box_dev[k] : a.box[k]);
     T qa[4], qb[4];
     T la = 0, lb = 0;
     for (int k = 0; k < 4; ++k) {
@@ -621,7 +621,7 @@ relcp_status mlp_forward_launch(int64_t npairs, const unsigned char* image, cons
 
 relcp_status mlp_guess(MlpState& m, int64_t npairs, const int* pa, const int* pb, View<3, const double> x,
                        View<4, const double> q, View<3, const double> axes, const double box[3], cudaStream_t s,
-                       const int* idx, const int* count_dev, int* status) {
+                       const int* idx, const int* count_dev, int* status, const double* box_dev) {
     if (!m.loaded) {
         set_error("learned guess not loaded");
         return RELCP_ERR_STATE;
@@ -637,6 +637,7 @@ relcp_status mlp_guess(MlpState& m, int64_t npairs, const int* pa, const int* pb
     fa.q = q;
     fa.axes = axes;
     for (int k = 0; k < 3; ++k) fa.box[k] = box[k];
+    fa.box_dev = box_dev;
     fa.snsd = nullptr;
     fa.feat = nullptr;
     fa.targets = nullptr;

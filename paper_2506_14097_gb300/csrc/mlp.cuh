@@ -40,6 +40,7 @@ struct MlpFeatArgs {
     View<4, const double> q;
     View<3, const double> axes;
     double box[3];
+    const double* box_dev;  // if set, the box is read here (device) instead
     const double* snsd;  // null, or per-pair (phi, n[3], ...) with stride snsd_s between pairs
     int64_t snsd_s, snsd_c;  // pair stride and component stride of `snsd`
     float* feat;         // npairs x 16
@@ -64,7 +65,8 @@ relcp_status mlp_train_step(int64_t B, float* params, float* am, float* av, cons
 // all npairs pairs); npairs bounds the count
 relcp_status mlp_guess(MlpState& m, int64_t npairs, const int* pa, const int* pb, View<3, const double> x,
                        View<4, const double> q, View<3, const double> axes, const double box[3], cudaStream_t s,
-                       const int* idx = nullptr, const int* count_dev = nullptr, int* status = nullptr);
+                       const int* idx = nullptr, const int* count_dev = nullptr, int* status = nullptr,
+                       const double* box_dev = nullptr);
 void mlp_release(MlpState& m, cudaStream_t s);
 
 }  // namespace relcp

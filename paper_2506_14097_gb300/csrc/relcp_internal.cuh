@@ -35,6 +35,7 @@ void set_error(const char* fmt, ...);
 relcp_status status_from_device(int bits);
 // counts every kernel launch of the library (relcp_kernel_launches)
 void note_launch();
+void note_launches(long long k);  // k launches at once (a replayed graph; negative: captured, not run)
 
 #define RELCP_CUDA(call)                                                                              \
     do {                                                                                              \
@@ -197,6 +198,8 @@ relcp_status exclusive_scan(const int* in, int* out, int64_t n, ScanScratch& sc,
 // RELCP_ERR_TIMEOUT if a scan on this scratch (without a status word) timed
 // out; synchronises s
 relcp_status scan_error(ScanScratch& sc, cudaStream_t s);
+// size the scratch for scans of up to n items (a later scan allocates nothing)
+relcp_status scan_reserve(ScanScratch& sc, int64_t n, cudaStream_t s);
 inline void release(ScanScratch& sc, cudaStream_t s) {
     sc.tiles.release(s);
     sc.ctr.release(s);
@@ -259,9 +262,10 @@ bool broadphase_lookahead_params(const BroadphaseScratch& sc, int64_t n, const d
 // The cached list's exact filter and compaction without a host round trip:
 // pairs into pa, pb, sc.pv (capacity sc.vn), their count at sc.vscan.p[sc.vn].
 // Valid only when the bound held for these positions (checked beforehand).
+// box_dev (may be null): the box read on the device instead of `box`
 relcp_status broadphase_filter_async(int64_t n, const double* x_soa, const double* rb, const double box[3],
-                                     double skin, DBuf<int>& pa, DBuf<int>& pb, BroadphaseScratch& sc,
-                                     cudaStream_t s);
+                                     const double* box_dev, double skin, DBuf<int>& pa, DBuf<int>& pb,
+                                     BroadphaseScratch& sc, cudaStream_t s);
 
 // ---------------------------------------------------------------------------
 // SNSD (snsd.cu)
@@ -272,6 +276,16 @@ struct SnsdOut {
     View<3, double> n, ra, rb;
     int32_t* iters;  // may be null
 };
+// Per-step scalars read by the step's kernels from device memory, so that the
+// kernels' arguments stay the same from step to step (CUDA-graph replay).
+struct StepConst {
+    double box0[3];  // box at C^k
+    double box1[3];  // box at the trial configurations / C^{k+1}
+    double sfac[3];  // box1 / the cached pair list's build box
+    int stamp_prev;  // memo stamp of the previous step (-1: none)
+    int pad;
+};
+
 struct SnsdArgs {
     int64_t npairs;
     const int32_t* pa;
@@ -280,6 +294,7 @@ struct SnsdArgs {
     View<3, const double> x;         // body centres
     View<6, const double> P;         // shape matrices
     double box[3];
+    const double* box_dev;           // if set, the box is read here (device) instead
     View<3, const double> guess;     // per-pair start normal (c[0] == nullptr: cold start)
     // optional pair subset: thread k < *count_dev evaluates pair idx[k] (its
     // start normal is guess(., k)); idx == nullptr: thread p evaluates pair p
@@ -343,6 +358,13 @@ struct LcpProblem {
     cudaEvent_t ev_before;       // recorded right before / after the persistent launch (or null)
     cudaEvent_t ev_after;
 };
+// lcp_solve in two parts: the body incidence CSR of the rows, then the
+// persistent solve (the second may be launched apart from the first, e.g.
+// between timing events while the first is part of a captured graph)
+relcp_status lcp_build_csr(const LcpProblem& pr, LcpScratch& sc, cudaStream_t s);
+relcp_status lcp_run(const LcpProblem& pr, LcpScratch& sc, int* blocks, cudaStream_t s);
+// size every buffer of lcp_solve for up to m_cap rows and nb bodies
+relcp_status lcp_reserve(LcpScratch& sc, int64_t m_cap, int64_t nb, bool mixed, cudaStream_t s);
 relcp_status lcp_solve(const LcpProblem& pr, LcpScratch& sc, int* blocks, float* kernel_ms, cudaStream_t s);
 relcp_status lcp_diag_launch(int64_t nrows, const int32_t* ia, const int32_t* ib, View<9, const double> geom,
                              View<7, const double> K, double c, double* diag, cudaStream_t s);

@@ -140,17 +140,23 @@ relcp_status exclusive_scan(const int* in, int* out, int64_t n, ScanScratch& sc,
     }
     const int64_t ntiles = (n + kTile - 1) / kTile;
     if (ntiles > (int64_t)1 << 30) return RELCP_ERR_INVALID_ARG;
-    if (sc.tiles.cap < (size_t)ntiles || !sc.ctr.p) {
-        // fresh words must start cleared; afterwards every call leaves them cleared
-        RELCP_TRY(sc.tiles.ensure((size_t)ntiles, s));
-        RELCP_TRY(sc.ctr.ensure(4, s));
-        RELCP_CUDA(cudaMemsetAsync(sc.tiles.p, 0, sc.tiles.cap * sizeof(unsigned long long), s));
-        RELCP_CUDA(cudaMemsetAsync(sc.ctr.p, 0, 4 * sizeof(int), s));
-    }
+    RELCP_TRY(scan_reserve(sc, n, s));
     int* status = sc.status ? sc.status : sc.ctr.p + 2;  // ctr[2]: the scratch's own error word
     note_launch();
     scan_lookback_kernel<<<(unsigned)ntiles, kScanThreads, 0, s>>>(in, n, out, sc.tiles.p, sc.ctr.p, status);
     RELCP_CUDA(cudaGetLastError());
+    return RELCP_OK;
+}
+
+relcp_status scan_reserve(ScanScratch& sc, int64_t n, cudaStream_t s) {
+    const int64_t ntiles = (n + kTile - 1) / kTile;
+    if (sc.tiles.cap < (size_t)ntiles || !sc.ctr.p) {
+        // fresh words must start cleared; afterwards every call leaves them cleared
+        RELCP_TRY(sc.tiles.ensure((size_t)(ntiles > 0 ? ntiles : 1), s));
+        RELCP_TRY(sc.ctr.ensure(4, s));
+        RELCP_CUDA(cudaMemsetAsync(sc.tiles.p, 0, sc.tiles.cap * sizeof(unsigned long long), s));
+        RELCP_CUDA(cudaMemsetAsync(sc.ctr.p, 0, 4 * sizeof(int), s));
+    }
     return RELCP_OK;
 }
 

@@ -46,7 +46,7 @@ __global__ void __launch_bounds__(kThreads) snsd_kernel(SnsdArgs a) {
         const int i = a.pa[p * a.pstride];
         const int j = a.pb[p * a.pstride];
         double d[3];
-        for (int k = 0; k < 3; ++k) d[k] = min_image(a.x(k, j) - a.x(k, i), a.box[k]);
+        for (int k = 0; k < 3; ++k) d[k] = min_image(a.x(k, j) - a.x(k, i), a.box_dev ? a.box_dev[k] : a.box[k]);
         const Sym3<double> Pa = load_P(a.P, i), Pb = load_P(a.P, j);
         const bool hg = a.guess.c[0] != nullptr;
         snsd_math::PairResult o;

@@ -127,7 +127,7 @@ __global__ void rows_kernel(RowsArgs a) {
                 xi[k] = a.x[k * a.nbodies + i];
                 xj[k] = a.x[k * a.nbodies + j];
             }
-            rate += a.strain_rate * step_math::affine_image_corr(xi, xj, nn, a.box);
+            rate += a.strain_rate * step_math::affine_image_corr(xi, xj, nn, a.box_dev ? a.box_dev : a.box);
         }
         qv = phi + a.c * rate;
     } else {
@@ -155,7 +155,8 @@ __global__ void reuse_kernel(ReuseArgs a) {
     bool need = false;
     if (p < a.npairs && p < *a.np_dev) {
         const PairMemo m = a.memo[a.pv[p]];
-        const bool hit = a.stamp_prev >= 0 && m.stamp == a.stamp_prev && m.pidx >= 0 && m.pidx < a.nprev;
+        const int sp = a.stamp_prev_dev ? *a.stamp_prev_dev : a.stamp_prev;
+        const bool hit = sp >= 0 && m.stamp == sp && m.pidx >= 0;
         a.gamma0[p] = (hit && a.use_gamma) ? m.gamma : 0.0;
         const bool take = hit && a.reuse_snsd;
         if (take) {
@@ -218,7 +219,9 @@ __global__ void trial_kernel(TrialArgs a) {
         // the same arithmetic as the broad phase's displacement check
         double d2 = 0.0;
         for (int k = 0; k < 3; ++k) {
-            const double d = min_image(xt[k] - a.sfac[k] * a.xb[k * n + i], a.la_box[k]);
+            const double sf = a.sfac_dev ? a.sfac_dev[k] : a.sfac[k];
+            const double lb = a.la_box_dev ? a.la_box_dev[k] : a.la_box[k];
+            const double d = min_image(xt[k] - sf * a.xb[k * n + i], lb);
             d2 += d * d;
         }
         dlen = sqrt(d2);

@@ -54,6 +54,7 @@ struct RowsArgs {
     float* gammaf;  // same for the mixed path or null
     int* nrows_dev; // set to base + number of flagged pairs
     int* status;
+    const double* box_dev;  // if set, the box is read here (device) instead of `box`
     // A_0 only: warm start per pair (null: 0) and the pair -> row map (-1: no row)
     const double* gamma0;
     int* rowof;
@@ -68,6 +69,7 @@ struct ReuseArgs {
     const int* pv;          // pair -> cached-list entry
     const PairMemo* memo;   // per entry
     int stamp_prev;         // stamp of the previous step (no memo matches a negative stamp)
+    const int* stamp_prev_dev;  // if set, read here (device) instead
     int reuse_snsd;
     int use_gamma;
     const double* sprev;    // previous step's last trial SNSD output, 10 x sprev_stride (SoA)
@@ -99,6 +101,8 @@ struct TrialArgs {
     // largest |min_image(x_t - sfac xb)| in box `la_box`, atomicMax of its bits
     const double* xb;
     double sfac[3], la_box[3];
+    const double* sfac_dev;    // if set: sfac and la_box read here (device) instead
+    const double* la_box_dev;
     unsigned long long* la_dmax;
     const double* x;
     const double* q;

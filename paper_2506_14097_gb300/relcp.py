@@ -38,6 +38,7 @@ RELCP_FLAG_NO_WARM_START = 2
 RELCP_FLAG_JACOBI = 4
 RELCP_FLAG_NO_SNSD_REUSE = 8
 RELCP_FLAG_LCP_TIMING = 16
+RELCP_FLAG_GRAPH = 32
 MAX_DEPTH_STATS = 64
 
 
@@ -58,7 +59,7 @@ class relcp_step_stats(ctypes.Structure):
                 ("ms_total", c_double), ("steps_done", c_int64), ("guess_used", c_int32),
                 ("newton_fallbacks", c_int32), ("ms_lcp_kernel", c_double), ("lcp_alg_bytes", c_double),
                 ("ms_snsd_kernel", c_double), ("snsd_evals", c_int64), ("lcp_launches", c_int32),
-                ("snsd_launches", c_int32), ("pair_list_rebuilt", c_int32), ("pad0", c_int32),
+                ("snsd_launches", c_int32), ("pair_list_rebuilt", c_int32), ("graph_replayed", c_int32),
                 ("newton_iters_c0", c_int64), ("snsd_c0_evaluated", c_int64),
                 ("host_ms", c_double), ("host_wait_ms", c_double)]
 
