@@ -123,6 +123,9 @@ struct relcp_ctx {
     bool la_ok = false, la_rebuild = true;
     bool prepped = false;  // the last accept pass also ran the next step's prep
     DBuf<StepConst> skd;      // per-step scalars on the device
+    double* hstage = nullptr;  // pinned staging of the body state (relcp_set_bodies / relcp_get_bodies)
+    size_t hstage_cap = 0;
+    DBuf<double> dstage;       // its device counterpart
     StepConst* skh = nullptr; // their pinned host staging copy
     std::vector<StepGraph> graphs;
     int stamp = 0;         // stamp written by the last completed step
@@ -861,16 +864,6 @@ relcp_status step_once(relcp_ctx* c) {
     return step_status;
 }
 
-relcp_status copy_in(const double* src, int64_t count, int32_t ptr_kind, std::vector<double>& out) {
-    out.resize((size_t)count);
-    if (count == 0) return RELCP_OK;
-    if (ptr_kind == RELCP_PTR_DEVICE) {
-        RELCP_CUDA(cudaMemcpy(out.data(), src, count * sizeof(double), cudaMemcpyDeviceToHost));
-    } else {
-        std::memcpy(out.data(), src, count * sizeof(double));
-    }
-    return RELCP_OK;
-}
 
 }  // namespace
 
@@ -922,14 +915,36 @@ relcp_status relcp_set_config(relcp_ctx* c, const relcp_config* cfg) {
     if (!c) return set_error("ctx is NULL"), RELCP_ERR_INVALID_ARG;
     RELCP_TRY(check_config(cfg));
     // the carried SNSD values hold for the current box and precision only
+    bool box_same = true;
     for (int k = 0; k < 3; ++k)
-        if (cfg->box[k] != c->box[k]) c->snsd_ok = false;
-    if (cfg->precision != c->cfg.precision || cfg->skin != c->cfg.skin) c->snsd_ok = false;
-    c->la_ok = false;  // the broad phase checks its cached list again
-    c->prepped = false;
-    drop_graphs(c);
+        if (cfg->box[k] != c->box[k]) box_same = false;
+    if (!box_same || cfg->precision != c->cfg.precision || cfg->skin != c->cfg.skin) c->snsd_ok = false;
+    // the config's box is the current box (it follows the compaction), the rest
+    // is compared with the config in force
+    relcp_config a = *cfg, b = c->cfg;
+    for (int k = 0; k < 3; ++k) a.box[k] = b.box[k] = 0.0;
+    if (!box_same || std::memcmp(&a, &b, sizeof(relcp_config)) != 0) {
+        c->la_ok = false;  // the broad phase checks its cached list again
+        c->prepped = false;
+        drop_graphs(c);
+    }
     c->cfg = *cfg;
     for (int k = 0; k < 3; ++k) c->box[k] = cfg->box[k];
+    return RELCP_OK;
+}
+
+// pinned host staging for the body state (grown on demand)
+static relcp_status ensure_hstage(relcp_ctx* c, size_t count) {
+    if (c->hstage_cap >= count && c->hstage) return RELCP_OK;
+    if (c->hstage) cudaFreeHost(c->hstage);
+    c->hstage = nullptr;
+    c->hstage_cap = 0;
+    const size_t nc = count + count / 4 + 64;
+    if (cudaMallocHost((void**)&c->hstage, nc * sizeof(double)) != cudaSuccess) {
+        set_error("pinned allocation of %zu doubles failed", nc);
+        return RELCP_ERR_CUDA;
+    }
+    c->hstage_cap = nc;
     return RELCP_OK;
 }
 
@@ -944,37 +959,55 @@ relcp_status relcp_set_bodies(relcp_ctx* c, int64_t n, const int32_t* scene_offs
     if (ptr_kind != RELCP_PTR_HOST && ptr_kind != RELCP_PTR_DEVICE)
         return set_error("bad ptr_kind"), RELCP_ERR_INVALID_ARG;
     if (n > 0 && (!x || !q || !semi_axes)) return set_error("x, q, semi_axes required"), RELCP_ERR_INVALID_ARG;
-    std::vector<double> hx, hq, ha, hv, hf;
-    RELCP_TRY(copy_in(x, 3 * n, ptr_kind, hx));
-    RELCP_TRY(copy_in(q, 4 * n, ptr_kind, hq));
-    RELCP_TRY(copy_in(semi_axes, 3 * n, ptr_kind, ha));
-    if (vel) RELCP_TRY(copy_in(vel, 6 * n, ptr_kind, hv));
-    else hv.assign((size_t)(6 * n), 0.0);
-    if (f_ext) RELCP_TRY(copy_in(f_ext, 6 * n, ptr_kind, hf));
-    else hf.assign((size_t)(6 * n), 0.0);
+    cudaStream_t s = c->s;
+    // the caller's rows gathered into one pinned row-major block of 22 doubles
+    // per body: x 3 | q 4 | axes 3 | vel 6 | fext 6
+    RELCP_TRY(ensure_hstage(c, (size_t)(22 * (n > 0 ? n : 1))));
+    double* st = c->hstage;
+    if (n > 0) {
+        if (ptr_kind == RELCP_PTR_DEVICE) RELCP_CUDA(cudaStreamSynchronize(s));
+        auto gather = [&](const double* src, int w, int off) -> relcp_status {
+            if (!src) {
+                for (int64_t i = 0; i < n; ++i)
+                    for (int k = 0; k < w; ++k) st[22 * i + off + k] = 0.0;
+                return RELCP_OK;
+            }
+            if (ptr_kind == RELCP_PTR_DEVICE) {
+                RELCP_CUDA(cudaMemcpy2D(st + off, 22 * sizeof(double), src, w * sizeof(double), w * sizeof(double),
+                                        (size_t)n, cudaMemcpyDeviceToHost));
+            } else {
+                for (int64_t i = 0; i < n; ++i)
+                    for (int k = 0; k < w; ++k) st[22 * i + off + k] = src[w * i + k];
+            }
+            return RELCP_OK;
+        };
+        RELCP_TRY(gather(x, 3, 0));
+        RELCP_TRY(gather(q, 4, 3));
+        RELCP_TRY(gather(semi_axes, 3, 7));
+        RELCP_TRY(gather(vel, 6, 10));
+        RELCP_TRY(gather(f_ext, 6, 16));
+    }
+    double rbmax = 0.0;
     for (int64_t i = 0; i < n; ++i) {
+        const double* r = st + 22 * i;
         double qq = 0;
-        for (int k = 0; k < 4; ++k) qq += hq[4 * i + k] * hq[4 * i + k];
+        for (int k = 0; k < 4; ++k) qq += r[3 + k] * r[3 + k];
         if (!(fabs(sqrt(qq) - 1.0) <= 1e-6))
             return set_error("body %lld: quaternion norm %.17g is not 1", (long long)i, sqrt(qq)),
                    RELCP_ERR_INVALID_ARG;
         for (int k = 0; k < 3; ++k) {
-            if (!std::isfinite(hx[3 * i + k])) return set_error("body %lld: position not finite", (long long)i), RELCP_ERR_INVALID_ARG;
-            if (!(ha[3 * i + k] > 0) || !std::isfinite(ha[3 * i + k]))
+            if (!std::isfinite(r[k])) return set_error("body %lld: position not finite", (long long)i), RELCP_ERR_INVALID_ARG;
+            if (!(r[7 + k] > 0) || !std::isfinite(r[7 + k]))
                 return set_error("body %lld: semi-axes must be finite and > 0", (long long)i), RELCP_ERR_INVALID_ARG;
+            rbmax = r[7 + k] > rbmax ? r[7 + k] : rbmax;
         }
-        for (int k = 0; k < 6; ++k)
-            if (!std::isfinite(hv[6 * i + k]) || !std::isfinite(hf[6 * i + k]))
+        for (int k = 0; k < 12; ++k)
+            if (!std::isfinite(r[10 + k]))
                 return set_error("body %lld: velocity / force not finite", (long long)i), RELCP_ERR_INVALID_ARG;
     }
-    // transpose to SoA
-    auto soa = [&](const std::vector<double>& a, int w) {
-        std::vector<double> o((size_t)(w * n));
-        for (int64_t i = 0; i < n; ++i)
-            for (int k = 0; k < w; ++k) o[(size_t)(k * n + i)] = a[(size_t)(w * i + k)];
-        return o;
-    };
-    cudaStream_t s = c->s;
+    // what the step's carried data still holds depends on what changed: a
+    // bitwise comparison with the current state, on the device
+    const bool same_n = c->has_bodies && c->n == n;
     const int64_t na = n > 0 ? n : 1;
     RELCP_TRY(c->x.ensure(3 * na, s));
     RELCP_TRY(c->q.ensure(4 * na, s));
@@ -990,31 +1023,79 @@ relcp_status relcp_set_bodies(relcp_ctx* c, int64_t n, const int32_t* scene_offs
     RELCP_TRY(c->xt.ensure(3 * na, s));
     RELCP_TRY(c->qt.ensure(4 * na, s));
     RELCP_TRY(c->Pt.ensure(6 * na, s));
+    RELCP_TRY(c->dstage.ensure((size_t)(22 * na), s));
+    int changed = 3;
     if (n > 0) {
-        std::vector<double> sx = soa(hx, 3), sq = soa(hq, 4), sa = soa(ha, 3), sv = soa(hv, 6), sf = soa(hf, 6);
-        RELCP_CUDA(cudaMemcpyAsync(c->x.p, sx.data(), 3 * n * sizeof(double), cudaMemcpyHostToDevice, s));
-        RELCP_CUDA(cudaMemcpyAsync(c->q.p, sq.data(), 4 * n * sizeof(double), cudaMemcpyHostToDevice, s));
-        RELCP_CUDA(cudaMemcpyAsync(c->axes.p, sa.data(), 3 * n * sizeof(double), cudaMemcpyHostToDevice, s));
-        RELCP_CUDA(cudaMemcpyAsync(c->vel.p, sv.data(), 6 * n * sizeof(double), cudaMemcpyHostToDevice, s));
-        RELCP_CUDA(cudaMemcpyAsync(c->fext.p, sf.data(), 6 * n * sizeof(double), cudaMemcpyHostToDevice, s));
-        RELCP_CUDA(cudaMemsetAsync(c->ustep.p, 0, 6 * n * sizeof(double), s));
         for (int k = 0; k < 3; ++k) c->box[k] = c->cfg.box[k];
-        RELCP_TRY(wrap_launch(n, c->x.p, c->box, s));
-        RELCP_CUDA(cudaStreamSynchronize(s));  // host staging buffers go out of scope
+        RELCP_CUDA(cudaMemcpyAsync(c->dstage.p, st, 22 * n * sizeof(double), cudaMemcpyHostToDevice, s));
+        RELCP_CUDA(cudaMemsetAsync(&c->dstep.p->status, 0, sizeof(int), s));
+        LoadArgs la{};
+        la.n = n;
+        la.stage = c->dstage.p;
+        la.x = c->x.p;
+        la.q = c->q.p;
+        la.axes = c->axes.p;
+        la.vel = c->vel.p;
+        la.fext = c->fext.p;
+        for (int k = 0; k < 3; ++k) la.box[k] = c->box[k];
+        la.compare = same_n ? 1 : 0;
+        la.changed = &c->dstep.p->status;  // scratch word, cleared above and by the next step
+        RELCP_TRY(load_bodies_launch(la, s));
+        RELCP_CUDA(cudaMemcpyAsync(&c->hstep->status, &c->dstep.p->status, sizeof(int), cudaMemcpyDeviceToHost, s));
+        RELCP_CUDA(cudaMemsetAsync(c->ustep.p, 0, 6 * n * sizeof(double), s));
+        RELCP_CUDA(cudaStreamSynchronize(s));  // the pinned staging is reused by the next call
+        if (same_n) changed = c->hstep->status;
     }
-    c->memo_ok = false;
-    c->snsd_ok = false;
-    c->la_ok = false;
-    c->prepped = false;
-    drop_graphs(c);
-    c->bp.valid = false;
-    c->rb_max = 0.0;
-    for (size_t i = 0; i < ha.size(); ++i) c->rb_max = ha[i] > c->rb_max ? ha[i] : c->rb_max;
+    if (!same_n || (changed & 2)) {
+        // other bodies or other shapes: nothing carried over
+        c->memo_ok = false;
+        c->bp.valid = false;
+        c->rb_max = rbmax;
+    }
+    if (changed) {
+        // the carried SNSD values, the list look-ahead, the prepared body
+        // operators and the captured graphs hold only for the state they were
+        // made for; the cached pair list (guarded by its displacement check)
+        // and the warm-start gammas (a start only) stay
+        c->snsd_ok = false;
+        c->la_ok = false;
+        c->prepped = false;
+        drop_graphs(c);
+    }
     c->n = n;
     c->has_bodies = true;
     c->steps_done = 0;
     c->nrows = 0;
-    c->npairs = 0;
+    if (changed) c->npairs = 0;
+    return RELCP_OK;
+}
+
+relcp_status relcp_get_bodies_impl(relcp_ctx* c, double* x, double* q, double* vel, int32_t ptr_kind) {
+    const int64_t n = c->n;
+    if (n == 0) return RELCP_OK;
+    cudaStream_t s = c->s;
+    const double* vsrc = c->steps_done > 0 ? c->ustep.p : c->vel.p;
+    RELCP_TRY(c->dstage.ensure((size_t)(22 * n), s));
+    RELCP_TRY(ensure_hstage(c, (size_t)(13 * n)));
+    RELCP_TRY(store_bodies_launch(n, x ? c->x.p : nullptr, q ? c->q.p : nullptr, vel ? vsrc : nullptr,
+                                  c->dstage.p, s));
+    RELCP_CUDA(cudaMemcpyAsync(c->hstage, c->dstage.p, 13 * n * sizeof(double), cudaMemcpyDeviceToHost, s));
+    RELCP_CUDA(cudaStreamSynchronize(s));
+    const double* r0 = c->hstage;
+    auto put = [&](double* dst, int w, int off) -> relcp_status {
+        if (!dst) return RELCP_OK;
+        if (ptr_kind == RELCP_PTR_DEVICE) {
+            RELCP_CUDA(cudaMemcpy2D(dst, w * sizeof(double), r0 + off, 13 * sizeof(double), w * sizeof(double),
+                                    (size_t)n, cudaMemcpyHostToDevice));
+        } else {
+            for (int64_t i = 0; i < n; ++i)
+                for (int k = 0; k < w; ++k) dst[w * i + k] = r0[13 * i + off + k];
+        }
+        return RELCP_OK;
+    };
+    RELCP_TRY(put(x, 3, 0));
+    RELCP_TRY(put(q, 4, 3));
+    RELCP_TRY(put(vel, 6, 7));
     return RELCP_OK;
 }
 
@@ -1034,28 +1115,8 @@ relcp_status relcp_step(relcp_ctx* c, int32_t nsteps) {
 relcp_status relcp_get_bodies(relcp_ctx* c, double* x, double* q, double* vel, int32_t ptr_kind) {
     if (!c) return set_error("ctx is NULL"), RELCP_ERR_INVALID_ARG;
     if (!c->has_bodies) return set_error("no bodies"), RELCP_ERR_STATE;
-    const int64_t n = c->n;
-    if (n == 0) return RELCP_OK;
-    cudaStream_t s = c->s;
-    auto out = [&](const double* dsoa, int w, double* dst) -> relcp_status {
-        if (!dst) return RELCP_OK;
-        std::vector<double> hs((size_t)(w * n)), ha((size_t)(w * n));
-        RELCP_CUDA(cudaMemcpyAsync(hs.data(), dsoa, w * n * sizeof(double), cudaMemcpyDeviceToHost, s));
-        RELCP_CUDA(cudaStreamSynchronize(s));
-        for (int64_t i = 0; i < n; ++i)
-            for (int k = 0; k < w; ++k) ha[(size_t)(w * i + k)] = hs[(size_t)(k * n + i)];
-        if (ptr_kind == RELCP_PTR_DEVICE) {
-            RELCP_CUDA(cudaMemcpyAsync(dst, ha.data(), w * n * sizeof(double), cudaMemcpyHostToDevice, s));
-            RELCP_CUDA(cudaStreamSynchronize(s));
-        } else {
-            std::memcpy(dst, ha.data(), w * n * sizeof(double));
-        }
-        return RELCP_OK;
-    };
-    RELCP_TRY(out(c->x.p, 3, x));
-    RELCP_TRY(out(c->q.p, 4, q));
-    RELCP_TRY(out(c->steps_done > 0 ? c->ustep.p : c->vel.p, 6, vel));
-    return RELCP_OK;
+    if (ptr_kind != RELCP_PTR_HOST && ptr_kind != RELCP_PTR_DEVICE) return set_error("bad ptr_kind"), RELCP_ERR_INVALID_ARG;
+    return relcp_get_bodies_impl(c, x, q, vel, ptr_kind);
 }
 
 relcp_status relcp_get_box(relcp_ctx* c, double* box3) {
@@ -1171,6 +1232,7 @@ void relcp_destroy(relcp_ctx* c) {
     c->r_invdf.release(s);
     c->dstep.release(s);
     c->skd.release(s);
+    c->dstage.release(s);
     c->bp.xb.release(s);
     c->bp.dmax.release(s);
     c->s1prev.release(s);
@@ -1190,6 +1252,7 @@ void relcp_destroy(relcp_ctx* c) {
     for (cudaEvent_t e : c->events) cudaEventDestroy(e);
     if (c->hstep) cudaFreeHost(c->hstep);
     if (c->skh) cudaFreeHost(c->skh);
+    if (c->hstage) cudaFreeHost(c->hstage);
     delete c;
 }
 

@@ -303,6 +303,58 @@ relcp_status memo_save_launch(const MemoSaveArgs& a, cudaStream_t s) {
     return RELCP_OK;
 }
 
+__global__ void load_bodies_kernel(LoadArgs a) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int ch = 0;
+    if (i < a.n) {
+        const double* r = a.stage + 22 * i;
+        const int64_t n = a.n;
+        auto put = [&](double* dst, int k, double v, int bit) {
+            if (a.compare && __double_as_longlong(dst[k * n + i]) != __double_as_longlong(v)) ch |= bit;
+            dst[k * n + i] = v;
+        };
+        for (int k = 0; k < 3; ++k) put(a.x, k, step_math::wrap_coord(r[k], a.box[k]), 1);
+        for (int k = 0; k < 4; ++k) put(a.q, k, r[3 + k], 1);
+        for (int k = 0; k < 3; ++k) put(a.axes, k, r[7 + k], 2);
+        for (int k = 0; k < 6; ++k) put(a.vel, k, r[10 + k], 1);
+        for (int k = 0; k < 6; ++k) put(a.fext, k, r[16 + k], 1);
+    }
+    if (a.compare) {
+        for (int o = 16; o > 0; o >>= 1) ch |= __shfl_xor_sync(0xffffffffu, ch, o);
+        if ((threadIdx.x & 31) == 0 && ch) atomicOr(a.changed, ch);
+    }
+}
+
+__global__ void store_bodies_kernel(int64_t n, const double* __restrict__ x, const double* __restrict__ q,
+                                    const double* __restrict__ vel, double* __restrict__ out) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double* r = out + 13 * i;
+    if (x)
+        for (int k = 0; k < 3; ++k) r[k] = x[k * n + i];
+    if (q)
+        for (int k = 0; k < 4; ++k) r[3 + k] = q[k * n + i];
+    if (vel)
+        for (int k = 0; k < 6; ++k) r[7 + k] = vel[k * n + i];
+}
+
+relcp_status load_bodies_launch(const LoadArgs& a, cudaStream_t s) {
+    if (a.n == 0) return RELCP_OK;
+    note_launch();
+    load_bodies_kernel<<<nb(a.n), kT, 0, s>>>(a);
+    RELCP_CUDA(cudaGetLastError());
+    return RELCP_OK;
+}
+
+relcp_status store_bodies_launch(int64_t n, const double* x, const double* q, const double* vel, double* out,
+                                 cudaStream_t s) {
+    if (n == 0) return RELCP_OK;
+    note_launch();
+    store_bodies_kernel<<<nb(n), kT, 0, s>>>(n, x, q, vel, out);
+    RELCP_CUDA(cudaGetLastError());
+    return RELCP_OK;
+}
+
 relcp_status wrap_launch(int64_t n, double* x, const double box[3], cudaStream_t s) {
     if (n == 0) return RELCP_OK;
     note_launch();

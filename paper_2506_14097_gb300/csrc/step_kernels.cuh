@@ -137,6 +137,28 @@ relcp_status rows_launch(const RowsArgs& a, cudaStream_t s);
 relcp_status trial_launch(const TrialArgs& a, cudaStream_t s);
 relcp_status accept_launch(const AcceptArgs& a, cudaStream_t s);
 relcp_status wrap_launch(int64_t n, double* x, const double box[3], cudaStream_t s);
+
+// Body state in from a row-major staging block [x 3 | q 4 | axes 3 | vel 6 |
+// fext 6] per body (22 doubles), transposed into the SoA arrays with x
+// wrapped into the box.  With `compare`, *changed gets bit 0 if x, q, vel or
+// fext differ (bitwise) from what the arrays held, bit 1 if the axes differ.
+struct LoadArgs {
+    int64_t n;
+    const double* stage;
+    double* x;
+    double* q;
+    double* axes;
+    double* vel;
+    double* fext;
+    double box[3];
+    int compare;
+    int* changed;
+};
+relcp_status load_bodies_launch(const LoadArgs& a, cudaStream_t s);
+// x (3), q (4), vel (6) of every body into a row-major block (13 doubles per
+// body; a null source is skipped and its columns are left unwritten)
+relcp_status store_bodies_launch(int64_t n, const double* x, const double* q, const double* vel, double* out,
+                                 cudaStream_t s);
 relcp_status reuse_launch(const ReuseArgs& a, cudaStream_t s);
 relcp_status memo_save_launch(const MemoSaveArgs& a, cudaStream_t s);
 

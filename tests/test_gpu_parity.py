@@ -464,3 +464,57 @@ def test_graph_replay_matches_direct_launches(relcp_gpu, learned_start):
         assert np.array_equal(a, b)
     assert launches[0] == launches[1]
     assert replayed[0] >= 10 and replayed[1] == 0
+
+
+def test_host_roundtrip_keeps_carried_state(relcp_gpu):
+    """relcp_set_bodies with the state relcp_get_bodies returned (and an
+    unchanged config) keeps everything a step carries to the next: the
+    trajectory is bit for bit that of stepping without the round trip and the
+    carried SNSD values stay in use.  Moving one body drops the carried SNSD
+    values; changing a semi-axis drops the cached pair list too."""
+    R = relcp_gpu
+    sc = scenes.suspension_scene(seed=7, n=2048, phi=0.15, phi_final=0.45, steps=200, dt=5e-3)
+    amin = float(sc.axes.min())
+    cfg = R.make_config(dynamics=R.RELCP_OVERDAMPED, precision=R.RELCP_MIXED, dt=sc.dt, eps_ncp=1e-3 * amin,
+                        box=tuple(sc.box), skin=0.1 * amin, strain_rate=sc.meta["strain_rate"], length_scale=amin)
+    a = R.Simulation(cfg)
+    a.set_bodies(sc.x, sc.q, sc.axes)
+    for _ in range(20):
+        a.step(1, allow=(R.RELCP_ERR_NOT_CONVERGED,))
+    b = R.Simulation(cfg)
+    b.set_bodies(sc.x, sc.q, sc.axes)
+    evals = []
+    for _ in range(20):
+        b.step(1, allow=(R.RELCP_ERR_NOT_CONVERGED,))
+        st = b.stats()
+        evals.append((st.snsd_c0_evaluated, st.n_pairs))
+        x, q, v = b.bodies()
+        box = R.relcp_get_box(b.ctx)
+        for k in range(3):
+            cfg.box[k] = box[k]
+        R.relcp_set_config(b.ctx, cfg)
+        b.set_bodies(x, q, sc.axes)
+    for u, w in zip(a.bodies()[:2], b.bodies()[:2]):
+        assert np.array_equal(u, w)
+    assert sum(e for e, _ in evals[1:]) < 0.2 * sum(n for _, n in evals[1:])
+    # a moved body: the next C^k evaluates every pair again, while the cached
+    # pair list (checked by its displacement bound) survives most such moves
+    rebuilt = 0
+    for _ in range(6):
+        x, q, _ = b.bodies()
+        x[0, 0] += 1e-9
+        b.set_bodies(x, q, sc.axes)
+        b.step(1, allow=(R.RELCP_ERR_NOT_CONVERGED,))
+        st = b.stats()
+        assert st.snsd_c0_evaluated == st.n_pairs
+        rebuilt += st.pair_list_rebuilt
+    assert rebuilt <= 2
+    # a changed shape: the cached pair list is rebuilt
+    x, q, _ = b.bodies()
+    ax = sc.axes.copy()
+    ax[0, 0] *= 1.01
+    b.set_bodies(x, q, ax)
+    b.step(1, allow=(R.RELCP_ERR_NOT_CONVERGED,))
+    assert b.stats().pair_list_rebuilt == 1
+    a.close()
+    b.close()
