@@ -96,6 +96,9 @@ enum {
                                       gamma of the same pair (the solution is the same within lcp_tol) */
     RELCP_FLAG_JACOBI = 4u,        /* projected-gradient steps scaled by 1 / A_aa, BB lengths in the
                                       matching metric (same solution, fewer iterations on uneven rows) */
+    RELCP_FLAG_HOST_STAGING = 64u, /* relcp_set_bodies / relcp_get_bodies copy host arrays through pinned
+                                      staging buffers even where the device can read and write the caller's
+                                      host memory in place (through the host page tables) */
     RELCP_FLAG_GRAPH = 32u,        /* replay the step's first level (broad-phase filter to overlap test, the
                                       LCP launched between the two graphs) from CUDA graphs captured per
                                       configuration; pays off only while the cached pair list is not rebuilt

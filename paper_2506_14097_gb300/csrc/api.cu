@@ -12,6 +12,7 @@
 // buffers and decide the loop; everything else stays on the device.
 #include <atomic>
 #include <chrono>
+#include <climits>
 #include <functional>
 #include <cstdarg>
 #include <cstring>
@@ -126,6 +127,9 @@ struct relcp_ctx {
     double* hstage = nullptr;  // pinned staging of the body state (relcp_set_bodies / relcp_get_bodies)
     size_t hstage_cap = 0;
     DBuf<double> dstage;       // its device counterpart
+    bool pageable_ok = false;  // the device reads / writes pageable host memory (host page tables)
+    DBuf<BodyCheck> dcheck;    // relcp_set_bodies' validation result
+    BodyCheck* hcheck = nullptr;  // pinned
     StepConst* skh = nullptr; // their pinned host staging copy
     std::vector<StepGraph> graphs;
     int stamp = 0;         // stamp written by the last completed step
@@ -894,6 +898,18 @@ relcp_status relcp_create(const relcp_config* cfg, void* cuda_stream, relcp_ctx*
         st = RELCP_ERR_CUDA;
     }
     if (st == RELCP_OK) st = c->skd.ensure(1, c->s);
+    if (st == RELCP_OK) st = c->dcheck.ensure(1, c->s);
+    if (st == RELCP_OK && cudaMallocHost((void**)&c->hcheck, sizeof(BodyCheck)) != cudaSuccess) {
+        set_error("pinned allocation failed");
+        st = RELCP_ERR_CUDA;
+    }
+    if (st == RELCP_OK) {
+        int dev = 0, pma = 0, pht = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&pma, cudaDevAttrPageableMemoryAccess, dev);
+        cudaDeviceGetAttribute(&pht, cudaDevAttrPageableMemoryAccessUsesHostPageTables, dev);
+        c->pageable_ok = pma == 1 && pht == 1;
+    }
     if (st == RELCP_OK && cudaMallocHost((void**)&c->skh, sizeof(StepConst)) != cudaSuccess) {
         set_error("pinned allocation failed");
         st = RELCP_ERR_CUDA;
@@ -933,6 +949,29 @@ relcp_status relcp_set_config(relcp_ctx* c, const relcp_config* cfg) {
     return RELCP_OK;
 }
 
+relcp_status after_set_bodies(relcp_ctx* c, int64_t n, bool same_n, int changed, double rbmax);
+
+// the per-body state and scratch arrays for n bodies
+static relcp_status ensure_body_arrays(relcp_ctx* c, int64_t n) {
+    cudaStream_t s = c->s;
+    const int64_t na = n > 0 ? n : 1;
+    RELCP_TRY(c->x.ensure(3 * na, s));
+    RELCP_TRY(c->q.ensure(4 * na, s));
+    RELCP_TRY(c->axes.ensure(3 * na, s));
+    RELCP_TRY(c->vel.ensure(6 * na, s));
+    RELCP_TRY(c->fext.ensure(6 * na, s));
+    RELCP_TRY(c->P.ensure(6 * na, s));
+    RELCP_TRY(c->K.ensure(7 * na, s));
+    RELCP_TRY(c->rb.ensure(na, s));
+    RELCP_TRY(c->ufree.ensure(6 * na, s));
+    RELCP_TRY(c->uc.ensure(6 * na, s));
+    RELCP_TRY(c->ustep.ensure(6 * na, s));
+    RELCP_TRY(c->xt.ensure(3 * na, s));
+    RELCP_TRY(c->qt.ensure(4 * na, s));
+    RELCP_TRY(c->Pt.ensure(6 * na, s));
+    return RELCP_OK;
+}
+
 // pinned host staging for the body state (grown on demand)
 static relcp_status ensure_hstage(relcp_ctx* c, size_t count) {
     if (c->hstage_cap >= count && c->hstage) return RELCP_OK;
@@ -960,8 +999,65 @@ relcp_status relcp_set_bodies(relcp_ctx* c, int64_t n, const int32_t* scene_offs
         return set_error("bad ptr_kind"), RELCP_ERR_INVALID_ARG;
     if (n > 0 && (!x || !q || !semi_axes)) return set_error("x, q, semi_axes required"), RELCP_ERR_INVALID_ARG;
     cudaStream_t s = c->s;
-    // the caller's rows gathered into one pinned row-major block of 22 doubles
-    // per body: x 3 | q 4 | axes 3 | vel 6 | fext 6
+    const bool same_n = c->has_bodies && c->n == n;
+    const bool direct = ptr_kind == RELCP_PTR_DEVICE || (c->pageable_ok && !(c->cfg.flags & RELCP_FLAG_HOST_STAGING));
+    if (direct && n > 0) {
+        // the device reads the caller's arrays in place: one pass validates,
+        // compares with the current state and copies the rows to the device
+        // stage, writing nothing to the state; the load follows only for a
+        // valid, changed state
+        RELCP_TRY(ensure_body_arrays(c, n));
+        RELCP_TRY(c->dstage.ensure((size_t)(22 * n), s));
+        for (int k = 0; k < 3; ++k) c->box[k] = c->cfg.box[k];
+        BodyCheck init{};
+        init.bad_key = ~0ull;
+        *c->hcheck = init;
+        RELCP_CUDA(cudaMemcpyAsync(c->dcheck.p, c->hcheck, sizeof(BodyCheck), cudaMemcpyHostToDevice, s));
+        CheckArgs ca{};
+        ca.n = n;
+        ca.in = BodyIn{x, q, semi_axes, vel, f_ext};
+        ca.x = c->x.p;
+        ca.q = c->q.p;
+        ca.axes = c->axes.p;
+        ca.vel = c->vel.p;
+        ca.fext = c->fext.p;
+        for (int k = 0; k < 3; ++k) ca.box[k] = c->box[k];
+        ca.compare = same_n ? 1 : 0;
+        ca.stage = c->dstage.p;
+        ca.out = c->dcheck.p;
+        RELCP_TRY(check_bodies_launch(ca, s));
+        RELCP_CUDA(cudaMemcpyAsync(c->hcheck, c->dcheck.p, sizeof(BodyCheck), cudaMemcpyDeviceToHost, s));
+        RELCP_CUDA(cudaStreamSynchronize(s));  // the caller's arrays are free again after this
+        const BodyCheck chk = *c->hcheck;
+        if (chk.bad_key != ~0ull) {
+            const int bits = (int)(chk.bad_key & 15);
+            const long long i = (long long)(chk.bad_key >> 4);
+            const char* why = (bits & 1)   ? "quaternion norm is not 1"
+                              : (bits & 2) ? "position not finite"
+                              : (bits & 4) ? "semi-axes must be finite and > 0"
+                                           : "velocity / force not finite";
+            return set_error("body %lld: %s", i, why), RELCP_ERR_INVALID_ARG;
+        }
+        const int changed = same_n ? chk.changed : 3;
+        if (changed) {
+            LoadArgs la{};
+            la.n = n;
+            la.stage = c->dstage.p;
+            la.x = c->x.p;
+            la.q = c->q.p;
+            la.axes = c->axes.p;
+            la.vel = c->vel.p;
+            la.fext = c->fext.p;
+            for (int k = 0; k < 3; ++k) la.box[k] = c->box[k];
+            la.compare = 0;
+            la.changed = nullptr;
+            RELCP_TRY(load_bodies_launch(la, s));
+            RELCP_CUDA(cudaMemsetAsync(c->ustep.p, 0, 6 * n * sizeof(double), s));
+        }
+        return after_set_bodies(c, n, same_n, changed, __builtin_bit_cast(double, chk.rbmax_bits));
+    }
+    // otherwise the caller's rows are gathered into one pinned row-major block
+    // of 22 doubles per body: x 3 | q 4 | axes 3 | vel 6 | fext 6
     RELCP_TRY(ensure_hstage(c, (size_t)(22 * (n > 0 ? n : 1))));
     double* st = c->hstage;
     if (n > 0) {
@@ -1007,22 +1103,8 @@ relcp_status relcp_set_bodies(relcp_ctx* c, int64_t n, const int32_t* scene_offs
     }
     // what the step's carried data still holds depends on what changed: a
     // bitwise comparison with the current state, on the device
-    const bool same_n = c->has_bodies && c->n == n;
     const int64_t na = n > 0 ? n : 1;
-    RELCP_TRY(c->x.ensure(3 * na, s));
-    RELCP_TRY(c->q.ensure(4 * na, s));
-    RELCP_TRY(c->axes.ensure(3 * na, s));
-    RELCP_TRY(c->vel.ensure(6 * na, s));
-    RELCP_TRY(c->fext.ensure(6 * na, s));
-    RELCP_TRY(c->P.ensure(6 * na, s));
-    RELCP_TRY(c->K.ensure(7 * na, s));
-    RELCP_TRY(c->rb.ensure(na, s));
-    RELCP_TRY(c->ufree.ensure(6 * na, s));
-    RELCP_TRY(c->uc.ensure(6 * na, s));
-    RELCP_TRY(c->ustep.ensure(6 * na, s));
-    RELCP_TRY(c->xt.ensure(3 * na, s));
-    RELCP_TRY(c->qt.ensure(4 * na, s));
-    RELCP_TRY(c->Pt.ensure(6 * na, s));
+    RELCP_TRY(ensure_body_arrays(c, n));
     RELCP_TRY(c->dstage.ensure((size_t)(22 * na), s));
     int changed = 3;
     if (n > 0) {
@@ -1046,6 +1128,13 @@ relcp_status relcp_set_bodies(relcp_ctx* c, int64_t n, const int32_t* scene_offs
         RELCP_CUDA(cudaStreamSynchronize(s));  // the pinned staging is reused by the next call
         if (same_n) changed = c->hstep->status;
     }
+    return after_set_bodies(c, n, same_n, changed, rbmax);
+}
+
+// what the context keeps after new bodies: everything for an unchanged state;
+// the pair list (guarded by its displacement check) and the warm starts for
+// moved bodies; nothing for other bodies or shapes
+relcp_status after_set_bodies(relcp_ctx* c, int64_t n, bool same_n, int changed, double rbmax) {
     if (!same_n || (changed & 2)) {
         // other bodies or other shapes: nothing carried over
         c->memo_ok = false;
@@ -1075,6 +1164,12 @@ relcp_status relcp_get_bodies_impl(relcp_ctx* c, double* x, double* q, double* v
     if (n == 0) return RELCP_OK;
     cudaStream_t s = c->s;
     const double* vsrc = c->steps_done > 0 ? c->ustep.p : c->vel.p;
+    if (ptr_kind == RELCP_PTR_DEVICE || (c->pageable_ok && !(c->cfg.flags & RELCP_FLAG_HOST_STAGING))) {
+        // written in place into the caller's arrays
+        RELCP_TRY(store_direct_launch(n, c->x.p, c->q.p, vsrc, x, q, vel, s));
+        RELCP_CUDA(cudaStreamSynchronize(s));
+        return RELCP_OK;
+    }
     RELCP_TRY(c->dstage.ensure((size_t)(22 * n), s));
     RELCP_TRY(ensure_hstage(c, (size_t)(13 * n)));
     RELCP_TRY(store_bodies_launch(n, x ? c->x.p : nullptr, q ? c->q.p : nullptr, vel ? vsrc : nullptr,
@@ -1233,6 +1328,7 @@ void relcp_destroy(relcp_ctx* c) {
     c->dstep.release(s);
     c->skd.release(s);
     c->dstage.release(s);
+    c->dcheck.release(s);
     c->bp.xb.release(s);
     c->bp.dmax.release(s);
     c->s1prev.release(s);
@@ -1253,6 +1349,7 @@ void relcp_destroy(relcp_ctx* c) {
     if (c->hstep) cudaFreeHost(c->hstep);
     if (c->skh) cudaFreeHost(c->skh);
     if (c->hstage) cudaFreeHost(c->hstage);
+    if (c->hcheck) cudaFreeHost(c->hcheck);
     delete c;
 }
 

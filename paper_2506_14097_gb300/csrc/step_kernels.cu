@@ -338,6 +338,93 @@ __global__ void store_bodies_kernel(int64_t n, const double* __restrict__ x, con
         for (int k = 0; k < 6; ++k) r[7 + k] = vel[k * n + i];
 }
 
+__global__ void check_bodies_kernel(CheckArgs a) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int bad = 0, ch = 0;
+    double amax = 0.0;
+    if (i < a.n) {
+        const int64_t n = a.n;
+        double x[3], q[4], ax[3], v[6], f[6];
+        for (int k = 0; k < 3; ++k) {
+            x[k] = a.in.x[3 * i + k];
+            ax[k] = a.in.axes[3 * i + k];
+        }
+        for (int k = 0; k < 4; ++k) q[k] = a.in.q[4 * i + k];
+        for (int k = 0; k < 6; ++k) {
+            v[k] = a.in.vel ? a.in.vel[6 * i + k] : 0.0;
+            f[k] = a.in.fext ? a.in.fext[6 * i + k] : 0.0;
+        }
+        const double qq = q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3];
+        if (!(fabs(sqrt(qq) - 1.0) <= 1e-6)) bad |= 1;
+        for (int k = 0; k < 3; ++k) {
+            if (!isfinite(x[k])) bad |= 2;
+            if (!(ax[k] > 0) || !isfinite(ax[k])) bad |= 4;
+            amax = fmax(amax, ax[k]);
+        }
+        for (int k = 0; k < 6; ++k)
+            if (!isfinite(v[k]) || !isfinite(f[k])) bad |= 8;
+        double* r = a.stage + 22 * i;
+        for (int k = 0; k < 3; ++k) {
+            r[k] = x[k];
+            r[7 + k] = ax[k];
+        }
+        for (int k = 0; k < 4; ++k) r[3 + k] = q[k];
+        for (int k = 0; k < 6; ++k) {
+            r[10 + k] = v[k];
+            r[16 + k] = f[k];
+        }
+        if (a.compare && !bad) {
+            auto diff = [](double u, double w) { return __double_as_longlong(u) != __double_as_longlong(w); };
+            for (int k = 0; k < 3; ++k)
+                if (diff(a.x[k * n + i], step_math::wrap_coord(x[k], a.box[k]))) ch |= 1;
+            for (int k = 0; k < 4; ++k)
+                if (diff(a.q[k * n + i], q[k])) ch |= 1;
+            for (int k = 0; k < 3; ++k)
+                if (diff(a.axes[k * n + i], ax[k])) ch |= 2;
+            for (int k = 0; k < 6; ++k)
+                if (diff(a.vel[k * n + i], v[k]) || diff(a.fext[k * n + i], f[k])) ch |= 1;
+        }
+        if (bad) atomicMin(&a.out->bad_key, ((unsigned long long)i << 4) | (unsigned long long)bad);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        ch |= __shfl_xor_sync(0xffffffffu, ch, o);
+        amax = fmax(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        if (ch) atomicOr(&a.out->changed, ch);
+        if (amax > 0.0) atomicMax(&a.out->rbmax_bits, (unsigned long long)__double_as_longlong(amax));
+    }
+}
+
+__global__ void store_direct_kernel(int64_t n, const double* __restrict__ x, const double* __restrict__ q,
+                                    const double* __restrict__ vel, double* ox, double* oq, double* ov) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    if (ox)
+        for (int k = 0; k < 3; ++k) ox[3 * i + k] = x[k * n + i];
+    if (oq)
+        for (int k = 0; k < 4; ++k) oq[4 * i + k] = q[k * n + i];
+    if (ov)
+        for (int k = 0; k < 6; ++k) ov[6 * i + k] = vel[k * n + i];
+}
+
+relcp_status check_bodies_launch(const CheckArgs& a, cudaStream_t s) {
+    if (a.n == 0) return RELCP_OK;
+    note_launch();
+    check_bodies_kernel<<<nb(a.n), kT, 0, s>>>(a);
+    RELCP_CUDA(cudaGetLastError());
+    return RELCP_OK;
+}
+
+relcp_status store_direct_launch(int64_t n, const double* x, const double* q, const double* vel, double* ox,
+                                 double* oq, double* ov, cudaStream_t s) {
+    if (n == 0) return RELCP_OK;
+    note_launch();
+    store_direct_kernel<<<nb(n), kT, 0, s>>>(n, x, q, vel, ox, oq, ov);
+    RELCP_CUDA(cudaGetLastError());
+    return RELCP_OK;
+}
+
 relcp_status load_bodies_launch(const LoadArgs& a, cudaStream_t s) {
     if (a.n == 0) return RELCP_OK;
     note_launch();

@@ -155,6 +155,43 @@ struct LoadArgs {
     int* changed;
 };
 relcp_status load_bodies_launch(const LoadArgs& a, cudaStream_t s);
+
+// Body state read in place from the caller's row-major arrays (device memory,
+// or host memory the device reaches through the host page tables): x n x 3,
+// q n x 4, axes n x 3, vel / fext n x 6 (null: zeros).
+struct BodyIn {
+    const double* x;
+    const double* q;
+    const double* axes;
+    const double* vel;
+    const double* fext;
+};
+// validation and comparison, writing nothing to the state
+struct BodyCheck {
+    unsigned long long bad_key;  // min over invalid bodies of (index << 4 | reasons), all ones: none;
+                                 // reasons 1: |q| not 1 within 1e-6, 2: position not finite,
+                                 // 4: semi-axis not > 0 or not finite, 8: velocity / force not finite
+    unsigned long long rbmax_bits;  // bits of the largest semi-axis
+    int changed;                    // as LoadArgs::changed
+    int pad;
+};
+struct CheckArgs {
+    int64_t n;
+    BodyIn in;
+    const double* x;  // current SoA state (compared when `compare`)
+    const double* q;
+    const double* axes;
+    const double* vel;
+    const double* fext;
+    double box[3];
+    int compare;
+    double* stage;  // the rows copied out as load_bodies_launch reads them (22 doubles per body)
+    BodyCheck* out;
+};
+relcp_status check_bodies_launch(const CheckArgs& a, cudaStream_t s);
+// x, q, vel (SoA) into the caller's row-major arrays (any may be null)
+relcp_status store_direct_launch(int64_t n, const double* x, const double* q, const double* vel, double* ox,
+                                 double* oq, double* ov, cudaStream_t s);
 // x (3), q (4), vel (6) of every body into a row-major block (13 doubles per
 // body; a null source is skipped and its columns are left unwritten)
 relcp_status store_bodies_launch(int64_t n, const double* x, const double* q, const double* vel, double* out,

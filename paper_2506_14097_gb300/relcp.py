@@ -39,6 +39,7 @@ RELCP_FLAG_JACOBI = 4
 RELCP_FLAG_NO_SNSD_REUSE = 8
 RELCP_FLAG_LCP_TIMING = 16
 RELCP_FLAG_GRAPH = 32
+RELCP_FLAG_HOST_STAGING = 64
 MAX_DEPTH_STATS = 64
 
 

@@ -307,9 +307,11 @@ def test_empty_and_single_body(relcp_gpu):
     sim.close()
 
 
-def test_invalid_arguments_rejected(relcp_gpu):
+@pytest.mark.parametrize("staging", [False, True], ids=["in_place", "pinned_staging"])
+def test_invalid_arguments_rejected(relcp_gpu, staging):
     R = relcp_gpu
-    cfg = R.make_config(dt=1e-3, eps_ncp=1e-3, box=(10, 10, 10), skin=0.05)
+    cfg = R.make_config(dt=1e-3, eps_ncp=1e-3, box=(10, 10, 10), skin=0.05,
+                        flags=R.RELCP_FLAG_HOST_STAGING if staging else 0)
     sim = R.Simulation(cfg)
     x = np.array([[1.0, 2.0, 3.0]])
     with pytest.raises(R.RelcpError) as e:
@@ -328,6 +330,71 @@ def test_invalid_arguments_rejected(relcp_gpu):
     assert e.value.status == R.RELCP_ERR_STATE
     sim.close()
     sim2.close()
+
+
+@pytest.mark.parametrize("staging", [False, True], ids=["in_place", "pinned_staging"])
+def test_rejected_bodies_leave_state_untouched(relcp_gpu, staging):
+    """Invalid body input names the first invalid body and changes nothing:
+    stepping on afterwards is bit for bit stepping without the call."""
+    R = relcp_gpu
+    sc = scenes.lattice_scene(seed=4, n=512, spacing=1.9, dt=1e-2, vel_sigma=2.0, omega_sigma=1.0)
+    amin = float(sc.axes.min())
+    cfg = R.make_config(dynamics=R.RELCP_INERTIAL, dt=1e-2, eps_ncp=1e-3 * amin, box=tuple(sc.box),
+                        skin=0.1 * amin, length_scale=amin, flags=R.RELCP_FLAG_HOST_STAGING if staging else 0)
+    a, b = R.Simulation(cfg), R.Simulation(cfg)
+    for s_ in (a, b):
+        s_.set_bodies(sc.x, sc.q, sc.axes, sc.vel)
+        s_.step(3)
+    cases = []
+    q = sc.q.copy()
+    q[300] *= 1.5
+    q[450] *= 2.0
+    cases.append(((sc.x, q, sc.axes, sc.vel), "body 300: quaternion"))
+    x = sc.x.copy()
+    x[77, 1] = np.inf
+    cases.append(((x, sc.q, sc.axes, sc.vel), "body 77: position"))
+    ax = sc.axes.copy()
+    ax[200, 2] = 0.0
+    x2 = sc.x.copy()
+    x2[201, 0] = np.nan
+    cases.append(((x2, sc.q, ax, sc.vel), "body 200: semi-axes"))
+    v = sc.vel.copy()
+    v[5, 4] = np.nan
+    cases.append(((sc.x, sc.q, sc.axes, v), "body 5: velocity"))
+    for args, msg in cases:
+        with pytest.raises(R.RelcpError) as e:
+            b.set_bodies(*args)
+        assert e.value.status == R.RELCP_ERR_INVALID_ARG and msg in str(e.value)
+    a.step(3)
+    b.step(3)
+    for u, w in zip(a.bodies(), b.bodies()):
+        assert np.array_equal(u, w)
+    a.close()
+    b.close()
+
+
+def test_device_body_io_matches_host(relcp_gpu):
+    """Body state given and read back as device arrays steps bit for bit as
+    the same state given and read back as host arrays."""
+    R = relcp_gpu
+    sc = scenes.lattice_scene(seed=6, n=700, spacing=1.9, dt=1e-2, vel_sigma=2.0, omega_sigma=1.0)
+    amin = float(sc.axes.min())
+    cfg = R.make_config(dynamics=R.RELCP_INERTIAL, dt=1e-2, eps_ncp=1e-3 * amin, box=tuple(sc.box),
+                        skin=0.1 * amin, length_scale=amin)
+    a, b = R.Simulation(cfg), R.Simulation(cfg)
+    a.set_bodies(sc.x, sc.q, sc.axes, sc.vel)
+    R.relcp_set_bodies(b.ctx, dev(sc.x), dev(sc.q), dev(sc.axes), dev(sc.vel))
+    b.n = sc.x.shape[0]
+    a.step(4)
+    b.step(4)
+    xd = torch.zeros((b.n, 3), dtype=torch.float64, device="cuda")
+    qd = torch.zeros((b.n, 4), dtype=torch.float64, device="cuda")
+    vd = torch.zeros((b.n, 6), dtype=torch.float64, device="cuda")
+    R.relcp_get_bodies(b.ctx, xd, qd, vd)
+    for u, w in zip(a.bodies(), (xd, qd, vd)):
+        assert np.array_equal(u, w.cpu().numpy())
+    a.close()
+    b.close()
 
 
 def test_fault_injection_and_caps(relcp_gpu, orc):
@@ -466,7 +533,8 @@ def test_graph_replay_matches_direct_launches(relcp_gpu, learned_start):
     assert replayed[0] >= 10 and replayed[1] == 0
 
 
-def test_host_roundtrip_keeps_carried_state(relcp_gpu):
+@pytest.mark.parametrize("staging", [False, True], ids=["in_place", "pinned_staging"])
+def test_host_roundtrip_keeps_carried_state(relcp_gpu, staging):
     """relcp_set_bodies with the state relcp_get_bodies returned (and an
     unchanged config) keeps everything a step carries to the next: the
     trajectory is bit for bit that of stepping without the round trip and the
@@ -476,7 +544,8 @@ def test_host_roundtrip_keeps_carried_state(relcp_gpu):
     sc = scenes.suspension_scene(seed=7, n=2048, phi=0.15, phi_final=0.45, steps=200, dt=5e-3)
     amin = float(sc.axes.min())
     cfg = R.make_config(dynamics=R.RELCP_OVERDAMPED, precision=R.RELCP_MIXED, dt=sc.dt, eps_ncp=1e-3 * amin,
-                        box=tuple(sc.box), skin=0.1 * amin, strain_rate=sc.meta["strain_rate"], length_scale=amin)
+                        box=tuple(sc.box), skin=0.1 * amin, strain_rate=sc.meta["strain_rate"], length_scale=amin,
+                        flags=R.RELCP_FLAG_HOST_STAGING if staging else 0)
     a = R.Simulation(cfg)
     a.set_bodies(sc.x, sc.q, sc.axes)
     for _ in range(20):
