@@ -173,7 +173,7 @@ def new_sim(R, sc, precision, guess, timing, stream, mlp_params):
 
 
 def run_gpu_arm(R, torch, sc, precision, guess, steps, warmup, flush, stream, nvtx_from=None, mlp_params=None,
-                timing="lcp"):
+                timing="lcp", nvtx_to=None):
     """W warm-up steps on one context, then `steps` timed steps from the initial
     state on a fresh context.  Returns per-step times and accumulated stats."""
     x, q, axes = (np.ascontiguousarray(a) for a in (sc.x, sc.q, sc.axes))
@@ -196,6 +196,8 @@ def run_gpu_arm(R, torch, sc, precision, guess, steps, warmup, flush, stream, nv
             flush.zero_()
             if nvtx_from is not None and k == nvtx_from:
                 torch.cuda.nvtx.range_push("relcp_profile")
+            if nvtx_from is not None and nvtx_to is not None and k == nvtx_to:
+                torch.cuda.nvtx.range_pop()
             ev[k][0].record(stream)
             st = sim.step(1, allow=(R.RELCP_ERR_NOT_CONVERGED,))
             ev[k][1].record(stream)
@@ -222,7 +224,7 @@ def run_gpu_arm(R, torch, sc, precision, guess, steps, warmup, flush, stream, nv
             acc["newton_c0"] = acc.get("newton_c0", 0) + s.newton_iters_c0
             acc["pairs_total"] = acc.get("pairs_total", 0) + s.n_pairs
     torch.cuda.synchronize()
-    if nvtx_from is not None and nvtx_from < steps:
+    if nvtx_from is not None and nvtx_from < steps and (nvtx_to is None or nvtx_to >= steps):
         torch.cuda.nvtx.range_pop()
     acc["launches"] = R.relcp_kernel_launches() - launches0
     times = [a.elapsed_time(b) for a, b in ev]
@@ -350,6 +352,9 @@ def main():
                     help="scenes of the batched-scene measurement (0 skips it)")
     ap.add_argument("--nvtx-from", type=int, default=None,
                     help="profiling aid: wrap timed steps >= this index in the NVTX range relcp_profile")
+    ap.add_argument("--nvtx-to", type=int, default=None, help="profiling aid: end of that range (exclusive)")
+    ap.add_argument("--step-times", default=None,
+                    help="write the headline run's per-step CUDA-event times (ms, one per line) to this file")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -405,7 +410,10 @@ def main():
     clocks.start()
     t_wall0 = time.perf_counter()
     times, acc = run_gpu_arm(R, torch, sc, precision, guess, args.steps, args.warmup, flush, stream, args.nvtx_from,
-                             mlp_params)
+                             mlp_params, nvtx_to=args.nvtx_to)
+    if args.step_times and rank == 0:
+        with open(args.step_times, "w") as f:
+            f.write("".join("%.6f\n" % t for t in times))
     t_wall = time.perf_counter() - t_wall0
     clk = clocks.stop()
     total_ms = float(sum(times))

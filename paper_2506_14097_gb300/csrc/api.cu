@@ -76,6 +76,14 @@ struct DevStep {
     int pad;
 };
 
+// the per-step scalars and the step's device-side counters in one block, so
+// that the start of a step uploads both with one copy (the DevStep half of
+// the pinned upload image stays zero)
+struct StepBlock {
+    StepConst k;
+    DevStep d;
+};
+
 // a captured first level of a step (see step_once)
 struct StepGraph {
     std::vector<uintptr_t> key;
@@ -98,7 +106,8 @@ struct relcp_ctx {
     int64_t npairs = 0;
     DBuf<double> s0, s1;  // SNSD outputs at C^k and at the trial (10 x npairs)
     DBuf<int> it0, it1, flags, fscan;
-    DBuf<DevStep> dstep;
+    DBuf<StepBlock> sblk;      // StepConst + DevStep on the device
+    StepBlock* hup = nullptr;  // pinned upload image (DevStep half zero)
     DevStep* hstep = nullptr;  // pinned host copy (asynchronous readback)
     // rows (capacity rcap, SoA)
     int64_t nrows = 0, nrows0 = 0, rcap = 0;
@@ -123,14 +132,12 @@ struct relcp_ctx {
     // phase needs no host round trip
     bool la_ok = false, la_rebuild = true;
     bool prepped = false;  // the last accept pass also ran the next step's prep
-    DBuf<StepConst> skd;      // per-step scalars on the device
     double* hstage = nullptr;  // pinned staging of the body state (relcp_set_bodies / relcp_get_bodies)
     size_t hstage_cap = 0;
     DBuf<double> dstage;       // its device counterpart
     bool pageable_ok = false;  // the device reads / writes pageable host memory (host page tables)
     DBuf<BodyCheck> dcheck;    // relcp_set_bodies' validation result
     BodyCheck* hcheck = nullptr;  // pinned
-    StepConst* skh = nullptr; // their pinned host staging copy
     std::vector<StepGraph> graphs;
     int stamp = 0;         // stamp written by the last completed step
     bool memo_ok = false;  // memo and s1prev describe the current state
@@ -280,7 +287,7 @@ static void step_key(relcp_ctx* c, int64_t PC, std::vector<uintptr_t>& key) {
                           c->lcp.inc_count.p, c->lcp.inc_off.p, c->lcp.inc_tmp.p, c->lcp.inc.p, c->lcp.packf.p,
                           c->lcp.packd.p, c->lcp.partials.p, c->scan.tiles.p, c->scan.ctr.p, c->bp.scan.tiles.p,
                           c->bp.scan.ctr.p, c->lcp.scan.tiles.p, c->lcp.scan.ctr.p, c->mlp.image.p, c->mlp.guess.p,
-                          c->dstep.p, c->hstep, c->skd.p, c->skh};
+                          c->sblk.p, c->hstep, c->hup};
     for (const void* q : ptrs) add(q);
     for (size_t k = 0; k < 2 && k < c->events.size(); ++k) add(c->events[k]);
 }
@@ -315,12 +322,12 @@ relcp_status step_once(relcp_ctx* c) {
     RELCP_TRY(tm.start((cfg.flags & RELCP_FLAG_PHASE_TIMING) != 0, (cfg.flags & RELCP_FLAG_LCP_TIMING) != 0, s,
                        &c->events));
     std::vector<std::pair<int, int>> snsd_marks, lcp_marks, lcpk_marks;
-    DevStep* ds = c->dstep.p;
+    DevStep* ds = &c->sblk.p->d;
     const bool memo_ok = c->memo_ok;
     const bool prepped = c->prepped;
 
     // per-step scalars, read by the kernels from device memory
-    StepConst& sk = *c->skh;
+    StepConst& sk = c->hup->k;
     for (int k = 0; k < 3; ++k) {
         sk.box0[k] = box0[k];
         sk.box1[k] = box1[k];
@@ -329,8 +336,8 @@ relcp_status step_once(relcp_ctx* c) {
         for (int k = 0; k < 3; ++k) sk.sfac[k] = 1.0;
     sk.stamp_prev = memo_ok ? c->stamp : -1;
     sk.pad = 0;
-    const double* box0_dev = c->skd.p->box0;
-    const double* box1_dev = c->skd.p->box1;
+    const double* box0_dev = c->sblk.p->k.box0;
+    const double* box1_dev = c->sblk.p->k.box1;
 
     // bodies: normalised q, P, K, rb, U_free
     PrepArgs pa{};
@@ -397,8 +404,8 @@ relcp_status step_once(relcp_ctx* c) {
         return RELCP_OK;
     };
     auto head = [&]() -> relcp_status {
-        RELCP_CUDA(cudaMemsetAsync(ds, 0, sizeof(DevStep), s));
-        RELCP_CUDA(cudaMemcpyAsync(c->skd.p, c->skh, sizeof(StepConst), cudaMemcpyHostToDevice, s));
+        // StepConst and a zeroed DevStep in one copy
+        RELCP_CUDA(cudaMemcpyAsync(c->sblk.p, c->hup, sizeof(StepBlock), cudaMemcpyHostToDevice, s));
         if (!prepped) RELCP_TRY(prep_launch(pa, s));
         return RELCP_OK;
     };
@@ -441,7 +448,7 @@ relcp_status step_once(relcp_ctx* c) {
     ru.pv = c->bp.pv.p;
     ru.memo = c->bp.memo.p;
     ru.stamp_prev = sk.stamp_prev;
-    ru.stamp_prev_dev = &c->skd.p->stamp_prev;
+    ru.stamp_prev_dev = &c->sblk.p->k.stamp_prev;
     ru.reuse_snsd = c->snsd_ok && !(cfg.flags & RELCP_FLAG_NO_SNSD_REUSE);
     ru.use_gamma = !(cfg.flags & RELCP_FLAG_NO_WARM_START);
     ru.sprev = c->s1prev.p;
@@ -501,6 +508,13 @@ relcp_status step_once(relcp_ctx* c) {
     ra.uc = c->uc.p;
     ra.K = c->K.p;
     ra.nrows_dev = &ds->nrows;
+    ra.nrows0_dev = &ds->nrows0;
+    // the trial's per-level fields (largest overlap, look-ahead displacement,
+    // violator count + pad) are cleared by each level's row kernel
+    static_assert(offsetof(DevStep, la_dmax) == offsetof(DevStep, maxov_bits) + 8 &&
+                      offsetof(DevStep, nviol) == offsetof(DevStep, maxov_bits) + 16,
+                  "per-level fields of DevStep must be three consecutive words");
+    ra.clear3 = &ds->maxov_bits;
     ra.status = &ds->status;
     ra.gamma0 = c->gamma0.p;
     ra.rowof = c->rowof.p;
@@ -572,7 +586,7 @@ relcp_status step_once(relcp_ctx* c) {
     if (broadphase_lookahead_params(c->bp, n, box1, ta.sfac)) {
         ta.xb = c->bp.xb.p;
         for (int k = 0; k < 3; ++k) ta.la_box[k] = box1[k];
-        ta.sfac_dev = c->skd.p->sfac;
+        ta.sfac_dev = c->sblk.p->k.sfac;
         ta.la_box_dev = box1_dev;
         ta.la_dmax = &ds->la_dmax;
     }
@@ -605,8 +619,8 @@ relcp_status step_once(relcp_ctx* c) {
     };
     // after the LCP: trial, overlap test, readback
     auto post_lcp = [&]() -> relcp_status {
-        // the per-level fields (largest overlap, look-ahead displacement, violator count)
-        RELCP_CUDA(cudaMemsetAsync(&ds->maxov_bits, 0, 2 * sizeof(unsigned long long) + 2 * sizeof(int), s));
+        // (the per-level fields were cleared by the level's row kernel, or with
+        // the whole DevStep at the start of the step)
         RELCP_TRY(trial_launch(ta, s));
         {
             int e0 = tm.mark();
@@ -628,7 +642,7 @@ relcp_status step_once(relcp_ctx* c) {
     // level 0 after the broad phase, up to the LCP's incidence CSR
     auto level0_pre = [&]() -> relcp_status {
         if (np > 0) {
-            RELCP_CUDA(cudaMemcpyAsync(&ds->np, npd, sizeof(int), cudaMemcpyDeviceToDevice, s));
+            if (!fast_bp) RELCP_CUDA(cudaMemcpyAsync(&ds->np, npd, sizeof(int), cudaMemcpyDeviceToDevice, s));
             RELCP_TRY(reuse_launch(ru, s));
             if (learned)
                 RELCP_TRY(mlp_guess(c->mlp, np, c->pa.p, c->pb.p, xv, View<4, const double>::soa(c->q.p, n),
@@ -644,7 +658,6 @@ relcp_status step_once(relcp_ctx* c) {
             RELCP_TRY(flag_le_launch(np, npd, c->s0.p, cfg.phi_skin, c->flags.p, s));
             RELCP_TRY(exclusive_scan(c->flags.p, c->fscan.p, np, c->scan, s));
             RELCP_TRY(rows_launch(ra, s));
-            RELCP_CUDA(cudaMemcpyAsync(&ds->nrows0, &ds->nrows, sizeof(int), cudaMemcpyDeviceToDevice, s));
         }
         make_pr(pr);
         lcp_l0 = tm.mark();
@@ -654,7 +667,8 @@ relcp_status step_once(relcp_ctx* c) {
     auto level0_fast_pre = [&]() -> relcp_status {
         t_begin = tm.mark();
         RELCP_TRY(head());
-        RELCP_TRY(broadphase_filter_async(n, c->x.p, c->rb.p, box0, box0_dev, cfg.skin, c->pa, c->pb, c->bp, s));
+        RELCP_TRY(broadphase_filter_async(n, c->x.p, c->rb.p, box0, box0_dev, cfg.skin, c->pa, c->pb, c->bp, s,
+                                          &ds->np));
         t_bp = tm.mark();
         return level0_pre();
     };
@@ -781,6 +795,7 @@ relcp_status step_once(relcp_ctx* c) {
         RowsArgs rb2 = ra;
         rb2.gamma0 = nullptr;
         rb2.rowof = nullptr;
+        rb2.nrows0_dev = nullptr;
         bind_rows(rb2);
         rb2.snsd = c->s1.p;
         rb2.base = c->nrows;
@@ -830,6 +845,8 @@ relcp_status step_once(relcp_ctx* c) {
     // the next step's prep in the same pass, on the accepted state in the next box
     aa.next = pa;
     for (int k = 0; k < 3; ++k) aa.next.box[k] = box1[k];
+    aa.keep = cfg.dynamics == RELCP_OVERDAMPED;
+    aa.Pt = c->Pt.p;
     RELCP_TRY(accept_launch(aa, s));
     c->prepped = true;
     for (int k = 0; k < 3; ++k) c->box[k] = box1[k];
@@ -892,12 +909,11 @@ relcp_status relcp_create(const relcp_config* cfg, void* cuda_stream, relcp_ctx*
     c->cfg = *cfg;
     c->s = (cudaStream_t)cuda_stream;
     for (int k = 0; k < 3; ++k) c->box[k] = cfg->box[k];
-    relcp_status st = c->dstep.ensure(1, c->s);
+    relcp_status st = c->sblk.ensure(1, c->s);
     if (st == RELCP_OK && cudaMallocHost((void**)&c->hstep, sizeof(DevStep)) != cudaSuccess) {
         set_error("pinned allocation failed");
         st = RELCP_ERR_CUDA;
     }
-    if (st == RELCP_OK) st = c->skd.ensure(1, c->s);
     if (st == RELCP_OK) st = c->dcheck.ensure(1, c->s);
     if (st == RELCP_OK && cudaMallocHost((void**)&c->hcheck, sizeof(BodyCheck)) != cudaSuccess) {
         set_error("pinned allocation failed");
@@ -910,16 +926,21 @@ relcp_status relcp_create(const relcp_config* cfg, void* cuda_stream, relcp_ctx*
         cudaDeviceGetAttribute(&pht, cudaDevAttrPageableMemoryAccessUsesHostPageTables, dev);
         c->pageable_ok = pma == 1 && pht == 1;
     }
-    if (st == RELCP_OK && cudaMallocHost((void**)&c->skh, sizeof(StepConst)) != cudaSuccess) {
+    if (st == RELCP_OK && cudaMallocHost((void**)&c->hup, sizeof(StepBlock)) != cudaSuccess) {
         set_error("pinned allocation failed");
         st = RELCP_ERR_CUDA;
     }
+    if (st == RELCP_OK) std::memset(c->hup, 0, sizeof(StepBlock));
     if (st == RELCP_OK) {
         // the context's prefix sums report a look-back timeout in the step's status word
-        c->scan.status = c->bp.scan.status = c->lcp.scan.status = &c->dstep.p->status;
+        c->scan.status = c->bp.scan.status = c->lcp.scan.status = &c->sblk.p->d.status;
     }
     if (st != RELCP_OK) {
-        c->dstep.release(c->s);
+        c->sblk.release(c->s);
+        c->dcheck.release(c->s);
+        if (c->hstep) cudaFreeHost(c->hstep);
+        if (c->hup) cudaFreeHost(c->hup);
+        if (c->hcheck) cudaFreeHost(c->hcheck);
         delete c;
         return st;
     }
@@ -1110,7 +1131,7 @@ relcp_status relcp_set_bodies(relcp_ctx* c, int64_t n, const int32_t* scene_offs
     if (n > 0) {
         for (int k = 0; k < 3; ++k) c->box[k] = c->cfg.box[k];
         RELCP_CUDA(cudaMemcpyAsync(c->dstage.p, st, 22 * n * sizeof(double), cudaMemcpyHostToDevice, s));
-        RELCP_CUDA(cudaMemsetAsync(&c->dstep.p->status, 0, sizeof(int), s));
+        RELCP_CUDA(cudaMemsetAsync(&c->sblk.p->d.status, 0, sizeof(int), s));
         LoadArgs la{};
         la.n = n;
         la.stage = c->dstage.p;
@@ -1121,9 +1142,9 @@ relcp_status relcp_set_bodies(relcp_ctx* c, int64_t n, const int32_t* scene_offs
         la.fext = c->fext.p;
         for (int k = 0; k < 3; ++k) la.box[k] = c->box[k];
         la.compare = same_n ? 1 : 0;
-        la.changed = &c->dstep.p->status;  // scratch word, cleared above and by the next step
+        la.changed = &c->sblk.p->d.status;  // scratch word, cleared above and by the next step
         RELCP_TRY(load_bodies_launch(la, s));
-        RELCP_CUDA(cudaMemcpyAsync(&c->hstep->status, &c->dstep.p->status, sizeof(int), cudaMemcpyDeviceToHost, s));
+        RELCP_CUDA(cudaMemcpyAsync(&c->hstep->status, &c->sblk.p->d.status, sizeof(int), cudaMemcpyDeviceToHost, s));
         RELCP_CUDA(cudaMemsetAsync(c->ustep.p, 0, 6 * n * sizeof(double), s));
         RELCP_CUDA(cudaStreamSynchronize(s));  // the pinned staging is reused by the next call
         if (same_n) changed = c->hstep->status;
@@ -1325,8 +1346,7 @@ void relcp_destroy(relcp_ctx* c) {
     c->Kf.release(s);
     c->r_invd.release(s);
     c->r_invdf.release(s);
-    c->dstep.release(s);
-    c->skd.release(s);
+    c->sblk.release(s);
     c->dstage.release(s);
     c->dcheck.release(s);
     c->bp.xb.release(s);
@@ -1347,7 +1367,7 @@ void relcp_destroy(relcp_ctx* c) {
     cudaStreamSynchronize(s);
     for (cudaEvent_t e : c->events) cudaEventDestroy(e);
     if (c->hstep) cudaFreeHost(c->hstep);
-    if (c->skh) cudaFreeHost(c->skh);
+    if (c->hup) cudaFreeHost(c->hup);
     if (c->hstage) cudaFreeHost(c->hstage);
     if (c->hcheck) cudaFreeHost(c->hcheck);
     delete c;

@@ -446,7 +446,7 @@ relcp_status broadphase_lookahead(int64_t n, const double* x_soa, const double b
 
 relcp_status broadphase_filter_async(int64_t n, const double* x_soa, const double* rb, const double box[3],
                                      const double* box_dev, double skin, DBuf<int>& pa, DBuf<int>& pb,
-                                     BroadphaseScratch& sc, cudaStream_t s) {
+                                     BroadphaseScratch& sc, cudaStream_t s, int* np_copy) {
     const int64_t nv = sc.vn;
     if (n < 2 || nv == 0) return RELCP_OK;
     View<3, const double> xv = View<3, const double>::soa(x_soa, n);
@@ -455,7 +455,7 @@ relcp_status broadphase_filter_async(int64_t n, const double* x_soa, const doubl
                                                                                   box[0], box[1], box[2], box_dev,
                                                                                   skin, sc.vflag.p);
     RELCP_CUDA(cudaGetLastError());
-    RELCP_TRY(exclusive_scan(sc.vflag.p, sc.vscan.p, nv, sc.scan, s));
+    RELCP_TRY(exclusive_scan(sc.vflag.p, sc.vscan.p, nv, sc.scan, s, np_copy));
     note_launch();
     compact_kernel<<<(unsigned)((nv + kThreads - 1) / kThreads), kThreads, 0, s>>>(nv, sc.vpa.p, sc.vpb.p,
                                                                                   sc.vflag.p, sc.vscan.p, pa.p, pb.p,

@@ -194,7 +194,10 @@ struct ScanScratch {
     int* status = nullptr;           // DEV_TIMEOUT goes here if set (else into ctr[2])
 };
 // out[i] = sum_{j<i} in[i]; out[n] = total.  `out` has n+1 entries.
-relcp_status exclusive_scan(const int* in, int* out, int64_t n, ScanScratch& sc, cudaStream_t s);
+// out[0..n] = exclusive prefix sums of in[0..n) and the total; the total is
+// also written to *total_copy when that is not null
+relcp_status exclusive_scan(const int* in, int* out, int64_t n, ScanScratch& sc, cudaStream_t s,
+                            int* total_copy = nullptr);
 // RELCP_ERR_TIMEOUT if a scan on this scratch (without a status word) timed
 // out; synchronises s
 relcp_status scan_error(ScanScratch& sc, cudaStream_t s);
@@ -262,10 +265,11 @@ bool broadphase_lookahead_params(const BroadphaseScratch& sc, int64_t n, const d
 // The cached list's exact filter and compaction without a host round trip:
 // pairs into pa, pb, sc.pv (capacity sc.vn), their count at sc.vscan.p[sc.vn].
 // Valid only when the bound held for these positions (checked beforehand).
-// box_dev (may be null): the box read on the device instead of `box`
+// box_dev (may be null): the box read on the device instead of `box`;
+// np_copy (may be null): a second word that receives the count
 relcp_status broadphase_filter_async(int64_t n, const double* x_soa, const double* rb, const double box[3],
                                      const double* box_dev, double skin, DBuf<int>& pa, DBuf<int>& pb,
-                                     BroadphaseScratch& sc, cudaStream_t s);
+                                     BroadphaseScratch& sc, cudaStream_t s, int* np_copy = nullptr);
 
 // ---------------------------------------------------------------------------
 // SNSD (snsd.cu)

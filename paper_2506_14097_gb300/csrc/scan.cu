@@ -7,8 +7,10 @@
 // processed by a block that started after the blocks of tiles 0..t-1: those
 // are resident and never wait on later tiles, hence every wait below ends.
 // A tile publishes its aggregate, then its inclusive prefix, as one 64-bit
-// word (status in the high half, value in the low half); thread 0 walks back
-// over the predecessors, adding aggregates until it meets an inclusive prefix.
+// word (status in the high half, value in the low half); warp 0 walks back
+// over the predecessors 32 at a time (one word per lane), adding aggregates up
+// to the nearest inclusive prefix, so a look-back costs one L2 round trip per
+// 32 predecessors rather than one per predecessor.
 // The spin on a predecessor is bounded: past the limit the block records
 // DEV_TIMEOUT in the caller's status word (or the scratch's own) and goes on.
 // The last block to finish clears the tile words and the counters, so the next
@@ -19,7 +21,7 @@ namespace relcp {
 
 namespace {
 
-constexpr int kScanThreads = 256;
+constexpr int kScanThreads = 512;
 constexpr int kScanItems = 8;
 constexpr int kTile = kScanThreads * kScanItems;
 constexpr long long kLookbackLimit = 1ll << 22;
@@ -68,8 +70,8 @@ __device__ __forceinline__ unsigned long long ld_relaxed64(const unsigned long l
 __global__ void __launch_bounds__(kScanThreads) scan_lookback_kernel(const int* __restrict__ in, int64_t n,
                                                                      int* __restrict__ out,
                                                                      unsigned long long* tiles, int* ctr,
-                                                                     int* status) {
-    __shared__ int sh_tile, sh_excl;
+                                                                     int* status, int* total_copy) {
+    __shared__ int sh_tile, sh_excl, sh_last;
     if (threadIdx.x == 0) sh_tile = atomicAdd(&ctr[0], 1);
     __syncthreads();
     const int t = sh_tile;
@@ -83,31 +85,45 @@ __global__ void __launch_bounds__(kScanThreads) scan_lookback_kernel(const int* 
     }
     int tot;
     const int inc = block_inclusive_scan(s, &tot);
-    if (threadIdx.x == 0) {
+    if (threadIdx.x < 32) {
+        const int lane = threadIdx.x;
         int excl = 0;
         if (t == 0) {
-            st_relaxed64(tiles, kInclusive | (unsigned)tot);
+            if (lane == 0) st_relaxed64(tiles, kInclusive | (unsigned)tot);
         } else {
-            st_relaxed64(tiles + t, kAggregate | (unsigned)tot);
+            if (lane == 0) st_relaxed64(tiles + t, kAggregate | (unsigned)tot);
             long long spins = 0;
-            for (int j = t - 1; j >= 0;) {
-                const unsigned long long w = ld_relaxed64(tiles + j);
+            bool timed_out = false;
+            // window of predecessors t-1-32w-lane; a lane before tile 0 reads
+            // an inclusive zero
+            for (int top = t - 1;;) {
+                const int j = top - lane;
+                const unsigned long long w = j >= 0 ? ld_relaxed64(tiles + j) : kInclusive;
                 const unsigned long long st = w & (3ull << 32);
-                if (st == 0) {
+                if (__any_sync(0xffffffffu, st == 0)) {
+                    // a predecessor has not published yet (warp-uniform decision)
                     if (++spins > kLookbackLimit) {
-                        atomicOr(status, DEV_TIMEOUT);
+                        timed_out = true;
                         break;
                     }
                     if (spins > 64) __nanosleep(32);
                     continue;
                 }
-                excl += (int)(unsigned)(w & 0xffffffffull);
-                if (st == kInclusive) break;
-                --j;
+                const unsigned incl = __ballot_sync(0xffffffffu, st == kInclusive);
+                const int upto = incl ? __ffs(incl) - 1 : 31;  // nearest inclusive prefix
+                int c = lane <= upto ? (int)(unsigned)(w & 0xffffffffull) : 0;
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+                excl += c;
+                if (incl) break;
+                top -= 32;
             }
-            st_relaxed64(tiles + t, kInclusive | (unsigned)(excl + tot));
+            if (lane == 0) {
+                if (timed_out) atomicOr(status, DEV_TIMEOUT);
+                st_relaxed64(tiles + t, kInclusive | (unsigned)(excl + tot));
+            }
         }
-        sh_excl = excl;
+        if (lane == 0) sh_excl = excl;
     }
     __syncthreads();
     int run = sh_excl + inc - s;
@@ -116,26 +132,34 @@ __global__ void __launch_bounds__(kScanThreads) scan_lookback_kernel(const int* 
         if (base + k < n) out[base + k] = run;
         run += v[k];
     }
-    if (t == (int)gridDim.x - 1 && threadIdx.x == 0) out[n] = sh_excl + tot;
+    if (t == (int)gridDim.x - 1 && threadIdx.x == 0) {
+        out[n] = sh_excl + tot;
+        if (total_copy) *total_copy = sh_excl + tot;
+    }
     // the last block to finish clears the tiles and counters for the next call
     __syncthreads();
     if (threadIdx.x == 0) {
         __threadfence();
-        if (atomicAdd(&ctr[1], 1) == (int)gridDim.x - 1) {
-            for (unsigned j = 0; j < gridDim.x; ++j) st_relaxed64(tiles + j, 0ull);
+        sh_last = atomicAdd(&ctr[1], 1) == (int)gridDim.x - 1;
+    }
+    __syncthreads();
+    if (sh_last) {
+        for (unsigned j = threadIdx.x; j < gridDim.x; j += blockDim.x) st_relaxed64(tiles + j, 0ull);
+        if (threadIdx.x == 0) {
             ctr[0] = 0;
             ctr[1] = 0;
-            __threadfence();
         }
+        __threadfence();
     }
 }
 
 }  // namespace
 
-relcp_status exclusive_scan(const int* in, int* out, int64_t n, ScanScratch& sc, cudaStream_t s) {
+relcp_status exclusive_scan(const int* in, int* out, int64_t n, ScanScratch& sc, cudaStream_t s, int* total_copy) {
     if (n < 0) return RELCP_ERR_INVALID_ARG;
     if (n == 0) {
         RELCP_CUDA(cudaMemsetAsync(out, 0, sizeof(int), s));
+        if (total_copy) RELCP_CUDA(cudaMemsetAsync(total_copy, 0, sizeof(int), s));
         return RELCP_OK;
     }
     const int64_t ntiles = (n + kTile - 1) / kTile;
@@ -143,7 +167,8 @@ relcp_status exclusive_scan(const int* in, int* out, int64_t n, ScanScratch& sc,
     RELCP_TRY(scan_reserve(sc, n, s));
     int* status = sc.status ? sc.status : sc.ctr.p + 2;  // ctr[2]: the scratch's own error word
     note_launch();
-    scan_lookback_kernel<<<(unsigned)ntiles, kScanThreads, 0, s>>>(in, n, out, sc.tiles.p, sc.ctr.p, status);
+    scan_lookback_kernel<<<(unsigned)ntiles, kScanThreads, 0, s>>>(in, n, out, sc.tiles.p, sc.ctr.p, status,
+                                                                    total_copy);
     RELCP_CUDA(cudaGetLastError());
     return RELCP_OK;
 }

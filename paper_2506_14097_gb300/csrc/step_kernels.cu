@@ -56,6 +56,36 @@ __device__ __forceinline__ void prep_one(const PrepArgs& a, int64_t i) {
     for (int k = 0; k < 6; ++k) a.ufree[k * n + i] = b.ufree[k];
 }
 
+// the next step's prep after an accepted trial (overdamped): q was normalised
+// by the trial and P at that orientation is Pt; K, Kf and rb depend on the
+// semi-axes and the config only, so they hold; U_free = vel + K F_ext (+ the
+// affine background velocity at the accepted position)
+__device__ __forceinline__ void prep_keep(const PrepArgs& a, const double* __restrict__ Pt, int64_t i) {
+    const int64_t n = a.n;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) a.P[k * n + i] = Pt[k * n + i];
+    double K[7], u[6], f[6];
+#pragma unroll
+    for (int k = 0; k < 7; ++k) K[k] = a.K[k * n + i];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+        u[k] = a.vel[k * n + i];
+        f[k] = a.fext[k * n + i];
+    }
+    // the same operations, in the same order, as prep_body
+    u[0] += K[0] * f[0];
+    u[1] += K[0] * f[1];
+    u[2] += K[0] * f[2];
+    u[3] += K[1] * f[3] + K[4] * f[4] + K[5] * f[5];
+    u[4] += K[4] * f[3] + K[2] * f[4] + K[6] * f[5];
+    u[5] += K[5] * f[3] + K[6] * f[4] + K[3] * f[5];
+    if (a.strain_rate != 0.0)
+        for (int k = 0; k < 3; ++k)
+            if (a.box[k] > 0.0) u[k] += a.strain_rate * (a.x[k * n + i] - 0.5 * a.box[k]);
+#pragma unroll
+    for (int k = 0; k < 6; ++k) a.ufree[k * n + i] = u[k];
+}
+
 __global__ void prep_kernel(PrepArgs a) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < a.n) prep_one(a, i);
@@ -82,6 +112,8 @@ __global__ void rows_kernel(RowsArgs a) {
     if (p == 0) {
         int64_t total = a.base + a.scan[a.npairs];
         *a.nrows_dev = (int)(total < a.cap ? total : a.cap);
+        if (a.nrows0_dev) *a.nrows0_dev = (int)(total < a.cap ? total : a.cap);
+        if (a.clear3) a.clear3[0] = a.clear3[1] = a.clear3[2] = 0ull;
     }
     if (p >= a.npairs) return;
     int64_t r = a.flags[p] ? a.base + a.scan[p] : -1;
@@ -241,7 +273,10 @@ __global__ void accept_kernel(AcceptArgs a) {
     for (int k = 0; k < 4; ++k) a.q[k * n + i] = a.qt[k * n + i];
     if (a.inertial)
         for (int k = 0; k < 6; ++k) a.vel[k * n + i] = a.ustep[k * n + i];
-    if (a.next.n == n) prep_one(a.next, i);  // reads back this thread's own writes
+    if (a.next.n == n) {  // reads back this thread's own writes
+        if (a.keep) prep_keep(a.next, a.Pt, i);
+        else prep_one(a.next, i);
+    }
 }
 
 __global__ void wrap_kernel(int64_t n, double* x, double L0, double L1, double L2) {

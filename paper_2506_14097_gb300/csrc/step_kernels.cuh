@@ -53,6 +53,8 @@ struct RowsArgs {
     double* gamma;  // warm start of new rows set to 0 (FP64 path) or null
     float* gammaf;  // same for the mixed path or null
     int* nrows_dev; // set to base + number of flagged pairs
+    int* nrows0_dev;  // if set, also receives that count (|A_0|)
+    unsigned long long* clear3;  // if set, three words zeroed (the per-level fields of the next trial)
     int* status;
     const double* box_dev;  // if set, the box is read here (device) instead of `box`
     // A_0 only: warm start per pair (null: 0) and the pair -> row map (-1: no row)
@@ -122,6 +124,12 @@ struct AcceptArgs {
     // optional: the next step's prep on the accepted state, in the same pass
     // (next.n == 0: none)
     PrepArgs next;
+    // overdamped, with K, Kf and rb computed for the current semi-axes and
+    // config: the next prep keeps them, takes q as the trial normalised it
+    // and P = Pt (the shape matrix of the accepted trial orientation), so
+    // only U_free is recomputed
+    int keep;
+    const double* Pt;
     const double* xt;
     const double* qt;
     const double* ustep;

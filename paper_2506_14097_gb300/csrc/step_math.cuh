@@ -150,7 +150,11 @@ __device__ __forceinline__ void trial_body(const double x[3], const double q[4],
 }
 
 // position wrapped into [0, L) on a periodic axis
-__device__ __forceinline__ double wrap_coord(double v, double L) { return L > 0.0 ? v - L * floor(v / L) : v; }
+// (v itself when already inside, without the division)
+__device__ __forceinline__ double wrap_coord(double v, double L) {
+    if (!(L > 0.0) || (v >= 0.0 && v < L)) return v;
+    return v - L * floor(v / L);
+}
 
 }  // namespace step_math
 }  // namespace relcp

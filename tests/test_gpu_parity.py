@@ -46,7 +46,7 @@ def cfg_pair(R, orc, sc, dynamics, precision, dt=None, **kw):
 # broad phase
 # ---------------------------------------------------------------------------
 @pytest.mark.parametrize("n,side,skin", [(0, 10.0, 0.1), (1, 10.0, 0.1), (300, 12.0, 0.05), (5000, 40.0, 0.04),
-                                         (20000, 55.0, 0.05)])
+                                         (20000, 55.0, 0.05), (32768, 30.0, 0.05)])
 def test_broadphase_bitexact(relcp_gpu, orc, n, side, skin):
     R = relcp_gpu
     rng = np.random.default_rng(100 + n)
