@@ -155,6 +155,8 @@ __global__ void max_reduce(int64_t n, const double* __restrict__ v, double* __re
 // scaling s = L / Lb (per periodic axis) taken out: |min_image(x - s xb)|
 __global__ void disp_kernel(int64_t n, const double* __restrict__ x, const double* __restrict__ xb, double s0,
                             double s1, double s2, double L0, double L1, double L2, unsigned long long* dmax) {
+    pdl_wait();
+    pdl_trigger();
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     double d2 = 0.0;
     if (i < n) {
@@ -173,6 +175,8 @@ __global__ void disp_kernel(int64_t n, const double* __restrict__ x, const doubl
 __global__ void filter_kernel(int64_t nv, const int* __restrict__ vpa, const int* __restrict__ vpb,
                               View<3, const double> x, const double* __restrict__ rb, double L0, double L1,
                               double L2, const double* __restrict__ Ldev, double skin, int* __restrict__ flag) {
+    pdl_wait();
+    pdl_trigger();
     int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= nv) return;
     if (Ldev) {
@@ -186,6 +190,8 @@ __global__ void filter_kernel(int64_t nv, const int* __restrict__ vpa, const int
 __global__ void compact_kernel(int64_t nv, const int* __restrict__ vpa, const int* __restrict__ vpb,
                                const int* __restrict__ flag, const int* __restrict__ pos, int* __restrict__ pa,
                                int* __restrict__ pb, int* __restrict__ pv) {
+    pdl_wait();
+    pdl_trigger();
     int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (v >= nv || !flag[v]) return;
     pa[pos[v]] = vpa[v];
@@ -198,6 +204,8 @@ __global__ void compact_kernel(int64_t nv, const int* __restrict__ vpa, const in
 __global__ void memo_remap_kernel(int64_t nv, const int* __restrict__ vpa, const int* __restrict__ vpb,
                                   int64_t nold, const int* __restrict__ opa, const int* __restrict__ opb,
                                   const PairMemo* __restrict__ omemo, PairMemo* __restrict__ memo) {
+    pdl_wait();
+    pdl_trigger();
     int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (v >= nv) return;
     const long long key = ((long long)vpa[v] << 32) | (long long)(unsigned)vpb[v];
@@ -339,8 +347,8 @@ relcp_status broadphase_cached(int64_t n, const double* x_soa, const double* rb,
             RELCP_TRY(sc.memo.ensure((size_t)(nv > 0 ? nv : 1), s));
             if (nv > 0) {
                 note_launch();
-                memo_remap_kernel<<<(unsigned)((nv + kThreads - 1) / kThreads), kThreads, 0, s>>>(
-                    nv, sc.vpa.p, sc.vpb.p, nold, sc.vpa_old.p, sc.vpb_old.p, sc.memo_old.p, sc.memo.p);
+                launch_pdl(memo_remap_kernel, dim3((unsigned)((nv + kThreads - 1) / kThreads)), dim3(kThreads), 0,
+                           s, nv, sc.vpa.p, sc.vpb.p, nold, sc.vpa_old.p, sc.vpb_old.p, sc.memo_old.p, sc.memo.p);
                 RELCP_CUDA(cudaGetLastError());
             }
             RELCP_TRY(sc.xb.ensure((size_t)(3 * n), s));
@@ -359,13 +367,13 @@ relcp_status broadphase_cached(int64_t n, const double* x_soa, const double* rb,
         RELCP_TRY(sc.dmax.ensure(1, s));
         RELCP_CUDA(cudaMemsetAsync(sc.dmax.p, 0, sizeof(unsigned long long), s));
         note_launch();
-        disp_kernel<<<nbk, kThreads, 0, s>>>(n, x_soa, sc.xb.p, sfac[0], sfac[1], sfac[2], box[0], box[1], box[2],
-                                              sc.dmax.p);
+        launch_pdl(disp_kernel, dim3(nbk), dim3(kThreads), 0, s, n, x_soa, sc.xb.p, sfac[0], sfac[1], sfac[2],
+                   box[0], box[1], box[2], sc.dmax.p);
         RELCP_CUDA(cudaGetLastError());
         if (nv > 0) {
             note_launch();
-            filter_kernel<<<(unsigned)((nv + kThreads - 1) / kThreads), kThreads, 0, s>>>(
-                nv, sc.vpa.p, sc.vpb.p, xv, rb, box[0], box[1], box[2], nullptr, skin, sc.vflag.p);
+            launch_pdl(filter_kernel, dim3((unsigned)((nv + kThreads - 1) / kThreads)), dim3(kThreads), 0, s, nv,
+                       sc.vpa.p, sc.vpb.p, xv, rb, box[0], box[1], box[2], nullptr, skin, sc.vflag.p);
             RELCP_CUDA(cudaGetLastError());
         }
         RELCP_TRY(exclusive_scan(sc.vflag.p, sc.vscan.p, nv, sc.scan, s));
@@ -396,9 +404,8 @@ relcp_status broadphase_cached(int64_t n, const double* x_soa, const double* rb,
         RELCP_TRY(sc.pv.ensure((size_t)nva, s));
         if (total > 0) {
             note_launch();
-            compact_kernel<<<(unsigned)((nv + kThreads - 1) / kThreads), kThreads, 0, s>>>(nv, sc.vpa.p, sc.vpb.p,
-                                                                                          sc.vflag.p, sc.vscan.p,
-                                                                                          pa.p, pb.p, sc.pv.p);
+            launch_pdl(compact_kernel, dim3((unsigned)((nv + kThreads - 1) / kThreads)), dim3(kThreads), 0, s, nv,
+                       sc.vpa.p, sc.vpb.p, sc.vflag.p, sc.vscan.p, pa.p, pb.p, sc.pv.p);
             RELCP_CUDA(cudaGetLastError());
         }
         return RELCP_OK;
@@ -437,9 +444,8 @@ relcp_status broadphase_lookahead(int64_t n, const double* x_soa, const double b
     double sfac[3];
     for (int k = 0; k < 3; ++k) sfac[k] = (box[k] > 0 && sc.Lb[k] > 0) ? box[k] / sc.Lb[k] : 1.0;
     note_launch();
-    disp_kernel<<<(unsigned)((n + kThreads - 1) / kThreads), kThreads, 0, s>>>(n, x_soa, sc.xb.p, sfac[0], sfac[1],
-                                                                                  sfac[2], box[0], box[1], box[2],
-                                                                                  dmax_dev);
+    launch_pdl(disp_kernel, dim3((unsigned)((n + kThreads - 1) / kThreads)), dim3(kThreads), 0, s, n, x_soa,
+               sc.xb.p, sfac[0], sfac[1], sfac[2], box[0], box[1], box[2], dmax_dev);
     RELCP_CUDA(cudaGetLastError());
     return RELCP_OK;
 }
@@ -451,15 +457,13 @@ relcp_status broadphase_filter_async(int64_t n, const double* x_soa, const doubl
     if (n < 2 || nv == 0) return RELCP_OK;
     View<3, const double> xv = View<3, const double>::soa(x_soa, n);
     note_launch();
-    filter_kernel<<<(unsigned)((nv + kThreads - 1) / kThreads), kThreads, 0, s>>>(nv, sc.vpa.p, sc.vpb.p, xv, rb,
-                                                                                  box[0], box[1], box[2], box_dev,
-                                                                                  skin, sc.vflag.p);
+    launch_pdl(filter_kernel, dim3((unsigned)((nv + kThreads - 1) / kThreads)), dim3(kThreads), 0, s, nv, sc.vpa.p,
+               sc.vpb.p, xv, rb, box[0], box[1], box[2], box_dev, skin, sc.vflag.p);
     RELCP_CUDA(cudaGetLastError());
     RELCP_TRY(exclusive_scan(sc.vflag.p, sc.vscan.p, nv, sc.scan, s, np_copy));
     note_launch();
-    compact_kernel<<<(unsigned)((nv + kThreads - 1) / kThreads), kThreads, 0, s>>>(nv, sc.vpa.p, sc.vpb.p,
-                                                                                  sc.vflag.p, sc.vscan.p, pa.p, pb.p,
-                                                                                  sc.pv.p);
+    launch_pdl(compact_kernel, dim3((unsigned)((nv + kThreads - 1) / kThreads)), dim3(kThreads), 0, s, nv, sc.vpa.p,
+               sc.vpb.p, sc.vflag.p, sc.vscan.p, pa.p, pb.p, sc.pv.p);
     RELCP_CUDA(cudaGetLastError());
     return RELCP_OK;
 }

@@ -683,6 +683,7 @@ __global__ void __launch_bounds__(kThreads) lcp_kernel(KArgs<R> a) {
         if (it > a.max_iter) it = a.max_iter;
     }
     resid = sh_resid;
+    pdl_trigger();  // the next kernel in the stream may start launching
     // outputs: gamma of the last iterate (buffer cur) and the contact velocity
     // in double; every write of the last iteration happened before the last
     // grid barrier
@@ -703,6 +704,8 @@ __global__ void __launch_bounds__(kThreads) lcp_kernel(KArgs<R> a) {
 // ---- incidence CSR (rows ascending within each body)
 __global__ void inc_count(const int* __restrict__ nrows_dev, const int* __restrict__ ia, const int* __restrict__ ib,
                           int* __restrict__ cnt) {
+    pdl_wait();
+    pdl_trigger();
     int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= *nrows_dev) return;
     atomicAdd(&cnt[ia[r]], 1);
@@ -711,6 +714,8 @@ __global__ void inc_count(const int* __restrict__ nrows_dev, const int* __restri
 
 __global__ void inc_fill(const int* __restrict__ nrows_dev, const int* __restrict__ ia, const int* __restrict__ ib,
                          const int* __restrict__ off, int* __restrict__ cursor, int* __restrict__ inc) {
+    pdl_wait();
+    pdl_trigger();
     int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= *nrows_dev) return;
     int a = ia[r], b = ib[r];
@@ -723,6 +728,8 @@ __global__ void inc_fill(const int* __restrict__ nrows_dev, const int* __restric
 // (the atomic fill above leaves the order of a segment to the scheduler)
 __global__ void inc_rank(const int* __restrict__ nrows_dev, const int* __restrict__ ia, const int* __restrict__ ib,
                          const int* __restrict__ off, const int* __restrict__ unsorted, int* __restrict__ inc) {
+    pdl_wait();
+    pdl_trigger();
     const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= 2 * (int64_t)*nrows_dev) return;
     const int v = unsorted[e];
@@ -865,14 +872,16 @@ relcp_status lcp_build_csr(const LcpProblem& pr, LcpScratch& sc, cudaStream_t s)
     int* cursor = cnt + nba;
     RELCP_CUDA(cudaMemsetAsync(cnt, 0, (2 * nba + 2) * sizeof(int), s));
     note_launch();
-    inc_count<<<nblk(mc), 256, 0, s>>>(pr.nrows_dev, pr.ia, pr.ib, cnt);
+    launch_pdl(inc_count, dim3(nblk(mc)), dim3(256), 0, s, pr.nrows_dev, pr.ia, pr.ib, cnt);
     RELCP_CUDA(cudaGetLastError());
     RELCP_TRY(exclusive_scan(cnt, sc.inc_off.p, nb, sc.scan, s));
     note_launch();
-    inc_fill<<<nblk(mc), 256, 0, s>>>(pr.nrows_dev, pr.ia, pr.ib, sc.inc_off.p, cursor, sc.inc_tmp.p);
+    launch_pdl(inc_fill, dim3(nblk(mc)), dim3(256), 0, s, pr.nrows_dev, pr.ia, pr.ib, sc.inc_off.p, cursor,
+               sc.inc_tmp.p);
     RELCP_CUDA(cudaGetLastError());
     note_launch();
-    inc_rank<<<nblk(2 * mc), 256, 0, s>>>(pr.nrows_dev, pr.ia, pr.ib, sc.inc_off.p, sc.inc_tmp.p, sc.inc.p);
+    launch_pdl(inc_rank, dim3(nblk(2 * mc)), dim3(256), 0, s, pr.nrows_dev, pr.ia, pr.ib, sc.inc_off.p, sc.inc_tmp.p,
+               sc.inc.p);
     RELCP_CUDA(cudaGetLastError());
     return RELCP_OK;
 }

@@ -374,6 +374,8 @@ constexpr size_t kGuessSmem = kFwdSmem + 16 + (size_t)kGuessTile * (16 + 8) * si
 
 __global__ void __launch_bounds__(kFwdWarps * 32) mlp_guess_kernel(MlpFeatArgs fa, const unsigned char* __restrict__ image,
                                                                    View<3, double> guess, int* __restrict__ status) {
+    pdl_wait();
+    pdl_trigger();
     const int64_t count = fa.count_dev ? (int64_t)*fa.count_dev : fa.npairs;
     if ((int64_t)blockIdx.x * kGuessTile >= count) return;  // no tile for this block
     extern __shared__ __align__(16) unsigned char smem[];
@@ -655,9 +657,8 @@ relcp_status mlp_guess(MlpState& m, int64_t npairs, const int* pa, const int* pb
     int64_t blocks = (int64_t)(sms > 0 ? sms : 1) * 2;
     if (blocks > ntiles) blocks = ntiles;
     note_launch();
-    mlp_guess_kernel<<<(unsigned)blocks, kFwdWarps * 32, kGuessSmem, s>>>(fa, m.image.p,
-                                                                          View<3, double>::soa(m.guess.p, npairs),
-                                                                          status);
+    launch_pdl(mlp_guess_kernel, dim3((unsigned)blocks), dim3(kFwdWarps * 32), kGuessSmem, s, fa, m.image.p,
+               View<3, double>::soa(m.guess.p, npairs), status);
     RELCP_CUDA(cudaGetLastError());
     return RELCP_OK;
 }

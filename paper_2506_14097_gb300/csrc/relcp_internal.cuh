@@ -186,6 +186,33 @@ __device__ __forceinline__ bool near_pair_exact(double xi0, double xi1, double x
 }
 
 // ---------------------------------------------------------------------------
+// programmatic dependent launch: a kernel launched with launch_pdl may start
+// while the previous kernel in the stream drains (its launch overlaps that
+// kernel's tail); it executes pdl_wait() before touching anything earlier
+// work in the stream wrote (the wait returns once that kernel has completed
+// and its writes are visible), then pdl_trigger() to let its own dependents
+// start launching.  Both are no-ops for a kernel launched the ordinary way.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+template <typename... Params, typename... Args>
+inline cudaError_t launch_pdl(void (*kernel)(Params...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                              Args... args) {
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
+// ---------------------------------------------------------------------------
 // device-wide exclusive scan (int32) and helpers (scan.cu)
 // ---------------------------------------------------------------------------
 struct ScanScratch {

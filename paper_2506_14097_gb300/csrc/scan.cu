@@ -71,6 +71,8 @@ __global__ void __launch_bounds__(kScanThreads) scan_lookback_kernel(const int* 
                                                                      int* __restrict__ out,
                                                                      unsigned long long* tiles, int* ctr,
                                                                      int* status, int* total_copy) {
+    pdl_wait();
+    pdl_trigger();
     __shared__ int sh_tile, sh_excl, sh_last;
     if (threadIdx.x == 0) sh_tile = atomicAdd(&ctr[0], 1);
     __syncthreads();
@@ -167,8 +169,8 @@ relcp_status exclusive_scan(const int* in, int* out, int64_t n, ScanScratch& sc,
     RELCP_TRY(scan_reserve(sc, n, s));
     int* status = sc.status ? sc.status : sc.ctr.p + 2;  // ctr[2]: the scratch's own error word
     note_launch();
-    scan_lookback_kernel<<<(unsigned)ntiles, kScanThreads, 0, s>>>(in, n, out, sc.tiles.p, sc.ctr.p, status,
-                                                                    total_copy);
+    launch_pdl(scan_lookback_kernel, dim3((unsigned)ntiles), dim3(kScanThreads), 0, s, in, n, out, sc.tiles.p,
+               sc.ctr.p, status, total_copy);
     RELCP_CUDA(cudaGetLastError());
     return RELCP_OK;
 }

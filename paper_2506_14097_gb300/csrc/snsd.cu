@@ -33,6 +33,8 @@ __device__ __forceinline__ Sym3<double> load_P(View<6, const double> P, int64_t 
 }
 
 __global__ void __launch_bounds__(kThreads) snsd_kernel(SnsdArgs a) {
+    pdl_wait();
+    pdl_trigger();
     const int64_t k_thr = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t count = a.count_dev ? (int64_t)*a.count_dev : a.npairs;
     double maxov = 0.0;
@@ -132,7 +134,7 @@ relcp_status snsd_launch(const SnsdArgs& a, cudaStream_t s) {
     unsigned nb = (unsigned)((a.npairs + kThreads - 1) / kThreads);
     if (a.npairs == 0) return RELCP_OK;
     note_launch();
-    snsd_kernel<<<nb, kThreads, 0, s>>>(a);
+    launch_pdl(snsd_kernel, dim3(nb), dim3(kThreads), 0, s, a);
     RELCP_CUDA(cudaGetLastError());
     return RELCP_OK;
 }

@@ -87,12 +87,16 @@ __device__ __forceinline__ void prep_keep(const PrepArgs& a, const double* __res
 }
 
 __global__ void prep_kernel(PrepArgs a) {
+    pdl_wait();
+    pdl_trigger();
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < a.n) prep_one(a, i);
 }
 
 __global__ void flag_le_kernel(int64_t cap, const int* __restrict__ np_dev, const double* __restrict__ phi, double thr,
                                int* __restrict__ flags) {
+    pdl_wait();
+    pdl_trigger();
     int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p < cap) flags[p] = (p < *np_dev && phi[p] <= thr) ? 1 : 0;
 }
@@ -108,6 +112,8 @@ __device__ __forceinline__ double body_rate(const double* U, int64_t n, int i, i
 }
 
 __global__ void rows_kernel(RowsArgs a) {
+    pdl_wait();
+    pdl_trigger();
     int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p == 0) {
         int64_t total = a.base + a.scan[a.npairs];
@@ -183,6 +189,8 @@ __global__ void rows_kernel(RowsArgs a) {
 }
 
 __global__ void reuse_kernel(ReuseArgs a) {
+    pdl_wait();
+    pdl_trigger();
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     bool need = false;
     if (p < a.npairs && p < *a.np_dev) {
@@ -210,6 +218,8 @@ __global__ void reuse_kernel(ReuseArgs a) {
 }
 
 __global__ void memo_save_kernel(MemoSaveArgs a) {
+    pdl_wait();
+    pdl_trigger();
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= a.npairs || p >= *a.np_dev) return;
     const int r = a.rowof[p];
@@ -223,6 +233,8 @@ __global__ void memo_save_kernel(MemoSaveArgs a) {
 }
 
 __global__ void trial_kernel(TrialArgs a) {
+    pdl_wait();
+    pdl_trigger();
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     double dlen = 0.0;  // look-ahead displacement of this body
     if (i < a.n) {
@@ -266,6 +278,8 @@ __global__ void trial_kernel(TrialArgs a) {
 }
 
 __global__ void accept_kernel(AcceptArgs a) {
+    pdl_wait();
+    pdl_trigger();
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= a.n) return;
     const int64_t n = a.n;
@@ -291,49 +305,49 @@ __global__ void wrap_kernel(int64_t n, double* x, double L0, double L1, double L
 relcp_status prep_launch(const PrepArgs& a, cudaStream_t s) {
     if (a.n == 0) return RELCP_OK;
     note_launch();
-    prep_kernel<<<nb(a.n), kT, 0, s>>>(a);
+    launch_pdl(prep_kernel, dim3(nb(a.n)), dim3(kT), 0, s, a);
     RELCP_CUDA(cudaGetLastError());
     return RELCP_OK;
 }
 relcp_status flag_le_launch(int64_t cap, const int* np_dev, const double* phi, double thr, int* flags, cudaStream_t s) {
     if (cap == 0) return RELCP_OK;
     note_launch();
-    flag_le_kernel<<<nb(cap), kT, 0, s>>>(cap, np_dev, phi, thr, flags);
+    launch_pdl(flag_le_kernel, dim3(nb(cap)), dim3(kT), 0, s, cap, np_dev, phi, thr, flags);
     RELCP_CUDA(cudaGetLastError());
     return RELCP_OK;
 }
 relcp_status rows_launch(const RowsArgs& a, cudaStream_t s) {
     if (a.npairs == 0) return RELCP_OK;
     note_launch();
-    rows_kernel<<<nb(a.npairs), kT, 0, s>>>(a);
+    launch_pdl(rows_kernel, dim3(nb(a.npairs)), dim3(kT), 0, s, a);
     RELCP_CUDA(cudaGetLastError());
     return RELCP_OK;
 }
 relcp_status trial_launch(const TrialArgs& a, cudaStream_t s) {
     if (a.n == 0) return RELCP_OK;
     note_launch();
-    trial_kernel<<<nb(a.n), kT, 0, s>>>(a);
+    launch_pdl(trial_kernel, dim3(nb(a.n)), dim3(kT), 0, s, a);
     RELCP_CUDA(cudaGetLastError());
     return RELCP_OK;
 }
 relcp_status accept_launch(const AcceptArgs& a, cudaStream_t s) {
     if (a.n == 0) return RELCP_OK;
     note_launch();
-    accept_kernel<<<nb(a.n), kT, 0, s>>>(a);
+    launch_pdl(accept_kernel, dim3(nb(a.n)), dim3(kT), 0, s, a);
     RELCP_CUDA(cudaGetLastError());
     return RELCP_OK;
 }
 relcp_status reuse_launch(const ReuseArgs& a, cudaStream_t s) {
     if (a.npairs == 0) return RELCP_OK;
     note_launch();
-    reuse_kernel<<<nb(a.npairs), kT, 0, s>>>(a);
+    launch_pdl(reuse_kernel, dim3(nb(a.npairs)), dim3(kT), 0, s, a);
     RELCP_CUDA(cudaGetLastError());
     return RELCP_OK;
 }
 relcp_status memo_save_launch(const MemoSaveArgs& a, cudaStream_t s) {
     if (a.npairs == 0) return RELCP_OK;
     note_launch();
-    memo_save_kernel<<<nb(a.npairs), kT, 0, s>>>(a);
+    launch_pdl(memo_save_kernel, dim3(nb(a.npairs)), dim3(kT), 0, s, a);
     RELCP_CUDA(cudaGetLastError());
     return RELCP_OK;
 }
