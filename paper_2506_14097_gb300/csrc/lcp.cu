@@ -17,9 +17,17 @@
 //   grid barrier; every block reduces the per-block partials in the same
 //     fixed order, so all blocks take identical decisions and the result is
 //     bit-for-bit reproducible.
-// Steps alternate BB1 = s^T s / s^T y and BB2 = s^T y / y^T y.  The grid
-// barrier spins a bounded number of times; a timeout sets DEV_TIMEOUT and the
-// kernel returns.  Data written inside the launch is read with ld.global.cg
+// Steps alternate BB1 = s^T s / s^T y and BB2 = s^T y / y^T y.  On the mixed
+// path the step length of iteration k+1 comes from the products of iteration
+// k-1 (Barzilai-Borwein with one retard, Friedlander, Martinez, Molina and
+// Raydan, SIAM J. Numer. Anal. 36, 1999): those partials are complete one
+// barrier earlier, so every block folds them while it gathers and the
+// iteration needs no grid-wide read after its second barrier except on the
+// residual checks (every fourth iteration).  With FP32 iterates the retarded
+// steps also took fewer iterations on the compaction's LCPs.  The FP64 path
+// checks every iteration and keeps the plain alternation.  The grid barrier
+// spins a bounded number of times; a timeout sets DEV_TIMEOUT and the kernel
+// returns.  Data written inside the launch is read with ld.global.cg
 // (L2), never from a possibly stale L1 line.
 #include <cooperative_groups.h>
 
@@ -99,7 +107,7 @@ struct KArgs {
     double c, tol;
     int max_iter;
     int check_every;  // FP64 residual on every check_every-th iteration (and the first)
-    unsigned long long* partials;  // kNred words per block (see block_partials)
+    unsigned long long* partials;  // two buffers of kMaxBlocks x kNred words (see block_partials)
     unsigned* bar;
     int* status;
     LcpDevResult* result;
@@ -197,35 +205,56 @@ __device__ __forceinline__ unsigned long long umax64(unsigned long long x, unsig
     return x > y ? x : y;
 }
 
-// every block: reduce all blocks' partials in a fixed order.  All partials
-// are fetched at once (one L2 round trip, one word per thread) into shared
-// memory; warp 0 then folds them block by block.  The reduced words are valid
-// in thread 0 only; the caller ends the step with a __syncthreads.
+// Fold all blocks' partials (staged in shared memory, kNred words per block)
+// in a fixed order: warp k folds slot k (lane-strided sums, then a shuffle
+// tree), slot k a max when bit k of maxmask is set, a sum in the solve
+// precision R otherwise; only the slots in `slots` are folded.  The results
+// land in out[k] (shared); the caller's next __syncthreads publishes them.
 constexpr int kMaxBlocks = 256;
 template <class R>
-__device__ void grid_reduce_t0(const unsigned long long* partials, unsigned maxmask,
-                               unsigned long long tot[kNred]) {
+__device__ __forceinline__ void fold_slots(const unsigned long long* buf, unsigned slots, unsigned maxmask,
+                                           unsigned long long* out) {
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (w < kNred && ((slots >> w) & 1u)) {
+        if ((maxmask >> w) & 1u) {
+            unsigned long long m = 0;
+            for (int b = lane; b < (int)gridDim.x; b += 32) m = umax64(m, buf[b * kNred + w]);
+            for (int o = 16; o > 0; o >>= 1) m = umax64(m, __shfl_down_sync(0xffffffffu, m, o));
+            if (lane == 0) out[w] = m;
+        } else {
+            R x = R(0);
+            for (int b = lane; b < (int)gridDim.x; b += 32) x += from_word<R>(buf[b * kNred + w]);
+            for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+            if (lane == 0) out[w] = to_word(x);
+        }
+    }
+}
+
+// every block: reduce all blocks' partials in a fixed order.  All partials
+// are fetched at once (one L2 round trip, one word per thread) into shared
+// memory and folded one slot per warp; every thread gets the reduced words.
+template <class R>
+__device__ void grid_reduce(const unsigned long long* partials, unsigned maxmask, unsigned long long tot[kNred]) {
     __shared__ unsigned long long buf[kMaxBlocks * kNred];
+    __shared__ unsigned long long red[kNred];
     const int n = gridDim.x * kNred;
     for (int t = threadIdx.x; t < n; t += blockDim.x) buf[t] = __ldcg(partials + t);
     __syncthreads();
-    if (threadIdx.x < 32) {
-        const int lane = threadIdx.x;
+    fold_slots<R>(buf, (1u << kNred) - 1u, maxmask, red);
+    __syncthreads();
 #pragma unroll
-        for (int k = 0; k < kNred; ++k) {
-            if ((maxmask >> k) & 1u) {
-                unsigned long long m = 0;
-                for (int b = lane; b < (int)gridDim.x; b += 32) m = umax64(m, buf[b * kNred + k]);
-                for (int o = 16; o > 0; o >>= 1) m = umax64(m, __shfl_down_sync(0xffffffffu, m, o));
-                tot[k] = m;
-            } else {
-                R x = R(0);
-                for (int b = lane; b < (int)gridDim.x; b += 32) x += from_word<R>(buf[b * kNred + k]);
-                for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
-                tot[k] = to_word(x);
-            }
-        }
-    }
+    for (int k = 0; k < kNred; ++k) tot[k] = red[k];
+}
+
+// the BB step length after an iteration with products ss, sy, yy (BB1 after
+// odd iterations, BB2 after even ones); a non-positive or non-finite ratio
+// keeps the previous step
+template <class R>
+__device__ __forceinline__ R bb_step(int it, R ss, R sy, R yy, R prev) {
+    R na;
+    if (it & 1) na = (sy > R(0)) ? ss / sy : prev;
+    else na = (yy > R(0) && sy > R(0)) ? sy / yy : prev;
+    return (isfinite(na) && na > R(0)) ? na : prev;
 }
 
 // per-block partials of an iteration: the three BB products (sums in the
@@ -616,7 +645,7 @@ __global__ void __launch_bounds__(kThreads) lcp_kernel(KArgs<R> a) {
         }
     }
     if (!grid_barrier(a.bar, &epoch, a.status)) return;
-    grid_reduce_t0<R>(a.partials, 0x9u, tot);
+    grid_reduce<R>(a.partials, 0x9u, tot);
     // the step length, the residual and the stop decision are computed by
     // thread 0 of each block (identically in every block: same reduced values)
     // and broadcast through shared memory, so FP64 scalar work is not repeated
@@ -640,39 +669,64 @@ __global__ void __launch_bounds__(kThreads) lcp_kernel(KArgs<R> a) {
 #ifdef RELCP_LCP_TRACE
         unsigned long long t_prev = gtimer();
 #endif
+        constexpr bool kRetard = sizeof(R) == sizeof(float);
+        constexpr size_t kBuf = (size_t)kMaxBlocks * kNred;
+        __shared__ unsigned long long pbuf[kMaxBlocks * kNred];
+        __shared__ unsigned long long pred[kNred];
         for (it = 1; it <= a.max_iter; ++it) {
             // all blocks have read partials before any block rewrites them:
             // the barrier after phase 1 separates the reads from the writes
             const bool check = (it % a.check_every) == 0 || it == a.max_iter;
+            unsigned long long* part = a.partials + (kRetard ? (size_t)(it & 1) * kBuf : 0);
             scatter_phase(a, bs, cur, true, alpha_r);
             TRACE_MARK(0);
             if (!grid_barrier(a.bar, &epoch, a.status)) return;
             TRACE_MARK(1);
+            // the previous iteration's partials (complete since its second
+            // barrier) are loaded before this iteration gathers and stored to
+            // shared memory after it, so the two sets of loads overlap
+            // (the FP32 sums are the low halves of their words)
+            const int npw = (int)gridDim.x * kNred;
+            unsigned pf = 0u;
+            if (kRetard && it >= 2 && (int)threadIdx.x < npw)
+                pf = __ldcg(reinterpret_cast<const unsigned*>(a.partials + (size_t)((it - 1) & 1) * kBuf +
+                                                              threadIdx.x));
             gather_phase(a, rs, nrows, 1 - cur, cur, check, alpha_r, v, &res_t);
             TRACE_MARK(2);
-            block_partials<R>(v, res_t, check, a.partials + (size_t)blockIdx.x * kNred);
+            if (kRetard && it >= 2) {
+                if ((int)threadIdx.x < npw) pbuf[threadIdx.x] = pf;
+                // (only a grid of more than kThreads / kNred blocks has words left)
+                for (int t = threadIdx.x + kThreads; t < npw; t += kThreads)
+                    pbuf[t] = __ldcg(a.partials + (size_t)((it - 1) & 1) * kBuf + t);
+            }
+            block_partials<R>(v, res_t, check, part + (size_t)blockIdx.x * kNred);  // ends with __syncthreads
+            if (kRetard && it >= 2) {
+                fold_slots<R>(pbuf, 0x7u, 0u, pred);
+                __syncthreads();
+                if (threadIdx.x == 0)
+                    sh_alpha_r = bb_step<R>(it, from_word<R>(pred[0]), from_word<R>(pred[1]),
+                                            from_word<R>(pred[2]), sh_alpha_r);
+            }
             TRACE_MARK(3);
             if (!grid_barrier(a.bar, &epoch, a.status)) return;
             TRACE_MARK(4);
-            grid_reduce_t0<R>(a.partials, 0x8u, tot);
             cur = 1 - cur;
-            if (threadIdx.x == 0) {
-                int stop = 0;
-                if (check) {
-                    const double rs = from_word<double>(tot[3]);
-                    sh_resid = rs;
-                    stop = rs <= a.tol;
+            if (!kRetard || check) {
+                grid_reduce<R>(part, 0x8u, tot);
+                if (threadIdx.x == 0) {
+                    int stop = 0;
+                    if (check) {
+                        const double rs = from_word<double>(tot[3]);
+                        sh_resid = rs;
+                        stop = rs <= a.tol;
+                    }
+                    if (!kRetard)
+                        sh_alpha_r = bb_step<R>(it, from_word<R>(tot[0]), from_word<R>(tot[1]),
+                                                from_word<R>(tot[2]), sh_alpha_r);
+                    sh_stop = stop;
                 }
-                // BB1 / BB2 in the solve precision; a non-positive or
-                // non-finite ratio keeps the previous step
-                const R ss = from_word<R>(tot[0]), sy = from_word<R>(tot[1]), yy = from_word<R>(tot[2]);
-                R na;
-                if (it & 1) na = (sy > R(0)) ? ss / sy : sh_alpha_r;
-                else na = (yy > R(0) && sy > R(0)) ? sy / yy : sh_alpha_r;
-                if (isfinite(na) && na > R(0)) sh_alpha_r = na;
-                sh_stop = stop;
+                __syncthreads();
             }
-            __syncthreads();
             alpha_r = sh_alpha_r;
             TRACE_MARK(5);
 #ifdef RELCP_LCP_TRACE
@@ -781,7 +835,7 @@ relcp_status launch_lcp(KArgs<R>& ka, int64_t work, LcpScratch& sc, cudaStream_t
     int64_t maxb = (int64_t)sms * (per_sm < kMaxCtasPerSm ? per_sm : kMaxCtasPerSm);
     if (maxb > kMaxBlocks) maxb = kMaxBlocks;  // the grid reduction stages kMaxBlocks blocks' partials
     int blocks = (int)(want < 1 ? 1 : (want > maxb ? maxb : want));
-    RELCP_TRY(sc.partials.ensure((size_t)blocks * kNred, s));
+    RELCP_TRY(sc.partials.ensure((size_t)2 * kMaxBlocks * kNred, s));
     ka.partials = reinterpret_cast<unsigned long long*>(sc.partials.p);
     void* args[] = {&ka};
     if (ev0) RELCP_CUDA(cudaEventRecord(ev0, s));
@@ -852,7 +906,7 @@ relcp_status lcp_reserve(LcpScratch& sc, int64_t m_cap, int64_t nb, bool mixed, 
     const size_t pack = (size_t)(2 * mc) * 2 + (size_t)(8 * nba);
     if (mixed) RELCP_TRY(sc.packf.ensure(pack, s));
     else RELCP_TRY(sc.packd.ensure(pack, s));
-    RELCP_TRY(sc.partials.ensure((size_t)kMaxBlocks * kNred, s));
+    RELCP_TRY(sc.partials.ensure((size_t)2 * kMaxBlocks * kNred, s));
     RELCP_TRY(scan_reserve(sc.scan, nba, s));
     return RELCP_OK;
 }
