@@ -258,35 +258,57 @@ __device__ __forceinline__ R bb_step(int it, R ss, R sy, R yy, R prev) {
 }
 
 // per-block partials of an iteration: the three BB products (sums in the
-// solve precision) and, on check iterations, the FP64 residual (a max);
-// threads 0..3 write the block's words
+// solve precision) and, on check iterations, the FP64 residual (a max).  Each
+// warp reduces its threads' values by shuffles; then warp 0 folds the warps'
+// values (all four slots at once) and writes the block's words, while warp 1
+// (when `prev` is given) folds the previous iteration's partials of all
+// blocks, staged in shared memory, and sets the next step length *alpha.
+// Both folds run in a fixed order; the caller's next __syncthreads (the grid
+// barrier's) publishes *alpha to the block.
 template <class R>
-__device__ void block_partials(const R v[3], double res, bool with_res, unsigned long long* out) {
-    __shared__ R sh[kThreads / 32][3];
-    __shared__ unsigned long long shr[kThreads / 32];
+__device__ void block_partials(const R v[3], double res, bool with_res, unsigned long long* out,
+                               const unsigned long long* prev, int it, R* alpha) {
+    constexpr int kWarps = kThreads / 32;
+    static_assert(kWarps <= 32, "one lane per warp in the fold");
+    __shared__ R sh[kWarps][3];
+    __shared__ unsigned long long shr[kWarps];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    R x[3] = {v[0], v[1], v[2]};
+    unsigned long long m = with_res ? (unsigned long long)__double_as_longlong(res) : 0ull;
+    for (int o = 16; o > 0; o >>= 1) {
 #pragma unroll
-    for (int k = 0; k < 3; ++k) {
-        R x = v[k];
-        for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
-        if (lane == 0) sh[wid][k] = x;
+        for (int k = 0; k < 3; ++k) x[k] += __shfl_down_sync(0xffffffffu, x[k], o);
+        m = umax64(m, __shfl_down_sync(0xffffffffu, m, o));
     }
-    if (with_res) {
-        unsigned long long m = (unsigned long long)__double_as_longlong(res);
-        for (int o = 16; o > 0; o >>= 1) m = umax64(m, __shfl_down_sync(0xffffffffu, m, o));
-        if (lane == 0) shr[wid] = m;
+    if (lane == 0) {
+#pragma unroll
+        for (int k = 0; k < 3; ++k) sh[wid][k] = x[k];
+        shr[wid] = m;
     }
     __syncthreads();
-    if (threadIdx.x < 3) {
-        const int k = threadIdx.x;
-        R x = sh[0][k];
-        for (int w = 1; w < kThreads / 32; ++w) x += sh[w][k];
-        out[k] = to_word(x);
-    } else if (threadIdx.x == 3) {
-        unsigned long long m = 0;
-        if (with_res)
-            for (int w = 0; w < kThreads / 32; ++w) m = umax64(m, shr[w]);
-        out[3] = m;
+    if (wid == 0) {
+#pragma unroll
+        for (int k = 0; k < 3; ++k) x[k] = lane < kWarps ? sh[lane][k] : R(0);
+        m = lane < kWarps ? shr[lane] : 0ull;
+        for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+            for (int k = 0; k < 3; ++k) x[k] += __shfl_down_sync(0xffffffffu, x[k], o);
+            m = umax64(m, __shfl_down_sync(0xffffffffu, m, o));
+        }
+        if (lane == 0) {
+#pragma unroll
+            for (int k = 0; k < 3; ++k) out[k] = to_word(x[k]);
+            out[3] = m;
+        }
+    } else if (wid == 1 && prev) {
+        R y[3] = {R(0), R(0), R(0)};
+        for (int b = lane; b < (int)gridDim.x; b += 32)
+#pragma unroll
+            for (int k = 0; k < 3; ++k) y[k] += from_word<R>(prev[b * kNred + k]);
+        for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+            for (int k = 0; k < 3; ++k) y[k] += __shfl_down_sync(0xffffffffu, y[k], o);
+        if (lane == 0) *alpha = bb_step<R>(it, y[0], y[1], y[2], *alpha);
     }
 }
 
@@ -672,7 +694,6 @@ __global__ void __launch_bounds__(kThreads) lcp_kernel(KArgs<R> a) {
         constexpr bool kRetard = sizeof(R) == sizeof(float);
         constexpr size_t kBuf = (size_t)kMaxBlocks * kNred;
         __shared__ unsigned long long pbuf[kMaxBlocks * kNred];
-        __shared__ unsigned long long pred[kNred];
         for (it = 1; it <= a.max_iter; ++it) {
             // all blocks have read partials before any block rewrites them:
             // the barrier after phase 1 separates the reads from the writes
@@ -699,14 +720,8 @@ __global__ void __launch_bounds__(kThreads) lcp_kernel(KArgs<R> a) {
                 for (int t = threadIdx.x + kThreads; t < npw; t += kThreads)
                     pbuf[t] = __ldcg(a.partials + (size_t)((it - 1) & 1) * kBuf + t);
             }
-            block_partials<R>(v, res_t, check, part + (size_t)blockIdx.x * kNred);  // ends with __syncthreads
-            if (kRetard && it >= 2) {
-                fold_slots<R>(pbuf, 0x7u, 0u, pred);
-                __syncthreads();
-                if (threadIdx.x == 0)
-                    sh_alpha_r = bb_step<R>(it, from_word<R>(pred[0]), from_word<R>(pred[1]),
-                                            from_word<R>(pred[2]), sh_alpha_r);
-            }
+            block_partials<R>(v, res_t, check, part + (size_t)blockIdx.x * kNred,
+                              (kRetard && it >= 2) ? pbuf : nullptr, it, &sh_alpha_r);
             TRACE_MARK(3);
             if (!grid_barrier(a.bar, &epoch, a.status)) return;
             TRACE_MARK(4);
