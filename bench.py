@@ -221,6 +221,7 @@ def run_gpu_arm(R, torch, sc, precision, guess, steps, warmup, flush, stream, nv
             acc["ms_other"] += s.ms_augment
             acc["ms_step_events"] += s.ms_total
             acc["rebuilds"] += s.pair_list_rebuilt
+            acc["guess_steps"] = acc.get("guess_steps", 0) + s.guess_used
             acc["newton_c0"] = acc.get("newton_c0", 0) + s.newton_iters_c0
             acc["pairs_total"] = acc.get("pairs_total", 0) + s.n_pairs
     torch.cuda.synchronize()
@@ -430,7 +431,8 @@ def main():
         tc = float(sum(times_c))
         cold = {"value": sc.n * args.steps / (tc / 1e3), "unit": UNIT, "ms_per_step": tc / args.steps,
                 "newton_iters_per_pair_c0": acc_c.get("newton_c0", 0) / max(acc_c.get("pairs_total", 1), 1),
-                "max_overlap": acc_c["max_overlap"]}
+                "max_overlap": acc_c["max_overlap"], "lcp_iters_total": acc_c["lcp_iters"],
+                "lcp_kernel_ms": acc_c["lcp_ms"], "gpu_launches": acc_c["launches"]}
 
     fp64 = None
     if not args.no_fp64:
@@ -502,6 +504,7 @@ def main():
                       "lcp_kernel_ms": acc["lcp_ms"], "wall_s": t_wall,
                       "phase_ms": phases,
                       "pair_list_rebuilds": acc["rebuilds"],
+                      "learned_start_steps": acc.get("guess_steps", 0),
                       "newton_iters_per_pair_c0": acc.get("newton_c0", 0) / max(acc.get("pairs_total", 1), 1),
                       "phi_final": sc.meta["volume"] / float(np.prod(acc["box_final"]))},
         }

@@ -66,7 +66,12 @@ typedef struct relcp_config {
     int32_t dynamics;      /* RELCP_INERTIAL (Eq. law_inertia) or RELCP_OVERDAMPED (Eq. law_overdamped) */
     int32_t precision;     /* RELCP_FP64: every operation FP64.  RELCP_MIXED: FP32 LCP mat-vecs and
                               SNSD iterations; FP64 SNSD polish, overlap test and LCP residual. */
-    int32_t guess;         /* SNSD Newton start: RELCP_GUESS_COLD or RELCP_GUESS_MLP (needs relcp_load_mlp) */
+    int32_t guess;         /* SNSD Newton start: RELCP_GUESS_COLD or RELCP_GUESS_MLP (needs relcp_load_mlp).
+                              With RELCP_GUESS_MLP the network seeds a step's C^k evaluation when that
+                              step evaluates at least 4096 pairs (decided on the device); fewer pairs (the
+                              usual case once a step carries the previous step's values) take the cold
+                              seeds, whose Newton solves are cheaper than the network's fixed latency.
+                              Either start converges to the same SNSD within the Newton tolerance. */
     int32_t lcp_max_iter;  /* projected-gradient iteration cap per LCP (> 0) */
     int32_t max_recursion; /* augmentation cap; 0 gives the single-constraint SNSD-LCP */
     int32_t n_scenes;      /* 1 (batched scenes are a separate entry point) */
@@ -132,7 +137,7 @@ typedef struct relcp_step_stats {
     double box[3];              /* box sides after the step */
     double ms_broadphase, ms_snsd, ms_lcp, ms_augment, ms_total; /* only with RELCP_FLAG_PHASE_TIMING */
     int64_t steps_done;         /* steps since relcp_set_bodies */
-    int32_t guess_used;         /* 1 when the learned SNSD guess seeded the C^k evaluation */
+    int32_t guess_used;         /* 1 when the learned SNSD guess seeded this step's C^k evaluation */
     int32_t newton_fallbacks;   /* pairs whose learned guess was rejected and re-solved cold */
     /* kernel-level timing (only with RELCP_FLAG_PHASE_TIMING): CUDA events around
      * each launch of the persistent LCP kernel and of the SNSD kernel */

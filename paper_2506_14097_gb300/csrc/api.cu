@@ -69,6 +69,8 @@ struct DevStep {
     LcpDevResult lcp;   // iterations and residual of the last LCP
     int c0_evals;       // pairs evaluated at C^k (the others reused the previous step's values)
     int np;             // candidate pairs of the step
+    int guess_on;       // the learned start seeded this step's C^k evaluation
+    int pad0;
     // per recursion level (cleared together before each trial)
     unsigned long long maxov_bits;  // bits of the largest overlap at the last trial
     unsigned long long la_dmax;     // bits of the largest displacement of the trial positions since the list build
@@ -303,6 +305,15 @@ void drop_graphs(relcp_ctx* c) {
     c->graphs.clear();
 }
 
+// The learned SNSD start runs on a step only when at least this many pairs are
+// evaluated at C^k.  With the previous step's values carried over, a step
+// typically evaluates tens of new pairs (a few thousand at most on the
+// compaction), and for those the network's fixed latency (one tile through
+// three 128-wide layers, about 10 us) exceeds the Newton iterations it saves
+// (the cold seeds converge in at most four); they take the cold seeds, with
+// the same converged result.  Such steps do not launch the network at all.
+constexpr int64_t kLearnedMinPairs = 4096;
+
 relcp_status step_once(relcp_ctx* c) {
     const auto h0 = std::chrono::steady_clock::now();
     double wait_ms = 0.0;
@@ -401,6 +412,7 @@ relcp_status step_once(relcp_ctx* c) {
         RELCP_TRY(lcp_reserve(c->lcp, npa, n, mixed, s));
         RELCP_TRY(scan_reserve(c->scan, npa, s));
         RELCP_TRY(scan_reserve(c->bp.scan, c->bp.vn > 0 ? c->bp.vn : 1, s));
+        RELCP_TRY(scan_reserve_tiles(c->bp.scan, broadphase_filter_tiles(c->bp.vn > 0 ? c->bp.vn : 1), s));
         return RELCP_OK;
     };
     auto head = [&]() -> relcp_status {
@@ -477,7 +489,7 @@ relcp_status step_once(relcp_ctx* c) {
     sa.count_dev = count_dev;
     if (learned) {
         sa.guess = View<3, const double>::soa(c->mlp.guess.p, np);
-        st.guess_used = 1;
+        sa.guess_on = &ds->guess_on;
     }
     sa.mixed = mixed ? 1 : 0;
     sa.out = snsd_out(c->s0, c->it0);
@@ -644,10 +656,13 @@ relcp_status step_once(relcp_ctx* c) {
         if (np > 0) {
             if (!fast_bp) RELCP_CUDA(cudaMemcpyAsync(&ds->np, npd, sizeof(int), cudaMemcpyDeviceToDevice, s));
             RELCP_TRY(reuse_launch(ru, s));
-            if (learned)
+            // (a step that carries the previous step's values evaluates only the
+            // pairs new to the list, far fewer than kLearnedMinPairs: the
+            // network is not launched at all then; its flag stays 0)
+            if (learned && !ru.reuse_snsd)
                 RELCP_TRY(mlp_guess(c->mlp, np, c->pa.p, c->pb.p, xv, View<4, const double>::soa(c->q.p, n),
                                     View<3, const double>::soa(c->axes.p, n), box0, s, c->idx.p, count_dev,
-                                    &ds->status, box0_dev));
+                                    &ds->status, box0_dev, kLearnedMinPairs, &ds->guess_on));
         }
         {
             int e0 = tm.mark();
@@ -861,6 +876,7 @@ relcp_status step_once(relcp_ctx* c) {
     st.newton_iters_c0 = (int64_t)hs.iters0;
     st.n_pairs = hs.np;
     st.snsd_c0_evaluated = hs.c0_evals;
+    st.guess_used = learned ? hs.guess_on : 0;
     st.lcp_residual = hs.lcp.residual;
     st.max_overlap = __builtin_bit_cast(double, hs.maxov_bits);
     for (int k = 0; k < 3; ++k) st.box[k] = c->box[k];

@@ -15,6 +15,7 @@
 #include <utility>
 
 #include "relcp_internal.cuh"
+#include "scan_tile.cuh"
 
 namespace relcp {
 
@@ -185,6 +186,82 @@ __global__ void filter_kernel(int64_t nv, const int* __restrict__ vpa, const int
         L2 = Ldev[2];
     }
     flag[p] = near_pair(x, rb, vpa[p], vpb[p], L0, L1, L2, skin) ? 1 : 0;
+}
+
+// The cached list's exact filter, the prefix sum of its flags and the
+// compaction in one pass: each block takes a tile of kFcThreads x kFcItems
+// entries (entry e of the tile's k-th round at tile base + k kFcThreads +
+// thread, so the loads coalesce), tests them, scans the flags across the
+// device by look-back (scan_tile.cuh) and writes the surviving entries in
+// list order, exactly as the filter, scan and compaction kernels do apart.
+// The last tile writes the count to *count_out (and *count_copy).
+constexpr int kFcThreads = 512, kFcItems = 2, kFcTile = kFcThreads * kFcItems;
+__global__ void __launch_bounds__(kFcThreads)
+    filter_compact_kernel(int64_t nv, const int* __restrict__ vpa, const int* __restrict__ vpb,
+                          View<3, const double> x, const double* __restrict__ rb, const double* __restrict__ Ldev,
+                          double L0, double L1, double L2, double skin, int* __restrict__ pa, int* __restrict__ pb,
+                          int* __restrict__ pv, int* count_out, int* count_copy, unsigned long long* tiles, int* ctr,
+                          int* status) {
+    pdl_wait();
+    pdl_trigger();
+    __shared__ int fl[kFcTile];
+    const int t = tile_scan::take_ticket(ctr);
+    const int64_t base = (int64_t)t * kFcTile;
+    if (Ldev) {
+        L0 = Ldev[0];
+        L1 = Ldev[1];
+        L2 = Ldev[2];
+    }
+    int ia[kFcItems], ib[kFcItems];
+    bool f[kFcItems];
+#pragma unroll
+    for (int k = 0; k < kFcItems; ++k) {
+        const int64_t e = base + k * kFcThreads + threadIdx.x;
+        ia[k] = ib[k] = 0;
+        if (e < nv) {
+            ia[k] = vpa[e];
+            ib[k] = vpb[e];
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < kFcItems; ++k) {
+        const int64_t e = base + k * kFcThreads + threadIdx.x;
+        f[k] = e < nv && near_pair(x, rb, ia[k], ib[k], L0, L1, L2, skin);
+        fl[k * kFcThreads + threadIdx.x] = f[k] ? 1 : 0;
+    }
+    __syncthreads();
+    // thread r scans the tile's entries r kFcItems .. r kFcItems + kFcItems - 1
+    int my[kFcItems], c = 0;
+#pragma unroll
+    for (int k = 0; k < kFcItems; ++k) {
+        my[k] = fl[threadIdx.x * kFcItems + k];
+        c += my[k];
+    }
+    int tot;
+    const int inc = tile_scan::block_inclusive_scan(c, &tot);
+    const int excl = tile_scan::tile_prefix(t, tot, tiles, status);
+    int run = excl + inc - c;
+#pragma unroll
+    for (int k = 0; k < kFcItems; ++k) {
+        fl[threadIdx.x * kFcItems + k] = run;  // each thread rewrites only the words it read
+        run += my[k];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < kFcItems; ++k) {
+        const int64_t e = base + k * kFcThreads + threadIdx.x;
+        if (f[k]) {
+            const int p = fl[k * kFcThreads + threadIdx.x];
+            pa[p] = ia[k];
+            pb[p] = ib[k];
+            pv[p] = (int)e;
+        }
+    }
+    if (t == (int)gridDim.x - 1 && threadIdx.x == 0) {
+        *count_out = excl + tot;
+        if (count_copy) *count_copy = excl + tot;
+    }
+    tile_scan::tile_finish(tiles, ctr);
 }
 
 __global__ void compact_kernel(int64_t nv, const int* __restrict__ vpa, const int* __restrict__ vpb,
@@ -450,20 +527,22 @@ relcp_status broadphase_lookahead(int64_t n, const double* x_soa, const double b
     return RELCP_OK;
 }
 
+int64_t broadphase_filter_tiles(int64_t nv) { return (nv + kFcTile - 1) / kFcTile; }
+
 relcp_status broadphase_filter_async(int64_t n, const double* x_soa, const double* rb, const double box[3],
                                      const double* box_dev, double skin, DBuf<int>& pa, DBuf<int>& pb,
                                      BroadphaseScratch& sc, cudaStream_t s, int* np_copy) {
     const int64_t nv = sc.vn;
     if (n < 2 || nv == 0) return RELCP_OK;
     View<3, const double> xv = View<3, const double>::soa(x_soa, n);
+    const int64_t ntiles = (nv + kFcTile - 1) / kFcTile;
+    if (ntiles > (int64_t)1 << 30) return RELCP_ERR_INVALID_ARG;
+    RELCP_TRY(scan_reserve_tiles(sc.scan, ntiles, s));
+    int* status = sc.scan.status ? sc.scan.status : sc.scan.ctr.p + 2;
     note_launch();
-    launch_pdl(filter_kernel, dim3((unsigned)((nv + kThreads - 1) / kThreads)), dim3(kThreads), 0, s, nv, sc.vpa.p,
-               sc.vpb.p, xv, rb, box[0], box[1], box[2], box_dev, skin, sc.vflag.p);
-    RELCP_CUDA(cudaGetLastError());
-    RELCP_TRY(exclusive_scan(sc.vflag.p, sc.vscan.p, nv, sc.scan, s, np_copy));
-    note_launch();
-    launch_pdl(compact_kernel, dim3((unsigned)((nv + kThreads - 1) / kThreads)), dim3(kThreads), 0, s, nv, sc.vpa.p,
-               sc.vpb.p, sc.vflag.p, sc.vscan.p, pa.p, pb.p, sc.pv.p);
+    launch_pdl(filter_compact_kernel, dim3((unsigned)ntiles), dim3(kFcThreads), 0, s, nv, sc.vpa.p, sc.vpb.p, xv,
+               rb, box_dev, box[0], box[1], box[2], skin, pa.p, pb.p, sc.pv.p, sc.vscan.p + nv, np_copy,
+               sc.scan.tiles.p, sc.scan.ctr.p, status);
     RELCP_CUDA(cudaGetLastError());
     return RELCP_OK;
 }

@@ -23,7 +23,7 @@
 // Raydan, SIAM J. Numer. Anal. 36, 1999): those partials are complete one
 // barrier earlier, so every block folds them while it gathers and the
 // iteration needs no grid-wide read after its second barrier except on the
-// residual checks (every fourth iteration).  With FP32 iterates the retarded
+// residual checks (every second iteration).  With FP32 iterates the retarded
 // steps also took fewer iterations on the compaction's LCPs.  The FP64 path
 // checks every iteration and keeps the plain alternation.  The grid barrier
 // spins a bounded number of times; a timeout sets DEV_TIMEOUT and the kernel
@@ -47,7 +47,7 @@ namespace {
 // body slots and the 10 register-resident incidences per body fit unspilled
 constexpr int kThreads = RELCP_LCP_THREADS;
 constexpr int kMaxCtasPerSm = 1;
-constexpr int kMixedCheckEvery = 4;  // mixed path: FP64 termination residual every 4th iteration
+constexpr int kMixedCheckEvery = 2;  // mixed path: FP64 termination residual every 2nd iteration
 
 #ifdef RELCP_LCP_TRACE
 // optional phase timing of block 0 (nanoseconds summed over iterations):

@@ -373,11 +373,14 @@ constexpr int kGuessTile = 16 * kFwdWarps;
 constexpr size_t kGuessSmem = kFwdSmem + 16 + (size_t)kGuessTile * (16 + 8) * sizeof(float);
 
 __global__ void __launch_bounds__(kFwdWarps * 32) mlp_guess_kernel(MlpFeatArgs fa, const unsigned char* __restrict__ image,
-                                                                   View<3, double> guess, int* __restrict__ status) {
+                                                                   View<3, double> guess, int* __restrict__ status,
+                                                                   int64_t min_count, int* __restrict__ ran) {
     pdl_wait();
     pdl_trigger();
     const int64_t count = fa.count_dev ? (int64_t)*fa.count_dev : fa.npairs;
-    if ((int64_t)blockIdx.x * kGuessTile >= count) return;  // no tile for this block
+    const bool run = count >= min_count;
+    if (ran && blockIdx.x == 0 && threadIdx.x == 0) *ran = run ? 1 : 0;
+    if (!run || (int64_t)blockIdx.x * kGuessTile >= count) return;  // no tile for this block
     extern __shared__ __align__(16) unsigned char smem[];
     if (!bulk_copy_to_smem(smem, image, (unsigned)kFwdSmem, reinterpret_cast<unsigned long long*>(smem + kFwdSmem),
                            status))
@@ -623,7 +626,8 @@ relcp_status mlp_forward_launch(int64_t npairs, const unsigned char* image, cons
 
 relcp_status mlp_guess(MlpState& m, int64_t npairs, const int* pa, const int* pb, View<3, const double> x,
                        View<4, const double> q, View<3, const double> axes, const double box[3], cudaStream_t s,
-                       const int* idx, const int* count_dev, int* status, const double* box_dev) {
+                       const int* idx, const int* count_dev, int* status, const double* box_dev, int64_t min_count,
+                       int* ran) {
     if (!m.loaded) {
         set_error("learned guess not loaded");
         return RELCP_ERR_STATE;
@@ -658,7 +662,7 @@ relcp_status mlp_guess(MlpState& m, int64_t npairs, const int* pa, const int* pb
     if (blocks > ntiles) blocks = ntiles;
     note_launch();
     launch_pdl(mlp_guess_kernel, dim3((unsigned)blocks), dim3(kFwdWarps * 32), kGuessSmem, s, fa, m.image.p,
-               View<3, double>::soa(m.guess.p, npairs), status);
+               View<3, double>::soa(m.guess.p, npairs), status, min_count, ran);
     RELCP_CUDA(cudaGetLastError());
     return RELCP_OK;
 }

@@ -230,6 +230,8 @@ relcp_status exclusive_scan(const int* in, int* out, int64_t n, ScanScratch& sc,
 relcp_status scan_error(ScanScratch& sc, cudaStream_t s);
 // size the scratch for scans of up to n items (a later scan allocates nothing)
 relcp_status scan_reserve(ScanScratch& sc, int64_t n, cudaStream_t s);
+// the same for a kernel of its own with `ntiles` look-back tiles (scan_tile.cuh)
+relcp_status scan_reserve_tiles(ScanScratch& sc, int64_t ntiles, cudaStream_t s);
 inline void release(ScanScratch& sc, cudaStream_t s) {
     sc.tiles.release(s);
     sc.ctr.release(s);
@@ -293,7 +295,9 @@ bool broadphase_lookahead_params(const BroadphaseScratch& sc, int64_t n, const d
 // pairs into pa, pb, sc.pv (capacity sc.vn), their count at sc.vscan.p[sc.vn].
 // Valid only when the bound held for these positions (checked beforehand).
 // box_dev (may be null): the box read on the device instead of `box`;
-// np_copy (may be null): a second word that receives the count
+// np_copy (may be null): a second word that receives the count.  Its look-back
+// tiles: broadphase_filter_tiles(sc.vn) words of sc.scan (scan_reserve_tiles)
+int64_t broadphase_filter_tiles(int64_t nv);
 relcp_status broadphase_filter_async(int64_t n, const double* x_soa, const double* rb, const double box[3],
                                      const double* box_dev, double skin, DBuf<int>& pa, DBuf<int>& pb,
                                      BroadphaseScratch& sc, cudaStream_t s, int* np_copy = nullptr);
@@ -327,6 +331,7 @@ struct SnsdArgs {
     double box[3];
     const double* box_dev;           // if set, the box is read here (device) instead
     View<3, const double> guess;     // per-pair start normal (c[0] == nullptr: cold start)
+    const int* guess_on;             // if set, the start normals are used only when *guess_on != 0
     // optional pair subset: thread k < *count_dev evaluates pair idx[k] (its
     // start normal is guess(., k)); idx == nullptr: thread p evaluates pair p
     const int* idx;

@@ -50,7 +50,7 @@ __global__ void __launch_bounds__(kThreads) snsd_kernel(SnsdArgs a) {
         double d[3];
         for (int k = 0; k < 3; ++k) d[k] = min_image(a.x(k, j) - a.x(k, i), a.box_dev ? a.box_dev[k] : a.box[k]);
         const Sym3<double> Pa = load_P(a.P, i), Pb = load_P(a.P, j);
-        const bool hg = a.guess.c[0] != nullptr;
+        const bool hg = a.guess.c[0] != nullptr && (!a.guess_on || *a.guess_on != 0);
         snsd_math::PairResult o;
         snsd_math::snsd_pair(d, Pa, Pb, hg, hg ? a.guess(0, gk) : 0.0, hg ? a.guess(1, gk) : 0.0,
                              hg ? a.guess(2, gk) : 0.0, a.mixed != 0, o);
