@@ -115,7 +115,7 @@ struct relcp_ctx {
     int64_t nrows = 0, nrows0 = 0, rcap = 0;
     DBuf<int> r_ia, r_ib, r_rec, r_pair;
     DBuf<double> r_geom, r_q, r_diag, r_gamma, r_invd;
-    DBuf<float> r_geomf, r_gammaf, r_qf, Kf, r_invdf;
+    DBuf<float> r_geomf, r_gammaf, r_qf, Kf, r_invdf, ufreef;
     BroadphaseScratch bp;
     LcpScratch lcp;
     ScanScratch scan;
@@ -280,7 +280,7 @@ static void step_key(relcp_ctx* c, int64_t PC, std::vector<uintptr_t>& key) {
     key.push_back((uintptr_t)c->rcap);
     key.push_back((uintptr_t)c->sprev_stride);
     key.push_back((uintptr_t)(c->memo_ok ? 1 : 0) | (uintptr_t)(c->snsd_ok ? 2 : 0) | (uintptr_t)(c->mlp.loaded ? 4 : 0));
-    const void* ptrs[] = {c->x.p, c->q.p, c->axes.p, c->vel.p, c->fext.p, c->P.p, c->K.p, c->Kf.p, c->rb.p,
+    const void* ptrs[] = {c->x.p, c->q.p, c->axes.p, c->vel.p, c->fext.p, c->P.p, c->K.p, c->Kf.p, c->ufreef.p, c->rb.p,
                           c->ufree.p, c->uc.p, c->ustep.p, c->xt.p, c->qt.p, c->Pt.p, c->s0.p, c->s1.p, c->s1prev.p,
                           c->it0.p, c->it1.p, c->flags.p, c->fscan.p, c->gamma0.p, c->idx.p, c->rowof.p, c->pa.p,
                           c->pb.p, c->bp.pv.p, c->bp.memo.p, c->bp.vpa.p, c->bp.vpb.p, c->bp.vflag.p, c->bp.vscan.p,
@@ -367,9 +367,12 @@ relcp_status step_once(relcp_ctx* c) {
     pa.P = c->P.p;
     pa.K = c->K.p;
     pa.Kf = nullptr;
+    pa.ufreef = nullptr;
     if (mixed) {
         RELCP_TRY(c->Kf.ensure((size_t)(7 * (n > 0 ? n : 1)), s));
+        RELCP_TRY(c->ufreef.ensure((size_t)(6 * (n > 0 ? n : 1)), s));
         pa.Kf = c->Kf.p;
+        pa.ufreef = c->ufreef.p;
     }
     pa.rb = c->rb.p;
     pa.ufree = c->ufree.p;
@@ -517,6 +520,8 @@ relcp_status step_once(relcp_ctx* c) {
     ra.box_dev = box0_dev;
     ra.x = c->x.p;
     ra.ufree = c->ufree.p;
+    ra.ufreef = pa.ufreef;
+    ra.Kf = pa.Kf;
     ra.uc = c->uc.p;
     ra.K = c->K.p;
     ra.nrows_dev = &ds->nrows;
@@ -1360,6 +1365,7 @@ void relcp_destroy(relcp_ctx* c) {
     c->r_gammaf.release(s);
     c->r_qf.release(s);
     c->Kf.release(s);
+    c->ufreef.release(s);
     c->r_invd.release(s);
     c->r_invdf.release(s);
     c->sblk.release(s);

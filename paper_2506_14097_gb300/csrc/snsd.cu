@@ -32,17 +32,26 @@ __device__ __forceinline__ Sym3<double> load_P(View<6, const double> P, int64_t 
     return Sym3<double>{P(0, i), P(1, i), P(2, i), P(3, i), P(4, i), P(5, i)};
 }
 
+// A grid-stride loop over the pairs: a subset launch is sized to one wave of
+// resident blocks, not to the capacity, so a C^k evaluation of the few pairs
+// new to the list costs one wave of blocks that mostly find no work.
 __global__ void __launch_bounds__(kThreads) snsd_kernel(SnsdArgs a) {
     pdl_wait();
     pdl_trigger();
-    const int64_t k_thr = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t count = a.count_dev ? (int64_t)*a.count_dev : a.npairs;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    // a subset launch has no violator flags; a capacity-sized one clears the
+    // flags of the slots past the count
+    const int64_t kend = (a.viol && !a.idx) ? a.npairs : count;
     double maxov = 0.0;
-    int iters_out = 0;
-    bool viol_here = false;
-    // pairs past the count of a capacity-sized launch: no violation
-    if (a.viol && !a.idx && k_thr >= count && k_thr < a.npairs) a.viol[k_thr] = 0;
-    if (k_thr < count) {
+    int it_max = 0;
+    long long it_sum = 0;
+    int nvl = 0;
+    for (int64_t k_thr = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k_thr < kend; k_thr += stride) {
+        if (k_thr >= count) {
+            a.viol[k_thr] = 0;  // (a.viol set: kend is the capacity only then)
+            continue;
+        }
         const int64_t p = a.idx ? (int64_t)a.idx[k_thr] : k_thr;  // the pair
         const int64_t gk = k_thr;                                  // its start-normal slot
         const int i = a.pa[p * a.pstride];
@@ -64,33 +73,34 @@ __global__ void __launch_bounds__(kThreads) snsd_kernel(SnsdArgs a) {
             a.out.rb(k, p) = o.rb[k];
         }
         if (a.out.iters) a.out.iters[p] = iters;
-        iters_out = iters;
-        viol_here = G < -a.eps;
+        const int itabs = iters < 0 ? -iters : iters;
+        it_max = max(it_max, itabs);
+        it_sum += itabs;
+        const bool viol_here = G < -a.eps;
         if (a.viol) a.viol[p] = viol_here ? 1 : 0;
-        maxov = G < 0.0 ? -G : 0.0;
+        nvl += viol_here ? 1 : 0;
+        if (G < 0.0 && -G > maxov) maxov = -G;
     }
-    // one atomic per block for the largest overlap, the iteration counts and
-    // the violators; the overlap maximum is taken on the bits of non-negative
-    // doubles (integer max, no FP64 unit)
+    // one atomic per block (skipped when it would change nothing) for the
+    // largest overlap, the iteration counts and the violators; the overlap
+    // maximum is taken on the bits of non-negative doubles (integer max, no
+    // FP64 unit)
     __shared__ unsigned long long sh_ov[kThreads / 32];
     __shared__ int sh_it[kThreads / 32];
-    __shared__ int sh_is[kThreads / 32];
+    __shared__ long long sh_is[kThreads / 32];
     __shared__ int sh_nv[kThreads / 32];
     unsigned long long ovb = (unsigned long long)__double_as_longlong(maxov);
-    int itabs = iters_out < 0 ? -iters_out : iters_out;
-    int itsum = itabs;
-    int nvl = viol_here ? 1 : 0;
     for (int o = 16; o > 0; o >>= 1) {
         const unsigned long long y = __shfl_xor_sync(0xffffffffu, ovb, o);
         ovb = y > ovb ? y : ovb;
-        itabs = max(itabs, __shfl_xor_sync(0xffffffffu, itabs, o));
-        itsum += __shfl_xor_sync(0xffffffffu, itsum, o);
+        it_max = max(it_max, __shfl_xor_sync(0xffffffffu, it_max, o));
+        it_sum += __shfl_xor_sync(0xffffffffu, it_sum, o);
         nvl += __shfl_xor_sync(0xffffffffu, nvl, o);
     }
     if ((threadIdx.x & 31) == 0) {
         sh_ov[threadIdx.x >> 5] = ovb;
-        sh_it[threadIdx.x >> 5] = itabs;
-        sh_is[threadIdx.x >> 5] = itsum;
+        sh_it[threadIdx.x >> 5] = it_max;
+        sh_is[threadIdx.x >> 5] = it_sum;
         sh_nv[threadIdx.x >> 5] = nvl;
     }
     __syncthreads();
@@ -105,8 +115,8 @@ __global__ void __launch_bounds__(kThreads) snsd_kernel(SnsdArgs a) {
             nv += sh_nv[w];
         }
         if (a.maxov_bits && m) atomicMax(a.maxov_bits, m);
-        if (a.newton_max) atomicMax(a.newton_max, mi);
-        if (a.iters_sum) atomicAdd(a.iters_sum, (unsigned long long)ms);
+        if (a.newton_max && mi) atomicMax(a.newton_max, mi);
+        if (a.iters_sum && ms) atomicAdd(a.iters_sum, (unsigned long long)ms);
         if (a.nviol && nv) atomicAdd(a.nviol, nv);
     }
 }
@@ -131,10 +141,25 @@ __global__ void shape_kernel(int64_t n, View<4, const double> q, View<3, const d
 }  // namespace
 
 relcp_status snsd_launch(const SnsdArgs& a, cudaStream_t s) {
-    unsigned nb = (unsigned)((a.npairs + kThreads - 1) / kThreads);
     if (a.npairs == 0) return RELCP_OK;
+    // blocks resident at once per SM (register-limited)
+    static int per_sm = 0;
+    if (per_sm == 0) {
+        int b = 0;
+        RELCP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, snsd_kernel, kThreads, 0));
+        per_sm = b > 0 ? b : 1;
+    }
+    // a subset launch (a few new pairs against the list's capacity) takes
+    // one wave of blocks that loop; a full evaluation one thread per pair
+    const int64_t need = (a.npairs + kThreads - 1) / kThreads;
+    int64_t nb = need;
+    if (a.idx) {
+        const int sms = device_sm_count();
+        nb = (int64_t)(sms > 0 ? sms : 1) * per_sm;
+        if (nb > need) nb = need;
+    }
     note_launch();
-    launch_pdl(snsd_kernel, dim3(nb), dim3(kThreads), 0, s, a);
+    launch_pdl(snsd_kernel, dim3((unsigned)nb), dim3(kThreads), 0, s, a);
     RELCP_CUDA(cudaGetLastError());
     return RELCP_OK;
 }

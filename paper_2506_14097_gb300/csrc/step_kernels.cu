@@ -54,6 +54,8 @@ __device__ __forceinline__ void prep_one(const PrepArgs& a, int64_t i) {
     if (a.Kf)
         for (int k = 0; k < 7; ++k) a.Kf[k * n + i] = (float)b.K[k];
     for (int k = 0; k < 6; ++k) a.ufree[k * n + i] = b.ufree[k];
+    if (a.ufreef)
+        for (int k = 0; k < 6; ++k) a.ufreef[k * n + i] = (float)b.ufree[k];
 }
 
 // the next step's prep after an accepted trial (overdamped): q was normalised
@@ -84,6 +86,9 @@ __device__ __forceinline__ void prep_keep(const PrepArgs& a, const double* __res
             if (a.box[k] > 0.0) u[k] += a.strain_rate * (a.x[k * n + i] - 0.5 * a.box[k]);
 #pragma unroll
     for (int k = 0; k < 6; ++k) a.ufree[k * n + i] = u[k];
+    if (a.ufreef)
+#pragma unroll
+        for (int k = 0; k < 6; ++k) a.ufreef[k * n + i] = (float)u[k];
 }
 
 __global__ void prep_kernel(PrepArgs a) {
@@ -111,6 +116,90 @@ __device__ __forceinline__ double body_rate(const double* U, int64_t n, int i, i
     return step_math::row_rate(Ui, Uj, nn, ta, tb);
 }
 
+// One row on the mixed path: the Jacobian row, its rate and its diagonal in
+// FP32 (the LCP iterates on FP32 geometry anyway, and the lever arms come from
+// the FP32 Newton phase); the offset q = Phi + c d^T U keeps Phi in FP64 and
+// adds the FP32 rate term, whose rounding (relative 1e-7 of c |d^T U|) is far
+// below the LCP tolerance.  The FP64 geometry written for read-outs is the
+// widened FP32 one.  The periodic-image correction of the affine background
+// velocity needs only which image the pair uses: decided from the FP64
+// separation, as in the FP64 path.
+__device__ __forceinline__ void rows_mixed(const RowsArgs& a, int64_t p, int64_t r, int i, int j) {
+    const int64_t P = a.npairs, C = a.cap, n = a.nbodies;
+    float nn[3], ra[3], rb[3], ta[3], tb[3];
+    for (int k = 0; k < 3; ++k) {
+        nn[k] = (float)a.snsd[(1 + k) * P + p];
+        ra[k] = (float)a.snsd[(4 + k) * P + p];
+        rb[k] = (float)a.snsd[(7 + k) * P + p];
+    }
+    const double phi = a.snsd[p];
+    ta[0] = ra[1] * nn[2] - ra[2] * nn[1];
+    ta[1] = ra[2] * nn[0] - ra[0] * nn[2];
+    ta[2] = ra[0] * nn[1] - ra[1] * nn[0];
+    tb[0] = rb[1] * nn[2] - rb[2] * nn[1];
+    tb[1] = rb[2] * nn[0] - rb[0] * nn[2];
+    tb[2] = rb[0] * nn[1] - rb[1] * nn[0];
+    a.ia[r] = i;
+    a.ib[r] = j;
+    a.rec[r] = a.rec_index;
+    a.pair[r] = (int)p;
+    for (int k = 0; k < 3; ++k) {
+        a.geomf[k * C + r] = nn[k];
+        a.geomf[(3 + k) * C + r] = ta[k];
+        a.geomf[(6 + k) * C + r] = tb[k];
+        a.geom[k * C + r] = (double)nn[k];
+        a.geom[(3 + k) * C + r] = (double)ta[k];
+        a.geom[(6 + k) * C + r] = (double)tb[k];
+    }
+    float Ui[6], Uj[6];
+    if (a.rec_index == 0) {
+        for (int k = 0; k < 6; ++k) {
+            Ui[k] = a.ufreef[k * n + i];
+            Uj[k] = a.ufreef[k * n + j];
+        }
+    } else {
+        for (int k = 0; k < 6; ++k) {
+            Ui[k] = (float)a.uc[k * n + i];
+            Uj[k] = (float)a.uc[k * n + j];
+        }
+    }
+    float rate = 0.f;
+    for (int k = 0; k < 3; ++k) rate += nn[k] * (Uj[k] - Ui[k]);
+    for (int k = 0; k < 3; ++k) rate += tb[k] * Uj[3 + k] - ta[k] * Ui[3 + k];
+    double qv;
+    if (a.rec_index == 0) {
+        if (a.strain_rate != 0.0) {
+            const double* L = a.box_dev ? a.box_dev : a.box;
+            float corr = 0.f;
+            for (int k = 0; k < 3; ++k) {
+                const double raw = a.x[k * n + j] - a.x[k * n + i];
+                corr += nn[k] * (float)(min_image(raw, L[k]) - raw);  // 0 or a multiple of the box side
+            }
+            rate += (float)a.strain_rate * corr;
+        }
+        qv = phi + a.c * (double)rate;
+    } else {
+        qv = phi - a.c * (double)rate;
+    }
+    a.q[r] = qv;
+    if (a.qf) a.qf[r] = (float)qv;
+    // diagonal c d^T K d
+    float acc = (a.Kf[i] + a.Kf[j]) * (nn[0] * nn[0] + nn[1] * nn[1] + nn[2] * nn[2]);
+    for (int side = 0; side < 2; ++side) {
+        const int b = side ? j : i;
+        const float* t = side ? tb : ta;
+        const float kxx = a.Kf[n + b], kyy = a.Kf[2 * n + b], kzz = a.Kf[3 * n + b], kxy = a.Kf[4 * n + b],
+                    kxz = a.Kf[5 * n + b], kyz = a.Kf[6 * n + b];
+        acc += t[0] * (kxx * t[0] + kxy * t[1] + kxz * t[2]) + t[1] * (kxy * t[0] + kyy * t[1] + kyz * t[2]) +
+               t[2] * (kxz * t[0] + kyz * t[1] + kzz * t[2]);
+    }
+    const float cf = (float)a.c;
+    a.diag[r] = (double)(cf * acc);
+    if (a.invdf) a.invdf[r] = 1.f / (cf * acc);
+    if (a.gammaf) a.gammaf[r] = (a.rec_index == 0 && a.gamma0) ? (float)a.gamma0[p] : 0.f;
+    if (a.gamma) a.gamma[r] = (a.rec_index == 0 && a.gamma0) ? a.gamma0[p] : 0.0;
+}
+
 __global__ void rows_kernel(RowsArgs a) {
     pdl_wait();
     pdl_trigger();
@@ -131,6 +220,10 @@ __global__ void rows_kernel(RowsArgs a) {
     if (r < 0) return;
     int i = a.pa[p], j = a.pb[p];
     const int64_t P = a.npairs;
+    if (a.geomf && a.ufreef && a.Kf) {
+        rows_mixed(a, p, r, i, j);
+        return;
+    }
     double nn[3], ra[3], rb[3], ta[3], tb[3];
     for (int k = 0; k < 3; ++k) {
         nn[k] = a.snsd[(1 + k) * P + p];

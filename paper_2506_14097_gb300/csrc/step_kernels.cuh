@@ -22,6 +22,7 @@ struct PrepArgs {
     float* Kf;  // FP32 mirror of K (mixed path)
     double* rb;
     double* ufree;
+    float* ufreef;  // FP32 mirror of U_free (mixed path) or null
 };
 
 struct RowsArgs {
@@ -39,6 +40,10 @@ struct RowsArgs {
     const double* ufree;  // A_0 offsets
     const double* uc;     // appended offsets: K D gamma of the last LCP
     const double* K;
+    // mixed path (all three set): the row's torques, rate and diagonal in FP32
+    // from FP32 mirrors of U_free and K; only Phi + c rate stays FP64
+    const float* ufreef;
+    const float* Kf;
     int* ia;
     int* ib;
     int* rec;
