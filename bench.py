@@ -241,7 +241,9 @@ def run_e2e(R, torch, sc, precision, guess, steps, mlp_params=None):
     (get_bodies: x, q and the step velocity).  The workload has no background
     velocity or external force, so none is passed in."""
     n = sc.n
-    x, q, axes = (np.ascontiguousarray(a) for a in (sc.x, sc.q, sc.axes))
+    # copies: relcp_get_bodies writes each step's result into x and q, and the
+    # scene's own arrays must keep the initial state for the runs after this one
+    x, q, axes = (np.array(a, dtype=np.float64, order="C", copy=True) for a in (sc.x, sc.q, sc.axes))
     u = np.zeros((n, 6))
     cfg = make_cfg(R, sc, precision, guess, timing=None)
     sim = R.Simulation(cfg)
