@@ -12,6 +12,7 @@
 // buffers and decide the loop; everything else stays on the device.
 #include <atomic>
 #include <chrono>
+#include <cmath>
 #include <climits>
 #include <functional>
 #include <cstdarg>
@@ -73,7 +74,7 @@ struct DevStep {
     int pad0;
     // per recursion level (cleared together before each trial)
     unsigned long long maxov_bits;  // bits of the largest overlap at the last trial
-    unsigned long long la_dmax;     // bits of the largest displacement of the trial positions since the list build
+    unsigned long long la_dmax;     // bits of the largest squared displacement of the trial positions since the list build
     int nviol;                      // violators of the last overlap test
     int pad;
 };
@@ -849,7 +850,8 @@ relcp_status step_once(relcp_ctx* c) {
     c->snsd_ok = true;
     // the last look-ahead was taken at the configuration accepted below
     c->la_ok = true;
-    c->la_rebuild = !verlet_bound_holds(c->bp, n, box1, c->rb_max, cfg.skin, __builtin_bit_cast(double, hs.la_dmax));
+    c->la_rebuild =
+        !verlet_bound_holds(c->bp, n, box1, c->rb_max, cfg.skin, std::sqrt(__builtin_bit_cast(double, hs.la_dmax)));
 
     // accept C^{k+1} (no synchronisation: the next call queues behind it)
     AcceptArgs aa{};

@@ -329,7 +329,7 @@ __global__ void trial_kernel(TrialArgs a) {
     pdl_wait();
     pdl_trigger();
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    double dlen = 0.0;  // look-ahead displacement of this body
+    double d2max = 0.0;  // squared look-ahead displacement of this body
     if (i < a.n) {
     const int64_t n = a.n;
     double U[6], x[3], q[4], ax[3], xt[3], qt[4];
@@ -361,12 +361,18 @@ __global__ void trial_kernel(TrialArgs a) {
             const double d = min_image(xt[k] - sf * a.xb[k * n + i], lb);
             d2 += d * d;
         }
-        dlen = sqrt(d2);
+        d2max = d2;
     }
     }
     if (a.xb) {
-        for (int o = 16; o > 0; o >>= 1) dlen = fmax(dlen, __shfl_xor_sync(0xffffffffu, dlen, o));
-        if ((threadIdx.x & 31) == 0 && dlen > 0.0) atomicMax(a.la_dmax, (unsigned long long)__double_as_longlong(dlen));
+        // the largest squared displacement (the host takes its square root):
+        // integer max of the non-negative doubles' bits
+        unsigned long long b = (unsigned long long)__double_as_longlong(d2max);
+        for (int o = 16; o > 0; o >>= 1) {
+            const unsigned long long y = __shfl_xor_sync(0xffffffffu, b, o);
+            b = y > b ? y : b;
+        }
+        if ((threadIdx.x & 31) == 0 && b) atomicMax(a.la_dmax, b);
     }
 }
 

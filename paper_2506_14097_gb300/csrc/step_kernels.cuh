@@ -110,7 +110,7 @@ struct TrialArgs {
     double sfac[3], la_box[3];
     const double* sfac_dev;    // if set: sfac and la_box read here (device) instead
     const double* la_box_dev;
-    unsigned long long* la_dmax;
+    unsigned long long* la_dmax;  // bits of the largest squared displacement (atomic max)
     const double* x;
     const double* q;
     const double* axes;

@@ -28,8 +28,8 @@ __device__ __forceinline__ void prep_body(const double qin[4], const double ax[3
                                           double drag_xi, double density, double strain_rate, const double box[3],
                                           BodyPrep& b) {
     double s = qin[0], x1 = qin[1], y1 = qin[2], z1 = qin[3];
-    // one FP64 division (a slow sequence on this part), four products
-    const double il = 1.0 / sqrt(s * s + x1 * x1 + y1 * y1 + z1 * z1);
+    // one FP64 reciprocal square root (no separate division), four products
+    const double il = rsqrt(s * s + x1 * x1 + y1 * y1 + z1 * z1);
     s *= il;
     x1 *= il;
     y1 *= il;
@@ -135,7 +135,7 @@ __device__ __forceinline__ void trial_body(const double x[3], const double q[4],
     double nx = x1 + h * (s * w0 + (w1 * z1 - w2 * y1));
     double ny = y1 + h * (s * w1 + (w2 * x1 - w0 * z1));
     double nz = z1 + h * (s * w2 + (w0 * y1 - w1 * x1));
-    const double il = 1.0 / sqrt(ns * ns + nx * nx + ny * ny + nz * nz);
+    const double il = rsqrt(ns * ns + nx * nx + ny * ny + nz * nz);
     ns *= il;
     nx *= il;
     ny *= il;

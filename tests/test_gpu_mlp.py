@@ -131,6 +131,11 @@ def test_trained_guess_gain_and_same_results(relcp_gpu, orc):
         ids, geom, gam = R.relcp_get_rows(s.ctx)
         xb, qb, vb = s.bodies()
         res[guess] = (st, pairs, phi0, ids, vb)
+        # the next step carries the SNSD values of this one and evaluates only
+        # the pairs new to the list, too few for the network: cold seeds
+        s.step(1)
+        st2 = s.stats()
+        assert st2.guess_used == 0 and st2.snsd_c0_evaluated < 4096
         s.close()
     (sc_, pc, phc, idc, vc), (sm_, pm, phm, idm, vm) = res[R.RELCP_GUESS_COLD], res[R.RELCP_GUESS_MLP]
     assert sm_.guess_used == 1 and sc_.guess_used == 0
