@@ -290,6 +290,42 @@ def test_cached_pair_list_bitexact_over_steps(relcp_gpu, orc):
     sim.close()
 
 
+def test_cached_pair_list_bitexact_32k(relcp_gpu, orc):
+    """At the benchmark's size and density the cached list's fused filter and
+    compaction runs over more than 32 look-back tiles of 1024 entries (several
+    look-back windows); its pairs equal the oracle's brute force on the same
+    positions, bit for bit."""
+    R = relcp_gpu
+    sc = scenes.suspension_scene(seed=23, n=32768, phi=0.1, phi_final=0.45, steps=60, dt=5e-3)
+    amin = float(sc.axes.min())
+    cfg = R.make_config(dynamics=R.RELCP_OVERDAMPED, precision=R.RELCP_MIXED, dt=sc.dt, eps_ncp=1e-3 * amin,
+                        box=tuple(sc.box), skin=0.1 * amin, strain_rate=sc.meta["strain_rate"], length_scale=amin)
+    sim = R.Simulation(cfg)
+    sim.set_bodies(sc.x, sc.q, sc.axes)
+    sim.step(57, allow=(R.RELCP_ERR_NOT_CONVERGED,))
+    # hold the box from here on, so that the following steps serve their
+    # pairs from the cached list (the first one after the change re-checks it)
+    box = R.relcp_get_box(sim.ctx)
+    for k in range(3):
+        cfg.box[k] = box[k]
+    cfg.strain_rate = 0.0
+    R.relcp_set_config(sim.ctx, cfg)
+    sim.step(1, allow=(R.RELCP_ERR_NOT_CONVERGED,))
+    rb = sc.axes.max(axis=1)
+    cached = 0
+    for _ in range(2):
+        x, q, _ = sim.bodies()
+        box = R.relcp_get_box(sim.ctx)
+        sim.step(1, allow=(R.RELCP_ERR_NOT_CONVERGED,))
+        cached += sim.stats().pair_list_rebuilt == 0
+        pairs, _ = R.relcp_get_pairs(sim.ctx)
+        ref = orc.candidate_pairs(x, rb, box, 0.1 * amin)
+        assert ref.shape[0] > 40 * 1024
+        assert np.array_equal(pairs, ref)
+    assert cached >= 1
+    sim.close()
+
+
 # ---------------------------------------------------------------------------
 # edge cases and error paths
 # ---------------------------------------------------------------------------
