@@ -64,8 +64,9 @@ enum { RELCP_PTR_HOST = 0, RELCP_PTR_DEVICE = 1 };
 /* Time-step parameters (Algorithm 1: Require C^k, F_ext, M, eps_NCP). */
 typedef struct relcp_config {
     int32_t dynamics;      /* RELCP_INERTIAL (Eq. law_inertia) or RELCP_OVERDAMPED (Eq. law_overdamped) */
-    int32_t precision;     /* RELCP_FP64: every operation FP64.  RELCP_MIXED: FP32 LCP mat-vecs and
-                              SNSD iterations; FP64 SNSD polish, overlap test and LCP residual. */
+    int32_t precision;     /* RELCP_FP64: every operation FP64.  RELCP_MIXED: FP32 LCP iterations, SNSD
+                              Newton iterations and constraint-row assembly; FP64 SNSD polish (Phi),
+                              row offsets (Phi + c d^T U), overlap test, LCP residual and the state. */
     int32_t guess;         /* SNSD Newton start: RELCP_GUESS_COLD or RELCP_GUESS_MLP (needs relcp_load_mlp).
                               With RELCP_GUESS_MLP the network seeds a step's C^k evaluation when that
                               step evaluates at least 4096 pairs (decided on the device); fewer pairs (the
@@ -115,7 +116,7 @@ enum {
                                       pair that was a candidate in the previous step takes its C^k
                                       values from that step's last overlap test, which evaluated it at
                                       the configuration the step accepted (= this step's C^k); only
-                                      new pairs are evaluated (and given the learned guess) */
+                                      new pairs are evaluated */
 };
 
 #define RELCP_MAX_DEPTH_STATS 64
@@ -139,8 +140,9 @@ typedef struct relcp_step_stats {
     int64_t steps_done;         /* steps since relcp_set_bodies */
     int32_t guess_used;         /* 1 when the learned SNSD guess seeded this step's C^k evaluation */
     int32_t newton_fallbacks;   /* pairs whose learned guess was rejected and re-solved cold */
-    /* kernel-level timing (only with RELCP_FLAG_PHASE_TIMING): CUDA events around
-     * each launch of the persistent LCP kernel and of the SNSD kernel */
+    /* kernel-level timing: CUDA events around each launch of the persistent LCP
+     * kernel (with RELCP_FLAG_PHASE_TIMING or RELCP_FLAG_LCP_TIMING) and of the
+     * SNSD kernel (with RELCP_FLAG_PHASE_TIMING) */
     double ms_lcp_kernel;       /* sum over the step's LCP launches */
     double lcp_alg_bytes;       /* algorithmic bytes of those launches: per projected-gradient
                                    iteration 120 B per row + 152 B per body (FP64), 68 B + 104 B (mixed) */
@@ -183,7 +185,15 @@ relcp_status relcp_set_config(relcp_ctx* ctx, const relcp_config* cfg);
  * within 1e-6 of 1); semi_axes: n x 3 (> 0); vel: n x 6 or NULL (= 0):
  * inertial, the velocity U^k; overdamped, a background velocity added to
  * U = M (F_ext + D gamma); f_ext: n x 6 or NULL (= 0).  dt_per_scene must be
- * NULL.  Periodic positions are wrapped into [0, box).  Resets steps_done. */
+ * NULL.  Periodic positions are wrapped into [0, box).  Resets steps_done.
+ * Host arrays are read in place by the device where it can reach pageable
+ * host memory through the host page tables (Grace hosts), else through pinned
+ * staging (always with RELCP_FLAG_HOST_STAGING); the call returns once the
+ * arrays have been read.  An invalid body is reported as "body <i>: <reason>"
+ * (the smallest such index) with the context unchanged.  A state equal, bit
+ * for bit, to the current one keeps everything the next step carries over;
+ * moved bodies keep the cached pair list (its displacement bound still
+ * guards it) and the warm starts. */
 relcp_status relcp_set_bodies(relcp_ctx* ctx, int64_t n, const int32_t* scene_offsets, const double* x,
                               const double* q, const double* semi_axes, const double* vel,
                               const double* f_ext, const double* dt_per_scene, int32_t ptr_kind);
@@ -195,7 +205,9 @@ relcp_status relcp_step(relcp_ctx* ctx, int32_t nsteps);
 
 /* Copy out the state: x n x 3 (wrapped), q n x 4, vel n x 6 = velocity of
  * the last step (inertial: U^{k+1}; overdamped: U = U_free + M D gamma).
- * Any pointer may be NULL.  Synchronises the context stream. */
+ * Any pointer may be NULL.  Host arrays are written in place by the device
+ * where it reaches pageable host memory, else through pinned staging (as for
+ * relcp_set_bodies).  Synchronises the context stream. */
 relcp_status relcp_get_bodies(relcp_ctx* ctx, double* x, double* q, double* vel, int32_t ptr_kind);
 
 /* Current periodic box sides (they change under strain_rate). */
