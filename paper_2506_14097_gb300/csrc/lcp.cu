@@ -103,6 +103,7 @@ struct KArgs {
     R* gamma_io;         // caller's gamma (in: warm start, out: solution), SoA
     typename Vec2<R>::T* gg[2];  // (gamma, g) per row, double-buffered
     R* ucp;              // contact velocity, one 8-wide record per body (6 used)
+    R* ucp2;             // the second such buffer (one-barrier iterations, mixed path) or null
     double* ucd[6];      // double output (SoA)
     double c, tol;
     int max_iter;
@@ -267,7 +268,8 @@ __device__ __forceinline__ R bb_step(int it, R ss, R sy, R yy, R prev) {
 // barrier's) publishes *alpha to the block.
 template <class R>
 __device__ void block_partials(const R v[3], double res, bool with_res, unsigned long long* out,
-                               const unsigned long long* prev, int it, R* alpha) {
+                               const unsigned long long* prev, int it, R* alpha, bool res_f32 = false,
+                               bool prev_res = false, unsigned* prev_res_max = nullptr) {
     constexpr int kWarps = kThreads / 32;
     static_assert(kWarps <= 32, "one lane per warp in the fold");
     __shared__ R sh[kWarps][3];
@@ -298,8 +300,18 @@ __device__ void block_partials(const R v[3], double res, bool with_res, unsigned
         if (lane == 0) {
 #pragma unroll
             for (int k = 0; k < 3; ++k) out[k] = to_word(x[k]);
-            out[3] = m;
+            // (res_f32: the residual rounded up to FP32, its bits in the low
+            // half, so that a fold of the low halves sees it)
+            out[3] = res_f32 ? (unsigned long long)__float_as_uint(__double2float_ru(__longlong_as_double((long long)m)))
+                             : m;
         }
+    } else if (wid == 2 && prev && prev_res) {
+        // the previous iteration's residual (FP32 bits, rounded up): max over
+        // the blocks' low halves
+        unsigned mm = 0u;
+        for (int b = lane; b < (int)gridDim.x; b += 32) mm = max(mm, (unsigned)prev[b * kNred + 3]);
+        for (int o = 16; o > 0; o >>= 1) mm = max(mm, __shfl_down_sync(0xffffffffu, mm, o));
+        if (lane == 0) *prev_res_max = mm;
     } else if (wid == 1 && prev) {
         R y[3] = {R(0), R(0), R(0)};
         for (int b = lane; b < (int)gridDim.x; b += 32)
@@ -631,6 +643,149 @@ __device__ void gather_phase(const KArgs<R>& a, RowSlot<R>& S, const int nrows, 
     *resid = res;
 }
 
+// ---------------------------------------------------------------------------
+// One grid barrier per iteration (mixed path, every row in a row slot).  A row
+// record is one 64-bit word, g's FP32 bits in the high half and gamma's in the
+// low half, written and read as a single 64-bit access, so a reader sees one
+// iteration's (gamma, g) or another's, never a mix.  gamma >= 0, so its sign
+// bit is free: it carries the record's phase, bit 1 of the iteration number,
+// which tells the iteration k - 1 that the scatter of iteration k waits for
+// from the k - 3 that the same buffer held before.  The scatter of iteration
+// k polls only its own incident rows (bounded), so no grid barrier separates
+// a gather from the next scatter; the contact-velocity records are
+// double-buffered by iteration parity, and the hazards on both buffers are
+// ordered by the one remaining barrier (a buffer is rewritten two iterations
+// later, after every block has passed the barrier in between).
+// ---------------------------------------------------------------------------
+constexpr long long kRecSpinLimit = 1ll << 20;
+__device__ __forceinline__ unsigned rec_phase(int it) { return ((unsigned)it >> 1) & 1u; }
+__device__ __forceinline__ unsigned long long ld_rel64(const unsigned long long* p) {
+    // (no memory clobber: the loads of a body's incidences are issued together;
+    // a stale word is caught by its phase bit)
+    unsigned long long v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p));
+    return v;
+}
+__device__ __forceinline__ void st_rel64(unsigned long long* p, unsigned long long v) {
+    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ unsigned long long make_rec(float gm, float g, unsigned phase) {
+    return ((unsigned long long)__float_as_uint(g) << 32) | (unsigned long long)(__float_as_uint(gm) | (phase << 31));
+}
+__device__ __forceinline__ bool rec_ok(unsigned long long w, unsigned phase) { return ((unsigned)w >> 31) == phase; }
+
+// the row record of iteration `it` (phase rec_phase(it)), polled until it is
+// there; a wait past the limit records DEV_TIMEOUT and takes the word as is
+__device__ __forceinline__ unsigned long long rec_wait(const unsigned long long* p, unsigned long long w,
+                                                       unsigned phase, int* status) {
+    long long spins = 0;
+    while (!rec_ok(w, phase)) {
+        if (++spins > kRecSpinLimit) {
+            atomicOr(status, DEV_TIMEOUT);
+            break;
+        }
+        // another thread's timeout ends this wait too
+        if ((spins & 255) == 0 && (*(volatile int*)status & DEV_TIMEOUT)) break;
+        if (spins > 16) __nanosleep(20);
+        w = ld_rel64(p);
+    }
+    return w;
+}
+
+__device__ __forceinline__ void incidence_1b(const KArgs<float>& a, int code, const float c[6],
+                                             const unsigned long long* rec, unsigned phase, float alpha_r,
+                                             unsigned long long w0, float w[6]) {
+    const int r = code >> 1;
+    const unsigned long long wv = rec_ok(w0, phase) ? w0 : rec_wait(rec + r, w0, phase, a.status);
+    const float gm0 = fabsf(__uint_as_float((unsigned)wv));
+    const float g0 = __uint_as_float((unsigned)(wv >> 32));
+    const float inv = a.invd ? a.invd[r] : 1.f;
+    const float gm = proj_step(gm0, g0, inv, alpha_r);
+#pragma unroll
+    for (int k = 0; k < 6; ++k) w[k] += gm * c[k];
+}
+
+// phase 1 of iteration it: Uc(it) = K D gamma(it) from the records of it - 1
+__device__ void scatter_1b(const KArgs<float>& a, const BodySlot<float>& S, const unsigned long long* rec,
+                           unsigned phase, float* ucp, float alpha_r) {
+    const int lane = threadIdx.x & (kLanesPerBody - 1);
+    float w[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    unsigned long long w0[kIncPerLane];
+#pragma unroll
+    for (int k = 0; k < kIncPerLane; ++k) w0[k] = S.code[k] >= 0 ? ld_rel64(rec + (S.code[k] >> 1)) : 0ull;
+#pragma unroll
+    for (int k = 0; k < kIncPerLane; ++k)
+        if (S.code[k] >= 0) incidence_1b(a, S.code[k], S.c[k], rec, phase, alpha_r, w0[k], w);
+    const int e_over = S.e0 + kLanesPerBody * kIncPerLane + lane;
+    if (e_over < S.e1) {
+        float K[7];
+        load_K(a, S.b, K);
+        for (int e = e_over; e < S.e1; e += kLanesPerBody) {
+            const int code = a.inc[e];
+            float c[6];
+            load_coefs(a, code, c);
+            apply_K(K, c);
+            incidence_1b(a, code, c, rec, phase, alpha_r, ld_rel64(rec + (code >> 1)), w);
+        }
+    }
+    reduce_lanes(w);
+    if (S.b < a.nbodies && lane == 0) store_rec(ucp + 8 * (int64_t)S.b, w);
+    // bodies beyond one slot per thread
+    const int nslots = gridDim.x * blockDim.x;
+    const int groups_total = nslots / kLanesPerBody;
+    const int gid = (blockIdx.x * blockDim.x + threadIdx.x) / kLanesPerBody;
+    const int warp_first = gid & ~(32 / kLanesPerBody - 1);
+    for (int k = 1; warp_first + k * groups_total < a.nbodies; ++k) {
+        const int b = gid + k * groups_total;
+        float wb[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        if (b < a.nbodies) {
+            float K[7];
+            load_K(a, b, K);
+            const int e0 = a.inc_off[b], e1 = a.inc_off[b + 1];
+            for (int e = e0 + lane; e < e1; e += kLanesPerBody) {
+                const int code = a.inc[e];
+                float c[6];
+                load_coefs(a, code, c);
+                apply_K(K, c);
+                incidence_1b(a, code, c, rec, phase, alpha_r, ld_rel64(rec + (code >> 1)), wb);
+            }
+        }
+        reduce_lanes(wb);
+        if (b < a.nbodies && lane == 0) store_rec(ucp + 8 * (int64_t)b, wb);
+    }
+}
+
+// phase 2 of iteration it for the thread's row: g(it) from Uc(it), the record
+// of it, the BB products and (check) the FP64 residual
+__device__ __forceinline__ void gather_1b(const KArgs<float>& a, RowSlot<float>& S, const float* ucp,
+                                          unsigned long long* rec, unsigned phase, bool check, float alpha_r,
+                                          float v[3], double* resid) {
+    float acc[3] = {0.f, 0.f, 0.f};
+    double res = 0.0;
+    if (S.r >= 0) {
+        float ui[6], uj[6];
+        load_rec(ucp + 8 * (int64_t)S.i, ui);
+        load_rec(ucp + 8 * (int64_t)S.j, uj);
+        double qd = 0.0, dg = 0.0;
+        if (check) {
+            qd = a.q[S.r];
+            dg = a.diag[S.r];
+        }
+        const float gm = proj_step(S.gm, S.gv, S.invd, alpha_r);
+        const float rate = row_rate(S.g, ui, uj);
+        const float g = S.q + (float)a.c * rate;
+        st_rel64(rec + S.r, make_rec(gm, g, phase));
+        bb_accumulate(a, gm - S.gm, g - S.gv, S.invd, acc);
+        if (check) res = fmax(res, fabs(fmin(dg * (double)gm, qd + a.c * (double)rate)));
+        S.gm = gm;
+        S.gv = g;
+    }
+    v[0] = acc[0];
+    v[1] = acc[1];
+    v[2] = acc[2];
+    *resid = res;
+}
+
 template <class R>
 __global__ void __launch_bounds__(kThreads) lcp_kernel(KArgs<R> a) {
     __shared__ double part[kNred];
@@ -652,6 +807,18 @@ __global__ void __launch_bounds__(kThreads) lcp_kernel(KArgs<R> a) {
     scatter_phase(a, bs, 0, false, R(0));
     if (!grid_barrier(a.bar, &epoch, a.status)) return;
     gather_phase(a, rs, nrows, 0, -1, true, R(0), v, &res_t);
+    // one grid barrier per iteration (mixed path): every row has its own
+    // thread, whose records start as the phase-0 record of the initial
+    // iterate (buffer 0) and a phase-1 placeholder (buffer 1, which iteration
+    // 1 writes with phase 0)
+    const bool one_bar = sizeof(R) == sizeof(float) && a.ucp2 != nullptr && nrows <= stride;
+    if constexpr (sizeof(R) == sizeof(float)) {
+        if (one_bar && rs.r >= 0) {
+            rs.gm = fabsf(rs.gm);
+            st_rel64(reinterpret_cast<unsigned long long*>(a.gg[0]) + rs.r, make_rec(rs.gm, rs.gv, 0u));
+            st_rel64(reinterpret_cast<unsigned long long*>(a.gg[1]) + rs.r, make_rec(0.f, 0.f, 1u));
+        }
+    }
     {
         // init reduces two maxima: slot 0 = largest A_aa, slot 3 = residual
         double md = 0.0;
@@ -687,6 +854,101 @@ __global__ void __launch_bounds__(kThreads) lcp_kernel(KArgs<R> a) {
     __syncthreads();
     R alpha_r = sh_alpha_r;
     int cur = 0, it = 0;
+    if constexpr (sizeof(R) == sizeof(float)) {
+        if (one_bar) {
+            // ---- one grid barrier per iteration (see scatter_1b)
+            int fin = 0;  // the iterate returned
+            if (!sh_stop) {
+#ifdef RELCP_LCP_TRACE
+                unsigned long long t_prev = gtimer();
+#endif
+                constexpr size_t kBuf = (size_t)kMaxBlocks * kNred;
+                __shared__ unsigned long long pbuf1[kMaxBlocks * kNred];
+                __shared__ unsigned sh_rmax;
+                fin = -1;
+                for (it = 1; it <= a.max_iter; ++it) {
+                    const bool check = (it % a.check_every) == 0 || it == a.max_iter;
+                    const bool prev_check = it >= 2 && ((it - 1) % a.check_every) == 0;
+                    unsigned long long* part = a.partials + (size_t)(it & 1) * kBuf;
+                    R* uc_it = (it & 1) ? a.ucp2 : a.ucp;
+                    scatter_1b(a, bs, reinterpret_cast<const unsigned long long*>(a.gg[(it - 1) & 1]), rec_phase(it - 1),
+                               uc_it, alpha_r);
+                    TRACE_MARK(0);
+                    if (!grid_barrier(a.bar, &epoch, a.status)) return;
+                    TRACE_MARK(1);
+                    // the previous iteration's partials, complete since this
+                    // barrier: loaded before the gather, staged after it (the
+                    // FP32 sums and the rounded-up residual are low halves)
+                    const int npw = (int)gridDim.x * kNred;
+                    unsigned pf = 0u;
+                    if (it >= 2 && (int)threadIdx.x < npw)
+                        pf = __ldcg(reinterpret_cast<const unsigned*>(a.partials + (size_t)((it - 1) & 1) * kBuf +
+                                                                      threadIdx.x));
+                    gather_1b(a, rs, uc_it, reinterpret_cast<unsigned long long*>(a.gg[it & 1]), rec_phase(it), check,
+                              alpha_r, v, &res_t);
+                    TRACE_MARK(2);
+                    if (it >= 2) {
+                        if ((int)threadIdx.x < npw) pbuf1[threadIdx.x] = pf;
+                        for (int t = threadIdx.x + kThreads; t < npw; t += kThreads)
+                            pbuf1[t] = (unsigned)__ldcg(a.partials + (size_t)((it - 1) & 1) * kBuf + t);
+                    }
+                    block_partials<R>(v, res_t, check, part + (size_t)blockIdx.x * kNred, it >= 2 ? pbuf1 : nullptr,
+                                      it, &sh_alpha_r, true, prev_check, &sh_rmax);
+                    __syncthreads();
+                    alpha_r = sh_alpha_r;
+                    TRACE_MARK(3);
+#ifdef RELCP_LCP_TRACE
+                    if (blockIdx.x == 0 && threadIdx.x == 0) g_lcp_trace[6] += 1;
+#endif
+                    if (prev_check) {
+                        // every block folds the same words: the same decision
+                        const double rsd = (double)__uint_as_float(sh_rmax);
+                        if (rsd <= a.tol) {
+                            resid = rsd;
+                            fin = it - 1;
+                            break;
+                        }
+                    }
+                }
+                if (fin < 0) {
+                    // the cap: the last iterate's residual, after every block's partials
+                    it = a.max_iter;
+                    fin = it;
+                    if (!grid_barrier(a.bar, &epoch, a.status)) return;
+                    const unsigned long long* part = a.partials + (size_t)(it & 1) * kBuf;
+                    if (threadIdx.x < 32) {
+                        unsigned mm = 0u;
+                        for (int b = threadIdx.x; b < (int)gridDim.x; b += 32) mm = max(mm, (unsigned)__ldcg(part + b * kNred + 3));
+                        for (int o = 16; o > 0; o >>= 1) mm = max(mm, __shfl_down_sync(0xffffffffu, mm, o));
+                        if (threadIdx.x == 0) sh_rmax = mm;
+                    }
+                    __syncthreads();
+                    resid = (double)__uint_as_float(sh_rmax);
+                }
+            } else {
+                resid = sh_resid;
+            }
+            pdl_trigger();  // the next kernel in the stream may start launching
+            // outputs: gamma and the contact velocity of the returned iterate
+            // (its record buffer and velocity buffer are intact: iteration
+            // fin + 1 wrote the other ones)
+            const unsigned long long* rf = reinterpret_cast<const unsigned long long*>(a.gg[fin & 1]);
+            for (int r = tid; r < nrows; r += stride) a.gamma_io[r] = fabsf(__uint_as_float((unsigned)ld_rel64(rf + r)));
+            const R* uf = (fin & 1) ? a.ucp2 : a.ucp;
+            for (int b = tid; b < a.nbodies; b += stride) {
+                R u[6];
+                load_rec(uf + 8 * (int64_t)b, u);
+#pragma unroll
+                for (int k = 0; k < 6; ++k) a.ucd[k][b] = (double)u[k];
+            }
+            if (blockIdx.x == 0 && threadIdx.x == 0) {
+                a.result->iterations = (double)it;
+                a.result->residual = resid;
+                if (!(resid <= a.tol)) atomicOr(a.status, DEV_LCP_NOT_CONVERGED);
+            }
+            return;
+        }
+    }
     if (!sh_stop) {
 #ifdef RELCP_LCP_TRACE
         unsigned long long t_prev = gtimer();
@@ -868,7 +1130,9 @@ relcp_status solve_typed(const LcpProblem& pr, LcpScratch& sc, DBuf<R>& pack, in
     const int64_t mc = pr.m_cap > 0 ? pr.m_cap : 1, nb = pr.nbodies, nba = nb > 0 ? nb : 1;
     // (gamma, g) pairs for both buffers, then the 8-wide contact-velocity records
     const size_t pair_elems = (size_t)(2 * mc) * 2;
-    RELCP_TRY(pack.ensure(pair_elems + (size_t)(8 * nba), s));
+    // mixed path: a second contact-velocity buffer for the one-barrier iterations
+    const bool two_uc = sizeof(R) == sizeof(float);
+    RELCP_TRY(pack.ensure(pair_elems + (size_t)((two_uc ? 16 : 8) * nba), s));
     KArgs<R> ka{};
     ka.nrows_dev = pr.nrows_dev;
     ka.nbodies = (int)nb;
@@ -886,6 +1150,7 @@ relcp_status solve_typed(const LcpProblem& pr, LcpScratch& sc, DBuf<R>& pack, in
     ka.gg[0] = reinterpret_cast<V2*>(pack.p);
     ka.gg[1] = reinterpret_cast<V2*>(pack.p) + mc;
     ka.ucp = pack.p + pair_elems;
+    ka.ucp2 = two_uc ? pack.p + pair_elems + (size_t)(8 * nba) : nullptr;
     for (int k = 0; k < 6; ++k) ka.ucd[k] = pr.uc[k];
     ka.c = pr.c;
     ka.tol = pr.tol;
@@ -918,7 +1183,7 @@ relcp_status lcp_reserve(LcpScratch& sc, int64_t m_cap, int64_t nb, bool mixed, 
     RELCP_TRY(sc.inc_off.ensure((size_t)nba + 1, s));
     RELCP_TRY(sc.inc_tmp.ensure((size_t)(2 * mc), s));
     RELCP_TRY(sc.inc.ensure((size_t)(2 * mc), s));
-    const size_t pack = (size_t)(2 * mc) * 2 + (size_t)(8 * nba);
+    const size_t pack = (size_t)(2 * mc) * 2 + (size_t)((mixed ? 16 : 8) * nba);
     if (mixed) RELCP_TRY(sc.packf.ensure(pack, s));
     else RELCP_TRY(sc.packd.ensure(pack, s));
     RELCP_TRY(sc.partials.ensure((size_t)2 * kMaxBlocks * kNred, s));
