@@ -23,12 +23,18 @@
 // Raydan, SIAM J. Numer. Anal. 36, 1999): those partials are complete one
 // barrier earlier, so every block folds them while it gathers and the
 // iteration needs no grid-wide read after its second barrier except on the
-// residual checks (every second iteration).  With FP32 iterates the retarded
-// steps also took fewer iterations on the compaction's LCPs.  The FP64 path
-// checks every iteration and keeps the plain alternation.  The grid barrier
-// spins a bounded number of times; a timeout sets DEV_TIMEOUT and the kernel
-// returns.  Data written inside the launch is read with ld.global.cg
-// (L2), never from a possibly stale L1 line.
+// residual checks (every second iteration).  The FP64 path checks every
+// iteration and keeps the plain alternation.
+//
+// On the mixed path, when every row has a thread of its own, the second grid
+// barrier goes too (scatter_1b): phase 1 of iteration k waits, by polling,
+// only for the records of the rows incident to its body, and the residual
+// test is folded one iteration late like the step length.
+//
+// The grid barrier spins a bounded number of times; a timeout sets
+// DEV_TIMEOUT and the kernel returns.  Data written inside the launch is read
+// with ld.global.cg or ld.relaxed.gpu (L2), never from a possibly stale L1
+// line.
 #include <cooperative_groups.h>
 
 #include "relcp_internal.cuh"
