@@ -515,18 +515,6 @@ bool broadphase_lookahead_params(const BroadphaseScratch& sc, int64_t n, const d
     return true;
 }
 
-relcp_status broadphase_lookahead(int64_t n, const double* x_soa, const double box[3], BroadphaseScratch& sc,
-                                  unsigned long long* dmax_dev, cudaStream_t s) {
-    if (!sc.valid || sc.vn_bodies != n || n < 2) return RELCP_OK;
-    double sfac[3];
-    for (int k = 0; k < 3; ++k) sfac[k] = (box[k] > 0 && sc.Lb[k] > 0) ? box[k] / sc.Lb[k] : 1.0;
-    note_launch();
-    launch_pdl(disp_kernel, dim3((unsigned)((n + kThreads - 1) / kThreads)), dim3(kThreads), 0, s, n, x_soa,
-               sc.xb.p, sfac[0], sfac[1], sfac[2], box[0], box[1], box[2], dmax_dev);
-    RELCP_CUDA(cudaGetLastError());
-    return RELCP_OK;
-}
-
 int64_t broadphase_filter_tiles(int64_t nv) { return (nv + kFcTile - 1) / kFcTile; }
 
 relcp_status broadphase_filter_async(int64_t n, const double* x_soa, const double* rb, const double box[3],

@@ -284,12 +284,8 @@ relcp_status broadphase_cached(int64_t n, const double* x_soa, const double* rb,
 // since the build is dmax, in the box `box` (the bound of broadphase_cached).
 bool verlet_bound_holds(const BroadphaseScratch& sc, int64_t n, const double box[3], double rbmax, double skin,
                         double dmax);
-// atomicMax of the bits of that displacement for positions x_soa in `box` into
-// *dmax_dev (zeroed by the caller); nothing when the cache is not valid
-relcp_status broadphase_lookahead(int64_t n, const double* x_soa, const double box[3], BroadphaseScratch& sc,
-                                  unsigned long long* dmax_dev, cudaStream_t s);
 // the scale factors of that check (false: no valid cached list), for kernels
-// that fold the check into their own pass over the bodies
+// that fold the check into their own pass over the bodies (the trial pass)
 bool broadphase_lookahead_params(const BroadphaseScratch& sc, int64_t n, const double box[3], double sfac[3]);
 // The cached list's exact filter and compaction without a host round trip:
 // pairs into pa, pb, sc.pv (capacity sc.vn), their count at sc.vscan.p[sc.vn].

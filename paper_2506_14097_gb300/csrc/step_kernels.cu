@@ -392,12 +392,6 @@ __global__ void accept_kernel(AcceptArgs a) {
     }
 }
 
-__global__ void wrap_kernel(int64_t n, double* x, double L0, double L1, double L2) {
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const double L[3] = {L0, L1, L2};
-    for (int k = 0; k < 3; ++k) x[k * n + i] = step_math::wrap_coord(x[k * n + i], L[k]);
-}
 
 }  // namespace
 
@@ -590,12 +584,5 @@ relcp_status store_bodies_launch(int64_t n, const double* x, const double* q, co
     return RELCP_OK;
 }
 
-relcp_status wrap_launch(int64_t n, double* x, const double box[3], cudaStream_t s) {
-    if (n == 0) return RELCP_OK;
-    note_launch();
-    wrap_kernel<<<nb(n), kT, 0, s>>>(n, x, box[0], box[1], box[2]);
-    RELCP_CUDA(cudaGetLastError());
-    return RELCP_OK;
-}
 
 }  // namespace relcp

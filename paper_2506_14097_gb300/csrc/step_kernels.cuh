@@ -149,7 +149,6 @@ relcp_status flag_le_launch(int64_t cap, const int* np_dev, const double* phi, d
 relcp_status rows_launch(const RowsArgs& a, cudaStream_t s);
 relcp_status trial_launch(const TrialArgs& a, cudaStream_t s);
 relcp_status accept_launch(const AcceptArgs& a, cudaStream_t s);
-relcp_status wrap_launch(int64_t n, double* x, const double box[3], cudaStream_t s);
 
 // Body state in from a row-major staging block [x 3 | q 4 | axes 3 | vel 6 |
 // fext 6] per body (22 doubles), transposed into the SoA arrays with x
