@@ -293,7 +293,7 @@ relcp_status relcp_lcp_solve(int64_t nrows, int64_t nbodies, const int32_t* ia, 
 /* Learned SNSD initial guess                                           */
 /* ------------------------------------------------------------------ */
 /* A small MLP proposes the Newton start of the SNSD solve at C^k; Newton on
- * the sphere stays the judge of every result (a bad guess costs iterations,
+ * the sphere decides every result (a bad guess costs iterations,
  * never accuracy).  The paper uses no learned component: this is the learned
  * stand-in for the cold start.  Network: 16 inputs -> 128 -> 128 -> 128 -> 8
  * outputs (5 used), ReLU, BF16 tensor-core kernels with FP32 accumulation.

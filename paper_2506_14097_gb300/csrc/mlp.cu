@@ -1,5 +1,5 @@
 // Learned SNSD initial guess (the learned part of the method's Newton start;
-// Newton on the sphere remains the judge of every result).
+// Newton on the sphere decides every result).
 //
 // Network: features (16, 13 used) -> 128 -> 128 -> 128 -> outputs (8, 5 used),
 // ReLU, BF16 operands on the tensor cores (mma.sync.m16n8k16, FP32

@@ -1,7 +1,7 @@
 """Learned SNSD guess on the GPU: features, the BF16 tensor-core forward pass
 and the backward pass against the FP64 reference (oracle/mlp_oracle.py), and
 what the trained network gains inside a real step (fewer Newton iterations at
-C^k, same results: Newton stays the judge).
+C^k, same results: Newton decides every result).
 
 Tolerances: BF16 operands carry a relative rounding of 2^-8 per operand, so
 outputs and gradients of the 3-hidden-layer network agree with FP64 to a few
