@@ -168,6 +168,48 @@ def test_lcp_parity(relcp_gpu, orc, precision):
     assert gam.min() >= 0 and g.min() >= -10 * tol
 
 
+@pytest.mark.parametrize("nb", [30000, 60000])
+def test_lcp_large_random_complementarity(relcp_gpu, nb):
+    """A random contact LCP with 3 rows per body, solved on the mixed path at a
+    size where every row has its own thread (30,000 bodies, 90,000 rows: the
+    iterations with one grid barrier) and one where rows outnumber the threads
+    (60,000 bodies, 180,000 rows: the two-barrier iterations).  Too large for
+    the oracle's Lemke: checked by the properties of the solution, in FP64 on
+    the host: gamma >= 0, g = q + A gamma >= -tol, complementarity within the
+    tolerance, and the returned contact velocity equal to K D^T gamma."""
+    import scipy.sparse as sp
+
+    R = relcp_gpu
+    rng = np.random.default_rng(nb)
+    m = 3 * nb
+    ia = np.repeat(np.arange(nb), 3)
+    ib = (ia + rng.integers(1, nb, size=m)) % nb
+    nn = rng.standard_normal((m, 3))
+    nn /= np.linalg.norm(nn, axis=1, keepdims=True)
+    ta = np.cross(0.5 * rng.standard_normal((m, 3)), nn)
+    tb = np.cross(0.5 * rng.standard_normal((m, 3)), nn)
+    kt, kr, c = 1.0, 12.0, 1e-2
+    qv = rng.uniform(-0.02, 0.05, m)
+    K7 = np.tile(np.array([kt, kr, kr, kr, 0.0, 0.0, 0.0]), (nb, 1))
+    tol = 1e-6
+    geom = np.concatenate([nn, ta, tb], axis=1)
+    gam, uc, info = R.relcp_lcp_solve(dev(ia, torch.int32), dev(ib, torch.int32), dev(geom), dev(qv), dev(K7), c,
+                                      precision=R.RELCP_MIXED, tol=tol, max_iter=20000)
+    gam, uc = gam.cpu().numpy(), uc.cpu().numpy()
+    assert info.status == 0, (info.iterations, info.residual)
+    rows = np.repeat(np.arange(m), 12)
+    cols = np.concatenate([6 * ia[:, None] + np.arange(6), 6 * ib[:, None] + np.arange(6)], 1).ravel()
+    D = sp.csr_matrix((np.concatenate([-nn, -ta, nn, tb], 1).ravel(), (rows, cols)), shape=(m, 6 * nb))
+    Kd = np.tile(np.array([kt, kt, kt, kr, kr, kr]), nb)
+    U = Kd * (D.T @ gam)
+    g = qv + c * (D @ U)
+    Aaa = c * (2 * kt + kr * (ta ** 2).sum(1) + kr * (tb ** 2).sum(1))
+    assert gam.min() >= 0.0
+    assert g.min() >= -10 * tol
+    assert np.abs(np.minimum(Aaa * gam, g)).max() <= 10 * tol
+    assert rel_err(uc, U.reshape(nb, 6)) <= 1e-5
+
+
 def test_lcp_empty_and_zero_rows(relcp_gpu):
     R = relcp_gpu
     K7 = dev(np.ones((3, 7)))
