@@ -447,7 +447,14 @@ def main():
 
     e2e_steps = args.steps if args.e2e_steps is None else args.e2e_steps
     if e2e_steps > 0:
+        if dist:
+            dist.barrier()
         e2e_t, h2d, d2h = run_e2e(R, torch, sc, precision, guess, e2e_steps, mlp_params)
+        if dist:
+            # the slowest replica sets the job's rate, as for the timed region
+            t = torch.tensor([e2e_t], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e2e_t = float(t.item())
         e2e_value = world * sc.n * e2e_steps / e2e_t
     else:
         e2e_value, h2d, d2h = None, 0, 0
