@@ -8,10 +8,14 @@ FP64 GPU path timed on the same steps for comparison.
 
 One JSON line on rank 0.  A "step" is one full time step of Algorithm 1
 (broad phase, SNSD, LCP solves, trial re-evaluations, augmentations).
-Timing: W untimed warm-up steps on a separate context, then K steps from the
-initial state, each bracketed by CUDA events on the library's stream, with a
-256 MiB L2 flush between steps (outside the events); barrier +
-synchronize around the timed region; max over ranks.
+Timing: W untimed warm-up steps on a separate context; then the whole
+2,000-step schedule runs on a fresh context and K of its steps, spread evenly
+over it (step (i + 1/2) 2000 / K for i < K; all of them when K >= 2000), are
+timed, each bracketed by CUDA events on the library's stream after a 256 MiB
+L2 flush (outside the events); the steps in between run untimed.  Barrier +
+synchronize around the timed region; max over ranks.  The rate is
+bodies x K / (sum of the K step times): the schedule's mean step cost,
+estimated from the sample.
 """
 from __future__ import annotations
 
@@ -32,6 +36,17 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 WORKLOAD = "compacting ellipsoid suspension, 32768 bodies, phi 0.1->0.55 over 2000 steps, dt 5e-3, overdamped"
+SCHEDULE_STEPS = 2000
+
+
+def timed_indices(total: int, k: int) -> list:
+    """K step indices spread evenly over a schedule of `total` steps (the
+    midpoints of K equal windows); every step when K >= total."""
+    if k >= total:
+        return list(range(total))
+    return sorted({min(total - 1, int((i + 0.5) * total / k)) for i in range(k)})
+
+
 METRIC = "body-steps/sec at 32k ellipsoids, mixed+learned vs plain FP64 GPU, equal overlap tol"
 UNIT = "body-steps/s"
 
@@ -45,7 +60,7 @@ def peaks():
         return 6800.0, "fallback"
 
 
-def build_scene(n, seed=1, steps=2000):
+def build_scene(n, seed=1, steps=SCHEDULE_STEPS):
     from paper_2506_14097_gb300 import scenes
 
     return scenes.suspension_scene(seed=seed, n=n, phi=0.1, phi_final=0.55, steps=steps, dt=5e-3)
@@ -172,10 +187,12 @@ def new_sim(R, sc, precision, guess, timing, stream, mlp_params):
     return sim
 
 
-def run_gpu_arm(R, torch, sc, precision, guess, steps, warmup, flush, stream, nvtx_from=None, mlp_params=None,
-                timing="lcp", nvtx_to=None):
-    """W warm-up steps on one context, then `steps` timed steps from the initial
-    state on a fresh context.  Returns per-step times and accumulated stats."""
+def run_gpu_arm(R, torch, sc, precision, guess, total, timed, warmup, flush, stream, nvtx_from=None,
+                mlp_params=None, timing="lcp", nvtx_to=None):
+    """W warm-up steps on one context, then the whole schedule of `total`
+    steps from the initial state on a fresh context, with the steps listed in
+    `timed` timed.  Returns the per-step times of the timed steps, their
+    accumulated stats (the window), and stats over every step."""
     x, q, axes = (np.ascontiguousarray(a) for a in (sc.x, sc.q, sc.axes))
     if warmup > 0:
         sim = new_sim(R, sc, precision, guess, None, stream.cuda_stream, mlp_params)
@@ -185,61 +202,90 @@ def run_gpu_arm(R, torch, sc, precision, guess, steps, warmup, flush, stream, nv
         sim.close()
     sim = new_sim(R, sc, precision, guess, timing, stream.cuda_stream, mlp_params)
     sim.set_bodies(x, q, axes)
+    timed_set = set(timed)
     torch.cuda.synchronize()
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in timed]
     acc = dict(lcp_ms=0.0, lcp_bytes=0.0, lcp_launches=0, snsd_ms=0.0, snsd_evals=0, snsd_launches=0, depth_max=0,
                depth_sum=0, rows_max=0, pairs_max=0, lcp_iters=0, max_overlap=0.0, not_converged=0, status=set(),
-               ms_broadphase=0.0, ms_lcp_phase=0.0, ms_other=0.0, ms_step_events=0.0, rebuilds=0)
-    launches0 = R.relcp_kernel_launches()
+               ms_broadphase=0.0, ms_lcp_phase=0.0, ms_other=0.0, ms_step_events=0.0, rebuilds=0, launches=0,
+               rows_sum=0)
+    whole = dict(max_overlap=0.0, depth_max=0, depth_steps=0, lcp_iters=0, status=set(), rows_max=0)
+    windows = []
+    vol = sc.meta["volume"]
+    box = np.asarray(sc.box, dtype=np.float64)
+    j = 0
     with torch.cuda.stream(stream):
-        for k in range(steps):
-            flush.zero_()
+        for k in range(total):
             if nvtx_from is not None and k == nvtx_from:
                 torch.cuda.nvtx.range_push("relcp_profile")
             if nvtx_from is not None and nvtx_to is not None and k == nvtx_to:
                 torch.cuda.nvtx.range_pop()
-            ev[k][0].record(stream)
-            st = sim.step(1, allow=(R.RELCP_ERR_NOT_CONVERGED,))
-            ev[k][1].record(stream)
+            if k in timed_set:
+                flush.zero_()
+                l0 = R.relcp_kernel_launches()
+                ev[j][0].record(stream)
+                st = sim.step(1, allow=(R.RELCP_ERR_NOT_CONVERGED,))
+                ev[j][1].record(stream)
+                acc["launches"] += R.relcp_kernel_launches() - l0
+            else:
+                st = sim.step(1, allow=(R.RELCP_ERR_NOT_CONVERGED,))
             s = sim.stats()
-            acc["status"].add(R.STATUS_NAMES[st])
-            acc["not_converged"] += int(st == R.RELCP_ERR_NOT_CONVERGED)
-            acc["lcp_ms"] += s.ms_lcp_kernel
-            acc["lcp_bytes"] += s.lcp_alg_bytes
-            acc["lcp_launches"] += s.lcp_launches
-            acc["snsd_ms"] += s.ms_snsd_kernel
-            acc["snsd_evals"] += s.snsd_evals
-            acc["snsd_launches"] += s.snsd_launches
-            acc["depth_max"] = max(acc["depth_max"], s.depth)
-            acc["depth_sum"] += s.depth
-            acc["rows_max"] = max(acc["rows_max"], s.n_rows)
-            acc["pairs_max"] = max(acc["pairs_max"], s.n_pairs)
-            acc["lcp_iters"] += s.lcp_iters_total
-            acc["max_overlap"] = max(acc["max_overlap"], s.max_overlap)
-            acc["ms_broadphase"] += s.ms_broadphase
-            acc["ms_lcp_phase"] += s.ms_lcp
-            acc["ms_other"] += s.ms_augment
-            acc["ms_step_events"] += s.ms_total
-            acc["rebuilds"] += s.pair_list_rebuilt
-            acc["guess_steps"] = acc.get("guess_steps", 0) + s.guess_used
-            acc["newton_c0"] = acc.get("newton_c0", 0) + s.newton_iters_c0
-            acc["pairs_total"] = acc.get("pairs_total", 0) + s.n_pairs
+            whole["status"].add(R.STATUS_NAMES[st])
+            whole["max_overlap"] = max(whole["max_overlap"], s.max_overlap)
+            whole["depth_max"] = max(whole["depth_max"], s.depth)
+            whole["depth_steps"] += int(s.depth > 0)
+            whole["lcp_iters"] += s.lcp_iters_total
+            whole["rows_max"] = max(whole["rows_max"], s.n_rows)
+            if k in timed_set:
+                windows.append({"step": k, "phi": vol / float(np.prod(box)), "lcp_iters": s.lcp_iters_total,
+                                "rows": s.n_rows, "depth": s.depth})
+                acc["status"].add(R.STATUS_NAMES[st])
+                acc["not_converged"] += int(st == R.RELCP_ERR_NOT_CONVERGED)
+                acc["lcp_ms"] += s.ms_lcp_kernel
+                acc["lcp_bytes"] += s.lcp_alg_bytes
+                acc["lcp_launches"] += s.lcp_launches
+                acc["snsd_ms"] += s.ms_snsd_kernel
+                acc["snsd_evals"] += s.snsd_evals
+                acc["snsd_launches"] += s.snsd_launches
+                acc["depth_max"] = max(acc["depth_max"], s.depth)
+                acc["depth_sum"] += s.depth
+                acc["rows_max"] = max(acc["rows_max"], s.n_rows)
+                acc["rows_sum"] += s.n_rows
+                acc["pairs_max"] = max(acc["pairs_max"], s.n_pairs)
+                acc["lcp_iters"] += s.lcp_iters_total
+                acc["max_overlap"] = max(acc["max_overlap"], s.max_overlap)
+                acc["ms_broadphase"] += s.ms_broadphase
+                acc["ms_lcp_phase"] += s.ms_lcp
+                acc["ms_other"] += s.ms_augment
+                acc["ms_step_events"] += s.ms_total
+                acc["rebuilds"] += s.pair_list_rebuilt
+                acc["guess_steps"] = acc.get("guess_steps", 0) + s.guess_used
+                acc["newton_c0"] = acc.get("newton_c0", 0) + s.newton_iters_c0
+                acc["pairs_total"] = acc.get("pairs_total", 0) + s.n_pairs
+                j += 1
+            box = np.array(s.box[:3], dtype=np.float64)
     torch.cuda.synchronize()
-    if nvtx_from is not None and nvtx_from < steps and (nvtx_to is None or nvtx_to >= steps):
+    if nvtx_from is not None and nvtx_from < total and (nvtx_to is None or nvtx_to >= total):
         torch.cuda.nvtx.range_pop()
-    acc["launches"] = R.relcp_kernel_launches() - launches0
     times = [a.elapsed_time(b) for a, b in ev]
+    for w, t in zip(windows, times):
+        w["ms"] = t
+    acc["windows"] = windows
     acc["box_final"] = list(R.relcp_get_box(sim.ctx))
     sim.close()
     acc["status"] = sorted(acc["status"])
+    whole["status"] = sorted(whole["status"])
+    acc["whole"] = whole
     return times, acc
 
 
-def run_e2e(R, torch, sc, precision, guess, steps, mlp_params=None):
-    """The same steps through the public C ABI with host buffers: every step
-    copies the body state in (set_bodies: x, q, semi-axes) and the result out
-    (get_bodies: x, q and the step velocity).  The workload has no background
-    velocity or external force, so none is passed in."""
+def run_e2e(R, torch, sc, precision, guess, total, timed, mlp_params=None):
+    """The same schedule through the public C ABI with host buffers: every
+    step copies the body state in (set_bodies: x, q, semi-axes) and the result
+    out (get_bodies: x, q and the step velocity); the steps listed in `timed`
+    are timed on the host clock (device synchronised before each), from the
+    set_bodies call to the return of get_bodies.  The workload has no
+    background velocity or external force, so none is passed in."""
     n = sc.n
     # copies: relcp_get_bodies writes each step's result into x and q, and the
     # scene's own arrays must keep the initial state for the runs after this one
@@ -249,90 +295,201 @@ def run_e2e(R, torch, sc, precision, guess, steps, mlp_params=None):
     sim = R.Simulation(cfg)
     if guess == R.RELCP_GUESS_MLP:
         R.relcp_load_mlp(sim.ctx, mlp_params)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
+    timed_set = set(timed)
     box = np.asarray(sc.box, dtype=np.float64)
-    for _ in range(steps):
-        for k in range(3):
-            cfg.box[k] = box[k]
+    el = 0.0
+    for k in range(total):
+        if k in timed_set:
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+        for i in range(3):
+            cfg.box[i] = box[i]
         R.relcp_set_config(sim.ctx, cfg)
         sim.set_bodies(x, q, axes)
         sim.step(1, allow=(R.RELCP_ERR_NOT_CONVERGED,))
         R.relcp_get_bodies(sim.ctx, x, q, u)
         box = R.relcp_get_box(sim.ctx)
+        if k in timed_set:
+            el += time.perf_counter() - t0
     torch.cuda.synchronize()
-    dt = time.perf_counter() - t0
     sim.close()
     h2d = n * (3 + 4 + 3) * 8
     d2h = n * (3 + 4 + 6) * 8
-    return dt, h2d, d2h
+    return el, h2d, d2h
 
 
 # ---------------------------------------------------------------------------
-# CPU oracle (baseline leg and reference arm)
+# CPU oracle (baseline leg, subset errors and reference arm)
 # ---------------------------------------------------------------------------
-def _oracle_worker(n, steps, budget_s, out_q):
-    os.environ.setdefault("OMP_NUM_THREADS", "1")
+SNAPSHOTS = os.path.join(ROOT, "tests", "golden", "compaction1024_snapshots.npz")
+SUBSET_BODIES = 1024
+
+
+def subset_states():
+    """C^k of the 1,024-body version of the schedule at the start (from the
+    seeded generator) and at the steps stored in the snapshot file, which the
+    FP64 oracle's own trajectory wrote (tests/golden/make_compaction_snapshots.py).
+    Returns the scene and a list of (step, x, q, box)."""
+    sc = build_scene(SUBSET_BODIES)
+    states = [(0, sc.x, sc.q, np.asarray(sc.box, dtype=np.float64))]
+    if os.path.exists(SNAPSHOTS):
+        d = np.load(SNAPSHOTS)
+        if not np.array_equal(d["axes"], sc.axes):
+            raise RuntimeError("snapshot file does not belong to this scene")
+        for i, k in enumerate(d["steps"]):
+            states.append((int(k), d["x"][i], d["q"][i], d["box"][i]))
+    return sc, states
+
+
+def _oracle_steps_worker(x, q, axes, box, dt, eps, skin, rate, nsteps):
+    """`nsteps` consecutive oracle steps from one state (spawned process, one
+    thread); per step the results the parity check compares and its time."""
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[k] = "1"
     sys.path.insert(0, ROOT)
     from oracle import relcp_oracle as O
 
-    sc = build_scene(n)
-    amin = float(sc.axes.min())
-    cfg = O.Config(dynamics=O.OVERDAMPED, dt=sc.dt, eps_ncp=1e-3 * amin, box=tuple(sc.box), skin=0.1 * amin,
-                   strain_rate=sc.meta["strain_rate"])
-    x, q, box = sc.x, sc.q, np.asarray(sc.box)
-    vol = sc.meta["volume"]
-    done = 0
+    out = []
+    box = np.asarray(box, dtype=np.float64)
+    for _ in range(nsteps):
+        cfg = O.Config(dynamics=O.OVERDAMPED, dt=dt, eps_ncp=eps, box=tuple(box), skin=skin, strain_rate=rate)
+        t0 = time.perf_counter()
+        r = O.step(cfg, x, q, axes)
+        el = time.perf_counter() - t0
+        out.append({"seconds": el, "pairs": r.pairs, "ids": np.stack([r.rows_ia, r.rows_ib, r.rows_rec,
+                                                                      r.rows_pair], axis=1).astype(np.int32),
+                    "vel": r.vel, "uc": r.U_contact, "depth": r.depth, "max_overlap": r.max_overlap,
+                    "status": r.status, "ambiguous": r.ambiguous, "rows": int(r.rows_ia.size)})
+        x, q, box = r.x, r.q, np.asarray(r.box)
+    return out
+
+
+def run_oracle_pool(jobs, processes):
+    """Run (state, nsteps) oracle jobs in spawned worker processes (no GPU
+    context is inherited).  Returns the results in job order and the pool's
+    wall time."""
+    from concurrent.futures import ProcessPoolExecutor
+
+    ctx = mp.get_context("spawn")
     t0 = time.perf_counter()
-    phi0 = vol / np.prod(box)
-    while done < steps:
-        r = O.step(O.Config(**{**cfg.__dict__, "box": tuple(box)}), x, q, sc.axes)
-        x, q, box = r.x, r.q, r.box
-        done += 1
-        if time.perf_counter() - t0 > budget_s:
-            break
-    el = time.perf_counter() - t0
-    out_q.put({"bodies": n, "steps": done, "seconds": el, "phi_start": phi0, "phi_end": vol / np.prod(box)})
+    with ProcessPoolExecutor(max_workers=processes, mp_context=ctx) as ex:
+        futs = [ex.submit(_oracle_steps_worker, *job) for job in jobs]
+        res = [f.result() for f in futs]
+    return res, time.perf_counter() - t0
 
 
-def oracle_rate(n, steps, budget_s):
-    """The oracle as it stands, single-threaded (BLAS threads pinned to 1), in
-    a spawned process (no GPU context)."""
-    env_keys = ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")
-    old = {k: os.environ.get(k) for k in env_keys}
-    for k in env_keys:
-        os.environ[k] = "1"
+def host_cores():
     try:
-        ctx = mp.get_context("spawn")
-        qq = ctx.Queue()
-        p = ctx.Process(target=_oracle_worker, args=(n, steps, budget_s, qq))
-        p.start()
-        res = qq.get()
-        p.join()
-    finally:
-        for k, v in old.items():
-            if v is None:
-                os.environ.pop(k, None)
-            else:
-                os.environ[k] = v
-    res["value"] = res["bodies"] * res["steps"] / res["seconds"]
-    return res
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def subset_check(R, torch, arms, nsteps=2, processes=None):
+    """The oracle on the 1,024-body subset (the baseline leg) and the error of
+    each GPU arm against it.  From every subset state both the oracle and each
+    GPU arm take `nsteps` consecutive steps (the GPU carrying its SNSD values,
+    warm starts and cached pair list from its first step to the next, as in
+    the timed run).  Per step: candidate pairs and constraint ids (a, b,
+    recursion, pair) bit for bit, velocities and contact velocities as
+    normwise relative errors, and the GPU's max overlap against eps_NCP.  The
+    first step starts from the identical state; later steps start from each
+    side's own previous result."""
+    sc, states = subset_states()
+    amin = float(sc.axes.min())
+    eps, skin, rate = 1e-3 * amin, 0.1 * amin, sc.meta["strain_rate"]
+    jobs = [(x, q, sc.axes, box, sc.dt, eps, skin, rate, nsteps) for (_, x, q, box) in states]
+    processes = processes or max(1, min(len(jobs), host_cores()))
+    orc, wall = run_oracle_pool(jobs, processes)
+    vol = sc.meta["volume"]
+
+    def rel(a, b):
+        return float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)) if b.size else 0.0
+
+    report = {}
+    for name, (precision, guess, mlp_params) in arms.items():
+        per = []
+        for (k, x, q, box), ores in zip(states, orc):
+            cfg = make_cfg(R, sc, precision, guess, timing=None)
+            for i in range(3):
+                cfg.box[i] = float(box[i])
+            sim = R.Simulation(cfg)
+            if guess == R.RELCP_GUESS_MLP:
+                R.relcp_load_mlp(sim.ctx, mlp_params)
+            sim.set_bodies(np.ascontiguousarray(x), np.ascontiguousarray(q), np.ascontiguousarray(sc.axes))
+            for j, o in enumerate(ores):
+                st = sim.step(1, allow=(R.RELCP_ERR_NOT_CONVERGED,))
+                s = sim.stats()
+                pairs, _ = R.relcp_get_pairs(sim.ctx)
+                ids, _, _ = R.relcp_get_rows(sim.ctx)
+                _, _, v = sim.bodies()
+                uc = R.relcp_get_contact_velocity(sim.ctx, sc.n)
+                per.append({"step": k + j, "phi": vol / float(np.prod(box)) if j == 0 else None,
+                            "from_identical_state": j == 0, "status": R.STATUS_NAMES[st],
+                            "pairs_equal": bool(np.array_equal(pairs, o["pairs"])),
+                            "rows_equal": bool(np.array_equal(ids, o["ids"])), "rows": o["rows"],
+                            "depth": [int(s.depth), int(o["depth"])], "vel_rel_err": rel(v, o["vel"]),
+                            "contact_vel_rel_err": rel(uc, o["uc"]), "max_overlap": float(s.max_overlap),
+                            "oracle_ambiguous": int(o["ambiguous"])})
+            sim.close()
+        first = [p for p in per if p["from_identical_state"]]
+        report[name] = {
+            "identical_start": {"pairs_equal": all(p["pairs_equal"] for p in first),
+                                "rows_equal": all(p["rows_equal"] for p in first),
+                                "vel_rel_err_max": max(p["vel_rel_err"] for p in first),
+                                "contact_vel_rel_err_max": max(p["contact_vel_rel_err"] for p in first)},
+            "all_steps": {"pairs_equal": all(p["pairs_equal"] for p in per),
+                          "rows_equal": all(p["rows_equal"] for p in per),
+                          "vel_rel_err_max": max(p["vel_rel_err"] for p in per),
+                          "contact_vel_rel_err_max": max(p["contact_vel_rel_err"] for p in per)},
+            "max_overlap": max(p["max_overlap"] for p in per), "max_overlap_within_eps":
+                all(p["max_overlap"] <= eps for p in per), "steps": per}
+    steps_done = sum(len(o) for o in orc)
+    cpu_s = sum(r["seconds"] for o in orc for r in o)
+    sample = (f"{nsteps} consecutive oracle steps from each of {len(states)} states of the 1,024-body version of "
+              f"the schedule (steps {', '.join(str(k) for k, *_ in states)}; phi "
+              f"{vol / np.prod(states[0][3]):.3f}-{vol / np.prod(states[-1][3]):.3f}), one process per state on "
+              f"{processes} host cores, {wall:.1f} s wall, {cpu_s:.1f} s of oracle time")
+    cpu = {"value": SUBSET_BODIES * steps_done / wall, "unit": UNIT, "cores": processes, "kind": "oracle",
+           "sample": sample, "per_core_value": SUBSET_BODIES * steps_done / cpu_s,
+           "note": "1,024-body subset; not extrapolated to 32k"}
+    report["eps_ncp"] = eps
+    report["bounds"] = {"fp64": "relative 1e-9", "mixed": "relative 1e-5",
+                        "sets": "pairs and constraint ids bit for bit"}
+    return cpu, report
 
 
 def run_reference(args, rank, world):
+    """The reference arm: the FP64 oracle as it stands, on the host cores.
+    Each of the K sampled steps is one oracle step of the 1,024-body version of
+    the workload from the stored state nearest before its place in the
+    schedule (step (i + 1/2) 2000 / K), the steps run one per process."""
     if rank != 0:
         return
-    # warm-up: a few oracle steps (compiles/loads the C core)
-    oracle_rate(1024, max(1, args.warmup), 60.0)
-    res = oracle_rate(1024, args.steps, args.ref_budget)
-    sample = (f"first {res['steps']} steps (phi {res['phi_start']:.4f}->{res['phi_end']:.4f}) of the 1,024-body "
-              f"version of the workload (same schedule), single-threaded FP64 oracle, {res['seconds']:.1f} s")
-    line = {"impl": "reference", "metric": METRIC, "value": res["value"], "unit": UNIT, "n_gpus": args.gpus,
-            "steps": res["steps"], "warmup": args.warmup, "ms_per_step": 1e3 * res["seconds"] / res["steps"],
+    sc, states = subset_states()
+    amin = float(sc.axes.min())
+    eps, skin, rate = 1e-3 * amin, 0.1 * amin, sc.meta["strain_rate"]
+    pos = timed_indices(SCHEDULE_STEPS, args.steps)
+    picks = [max((st for st in states if st[0] <= p), key=lambda st: st[0]) for p in pos]
+    processes = max(1, min(len(picks), host_cores()))
+    # warm-up: W steps from the initial state (loads and compiles the C core)
+    run_oracle_pool([(sc.x, sc.q, sc.axes, states[0][3], sc.dt, eps, skin, rate, args.warmup)], 1)
+    jobs = [(x, q, sc.axes, box, sc.dt, eps, skin, rate, 1) for (_, x, q, box) in picks]
+    res, wall = run_oracle_pool(jobs, processes)
+    cpu_s = sum(r[0]["seconds"] for r in res)
+    n = len(picks)
+    value = SUBSET_BODIES * n / wall
+    sample = (f"{n} oracle steps of the 1,024-body version of the workload, one per sampled place in the "
+              f"2,000-step schedule, each from the stored state nearest before it (steps "
+              f"{', '.join(str(st[0]) for st in picks)}), {processes} processes, {wall:.1f} s wall, "
+              f"{cpu_s:.1f} s of oracle time")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": n, "warmup": args.warmup, "ms_per_step": 1e3 * wall / n,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "sample_bodies": 1024},
-            "cpu_baseline": {"value": res["value"], "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
-            "e2e": {"value": res["value"], "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+            "config": {"workload": WORKLOAD, "sample_bodies": SUBSET_BODIES},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": processes, "kind": "oracle", "sample": sample,
+                             "per_core_value": SUBSET_BODIES * n / cpu_s},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
@@ -340,24 +497,26 @@ def run_reference(args, rank, world):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--steps", type=int, default=SCHEDULE_STEPS,
+                    help="timed steps, spread evenly over the 2,000-step schedule (all of it at 2000)")
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--bodies", type=int, default=32768)
+    ap.add_argument("--schedule-steps", type=int, default=SCHEDULE_STEPS)
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 comparison run")
-    ap.add_argument("--e2e-steps", type=int, default=None)
-    ap.add_argument("--cpu-budget", type=float, default=20.0)
-    ap.add_argument("--ref-budget", type=float, default=150.0)
+    ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end run through host buffers")
+    ap.add_argument("--subset-steps", type=int, default=2,
+                    help="consecutive steps per 1,024-body subset state in the oracle leg (0 skips the leg)")
     ap.add_argument("--jacobi", type=int, default=0, help="1: Jacobi-scaled projected-gradient steps")
     ap.add_argument("--cold", action="store_true", help="cold SNSD start only (no learned guess)")
     ap.add_argument("--phase-breakdown", type=int, default=1, help="1: extra run with per-phase events")
     ap.add_argument("--batched-scenes", type=int, default=2048,
                     help="scenes of the batched-scene measurement (0 skips it)")
     ap.add_argument("--nvtx-from", type=int, default=None,
-                    help="profiling aid: wrap timed steps >= this index in the NVTX range relcp_profile")
+                    help="profiling aid: wrap schedule steps >= this index in the NVTX range relcp_profile")
     ap.add_argument("--nvtx-to", type=int, default=None, help="profiling aid: end of that range (exclusive)")
     ap.add_argument("--step-times", default=None,
-                    help="write the headline run's per-step CUDA-event times (ms, one per line) to this file")
+                    help="write the headline run's timed steps (schedule index, ms) to this file")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -386,7 +545,10 @@ def main():
     global EXTRA_FLAGS
     if args.jacobi:
         EXTRA_FLAGS |= R.RELCP_FLAG_JACOBI
-    sc = build_scene(args.bodies)
+    sc = build_scene(args.bodies, steps=args.schedule_steps)
+    total = args.schedule_steps
+    timed = timed_indices(total, args.steps)
+    K = len(timed)
     stream = torch.cuda.Stream()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 
@@ -412,50 +574,56 @@ def main():
     clocks = Clocks(local)
     clocks.start()
     t_wall0 = time.perf_counter()
-    times, acc = run_gpu_arm(R, torch, sc, precision, guess, args.steps, args.warmup, flush, stream, args.nvtx_from,
-                             mlp_params, nvtx_to=args.nvtx_to)
-    if args.step_times and rank == 0:
-        with open(args.step_times, "w") as f:
-            f.write("".join("%.6f\n" % t for t in times))
+    times, acc = run_gpu_arm(R, torch, sc, precision, guess, total, timed, args.warmup, flush, stream,
+                             args.nvtx_from, mlp_params, nvtx_to=args.nvtx_to)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
     t_wall = time.perf_counter() - t_wall0
     clk = clocks.stop()
+    if args.step_times and rank == 0:
+        with open(args.step_times, "w") as f:
+            f.write("".join("%d %.6f\n" % (k, t) for k, t in zip(timed, times)))
     total_ms = float(sum(times))
     if dist:
         t = torch.tensor([total_ms], device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         total_ms = float(t.item())
-    value = world * sc.n * args.steps / (total_ms / 1e3)
+    value = world * sc.n * K / (total_ms / 1e3)
+
+    def arm_summary(times_, acc_):
+        t_ = float(sum(times_))
+        return {"value": sc.n * K / (t_ / 1e3), "unit": UNIT, "ms_per_step": t_ / K,
+                "lcp_iters_total": acc_["lcp_iters"], "lcp_kernel_ms": acc_["lcp_ms"], "rows_max": acc_["rows_max"],
+                "depth_max": acc_["depth_max"], "max_overlap": acc_["max_overlap"], "status": acc_["status"],
+                "gpu_launches": acc_["launches"],
+                "whole_schedule": {"max_overlap": acc_["whole"]["max_overlap"],
+                                   "depth_max": acc_["whole"]["depth_max"],
+                                   "lcp_iters": acc_["whole"]["lcp_iters"], "status": acc_["whole"]["status"]}}
 
     cold = None
     if guess == R.RELCP_GUESS_MLP and not args.no_fp64:
-        times_c, acc_c = run_gpu_arm(R, torch, sc, precision, R.RELCP_GUESS_COLD, args.steps, args.warmup, flush,
+        times_c, acc_c = run_gpu_arm(R, torch, sc, precision, R.RELCP_GUESS_COLD, total, timed, args.warmup, flush,
                                      stream)
-        tc = float(sum(times_c))
-        cold = {"value": sc.n * args.steps / (tc / 1e3), "unit": UNIT, "ms_per_step": tc / args.steps,
-                "newton_iters_per_pair_c0": acc_c.get("newton_c0", 0) / max(acc_c.get("pairs_total", 1), 1),
-                "max_overlap": acc_c["max_overlap"], "lcp_iters_total": acc_c["lcp_iters"],
-                "lcp_kernel_ms": acc_c["lcp_ms"], "gpu_launches": acc_c["launches"]}
+        cold = arm_summary(times_c, acc_c)
+        cold["newton_iters_per_pair_c0"] = acc_c.get("newton_c0", 0) / max(acc_c.get("pairs_total", 1), 1)
 
     fp64 = None
     if not args.no_fp64:
-        times64, acc64 = run_gpu_arm(R, torch, sc, R.RELCP_FP64, R.RELCP_GUESS_COLD, args.steps, args.warmup, flush,
-                                     stream)
-        t64 = float(sum(times64))
-        fp64 = {"value": sc.n * args.steps / (t64 / 1e3), "unit": UNIT, "ms_per_step": t64 / args.steps,
-                "depth_max": acc64["depth_max"], "max_overlap": acc64["max_overlap"], "status": acc64["status"],
-                "lcp_iters_total": acc64["lcp_iters"]}
+        times64, acc64 = run_gpu_arm(R, torch, sc, R.RELCP_FP64, R.RELCP_GUESS_COLD, total, timed, args.warmup,
+                                     flush, stream)
+        fp64 = arm_summary(times64, acc64)
 
-    e2e_steps = args.steps if args.e2e_steps is None else args.e2e_steps
-    if e2e_steps > 0:
+    if not args.no_e2e:
         if dist:
             dist.barrier()
-        e2e_t, h2d, d2h = run_e2e(R, torch, sc, precision, guess, e2e_steps, mlp_params)
+        e2e_t, h2d, d2h = run_e2e(R, torch, sc, precision, guess, total, timed, mlp_params)
         if dist:
             # the slowest replica sets the job's rate, as for the timed region
             t = torch.tensor([e2e_t], device="cuda")
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
             e2e_t = float(t.item())
-        e2e_value = world * sc.n * e2e_steps / e2e_t
+        e2e_value = world * sc.n * K / e2e_t
     else:
         e2e_value, h2d, d2h = None, 0, 0
 
@@ -467,45 +635,58 @@ def main():
     # the timed run)
     phases, accp = None, None
     if args.phase_breakdown and rank == 0:
-        _, accp = run_gpu_arm(R, torch, sc, precision, guess, args.steps, args.warmup, flush, stream, None, mlp_params,
-                              timing="phases")
+        _, accp = run_gpu_arm(R, torch, sc, precision, guess, total, timed, args.warmup, flush, stream, None,
+                              mlp_params, timing="phases")
         phases = {"broadphase": accp["ms_broadphase"], "snsd_kernels": accp["snsd_ms"],
                   "lcp_incl_csr": accp["ms_lcp_phase"], "rest": accp["ms_other"],
-                  "to_last_sync": accp["ms_step_events"], "note": "separate run with per-phase CUDA events"}
+                  "to_last_sync": accp["ms_step_events"],
+                  "note": "separate run with per-phase CUDA events, summed over the timed steps"}
 
     hbm, peak_kind = peaks()
     lcp_gbs = acc["lcp_bytes"] / (acc["lcp_ms"] / 1e3) / 1e9 if acc["lcp_ms"] > 0 else 0.0
     line = None
     if rank == 0:
-        cpu = oracle_rate(1024, 10 ** 6, args.cpu_budget) if args.cpu_budget > 0 else None
+        cpu, subset = None, None
+        if args.subset_steps > 0 and world == 1:
+            arms = {"mixed_learned": (precision, guess, mlp_params), "fp64": (R.RELCP_FP64, R.RELCP_GUESS_COLD, None)}
+            cpu, subset = subset_check(R, torch, arms, nsteps=args.subset_steps)
+        vol = sc.meta["volume"]
+        wins = acc["windows"]
+        if len(wins) > 40:  # one entry per tenth of the sample
+            idx = sorted({int(i * len(wins) / 10) for i in range(10)})
+            wins = [wins[i] for i in idx]
         line = {
-            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
+            "warmup": args.warmup, "ms_per_step": total_ms / K, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "bodies": sc.n, "precision": "mixed (FP32 bulk, FP64 checks)",
                        "guess": "learned" if guess == R.RELCP_GUESS_MLP else "cold",
                        "lcp_steps": "jacobi-scaled BB" if args.jacobi else "BB",
-                       "l2": "flushed between steps (256 MiB write)",
+                       "timed_steps": (f"{K} of the {total} schedule steps, spread evenly (step (i + 1/2) {total}/"
+                                       f"{K}); the rest run untimed" if K < total else "all schedule steps"),
+                       "phi_timed": ([acc["windows"][0]["phi"], acc["windows"][-1]["phi"]]
+                                     if acc["windows"] else None),
+                       "l2": "flushed before each timed step (256 MiB write)",
                        "parallelism": "replicas" if world > 1 else "single"},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                    "steps": e2e_steps},
+                    "steps": K, "how": "set_bodies + step + get_bodies per step on host arrays, the same sampled "
+                                       "steps timed on the host clock"},
             "gpu_launches": acc["launches"],
             "roofline": {"kernel": "lcp_kernel (persistent BB projected gradient)", "bound": "hbm",
                          "achieved": lcp_gbs, "peak": hbm, "unit": "GB/s", "frac": lcp_gbs / hbm,
                          "traffic": None, "peak_kind": peak_kind, "launches": acc["lcp_launches"],
-                         "kernel_ms_total": acc["lcp_ms"]},
-            "cpu_baseline": None if cpu is None else {
-                "value": cpu["value"], "unit": UNIT, "cores": 1, "kind": "oracle",
-                "sample": (f"first {cpu['steps']} steps (phi {cpu['phi_start']:.4f}->{cpu['phi_end']:.4f})"
-                           f" of the 1,024-body version of the workload, {cpu['seconds']:.1f} s")},
+                         "kernel_ms_total": acc["lcp_ms"],
+                         "bytes": "per iteration 76 B per row + 75 B per body (FP32 rows, FP64 offsets)"},
+            "cpu_baseline": cpu,
+            "oracle_subset": subset,
             "clocks": clk,
             "fp64_gpu": fp64,
             "speedup_vs_fp64": (value / fp64["value"]) if fp64 else None,
             "mixed_cold": cold,
             "learned": learned_info,
             "batched": batched,
-            "stats": {"depth_max": acc["depth_max"], "depth_mean": acc["depth_sum"] / args.steps,
-                      "rows_max": acc["rows_max"], "pairs_max": acc["pairs_max"],
+            "stats": {"depth_max": acc["depth_max"], "depth_mean": acc["depth_sum"] / K,
+                      "rows_max": acc["rows_max"], "rows_mean": acc["rows_sum"] / K, "pairs_max": acc["pairs_max"],
                       "lcp_iters_total": acc["lcp_iters"], "max_overlap": acc["max_overlap"],
                       "eps_ncp": 1e-3 * float(sc.axes.min()), "status": acc["status"],
                       "snsd_kernel_ms": accp["snsd_ms"] if accp else None,
@@ -515,7 +696,9 @@ def main():
                       "pair_list_rebuilds": acc["rebuilds"],
                       "learned_start_steps": acc.get("guess_steps", 0),
                       "newton_iters_per_pair_c0": acc.get("newton_c0", 0) / max(acc.get("pairs_total", 1), 1),
-                      "phi_final": sc.meta["volume"] / float(np.prod(acc["box_final"]))},
+                      "phi_final": vol / float(np.prod(acc["box_final"])),
+                      "whole_schedule": acc["whole"],
+                      "windows": wins},
         }
         print(json.dumps(line), flush=True)
     if dist:

@@ -94,7 +94,14 @@ typedef struct relcp_config {
 /* fault injection (host side only; nothing is injected on the GPU) */
 enum {
     RELCP_FAULT_ROW_CAPACITY = 1u, /* pretend the row buffer is full: the step reports RELCP_ERR_CAPACITY */
-    RELCP_FAULT_LCP_ITERS = 2u     /* run every LCP with a cap of 1 iteration */
+    RELCP_FAULT_LCP_ITERS = 2u,    /* run every LCP with a cap of 1 iteration */
+    RELCP_FAULT_LCP_TIMEOUT = 4u,  /* the LCP launch's waits give up after 2 ms, and its last block leaves
+                                      before arriving at the first grid barrier: the other blocks' wait runs
+                                      out, the launch ends and the step reports RELCP_ERR_TIMEOUT with the
+                                      context still usable */
+    RELCP_FAULT_NEWTON_ITERS = 8u  /* cap every SNSD Newton phase at 1 iteration: pairs whose start is not
+                                      already stationary are not converged and the step reports
+                                      RELCP_ERR_NEWTON */
 };
 enum {
     RELCP_FLAG_PHASE_TIMING = 1u,  /* record per-phase CUDA-event timings in relcp_step_stats */
@@ -145,7 +152,7 @@ typedef struct relcp_step_stats {
      * SNSD kernel (with RELCP_FLAG_PHASE_TIMING) */
     double ms_lcp_kernel;       /* sum over the step's LCP launches */
     double lcp_alg_bytes;       /* algorithmic bytes of those launches: per projected-gradient
-                                   iteration 120 B per row + 152 B per body (FP64), 68 B + 104 B (mixed) */
+                                   iteration 136 B per row + 150 B per body (FP64), 76 B + 75 B (mixed) */
     double ms_snsd_kernel;      /* sum over the step's SNSD launches */
     int64_t snsd_evals;         /* pair evaluations in those launches */
     int32_t lcp_launches;
@@ -270,7 +277,8 @@ typedef struct relcp_lcp_info {
     int32_t status;       /* relcp_status */
     double residual;      /* max_a |min(A_aa gamma_a, g_a)| at exit (FP64) */
     int32_t grid_blocks;  /* persistent-kernel CTAs used */
-    int32_t pad;
+    int32_t one_barrier;  /* 1: the iterations ran with one grid barrier each (mixed path with every row
+                             in a thread of its own), 0: two grid barriers per iteration */
 } relcp_lcp_info;
 
 /* Matrix-free LCP (Eq. cqpp / Lemma LCP <=> CQP): find gamma >= 0 with

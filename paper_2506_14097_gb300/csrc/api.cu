@@ -55,6 +55,33 @@ int device_sm_count() {
     return sms;
 }
 
+// FP64 -> FP32 and back, element by element (the stateless LCP call's
+// one-time conversions)
+__global__ void narrow_kernel(const double* __restrict__ in, float* __restrict__ out, int64_t n) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = (float)in[i];
+}
+__global__ void widen_kernel(const float* __restrict__ in, double* __restrict__ out, int64_t n) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = (double)in[i];
+}
+static unsigned conv_blocks(int64_t n) {
+    const int64_t b = (n + 255) / 256;
+    return (unsigned)(b < 1 ? 1 : (b > 4096 ? 4096 : b));
+}
+relcp_status narrow_launch(const double* in, float* out, int64_t n, cudaStream_t s) {
+    note_launch();
+    narrow_kernel<<<conv_blocks(n), 256, 0, s>>>(in, out, n);
+    RELCP_CUDA(cudaGetLastError());
+    return RELCP_OK;
+}
+relcp_status widen_launch(const float* in, double* out, int64_t n, cudaStream_t s) {
+    note_launch();
+    widen_kernel<<<conv_blocks(n), 256, 0, s>>>(in, out, n);
+    RELCP_CUDA(cudaGetLastError());
+    return RELCP_OK;
+}
+
 }  // namespace relcp
 
 using namespace relcp;
@@ -496,6 +523,7 @@ relcp_status step_once(relcp_ctx* c) {
         sa.guess_on = &ds->guess_on;
     }
     sa.mixed = mixed ? 1 : 0;
+    sa.newton_cap = (cfg.fault_inject & RELCP_FAULT_NEWTON_ITERS) ? 1 : 0;
     sa.out = snsd_out(c->s0, c->it0);
     sa.eps = 0.0;
     sa.viol = nullptr;
@@ -579,6 +607,10 @@ relcp_status step_once(relcp_ctx* c) {
         pr.mixed = mixed ? 1 : 0;
         pr.tol = cfg.lcp_tol;
         pr.max_iter = (cfg.fault_inject & RELCP_FAULT_LCP_ITERS) ? 1 : cfg.lcp_max_iter;
+        if (cfg.fault_inject & RELCP_FAULT_LCP_TIMEOUT) {
+            pr.wait_ns = kFaultWaitNs;
+            pr.fault_skip_block = 1;
+        }
         pr.gamma = mixed ? (void*)c->r_gammaf.p : (void*)c->r_gamma.p;
         for (int k = 0; k < 6; ++k) pr.uc[k] = c->uc.p + k * n;
         pr.result = &ds->lcp;
@@ -1536,34 +1568,11 @@ relcp_status relcp_lcp_solve(int64_t nrows, int64_t nbodies, const int32_t* ia, 
             if (fail(gf.ensure(9 * ma, s)) || fail(gamf.ensure(ma, s)) || fail(qf.ensure(ma, s)) ||
                 fail(kf.ensure(7 * nba, s)))
                 break;
-            {
-                std::vector<double> hk((size_t)(7 * nb));
-                std::vector<float> hkf((size_t)(7 * nb));
-                if (nb > 0) {
-                    e = cudaMemcpyAsync(hk.data(), kd.p, 7 * nb * sizeof(double), cudaMemcpyDeviceToHost, s);
-                    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-                    for (size_t i = 0; i < hk.size(); ++i) hkf[i] = (float)hk[i];
-                    if (e == cudaSuccess)
-                        e = cudaMemcpyAsync(kf.p, hkf.data(), 7 * nb * sizeof(float), cudaMemcpyHostToDevice, s);
-                    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-                }
-            }
-            std::vector<double> hgd((size_t)(9 * m)), hg((size_t)m), hq((size_t)m);
-            std::vector<float> hgf((size_t)(9 * m)), hgamf((size_t)m), hqf((size_t)m);
-            // host round trip for the one-time conversion of a stateless call
-            if (m > 0) {
-                e = cudaMemcpyAsync(hgd.data(), gd.p, 9 * m * sizeof(double), cudaMemcpyDeviceToHost, s);
-                if (e == cudaSuccess) e = cudaMemcpyAsync(hg.data(), gamma, m * sizeof(double), cudaMemcpyDeviceToHost, s);
-                if (e == cudaSuccess) e = cudaMemcpyAsync(hq.data(), qv, m * sizeof(double), cudaMemcpyDeviceToHost, s);
-                if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-                for (size_t i = 0; i < hgd.size(); ++i) hgf[i] = (float)hgd[i];
-                for (size_t i = 0; i < hg.size(); ++i) hgamf[i] = (float)hg[i];
-                for (size_t i = 0; i < hq.size(); ++i) hqf[i] = (float)hq[i];
-                if (e == cudaSuccess) e = cudaMemcpyAsync(qf.p, hqf.data(), m * sizeof(float), cudaMemcpyHostToDevice, s);
-                if (e == cudaSuccess) e = cudaMemcpyAsync(gf.p, hgf.data(), 9 * m * sizeof(float), cudaMemcpyHostToDevice, s);
-                if (e == cudaSuccess) e = cudaMemcpyAsync(gamf.p, hgamf.data(), m * sizeof(float), cudaMemcpyHostToDevice, s);
-                if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-            }
+            // one-time narrowing of the stateless call's inputs, on the device
+            if (nb > 0 && fail(narrow_launch(kd.p, kf.p, 7 * nb, s))) break;
+            if (m > 0 && (fail(narrow_launch(gd.p, gf.p, 9 * m, s)) || fail(narrow_launch(gamma, gamf.p, m, s)) ||
+                          fail(narrow_launch(qv, qf.p, m, s))))
+                break;
             if (e != cudaSuccess) {
                 set_error("%s", cudaGetErrorString(e));
                 st = RELCP_ERR_CUDA;
@@ -1607,10 +1616,8 @@ relcp_status relcp_lcp_solve(int64_t nrows, int64_t nbodies, const int32_t* ia, 
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
         if (e == cudaSuccess && m > 0) {
             if (mixed) {
-                std::vector<float> hgamf((size_t)m);
-                e = cudaMemcpy(hgamf.data(), gamf.p, m * sizeof(float), cudaMemcpyDeviceToHost);
-                std::vector<double> hg(hgamf.begin(), hgamf.end());
-                if (e == cudaSuccess) e = cudaMemcpy(gamma, hg.data(), m * sizeof(double), cudaMemcpyHostToDevice);
+                if (fail(widen_launch(gamf.p, gamma, m, s))) break;
+                e = cudaStreamSynchronize(s);
             } else {
                 e = cudaMemcpyAsync(gamma, gam.p, m * sizeof(double), cudaMemcpyDeviceToDevice, s);
             }
@@ -1624,7 +1631,9 @@ relcp_status relcp_lcp_solve(int64_t nrows, int64_t nbodies, const int32_t* ia, 
         info->residual = hr.residual;
         info->grid_blocks = blocks;
         info->status = status_from_device(hst);
-        info->pad = 0;
+        // the kernel's rule for one grid barrier per iteration (mixed path,
+        // every row in a thread slot of its own)
+        info->one_barrier = (mixed && m <= (int64_t)blocks * lcp_threads()) ? 1 : 0;
     } while (0);
     gd.release(s);
     kd.release(s);

@@ -55,16 +55,18 @@ constexpr int kThreads = RELCP_LCP_THREADS;
 constexpr int kMaxCtasPerSm = 1;
 constexpr int kMixedCheckEvery = 2;  // mixed path: FP64 termination residual every 2nd iteration
 
-#ifdef RELCP_LCP_TRACE
-// optional phase timing of block 0 (nanoseconds summed over iterations):
-// [0] scatter, [1] barrier 1, [2] gather, [3] block reduction + partials,
-// [4] barrier 2, [5] grid reduction + step length, [6] iterations
-__device__ unsigned long long g_lcp_trace[8];
 __device__ __forceinline__ unsigned long long gtimer() {
     unsigned long long t;
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
     return t;
 }
+__device__ __forceinline__ int ld_status(const int* p) { return *(const volatile int*)p; }
+
+#ifdef RELCP_LCP_TRACE
+// optional phase timing of block 0 (nanoseconds summed over iterations):
+// [0] scatter, [1] barrier 1, [2] gather, [3] block reduction + partials,
+// [4] barrier 2, [5] grid reduction + step length, [6] iterations
+__device__ unsigned long long g_lcp_trace[8];
 #define TRACE_MARK(k)                                                            \
     do {                                                                         \
         if (blockIdx.x == 0 && threadIdx.x == 0) {                               \
@@ -79,7 +81,6 @@ __device__ __forceinline__ unsigned long long gtimer() {
     } while (0)
 #endif
 constexpr int kNred = 4;  // ss, sy, yy, residual-or-maxdiag
-constexpr long long kSpinLimit = 1ll << 26;
 
 template <class R>
 struct Vec2;
@@ -118,6 +119,8 @@ struct KArgs {
     unsigned* bar;
     int* status;
     LcpDevResult* result;
+    unsigned long long wait_ns;  // bound of every wait (grid barrier, row records)
+    int skip_block;              // fault injection: the last block leaves before its first barrier arrival
 };
 
 __device__ __forceinline__ double ldcg(const double* p) { return __ldcg(p); }
@@ -137,9 +140,12 @@ __device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
 // e * gridDim.x.  After a __syncthreads, thread 0 of each block arrives with
 // a release add (which publishes every write the block made before the
 // __syncthreads) and polls with acquire loads (the block's later reads see
-// every block's published writes).  It sleeps only after a short busy spin
-// and gives up after kSpinLimit polls (DEV_TIMEOUT).
-__device__ bool grid_barrier(unsigned* count, unsigned* epoch, int* status) {
+// every block's published writes).  It sleeps only after a short busy spin.
+// Each poll also loads the status word (issued before the acquire load, so
+// both are in flight together): a DEV_TIMEOUT set anywhere in the grid ends
+// the wait, and so does a wait longer than wait_ns (globaltimer), which sets
+// DEV_TIMEOUT.  Returns false on either; the caller returns from the kernel.
+__device__ bool grid_barrier(unsigned* count, unsigned* epoch, int* status, unsigned long long wait_ns) {
     __shared__ int timed_out;
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -147,13 +153,28 @@ __device__ bool grid_barrier(unsigned* count, unsigned* epoch, int* status) {
         const unsigned target = (++(*epoch)) * gridDim.x;
         red_add_release(count, 1u);
         long long spins = 0;
-        while (ld_acquire(count) < target) {
-            if (++spins > kSpinLimit) {
-                atomicOr(status, DEV_TIMEOUT);
+        unsigned long long t0 = 0;
+        for (;;) {
+            const int st = ld_status(status);
+            const unsigned cnt = ld_acquire(count);
+            if (st & DEV_TIMEOUT) {
                 timed_out = 1;
                 break;
             }
-            if (spins > 256) __nanosleep(16);
+            if (cnt >= target) break;
+            if (++spins > 256) {
+                __nanosleep(16);
+                if ((spins & 63) == 0) {
+                    const unsigned long long t = gtimer();
+                    if (t0 == 0) {
+                        t0 = t;
+                    } else if (t - t0 > wait_ns) {
+                        atomicOr(status, DEV_TIMEOUT);
+                        timed_out = 1;
+                        break;
+                    }
+                }
+            }
         }
     }
     __syncthreads();
@@ -663,7 +684,6 @@ __device__ void gather_phase(const KArgs<R>& a, RowSlot<R>& S, const int nrows, 
 // ordered by the one remaining barrier (a buffer is rewritten two iterations
 // later, after every block has passed the barrier in between).
 // ---------------------------------------------------------------------------
-constexpr long long kRecSpinLimit = 1ll << 20;
 __device__ __forceinline__ unsigned rec_phase(int it) { return ((unsigned)it >> 1) & 1u; }
 __device__ __forceinline__ unsigned long long ld_rel64(const unsigned long long* p) {
     // (no memory clobber: the loads of a body's incidences are issued together;
@@ -681,17 +701,25 @@ __device__ __forceinline__ unsigned long long make_rec(float gm, float g, unsign
 __device__ __forceinline__ bool rec_ok(unsigned long long w, unsigned phase) { return ((unsigned)w >> 31) == phase; }
 
 // the row record of iteration `it` (phase rec_phase(it)), polled until it is
-// there; a wait past the limit records DEV_TIMEOUT and takes the word as is
+// there; a wait past wait_ns records DEV_TIMEOUT and takes the word as is
+// (another thread's timeout ends the wait too), and the grid barrier that
+// follows returns false in every block that sees the flag
 __device__ __forceinline__ unsigned long long rec_wait(const unsigned long long* p, unsigned long long w,
-                                                       unsigned phase, int* status) {
+                                                       unsigned phase, int* status, unsigned long long wait_ns) {
     long long spins = 0;
+    unsigned long long t0 = 0;
     while (!rec_ok(w, phase)) {
-        if (++spins > kRecSpinLimit) {
-            atomicOr(status, DEV_TIMEOUT);
-            break;
+        ++spins;
+        if ((spins & 63) == 0) {
+            if (ld_status(status) & DEV_TIMEOUT) break;
+            const unsigned long long t = gtimer();
+            if (t0 == 0) {
+                t0 = t;
+            } else if (t - t0 > wait_ns) {
+                atomicOr(status, DEV_TIMEOUT);
+                break;
+            }
         }
-        // another thread's timeout ends this wait too
-        if ((spins & 255) == 0 && (*(volatile int*)status & DEV_TIMEOUT)) break;
         if (spins > 16) __nanosleep(20);
         w = ld_rel64(p);
     }
@@ -702,7 +730,7 @@ __device__ __forceinline__ void incidence_1b(const KArgs<float>& a, int code, co
                                              const unsigned long long* rec, unsigned phase, float alpha_r,
                                              unsigned long long w0, float w[6]) {
     const int r = code >> 1;
-    const unsigned long long wv = rec_ok(w0, phase) ? w0 : rec_wait(rec + r, w0, phase, a.status);
+    const unsigned long long wv = rec_ok(w0, phase) ? w0 : rec_wait(rec + r, w0, phase, a.status, a.wait_ns);
     const float gm0 = fabsf(__uint_as_float((unsigned)wv));
     const float g0 = __uint_as_float((unsigned)(wv >> 32));
     const float inv = a.invd ? a.invd[r] : 1.f;
@@ -808,10 +836,13 @@ __global__ void __launch_bounds__(kThreads) lcp_kernel(KArgs<R> a) {
     RowSlot<R> rs;
     load_body_slot(a, tid / kLanesPerBody, threadIdx.x & (kLanesPerBody - 1), bs);
     load_row_slot(a, tid, nrows, rs);
-    if (!grid_barrier(a.bar, &epoch, a.status)) return;
+    // fault injection: a block that never arrives; every other block's wait
+    // at the barrier below runs out (wait_ns) and the launch reports DEV_TIMEOUT
+    if (a.skip_block && blockIdx.x == gridDim.x - 1) return;
+    if (!grid_barrier(a.bar, &epoch, a.status, a.wait_ns)) return;
     // ---- init: Uc = K D gamma0, g0, residual, max diagonal
     scatter_phase(a, bs, 0, false, R(0));
-    if (!grid_barrier(a.bar, &epoch, a.status)) return;
+    if (!grid_barrier(a.bar, &epoch, a.status, a.wait_ns)) return;
     gather_phase(a, rs, nrows, 0, -1, true, R(0), v, &res_t);
     // one grid barrier per iteration (mixed path): every row has its own
     // thread, whose records start as the phase-0 record of the initial
@@ -839,7 +870,7 @@ __global__ void __launch_bounds__(kThreads) lcp_kernel(KArgs<R> a) {
             o[3] = to_word(part[3]);
         }
     }
-    if (!grid_barrier(a.bar, &epoch, a.status)) return;
+    if (!grid_barrier(a.bar, &epoch, a.status, a.wait_ns)) return;
     grid_reduce<R>(a.partials, 0x9u, tot);
     // the step length, the residual and the stop decision are computed by
     // thread 0 of each block (identically in every block: same reduced values)
@@ -880,7 +911,7 @@ __global__ void __launch_bounds__(kThreads) lcp_kernel(KArgs<R> a) {
                     scatter_1b(a, bs, reinterpret_cast<const unsigned long long*>(a.gg[(it - 1) & 1]), rec_phase(it - 1),
                                uc_it, alpha_r);
                     TRACE_MARK(0);
-                    if (!grid_barrier(a.bar, &epoch, a.status)) return;
+                    if (!grid_barrier(a.bar, &epoch, a.status, a.wait_ns)) return;
                     TRACE_MARK(1);
                     // the previous iteration's partials, complete since this
                     // barrier: loaded before the gather, staged after it (the
@@ -920,7 +951,7 @@ __global__ void __launch_bounds__(kThreads) lcp_kernel(KArgs<R> a) {
                     // the cap: the last iterate's residual, after every block's partials
                     it = a.max_iter;
                     fin = it;
-                    if (!grid_barrier(a.bar, &epoch, a.status)) return;
+                    if (!grid_barrier(a.bar, &epoch, a.status, a.wait_ns)) return;
                     const unsigned long long* part = a.partials + (size_t)(it & 1) * kBuf;
                     if (threadIdx.x < 32) {
                         unsigned mm = 0u;
@@ -969,7 +1000,7 @@ __global__ void __launch_bounds__(kThreads) lcp_kernel(KArgs<R> a) {
             unsigned long long* part = a.partials + (kRetard ? (size_t)(it & 1) * kBuf : 0);
             scatter_phase(a, bs, cur, true, alpha_r);
             TRACE_MARK(0);
-            if (!grid_barrier(a.bar, &epoch, a.status)) return;
+            if (!grid_barrier(a.bar, &epoch, a.status, a.wait_ns)) return;
             TRACE_MARK(1);
             // the previous iteration's partials (complete since its second
             // barrier) are loaded before this iteration gathers and stored to
@@ -991,7 +1022,7 @@ __global__ void __launch_bounds__(kThreads) lcp_kernel(KArgs<R> a) {
             block_partials<R>(v, res_t, check, part + (size_t)blockIdx.x * kNred,
                               (kRetard && it >= 2) ? pbuf : nullptr, it, &sh_alpha_r);
             TRACE_MARK(3);
-            if (!grid_barrier(a.bar, &epoch, a.status)) return;
+            if (!grid_barrier(a.bar, &epoch, a.status, a.wait_ns)) return;
             TRACE_MARK(4);
             cur = 1 - cur;
             if (!kRetard || check) {
@@ -1165,12 +1196,16 @@ relcp_status solve_typed(const LcpProblem& pr, LcpScratch& sc, DBuf<R>& pack, in
     ka.bar = reinterpret_cast<unsigned*>(sc.inc_count.p + 2 * (nb > 0 ? nb : 1));  // zeroed with the counts
     ka.status = pr.status;
     ka.result = pr.result;
+    ka.wait_ns = pr.wait_ns ? pr.wait_ns : kLcpWaitNs;
+    ka.skip_block = pr.fault_skip_block;
     int64_t work = pr.m_cap > kLanesPerBody * nb ? pr.m_cap : kLanesPerBody * nb;
     (void)kernel_ms;
     return launch_lcp(ka, work, sc, s, blocks, pr.ev_before, pr.ev_after);
 }
 
 }  // namespace
+
+int lcp_threads() { return kThreads; }
 
 relcp_status lcp_diag_launch(int64_t nrows, const int32_t* ia, const int32_t* ib, View<9, const double> geom,
                              View<7, const double> K, double c, double* diag, cudaStream_t s) {

@@ -343,6 +343,7 @@ struct SnsdArgs {
     int* newton_max;                 // may be null: atomicMax of the Newton iteration counts
     unsigned long long* iters_sum;   // may be null: sum of the Newton iteration counts
     int* status;                     // DEV_NEWTON
+    int newton_cap;                  // > 0: Newton iteration cap of every phase (fault injection)
 };
 relcp_status snsd_launch(const SnsdArgs& a, cudaStream_t s);
 
@@ -389,7 +390,13 @@ struct LcpProblem {
     int* status;                 // device status word (DEV_* bits OR-ed)
     cudaEvent_t ev_before;       // recorded right before / after the persistent launch (or null)
     cudaEvent_t ev_after;
+    // every device wait of the launch gives up after this many nanoseconds
+    // (0: kLcpWaitNs) and sets DEV_TIMEOUT
+    unsigned long long wait_ns;
+    int fault_skip_block;        // fault injection: the last block leaves before its first barrier arrival
 };
+constexpr unsigned long long kLcpWaitNs = 2000000000ull;  // 2 s
+constexpr unsigned long long kFaultWaitNs = 2000000ull;   // 2 ms (RELCP_FAULT_LCP_TIMEOUT)
 // lcp_solve in two parts: the body incidence CSR of the rows, then the
 // persistent solve (the second may be launched apart from the first, e.g.
 // between timing events while the first is part of a captured graph)
@@ -403,10 +410,18 @@ relcp_status lcp_diag_launch(int64_t nrows, const int32_t* ia, const int32_t* ib
 // algorithmic bytes of one projected-gradient iteration: every row's
 // geometry, offset, diagonal, gamma and g read once and gamma, g written once;
 // every body's operator read once and its contact velocity written and read once
+// Algorithmic bytes of one projected-gradient iteration: per row the ids
+// (8 B), the row's 9 geometry scalars, its offset, gamma, the previous gamma
+// and g read and gamma and g written (FP64: 136 B; FP32 geometry and iterates
+// with an FP64 offset: 76 B); per body its operator K, the contact velocity
+// written and read and the wrench (FP64: 150 B; FP32: 75 B).
 inline double lcp_bytes_per_iter(int64_t nrows, int64_t nbodies, bool mixed) {
-    return mixed ? 68.0 * nrows + 104.0 * nbodies : 120.0 * nrows + 152.0 * nbodies;
+    return mixed ? 76.0 * nrows + 75.0 * nbodies : 136.0 * nrows + 150.0 * nbodies;
 }
 void release(LcpScratch& sc, cudaStream_t s);
+int lcp_threads();  // threads per CTA of the persistent LCP kernel
+relcp_status narrow_launch(const double* in, float* out, int64_t n, cudaStream_t s);
+relcp_status widen_launch(const float* in, double* out, int64_t n, cudaStream_t s);
 
 int device_sm_count();
 

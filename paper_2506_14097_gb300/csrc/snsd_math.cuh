@@ -185,7 +185,9 @@ struct PairResult {
 // FP32 iterations + FP64 polish, else FP64 throughout
 __device__ __forceinline__ void snsd_pair(const double d[3], const Sym3<double>& Pa, const Sym3<double>& Pb,
                                           bool has_guess, double g0, double g1, double g2, bool mixed,
-                                          PairResult& o) {
+                                          PairResult& o, int cap = 0) {
+    // cap > 0 bounds every Newton phase (fault injection: RELCP_FAULT_NEWTON_ITERS)
+    const int cap32 = cap > 0 ? cap : 30, cap64 = cap > 0 ? cap : 50;
     double n[3];
     int iters = 0;
     double G = 0.0;
@@ -216,7 +218,7 @@ __device__ __forceinline__ void snsd_pair(const double d[3], const Sym3<double>&
         }
         if (!have) cold_start(df, Pfa, Pfb, nf);
         float Gf;
-        int rf = newton_sphere(nf, df, Pfa, Pfb, scalef, 30, &Gf);
+        int rf = newton_sphere(nf, df, Pfa, Pfb, scalef, cap32, &Gf);
         iters = rf >= 0 ? rf : -rf;
         n[0] = nf[0];
         n[1] = nf[1];
@@ -247,7 +249,7 @@ __device__ __forceinline__ void snsd_pair(const double d[3], const Sym3<double>&
             // the FP32 phase failed: FP64 Newton from its last iterate
             normalize3(n);
             const double scale = 1.0 + sqrt(dot3(d, d));
-            r = newton_sphere(n, d, Pa, Pb, scale, 50, &G);
+            r = newton_sphere(n, d, Pa, Pb, scale, cap64, &G);
         }
     } else {
         const double scale = 1.0 + sqrt(dot3(d, d));
@@ -263,7 +265,7 @@ __device__ __forceinline__ void snsd_pair(const double d[3], const Sym3<double>&
             }
         }
         if (!have) cold_start(d, Pa, Pb, n);
-        r = newton_sphere(n, d, Pa, Pb, scale, 50, &G);
+        r = newton_sphere(n, d, Pa, Pb, scale, cap64, &G);
     }
     o.ok = r >= 0;
     if (r < 0) iters = -(iters + (-r));

@@ -32,7 +32,7 @@ RELCP_INERTIAL, RELCP_OVERDAMPED = 0, 1
 RELCP_FP64, RELCP_MIXED = 0, 1
 RELCP_GUESS_COLD, RELCP_GUESS_MLP = 0, 1
 RELCP_PTR_HOST, RELCP_PTR_DEVICE = 0, 1
-RELCP_FAULT_ROW_CAPACITY, RELCP_FAULT_LCP_ITERS = 1, 2
+RELCP_FAULT_ROW_CAPACITY, RELCP_FAULT_LCP_ITERS, RELCP_FAULT_LCP_TIMEOUT, RELCP_FAULT_NEWTON_ITERS = 1, 2, 4, 8
 RELCP_FLAG_PHASE_TIMING = 1
 RELCP_FLAG_NO_WARM_START = 2
 RELCP_FLAG_JACOBI = 4
@@ -67,7 +67,7 @@ class relcp_step_stats(ctypes.Structure):
 
 class relcp_lcp_info(ctypes.Structure):
     _fields_ = [("iterations", c_int32), ("status", c_int32), ("residual", c_double), ("grid_blocks", c_int32),
-                ("pad", c_int32)]
+                ("one_barrier", c_int32)]
 
 
 MLP_IN, MLP_HID, MLP_OUT = 16, 128, 8

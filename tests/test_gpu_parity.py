@@ -197,6 +197,11 @@ def test_lcp_large_random_complementarity(relcp_gpu, nb):
                                       precision=R.RELCP_MIXED, tol=tol, max_iter=20000)
     gam, uc = gam.cpu().numpy(), uc.cpu().numpy()
     assert info.status == 0, (info.iterations, info.residual)
+    # the path taken: one grid barrier per iteration exactly when every row
+    # has a thread of its own (152 SMs x 640 threads = 97,280 slots on GB300)
+    assert info.one_barrier == int(m <= info.grid_blocks * 640)
+    if torch.cuda.get_device_properties(0).multi_processor_count >= 152:
+        assert info.one_barrier == (1 if nb == 30000 else 0)
     rows = np.repeat(np.arange(m), 12)
     cols = np.concatenate([6 * ia[:, None] + np.arange(6), 6 * ib[:, None] + np.arange(6)], 1).ravel()
     D = sp.csr_matrix((np.concatenate([-nn, -ta, nn, tb], 1).ravel(), (rows, cols)), shape=(m, 6 * nb))
@@ -305,6 +310,34 @@ def test_step_parity_compacting_suspension(relcp_gpu, orc):
         ref, stats = compare_step(R, orc, sck, oc, gcfg)
         assert ref.rows_ia.size > 100
         x, q, box = ref.x, ref.q, ref.box
+    # the same state translated by s and wrapped into the box: the wrapped
+    # bodies' background velocities change by multiples of strain_rate x L,
+    # which the minimum-image offsets of their pairs must cancel; the GPU step
+    # matches the oracle's from the shifted state, and its gamma per row and
+    # contact velocities equal those of the unshifted state
+    oc = orc.Config(**{**ocfg.__dict__, "box": tuple(box)})
+    gcfg = R.make_config(dynamics=R.RELCP_OVERDAMPED, dt=sc.dt, eps_ncp=1e-3 * amin, box=tuple(box),
+                         skin=0.1 * amin, strain_rate=rate, length_scale=amin)
+    out = []
+    for s_ in (np.zeros(3), np.array([0.37, 0.61, 0.5]) * box):
+        xs = x + s_
+        xs -= box * np.floor(xs / box)
+        sck = scenes.Scene(x=xs, q=q, axes=sc.axes, vel=np.zeros((sc.n, 6)), fext=np.zeros((sc.n, 6)), box=box,
+                           dt=sc.dt)
+        ref, stats = compare_step(R, orc, sck, oc, gcfg)
+        sim = R.Simulation(gcfg)
+        sim.set_bodies(np.ascontiguousarray(xs), np.ascontiguousarray(q), np.ascontiguousarray(sc.axes))
+        sim.step(1)
+        ids, _, gam = R.relcp_get_rows(sim.ctx)
+        out.append((ids, gam, R.relcp_get_contact_velocity(sim.ctx, sc.n), sim.bodies()[0], s_))
+        sim.close()
+    (ids0, g0, u0, x0, _), (ids1, g1, u1, x1, s1) = out
+    assert np.array_equal(ids0, ids1)
+    assert rel_err(g1, g0) <= 1e-9 and rel_err(u1, u0) <= 1e-9
+    box1 = box * (1 + rate * sc.dt)
+    d = x1 - s1 * (1 + rate * sc.dt) - x0
+    d -= box1 * np.rint(d / box1)
+    assert np.abs(d).max() <= 1e-12 * box1.max()
 
 
 def test_cached_pair_list_bitexact_over_steps(relcp_gpu, orc):
@@ -500,6 +533,62 @@ def test_fault_injection_and_caps(relcp_gpu, orc):
     assert sim.step(1, allow=(R.RELCP_ERR_RECURSION_LIMIT,)) == R.RELCP_ERR_RECURSION_LIMIT
     ids, geom, gam = R.relcp_get_rows(sim.ctx)
     assert (ids[:, 2] == 0).all()
+    sim.close()
+
+
+def test_device_wait_timeout_reported(relcp_gpu, orc):
+    """A block of the persistent LCP launch that never arrives at the grid
+    barrier (host-set fault RELCP_FAULT_LCP_TIMEOUT: the launch's waits give
+    up after 2 ms and its last block leaves before its first arrival): every
+    other block's bounded wait runs out, the launch ends, and the step returns
+    RELCP_ERR_TIMEOUT promptly.  The context stays usable: with the fault
+    cleared the same state steps like the oracle, on both precision paths."""
+    import time
+
+    R = relcp_gpu
+    sc = scenes.lattice_scene(seed=4, n=4096, spacing=1.9, dt=1e-2, vel_sigma=2.0, omega_sigma=1.0)
+    for precision, bound in ((R.RELCP_FP64, 1e-9), (R.RELCP_MIXED, 1e-5)):
+        ocfg, gcfg = cfg_pair(R, orc, sc, orc.INERTIAL, precision, fault_inject=R.RELCP_FAULT_LCP_TIMEOUT)
+        sim = R.Simulation(gcfg)
+        sim.set_bodies(sc.x, sc.q, sc.axes, sc.vel)
+        t0 = time.perf_counter()
+        st = sim.step(1, allow=(R.RELCP_ERR_TIMEOUT,))
+        assert st == R.RELCP_ERR_TIMEOUT
+        assert time.perf_counter() - t0 < 5.0
+        assert "timed out" in R.last_error()
+        gcfg.fault_inject = 0
+        R.relcp_set_config(sim.ctx, gcfg)
+        sim.set_bodies(sc.x, sc.q, sc.axes, sc.vel)
+        assert sim.step(1) == R.RELCP_OK
+        ref = orc.step(ocfg, sc.x, sc.q, sc.axes, sc.vel)
+        assert ref.status == 0 and ref.rows_ia.size > 100
+        ids, _, _ = R.relcp_get_rows(sim.ctx)
+        assert np.array_equal(ids, np.stack([ref.rows_ia, ref.rows_ib, ref.rows_rec, ref.rows_pair], axis=1))
+        x, q, v = sim.bodies()
+        assert rel_err(v, ref.vel) <= bound
+        sim.close()
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_newton_failure_reported(relcp_gpu, precision):
+    """With every SNSD Newton phase capped at one iteration (host-set fault
+    RELCP_FAULT_NEWTON_ITERS) the pairs whose start is not already stationary
+    do not converge: the step completes and reports RELCP_ERR_NEWTON; with the
+    cap lifted the same state steps without error."""
+    R = relcp_gpu
+    sc = scenes.lattice_scene(seed=2, n=64, spacing=1.8, dt=1e-2, vel_sigma=3.0, omega_sigma=1.5)
+    amin = float(sc.axes.min())
+    cfg = R.make_config(dynamics=R.RELCP_INERTIAL, precision=precision, dt=1e-2, eps_ncp=1e-3 * amin,
+                        box=tuple(sc.box), skin=0.1 * amin, length_scale=amin,
+                        fault_inject=R.RELCP_FAULT_NEWTON_ITERS)
+    sim = R.Simulation(cfg)
+    sim.set_bodies(sc.x, sc.q, sc.axes, sc.vel)
+    assert sim.step(1, allow=(R.RELCP_ERR_NEWTON,)) == R.RELCP_ERR_NEWTON
+    assert sim.stats().status == R.RELCP_ERR_NEWTON
+    cfg.fault_inject = 0
+    R.relcp_set_config(sim.ctx, cfg)
+    sim.set_bodies(sc.x, sc.q, sc.axes, sc.vel)
+    assert sim.step(1) == R.RELCP_OK
     sim.close()
 
 
