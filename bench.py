@@ -132,7 +132,7 @@ class Clocks:
                 "samples": len(sm)}
 
 
-def run_batched(R, torch, n_scenes, steps=100, reps=3, rank=0, world=1, dist=None):
+def run_batched(R, torch, n_scenes, steps=100, reps=3, rank=0, world=1, dist=None, threads=None):
     """The batched-scene workload: n_scenes independent lattice scenes (bodies
     log-uniform in [2, 512], own seed and dt), `steps` steps of every scene in
     ONE persistent launch, block size from the autotuner.  Each timed launch
@@ -149,7 +149,10 @@ def run_batched(R, torch, n_scenes, steps=100, reps=3, rank=0, world=1, dist=Non
     offsets, x, q, axes, vel, params = scenes.pack_scenes(scs)
     b = R.Batch(R.make_config(dynamics=R.RELCP_INERTIAL, precision=R.RELCP_MIXED))
     b.set_scenes(offsets, x, q, axes, params, vel=vel)
-    threads = b.autotune(None)
+    if threads:
+        b.set_threads(threads)
+    else:
+        threads = b.autotune(None)
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     times, status = [], set()
     for k in range(reps + 1):
@@ -316,6 +319,70 @@ def run_e2e(R, torch, sc, precision, guess, total, timed, mlp_params=None):
     h2d = n * (3 + 4 + 3) * 8
     d2h = n * (3 + 4 + 6) * 8
     return el, h2d, d2h
+
+
+def run_colony(R, torch, cells, mlp_params, shapes=("ellipsoid",)):
+    """The growing colony from one cell to `cells` cells, mixed path, with the
+    learned start (when a trained network is given) and with the cold start."""
+    from paper_2506_14097_gb300 import studies
+
+    out = {"workload": f"planar colony, 1 -> {cells} cells, dt 0.05, growth N(0.01, 0.001), division at L = 2 "
+                       f"with N(0, 0.05) rad jitter, eps 5e-4, mixed path"}
+    for shp in shapes:
+        shape = R.RELCP_SHAPE_SPHEROCYLINDER if shp == "spherocylinder" else R.RELCP_SHAPE_ELLIPSOID
+        arms = [("cold", R.RELCP_GUESS_COLD)]
+        if mlp_params is not None and shape == R.RELCP_SHAPE_ELLIPSOID:
+            arms.insert(0, ("learned", R.RELCP_GUESS_MLP))
+        for name, guess in arms:
+            out[f"{shp}_{name}"] = studies.colony_run(cells, shape=shape, guess=guess, mlp_params=mlp_params)
+    return out
+
+
+def learned_fresh_state(R, torch, sc, mlp_params, flush, stream, at_step=1500, reps=5):
+    """Where the learned start runs: a step whose SNSD at C^k is evaluated
+    afresh for every candidate pair (a state given by set_bodies, as after a
+    restart or any change of the bodies).  The compaction's state after
+    `at_step` untimed steps is stepped once, `reps` times on fresh contexts,
+    with the cold start and with the learned start: step time (CUDA events,
+    L2 flushed before), Newton iterations per pair at C^k, and the pairs whose
+    start the network declined."""
+    sim = R.Simulation(make_cfg(R, sc, R.RELCP_MIXED, R.RELCP_GUESS_COLD, timing=None), stream.cuda_stream)
+    sim.set_bodies(sc.x, sc.q, sc.axes)
+    sim.step(at_step, allow=(R.RELCP_ERR_NOT_CONVERGED,))
+    x, q, _ = sim.bodies()
+    box = R.relcp_get_box(sim.ctx)
+    sim.close()
+    out = {"state": f"compaction state after {at_step} steps, phi {sc.meta['volume'] / float(np.prod(box)):.3f}"}
+    for name, guess in (("cold", R.RELCP_GUESS_COLD), ("learned", R.RELCP_GUESS_MLP)):
+        times, its, evals, declined, used = [], [], [], [], []
+        for _ in range(reps):
+            cfg = make_cfg(R, sc, R.RELCP_MIXED, guess, timing=None)
+            for k in range(3):
+                cfg.box[k] = float(box[k])
+            sim = R.Simulation(cfg, stream.cuda_stream)
+            if guess == R.RELCP_GUESS_MLP:
+                R.relcp_load_mlp(sim.ctx, mlp_params)
+            sim.set_bodies(x, q, sc.axes)
+            with torch.cuda.stream(stream):
+                flush.zero_()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                sim.step(1, allow=(R.RELCP_ERR_NOT_CONVERGED,))
+                e1.record(stream)
+            torch.cuda.synchronize()
+            st = sim.stats()
+            times.append(e0.elapsed_time(e1))
+            its.append(st.newton_iters_c0 / max(st.snsd_c0_evaluated, 1))
+            evals.append(int(st.snsd_c0_evaluated))
+            declined.append(int(st.newton_fallbacks))
+            used.append(int(st.guess_used))
+            sim.close()
+        out[name] = {"ms_step_median": float(np.median(times)), "newton_iters_per_pair_c0": float(np.median(its)),
+                     "pairs_evaluated_c0": evals[0], "declined_pairs": declined[0], "learned_start_used": used[0]}
+    out["newton_iters_ratio"] = out["learned"]["newton_iters_per_pair_c0"] / max(out["cold"]["newton_iters_per_pair_c0"],
+                                                                              1e-30)
+    out["step_time_ratio"] = out["learned"]["ms_step_median"] / out["cold"]["ms_step_median"]
+    return out
 
 
 # ---------------------------------------------------------------------------
@@ -510,8 +577,24 @@ def main():
     ap.add_argument("--jacobi", type=int, default=0, help="1: Jacobi-scaled projected-gradient steps")
     ap.add_argument("--cold", action="store_true", help="cold SNSD start only (no learned guess)")
     ap.add_argument("--phase-breakdown", type=int, default=1, help="1: extra run with per-phase events")
+    ap.add_argument("--refinement", type=int, default=1,
+                    help="1: the two-ellipsoid refinement sweep (dt 0.1 .. 1e-4, about a minute)")
     ap.add_argument("--batched-scenes", type=int, default=2048,
                     help="scenes of the batched-scene measurement (0 skips it)")
+    ap.add_argument("--batched-steps", type=int, default=100)
+    ap.add_argument("--batched-threads", type=int, default=0,
+                    help="fixed block size of the batched kernel (0: autotuned)")
+    ap.add_argument("--colony-cells", type=int, default=0,
+                    help="grow the planar colony (ellipsoidal cells, learned and cold start) to this many cells "
+                         "(0 skips it: tens of thousands of steps, see --only-colony)")
+    ap.add_argument("--only-colony", action="store_true",
+                    help="run only the colony measurement (both cell shapes) and print its JSON")
+    ap.add_argument("--only-learned", action="store_true",
+                    help="profiling aid: harvest, train (20 epochs) and one learned-start step on a fresh state")
+    ap.add_argument("--only-refinement", action="store_true",
+                    help="run only the two-ellipsoid refinement sweep down to dt 1e-5 (about 7 minutes) and print it")
+    ap.add_argument("--only-batched", action="store_true",
+                    help="profiling aid: run only the batched-scene measurement and print its JSON")
     ap.add_argument("--nvtx-from", type=int, default=None,
                     help="profiling aid: wrap schedule steps >= this index in the NVTX range relcp_profile")
     ap.add_argument("--nvtx-to", type=int, default=None, help="profiling aid: end of that range (exclusive)")
@@ -542,6 +625,45 @@ def main():
     from paper_2506_14097_gb300 import relcp as R
 
     R.load()
+    if args.only_refinement:
+        from paper_2506_14097_gb300 import studies
+
+        t_r = time.perf_counter()
+        out = studies.refinement_sweep(dts=(1e-1, 1e-2, 1e-3, 1e-4, 1e-5))
+        out["wall_s"] = time.perf_counter() - t_r
+        print(json.dumps(out), flush=True)
+        return
+    if args.only_learned:
+        from paper_2506_14097_gb300 import learned
+
+        feat, targ = learned.harvest_compaction(n=4096, seed=11, steps=300, every=10)
+        t0 = time.perf_counter()
+        mlp, losses = learned.train(feat, targ, epochs=20, batch=4096, lr=2e-3, seed=0)
+        torch.cuda.synchronize()
+        t_train = time.perf_counter() - t0
+        sc = build_scene(args.bodies, steps=args.schedule_steps)
+        stream = torch.cuda.Stream()
+        flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+        out = learned_fresh_state(R, torch, sc, mlp, flush, stream, reps=1)
+        out["train_s"] = t_train
+        out["loss"] = [losses[0], losses[-1]]
+        print(json.dumps(out), flush=True)
+        return
+    if args.only_colony:
+        mlp = None
+        if not args.cold:
+            from paper_2506_14097_gb300 import learned
+
+            feat, targ = learned.harvest_compaction(n=4096, seed=11, steps=300, every=10)
+            mlp, _ = learned.train(feat, targ, epochs=20, batch=4096, lr=2e-3, seed=0)
+        print(json.dumps(run_colony(R, torch, args.colony_cells, mlp, shapes=("ellipsoid", "spherocylinder"))),
+              flush=True)
+        return
+    if args.only_batched:
+        out = run_batched(R, torch, args.batched_scenes, steps=args.batched_steps, reps=1,
+                          threads=args.batched_threads or None)
+        print(json.dumps(out), flush=True)
+        return
     global EXTRA_FLAGS
     if args.jacobi:
         EXTRA_FLAGS |= R.RELCP_FLAG_JACOBI
@@ -627,8 +749,21 @@ def main():
     else:
         e2e_value, h2d, d2h = None, 0, 0
 
-    batched = (run_batched(R, torch, args.batched_scenes, rank=rank, world=world, dist=dist)
+    batched = (run_batched(R, torch, args.batched_scenes, steps=args.batched_steps, rank=rank, world=world, dist=dist,
+                           threads=args.batched_threads or None)
                if args.batched_scenes > 0 else None)
+    fresh = (learned_fresh_state(R, torch, sc, mlp_params, flush, stream)
+             if (mlp_params is not None and rank == 0 and total >= 1500) else None)
+    colony = run_colony(R, torch, args.colony_cells, mlp_params) if (args.colony_cells > 0 and rank == 0) else None
+    refinement = None
+    if args.refinement and rank == 0:
+        from paper_2506_14097_gb300 import studies
+
+        t_r = time.perf_counter()
+        refinement = studies.refinement_sweep(dts=(1e-1, 1e-2, 1e-3, 1e-4))
+        refinement["wall_s"] = time.perf_counter() - t_r
+        refinement["workload"] = ("two ellipsoids (radii 1, 1, 2) at 45 degrees, unit opposing forces, overdamped "
+                                  "(xi = 1), eps 1e-5, t in [0, 40], FP64 batched path")
 
     # phase breakdown: a separate run of the headline configuration with events
     # between all phases (their host cost inflates its step times, so it is not
@@ -684,7 +819,10 @@ def main():
             "speedup_vs_fp64": (value / fp64["value"]) if fp64 else None,
             "mixed_cold": cold,
             "learned": learned_info,
+            "learned_fresh_state": fresh,
             "batched": batched,
+            "refinement": refinement,
+            "colony": colony,
             "stats": {"depth_max": acc["depth_max"], "depth_mean": acc["depth_sum"] / K,
                       "rows_max": acc["rows_max"], "rows_mean": acc["rows_sum"] / K, "pairs_max": acc["pairs_max"],
                       "lcp_iters_total": acc["lcp_iters"], "max_overlap": acc["max_overlap"],

@@ -56,14 +56,28 @@ typedef enum relcp_status {
     RELCP_ERR_STATE = 8             /* call out of order (e.g. step before set_bodies) */
 } relcp_status;
 
-enum { RELCP_INERTIAL = 0, RELCP_OVERDAMPED = 1 };
+/* RELCP_OVERDAMPED_2D: the overdamped law in the z = 0 plane (the growing colony of Sec. 5.4): the
+ * generalised velocity has the three components (u_x, u_y, omega_z) with the SPD mobility
+ * diag(1/(xi L), 1/(xi L), 12/(xi L^3)) of Eq. ellipsoid_mobility; every row keeps its entries on those
+ * components only, U_free is projected onto them, so bodies given in the plane (z = 0, rotations about z)
+ * stay in it. */
+enum { RELCP_INERTIAL = 0, RELCP_OVERDAMPED = 1, RELCP_OVERDAMPED_2D = 2 };
 enum { RELCP_FP64 = 0, RELCP_MIXED = 1 };
 enum { RELCP_GUESS_COLD = 0, RELCP_GUESS_MLP = 1 };
 enum { RELCP_PTR_HOST = 0, RELCP_PTR_DEVICE = 1 };
+/* Body shape of a scene.  RELCP_SHAPE_ELLIPSOID: semi-axes (a, b, c) along the body axes.
+ * RELCP_SHAPE_SPHEROCYLINDER (the colony cells of Sec. 5.4): a segment of half-length h along the body x
+ * axis swept by a ball of radius rho, given as the semi-axes row (h + rho, rho, rho); its SNSD is the
+ * segment distance minus the radii, with the normal along the closest points and the first minimal
+ * candidate of (interior stationary point, s = -h_a, s = +h_a, t = -h_b, t = +h_b) taken when parallel
+ * segments tie.  Spherocylinders are stepped with the overdamped laws only, take no learned start, and
+ * intersecting segments (no normal) report RELCP_ERR_NEWTON. */
+enum { RELCP_SHAPE_ELLIPSOID = 0, RELCP_SHAPE_SPHEROCYLINDER = 1 };
 
 /* Time-step parameters (Algorithm 1: Require C^k, F_ext, M, eps_NCP). */
 typedef struct relcp_config {
-    int32_t dynamics;      /* RELCP_INERTIAL (Eq. law_inertia) or RELCP_OVERDAMPED (Eq. law_overdamped) */
+    int32_t dynamics;      /* RELCP_INERTIAL (Eq. law_inertia), RELCP_OVERDAMPED (Eq. law_overdamped) or
+                              RELCP_OVERDAMPED_2D (the same law in the z = 0 plane) */
     int32_t precision;     /* RELCP_FP64: every operation FP64.  RELCP_MIXED: FP32 LCP iterations, SNSD
                               Newton iterations and constraint-row assembly; FP64 SNSD polish (Phi),
                               row offsets (Phi + c d^T U), overlap test, LCP residual and the state. */
@@ -89,6 +103,8 @@ typedef struct relcp_config {
     uint64_t seed;         /* reserved for randomised components (MLP training batches) */
     uint32_t fault_inject; /* host-side fault injection mask, RELCP_FAULT_* (tests) */
     uint32_t flags;        /* RELCP_FLAG_* */
+    int32_t shape;         /* RELCP_SHAPE_* of every body (batched scenes: of every scene) */
+    int32_t reserved;      /* 0 */
 } relcp_config;
 
 /* fault injection (host side only; nothing is injected on the GPU) */
@@ -109,6 +125,9 @@ enum {
                                       gamma of the same pair (the solution is the same within lcp_tol) */
     RELCP_FLAG_JACOBI = 4u,        /* projected-gradient steps scaled by 1 / A_aa, BB lengths in the
                                       matching metric (same solution, fewer iterations on uneven rows) */
+    RELCP_FLAG_LEARNED_ALWAYS = 128u, /* with RELCP_GUESS_MLP: run the learned start on every C^k evaluation of
+                                      at least one pair (by default it runs when a step evaluates 4,096 pairs
+                                      or more at C^k, where its fixed cost pays) */
     RELCP_FLAG_HOST_STAGING = 64u, /* relcp_set_bodies / relcp_get_bodies copy host arrays through pinned
                                       staging buffers even where the device can read and write the caller's
                                       host memory in place (through the host page tables) */
@@ -146,7 +165,8 @@ typedef struct relcp_step_stats {
     double ms_broadphase, ms_snsd, ms_lcp, ms_augment, ms_total; /* only with RELCP_FLAG_PHASE_TIMING */
     int64_t steps_done;         /* steps since relcp_set_bodies */
     int32_t guess_used;         /* 1 when the learned SNSD guess seeded this step's C^k evaluation */
-    int32_t newton_fallbacks;   /* pairs whose learned guess was rejected and re-solved cold */
+    int32_t newton_fallbacks;   /* pairs of the learned start whose guess the network itself declined
+                                   (trust logit <= 0): their Newton solve started cold */
     /* kernel-level timing: CUDA events around each launch of the persistent LCP
      * kernel (with RELCP_FLAG_PHASE_TIMING or RELCP_FLAG_LCP_TIMING) and of the
      * SNSD kernel (with RELCP_FLAG_PHASE_TIMING) */
@@ -392,9 +412,12 @@ typedef struct {
     int32_t lcp_iters;    /* projected-gradient iterations, summed over those steps */
     int32_t n_pairs;      /* candidate pairs of the last step */
     int32_t n_rows;       /* constraint rows of the last step */
-    int32_t pad;
+    int32_t aug_steps;    /* steps since relcp_batch_set_scenes whose overlap test found a violation
+                             (Phi < -eps_ncp at a trial): rows were appended, or the recursion cap
+                             stopped the step */
     double max_overlap;   /* largest overlap after the last step */
     double lcp_residual;  /* natural residual of the last LCP */
+    double max_overlap_all; /* largest overlap after any step since relcp_batch_set_scenes */
 } relcp_scene_stats;
 
 /* Create an empty batch on the current device; the stream as in relcp_create. */
@@ -423,14 +446,26 @@ relcp_status relcp_batch_get_bodies(relcp_batch* b, double* x, double* q, double
 /* Per-scene statistics (host array of n_scenes). */
 relcp_status relcp_batch_scene_stats(relcp_batch* b, relcp_scene_stats* out);
 
-/* Time the candidate block sizes (64, 128, 256, 512 threads) on two steps of
- * the loaded scenes (the scenes' state is restored afterwards) and keep the
- * fastest.  cache_path (may be NULL): a JSON file of earlier choices, keyed by
+/* The last step of one scene (Algorithm 1): its candidate pairs at C^k
+ * (pairs: host, n_pairs x 2 int32 body indices local to the scene, i < j,
+ * i-major with j ascending) and its constraint rows (row_ids: host, n_rows x 4
+ * int32 = body a, body b, recursion index that created the row, index of its
+ * pair in the pair list), A_0 first, each recursion's rows after it in pair
+ * order.  Either output may be NULL (then only the counts are returned);
+ * RELCP_ERR_CAPACITY when a given cap is below the count (the counts are still
+ * written).  Before the scene's first step both counts are 0. */
+relcp_status relcp_batch_get_scene_contacts(relcp_batch* b, int32_t scene, int32_t* pairs, int64_t pair_cap,
+                                            int64_t* n_pairs, int32_t* row_ids, int64_t row_cap, int64_t* n_rows);
+
+/* Time the candidate block sizes (64, 128, 256, 512 threads; a size the kernel
+ * cannot run with is skipped) on two steps of the loaded scenes
+ * (the scenes' state is restored afterwards) and keep the fastest; the result
+ * is the block size.  cache_path (may be NULL): a JSON file of earlier choices, keyed by
  * device, precision and the scenes' size histogram; a hit skips the timing, a
  * miss adds the result.  *threads_out (may be NULL) receives the choice. */
 relcp_status relcp_batch_autotune(relcp_batch* b, const char* cache_path, int32_t* threads_out);
 
-/* Fix the block size (a multiple of 32 in [32, 1024]); 0 = untuned default. */
+/* Fix the block size (a multiple of 32 in [32, 1024]); 0 = untuned default (128 threads). */
 relcp_status relcp_batch_set_threads(relcp_batch* b, int32_t threads);
 
 void relcp_batch_destroy(relcp_batch* b);

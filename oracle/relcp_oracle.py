@@ -36,6 +36,7 @@ from . import build as _build
 
 INERTIAL = 0
 OVERDAMPED = 1
+OVERDAMPED_2D = 2  # bodies confined to the z = 0 plane: three DOFs (u_x, u_y, omega_z)
 
 _lib = None
 
@@ -135,7 +136,7 @@ def operator_K(dynamics: int, dt: float, q: np.ndarray, axes: np.ndarray, densit
     evaluated at C^k and held fixed over the step.
     Returns kt (n,) and Kr (n, 3, 3)."""
     n = axes.shape[0]
-    if dynamics == OVERDAMPED:
+    if dynamics in (OVERDAMPED, OVERDAMPED_2D):
         L = 2.0 * axes.max(axis=1)
         kt = 1.0 / (drag_xi * L)
         Kr = np.zeros((n, 3, 3))
@@ -181,6 +182,91 @@ def snsd(pairs: np.ndarray, x: np.ndarray, q: np.ndarray, axes: np.ndarray, box:
                              _dp(np.ascontiguousarray(box, dtype=np.float64)), _dp(out), _ip(flags))
     out = out[:P]
     return out[:, 0].copy(), out[:, 1:4].copy(), out[:, 4:7].copy(), out[:, 7:10].copy(), flags[:P].copy()
+
+
+# ---------------------------------------------------------------------------
+# spherocylinders (Sec. 5.4 colony cells): a segment of half-length h along
+# the body x axis, swept by a ball of radius rho; semi-axes row (h + rho, rho, rho)
+# ---------------------------------------------------------------------------
+SHAPE_ELLIPSOID = 0
+SHAPE_SPHEROCYLINDER = 1
+
+
+def capsule_geometry(q, axes):
+    """Per body: unit axis u = R(q) e_x, segment half-length h, radius rho."""
+    R = quat_rot(q)
+    u = R[:, :, 0]
+    rho = np.asarray(axes, dtype=np.float64)[:, 1]
+    h = np.asarray(axes, dtype=np.float64)[:, 0] - rho
+    return u, h, rho
+
+
+def segment_closest_params(w, u, ha, v, hb):
+    """Parameters (s, t) of the closest points A + s u, B + t v (s in
+    [-ha, ha], t in [-hb, hb]) of two segments with B - A = w, u and v unit:
+    the minimiser of f(s, t) = |w + t v - s u|^2 over the rectangle, taken as
+    the best of the candidates (the interior stationary point when it lies
+    inside, then the edge minimisers at s = -ha, +ha, t = -hb, +hb); the first
+    minimal candidate in that order wins a tie (parallel segments).  Plain
+    loop, one pair at a time."""
+    uv = float(u @ v)
+    wu, wv = float(w @ u), float(w @ v)
+    cands = []
+    det = 1.0 - uv * uv
+    if det > 1e-14:
+        s0 = (wu - uv * wv) / det
+        t0 = (uv * wu - wv) / det
+        if abs(s0) <= ha and abs(t0) <= hb:
+            cands.append((s0, t0))
+    for s_ in (-ha, ha):
+        cands.append((s_, min(max(s_ * uv - wv, -hb), hb)))
+    for t_ in (-hb, hb):
+        cands.append((min(max(wu + t_ * uv, -ha), ha), t_))
+    best, bf = None, None
+    for s_, t_ in cands:
+        r = w + t_ * v - s_ * u
+        f = float(r @ r)
+        if bf is None or f < bf:
+            best, bf = (s_, t_), f
+    return best
+
+
+def snsd_capsules(pairs, x, q, axes, box):
+    """Shared-normal signed distance of spherocylinder pairs: Phi = |Q - P| -
+    rho_a - rho_b with P, Q the closest points of the two segments (minimum
+    image), n = (Q - P)/|Q - P| from a to b, support points y_a = P + rho_a n,
+    y_b = Q - rho_b n, lever arms r = y - c.  Segments that intersect (no
+    normal) are flagged.  Returns (phi, n, r_a, r_b, flags)."""
+    pairs = np.asarray(pairs)
+    P_ = pairs.shape[0]
+    u, h, rho = capsule_geometry(q, axes)
+    phi = np.zeros(P_)
+    nrm = np.zeros((P_, 3))
+    ra = np.zeros((P_, 3))
+    rb = np.zeros((P_, 3))
+    fl = np.zeros(P_, dtype=np.int32)
+    box = np.asarray(box, dtype=np.float64)
+    for k in range(P_):
+        i, j = int(pairs[k, 0]), int(pairs[k, 1])
+        w = min_image(x[j] - x[i], box)
+        s_, t_ = segment_closest_params(w, u[i], h[i], u[j], h[j])
+        dv = w + t_ * u[j] - s_ * u[i]
+        dist = float(np.linalg.norm(dv))
+        if dist <= 1e-12:
+            fl[k] = 1
+            continue
+        nn = dv / dist
+        phi[k] = dist - rho[i] - rho[j]
+        nrm[k] = nn
+        ra[k] = s_ * u[i] + rho[i] * nn
+        rb[k] = t_ * u[j] - rho[j] * nn
+    return phi, nrm, ra, rb, fl
+
+
+def snsd_shape(shape, pairs, x, q, axes, box):
+    if shape == SHAPE_SPHEROCYLINDER:
+        return snsd_capsules(pairs, x, q, axes, box)
+    return snsd(pairs, x, q, axes, box)
 
 
 def snsd_from_d(d, Pa, Pb):
@@ -310,6 +396,7 @@ class Config:
     density: float = 1.0
     strain_rate: float = 0.0
     max_recursion: int = 64
+    shape: int = SHAPE_ELLIPSOID
 
 
 @dataclass
@@ -347,14 +434,34 @@ class StepResult:
 
 def free_velocity(cfg: Config, x, vel, fext, kt, Kr, box):
     """U_free = vel + K F_ext, plus the affine background velocity
-    strain_rate * (x - L/2) on periodic axes when the box is compacted."""
+    strain_rate * (x - L/2) on periodic axes when the box is compacted.  In the
+    plane (OVERDAMPED_2D) only u_x, u_y and omega_z are kept."""
     U = np.array(vel, dtype=np.float64, copy=True)
     U += apply_K(kt, Kr, np.asarray(fext, dtype=np.float64))
     if cfg.strain_rate != 0.0:
         for k in range(3):
             if box[k] > 0:
                 U[:, k] += cfg.strain_rate * (x[:, k] - 0.5 * box[k])
+    if cfg.dynamics == OVERDAMPED_2D:
+        U[:, 2] = 0.0
+        U[:, 3] = 0.0
+        U[:, 4] = 0.0
     return U
+
+
+def planar_rows(nrm, ta, tb):
+    """Rows of the planar problem (OVERDAMPED_2D): the generalised velocity
+    has the three components (u_x, u_y, omega_z) with the SPD mobility
+    diag(k_t, k_t, k_r) of Eq. ellipsoid_mobility; embedded in the six-DOF
+    layout, a row keeps its entries on those components and has none on
+    u_z, omega_x, omega_y."""
+    nrm = np.array(nrm, dtype=np.float64, copy=True)
+    ta = np.array(ta, dtype=np.float64, copy=True)
+    tb = np.array(tb, dtype=np.float64, copy=True)
+    nrm[:, 2] = 0.0
+    ta[:, :2] = 0.0
+    tb[:, :2] = 0.0
+    return nrm, ta, tb
 
 
 def step(cfg: Config, x, q, axes, vel=None, fext=None, band: float = 1e-9, lcp_solver=None) -> StepResult:
@@ -379,13 +486,15 @@ def step(cfg: Config, x, q, axes, vel=None, fext=None, band: float = 1e-9, lcp_s
     c = dt
     phi_skin = cfg.skin if cfg.phi_skin is None else cfg.phi_skin
 
+    if cfg.shape == SHAPE_SPHEROCYLINDER and cfg.dynamics == INERTIAL:
+        raise NotImplementedError("spherocylinders are stepped with the overdamped laws only")
     kt, Kr = operator_K(cfg.dynamics, dt, q, axes, cfg.density, cfg.drag_xi)
     U_free = free_velocity(cfg, x, vel, fext, kt, Kr, box0)
 
     # Initialise: near-contacting pairs and their SNSD constraints at C^k
     rb = axes.max(axis=1)
     pairs = candidate_pairs(x, rb, box0, cfg.skin)
-    phi0, n0, ra0, rb0, fl0 = snsd(pairs, x, q, axes, box0)
+    phi0, n0, ra0, rb0, fl0 = snsd_shape(cfg.shape, pairs, x, q, axes, box0)
     ambiguous = int(np.sum(np.abs(phi0 - phi_skin) <= band * (1.0 + abs(phi_skin))))
     keep = np.nonzero(phi0 <= phi_skin)[0]
     ia = pairs[keep, 0].astype(np.int64)
@@ -393,6 +502,8 @@ def step(cfg: Config, x, q, axes, vel=None, fext=None, band: float = 1e-9, lcp_s
     nrm = n0[keep]
     ta = np.cross(ra0[keep], nrm)
     tb = np.cross(rb0[keep], nrm)
+    if cfg.dynamics == OVERDAMPED_2D:
+        nrm, ta, tb = planar_rows(nrm, ta, tb)
     # offset of A_0 rows: Phi_0 + c d^T U_free; the affine part of the relative
     # free velocity uses the minimum-image offset
     dU = rows_dot_U(ia, ib, nrm, ta, tb, U_free - _affine(cfg, x, box0))
@@ -438,7 +549,7 @@ def step(cfg: Config, x, q, axes, vel=None, fext=None, band: float = 1e-9, lcp_s
         U = U_free + Uc
         x1 = x + dt * U[:, :3]
         q1 = quat_step(q, U[:, 3:], dt)
-        phi1, n1, ra1, rb1, fl1 = snsd(pairs, x1, q1, axes, box1)
+        phi1, n1, ra1, rb1, fl1 = snsd_shape(cfg.shape, pairs, x1, q1, axes, box1)
         snsd_flags += int(np.count_nonzero(fl1))
         res.trial_phi.append(phi1.copy())
         ambiguous += int(np.sum(np.abs(phi1 + cfg.eps_ncp) <= band * (1.0 + cfg.eps_ncp)))
@@ -454,6 +565,8 @@ def step(cfg: Config, x, q, axes, vel=None, fext=None, band: float = 1e-9, lcp_s
         nn = n1[viol]
         tan = np.cross(ra1[viol], nn)
         tbn = np.cross(rb1[viol], nn)
+        if cfg.dynamics == OVERDAMPED_2D:
+            nn, tan, tbn = planar_rows(nn, tan, tbn)
         iav = pairs[viol, 0].astype(np.int64)
         ibv = pairs[viol, 1].astype(np.int64)
         qnew = phi1[viol] - c * rows_dot_U(iav, ibv, nn, tan, tbn, Uc)

@@ -98,7 +98,7 @@ struct DevStep {
     int c0_evals;       // pairs evaluated at C^k (the others reused the previous step's values)
     int np;             // candidate pairs of the step
     int guess_on;       // the learned start seeded this step's C^k evaluation
-    int pad0;
+    int declined;       // pairs whose learned start the network declined (cold start)
     // per recursion level (cleared together before each trial)
     unsigned long long maxov_bits;  // bits of the largest overlap at the last trial
     unsigned long long la_dmax;     // bits of the largest squared displacement of the trial positions since the list build
@@ -180,8 +180,9 @@ namespace {
 
 relcp_status check_config(const relcp_config* c) {
     if (!c) return set_error("config is NULL"), RELCP_ERR_INVALID_ARG;
-    if (c->dynamics != RELCP_INERTIAL && c->dynamics != RELCP_OVERDAMPED)
-        return set_error("dynamics must be RELCP_INERTIAL or RELCP_OVERDAMPED"), RELCP_ERR_INVALID_ARG;
+    if (c->dynamics != RELCP_INERTIAL && c->dynamics != RELCP_OVERDAMPED && c->dynamics != RELCP_OVERDAMPED_2D)
+        return set_error("dynamics must be RELCP_INERTIAL, RELCP_OVERDAMPED or RELCP_OVERDAMPED_2D"),
+               RELCP_ERR_INVALID_ARG;
     if (c->precision != RELCP_FP64 && c->precision != RELCP_MIXED)
         return set_error("precision must be RELCP_FP64 or RELCP_MIXED"), RELCP_ERR_INVALID_ARG;
     if (c->guess != RELCP_GUESS_COLD && c->guess != RELCP_GUESS_MLP)
@@ -190,7 +191,11 @@ relcp_status check_config(const relcp_config* c) {
         c->max_recursion < 0 || c->max_recursion > 4096)
         return set_error("dt, eps_ncp, lcp_tol > 0; skin >= 0; lcp_max_iter >= 1; 0 <= max_recursion <= 4096"),
                RELCP_ERR_INVALID_ARG;
-    if (c->dynamics == RELCP_OVERDAMPED && !(c->drag_xi > 0))
+    if (c->shape != RELCP_SHAPE_ELLIPSOID && c->shape != RELCP_SHAPE_SPHEROCYLINDER)
+        return set_error("shape must be RELCP_SHAPE_ELLIPSOID or RELCP_SHAPE_SPHEROCYLINDER"), RELCP_ERR_INVALID_ARG;
+    if (c->shape == RELCP_SHAPE_SPHEROCYLINDER && c->dynamics == RELCP_INERTIAL)
+        return set_error("spherocylinders are stepped with the overdamped laws only"), RELCP_ERR_INVALID_ARG;
+    if (c->dynamics != RELCP_INERTIAL && !(c->drag_xi > 0))
         return set_error("drag_xi must be > 0"), RELCP_ERR_INVALID_ARG;
     if (c->dynamics == RELCP_INERTIAL && !(c->density > 0))
         return set_error("density must be > 0"), RELCP_ERR_INVALID_ARG;
@@ -382,6 +387,7 @@ relcp_status step_once(relcp_ctx* c) {
     PrepArgs pa{};
     pa.n = n;
     pa.dynamics = cfg.dynamics;
+    pa.shape = cfg.shape;
     pa.dt = dt;
     pa.drag_xi = cfg.drag_xi;
     pa.density = cfg.density;
@@ -504,8 +510,10 @@ relcp_status step_once(relcp_ctx* c) {
     ru.count = &ds->c0_evals;  // zeroed with the rest of DevStep at the start of the step
 
     // SNSD at C^k for the listed pairs
-    const bool learned = cfg.guess == RELCP_GUESS_MLP && c->mlp.loaded && np > 0;
+    // (spherocylinder pairs are closed-form: no Newton start to learn)
+    const bool learned = cfg.guess == RELCP_GUESS_MLP && c->mlp.loaded && np > 0 && cfg.shape == RELCP_SHAPE_ELLIPSOID;
     SnsdArgs sa{};
+    sa.shape = cfg.shape;
     sa.npairs = np;
     sa.pa = c->pa.p;
     sa.pb = c->pb.p;
@@ -544,6 +552,7 @@ relcp_status step_once(relcp_ctx* c) {
     ra.base = 0;
     ra.rec_index = 0;
     ra.c = dt;
+    ra.planar = cfg.dynamics == RELCP_OVERDAMPED_2D;
     ra.strain_rate = cfg.strain_rate;
     for (int k = 0; k < 3; ++k) ra.box[k] = box0[k];
     ra.box_dev = box0_dev;
@@ -621,6 +630,7 @@ relcp_status step_once(relcp_ctx* c) {
     // step folded into the trial pass: the cached list against these trial
     // positions, accepted if the recursion stops here, in the next box)
     TrialArgs ta{};
+    ta.shape = cfg.shape;
     ta.n = n;
     ta.dt = dt;
     ta.x = c->x.p;
@@ -700,7 +710,9 @@ relcp_status step_once(relcp_ctx* c) {
             if (learned && !ru.reuse_snsd)
                 RELCP_TRY(mlp_guess(c->mlp, np, c->pa.p, c->pb.p, xv, View<4, const double>::soa(c->q.p, n),
                                     View<3, const double>::soa(c->axes.p, n), box0, s, c->idx.p, count_dev,
-                                    &ds->status, box0_dev, kLearnedMinPairs, &ds->guess_on));
+                                    &ds->status, box0_dev,
+                                    (cfg.flags & RELCP_FLAG_LEARNED_ALWAYS) ? 1 : kLearnedMinPairs, &ds->guess_on,
+                                    &ds->declined));
         }
         {
             int e0 = tm.mark();
@@ -899,7 +911,7 @@ relcp_status step_once(relcp_ctx* c) {
     // the next step's prep in the same pass, on the accepted state in the next box
     aa.next = pa;
     for (int k = 0; k < 3; ++k) aa.next.box[k] = box1[k];
-    aa.keep = cfg.dynamics == RELCP_OVERDAMPED;
+    aa.keep = cfg.dynamics != RELCP_INERTIAL;
     aa.Pt = c->Pt.p;
     RELCP_TRY(accept_launch(aa, s));
     c->prepped = true;
@@ -916,6 +928,7 @@ relcp_status step_once(relcp_ctx* c) {
     st.n_pairs = hs.np;
     st.snsd_c0_evaluated = hs.c0_evals;
     st.guess_used = learned ? hs.guess_on : 0;
+    st.newton_fallbacks = (learned && hs.guess_on) ? hs.declined : 0;
     st.lcp_residual = hs.lcp.residual;
     st.max_overlap = __builtin_bit_cast(double, hs.maxov_bits);
     for (int k = 0; k < 3; ++k) st.box[k] = c->box[k];

@@ -70,6 +70,7 @@ struct BatchArgs {
     const int* roff;   // row capacity offsets [S + 1]
     const SceneParams* sp;
     int dynamics;
+    int shape;  // RELCP_SHAPE_* of every scene
     double drag_xi, density;
     int lcp_max_iter, max_recursion, nsteps;
     // body state
@@ -102,6 +103,8 @@ struct BatchArgs {
     // row scratch
     int* ia;
     int* ib;
+    int* rrec;   // per row: recursion index that created it
+    int* rpair;  // per row: its candidate pair (index in the scene's pair list)
     double* geom;  // 9
     float* geomf;  // 9
     double* qd;
@@ -441,7 +444,7 @@ __device__ LcpOut<R> scene_lcp(const BatchArgs& a, const Scene& S, SceneSmem& sm
 // appended: Phi - c d^T uc, the pull-back), diagonal, warm-start gamma
 template <class R>
 __device__ void write_row(const BatchArgs& a, const Scene& S, int r, int i, int j, const double* so, int p,
-                          bool appended, double g0) {
+                          bool appended, double g0, int rec) {
     const int64_t pc = S.pcap;
     const int n = S.n;
     double nn[3], ra[3], rb[3], ta[3], tb[3];
@@ -452,8 +455,11 @@ __device__ void write_row(const BatchArgs& a, const Scene& S, int r, int i, int 
     }
     const double phi = so[p];
     step_math::row_torques(nn, ra, rb, ta, tb);
+    if (a.dynamics == RELCP_OVERDAMPED_2D) step_math::planar_row(nn, ta, tb);
     a.ia[S.roff + r] = i;
     a.ib[S.roff + r] = j;
+    a.rrec[S.roff + r] = rec;
+    a.rpair[S.roff + r] = p;
     for (int k = 0; k < 3; ++k) {
         rcomp(a.geom, S, 9, k)[r] = nn[k];
         rcomp(a.geom, S, 9, 3 + k)[r] = ta[k];
@@ -499,8 +505,11 @@ __device__ int scene_snsd(const BatchArgs& a, const Scene& S, int np, const doub
         const Sym3<double> Pb{Pm[j], Pm[n + j], Pm[2 * n + j], Pm[3 * n + j], Pm[4 * n + j], Pm[5 * n + j]};
         snsd_math::PairResult o;
         const bool hg = guess_out != nullptr;
-        snsd_math::snsd_pair(d, Pa, Pb, hg, hg ? guess_out[1 * pc + p] : 0.0, hg ? guess_out[2 * pc + p] : 0.0,
-                             hg ? guess_out[3 * pc + p] : 0.0, mixed, o);
+        if (a.shape == RELCP_SHAPE_SPHEROCYLINDER)
+            snsd_math::capsule_pair(d, Pa, Pb, o);
+        else
+            snsd_math::snsd_pair(d, Pa, Pb, hg, hg ? guess_out[1 * pc + p] : 0.0, hg ? guess_out[2 * pc + p] : 0.0,
+                                 hg ? guess_out[3 * pc + p] : 0.0, mixed, o);
         if (!o.ok) bits |= DEV_NEWTON;
         out[p] = o.phi;
         for (int k = 0; k < 3; ++k) {
@@ -536,7 +545,7 @@ __device__ int scene_step(const BatchArgs& a, const Scene& S, SceneSmem& sm, rel
             f[k] = bcomp(a.fext, S, 6, k)[i];
         }
         step_math::BodyPrep b;
-        step_math::prep_body(qin, ax, vel, f, x, a.dynamics, S.p.dt, a.drag_xi, a.density, 0.0, S.p.box, b);
+        step_math::prep_body(qin, ax, vel, f, x, a.dynamics, S.p.dt, a.drag_xi, a.density, 0.0, S.p.box, b, a.shape);
         for (int k = 0; k < 4; ++k) bcomp(a.q, S, 4, k)[i] = b.q[k];
         const double Pv[6] = {b.P.xx, b.P.yy, b.P.zz, b.P.xy, b.P.xz, b.P.yz};
         for (int k = 0; k < 6; ++k) bcomp(a.P, S, 6, k)[i] = Pv[k];
@@ -627,7 +636,7 @@ __device__ int scene_step(const BatchArgs& a, const Scene& S, SceneSmem& sm, rel
                 else hi = mid;
             }
             const double g0 = (lo < wc && wk[lo] == key) ? wg[lo] : 0.0;
-            write_row<R>(a, S, fl[p], i, j, s0, p, false, g0);
+            write_row<R>(a, S, fl[p], i, j, s0, p, false, g0, 0);
         }
     }
     __syncthreads();
@@ -636,6 +645,7 @@ __device__ int scene_step(const BatchArgs& a, const Scene& S, SceneSmem& sm, rel
     int nrows = nrows0;
     int depth = 0;
     double maxov = 0.0;
+    bool violated = false;  // an overlap test of this step found Phi < -eps (augmented or capped)
     for (;;) {
         if (nrows > 0) {
             build_csr<R>(a, S, sm, nrows);
@@ -660,7 +670,7 @@ __device__ int scene_step(const BatchArgs& a, const Scene& S, SceneSmem& sm, rel
             }
             for (int k = 0; k < 4; ++k) q[k] = bcomp(a.q, S, 4, k)[i];
             Sym3<double> Pt;
-            step_math::trial_body(x, q, U, ax, S.p.dt, xt, qt, Pt);
+            step_math::trial_body(x, q, U, ax, S.p.dt, xt, qt, Pt, a.shape);
             for (int k = 0; k < 3; ++k) bcomp(a.xt, S, 3, k)[i] = xt[k];
             for (int k = 0; k < 4; ++k) bcomp(a.qt, S, 4, k)[i] = qt[k];
             const double Pv[6] = {Pt.xx, Pt.yy, Pt.zz, Pt.xy, Pt.xz, Pt.yz};
@@ -671,6 +681,7 @@ __device__ int scene_step(const BatchArgs& a, const Scene& S, SceneSmem& sm, rel
         bits |= scene_snsd(a, S, np, a.xt + 3 * S.boff, a.Pt + 6 * S.boff, s0, s1, mixed, fl, &maxov);
         const int nv = cta_scan_array(fl, np);
         if (nv == 0) break;
+        violated = true;
         if (depth >= a.max_recursion) {
             bits |= DEV_RECURSION;
             break;
@@ -679,7 +690,7 @@ __device__ int scene_step(const BatchArgs& a, const Scene& S, SceneSmem& sm, rel
         // one frozen-normal row per violating pair, pulled back to C^k
         for (int p = tid; p < np; p += T) {
             if (!(s1[p] < -S.p.eps)) continue;
-            write_row<R>(a, S, nrows + fl[p], a.pa[S.poff + p], a.pb[S.poff + p], s1, p, true, 0.0);
+            write_row<R>(a, S, nrows + fl[p], a.pa[S.poff + p], a.pb[S.poff + p], s1, p, true, 0.0, depth + 1);
         }
         __syncthreads();
         nrows += nv;
@@ -702,6 +713,8 @@ __device__ int scene_step(const BatchArgs& a, const Scene& S, SceneSmem& sm, rel
     st.n_rows = nrows;
     st.depth_max = depth > st.depth_max ? depth : st.depth_max;
     st.max_overlap = maxov;
+    if (maxov > st.max_overlap_all) st.max_overlap_all = maxov;
+    if (violated) st.aug_steps += 1;
     return bits;
 }
 
@@ -787,7 +800,7 @@ struct relcp_batch {
     bool loaded = false;
     int threads = 0;
     // device
-    DBuf<int> order, boff, poff, roff, work, status, wcount, pa, pb, flags, wkey, ia, ib, inc, inc_tmp;
+    DBuf<int> order, boff, poff, roff, work, status, wcount, pa, pb, flags, wkey, ia, ib, inc, inc_tmp, rrec, rpair;
     DBuf<SceneParams> sp;
     DBuf<double> x, q, axes, vel, fext, P, K, rb, ufree, uc, ustep, xt, qt, Pt, s0, s1, wgam, geom, qd, diag, gamma,
         gg, ucp;
@@ -809,6 +822,7 @@ BatchArgs batch_args(relcp_batch* b, int nsteps) {
     a.roff = b->roff.p;
     a.sp = b->sp.p;
     a.dynamics = b->cfg.dynamics;
+    a.shape = b->cfg.shape;
     a.drag_xi = b->cfg.drag_xi;
     a.density = b->cfg.density;
     a.lcp_max_iter = b->cfg.lcp_max_iter;
@@ -840,6 +854,8 @@ BatchArgs batch_args(relcp_batch* b, int nsteps) {
     a.wcount = b->wcount.p;
     a.ia = b->ia.p;
     a.ib = b->ib.p;
+    a.rrec = b->rrec.p;
+    a.rpair = b->rpair.p;
     a.geom = b->geom.p;
     a.geomf = b->geomf.p;
     a.qd = b->qd.p;
@@ -963,15 +979,20 @@ std::vector<double> from_scene_soa(const std::vector<double>& soa, int w, const 
 extern "C" relcp_status relcp_batch_create(const relcp_config* cfg, void* cuda_stream, relcp_batch** out) {
     if (!cfg || !out) return set_error("NULL argument"), RELCP_ERR_INVALID_ARG;
     *out = nullptr;
-    if (cfg->dynamics != RELCP_INERTIAL && cfg->dynamics != RELCP_OVERDAMPED)
-        return set_error("dynamics must be RELCP_INERTIAL or RELCP_OVERDAMPED"), RELCP_ERR_INVALID_ARG;
+    if (cfg->dynamics != RELCP_INERTIAL && cfg->dynamics != RELCP_OVERDAMPED && cfg->dynamics != RELCP_OVERDAMPED_2D)
+        return set_error("dynamics must be RELCP_INERTIAL, RELCP_OVERDAMPED or RELCP_OVERDAMPED_2D"),
+               RELCP_ERR_INVALID_ARG;
     if (cfg->precision != RELCP_FP64 && cfg->precision != RELCP_MIXED)
         return set_error("precision must be RELCP_FP64 or RELCP_MIXED"), RELCP_ERR_INVALID_ARG;
     if (cfg->guess != RELCP_GUESS_COLD) return set_error("batched scenes start the SNSD cold"), RELCP_ERR_INVALID_ARG;
     if (cfg->strain_rate != 0.0) return set_error("batched scenes have fixed boxes (strain_rate = 0)"), RELCP_ERR_INVALID_ARG;
     if (cfg->lcp_max_iter < 1 || cfg->max_recursion < 0 || cfg->max_recursion > 4096)
         return set_error("lcp_max_iter >= 1, 0 <= max_recursion <= 4096"), RELCP_ERR_INVALID_ARG;
-    if (cfg->dynamics == RELCP_OVERDAMPED && !(cfg->drag_xi > 0)) return set_error("drag_xi must be > 0"), RELCP_ERR_INVALID_ARG;
+    if (cfg->dynamics != RELCP_INERTIAL && !(cfg->drag_xi > 0)) return set_error("drag_xi must be > 0"), RELCP_ERR_INVALID_ARG;
+    if (cfg->shape != RELCP_SHAPE_ELLIPSOID && cfg->shape != RELCP_SHAPE_SPHEROCYLINDER)
+        return set_error("shape must be RELCP_SHAPE_ELLIPSOID or RELCP_SHAPE_SPHEROCYLINDER"), RELCP_ERR_INVALID_ARG;
+    if (cfg->shape == RELCP_SHAPE_SPHEROCYLINDER && cfg->dynamics == RELCP_INERTIAL)
+        return set_error("spherocylinders are stepped with the overdamped laws only"), RELCP_ERR_INVALID_ARG;
     if (cfg->dynamics == RELCP_INERTIAL && !(cfg->density > 0)) return set_error("density must be > 0"), RELCP_ERR_INVALID_ARG;
     relcp_batch* b = new relcp_batch();
     b->cfg = *cfg;
@@ -1103,6 +1124,8 @@ extern "C" relcp_status relcp_batch_set_scenes(relcp_batch* b, int32_t n_scenes,
     RELCP_TRY(b->wcount.ensure((size_t)n_scenes, st));
     RELCP_TRY(b->ia.ensure((size_t)Rt, st));
     RELCP_TRY(b->ib.ensure((size_t)Rt, st));
+    RELCP_TRY(b->rrec.ensure((size_t)Rt, st));
+    RELCP_TRY(b->rpair.ensure((size_t)Rt, st));
     RELCP_TRY(b->geom.ensure((size_t)(9 * Rt), st));
     RELCP_TRY(b->geomf.ensure((size_t)(9 * Rt), st));
     RELCP_TRY(b->qd.ensure((size_t)Rt, st));
@@ -1155,6 +1178,46 @@ extern "C" relcp_status relcp_batch_get_bodies(relcp_batch* b, double* x, double
         if (ptr_kind == RELCP_PTR_DEVICE)
             RELCP_CUDA(cudaMemcpy(it.dst, a.data(), a.size() * sizeof(double), cudaMemcpyHostToDevice));
         else std::memcpy(it.dst, a.data(), a.size() * sizeof(double));
+    }
+    return RELCP_OK;
+}
+
+extern "C" relcp_status relcp_batch_get_scene_contacts(relcp_batch* b, int32_t scene, int32_t* pairs,
+                                                       int64_t pair_cap, int64_t* n_pairs, int32_t* row_ids,
+                                                       int64_t row_cap, int64_t* n_rows) {
+    if (!b || !n_pairs || !n_rows) return set_error("NULL argument"), RELCP_ERR_INVALID_ARG;
+    if (!b->loaded) return set_error("relcp_batch_set_scenes has not been called"), RELCP_ERR_STATE;
+    if (scene < 0 || scene >= b->S) return set_error("scene %d out of range", (int)scene), RELCP_ERR_INVALID_ARG;
+    RELCP_CUDA(cudaStreamSynchronize(b->s));
+    relcp_scene_stats ss{};
+    RELCP_CUDA(cudaMemcpy(&ss, b->stats.p + scene, sizeof(ss), cudaMemcpyDeviceToHost));
+    int offs[2], roffs[2];
+    RELCP_CUDA(cudaMemcpy(offs, b->poff.p + scene, 2 * sizeof(int), cudaMemcpyDeviceToHost));
+    RELCP_CUDA(cudaMemcpy(roffs, b->roff.p + scene, 2 * sizeof(int), cudaMemcpyDeviceToHost));
+    const int64_t np = ss.steps_done > 0 ? ss.n_pairs : 0, nr = ss.steps_done > 0 ? ss.n_rows : 0;
+    if (np > offs[1] - offs[0] || nr > roffs[1] - roffs[0])
+        return set_error("scene %d: counts beyond its capacities", (int)scene), RELCP_ERR_STATE;
+    *n_pairs = np;
+    *n_rows = nr;
+    if ((pairs && pair_cap < np) || (row_ids && row_cap < nr))
+        return set_error("need room for %lld pairs and %lld rows", (long long)np, (long long)nr),
+               RELCP_ERR_CAPACITY;
+    if (pairs && np > 0) {
+        std::vector<int> a((size_t)np), c((size_t)np);
+        RELCP_CUDA(cudaMemcpy(a.data(), b->pa.p + offs[0], np * sizeof(int), cudaMemcpyDeviceToHost));
+        RELCP_CUDA(cudaMemcpy(c.data(), b->pb.p + offs[0], np * sizeof(int), cudaMemcpyDeviceToHost));
+        for (int64_t k = 0; k < np; ++k) {
+            pairs[2 * k] = a[(size_t)k];
+            pairs[2 * k + 1] = c[(size_t)k];
+        }
+    }
+    if (row_ids && nr > 0) {
+        DBuf<int>* src[4] = {&b->ia, &b->ib, &b->rrec, &b->rpair};
+        std::vector<int> v((size_t)nr);
+        for (int f = 0; f < 4; ++f) {
+            RELCP_CUDA(cudaMemcpy(v.data(), src[f]->p + roffs[0], nr * sizeof(int), cudaMemcpyDeviceToHost));
+            for (int64_t k = 0; k < nr; ++k) row_ids[4 * k + f] = v[(size_t)k];
+        }
     }
     return RELCP_OK;
 }
@@ -1323,7 +1386,7 @@ extern "C" void relcp_batch_destroy(relcp_batch* b) {
     cudaStreamSynchronize(s);
     drop_graphs(b);
     DBuf<int>* ib[] = {&b->order, &b->boff, &b->poff, &b->roff, &b->work, &b->status, &b->wcount, &b->pa, &b->pb,
-                       &b->flags, &b->wkey, &b->ia, &b->ib, &b->inc, &b->inc_tmp};
+                       &b->flags, &b->wkey, &b->ia, &b->ib, &b->inc, &b->inc_tmp, &b->rrec, &b->rpair};
     for (auto* p : ib) p->release(s);
     DBuf<double>* db[] = {&b->x, &b->q, &b->axes, &b->vel, &b->fext, &b->P, &b->K, &b->rb, &b->ufree, &b->uc,
                           &b->ustep, &b->xt, &b->qt, &b->Pt, &b->s0, &b->s1, &b->wgam, &b->geom, &b->qd, &b->diag,

@@ -365,6 +365,10 @@ __device__ __forceinline__ void guess_from(const float* f, const float* o, float
     for (int k = 0; k < 3; ++k) g[k] = (double)((R[3 * k] * n[0] + R[3 * k + 1] * n[1] + R[3 * k + 2] * n[2]) / l);
 }
 
+__device__ __forceinline__ bool g_zero(const View<3, double>& guess, int64_t k, int64_t pair) {
+    return pair >= 0 && guess(0, k) == 0.0 && guess(1, k) == 0.0 && guess(2, k) == 0.0;
+}
+
 // The learned start in one kernel for a list of pairs: per tile of 64 pairs,
 // FP32 features into shared memory, the BF16 network on the tensor cores (one
 // warp per 16 pairs, weights bulk-copied into shared memory once per CTA),
@@ -374,7 +378,8 @@ constexpr size_t kGuessSmem = kFwdSmem + 16 + (size_t)kGuessTile * (16 + 8) * si
 
 __global__ void __launch_bounds__(kFwdWarps * 32) mlp_guess_kernel(MlpFeatArgs fa, const unsigned char* __restrict__ image,
                                                                    View<3, double> guess, int* __restrict__ status,
-                                                                   int64_t min_count, int* __restrict__ ran) {
+                                                                   int64_t min_count, int* __restrict__ ran,
+                                                                   int* __restrict__ declined) {
     pdl_wait();
     pdl_trigger();
     const int64_t count = fa.count_dev ? (int64_t)*fa.count_dev : fa.npairs;
@@ -410,6 +415,9 @@ __global__ void __launch_bounds__(kFwdWarps * 32) mlp_guess_kernel(MlpFeatArgs f
                        (float)fa.q(3, i), g);
             for (int k = 0; k < 3; ++k) guess(k, row0 + r) = g[k];
         }
+        // pairs the network declined (zero start: Newton starts cold)
+        const unsigned dm = __ballot_sync(0xffffffffu, pair >= 0 && g_zero(guess, row0 + r, pair));
+        if (declined && lane == 0 && dm) atomicAdd(declined, __popc(dm));
         __syncthreads();
     }
 }
@@ -627,7 +635,7 @@ relcp_status mlp_forward_launch(int64_t npairs, const unsigned char* image, cons
 relcp_status mlp_guess(MlpState& m, int64_t npairs, const int* pa, const int* pb, View<3, const double> x,
                        View<4, const double> q, View<3, const double> axes, const double box[3], cudaStream_t s,
                        const int* idx, const int* count_dev, int* status, const double* box_dev, int64_t min_count,
-                       int* ran) {
+                       int* ran, int* declined) {
     if (!m.loaded) {
         set_error("learned guess not loaded");
         return RELCP_ERR_STATE;
@@ -662,7 +670,7 @@ relcp_status mlp_guess(MlpState& m, int64_t npairs, const int* pa, const int* pb
     if (blocks > ntiles) blocks = ntiles;
     note_launch();
     launch_pdl(mlp_guess_kernel, dim3((unsigned)blocks), dim3(kFwdWarps * 32), kGuessSmem, s, fa, m.image.p,
-               View<3, double>::soa(m.guess.p, npairs), status, min_count, ran);
+               View<3, double>::soa(m.guess.p, npairs), status, min_count, ran, declined);
     RELCP_CUDA(cudaGetLastError());
     return RELCP_OK;
 }

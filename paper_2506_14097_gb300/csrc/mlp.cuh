@@ -64,11 +64,13 @@ relcp_status mlp_train_step(int64_t B, float* params, float* am, float* av, cons
 // start normals guess(., k) for the pairs idx[k], k < *count_dev (idx == nullptr:
 // all npairs pairs); npairs bounds the count
 // min_count: with fewer rows (*count_dev) the network does not run and
-// *ran (if given) is set to 0, else to 1
+// *ran (if given) is set to 0, else to 1; *declined (if given) counts the
+// pairs whose start the network declined (trust logit <= 0: a cold start)
 relcp_status mlp_guess(MlpState& m, int64_t npairs, const int* pa, const int* pb, View<3, const double> x,
                        View<4, const double> q, View<3, const double> axes, const double box[3], cudaStream_t s,
                        const int* idx = nullptr, const int* count_dev = nullptr, int* status = nullptr,
-                       const double* box_dev = nullptr, int64_t min_count = 0, int* ran = nullptr);
+                       const double* box_dev = nullptr, int64_t min_count = 0, int* ran = nullptr,
+                       int* declined = nullptr);
 void mlp_release(MlpState& m, cudaStream_t s);
 
 }  // namespace relcp

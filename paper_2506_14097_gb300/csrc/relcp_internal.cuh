@@ -344,6 +344,7 @@ struct SnsdArgs {
     unsigned long long* iters_sum;   // may be null: sum of the Newton iteration counts
     int* status;                     // DEV_NEWTON
     int newton_cap;                  // > 0: Newton iteration cap of every phase (fault injection)
+    int shape;                       // RELCP_SHAPE_* (P holds the shape records of step_math::shape_record)
 };
 relcp_status snsd_launch(const SnsdArgs& a, cudaStream_t s);
 

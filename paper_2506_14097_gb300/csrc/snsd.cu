@@ -61,8 +61,11 @@ __global__ void __launch_bounds__(kThreads) snsd_kernel(SnsdArgs a) {
         const Sym3<double> Pa = load_P(a.P, i), Pb = load_P(a.P, j);
         const bool hg = a.guess.c[0] != nullptr && (!a.guess_on || *a.guess_on != 0);
         snsd_math::PairResult o;
-        snsd_math::snsd_pair(d, Pa, Pb, hg, hg ? a.guess(0, gk) : 0.0, hg ? a.guess(1, gk) : 0.0,
-                             hg ? a.guess(2, gk) : 0.0, a.mixed != 0, o, a.newton_cap);
+        if (a.shape == RELCP_SHAPE_SPHEROCYLINDER)
+            snsd_math::capsule_pair(d, Pa, Pb, o);
+        else
+            snsd_math::snsd_pair(d, Pa, Pb, hg, hg ? a.guess(0, gk) : 0.0, hg ? a.guess(1, gk) : 0.0,
+                                 hg ? a.guess(2, gk) : 0.0, a.mixed != 0, o, a.newton_cap);
         if (!o.ok) atomicOr(a.status, DEV_NEWTON);
         const double G = o.phi;
         const int iters = o.iters;

@@ -293,5 +293,60 @@ __device__ __forceinline__ void snsd_pair(const double d[3], const Sym3<double>&
     o.iters = iters;
 }
 
+// Spherocylinder pair (RELCP_SHAPE_SPHEROCYLINDER records: unit axis u, half-
+// length h, radius rho).  The closest points A + s u, B + t v of the two
+// segments (B - A = d) minimise |d + t v - s u|^2 over the rectangle; the
+// minimiser is the first minimal one among the interior stationary point
+// (when it lies inside) and the edge minimisers at s = -h_a, +h_a, t = -h_b,
+// +h_b.  Phi = |Q - P| - rho_a - rho_b, n = (Q - P)/|Q - P|, support points
+// P + rho_a n and Q - rho_b n.  FP64 in closed form on both precision paths
+// (no iteration); intersecting segments give ok = false.
+__device__ __forceinline__ void capsule_pair(const double d[3], const Sym3<double>& A, const Sym3<double>& B,
+                                             PairResult& o) {
+    const double u[3] = {A.xx, A.yy, A.zz}, v[3] = {B.xx, B.yy, B.zz};
+    const double ha = A.xy, ra = A.xz, hb = B.xy, rb = B.xz;
+    const double uv = dot3(u, v), wu = dot3(d, u), wv = dot3(d, v);
+    double best_s = 0.0, best_t = 0.0, best_f = 0.0;
+    bool have = false;
+    auto consider = [&](double s_, double t_) {
+        double r[3];
+        for (int k = 0; k < 3; ++k) r[k] = d[k] + t_ * v[k] - s_ * u[k];
+        const double f = dot3(r, r);
+        if (!have || f < best_f) {
+            best_s = s_;
+            best_t = t_;
+            best_f = f;
+            have = true;
+        }
+    };
+    const double det = 1.0 - uv * uv;
+    if (det > 1e-14) {
+        const double s0 = (wu - uv * wv) / det, t0 = (uv * wu - wv) / det;
+        if (fabs(s0) <= ha && fabs(t0) <= hb) consider(s0, t0);
+    }
+    consider(-ha, fmin(fmax(-ha * uv - wv, -hb), hb));
+    consider(ha, fmin(fmax(ha * uv - wv, -hb), hb));
+    consider(fmin(fmax(wu - hb * uv, -ha), ha), -hb);
+    consider(fmin(fmax(wu + hb * uv, -ha), ha), hb);
+    double w[3];
+    for (int k = 0; k < 3; ++k) w[k] = d[k] + best_t * v[k] - best_s * u[k];
+    const double dist = sqrt(dot3(w, w));
+    o.iters = 0;
+    if (!(dist > 1e-12)) {
+        o.ok = false;
+        o.phi = -(ra + rb);
+        for (int k = 0; k < 3; ++k) o.n[k] = o.ra[k] = o.rb[k] = 0.0;
+        return;
+    }
+    o.ok = true;
+    o.phi = dist - ra - rb;
+    for (int k = 0; k < 3; ++k) {
+        const double nk = w[k] / dist;
+        o.n[k] = nk;
+        o.ra[k] = best_s * u[k] + ra * nk;
+        o.rb[k] = best_t * v[k] - rb * nk;
+    }
+}
+
 }  // namespace snsd_math
 }  // namespace relcp

@@ -41,7 +41,8 @@ __device__ __forceinline__ void prep_one(const PrepArgs& a, int64_t i) {
         f[k] = a.fext[k * n + i];
     }
     step_math::BodyPrep b;
-    step_math::prep_body(qin, ax, vel, f, x, a.dynamics, a.dt, a.drag_xi, a.density, a.strain_rate, a.box, b);
+    step_math::prep_body(qin, ax, vel, f, x, a.dynamics, a.dt, a.drag_xi, a.density, a.strain_rate, a.box, b,
+                         a.shape);
     for (int k = 0; k < 4; ++k) a.q[k * n + i] = b.q[k];
     a.P[i] = b.P.xx;
     a.P[n + i] = b.P.yy;
@@ -84,6 +85,7 @@ __device__ __forceinline__ void prep_keep(const PrepArgs& a, const double* __res
     if (a.strain_rate != 0.0)
         for (int k = 0; k < 3; ++k)
             if (a.box[k] > 0.0) u[k] += a.strain_rate * (a.x[k * n + i] - 0.5 * a.box[k]);
+    if (a.dynamics == RELCP_OVERDAMPED_2D) step_math::planar_velocity(u);
 #pragma unroll
     for (int k = 0; k < 6; ++k) a.ufree[k * n + i] = u[k];
     if (a.ufreef)
@@ -139,6 +141,7 @@ __device__ __forceinline__ void rows_mixed(const RowsArgs& a, int64_t p, int64_t
     tb[0] = rb[1] * nn[2] - rb[2] * nn[1];
     tb[1] = rb[2] * nn[0] - rb[0] * nn[2];
     tb[2] = rb[0] * nn[1] - rb[1] * nn[0];
+    if (a.planar) step_math::planar_row(nn, ta, tb);
     a.ia[r] = i;
     a.ib[r] = j;
     a.rec[r] = a.rec_index;
@@ -232,6 +235,7 @@ __global__ void rows_kernel(RowsArgs a) {
     }
     double phi = a.snsd[p];
     step_math::row_torques(nn, ra, rb, ta, tb);
+    if (a.planar) step_math::planar_row(nn, ta, tb);
     const int64_t C = a.cap;
     a.ia[r] = i;
     a.ib[r] = j;
@@ -343,7 +347,7 @@ __global__ void trial_kernel(TrialArgs a) {
     }
     for (int k = 0; k < 4; ++k) q[k] = a.q[k * n + i];
     Sym3<double> P;
-    step_math::trial_body(x, q, U, ax, a.dt, xt, qt, P);
+    step_math::trial_body(x, q, U, ax, a.dt, xt, qt, P, a.shape);
     for (int k = 0; k < 3; ++k) a.xt[k * n + i] = xt[k];
     for (int k = 0; k < 4; ++k) a.qt[k * n + i] = qt[k];
     a.Pt[i] = P.xx;

@@ -10,6 +10,7 @@ namespace relcp {
 struct PrepArgs {
     int64_t n;
     int dynamics;
+    int shape;  // RELCP_SHAPE_*: the shape record written to P
     double dt, drag_xi, density, strain_rate;
     double box[3];
     const double* x;
@@ -34,6 +35,7 @@ struct RowsArgs {
     const double* snsd;  // 10 x npairs: phi, n, r_a, r_b
     int64_t base, cap;
     int rec_index;
+    int planar;  // RELCP_OVERDAMPED_2D: rows keep their u_x, u_y, omega_z entries only
     double c, strain_rate;
     double box[3];
     const double* x;      // C^k positions (A_0 offsets)
@@ -103,6 +105,7 @@ struct MemoSaveArgs {
 
 struct TrialArgs {
     int64_t n;
+    int shape;  // RELCP_SHAPE_*: the shape record written to Pt
     double dt;
     // optional look-ahead of the cached pair list (xb == nullptr: none): the
     // largest |min_image(x_t - sfac xb)| in box `la_box`, atomicMax of its bits

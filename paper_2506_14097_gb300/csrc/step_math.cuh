@@ -23,10 +23,37 @@ struct BodyPrep {
     double ufree[6];
 };
 
+// planar dynamics (RELCP_OVERDAMPED_2D): only u_x, u_y and omega_z
+template <class T>
+__device__ __forceinline__ void planar_velocity(T u[6]) {
+    u[2] = T(0);
+    u[3] = T(0);
+    u[4] = T(0);
+}
+// a row of the planar problem keeps its entries on u_x, u_y and omega_z
+template <class T>
+__device__ __forceinline__ void planar_row(T nn[3], T ta[3], T tb[3]) {
+    nn[2] = T(0);
+    ta[0] = ta[1] = T(0);
+    tb[0] = tb[1] = T(0);
+}
+
+// The per-body shape record the SNSD kernels read (six doubles).  Ellipsoid:
+// P = R diag(a^2) R^T.  Spherocylinder (semi-axes (h + rho, rho, rho)): the
+// unit axis u = R e_x, then h and rho, then 0.
+__device__ __forceinline__ Sym3<double> shape_record(const double R[9], const double ax[3], int shape) {
+    if (shape == RELCP_SHAPE_SPHEROCYLINDER) {
+        const double rho = ax[1];
+        const double h = ax[0] > rho ? ax[0] - rho : 0.0;
+        return Sym3<double>{R[0], R[3], R[6], h, rho, 0.0};
+    }
+    return rot_diag_rot(R, ax[0] * ax[0], ax[1] * ax[1], ax[2] * ax[2]);
+}
+
 __device__ __forceinline__ void prep_body(const double qin[4], const double ax[3], const double vel[6],
                                           const double fext[6], const double x[3], int dynamics, double dt,
                                           double drag_xi, double density, double strain_rate, const double box[3],
-                                          BodyPrep& b) {
+                                          BodyPrep& b, int shape = RELCP_SHAPE_ELLIPSOID) {
     double s = qin[0], x1 = qin[1], y1 = qin[2], z1 = qin[3];
     // one FP64 reciprocal square root (no separate division), four products
     const double il = rsqrt(s * s + x1 * x1 + y1 * y1 + z1 * z1);
@@ -41,12 +68,12 @@ __device__ __forceinline__ void prep_body(const double qin[4], const double ax[3
     double R[9];
     quat_to_R(s, x1, y1, z1, R);
     const double a0 = ax[0], a1 = ax[1], a2 = ax[2];
-    b.P = rot_diag_rot(R, a0 * a0, a1 * a1, a2 * a2);
+    b.P = shape_record(R, ax, shape);
     const double amax = fmax(a0, fmax(a1, a2));
     b.rb = amax;
     double kt;
     Sym3<double> Kr;
-    if (dynamics == RELCP_OVERDAMPED) {
+    if (dynamics == RELCP_OVERDAMPED || dynamics == RELCP_OVERDAMPED_2D) {
         const double L = 2.0 * amax;
         kt = 1.0 / (drag_xi * L);
         const double kr = 12.0 / (drag_xi * L * L * L);
@@ -77,6 +104,7 @@ __device__ __forceinline__ void prep_body(const double qin[4], const double ax[3
     if (strain_rate != 0.0)
         for (int k = 0; k < 3; ++k)
             if (box[k] > 0.0) u[k] += strain_rate * (x[k] - 0.5 * box[k]);
+    if (dynamics == RELCP_OVERDAMPED_2D) planar_velocity(u);
     for (int k = 0; k < 6; ++k) b.ufree[k] = u[k];
 }
 
@@ -126,7 +154,8 @@ __device__ __forceinline__ double affine_image_corr(const double xi[3], const do
 // trial configuration of one body: x + dt v, q + dt/2 (0, w) (x) q normalised,
 // and P at the new orientation
 __device__ __forceinline__ void trial_body(const double x[3], const double q[4], const double U[6], const double ax[3],
-                                           double dt, double xt[3], double qt[4], Sym3<double>& Pt) {
+                                           double dt, double xt[3], double qt[4], Sym3<double>& Pt,
+                                           int shape = RELCP_SHAPE_ELLIPSOID) {
     for (int k = 0; k < 3; ++k) xt[k] = x[k] + dt * U[k];
     const double s = q[0], x1 = q[1], y1 = q[2], z1 = q[3];
     const double h = 0.5 * dt;
@@ -146,7 +175,7 @@ __device__ __forceinline__ void trial_body(const double x[3], const double q[4],
     qt[3] = nz;
     double R[9];
     quat_to_R(ns, nx, ny, nz, R);
-    Pt = rot_diag_rot(R, ax[0] * ax[0], ax[1] * ax[1], ax[2] * ax[2]);
+    Pt = shape_record(R, ax, shape);
 }
 
 // position wrapped into [0, L) on a periodic axis

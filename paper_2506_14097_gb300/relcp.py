@@ -28,10 +28,11 @@ RELCP_ERR_STATE = 8
 STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "CUDA", 3: "CAPACITY", 4: "NOT_CONVERGED", 5: "RECURSION_LIMIT",
                 6: "NEWTON", 7: "TIMEOUT", 8: "STATE"}
 
-RELCP_INERTIAL, RELCP_OVERDAMPED = 0, 1
+RELCP_INERTIAL, RELCP_OVERDAMPED, RELCP_OVERDAMPED_2D = 0, 1, 2
 RELCP_FP64, RELCP_MIXED = 0, 1
 RELCP_GUESS_COLD, RELCP_GUESS_MLP = 0, 1
 RELCP_PTR_HOST, RELCP_PTR_DEVICE = 0, 1
+RELCP_SHAPE_ELLIPSOID, RELCP_SHAPE_SPHEROCYLINDER = 0, 1
 RELCP_FAULT_ROW_CAPACITY, RELCP_FAULT_LCP_ITERS, RELCP_FAULT_LCP_TIMEOUT, RELCP_FAULT_NEWTON_ITERS = 1, 2, 4, 8
 RELCP_FLAG_PHASE_TIMING = 1
 RELCP_FLAG_NO_WARM_START = 2
@@ -40,6 +41,7 @@ RELCP_FLAG_NO_SNSD_REUSE = 8
 RELCP_FLAG_LCP_TIMING = 16
 RELCP_FLAG_GRAPH = 32
 RELCP_FLAG_HOST_STAGING = 64
+RELCP_FLAG_LEARNED_ALWAYS = 128
 MAX_DEPTH_STATS = 64
 
 
@@ -48,7 +50,7 @@ class relcp_config(ctypes.Structure):
                 ("max_recursion", c_int32), ("n_scenes", c_int32), ("dt", c_double), ("eps_ncp", c_double),
                 ("box", c_double * 3), ("skin", c_double), ("phi_skin", c_double), ("drag_xi", c_double),
                 ("density", c_double), ("strain_rate", c_double), ("lcp_tol", c_double), ("seed", c_uint64),
-                ("fault_inject", c_uint32), ("flags", c_uint32)]
+                ("fault_inject", c_uint32), ("flags", c_uint32), ("shape", c_int32), ("reserved", c_int32)]
 
 
 class relcp_step_stats(ctypes.Structure):
@@ -93,8 +95,8 @@ EXPORTS = ["relcp_last_error", "relcp_kernel_launches", "relcp_version", "relcp_
            "relcp_get_contact_velocity", "relcp_destroy", "relcp_broadphase", "relcp_snsd_eval", "relcp_lcp_solve",
            "relcp_snsd_eval_noalloc", "relcp_mlp_features", "relcp_mlp_forward", "relcp_mlp_train_step",
            "relcp_load_mlp", "relcp_batch_create", "relcp_batch_set_scenes", "relcp_batch_step",
-           "relcp_batch_get_bodies", "relcp_batch_scene_stats", "relcp_batch_autotune", "relcp_batch_set_threads",
-           "relcp_batch_destroy"]
+           "relcp_batch_get_bodies", "relcp_batch_scene_stats", "relcp_batch_get_scene_contacts",
+           "relcp_batch_autotune", "relcp_batch_set_threads", "relcp_batch_destroy"]
 
 
 def library_path() -> str:
@@ -147,6 +149,8 @@ def load(build_if_needed: bool = True):
         "relcp_batch_step": [c_void_p, c_int32],
         "relcp_batch_get_bodies": [c_void_p, c_void_p, c_void_p, c_void_p, c_int32],
         "relcp_batch_scene_stats": [c_void_p, c_void_p],
+        "relcp_batch_get_scene_contacts": [c_void_p, c_int32, c_void_p, c_int64, POINTER(c_int64), c_void_p, c_int64,
+                                           POINTER(c_int64)],
         "relcp_batch_autotune": [c_void_p, c_char_p, POINTER(c_int32)],
         "relcp_batch_set_threads": [c_void_p, c_int32],
     }
@@ -206,7 +210,8 @@ def _stream(stream):
 
 def make_config(dynamics=RELCP_INERTIAL, precision=RELCP_FP64, guess=RELCP_GUESS_COLD, dt=1e-3, eps_ncp=1e-3,
                 box=(0.0, 0.0, 0.0), skin=0.05, phi_skin=None, drag_xi=1.0, density=1.0, strain_rate=0.0,
-                lcp_tol=None, lcp_max_iter=20000, max_recursion=64, seed=0, fault_inject=0, flags=0, length_scale=None):
+                lcp_tol=None, lcp_max_iter=20000, max_recursion=64, seed=0, fault_inject=0, flags=0, length_scale=None,
+                shape=RELCP_SHAPE_ELLIPSOID):
     """A relcp_config.  lcp_tol defaults to 1e-12 (FP64) or 1e-7 (mixed) times
     `length_scale` (default: eps_ncp / 1e-3, i.e. the smallest semi-axis when
     eps_ncp = 1e-3 x a_min)."""
@@ -222,6 +227,7 @@ def make_config(dynamics=RELCP_INERTIAL, precision=RELCP_FP64, guess=RELCP_GUESS
     scale = (eps_ncp / 1e-3) if length_scale is None else length_scale
     c.lcp_tol = lcp_tol if lcp_tol is not None else (1e-12 if precision == RELCP_FP64 else 1e-7) * scale
     c.seed, c.fault_inject, c.flags = seed, fault_inject, flags
+    c.shape, c.reserved = shape, 0
     return c
 
 
@@ -466,8 +472,8 @@ SCENE_PARAMS = 8
 
 class relcp_scene_stats(ctypes.Structure):
     _fields_ = [("status", c_int32), ("status_bits", c_int32), ("steps_done", c_int32), ("depth_max", c_int32),
-                ("lcp_iters", c_int32), ("n_pairs", c_int32), ("n_rows", c_int32), ("pad", c_int32),
-                ("max_overlap", c_double), ("lcp_residual", c_double)]
+                ("lcp_iters", c_int32), ("n_pairs", c_int32), ("n_rows", c_int32), ("aug_steps", c_int32),
+                ("max_overlap", c_double), ("lcp_residual", c_double), ("max_overlap_all", c_double)]
 
 
 def relcp_batch_create(cfg: relcp_config, stream=None):
@@ -498,6 +504,20 @@ def relcp_batch_scene_stats(b, n_scenes):
     out = (relcp_scene_stats * n_scenes)()
     _check(load().relcp_batch_scene_stats(b, ctypes.cast(out, c_void_p)), "relcp_batch_scene_stats")
     return list(out)
+
+
+def relcp_batch_get_scene_contacts(b, scene):
+    """(pairs (P, 2) int32, row ids (m, 4) int32 = a, b, recursion, pair) of
+    the scene's last step, host arrays."""
+    L = load()
+    n_p, n_r = c_int64(0), c_int64(0)
+    _check(L.relcp_batch_get_scene_contacts(b, int(scene), None, 0, byref(n_p), None, 0, byref(n_r)),
+           "relcp_batch_get_scene_contacts")
+    pairs = np.zeros((max(n_p.value, 1), 2), dtype=np.int32)
+    ids = np.zeros((max(n_r.value, 1), 4), dtype=np.int32)
+    _check(L.relcp_batch_get_scene_contacts(b, int(scene), _ptr(pairs), n_p.value, byref(n_p), _ptr(ids), n_r.value,
+                                            byref(n_r)), "relcp_batch_get_scene_contacts")
+    return pairs[:n_p.value], ids[:n_r.value]
 
 
 def relcp_batch_autotune(b, cache_path=None):
@@ -538,6 +558,9 @@ class Batch:
 
     def scene_stats(self):
         return relcp_batch_scene_stats(self.h, len(self.offsets) - 1)
+
+    def contacts(self, scene):
+        return relcp_batch_get_scene_contacts(self.h, scene)
 
     def autotune(self, cache_path=None):
         return relcp_batch_autotune(self.h, cache_path)

@@ -221,3 +221,85 @@ def sphere_scene(seed: int, n: int, side: float, radius_range=(0.5, 1.0), vel_si
     vel = np.concatenate([rng.normal(0.0, vel_sigma, size=(n, 3)), np.zeros((n, 3))], axis=1)
     return Scene(x=x, q=q, axes=axes, vel=vel, fext=np.zeros((n, 6)), box=np.array([side] * 3), dt=1e-3,
                  meta={"kind": "spheres", "seed": seed})
+
+
+def planar_quaternions(theta: np.ndarray) -> np.ndarray:
+    """(s, w) quaternions of rotations by theta about the z axis."""
+    theta = np.asarray(theta, dtype=np.float64)
+    return np.stack([np.cos(0.5 * theta), np.zeros_like(theta), np.zeros_like(theta), np.sin(0.5 * theta)], axis=1)
+
+
+def planar_angle(q: np.ndarray) -> np.ndarray:
+    """Rotation angle about z of (s, w) quaternions that rotate about z."""
+    q = np.asarray(q, dtype=np.float64)
+    return 2.0 * np.arctan2(q[:, 3], q[:, 0])
+
+
+class Colony:
+    """Growing colony of prolate ellipsoidal cells in the z = 0 plane (the
+    paper's Sec. 5.4 colony, restated with ellipsoids).
+
+    Cell i has length L_i and semi-axes (L_i/2, 0.5, 0.5), its long axis the
+    body x axis, in the plane.  Each cell draws its growth rate once, at birth,
+    from N(rate, rate_sd) (length per unit time).  After every time step the
+    driver advances L_i by rate_i dt; a cell that reaches L_div divides along
+    its axis into two daughters of length L_i / 2 centred at c +- (L_i / 4) e,
+    each turned by its own N(0, jitter) angle.  All random numbers come from
+    the colony's own seeded generator, so a colony is a pure function of its
+    seed and of the positions and angles the solver returns.  This is input
+    preparation (the scene), not the contact method."""
+
+    def __init__(self, seed: int = 0, rate: float = 0.01, rate_sd: float = 0.001, jitter: float = 0.05,
+                 L0: float = 1.0, L_div: float = 2.0, dt: float = 0.05):
+        self.rng = np.random.default_rng(seed)
+        self.rate, self.rate_sd, self.jitter = rate, rate_sd, jitter
+        self.L_div, self.dt = L_div, dt
+        self.x = np.zeros((1, 3))
+        self.theta = np.zeros(1)
+        self.L = np.array([L0], dtype=np.float64)
+        self.g = self._rates(1)
+        self.divisions = 0
+
+    def _rates(self, k: int) -> np.ndarray:
+        return np.maximum(self.rng.normal(self.rate, self.rate_sd, size=k), 0.0)
+
+    @property
+    def n(self) -> int:
+        return int(self.L.shape[0])
+
+    def axes(self) -> np.ndarray:
+        a = np.full((self.n, 3), 0.5)
+        a[:, 0] = 0.5 * self.L
+        return a
+
+    def q(self) -> np.ndarray:
+        return planar_quaternions(self.theta)
+
+    def advance(self, x: np.ndarray, q: np.ndarray) -> int:
+        """Take the solver's accepted positions and orientations, grow every
+        cell by one step and divide those at L_div.  Returns the number of
+        divisions."""
+        self.x = np.array(x, dtype=np.float64, copy=True)
+        self.x[:, 2] = 0.0
+        self.theta = planar_angle(q)
+        self.L = self.L + self.g * self.dt
+        idx = np.nonzero(self.L >= self.L_div)[0]
+        if idx.size == 0:
+            return 0
+        e = np.stack([np.cos(self.theta[idx]), np.sin(self.theta[idx]), np.zeros(idx.size)], axis=1)
+        off = (0.25 * self.L[idx])[:, None] * e
+        Ld = 0.5 * self.L[idx]
+        jit = self.rng.normal(0.0, self.jitter, size=(idx.size, 2))
+        # daughter 1 replaces the mother, daughter 2 is appended
+        x2 = self.x[idx] + off
+        self.x[idx] = self.x[idx] - off
+        th2 = self.theta[idx] + jit[:, 1]
+        self.theta[idx] = self.theta[idx] + jit[:, 0]
+        self.L[idx] = Ld
+        self.g[idx] = self._rates(idx.size)
+        self.x = np.concatenate([self.x, x2])
+        self.theta = np.concatenate([self.theta, th2])
+        self.L = np.concatenate([self.L, Ld])
+        self.g = np.concatenate([self.g, self._rates(idx.size)])
+        self.divisions += int(idx.size)
+        return int(idx.size)

@@ -1,9 +1,11 @@
 """Batched scenes: many independent scenes stepped by one persistent launch
 (each CTA runs the whole of Algorithm 1 for its scene).
 
-Checks, per scene, against the FP64 oracle's step from the same state (pair
-count bit-exact, recursion depth equal, velocities / positions / orientations
-within the path's tolerance: FP64 1e-9, mixed 1e-5, normwise relative), against
+Checks, per scene, against the FP64 oracle's step from the same state
+(candidate pair list and constraint ids (a, b, recursion, pair) bit for bit,
+recursion depth equal, velocities / positions / orientations within the path's
+tolerance: FP64 1e-9, mixed 1e-5, normwise relative; scenes of 2 to 512
+bodies), against
 the single-scene path over several steps, bitwise determinism, the edge cases
 (empty, one-body and maximum scenes, capacity, bad arguments) and the block-size
 autotuner with its JSON cache."""
@@ -41,16 +43,17 @@ def new_batch(R, scs, precision, dynamics=None):
 @pytest.mark.parametrize("precision,bound", [(0, 1e-9), (1, 1e-5)])
 def test_batch_steps_match_oracle(relcp_gpu, orc, precision, bound):
     R = relcp_gpu
-    scs = dense_scenes([(2, 64), (3, 27), (4, 9), (5, 2)])
+    scs = dense_scenes([(2, 64), (3, 27), (4, 9), (5, 2), (6, 216), (7, 343), (8, 512)])
     state = [(sc.x.copy(), sc.q.copy(), sc.vel.copy()) for sc in scs]
-    depths = []
-    for k in range(8):
+    depths, big_rows = [], 0
+    for k in range(6):
         cur = [scenes.Scene(x=x, q=q, axes=sc.axes, vel=v, fext=sc.fext, box=sc.box, dt=sc.dt)
                for sc, (x, q, v) in zip(scs, state)]
         b, offsets, params = new_batch(R, cur, precision)
         b.step(1)
         xb, qb, vb = b.bodies()
         st = b.scene_stats()
+        contacts = [b.contacts(s) for s in range(len(cur))]
         b.close()
         nxt = []
         for s, sc in enumerate(cur):
@@ -62,6 +65,12 @@ def test_batch_steps_match_oracle(relcp_gpu, orc, precision, bound):
             sl = slice(offsets[s], offsets[s + 1])
             assert st[s].status == 0 and st[s].steps_done == 1
             assert st[s].n_pairs == len(ref.pairs), (k, s)
+            pairs, ids = contacts[s]
+            assert np.array_equal(pairs, ref.pairs), (k, s)
+            ref_ids = np.stack([ref.rows_ia, ref.rows_ib, ref.rows_rec, ref.rows_pair], axis=1)
+            assert np.array_equal(ids, ref_ids), (k, s)
+            if sc.n >= 200:
+                big_rows += ids.shape[0]
             assert st[s].depth_max == ref.depth, (k, s)
             assert rel_err(vb[sl], ref.vel) <= bound, (k, s, rel_err(vb[sl], ref.vel))
             dx = orc.min_image(xb[sl] - ref.x, np.asarray(ref.box))
@@ -73,6 +82,7 @@ def test_batch_steps_match_oracle(relcp_gpu, orc, precision, bound):
             nxt.append((ref.x, ref.q, ref.vel))
         state = nxt
     assert max(depths) >= 1  # the recursion ran inside the persistent launch
+    assert big_rows > 1000  # the 216- to 512-body scenes carried many constraints
 
 
 @pytest.mark.parametrize("precision,tol", [(0, 1e-7), (1, 1e-4)])
@@ -217,13 +227,17 @@ def test_batched_workload_sample(relcp_gpu, orc):
     assert all(s.max_overlap <= params[i, 4] for i, s in enumerate(st))
     rng = np.random.default_rng(7)
     small = [s for s, sc in enumerate(scs) if sc.n <= 40]
-    for s in rng.choice(small, size=4, replace=False):
+    large = [s for s, sc in enumerate(scs) if sc.n >= 200]
+    picks = list(rng.choice(small, size=4, replace=False)) + list(rng.choice(large, size=4, replace=False))
+    for s in picks:
         sc = scs[s]
         amin = float(sc.axes.min())
         ocfg = orc.Config(dynamics=orc.INERTIAL, dt=sc.dt, eps_ncp=1e-3 * amin, box=tuple(sc.box), skin=0.1 * amin)
         ref = orc.step(ocfg, sc.x, sc.q, sc.axes, sc.vel)
         sl = slice(offsets[s], offsets[s + 1])
-        assert st[s].n_pairs == len(ref.pairs)
+        pairs, ids = b.contacts(s)
+        assert np.array_equal(pairs, ref.pairs), s
+        assert np.array_equal(ids, np.stack([ref.rows_ia, ref.rows_ib, ref.rows_rec, ref.rows_pair], axis=1)), s
         assert rel_err(vb[sl], ref.vel) <= 1e-5
     b.step(4, allow=(R.RELCP_ERR_NOT_CONVERGED,))
     st = b.scene_stats()

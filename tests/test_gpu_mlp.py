@@ -91,8 +91,12 @@ def test_trained_guess_gain_and_same_results(relcp_gpu, orc):
     """Train on pairs the method generates (a 4,096-body compaction, FP64 SNSD
     targets), then on a held-out state: the learned correction lands closer to
     the SNSD normal than the analytic seed it corrects, the step with the
-    learned start needs no more Newton iterations at C^k than the cold start,
-    and every result is the same (Newton judges)."""
+    learned start needs no more Newton iterations at C^k than the cold start
+    over the state's pairs (all evaluated afresh), and every result is the
+    same (Newton judges).  The gain is not asserted: from the analytic seed
+    Newton converges in about two iterations, and saving one would take a
+    start about ten times closer than this network's; the iteration counts,
+    declined guesses and kernel times are printed for the record."""
     R = relcp_gpu
     feat, targ = learned.harvest_compaction(n=4096, seed=11, steps=300, every=10)
     assert feat.shape[0] > 100000
@@ -120,7 +124,8 @@ def test_trained_guess_gain_and_same_results(relcp_gpu, orc):
     assert err_mlp < 0.9 * err_seed
     res = {}
     for guess in (R.RELCP_GUESS_COLD, R.RELCP_GUESS_MLP):
-        cfg = R.make_config(**{**base, "box": tuple(box), "guess": guess})
+        cfg = R.make_config(**{**base, "box": tuple(box), "guess": guess,
+                               "flags": base["flags"] | R.RELCP_FLAG_PHASE_TIMING})
         s = R.Simulation(cfg)
         if guess == R.RELCP_GUESS_MLP:
             R.relcp_load_mlp(s.ctx, params)
@@ -144,5 +149,8 @@ def test_trained_guess_gain_and_same_results(relcp_gpu, orc):
     assert np.abs(vc - vm).max() <= 1e-5 * np.abs(vc).max()
     it_cold = sc_.newton_iters_c0 / len(pc)
     it_mlp = sm_.newton_iters_c0 / len(pm)
-    print(f"Newton iterations per pair at C^k: cold {it_cold:.4f}, learned {it_mlp:.4f}")
-    assert it_mlp <= it_cold
+    print(f"Newton iterations per pair at C^k: cold {it_cold:.4f}, learned {it_mlp:.4f}; "
+          f"rejected guesses {sm_.newton_fallbacks} of {len(pm)}; SNSD kernel time "
+          f"cold {sc_.ms_snsd_kernel:.4f} ms, learned {sm_.ms_snsd_kernel:.4f} ms")
+    assert sc_.snsd_c0_evaluated == len(pc) and sm_.snsd_c0_evaluated == len(pm)
+    assert it_mlp <= it_cold, (it_mlp, it_cold)
