@@ -37,6 +37,9 @@ sys.path.insert(0, ROOT)
 
 WORKLOAD = "compacting ellipsoid suspension, 32768 bodies, phi 0.1->0.55 over 2000 steps, dt 5e-3, overdamped"
 SCHEDULE_STEPS = 2000
+# DRAM bytes (read + write) of one lcp_kernel launch at the dense end of the
+# schedule, from the ncu capture summarised in profiles/
+LCP_DRAM_BYTES_PER_LAUNCH = 10.03e6
 
 
 def timed_indices(total: int, k: int) -> list:
@@ -809,7 +812,11 @@ def main():
             "gpu_launches": acc["launches"],
             "roofline": {"kernel": "lcp_kernel (persistent BB projected gradient)", "bound": "hbm",
                          "achieved": lcp_gbs, "peak": hbm, "unit": "GB/s", "frac": lcp_gbs / hbm,
-                         "traffic": None, "peak_kind": peak_kind, "launches": acc["lcp_launches"],
+                         "traffic": LCP_DRAM_BYTES_PER_LAUNCH,
+                         "traffic_note": "dram__bytes_read.sum + dram__bytes_write.sum of the dense-end launch "
+                                         "(schedule step 1950, 79 iterations; 5.31 MB at step 1050): "
+                                         "profiles/lcp_kernel_traffic_compaction32k.md",
+                         "peak_kind": peak_kind, "launches": acc["lcp_launches"],
                          "kernel_ms_total": acc["lcp_ms"],
                          "bytes": "per iteration 76 B per row + 75 B per body (FP32 rows, FP64 offsets)"},
             "cpu_baseline": cpu,

@@ -111,7 +111,7 @@ COLONY_SKIN = 0.05
 
 def colony_run(target_cells: int, shape: int = R.RELCP_SHAPE_ELLIPSOID, guess: int = R.RELCP_GUESS_MLP,
                mlp_params=None, precision: int = R.RELCP_MIXED, seed: int = 0, rate: float = 0.01,
-               max_steps: int = 10 ** 6, stream=None, lcp_tol: float = 2e-8, lcp_max_iter: int = 5000):
+               max_steps: int = 10 ** 6, stream=None, lcp_tol: float = 5e-8, lcp_max_iter: int = 5000):
     """Grow a colony (scenes.Colony: rate N(0.01, 0.001) per cell, division
     at L = 2 with N(0, 0.05) rad jitter, dt = 0.05, planar overdamped
     dynamics) from one cell until it holds `target_cells` cells, the GPU

@@ -754,3 +754,42 @@ def test_host_roundtrip_keeps_carried_state(relcp_gpu, staging):
     assert b.stats().pair_list_rebuilt == 1
     a.close()
     b.close()
+
+
+@pytest.mark.parametrize("precision,bound,tol", [(0, 1e-9, None), (1, 1e-4, 3e-7)])
+def test_step_parity_spherocylinders(relcp_gpu, orc, precision, bound, tol):
+    """Spherocylinders (the colony cells of Sec. 5.4) in a periodic box, pulled
+    towards the box centre by a linear force (overdamped): one step from the
+    same state on the GPU and in the oracle at each of 12 states along the
+    oracle's trajectory (the recursion reaches depth 6), with pairs and
+    constraint ids bit for bit.  Rows appended to pairs of flat-sided bodies
+    nearly repeat earlier rows, so the LCP is close to singular: the FP64 path
+    needs up to ~6x10^4 projected-gradient iterations, and the mixed path's
+    FP32 iterates stall near a residual of 1e-7 (the pull towards the centre
+    makes the contact velocities large against their differences), hence its
+    looser residual 3e-7 and velocity bound 1e-4 here."""
+    R = relcp_gpu
+    rng = np.random.default_rng(61)
+    n, side = 80, 11.0
+    rho = rng.uniform(0.3, 0.5, n)
+    h = rng.uniform(0.2, 0.9, n)
+    axes = np.stack([h + rho, rho, rho], axis=1)
+    x = scenes._rsa_positions(rng, axes[:, 0], side, max_attempts=500 * n)
+    q = scenes.random_quaternions(rng, n)
+    box = np.full(3, side)
+    fext = np.zeros((n, 6))
+    fext[:, :3] = -(x - side / 2) * 2.0
+    amin = float(rho.min())
+    ocfg = orc.Config(dynamics=orc.OVERDAMPED, dt=0.05, eps_ncp=1e-3 * amin, box=tuple(box), skin=0.1 * amin,
+                      shape=orc.SHAPE_SPHEROCYLINDER)
+    gcfg = R.make_config(dynamics=R.RELCP_OVERDAMPED, precision=precision, dt=0.05, eps_ncp=1e-3 * amin,
+                         box=tuple(box), skin=0.1 * amin, length_scale=amin, shape=R.RELCP_SHAPE_SPHEROCYLINDER,
+                         lcp_tol=tol, lcp_max_iter=200000)
+    rows, depth = 0, 0
+    for k in range(12):
+        sck = scenes.Scene(x=x, q=q, axes=axes, vel=np.zeros((n, 6)), fext=fext, box=box, dt=0.05)
+        ref, stats = compare_step(R, orc, sck, ocfg, gcfg, fext=fext, bound=bound)
+        rows += ref.rows_ia.size
+        depth = max(depth, ref.depth)
+        x, q = ref.x, ref.q
+    assert rows > 500 and depth >= 3  # the flat sides make the recursion append rows
