@@ -2,8 +2,9 @@
 // Newton on the sphere decides every result).
 //
 // Network: features (16, 13 used) -> 128 -> 128 -> 128 -> outputs (8, 5 used),
-// ReLU, BF16 operands on the tensor cores (mma.sync.m16n8k16, FP32
-// accumulation).
+// ReLU, BF16 operands on the tensor cores, FP32 accumulation: inference with
+// mma.sync.m16n8k16 fragments chained through registers, training GEMMs with
+// tcgen05.mma into tensor memory (the 8-wide output layer with mma.sync).
 //   features : d = c_b - c_a (minimum image) in a's frame divided by
 //              s = max(a_a) + max(a_b); q_rel = conj(q_a) (x) q_b with s >= 0;
 //              a's and b's semi-axes; the analytic seed (P_a + P_b)^-1 d,
@@ -20,9 +21,9 @@
 // registers.  Inside a step one kernel does the whole start for a list of
 // pairs (features, network, rotated normal); relcp_mlp_forward runs the
 // network alone on given features.
-// Training is layer by layer with a generic tensor-core GEMM
-// C = A B^T (both operands K-contiguous BF16), transposes, the loss, bias sums
-// and Adam (Kingma & Ba) on FP32 master parameters.
+// Training is layer by layer with a tensor-core GEMM C = A B^T (both operands
+// K-contiguous BF16), transposes, the loss, bias sums and Adam (Kingma & Ba)
+// on FP32 master parameters.
 #include <cuda_bf16.h>
 
 #include <vector>
@@ -423,6 +424,189 @@ __global__ void __launch_bounds__(kFwdWarps * 32) mlp_guess_kernel(MlpFeatArgs f
 }
 
 // ---------------------------------------------------------------------------
+// training GEMM on the fifth-generation tensor cores (tcgen05):
+//     C[M x N] (+)= A[M x K] B[N x K]^T,  BF16 operands, FP32 accumulation
+// in tensor memory, for N a multiple of 16 in [16, 128] and K a multiple of
+// 16 (the hidden and input layers of the network; the 8-wide output layer
+// takes gemm_nt_kernel below).  One CTA of 128 threads per 128-row tile of C:
+// the threads stage 64-wide K chunks of A and B into shared memory in the
+// no-swizzle K-major core-matrix layout, one thread issues the chunk's
+// 128 x N x 16 MMAs (tcgen05.mma.cta_group::1.kind::f16) into a 128-lane x
+// 128-column FP32 accumulator in tensor memory and commits them to an
+// mbarrier, and after the last chunk each warp reads its 32 lanes back
+// (tcgen05.ld.32x32b).  Every wait is bounded: a timeout records DEV_TIMEOUT,
+// waits once more (bounded) for the MMAs in flight, frees the tensor memory
+// and skips the store.
+// ---------------------------------------------------------------------------
+constexpr int kTcM = 128;              // rows of a tile (the MMA's M)
+constexpr int kTcK = 64;               // K staged per chunk
+constexpr int kTcMaxN = 128;           // widest N handled (one tile, 128 TMEM columns)
+constexpr int kTcThreads = 128;
+constexpr unsigned kTcCols = 128;      // TMEM columns allocated per CTA
+// 4 CTAs per SM at most (4 x 128 = all 512 TMEM columns): the dynamic shared
+// memory request keeps a fifth CTA off the SM, so no allocation ever waits
+constexpr size_t kTcSmem = 56 * 1024;
+constexpr long long kTcWaitLimit = 1ll << 20;
+
+// byte offset of element (r, k) in a [rows x kTcK] K-major chunk: core
+// matrices of 8 rows x 16 bytes (8 BF16 along K), consecutive along K 128 bytes
+// apart (the descriptor's leading-dimension byte offset), 8-row groups
+// kTcK / 8 x 128 = 1024 bytes apart (its stride-dimension byte offset)
+__device__ __forceinline__ uint32_t tc_core_off(int r, int k) {
+    return (uint32_t)((((r >> 3) * (kTcK / 8) + (k >> 3)) << 7) + ((r & 7) << 4) + ((k & 7) << 1));
+}
+
+// shared-memory matrix descriptor: start address >> 4 (bits 0-13), leading
+// byte offset >> 4 (16-29), stride byte offset >> 4 (32-45), the fixed value
+// 0b001 in bits 46-48, base offset 0, no swizzle (bits 61-63 = 0)
+__device__ __forceinline__ uint64_t tc_smem_desc(uint32_t saddr) {
+    uint64_t d = (uint64_t)((saddr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)(128u >> 4) << 16;
+    d |= (uint64_t)(1024u >> 4) << 32;
+    d |= (uint64_t)1 << 46;
+    return d;
+}
+
+// instruction descriptor of kind::f16: FP32 accumulator (bits 4-5 = 1), BF16
+// A and B (bits 7-9, 10-12 = 1), both K-major (bits 15, 16 = 0), N >> 3 in
+// bits 17-22, M >> 4 in bits 24-28
+__host__ __device__ constexpr uint32_t tc_idesc(int n) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(kTcM >> 4) << 24);
+}
+
+__device__ __forceinline__ bool tc_wait(uint32_t bar, unsigned parity) {
+    unsigned done = 0;
+    for (long long it = 0; it < kTcWaitLimit && !done; ++it) {
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+            : "=r"(done)
+            : "r"(bar), "r"(parity)
+            : "memory");
+    }
+    return done != 0;
+}
+
+__global__ void __launch_bounds__(kTcThreads) gemm_nt_tc_kernel(int M, int N, int K, const __nv_bfloat16* __restrict__ A,
+                                                                int lda, const __nv_bfloat16* __restrict__ B, int ldb,
+                                                                float* __restrict__ C, int ldc, int accumulate,
+                                                                int* __restrict__ status) {
+    extern __shared__ __align__(1024) unsigned char tc_smem[];
+    unsigned char* sA = tc_smem;                    // kTcM x kTcK BF16 (16 KB)
+    unsigned char* sB = tc_smem + kTcM * kTcK * 2;  // kTcMaxN x kTcK BF16 (16 KB)
+    __shared__ __align__(8) unsigned long long mbar;
+    __shared__ uint32_t tmem_base;
+    __shared__ int failed;
+    const int m0 = blockIdx.x * kTcM;
+    // split K: CTA y takes the K range [kbeg, kend) and adds its partial
+    // product to C with atomics (the caller has C initialised: accumulate)
+    const int kper = ((K + (int)gridDim.y - 1) / (int)gridDim.y + kTcK - 1) / kTcK * kTcK;
+    const int kbeg = (int)blockIdx.y * kper, kend = kbeg + kper < K ? kbeg + kper : K;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t bar = (uint32_t)__cvta_generic_to_shared(&mbar);
+    const uint32_t a_s = (uint32_t)__cvta_generic_to_shared(sA), b_s = (uint32_t)__cvta_generic_to_shared(sB);
+    if (threadIdx.x == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        failed = 0;
+    }
+    if (warp == 0) {
+        const uint32_t dst = (uint32_t)__cvta_generic_to_shared(&tmem_base);
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(dst), "r"(kTcCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = tmem_base;
+    const uint32_t idesc = tc_idesc(N);
+    unsigned parity = 0;
+    bool issued = false;  // MMAs of this CTA may be in flight
+    for (int k0 = kbeg; k0 < kend; k0 += kTcK) {
+        const int kc = kend - k0 < kTcK ? kend - k0 : kTcK;  // a multiple of 16
+        // stage the chunk: 16-byte units of 8 BF16 along K; rows past M and
+        // units past the chunk's K are zero
+        for (int e = threadIdx.x; e < kTcM * (kTcK / 8); e += kTcThreads) {
+            const int r = e / (kTcK / 8), c = e % (kTcK / 8);
+            uint4 v = make_uint4(0u, 0u, 0u, 0u);
+            if (m0 + r < M && 8 * c < kc) v = *reinterpret_cast<const uint4*>(A + (int64_t)(m0 + r) * lda + k0 + 8 * c);
+            *reinterpret_cast<uint4*>(sA + tc_core_off(r, 8 * c)) = v;
+        }
+        for (int e = threadIdx.x; e < N * (kTcK / 8); e += kTcThreads) {
+            const int r = e / (kTcK / 8), c = e % (kTcK / 8);
+            uint4 v = make_uint4(0u, 0u, 0u, 0u);
+            if (8 * c < kc) v = *reinterpret_cast<const uint4*>(B + (int64_t)r * ldb + k0 + 8 * c);
+            *reinterpret_cast<uint4*>(sB + tc_core_off(r, 8 * c)) = v;
+        }
+        // the tensor cores read shared memory through the async proxy
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            for (int j = 0; j < kc / 16; ++j) {
+                // K = 16 per MMA: two core matrices along K, 256 bytes per step
+                const uint64_t da = tc_smem_desc(a_s + 256u * j), db = tc_smem_desc(b_s + 256u * j);
+                const uint32_t acc = (k0 > kbeg || j > 0) ? 1u : 0u;
+                asm volatile(
+                    "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                    " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(tmem),
+                    "l"(da), "l"(db), "r"(idesc), "r"(acc)
+                    : "memory");
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+                         : "memory");
+        }
+        issued = true;
+        // the next chunk overwrites the operands: wait for this chunk's MMAs
+        const bool ok = tc_wait(bar, parity);
+        parity ^= 1u;
+        if (!ok && threadIdx.x == 0) failed = 1;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        __syncthreads();
+        if (failed) break;
+        issued = false;
+    }
+    if (failed) {
+        if (threadIdx.x == 0) atomicOr(status, DEV_TIMEOUT);
+        if (issued) tc_wait(bar, parity ^ 1u);  // once more, bounded, for the MMAs in flight
+    } else if (kbeg < kend) {
+        // epilogue: warp w holds rows m0 + 32 w + lane in TMEM lanes 32 w .. 32 w + 31
+        const int row = m0 + warp * 32 + lane;
+        for (int c0 = 0; c0 < N; c0 += 16) {
+            uint32_t v[16];
+            const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
+                "[%16];"
+                : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+                  "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
+                  "=r"(v[15])
+                : "r"(taddr)
+                : "memory");
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            if (row < M) {
+                float* d = C + (int64_t)row * ldc + c0;
+                if (gridDim.y > 1) {
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) atomicAdd(d + j, __uint_as_float(v[j]));
+                } else {
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) {
+                        const float x = __uint_as_float(v[j]);
+                        d[j] = accumulate ? d[j] + x : x;
+                    }
+                }
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTcCols) : "memory");
+}
+
+// ---------------------------------------------------------------------------
 // training: generic tensor-core GEMM C[M x N] (+)= A[M x K] B[N x K]^T
 // ---------------------------------------------------------------------------
 constexpr int kGT = 64;  // tile M and N
@@ -573,11 +757,38 @@ __global__ void mask_grad_kernel(float* __restrict__ grad) {
 
 inline unsigned nb(int64_t n, int t = 256) { return (unsigned)((n + t - 1) / t); }
 
+// tcgen05 kernel when the shape and the 16-byte alignment of the operand rows
+// allow it (N a multiple of 16 in [16, 128], K a multiple of 16, row strides a
+// multiple of 8 elements, 16-byte aligned bases), else the mma.sync kernel
 relcp_status gemm_nt(int M, int N, int K, const __nv_bfloat16* A, int lda, const __nv_bfloat16* B, int ldb, float* C,
-                     int ldc, bool accumulate, cudaStream_t s) {
-    dim3 grid((N + kGT - 1) / kGT, (M + kGT - 1) / kGT);
+                     int ldc, bool accumulate, cudaStream_t s, int* status) {
+    if (M <= 0 || N <= 0) return RELCP_OK;
+    const bool tc = status != nullptr && N % 16 == 0 && N >= 16 && N <= kTcMaxN && K % 16 == 0 && K >= 16 &&
+                    lda % 8 == 0 && ldb % 8 == 0 && ((uintptr_t)A & 15) == 0 && ((uintptr_t)B & 15) == 0;
     note_launch();
-    gemm_nt_kernel<<<grid, 128, 0, s>>>(M, N, K, A, lda, B, ldb, C, ldc, accumulate ? 1 : 0);
+    if (tc) {
+        static bool attr_set[64] = {false};
+        int dev = 0;
+        RELCP_CUDA(cudaGetDevice(&dev));
+        if (dev >= 0 && dev < 64 && !attr_set[dev]) {
+            RELCP_CUDA(cudaFuncSetAttribute(gemm_nt_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmem));
+            attr_set[dev] = true;
+        }
+        // a long K with few row tiles (the weight gradients, K = batch) is
+        // split over CTAs that add into C (which then must hold its initial
+        // value: only with accumulate)
+        const int mt = (M + kTcM - 1) / kTcM;
+        int ks = 1;
+        if (accumulate && mt < 32 && K >= 8 * kTcK) {
+            ks = K / (8 * kTcK);
+            if (ks > 64) ks = 64;
+        }
+        gemm_nt_tc_kernel<<<dim3((unsigned)mt, (unsigned)ks), kTcThreads, kTcSmem, s>>>(M, N, K, A, lda, B, ldb, C, ldc,
+                                                                                       accumulate ? 1 : 0, status);
+    } else {
+        dim3 grid((N + kGT - 1) / kGT, (M + kGT - 1) / kGT);
+        gemm_nt_kernel<<<grid, 128, 0, s>>>(M, N, K, A, lda, B, ldb, C, ldc, accumulate ? 1 : 0);
+    }
     RELCP_CUDA(cudaGetLastError());
     return RELCP_OK;
 }
@@ -693,6 +904,7 @@ relcp_status mlp_train_step(int64_t B, float* params, float* am, float* av, cons
     DBuf<float> Z1, Z2, Z3, O, dO, dH, grad, dH2;
     DBuf<__nv_bfloat16> Xb, H1b, H2b, H3b, Wb, Wtb, T1, T2;
     DBuf<double> part;
+    DBuf<int> tstat;  // DEV_* bits of the tensor-core GEMMs
     relcp_status st = RELCP_OK;
     auto R = [&](relcp_status e) {
         if (st == RELCP_OK) st = e;
@@ -704,9 +916,10 @@ relcp_status mlp_train_step(int64_t B, float* params, float* am, float* av, cons
             R(grad.ensure(kMlpParams, s)) || R(Xb.ensure(B * 16, s)) || R(H1b.ensure(B * H, s)) ||
             R(H2b.ensure(B * H, s)) || R(H3b.ensure(B * H, s)) || R(Wb.ensure(H * H, s)) ||
             R(Wtb.ensure(H * H, s)) || R(T1.ensure(B * H, s)) || R(T2.ensure(B * H, s)) ||
-            R(part.ensure(nb(B), s)))
+            R(part.ensure(nb(B), s)) || R(tstat.ensure(1, s)))
             break;
         cudaError_t ce = cudaMemsetAsync(grad.p, 0, kMlpParams * sizeof(float), s);
+        if (ce == cudaSuccess) ce = cudaMemsetAsync(tstat.p, 0, sizeof(int), s);
         if (ce != cudaSuccess) {
             set_error("%s", cudaGetErrorString(ce));
             st = RELCP_ERR_CUDA;
@@ -724,7 +937,7 @@ relcp_status mlp_train_step(int64_t B, float* params, float* am, float* av, cons
         for (int l = 0; l < 4 && st == RELCP_OK; ++l) {
             const L& ly = layers[l];
             if (R(cast(ly.out, ly.in, params + ly.offw, Wb.p, false, s))) break;
-            if (R(gemm_nt((int)B, ly.out, ly.in, Ins[l], ly.in, Wb.p, ly.in, Zs[l], ly.out, false, s))) break;
+            if (R(gemm_nt((int)B, ly.out, ly.in, Ins[l], ly.in, Wb.p, ly.in, Zs[l], ly.out, false, s, tstat.p))) break;
             note_launch();
             bias_relu_kernel<<<nb(B * ly.out), 256, 0, s>>>(B, ly.out, Zs[l], params + ly.offb, l < 3 ? 1 : 0);
             if (l < 3 && R(cast(B, ly.out, Zs[l], Outs[l], false, s))) break;
@@ -743,7 +956,11 @@ relcp_status mlp_train_step(int64_t B, float* params, float* am, float* av, cons
             if (R(cast(B, dzcols, dZ, T1.p, true, s))) break;
             const float* Hprev = l == 0 ? feat : Zs[l - 1];
             if (R(cast(B, ly.in, Hprev, T2.p, true, s))) break;
-            if (R(gemm_nt(ly.out, ly.in, (int)B, T1.p, (int)B, T2.p, (int)B, grad.p + ly.offw, ly.in, false, s))) break;
+            // (grad is zeroed above and each weight block receives one product:
+            // accumulating lets the tensor-core GEMM split its long K = batch)
+            if (R(gemm_nt(ly.out, ly.in, (int)B, T1.p, (int)B, T2.p, (int)B, grad.p + ly.offw, ly.in, true, s,
+                          tstat.p)))
+                break;
             note_launch();
             colsum_kernel<<<ly.out, 256, 0, s>>>(B, dzcols, dZ, grad.p + ly.offb);
             if (l == 0) break;
@@ -753,7 +970,7 @@ relcp_status mlp_train_step(int64_t B, float* params, float* am, float* av, cons
             const __nv_bfloat16* dZb = T1.p;
             if (R(cast(ly.out, ly.in, params + ly.offw, Wtb.p, true, s))) break;
             float* dHn = (l % 2 == 1) ? dH.p : dH2.p;
-            if (R(gemm_nt((int)B, ly.in, ly.out, dZb, ly.out, Wtb.p, ly.out, dHn, ly.in, false, s))) break;
+            if (R(gemm_nt((int)B, ly.in, ly.out, dZb, ly.out, Wtb.p, ly.out, dHn, ly.in, false, s, tstat.p))) break;
             note_launch();
             relu_back_kernel<<<nb(B * ly.in), 256, 0, s>>>(B * ly.in, dHn, Zs[l - 1]);
             dZ = dHn;
@@ -777,8 +994,15 @@ relcp_status mlp_train_step(int64_t B, float* params, float* am, float* av, cons
                                                        tc.eps, c1, c2);
         }
         std::vector<double> hp(nb(B));
+        int hstat = 0;
         ce = cudaMemcpyAsync(hp.data(), part.p, hp.size() * sizeof(double), cudaMemcpyDeviceToHost, s);
+        if (ce == cudaSuccess) ce = cudaMemcpyAsync(&hstat, tstat.p, sizeof(int), cudaMemcpyDeviceToHost, s);
         if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
+        if (ce == cudaSuccess && (hstat & DEV_TIMEOUT)) {
+            set_error("a tensor-core GEMM's wait for its MMAs timed out");
+            st = RELCP_ERR_TIMEOUT;
+            break;
+        }
         if (ce != cudaSuccess) {
             set_error("%s", cudaGetErrorString(ce));
             st = RELCP_ERR_CUDA;
@@ -793,6 +1017,7 @@ relcp_status mlp_train_step(int64_t B, float* params, float* am, float* av, cons
     DBuf<__nv_bfloat16>* bb[] = {&Xb, &H1b, &H2b, &H3b, &Wb, &Wtb, &T1, &T2};
     for (auto* b : bb) b->release(s);
     part.release(s);
+    tstat.release(s);
     return st;
 }
 

@@ -111,12 +111,15 @@ COLONY_SKIN = 0.05
 
 def colony_run(target_cells: int, shape: int = R.RELCP_SHAPE_ELLIPSOID, guess: int = R.RELCP_GUESS_MLP,
                mlp_params=None, precision: int = R.RELCP_MIXED, seed: int = 0, rate: float = 0.01,
-               max_steps: int = 10 ** 6, stream=None, lcp_tol: float = 5e-8, lcp_max_iter: int = 5000):
+               max_steps: int = 10 ** 6, stream=None, lcp_tol: float = 5e-8, lcp_max_iter: int = 5000,
+               max_seconds: float = 600.0):
     """Grow a colony (scenes.Colony: rate N(0.01, 0.001) per cell, division
     at L = 2 with N(0, 0.05) rad jitter, dt = 0.05, planar overdamped
-    dynamics) from one cell until it holds `target_cells` cells, the GPU
-    stepping it and the driver growing and dividing the cells between steps
-    (every step hands the library the new bodies).  Returns the steps, the
+    dynamics) from one cell until it holds `target_cells` cells (or
+    `max_seconds` pass), the GPU stepping it and the driver growing and
+    dividing the cells between steps (every step hands the library the new
+    bodies); steps whose LCP hit its iteration cap or whose recursion hit its
+    cap are counted and the run goes on.  Returns the steps, the
     final cell count, the host wall time, the summed device-synchronised step
     time, the largest accepted overlap, the steps whose C^k evaluation the
     learned start seeded and the Newton iterations per pair at C^k."""
@@ -131,18 +134,20 @@ def colony_run(target_cells: int, shape: int = R.RELCP_SHAPE_ELLIPSOID, guess: i
     sim = R.Simulation(cfg, stream)
     if guess == R.RELCP_GUESS_MLP:
         R.relcp_load_mlp(sim.ctx, mlp_params)
-    steps, maxov, learned, its, evals, worst, body_steps = 0, 0.0, 0, 0, 0, set(), 0
+    steps, maxov, learned, its, evals, worst, body_steps, capped, deep = 0, 0.0, 0, 0, 0, set(), 0, 0, 0
     t0 = time.perf_counter()
     step_s = 0.0
-    while col.n < target_cells and steps < max_steps:
+    while col.n < target_cells and steps < max_steps and time.perf_counter() - t0 < max_seconds:
         sim.set_bodies(np.ascontiguousarray(col.x), col.q(), col.axes())
         torch.cuda.synchronize()
         ts = time.perf_counter()
-        st = sim.step(1, allow=(R.RELCP_ERR_NOT_CONVERGED,))
+        st = sim.step(1, allow=(R.RELCP_ERR_NOT_CONVERGED, R.RELCP_ERR_RECURSION_LIMIT))
         x, q, _ = sim.bodies()
         step_s += time.perf_counter() - ts
         s = sim.stats()
         worst.add(R.STATUS_NAMES[st])
+        capped += int(st == R.RELCP_ERR_NOT_CONVERGED)
+        deep += int(st == R.RELCP_ERR_RECURSION_LIMIT)
         maxov = max(maxov, s.max_overlap)
         learned += s.guess_used
         its += s.newton_iters_c0
@@ -154,5 +159,7 @@ def colony_run(target_cells: int, shape: int = R.RELCP_SHAPE_ELLIPSOID, guess: i
     sim.close()
     return {"cells": col.n, "steps": steps, "divisions": col.divisions, "wall_s": wall, "step_s": step_s,
             "body_steps_per_s": body_steps / max(step_s, 1e-30),
-            "max_overlap": maxov, "eps_ncp": COLONY_EPS, "status": sorted(worst), "learned_start_steps": learned,
+            "max_overlap": maxov, "eps_ncp": COLONY_EPS, "status": sorted(worst), "lcp_capped_steps": capped,
+            "recursion_capped_steps": deep,
+            "learned_start_steps": learned,
             "newton_iters_per_pair_c0": its / max(evals, 1)}
