@@ -227,7 +227,12 @@ relcp_status relcp_set_bodies(relcp_ctx* ctx, int64_t n, const int32_t* scene_of
 
 /* Advance nsteps >= 1 ReLCP time steps (Algorithm 1 per step).  Returns the
  * first non-OK status; the state then holds the configuration accepted by
- * that step (or the last good one for RELCP_ERR_CUDA). */
+ * that step (or the last good one for RELCP_ERR_CUDA and RELCP_ERR_TIMEOUT,
+ * after which the context stays usable: every device wait is bounded in
+ * time).  RELCP_ERR_NOT_CONVERGED (an LCP reached lcp_max_iter),
+ * RELCP_ERR_RECURSION_LIMIT (max_recursion augmentations, the last trial
+ * accepted) and RELCP_ERR_NEWTON (an SNSD solve did not converge) still accept
+ * the step; RELCP_ERR_CAPACITY does not. */
 relcp_status relcp_step(relcp_ctx* ctx, int32_t nsteps);
 
 /* Copy out the state: x n x 3 (wrapped), q n x 4, vel n x 6 = velocity of
