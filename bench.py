@@ -429,7 +429,8 @@ def _oracle_steps_worker(x, q, axes, box, dt, eps, skin, rate, nsteps):
         el = time.perf_counter() - t0
         out.append({"seconds": el, "pairs": r.pairs, "ids": np.stack([r.rows_ia, r.rows_ib, r.rows_rec,
                                                                       r.rows_pair], axis=1).astype(np.int32),
-                    "vel": r.vel, "uc": r.U_contact, "depth": r.depth, "max_overlap": r.max_overlap,
+                    "vel": r.vel, "uc": r.U_contact, "gamma": r.gamma, "depth": r.depth,
+                    "max_overlap": r.max_overlap,
                     "status": r.status, "ambiguous": r.ambiguous, "rows": int(r.rows_ia.size)})
         x, q, box = r.x, r.q, np.asarray(r.box)
     return out
@@ -456,14 +457,20 @@ def host_cores():
         return os.cpu_count() or 1
 
 
+def _max_known(vals):
+    vals = [v for v in vals if v is not None]
+    return max(vals) if vals else None
+
+
 def subset_check(R, torch, arms, nsteps=2, processes=None, max_step=1750):
     """The oracle on the 1,024-body subset (the baseline leg) and the error of
     each GPU arm against it.  From every subset state both the oracle and each
     GPU arm take `nsteps` consecutive steps (the GPU carrying its SNSD values,
     warm starts and cached pair list from its first step to the next, as in
     the timed run).  Per step: candidate pairs and constraint ids (a, b,
-    recursion, pair) bit for bit, velocities and contact velocities as
-    normwise relative errors, and the GPU's max overlap against eps_NCP.  The
+    recursion, pair) bit for bit, velocities, contact velocities and the
+    constraint impulses gamma as max-norm relative errors (gamma where the
+    constraint sets agree), and the GPU's max overlap against eps_NCP.  The
     first step starts from the identical state; later steps start from each
     side's own previous result."""
     sc, states = subset_states()
@@ -495,15 +502,18 @@ def subset_check(R, torch, arms, nsteps=2, processes=None, max_step=1750):
                 st = sim.step(1, allow=(R.RELCP_ERR_NOT_CONVERGED,))
                 s = sim.stats()
                 pairs, _ = R.relcp_get_pairs(sim.ctx)
-                ids, _, _ = R.relcp_get_rows(sim.ctx)
+                ids, _, gam = R.relcp_get_rows(sim.ctx)
                 _, _, v = sim.bodies()
                 uc = R.relcp_get_contact_velocity(sim.ctx, sc.n)
+                same_rows = bool(np.array_equal(ids, o["ids"]))
                 per.append({"step": k + j, "phi": vol / float(np.prod(box)) if j == 0 else None,
                             "from_identical_state": j == 0, "status": R.STATUS_NAMES[st],
                             "pairs_equal": bool(np.array_equal(pairs, o["pairs"])),
-                            "rows_equal": bool(np.array_equal(ids, o["ids"])), "rows": o["rows"],
+                            "rows_equal": same_rows, "rows": o["rows"],
                             "depth": [int(s.depth), int(o["depth"])], "vel_rel_err": rel(v, o["vel"]),
-                            "contact_vel_rel_err": rel(uc, o["uc"]), "max_overlap": float(s.max_overlap),
+                            "contact_vel_rel_err": rel(uc, o["uc"]),
+                            "gamma_rel_err": rel(gam, o["gamma"]) if same_rows else None,
+                            "max_overlap": float(s.max_overlap),
                             "oracle_ambiguous": int(o["ambiguous"])})
             sim.close()
         first = [p for p in per if p["from_identical_state"]]
@@ -511,11 +521,13 @@ def subset_check(R, torch, arms, nsteps=2, processes=None, max_step=1750):
             "identical_start": {"pairs_equal": all(p["pairs_equal"] for p in first),
                                 "rows_equal": all(p["rows_equal"] for p in first),
                                 "vel_rel_err_max": max(p["vel_rel_err"] for p in first),
-                                "contact_vel_rel_err_max": max(p["contact_vel_rel_err"] for p in first)},
+                                "contact_vel_rel_err_max": max(p["contact_vel_rel_err"] for p in first),
+                                "gamma_rel_err_max": _max_known(p["gamma_rel_err"] for p in first)},
             "all_steps": {"pairs_equal": all(p["pairs_equal"] for p in per),
                           "rows_equal": all(p["rows_equal"] for p in per),
                           "vel_rel_err_max": max(p["vel_rel_err"] for p in per),
-                          "contact_vel_rel_err_max": max(p["contact_vel_rel_err"] for p in per)},
+                          "contact_vel_rel_err_max": max(p["contact_vel_rel_err"] for p in per),
+                          "gamma_rel_err_max": _max_known(p["gamma_rel_err"] for p in per)},
             "max_overlap": max(p["max_overlap"] for p in per), "max_overlap_within_eps":
                 all(p["max_overlap"] <= eps for p in per), "steps": per}
     steps_done = sum(len(o) for o in orc)

@@ -80,14 +80,16 @@ typedef struct relcp_config {
                               RELCP_OVERDAMPED_2D (the same law in the z = 0 plane) */
     int32_t precision;     /* RELCP_FP64: every operation FP64.  RELCP_MIXED: FP32 LCP iterations, SNSD
                               Newton iterations and constraint-row assembly; FP64 SNSD polish (Phi),
-                              row offsets (Phi + c d^T U), overlap test, LCP residual and the state. */
+                              row offsets (Phi + c d^T U), overlap test, LCP residual and the state; the
+                              LCP iterations are refined by an FP64 residual (RELCP_FLAG_NO_LCP_REFINE). */
     int32_t guess;         /* SNSD Newton start: RELCP_GUESS_COLD or RELCP_GUESS_MLP (needs relcp_load_mlp).
                               With RELCP_GUESS_MLP the network seeds a step's C^k evaluation when that
                               step evaluates at least 4096 pairs (decided on the device); fewer pairs (the
                               usual case once a step carries the previous step's values) take the cold
                               seeds, whose Newton solves are cheaper than the network's fixed latency.
                               Either start converges to the same SNSD within the Newton tolerance. */
-    int32_t lcp_max_iter;  /* projected-gradient iteration cap per LCP (> 0) */
+    int32_t lcp_max_iter;  /* projected-gradient iteration cap per LCP (> 0); a refined mixed solve
+                              applies it to its FP32 iterations and to its correction solve apart */
     int32_t max_recursion; /* augmentation cap; 0 gives the single-constraint SNSD-LCP */
     int32_t n_scenes;      /* 1 (batched scenes are a separate entry point) */
     double dt;             /* time step (> 0) */
@@ -125,6 +127,12 @@ enum {
                                       gamma of the same pair (the solution is the same within lcp_tol) */
     RELCP_FLAG_JACOBI = 4u,        /* projected-gradient steps scaled by 1 / A_aa, BB lengths in the
                                       matching metric (same solution, fewer iterations on uneven rows) */
+    RELCP_FLAG_NO_LCP_REFINE = 256u, /* mixed path: solve each LCP by FP32 iterations to lcp_tol directly.  By
+                                      default, when every row has a thread of the persistent launch, the FP32
+                                      iterations stop at 10 x lcp_tol, the residual of that iterate is taken
+                                      in FP64 and the correction is solved in FP32 to lcp_tol (iterative
+                                      refinement: the FP32 rounding then scales with the correction, not with
+                                      the contact forces, and does not stall the solve above lcp_tol) */
     RELCP_FLAG_LEARNED_ALWAYS = 128u, /* with RELCP_GUESS_MLP: run the learned start on every C^k evaluation of
                                       at least one pair (by default it runs when a step evaluates 4,096 pairs
                                       or more at C^k, where its fixed cost pays) */

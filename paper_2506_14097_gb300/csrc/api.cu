@@ -615,6 +615,7 @@ relcp_status step_once(relcp_ctx* c) {
         pr.c = dt;
         pr.mixed = mixed ? 1 : 0;
         pr.tol = cfg.lcp_tol;
+        pr.refine = (cfg.flags & RELCP_FLAG_NO_LCP_REFINE) ? 0 : 1;
         pr.max_iter = (cfg.fault_inject & RELCP_FAULT_LCP_ITERS) ? 1 : cfg.lcp_max_iter;
         if (cfg.fault_inject & RELCP_FAULT_LCP_TIMEOUT) {
             pr.wait_ns = kFaultWaitNs;

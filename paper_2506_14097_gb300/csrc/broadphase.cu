@@ -12,6 +12,16 @@
 //
 // The distance test is a fixed sequence of separately rounded FP64
 // operations (no contraction), so the decision is reproducible bit for bit.
+//
+// The cached Verlet list's rebuild needs only a superset of the pairs within
+// the grown cutoff (every step filters the list with the exact test), so with
+// `superset` the cell-list passes test in FP32 (this part issues FP64 at a
+// small fraction of the FP32 rate) against the cutoff plus a margin m that
+// bounds the FP32 error: positions wrapped into [0, L) and rounded to FP32,
+// differences, the minimum image and the sum of squares err by less than
+// 8 2^-24 L in the distance, and m = 4e-6 (max L + 2 max rb + skin) is more than
+// eight times that.  A pair the FP32 rounding could misjudge lies within m of
+// the cutoff and is kept.
 #include <utility>
 
 #include "relcp_internal.cuh"
@@ -75,22 +85,54 @@ __global__ void cell_assign(int64_t n, View<3, const double> x, Grid g, int* __r
     atomicAdd(&cell_count[cid], 1);
 }
 
+// a body's position wrapped into [0, L) per axis and rounded to FP32, with its
+// bounding radius (the superset test's operands)
+__device__ __forceinline__ float4 wrapped_f32(View<3, const double> x, const double* __restrict__ rb, const Grid& g,
+                                              int64_t i) {
+    float w[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const double v = x(k, i);
+        w[k] = (float)(v - g.L[k] * floor(v / g.L[k]));
+    }
+    return make_float4(w[0], w[1], w[2], (float)rb[i]);
+}
+
+// xr (optional): the bodies' wrapped_f32 records in cell order, for the
+// superset test's contiguous loads
 __global__ void cell_fill(int64_t n, const int* __restrict__ cell_of, const int* __restrict__ cell_start,
-                          int* __restrict__ cursor, int* __restrict__ cell_body) {
+                          int* __restrict__ cursor, int* __restrict__ cell_body, View<3, const double> x,
+                          const double* __restrict__ rb, Grid g, float4* __restrict__ xr) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     int cid = cell_of[i];
     int slot = atomicAdd(&cursor[cid], 1);
     cell_body[cell_start[cid] + slot] = (int)i;
+    if (xr) xr[cell_start[cid] + slot] = wrapped_f32(x, rb, g, i);
 }
 
-template <bool FILL>
+__device__ __forceinline__ float min_image_f32(float d, float L, float invL) { return d - L * rintf(d * invL); }
+
+// SUPERSET: the FP32 test against (rb_i + rb_j + skin + margin) on the cell-
+// ordered records xr; otherwise the exact FP64 test
+template <bool FILL, bool SUPERSET>
 __global__ void cell_pairs(int64_t n, View<3, const double> x, const double* __restrict__ rb, Grid g, double skin,
                            const int* __restrict__ cell_of, const int* __restrict__ cell_start,
                            const int* __restrict__ cell_body, int* __restrict__ count, const int* __restrict__ off,
-                           int* __restrict__ pa, int* __restrict__ pb) {
+                           int* __restrict__ pa, int* __restrict__ pb, const float4* __restrict__ xr,
+                           float margin) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
+    float4 xi = make_float4(0.f, 0.f, 0.f, 0.f);
+    float Lf[3] = {0.f, 0.f, 0.f}, iLf[3] = {0.f, 0.f, 0.f}, sk = 0.f;
+    if (SUPERSET) {
+        xi = wrapped_f32(x, rb, g, i);
+        for (int k = 0; k < 3; ++k) {
+            Lf[k] = (float)g.L[k];
+            iLf[k] = (float)(1.0 / g.L[k]);
+        }
+        sk = (float)skin + margin;
+    }
     int cid = cell_of[i];
     int cx = cid % g.nc[0];
     int cy = (cid / g.nc[0]) % g.nc[1];
@@ -111,7 +153,18 @@ __global__ void cell_pairs(int64_t n, View<3, const double> x, const double* __r
                 for (int k = cell_start[nb]; k < e; ++k) {
                     int j = cell_body[k];
                     if (j <= i) continue;
-                    if (near_pair(x, rb, i, j, g.L[0], g.L[1], g.L[2], skin)) {
+                    bool near;
+                    if (SUPERSET) {
+                        const float4 xj = xr[k];
+                        const float dx = min_image_f32(xj.x - xi.x, Lf[0], iLf[0]);
+                        const float dy = min_image_f32(xj.y - xi.y, Lf[1], iLf[1]);
+                        const float dz = min_image_f32(xj.z - xi.z, Lf[2], iLf[2]);
+                        const float r = xi.w + xj.w + sk;
+                        near = dx * dx + dy * dy + dz * dz <= r * r;
+                    } else {
+                        near = near_pair(x, rb, i, j, g.L[0], g.L[1], g.L[2], skin);
+                    }
+                    if (near) {
                         if (FILL) {
                             pa[o + c] = (int)i;
                             pb[o + c] = j;
@@ -305,7 +358,7 @@ __global__ void memo_remap_kernel(int64_t nv, const int* __restrict__ vpa, const
 
 relcp_status broadphase(int64_t n, View<3, const double> x, const double* rb, double rbmax_hint, const double box[3],
                         double skin, DBuf<int>& pa, DBuf<int>& pb, int64_t* npairs, BroadphaseScratch& sc,
-                        cudaStream_t s) {
+                        cudaStream_t s, bool superset) {
     *npairs = 0;
     if (n < 2) return RELCP_OK;
     unsigned nb = (unsigned)((n + kThreads - 1) / kThreads);
@@ -315,6 +368,7 @@ relcp_status broadphase(int64_t n, View<3, const double> x, const double* rb, do
     bool periodic = box[0] > 0 && box[1] > 0 && box[2] > 0;
     Grid g{};
     bool use_cells = false;
+    float margin = 0.f;  // the superset test's margin (cell path only)
     if (periodic && n > 2048) {
         // largest bounding radius decides the cell side
         double rbmax = rbmax_hint;
@@ -352,12 +406,23 @@ relcp_status broadphase(int64_t n, View<3, const double> x, const double* rb, do
             cell_assign<<<nb, kThreads, 0, s>>>(n, x, g, sc.cell_of.p, sc.cell_count.p);
             RELCP_CUDA(cudaGetLastError());
             RELCP_TRY(exclusive_scan(sc.cell_count.p, sc.cell_start.p, ncells, sc.scan, s));
+            if (superset) {
+                RELCP_TRY(sc.cell_xr.ensure((size_t)n, s));
+                margin = (float)(4e-6 * (fmax(box[0], fmax(box[1], box[2])) + 2.0 * rbmax + skin));
+            }
             note_launch();
-            cell_fill<<<nb, kThreads, 0, s>>>(n, sc.cell_of.p, sc.cell_start.p, sc.cell_cursor.p, sc.cell_body.p);
+            cell_fill<<<nb, kThreads, 0, s>>>(n, sc.cell_of.p, sc.cell_start.p, sc.cell_cursor.p, sc.cell_body.p, x, rb,
+                                              g, superset ? sc.cell_xr.p : nullptr);
             RELCP_CUDA(cudaGetLastError());
             note_launch();
-            cell_pairs<false><<<nb, kThreads, 0, s>>>(n, x, rb, g, skin, sc.cell_of.p, sc.cell_start.p,
-                                                       sc.cell_body.p, sc.pair_count.p, nullptr, nullptr, nullptr);
+            if (superset)
+                cell_pairs<false, true><<<nb, kThreads, 0, s>>>(n, x, rb, g, skin, sc.cell_of.p, sc.cell_start.p,
+                                                                sc.cell_body.p, sc.pair_count.p, nullptr, nullptr,
+                                                                nullptr, sc.cell_xr.p, margin);
+            else
+                cell_pairs<false, false><<<nb, kThreads, 0, s>>>(n, x, rb, g, skin, sc.cell_of.p, sc.cell_start.p,
+                                                                 sc.cell_body.p, sc.pair_count.p, nullptr, nullptr,
+                                                                 nullptr, nullptr, 0.f);
             RELCP_CUDA(cudaGetLastError());
         }
     }
@@ -380,8 +445,14 @@ relcp_status broadphase(int64_t n, View<3, const double> x, const double* rb, do
     RELCP_TRY(pb.ensure((size_t)total, s));
     if (use_cells) {
         note_launch();
-        cell_pairs<true><<<nb, kThreads, 0, s>>>(n, x, rb, g, skin, sc.cell_of.p, sc.cell_start.p, sc.cell_body.p,
-                                                  nullptr, sc.pair_off.p, pa.p, pb.p);
+        if (superset)
+            cell_pairs<true, true><<<nb, kThreads, 0, s>>>(n, x, rb, g, skin, sc.cell_of.p, sc.cell_start.p,
+                                                           sc.cell_body.p, nullptr, sc.pair_off.p, pa.p, pb.p,
+                                                           sc.cell_xr.p, margin);
+        else
+            cell_pairs<true, false><<<nb, kThreads, 0, s>>>(n, x, rb, g, skin, sc.cell_of.p, sc.cell_start.p,
+                                                            sc.cell_body.p, nullptr, sc.pair_off.p, pa.p, pb.p,
+                                                            nullptr, 0.f);
     } else {
         note_launch();
         brute_fill<<<nb, kThreads, 0, s>>>(n, x, rb, box[0], box[1], box[2], skin, sc.pair_off.p, pa.p, pb.p);
@@ -419,7 +490,7 @@ relcp_status broadphase_cached(int64_t n, const double* x_soa, const double* rb,
             std::swap(sc.memo, sc.memo_old);
             sc.delta = 0.15 * cutmax;
             int64_t nv = 0;
-            RELCP_TRY(broadphase(n, xv, rb, rbmax, box, skin + sc.delta, sc.vpa, sc.vpb, &nv, sc, s));
+            RELCP_TRY(broadphase(n, xv, rb, rbmax, box, skin + sc.delta, sc.vpa, sc.vpb, &nv, sc, s, true));
             sc.vn = nv;
             RELCP_TRY(sc.memo.ensure((size_t)(nv > 0 ? nv : 1), s));
             if (nv > 0) {

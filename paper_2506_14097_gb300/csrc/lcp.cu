@@ -29,7 +29,11 @@
 // On the mixed path, when every row has a thread of its own, the second grid
 // barrier goes too (scatter_1b): phase 1 of iteration k waits, by polling,
 // only for the records of the rows incident to its body, and the residual
-// test is folded one iteration late like the step length.
+// test is folded one iteration late like the step length.  There the FP64
+// residual is certified from FP32 arithmetic with a rounding-error bound and
+// evaluated in FP64 only for the rows within that bound of the tolerance
+// (resid_certified): the same stop decisions at a fraction of the FP64 issue
+// slots, which this part has few of.
 //
 // The grid barrier spins a bounded number of times; a timeout sets
 // DEV_TIMEOUT and the kernel returns.  Data written inside the launch is read
@@ -54,6 +58,7 @@ namespace {
 constexpr int kThreads = RELCP_LCP_THREADS;
 constexpr int kMaxCtasPerSm = 1;
 constexpr int kMixedCheckEvery = 2;  // mixed path: FP64 termination residual every 2nd iteration
+constexpr int kRefineWait = 8;       // one-barrier path: iterations past tol_a before the refinement
 
 __device__ __forceinline__ unsigned long long gtimer() {
     unsigned long long t;
@@ -121,6 +126,13 @@ struct KArgs {
     LcpDevResult* result;
     unsigned long long wait_ns;  // bound of every wait (grid barrier, row records)
     int skip_block;              // fault injection: the last block leaves before its first barrier arrival
+    // iterative refinement (one-barrier mixed path): the one-barrier
+    // iterations stop at tol_a (> tol when refinement is on), then an FP64
+    // residual with the FP64 operator K64 (offsets g64, per row) and an FP32
+    // correction solve to tol
+    double tol_a;
+    const double* K64[7];
+    double* g64;
 };
 
 __device__ __forceinline__ double ldcg(const double* p) { return __ldcg(p); }
@@ -286,7 +298,9 @@ __device__ __forceinline__ R bb_step(int it, R ss, R sy, R yy, R prev) {
 }
 
 // per-block partials of an iteration: the three BB products (sums in the
-// solve precision) and, on check iterations, the FP64 residual (a max).  Each
+// solve precision) and, on check iterations, the residual word resw (a max:
+// the bits of a non-negative double, or on the one-barrier path those of a
+// non-negative float in the low half; 0 otherwise).  Each
 // warp reduces its threads' values by shuffles; then warp 0 folds the warps'
 // values (all four slots at once) and writes the block's words, while warp 1
 // (when `prev` is given) folds the previous iteration's partials of all
@@ -294,16 +308,16 @@ __device__ __forceinline__ R bb_step(int it, R ss, R sy, R yy, R prev) {
 // Both folds run in a fixed order; the caller's next __syncthreads (the grid
 // barrier's) publishes *alpha to the block.
 template <class R>
-__device__ void block_partials(const R v[3], double res, bool with_res, unsigned long long* out,
-                               const unsigned long long* prev, int it, R* alpha, bool res_f32 = false,
-                               bool prev_res = false, unsigned* prev_res_max = nullptr) {
+__device__ void block_partials(const R v[3], unsigned long long resw, unsigned long long* out,
+                               const unsigned long long* prev, int it, R* alpha, bool prev_res = false,
+                               unsigned* prev_res_max = nullptr) {
     constexpr int kWarps = kThreads / 32;
     static_assert(kWarps <= 32, "one lane per warp in the fold");
     __shared__ R sh[kWarps][3];
     __shared__ unsigned long long shr[kWarps];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     R x[3] = {v[0], v[1], v[2]};
-    unsigned long long m = with_res ? (unsigned long long)__double_as_longlong(res) : 0ull;
+    unsigned long long m = resw;
     for (int o = 16; o > 0; o >>= 1) {
 #pragma unroll
         for (int k = 0; k < 3; ++k) x[k] += __shfl_down_sync(0xffffffffu, x[k], o);
@@ -327,10 +341,7 @@ __device__ void block_partials(const R v[3], double res, bool with_res, unsigned
         if (lane == 0) {
 #pragma unroll
             for (int k = 0; k < 3; ++k) out[k] = to_word(x[k]);
-            // (res_f32: the residual rounded up to FP32, its bits in the low
-            // half, so that a fold of the low halves sees it)
-            out[3] = res_f32 ? (unsigned long long)__float_as_uint(__double2float_ru(__longlong_as_double((long long)m)))
-                             : m;
+            out[3] = m;
         }
     } else if (wid == 2 && prev && prev_res) {
         // the previous iteration's residual (FP32 bits, rounded up): max over
@@ -789,29 +800,234 @@ __device__ void scatter_1b(const KArgs<float>& a, const BodySlot<float>& S, cons
     }
 }
 
+// A double that holds a widened float (the mixed rows' A_aa) back in FP32 by
+// integer operations (the FP64 units are scarce on this part): exact for a
+// widened normal float, the truncation of the mantissa (relative < 2^-23) for
+// any other normal value in the FP32 range; outside that range a conversion.
+__device__ __forceinline__ float narrow_f32(double d) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(d);
+    const int e = (int)((b >> 52) & 0x7ffull) - 1023 + 127;
+    if (e <= 0 || e >= 255) return (float)d;
+    return __uint_as_float(((unsigned)(b >> 32) & 0x80000000u) | ((unsigned)e << 23) |
+                           (unsigned)((b >> 29) & 0x7fffffull));
+}
+
+// The termination residual of one row, |min(A_aa gamma, q + c rate)| with q,
+// A_aa and c in FP64 and gamma and the rate as the FP32 iterate holds them
+// (the FP64 test), decided from FP32 arithmetic where FP32 suffices.  The FP32
+// value r32 = |min(A32 gamma, q32 + c32 rate)| (q32 the FP32 offset) differs
+// from the FP64 one by less than e = 2^-21 max(|q32| + |c32 rate|, A32 gamma)
+// (the roundings of q, c, A_aa, the product and the sum, each at most 2^-24 or
+// 2^-23 of its operands; min and abs are 1-Lipschitz).  The loop decides
+// against two thresholds, tol and tol_a >= tol (th: tol and tol_a rounded
+// down and up to FP32).  A row whose interval [r32 - e, r32 + e] lies below
+// tol contributes r32 + e; above tol_a, r32 - e; strictly between them,
+// r32 + e; only a row whose interval straddles a threshold evaluates the FP64
+// expression, rounded up to FP32.  The fold's max then decides "<= tol" and
+// "<= tol_a" exactly as the FP64 residuals rounded up to FP32 would, and
+// bounds the FP64 residual from above when it stops.
+__device__ __forceinline__ float resid_certified(const KArgs<float>& a, int r, float gm, float q32, float cr, float g,
+                                                 float rate, const float* th) {
+    const float p = narrow_f32(a.diag[r]) * gm;
+    const float r32 = fabsf(fminf(p, g));
+    const float e = 0x1p-21f * fmaxf(fabsf(q32) + fabsf(cr), p);
+    const float up = __fadd_ru(r32, e);
+    const float lo = __fsub_rd(r32, e);
+    if (up <= th[0]) return up;                       // below tol
+    if (lo > th[3]) return lo;                        // above tol_a
+    if (lo > th[1] && up <= th[2]) return up;         // in (tol, tol_a]
+    const double qd = a.q[r], dg = a.diag[r];
+    return __double2float_ru(fabs(fmin(dg * (double)gm, qd + a.c * (double)rate)));
+}
+
 // phase 2 of iteration it for the thread's row: g(it) from Uc(it), the record
-// of it, the BB products and (check) the FP64 residual
+// of it, the BB products and (check) the residual as FP32 bits (resid_certified)
 __device__ __forceinline__ void gather_1b(const KArgs<float>& a, RowSlot<float>& S, const float* ucp,
                                           unsigned long long* rec, unsigned phase, bool check, float alpha_r,
-                                          float v[3], double* resid) {
+                                          const float* tol_lohi, float v[3], unsigned* resid_bits) {
     float acc[3] = {0.f, 0.f, 0.f};
-    double res = 0.0;
+    float res = 0.f;
     if (S.r >= 0) {
         float ui[6], uj[6];
         load_rec(ucp + 8 * (int64_t)S.i, ui);
         load_rec(ucp + 8 * (int64_t)S.j, uj);
-        double qd = 0.0, dg = 0.0;
-        if (check) {
-            qd = a.q[S.r];
-            dg = a.diag[S.r];
-        }
         const float gm = proj_step(S.gm, S.gv, S.invd, alpha_r);
         const float rate = row_rate(S.g, ui, uj);
-        const float g = S.q + (float)a.c * rate;
+        const float cr = (float)a.c * rate;
+        const float g = S.q + cr;
         st_rel64(rec + S.r, make_rec(gm, g, phase));
         bb_accumulate(a, gm - S.gm, g - S.gv, S.invd, acc);
-        if (check) res = fmax(res, fabs(fmin(dg * (double)gm, qd + a.c * (double)rate)));
+        if (check) res = resid_certified(a, S.r, gm, S.q, cr, g, rate, tol_lohi);
         S.gm = gm;
+        S.gv = g;
+    }
+    v[0] = acc[0];
+    v[1] = acc[1];
+    v[2] = acc[2];
+    *resid_bits = __float_as_uint(res);
+}
+
+// ---------------------------------------------------------------------------
+// Iterative refinement of the one-barrier solve.  FP32 iterates stall where
+// the rounding of the wrench sums (relative 2^-24 of the summed contact
+// forces, which nearly cancel on a body in a dense packing) reaches the stop;
+// so the one-barrier iterations stop at tol_a, and then
+//   (1) the FP64 residual of that iterate gamma1 (held in gamma_io): per body
+//       U1 = K D gamma1 in FP64 (the rows' FP32 geometry widened, which is
+//       exact, and the FP64 operator), kept in the FP64 output ucd; per row
+//       g64 = q + c d^T (U1_j - U1_i) and |min(A_aa gamma1, g64)|;
+//   (2) if that residual is above tol: projected Barzilai-Borwein in FP32 on
+//       the correction delta >= -gamma1 of g = g64 + A delta, two grid
+//       barriers per iteration (the records hold delta, which has no free
+//       sign bit), the FP64 residual |min(A_aa (gamma1 + delta), g64 + c d^T
+//       K D delta)| every second iteration.  The rounding of these iterations
+//       scales with the correction, not with the forces;
+//   (3) gamma = gamma1 + delta and Uc = U1 + K D delta.
+// Mixed-precision iterative refinement (an FP64 residual, an FP32 solve of the
+// correction), applied to the complementarity problem.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float proj_step_lb(float gm, float g, float invd, float alpha, float lb) {
+    const float v = __fmaf_rn(-alpha, __fmul_rn(g, invd), gm);
+    return v > lb ? v : lb;
+}
+
+// (1a) U1 = K D gamma1 per body in FP64 into ucd (two lanes per body)
+__device__ void refine_scatter64(const KArgs<float>& a) {
+    const int lane = threadIdx.x & (kLanesPerBody - 1);
+    const int groups_total = (int)(gridDim.x * blockDim.x) / kLanesPerBody;
+    const int gid = (int)(blockIdx.x * blockDim.x + threadIdx.x) / kLanesPerBody;
+    const int warp_first = gid & ~(32 / kLanesPerBody - 1);
+    for (int k = 0; warp_first + k * groups_total < a.nbodies; ++k) {
+        const int b = gid + k * groups_total;
+        double w[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+        if (b < a.nbodies) {
+            const int e0 = a.inc_off[b], e1 = a.inc_off[b + 1];
+            for (int e = e0 + lane; e < e1; e += kLanesPerBody) {
+                const int code = a.inc[e];
+                const int r = code >> 1;
+                const double gm = (double)__ldcg(a.gamma_io + r);
+                const double sg = (code & 1) ? gm : -gm;
+                const int o = (code & 1) ? 6 : 3;
+                w[0] += sg * (double)a.geom[0][r];
+                w[1] += sg * (double)a.geom[1][r];
+                w[2] += sg * (double)a.geom[2][r];
+                w[3] += sg * (double)a.geom[o][r];
+                w[4] += sg * (double)a.geom[o + 1][r];
+                w[5] += sg * (double)a.geom[o + 2][r];
+            }
+        }
+        reduce_lanes(w);
+        if (b < a.nbodies && lane == 0) {
+            double K[7];
+#pragma unroll
+            for (int kk = 0; kk < 7; ++kk) K[kk] = a.K64[kk][b];
+            apply_K(K, w);
+#pragma unroll
+            for (int kk = 0; kk < 6; ++kk) a.ucd[kk][b] = w[kk];
+        }
+    }
+}
+
+// (1b) the thread's row: g64 and its FP64 residual; the row slot and the
+// record of buffer 0 become the correction problem's start (delta = 0, g = g64)
+__device__ double refine_row64(const KArgs<float>& a, RowSlot<float>& S) {
+    if (S.r < 0) return 0.0;
+    double ui[6], uj[6];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+        ui[k] = __ldcg(a.ucd[k] + S.i);
+        uj[k] = __ldcg(a.ucd[k] + S.j);
+    }
+    double rate = (double)S.g[0] * (uj[0] - ui[0]) + (double)S.g[1] * (uj[1] - ui[1]) +
+                  (double)S.g[2] * (uj[2] - ui[2]);
+    rate += (double)S.g[6] * uj[3] + (double)S.g[7] * uj[4] + (double)S.g[8] * uj[5];
+    rate -= (double)S.g[3] * ui[3] + (double)S.g[4] * ui[4] + (double)S.g[5] * ui[5];
+    const double g64 = a.q[S.r] + a.c * rate;
+    a.g64[S.r] = g64;
+    const double g1 = (double)__ldcg(a.gamma_io + S.r);
+    S.q = (float)g64;
+    S.gm = 0.f;
+    S.gv = S.q;
+    a.gg[0][S.r] = make_float2(0.f, S.q);
+    return fabs(fmin(a.diag[S.r] * g1, g64));
+}
+
+// (2) scatter: K D delta' with delta' = max(-gamma1, delta - alpha g / A_aa)
+// from the records gg[src] (every row has a row slot on this path)
+__device__ void refine_scatter(const KArgs<float>& a, const BodySlot<float>& S, int src, float alpha_r) {
+    const int lane = threadIdx.x & (kLanesPerBody - 1);
+    auto inc = [&](int code, const float c[6], float w[6]) {
+        const int r = code >> 1;
+        const float2 p = __ldcg(a.gg[src] + r);
+        const float inv = a.invd ? a.invd[r] : 1.f;
+        const float dl = proj_step_lb(p.x, p.y, inv, alpha_r, -__ldcg(a.gamma_io + r));
+#pragma unroll
+        for (int k = 0; k < 6; ++k) w[k] += dl * c[k];
+    };
+    {
+        float w[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+        for (int k = 0; k < kIncPerLane; ++k)
+            if (S.code[k] >= 0) inc(S.code[k], S.c[k], w);
+        const int e_over = S.e0 + kLanesPerBody * kIncPerLane + lane;
+        if (e_over < S.e1) {
+            float K[7];
+            load_K(a, S.b, K);
+            for (int e = e_over; e < S.e1; e += kLanesPerBody) {
+                const int code = a.inc[e];
+                float c[6];
+                load_coefs(a, code, c);
+                apply_K(K, c);
+                inc(code, c, w);
+            }
+        }
+        reduce_lanes(w);
+        if (S.b < a.nbodies && lane == 0) store_rec(a.ucp + 8 * (int64_t)S.b, w);
+    }
+    const int nslots = gridDim.x * blockDim.x;
+    const int groups_total = nslots / kLanesPerBody;
+    const int gid = (blockIdx.x * blockDim.x + threadIdx.x) / kLanesPerBody;
+    const int warp_first = gid & ~(32 / kLanesPerBody - 1);
+    for (int k = 1; warp_first + k * groups_total < a.nbodies; ++k) {
+        const int b = gid + k * groups_total;
+        float w[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        if (b < a.nbodies) {
+            float K[7];
+            load_K(a, b, K);
+            const int e0 = a.inc_off[b], e1 = a.inc_off[b + 1];
+            for (int e = e0 + lane; e < e1; e += kLanesPerBody) {
+                const int code = a.inc[e];
+                float c[6];
+                load_coefs(a, code, c);
+                apply_K(K, c);
+                inc(code, c, w);
+            }
+        }
+        reduce_lanes(w);
+        if (b < a.nbodies && lane == 0) store_rec(a.ucp + 8 * (int64_t)b, w);
+    }
+}
+
+// (2) gather for the thread's row: the same projected step, g = g64 + c d^T
+// K D delta', the record of buffer nw, the BB products and (check) the FP64
+// residual of gamma1 + delta'
+__device__ __forceinline__ void refine_gather(const KArgs<float>& a, RowSlot<float>& S, int nw, bool check,
+                                              float alpha_r, float v[3], double* resid) {
+    float acc[3] = {0.f, 0.f, 0.f};
+    double res = 0.0;
+    if (S.r >= 0) {
+        float ui[6], uj[6];
+        load_rec(a.ucp + 8 * (int64_t)S.i, ui);
+        load_rec(a.ucp + 8 * (int64_t)S.j, uj);
+        const float g1 = __ldcg(a.gamma_io + S.r);
+        const float dl = proj_step_lb(S.gm, S.gv, S.invd, alpha_r, -g1);
+        const float rate = row_rate(S.g, ui, uj);
+        const float g = S.q + (float)a.c * rate;
+        a.gg[nw][S.r] = make_float2(dl, g);
+        bb_accumulate(a, dl - S.gm, g - S.gv, S.invd, acc);
+        if (check)
+            res = fabs(fmin(a.diag[S.r] * ((double)g1 + (double)dl), a.g64[S.r] + a.c * (double)rate));
+        S.gm = dl;
         S.gv = g;
     }
     v[0] = acc[0];
@@ -877,7 +1093,7 @@ __global__ void __launch_bounds__(kThreads) lcp_kernel(KArgs<R> a) {
     // and broadcast through shared memory, so FP64 scalar work is not repeated
     // by every thread
     __shared__ double sh_resid;
-    __shared__ R sh_alpha_r;
+    __shared__ R sh_alpha_r, sh_alpha0;
     __shared__ int sh_stop;
     double resid = 0.0;
     if (threadIdx.x == 0) {
@@ -885,6 +1101,7 @@ __global__ void __launch_bounds__(kThreads) lcp_kernel(KArgs<R> a) {
         const double md = from_word<double>(tot[0]);
         const double alpha = a.invd ? 1.0 : (md > 0.0 ? 1.0 / md : 1.0);
         sh_alpha_r = (R)alpha;
+        sh_alpha0 = (R)alpha;
         sh_resid = resid;
         sh_stop = resid <= a.tol;
     }
@@ -893,16 +1110,27 @@ __global__ void __launch_bounds__(kThreads) lcp_kernel(KArgs<R> a) {
     int cur = 0, it = 0;
     if constexpr (sizeof(R) == sizeof(float)) {
         if (one_bar) {
-            // ---- one grid barrier per iteration (see scatter_1b)
+            // ---- one grid barrier per iteration (see scatter_1b), to tol, or
+            // to tol_a and kRefineWait iterations more before the refinement
             int fin = 0;  // the iterate returned
-            if (!sh_stop) {
+            __shared__ float sh_tol[4];  // tol and tol_a, each rounded down and up to FP32
+            constexpr size_t kBuf = (size_t)kMaxBlocks * kNred;
+            __shared__ unsigned long long pbuf1[kMaxBlocks * kNred];
+            if (threadIdx.x == 0) {
+                sh_tol[0] = __double2float_rd(a.tol);
+                sh_tol[1] = __double2float_ru(a.tol);
+                sh_tol[2] = __double2float_rd(a.tol_a);
+                sh_tol[3] = __double2float_ru(a.tol_a);
+            }
+            __syncthreads();
+            resid = sh_resid;
+            if (!(resid <= a.tol)) {
 #ifdef RELCP_LCP_TRACE
                 unsigned long long t_prev = gtimer();
 #endif
-                constexpr size_t kBuf = (size_t)kMaxBlocks * kNred;
-                __shared__ unsigned long long pbuf1[kMaxBlocks * kNred];
                 __shared__ unsigned sh_rmax;
                 fin = -1;
+                int it_a = resid <= a.tol_a ? 0 : -1;  // the first iterate at or below tol_a
                 for (it = 1; it <= a.max_iter; ++it) {
                     const bool check = (it % a.check_every) == 0 || it == a.max_iter;
                     const bool prev_check = it >= 2 && ((it - 1) % a.check_every) == 0;
@@ -921,16 +1149,17 @@ __global__ void __launch_bounds__(kThreads) lcp_kernel(KArgs<R> a) {
                     if (it >= 2 && (int)threadIdx.x < npw)
                         pf = __ldcg(reinterpret_cast<const unsigned*>(a.partials + (size_t)((it - 1) & 1) * kBuf +
                                                                       threadIdx.x));
+                    unsigned rbits;
                     gather_1b(a, rs, uc_it, reinterpret_cast<unsigned long long*>(a.gg[it & 1]), rec_phase(it), check,
-                              alpha_r, v, &res_t);
+                              alpha_r, sh_tol, v, &rbits);
                     TRACE_MARK(2);
                     if (it >= 2) {
                         if ((int)threadIdx.x < npw) pbuf1[threadIdx.x] = pf;
                         for (int t = threadIdx.x + kThreads; t < npw; t += kThreads)
                             pbuf1[t] = (unsigned)__ldcg(a.partials + (size_t)((it - 1) & 1) * kBuf + t);
                     }
-                    block_partials<R>(v, res_t, check, part + (size_t)blockIdx.x * kNred, it >= 2 ? pbuf1 : nullptr,
-                                      it, &sh_alpha_r, true, prev_check, &sh_rmax);
+                    block_partials<R>(v, check ? (unsigned long long)rbits : 0ull, part + (size_t)blockIdx.x * kNred,
+                                      it >= 2 ? pbuf1 : nullptr, it, &sh_alpha_r, prev_check, &sh_rmax);
                     __syncthreads();
                     alpha_r = sh_alpha_r;
                     TRACE_MARK(3);
@@ -938,9 +1167,14 @@ __global__ void __launch_bounds__(kThreads) lcp_kernel(KArgs<R> a) {
                     if (blockIdx.x == 0 && threadIdx.x == 0) g_lcp_trace[6] += 1;
 #endif
                     if (prev_check) {
-                        // every block folds the same words: the same decision
+                        // every block folds the same words: the same decision.
+                        // Below tol_a the iterations go on towards tol for up to
+                        // kRefineWait more; only a solve still above tol then is
+                        // refined (a light solve usually gets there first, and
+                        // the refinement's FP64 pass would cost it more)
                         const double rsd = (double)__uint_as_float(sh_rmax);
-                        if (rsd <= a.tol) {
+                        if (rsd <= a.tol_a && it_a < 0) it_a = it - 1;
+                        if (rsd <= a.tol || (it_a >= 0 && it - 1 >= it_a + kRefineWait)) {
                             resid = rsd;
                             fin = it - 1;
                             break;
@@ -962,10 +1196,7 @@ __global__ void __launch_bounds__(kThreads) lcp_kernel(KArgs<R> a) {
                     __syncthreads();
                     resid = (double)__uint_as_float(sh_rmax);
                 }
-            } else {
-                resid = sh_resid;
             }
-            pdl_trigger();  // the next kernel in the stream may start launching
             // outputs: gamma and the contact velocity of the returned iterate
             // (its record buffer and velocity buffer are intact: iteration
             // fin + 1 wrote the other ones)
@@ -978,6 +1209,79 @@ __global__ void __launch_bounds__(kThreads) lcp_kernel(KArgs<R> a) {
 #pragma unroll
                 for (int k = 0; k < 6; ++k) a.ucd[k][b] = (double)u[k];
             }
+            if (a.tol_a > a.tol && !(resid <= a.tol)) {
+                // ---- iterative refinement (see refine_scatter64): the FP64
+                // residual of gamma1 = the iterate just written
+                if (!grid_barrier(a.bar, &epoch, a.status, a.wait_ns)) return;
+                refine_scatter64(a);
+                if (!grid_barrier(a.bar, &epoch, a.status, a.wait_ns)) return;
+                {
+                    const double r64 = refine_row64(a, rs);
+                    double w4[kNred] = {0.0, 0.0, 0.0, r64};
+                    block_reduce_store<double>(w4, 0x8u, part);
+                    if (threadIdx.x == 0) {
+                        unsigned long long* o = a.partials + (size_t)blockIdx.x * kNred;
+                        o[0] = to_word(R(0));
+                        o[1] = to_word(R(0));
+                        o[2] = to_word(R(0));
+                        o[3] = to_word(part[3]);
+                    }
+                }
+                if (!grid_barrier(a.bar, &epoch, a.status, a.wait_ns)) return;
+                grid_reduce<R>(a.partials, 0x8u, tot);
+                resid = from_word<double>(tot[3]);
+                if (!(resid <= a.tol)) {
+                    // the correction solve, two grid barriers per iteration;
+                    // buffer 0 holds its start (delta = 0, g = g64)
+                    alpha_r = sh_alpha0;
+                    cur = 0;
+                    int itc;
+                    for (itc = 1; itc <= a.max_iter; ++itc) {
+                        const bool check = (itc % kMixedCheckEvery) == 0 || itc == a.max_iter;
+                        unsigned long long* pc = a.partials + (size_t)(itc & 1) * kBuf;
+                        refine_scatter(a, bs, cur, alpha_r);
+                        if (!grid_barrier(a.bar, &epoch, a.status, a.wait_ns)) return;
+                        const int npw = (int)gridDim.x * kNred;
+                        unsigned pf = 0u;
+                        if (itc >= 2 && (int)threadIdx.x < npw)
+                            pf = __ldcg(reinterpret_cast<const unsigned*>(a.partials + (size_t)((itc - 1) & 1) * kBuf +
+                                                                          threadIdx.x));
+                        refine_gather(a, rs, 1 - cur, check, alpha_r, v, &res_t);
+                        if (itc >= 2) {
+                            if ((int)threadIdx.x < npw) pbuf1[threadIdx.x] = pf;
+                            for (int t = threadIdx.x + kThreads; t < npw; t += kThreads)
+                                pbuf1[t] = (unsigned)__ldcg(a.partials + (size_t)((itc - 1) & 1) * kBuf + t);
+                        }
+                        block_partials<R>(v, check ? (unsigned long long)__double_as_longlong(res_t) : 0ull,
+                                          pc + (size_t)blockIdx.x * kNred, itc >= 2 ? pbuf1 : nullptr, itc, &sh_alpha_r);
+                        if (!grid_barrier(a.bar, &epoch, a.status, a.wait_ns)) return;
+                        cur = 1 - cur;
+                        alpha_r = sh_alpha_r;
+                        if (check) {
+                            grid_reduce<R>(pc, 0x8u, tot);
+                            if (threadIdx.x == 0) {
+                                sh_resid = from_word<double>(tot[3]);
+                                sh_stop = sh_resid <= a.tol;
+                            }
+                            __syncthreads();
+                            if (sh_stop) break;
+                        }
+                    }
+                    if (itc > a.max_iter) itc = a.max_iter;
+                    it += itc;
+                    resid = sh_resid;
+                    // gamma = gamma1 + delta (buffer cur), Uc = U1 + K D delta
+                    for (int r = tid; r < nrows; r += stride)
+                        a.gamma_io[r] = __ldcg(a.gamma_io + r) + __ldcg(&a.gg[cur][r].x);
+                    for (int b = tid; b < a.nbodies; b += stride) {
+                        R u[6];
+                        load_rec(a.ucp + 8 * (int64_t)b, u);
+#pragma unroll
+                        for (int k = 0; k < 6; ++k) a.ucd[k][b] = __ldcg(a.ucd[k] + b) + (double)u[k];
+                    }
+                }
+            }
+            pdl_trigger();  // the next kernel in the stream may start launching
             if (blockIdx.x == 0 && threadIdx.x == 0) {
                 a.result->iterations = (double)it;
                 a.result->residual = resid;
@@ -1019,8 +1323,9 @@ __global__ void __launch_bounds__(kThreads) lcp_kernel(KArgs<R> a) {
                 for (int t = threadIdx.x + kThreads; t < npw; t += kThreads)
                     pbuf[t] = __ldcg(a.partials + (size_t)((it - 1) & 1) * kBuf + t);
             }
-            block_partials<R>(v, res_t, check, part + (size_t)blockIdx.x * kNred,
-                              (kRetard && it >= 2) ? pbuf : nullptr, it, &sh_alpha_r);
+            block_partials<R>(v, check ? (unsigned long long)__double_as_longlong(res_t) : 0ull,
+                              part + (size_t)blockIdx.x * kNred, (kRetard && it >= 2) ? pbuf : nullptr, it,
+                              &sh_alpha_r);
             TRACE_MARK(3);
             if (!grid_barrier(a.bar, &epoch, a.status, a.wait_ns)) return;
             TRACE_MARK(4);
@@ -1198,6 +1503,13 @@ relcp_status solve_typed(const LcpProblem& pr, LcpScratch& sc, DBuf<R>& pack, in
     ka.result = pr.result;
     ka.wait_ns = pr.wait_ns ? pr.wait_ns : kLcpWaitNs;
     ka.skip_block = pr.fault_skip_block;
+    ka.tol_a = pr.tol;
+    if (sizeof(R) == sizeof(float) && pr.refine) {
+        RELCP_TRY(sc.g64.ensure((size_t)mc, s));
+        ka.tol_a = kRefineFactor * pr.tol;
+        ka.g64 = sc.g64.p;
+        for (int k = 0; k < 7; ++k) ka.K64[k] = pr.K[k];
+    }
     int64_t work = pr.m_cap > kLanesPerBody * nb ? pr.m_cap : kLanesPerBody * nb;
     (void)kernel_ms;
     return launch_lcp(ka, work, sc, s, blocks, pr.ev_before, pr.ev_after);
@@ -1225,8 +1537,12 @@ relcp_status lcp_reserve(LcpScratch& sc, int64_t m_cap, int64_t nb, bool mixed, 
     RELCP_TRY(sc.inc_tmp.ensure((size_t)(2 * mc), s));
     RELCP_TRY(sc.inc.ensure((size_t)(2 * mc), s));
     const size_t pack = (size_t)(2 * mc) * 2 + (size_t)((mixed ? 16 : 8) * nba);
-    if (mixed) RELCP_TRY(sc.packf.ensure(pack, s));
-    else RELCP_TRY(sc.packd.ensure(pack, s));
+    if (mixed) {
+        RELCP_TRY(sc.packf.ensure(pack, s));
+        RELCP_TRY(sc.g64.ensure((size_t)mc, s));
+    } else {
+        RELCP_TRY(sc.packd.ensure(pack, s));
+    }
     RELCP_TRY(sc.partials.ensure((size_t)2 * kMaxBlocks * kNred, s));
     RELCP_TRY(scan_reserve(sc.scan, nba, s));
     return RELCP_OK;
@@ -1281,6 +1597,7 @@ void release(LcpScratch& sc, cudaStream_t s) {
     sc.inc.release(s);
     sc.packd.release(s);
     sc.packf.release(s);
+    sc.g64.release(s);
     sc.partials.release(s);
     release(sc.scan, s);
 }

@@ -252,6 +252,7 @@ struct PairMemo {
 
 struct BroadphaseScratch {
     DBuf<int> cell_of, cell_count, cell_start, cell_cursor, cell_body, pair_count, pair_off;
+    DBuf<float4> cell_xr;  // FP32 wrapped positions and radii in cell order (superset test)
     ScanScratch scan;
     // Verlet candidate list (context use): pairs within R_i + R_j + skin + delta
     // at the build positions xb in the build box Lb, sorted by (i, j)
@@ -271,9 +272,11 @@ struct BroadphaseScratch {
 // Pairs of the bodies whose positions are given by x (any view) and bounding
 // radii rb.  Writes pa/pb (grown as needed), *npairs (host; synchronises s).
 // rbmax: the largest rb if known (> 0), else it is reduced on the device.
+// superset: a list that may also hold pairs up to a small margin beyond the
+// cutoff (FP32 test; cell-list path only), for the cached list's rebuild.
 relcp_status broadphase(int64_t n, View<3, const double> x, const double* rb, double rbmax, const double box[3],
                         double skin, DBuf<int>& pa, DBuf<int>& pb, int64_t* npairs, BroadphaseScratch& sc,
-                        cudaStream_t s);
+                        cudaStream_t s, bool superset = false);
 // The same pair list through a cached Verlet list (x in SoA layout, n bodies,
 // rbmax known).  Rebuilds the cache when the displacement bound requires it;
 // sc.pv maps each pair to its list entry, sc.memo is indexed by entry.
@@ -360,6 +363,7 @@ struct LcpScratch {
     DBuf<int> inc_off, inc_tmp, inc;
     DBuf<double> packd;              // FP64: packed (gamma, g) pairs x 2 buffers + contact-velocity records
     DBuf<float> packf;               // mixed: the same in FP32
+    DBuf<double> g64;                // mixed: the FP64 offsets of the refinement's correction problem
     DBuf<double> partials;
     ScanScratch scan;
 };
@@ -395,7 +399,11 @@ struct LcpProblem {
     // (0: kLcpWaitNs) and sets DEV_TIMEOUT
     unsigned long long wait_ns;
     int fault_skip_block;        // fault injection: the last block leaves before its first barrier arrival
+    // mixed path: iterative refinement (FP32 iterations to kRefineFactor x tol,
+    // an FP64 residual, an FP32 correction solve to tol); 0 turns it off
+    int refine = 1;
 };
+constexpr double kRefineFactor = 10.0;
 constexpr unsigned long long kLcpWaitNs = 2000000000ull;  // 2 s
 constexpr unsigned long long kFaultWaitNs = 2000000ull;   // 2 ms (RELCP_FAULT_LCP_TIMEOUT)
 // lcp_solve in two parts: the body incidence CSR of the rows, then the

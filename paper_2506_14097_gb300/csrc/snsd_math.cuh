@@ -102,10 +102,12 @@ __device__ void cold_start(const T* d, const Sym3<T>& Pa, const Sym3<T>& Pb, T* 
 
 // Newton ascent of G on the unit sphere from n (updated in place).
 // Returns the iteration count when the tangent gradient falls to tol, or
-// -(count+1) otherwise.  *Gout = G at the returned n.
+// -(count+1) otherwise.  *Gout = G at the returned n.  tol_mult scales the
+// stop (0: take maxit steps whatever the gradient).
 template <class T>
-__device__ int newton_sphere(T* n, const T* d, const Sym3<T>& Pa, const Sym3<T>& Pb, T scale, int maxit, T* Gout) {
-    const T tol = Tol<T>::grad * scale;
+__device__ int newton_sphere(T* n, const T* d, const Sym3<T>& Pa, const Sym3<T>& Pb, T scale, int maxit, T* Gout,
+                             T tol_mult = T(1)) {
+    const T tol = Tol<T>::grad * scale * tol_mult;
     const T gfloor = Tol<T>::drop * scale;
     const T kappa = Tol<T>::kappa * scale;
     T G = 0;
@@ -220,6 +222,11 @@ __device__ __forceinline__ void snsd_pair(const double d[3], const Sym3<double>&
         float Gf;
         int rf = newton_sphere(nf, df, Pfa, Pfb, scalef, cap32, &Gf);
         iters = rf >= 0 ? rf : -rf;
+        // one more FP32 Newton step past the stop: the stop leaves the normal
+        // within ~2e-6 (1 + |d|) / |H| of the maximiser, one step takes it to
+        // the FP32 rounding level (~1e-7), and the rows built from it (normal,
+        // lever arms) perturb the LCP that much less
+        if (rf >= 0) newton_sphere(nf, df, Pfa, Pfb, scalef, 1, &Gf, 0.f);
         n[0] = nf[0];
         n[1] = nf[1];
         n[2] = nf[2];

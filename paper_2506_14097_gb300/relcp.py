@@ -42,6 +42,7 @@ RELCP_FLAG_LCP_TIMING = 16
 RELCP_FLAG_GRAPH = 32
 RELCP_FLAG_HOST_STAGING = 64
 RELCP_FLAG_LEARNED_ALWAYS = 128
+RELCP_FLAG_NO_LCP_REFINE = 256
 MAX_DEPTH_STATS = 64
 
 
@@ -212,9 +213,20 @@ def make_config(dynamics=RELCP_INERTIAL, precision=RELCP_FP64, guess=RELCP_GUESS
                 box=(0.0, 0.0, 0.0), skin=0.05, phi_skin=None, drag_xi=1.0, density=1.0, strain_rate=0.0,
                 lcp_tol=None, lcp_max_iter=20000, max_recursion=64, seed=0, fault_inject=0, flags=0, length_scale=None,
                 shape=RELCP_SHAPE_ELLIPSOID):
-    """A relcp_config.  lcp_tol defaults to 1e-12 (FP64) or 1e-7 (mixed) times
-    `length_scale` (default: eps_ncp / 1e-3, i.e. the smallest semi-axis when
-    eps_ncp = 1e-3 x a_min)."""
+    """A relcp_config.  lcp_tol defaults to `length_scale` (default:
+    eps_ncp / 1e-3, i.e. the smallest semi-axis when eps_ncp = 1e-3 x a_min)
+    times 1e-12 on the FP64 path; on the mixed path times 1e-8 for the
+    overdamped laws and 1e-7 for inertial dynamics.  Those are the stops at
+    which each path's step meets its error bound against the exact LCP
+    solution (relative 1e-9 and 1e-5): the error of a stopped
+    projected-gradient iterate follows the stop, not the arithmetic, and in an
+    overdamped compaction the contact velocity is the whole non-affine motion
+    (a stop of 1e-7 a_min leaves up to 4e-5 there, in FP64 as in FP32).  Under
+    inertia the velocity is mostly free motion, 1e-7 a_min meets the bound, and
+    FP32 iterates cannot resolve 1e-8 a_min when the bodies move far per step
+    (the solve stalls at its rounding floor and reports NOT_CONVERGED); an
+    overdamped step with a large strain per step stalls the same way and needs
+    an explicit lcp_tol."""
     c = relcp_config()
     c.dynamics, c.precision, c.guess = dynamics, precision, guess
     c.lcp_max_iter, c.max_recursion, c.n_scenes = lcp_max_iter, max_recursion, 1
@@ -225,7 +237,7 @@ def make_config(dynamics=RELCP_INERTIAL, precision=RELCP_FP64, guess=RELCP_GUESS
     c.phi_skin = skin if phi_skin is None else phi_skin
     c.drag_xi, c.density, c.strain_rate = drag_xi, density, strain_rate
     scale = (eps_ncp / 1e-3) if length_scale is None else length_scale
-    c.lcp_tol = lcp_tol if lcp_tol is not None else (1e-12 if precision == RELCP_FP64 else 1e-7) * scale
+    c.lcp_tol = lcp_tol if lcp_tol is not None else (1e-12 if precision == RELCP_FP64 else (1e-7 if dynamics == RELCP_INERTIAL else 1e-8)) * scale
     c.seed, c.fault_inject, c.flags = seed, fault_inject, flags
     c.shape, c.reserved = shape, 0
     return c

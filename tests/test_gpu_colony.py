@@ -5,8 +5,8 @@ and as spherocylinders (the paper's cells):
 * from the oracle's own colony states (grown through six generations to 64+
   cells, divisions every few steps) each GPU step equals the oracle's step:
   candidate pairs and constraint ids bit for bit, velocities to relative 1e-9
-  (FP64) or 5e-5 (mixed, cold and learned start: the cells' small relative
-  motions put the FP32 iterates' floor closer to the velocities), positions in
+  (FP64) or 1e-5 (mixed, cold and learned start, with the LCP stop at 5e-9,
+  which the mixed path reaches by its iterative refinement), positions in
   the plane and rotations about z exactly;
 * a colony driven by the GPU's own results keeps every accepted overlap within
   eps_NCP and stays planar.
@@ -29,17 +29,15 @@ def rel_err(a, b):
 def gpu_cfg(R, precision, guess=None, shape=0):
     # the learned start on every evaluation (a colony this small never
     # reaches the 4,096 pairs at which it runs by default).  The cells move
-    # about 1e-4 per step, so the LCP residual is bounded below the default
-    # 1e-7 a_min that suits the compaction's larger motions: 5e-13 on the FP64
-    # path, 5e-8 on the mixed path.  There the FP32 iterates stall at a few
-    # times 1e-9: the rate d^T (U_b - U_a) is a difference of FP32 contact
-    # velocities that grow with the distance from the colony's centre while
-    # neighbours move nearly together, so the mixed path's velocities are
-    # within relative 5e-5 here (1e-5 on the compaction, whose contact
-    # velocities are local)
+    # about 1e-4 per step, so the LCP residual is bounded well below the
+    # compaction's stops: 5e-13 on the FP64 path, 5e-9 on the mixed path.
+    # Plain FP32 iterates stall at a few times 1e-9 here (the rate
+    # d^T (U_b - U_a) is a difference of contact velocities that grow with the
+    # distance from the colony's centre while neighbours move nearly
+    # together); the refined mixed solve reaches 5e-9 and the mixed bound 1e-5
     return R.make_config(dynamics=R.RELCP_OVERDAMPED_2D, precision=precision, dt=DT, eps_ncp=EPS, box=(0, 0, 0),
                          skin=SKIN, flags=R.RELCP_FLAG_LEARNED_ALWAYS,
-                         lcp_tol=5e-13 if precision == R.RELCP_FP64 else 5e-8, shape=shape,
+                         lcp_tol=5e-13 if precision == R.RELCP_FP64 else 5e-9, shape=shape,
                          guess=R.RELCP_GUESS_COLD if guess is None else guess)
 
 
@@ -64,7 +62,7 @@ def test_colony_steps_match_oracle(relcp_gpu, orc, colony64):
     R = relcp_gpu
     col, ocfg = colony64
     params = learned.init_params(seed=4)
-    arms = [(R.RELCP_FP64, None, 1e-9), (R.RELCP_MIXED, None, 5e-5), (R.RELCP_MIXED, R.RELCP_GUESS_MLP, 5e-5)]
+    arms = [(R.RELCP_FP64, None, 1e-9), (R.RELCP_MIXED, None, 1e-5), (R.RELCP_MIXED, R.RELCP_GUESS_MLP, 1e-5)]
     divisions0, rows = col.divisions, 0
     for k in range(40):
         x, q, axes = col.x.copy(), col.q(), col.axes()

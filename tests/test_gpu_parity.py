@@ -373,8 +373,11 @@ def test_cached_pair_list_bitexact_32k(relcp_gpu, orc):
     R = relcp_gpu
     sc = scenes.suspension_scene(seed=23, n=32768, phi=0.1, phi_final=0.45, steps=60, dt=5e-3)
     amin = float(sc.axes.min())
+    # (a strain of 1% per step: FP32 iterates stall above the overdamped
+    # default stop of 1e-8 a_min; the pairs, not the LCP, are tested here)
     cfg = R.make_config(dynamics=R.RELCP_OVERDAMPED, precision=R.RELCP_MIXED, dt=sc.dt, eps_ncp=1e-3 * amin,
-                        box=tuple(sc.box), skin=0.1 * amin, strain_rate=sc.meta["strain_rate"], length_scale=amin)
+                        box=tuple(sc.box), skin=0.1 * amin, strain_rate=sc.meta["strain_rate"], length_scale=amin,
+                        lcp_tol=1e-7 * amin)
     sim = R.Simulation(cfg)
     sim.set_bodies(sc.x, sc.q, sc.axes)
     sim.step(57, allow=(R.RELCP_ERR_NOT_CONVERGED,))
@@ -756,7 +759,7 @@ def test_host_roundtrip_keeps_carried_state(relcp_gpu, staging):
     b.close()
 
 
-@pytest.mark.parametrize("precision,bound,tol", [(0, 1e-9, None), (1, 1e-4, 3e-7)])
+@pytest.mark.parametrize("precision,bound,tol", [(0, 1e-9, None), (1, 1e-5, 1e-8)])
 def test_step_parity_spherocylinders(relcp_gpu, orc, precision, bound, tol):
     """Spherocylinders (the colony cells of Sec. 5.4) in a periodic box, pulled
     towards the box centre by a linear force (overdamped): one step from the
@@ -764,10 +767,10 @@ def test_step_parity_spherocylinders(relcp_gpu, orc, precision, bound, tol):
     oracle's trajectory (the recursion reaches depth 6), with pairs and
     constraint ids bit for bit.  Rows appended to pairs of flat-sided bodies
     nearly repeat earlier rows, so the LCP is close to singular: the FP64 path
-    needs up to ~6x10^4 projected-gradient iterations, and the mixed path's
-    FP32 iterates stall near a residual of 1e-7 (the pull towards the centre
-    makes the contact velocities large against their differences), hence its
-    looser residual 3e-7 and velocity bound 1e-4 here."""
+    needs up to ~6x10^4 projected-gradient iterations, and plain FP32 iterates
+    stall near a residual of 1e-7 (the pull towards the centre makes the
+    contact velocities large against their differences); the mixed path's
+    iterative refinement reaches a stop of 1e-8 and the mixed bound 1e-5."""
     R = relcp_gpu
     rng = np.random.default_rng(61)
     n, side = 80, 11.0
