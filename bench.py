@@ -389,6 +389,60 @@ def learned_fresh_state(R, torch, sc, mlp_params, flush, stream, at_step=1500, r
     return out
 
 
+def augmentation_at_scale(R, torch, sc, flush, stream, at_step=1990, factors=(1, 20), reps=3):
+    """The recursion on the full-size workload: the schedule's dense state
+    after `at_step` steps (volume fraction ~0.55) stepped once with the time
+    step scaled by each of `factors` (the strain rate unchanged, so the box
+    compacts that many steps' worth in one), on fresh contexts, on both
+    precision paths: step time (CUDA events, L2 flushed before; median of
+    `reps`), recursion depth, rows and LCP iterations per recursion level,
+    accepted overlap against eps_NCP and the step status.  At the schedule's
+    own time step no row is appended; a step 20 times longer appends rows at
+    every level the overlap test finds violated."""
+    sim = R.Simulation(make_cfg(R, sc, R.RELCP_MIXED, R.RELCP_GUESS_COLD, timing=None), stream.cuda_stream)
+    sim.set_bodies(sc.x, sc.q, sc.axes)
+    sim.step(at_step, allow=(R.RELCP_ERR_NOT_CONVERGED,))
+    x, q, _ = sim.bodies()
+    box = R.relcp_get_box(sim.ctx)
+    sim.close()
+    eps = 1e-3 * float(sc.axes.min())
+    out = {"state": f"compaction state after {at_step} steps, phi {sc.meta['volume'] / float(np.prod(box)):.3f}",
+           "eps_ncp": eps, "runs": []}
+    for factor in factors:
+        for name, prec in (("mixed", R.RELCP_MIXED), ("fp64", R.RELCP_FP64)):
+            times, st_last, status = [], None, set()
+            for _ in range(reps):
+                cfg = make_cfg(R, sc, prec, R.RELCP_GUESS_COLD, timing=None)
+                cfg.dt = factor * sc.dt
+                for k in range(3):
+                    cfg.box[k] = float(box[k])
+                sim = R.Simulation(cfg, stream.cuda_stream)
+                sim.set_bodies(x, q, sc.axes)
+                with torch.cuda.stream(stream):
+                    flush.zero_()
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    st = sim.step(1, allow=(R.RELCP_ERR_NOT_CONVERGED, R.RELCP_ERR_RECURSION_LIMIT))
+                    e1.record(stream)
+                torch.cuda.synchronize()
+                times.append(e0.elapsed_time(e1))
+                status.add(R.STATUS_NAMES[st])
+                st_last = sim.stats()
+                sim.close()
+            d = int(st_last.depth)
+            levels = min(d + 1, len(st_last.rows_per_rec))
+            out["runs"].append({"dt_factor": factor, "path": name, "ms_step_median": float(np.median(times)),
+                                "depth": d, "rows_per_level": [int(v) for v in st_last.rows_per_rec[:levels]],
+                                "lcp_iters_per_level": [int(v) for v in st_last.lcp_iters[:levels]],
+                                "max_overlap": float(st_last.max_overlap),
+                                "max_overlap_within_eps": bool(st_last.max_overlap <= eps),
+                                "status": sorted(status)})
+    for factor in factors:
+        r = {x_["path"]: x_ for x_ in out["runs"] if x_["dt_factor"] == factor}
+        out[f"speedup_vs_fp64_dt_x{factor}"] = r["fp64"]["ms_step_median"] / r["mixed"]["ms_step_median"]
+    return out
+
+
 # ---------------------------------------------------------------------------
 # CPU oracle (baseline leg, subset errors and reference arm)
 # ---------------------------------------------------------------------------
@@ -603,6 +657,9 @@ def main():
     ap.add_argument("--batched-steps", type=int, default=100)
     ap.add_argument("--batched-threads", type=int, default=0,
                     help="fixed block size of the batched kernel (0: autotuned)")
+    ap.add_argument("--augmentation", type=int, default=1,
+                    help="1: the recursion on the dense 32k state with a 20x time step, both paths")
+    ap.add_argument("--only-augmentation", action="store_true", help="only the recursion on the dense 32k state")
     ap.add_argument("--colony-cells", type=int, default=0,
                     help="grow the planar colony (ellipsoidal cells, learned and cold start) to this many cells "
                          "(0 skips it: tens of thousands of steps, see --only-colony)")
@@ -678,6 +735,12 @@ def main():
             mlp, _ = learned.train(feat, targ, epochs=20, batch=4096, lr=2e-3, seed=0)
         print(json.dumps(run_colony(R, torch, args.colony_cells, mlp, shapes=("ellipsoid", "spherocylinder"),
                                     seconds=args.colony_seconds)), flush=True)
+        return
+    if args.only_augmentation:
+        sc = build_scene(args.bodies, steps=args.schedule_steps)
+        stream = torch.cuda.Stream()
+        flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+        print(json.dumps(augmentation_at_scale(R, torch, sc, flush, stream)), flush=True)
         return
     if args.only_batched:
         out = run_batched(R, torch, args.batched_scenes, steps=args.batched_steps, reps=1,
@@ -774,6 +837,8 @@ def main():
                if args.batched_scenes > 0 else None)
     fresh = (learned_fresh_state(R, torch, sc, mlp_params, flush, stream)
              if (mlp_params is not None and rank == 0 and total >= 1500) else None)
+    augmentation = (augmentation_at_scale(R, torch, sc, flush, stream)
+                    if (args.augmentation and rank == 0 and total >= 1990) else None)
     colony = (run_colony(R, torch, args.colony_cells, mlp_params, seconds=args.colony_seconds)
               if (args.colony_cells > 0 and rank == 0) else None)
     refinement = None
@@ -847,6 +912,7 @@ def main():
             "learned_fresh_state": fresh,
             "batched": batched,
             "refinement": refinement,
+            "augmentation_at_scale": augmentation,
             "colony": colony,
             "stats": {"depth_max": acc["depth_max"], "depth_mean": acc["depth_sum"] / K,
                       "rows_max": acc["rows_max"], "rows_mean": acc["rows_sum"] / K, "pairs_max": acc["pairs_max"],

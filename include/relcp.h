@@ -89,7 +89,8 @@ typedef struct relcp_config {
                               seeds, whose Newton solves are cheaper than the network's fixed latency.
                               Either start converges to the same SNSD within the Newton tolerance. */
     int32_t lcp_max_iter;  /* projected-gradient iteration cap per LCP (> 0); a refined mixed solve
-                              applies it to its FP32 iterations and to its correction solve apart */
+                              applies it to its FP32 iterations and, apart, to the correction
+                              iterations of all its refinement rounds together */
     int32_t max_recursion; /* augmentation cap; 0 gives the single-constraint SNSD-LCP */
     int32_t n_scenes;      /* 1 (batched scenes are a separate entry point) */
     double dt;             /* time step (> 0) */
@@ -128,11 +129,12 @@ enum {
     RELCP_FLAG_JACOBI = 4u,        /* projected-gradient steps scaled by 1 / A_aa, BB lengths in the
                                       matching metric (same solution, fewer iterations on uneven rows) */
     RELCP_FLAG_NO_LCP_REFINE = 256u, /* mixed path: solve each LCP by FP32 iterations to lcp_tol directly.  By
-                                      default, when every row has a thread of the persistent launch, the FP32
-                                      iterations stop at 10 x lcp_tol, the residual of that iterate is taken
-                                      in FP64 and the correction is solved in FP32 to lcp_tol (iterative
-                                      refinement: the FP32 rounding then scales with the correction, not with
-                                      the contact forces, and does not stall the solve above lcp_tol) */
+                                      default the FP32 iterations hand over once below 10 x lcp_tol (after 8
+                                      more iterations) or when they stall (no 10% decrease of the residual in
+                                      128 iterations); the residual of that iterate is then taken in FP64 and
+                                      the correction solved in FP32, up to eight rounds (iterative refinement:
+                                      the FP32 rounding then scales with the correction, not with the contact
+                                      forces, and does not stall the solve above lcp_tol) */
     RELCP_FLAG_LEARNED_ALWAYS = 128u, /* with RELCP_GUESS_MLP: run the learned start on every C^k evaluation of
                                       at least one pair (by default it runs when a step evaluates 4,096 pairs
                                       or more at C^k, where its fixed cost pays) */

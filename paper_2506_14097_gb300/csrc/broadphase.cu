@@ -12,6 +12,9 @@
 //
 // The distance test is a fixed sequence of separately rounded FP64
 // operations (no contraction), so the decision is reproducible bit for bit.
+// The cached list's per-step filter takes that decision through
+// near_pair_fast: FP32 where a rounding-error bound certifies it, the FP64
+// test for the pairs within the bound of the cutoff.
 //
 // The cached Verlet list's rebuild needs only a superset of the pairs within
 // the grown cutoff (every step filters the list with the exact test), so with
@@ -238,7 +241,14 @@ __global__ void filter_kernel(int64_t nv, const int* __restrict__ vpa, const int
         L1 = Ldev[1];
         L2 = Ldev[2];
     }
-    flag[p] = near_pair(x, rb, vpa[p], vpb[p], L0, L1, L2, skin) ? 1 : 0;
+    const float Lf[3] = {trunc_f32(L0), trunc_f32(L1), trunc_f32(L2)};
+    const float iLf[3] = {Lf[0] > 0.f ? 1.f / Lf[0] : 0.f, Lf[1] > 0.f ? 1.f / Lf[1] : 0.f,
+                          Lf[2] > 0.f ? 1.f / Lf[2] : 0.f};
+    const int i = vpa[p], j = vpb[p];
+    flag[p] = near_pair_fast(x(0, i), x(1, i), x(2, i), x(0, j), x(1, j), x(2, j), rb[i], rb[j], L0, L1, L2, skin, Lf,
+                             iLf, fmaxf(Lf[0], fmaxf(Lf[1], Lf[2])), trunc_f32(skin))
+                  ? 1
+                  : 0;
 }
 
 // The cached list's exact filter, the prefix sum of its flags and the
@@ -276,10 +286,15 @@ __global__ void __launch_bounds__(kFcThreads)
             ib[k] = vpb[e];
         }
     }
+    const float Lf[3] = {trunc_f32(L0), trunc_f32(L1), trunc_f32(L2)};
+    const float iLf[3] = {Lf[0] > 0.f ? 1.f / Lf[0] : 0.f, Lf[1] > 0.f ? 1.f / Lf[1] : 0.f,
+                          Lf[2] > 0.f ? 1.f / Lf[2] : 0.f};
+    const float Lmaxf = fmaxf(Lf[0], fmaxf(Lf[1], Lf[2])), skinf = trunc_f32(skin);
 #pragma unroll
     for (int k = 0; k < kFcItems; ++k) {
         const int64_t e = base + k * kFcThreads + threadIdx.x;
-        f[k] = e < nv && near_pair(x, rb, ia[k], ib[k], L0, L1, L2, skin);
+        f[k] = e < nv && near_pair_fast(x(0, ia[k]), x(1, ia[k]), x(2, ia[k]), x(0, ib[k]), x(1, ib[k]), x(2, ib[k]),
+                                        rb[ia[k]], rb[ib[k]], L0, L1, L2, skin, Lf, iLf, Lmaxf, skinf);
         fl[k * kFcThreads + threadIdx.x] = f[k] ? 1 : 0;
     }
     __syncthreads();

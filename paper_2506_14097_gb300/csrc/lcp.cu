@@ -800,25 +800,14 @@ __device__ void scatter_1b(const KArgs<float>& a, const BodySlot<float>& S, cons
     }
 }
 
-// A double that holds a widened float (the mixed rows' A_aa) back in FP32 by
-// integer operations (the FP64 units are scarce on this part): exact for a
-// widened normal float, the truncation of the mantissa (relative < 2^-23) for
-// any other normal value in the FP32 range; outside that range a conversion.
-__device__ __forceinline__ float narrow_f32(double d) {
-    const unsigned long long b = (unsigned long long)__double_as_longlong(d);
-    const int e = (int)((b >> 52) & 0x7ffull) - 1023 + 127;
-    if (e <= 0 || e >= 255) return (float)d;
-    return __uint_as_float(((unsigned)(b >> 32) & 0x80000000u) | ((unsigned)e << 23) |
-                           (unsigned)((b >> 29) & 0x7fffffull));
-}
-
 // The termination residual of one row, |min(A_aa gamma, q + c rate)| with q,
 // A_aa and c in FP64 and gamma and the rate as the FP32 iterate holds them
 // (the FP64 test), decided from FP32 arithmetic where FP32 suffices.  The FP32
 // value r32 = |min(A32 gamma, q32 + c32 rate)| (q32 the FP32 offset) differs
 // from the FP64 one by less than e = 2^-21 max(|q32| + |c32 rate|, A32 gamma)
 // (the roundings of q, c, A_aa, the product and the sum, each at most 2^-24 or
-// 2^-23 of its operands; min and abs are 1-Lipschitz).  The loop decides
+// 2^-23 of its operands; min and abs are 1-Lipschitz; A32 is trunc_f32 of the
+// FP64 A_aa).  The loop decides
 // against two thresholds, tol and tol_a >= tol (th: tol and tol_a rounded
 // down and up to FP32).  A row whose interval [r32 - e, r32 + e] lies below
 // tol contributes r32 + e; above tol_a, r32 - e; strictly between them,
@@ -826,9 +815,9 @@ __device__ __forceinline__ float narrow_f32(double d) {
 // expression, rounded up to FP32.  The fold's max then decides "<= tol" and
 // "<= tol_a" exactly as the FP64 residuals rounded up to FP32 would, and
 // bounds the FP64 residual from above when it stops.
-__device__ __forceinline__ float resid_certified(const KArgs<float>& a, int r, float gm, float q32, float cr, float g,
-                                                 float rate, const float* th) {
-    const float p = narrow_f32(a.diag[r]) * gm;
+__device__ __forceinline__ float resid_certified(const KArgs<float>& a, int r, double dg, float gm, float q32, float cr,
+                                                 float g, float rate, const float* th) {
+    const float p = trunc_f32(dg) * gm;  // (exact: the mixed rows' A_aa is a widened float)
     const float r32 = fabsf(fminf(p, g));
     const float e = 0x1p-21f * fmaxf(fabsf(q32) + fabsf(cr), p);
     const float up = __fadd_ru(r32, e);
@@ -836,7 +825,7 @@ __device__ __forceinline__ float resid_certified(const KArgs<float>& a, int r, f
     if (up <= th[0]) return up;                       // below tol
     if (lo > th[3]) return lo;                        // above tol_a
     if (lo > th[1] && up <= th[2]) return up;         // in (tol, tol_a]
-    const double qd = a.q[r], dg = a.diag[r];
+    const double qd = a.q[r];
     return __double2float_ru(fabs(fmin(dg * (double)gm, qd + a.c * (double)rate)));
 }
 
@@ -851,13 +840,16 @@ __device__ __forceinline__ void gather_1b(const KArgs<float>& a, RowSlot<float>&
         float ui[6], uj[6];
         load_rec(ucp + 8 * (int64_t)S.i, ui);
         load_rec(ucp + 8 * (int64_t)S.j, uj);
+        // (A_aa is loaded with the velocity records: the record store below is
+        // a compiler barrier, and a load after it would be a second round trip)
+        const double dg = check ? a.diag[S.r] : 0.0;
         const float gm = proj_step(S.gm, S.gv, S.invd, alpha_r);
         const float rate = row_rate(S.g, ui, uj);
         const float cr = (float)a.c * rate;
         const float g = S.q + cr;
         st_rel64(rec + S.r, make_rec(gm, g, phase));
         bb_accumulate(a, gm - S.gm, g - S.gv, S.invd, acc);
-        if (check) res = resid_certified(a, S.r, gm, S.q, cr, g, rate, tol_lohi);
+        if (check) res = resid_certified(a, S.r, dg, gm, S.q, cr, g, rate, tol_lohi);
         S.gm = gm;
         S.gv = g;
     }
@@ -945,22 +937,68 @@ __device__ double refine_row64(const KArgs<float>& a, RowSlot<float>& S) {
     const double g64 = a.q[S.r] + a.c * rate;
     a.g64[S.r] = g64;
     const double g1 = (double)__ldcg(a.gamma_io + S.r);
-    S.q = (float)g64;
+    S.q = trunc_f32(g64);
     S.gm = 0.f;
     S.gv = S.q;
     a.gg[0][S.r] = make_float2(0.f, S.q);
     return fabs(fmin(a.diag[S.r] * g1, g64));
 }
 
+// (1b) a row beyond the row slots: g64 and its FP64 residual, the record of
+// buffer 0 = (0, g64 truncated to FP32, as for the slot rows)
+__device__ double refine_row64_mem(const KArgs<float>& a, int r) {
+    const int i = a.ia[r], j = a.ib[r];
+    double g9[9], ui[6], uj[6];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) g9[k] = (double)a.geom[k][r];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+        ui[k] = __ldcg(a.ucd[k] + i);
+        uj[k] = __ldcg(a.ucd[k] + j);
+    }
+    double rate = g9[0] * (uj[0] - ui[0]) + g9[1] * (uj[1] - ui[1]) + g9[2] * (uj[2] - ui[2]);
+    rate += g9[6] * uj[3] + g9[7] * uj[4] + g9[8] * uj[5];
+    rate -= g9[3] * ui[3] + g9[4] * ui[4] + g9[5] * ui[5];
+    const double g64 = a.q[r] + a.c * rate;
+    a.g64[r] = g64;
+    a.gg[0][r] = make_float2(0.f, trunc_f32(g64));
+    return fabs(fmin(a.diag[r] * (double)__ldcg(a.gamma_io + r), g64));
+}
+
+// (2) a row beyond the row slots: delta' (stored by the side-a body thread of
+// the scatter), g = g64 + c d^T K D delta', the BB products, the residual
+__device__ __forceinline__ void refine_gather_mem(const KArgs<float>& a, int r, int nw, int old, bool check,
+                                                  float acc[3], double& res) {
+    const int i = a.ia[r], j = a.ib[r];
+    float g9[9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) g9[k] = a.geom[k][r];
+    float ui[6], uj[6];
+    load_rec(a.ucp + 8 * (int64_t)i, ui);
+    load_rec(a.ucp + 8 * (int64_t)j, uj);
+    const double g64 = a.g64[r];
+    const float dl = __ldcg(&a.gg[nw][r].x);
+    const float2 po = __ldcg(a.gg[old] + r);
+    const float invd = a.invd ? a.invd[r] : 1.f;
+    const float rate = row_rate(g9, ui, uj);
+    const float g = trunc_f32(g64) + (float)a.c * rate;
+    a.gg[nw][r].y = g;
+    bb_accumulate(a, dl - po.x, g - po.y, invd, acc);
+    if (check)
+        res = fmax(res, fabs(fmin(a.diag[r] * ((double)__ldcg(a.gamma_io + r) + (double)dl), g64 + a.c * (double)rate)));
+}
+
 // (2) scatter: K D delta' with delta' = max(-gamma1, delta - alpha g / A_aa)
 // from the records gg[src] (every row has a row slot on this path)
 __device__ void refine_scatter(const KArgs<float>& a, const BodySlot<float>& S, int src, float alpha_r) {
     const int lane = threadIdx.x & (kLanesPerBody - 1);
+    const int nslots = gridDim.x * blockDim.x;
     auto inc = [&](int code, const float c[6], float w[6]) {
         const int r = code >> 1;
         const float2 p = __ldcg(a.gg[src] + r);
         const float inv = a.invd ? a.invd[r] : 1.f;
         const float dl = proj_step_lb(p.x, p.y, inv, alpha_r, -__ldcg(a.gamma_io + r));
+        if (!(code & 1) && r >= nslots) a.gg[1 - src][r].x = dl;  // rows beyond the row slots
 #pragma unroll
         for (int k = 0; k < 6; ++k) w[k] += dl * c[k];
     };
@@ -984,7 +1022,6 @@ __device__ void refine_scatter(const KArgs<float>& a, const BodySlot<float>& S, 
         reduce_lanes(w);
         if (S.b < a.nbodies && lane == 0) store_rec(a.ucp + 8 * (int64_t)S.b, w);
     }
-    const int nslots = gridDim.x * blockDim.x;
     const int groups_total = nslots / kLanesPerBody;
     const int gid = (blockIdx.x * blockDim.x + threadIdx.x) / kLanesPerBody;
     const int warp_first = gid & ~(32 / kLanesPerBody - 1);
@@ -1034,6 +1071,136 @@ __device__ __forceinline__ void refine_gather(const KArgs<float>& a, RowSlot<flo
     v[1] = acc[1];
     v[2] = acc[2];
     *resid = res;
+}
+
+constexpr int kRefineRounds = 8;        // FP64 residual passes per solve at most
+constexpr int kStallIters = 128;        // FP32 iterations: no 10% residual decrease in this many is a stall
+constexpr int kStallItersRefine = 256;  // the same for a correction solve
+
+// The residual history of a loop: a stall is `window` iterations in which the
+// smallest checked residual has not fallen by 10% (BB is not monotone, and a
+// near-singular LCP converges slowly without stalling; a stalled one stops
+// improving altogether).  Every thread of every block updates its own copy
+// from the same folded residuals, so all take the same decisions.
+struct StallWatch {
+    double best = 1e300;
+    int it_best = 0;
+    __device__ bool stalled(double rsd, int it, int window) {
+        if (rsd < 0.9 * best) {
+            best = rsd;
+            it_best = it;
+        }
+        return it - it_best > window;
+    }
+};
+
+// Iterative refinement of the mixed solve from the iterate in gamma_io (and
+// its velocity in ucd): up to kRefineRounds rounds of (1) the FP64 residual
+// and (2) the FP32 correction solve, which ends on tol, on a stall or when the
+// rounds' shared budget of max_iter iterations is spent; (3) gamma_io and ucd
+// then hold gamma1 + delta and U1 + K D delta, the next round's start.  resid:
+// the last residual; it: incremented by the correction iterations.  Returns
+// false when a grid barrier timed out (the caller returns from the kernel).
+#ifdef RELCP_REFINE_NOINLINE
+__device__ __noinline__
+#else
+__device__
+#endif
+bool refine_solve(const KArgs<float>& a, const BodySlot<float>& bs, RowSlot<float>& rs, int nrows,
+                             unsigned* epoch, float alpha0, unsigned long long* pbuf, double& resid, int& it) {
+    __shared__ double sh_part[kNred];
+    __shared__ double sh_res;
+    __shared__ float sh_alpha;
+    constexpr size_t kBuf = (size_t)kMaxBlocks * kNred;
+    const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+    const int stride = gridDim.x * blockDim.x;
+    unsigned long long tot[kNred];
+    int budget = a.max_iter;  // correction iterations, all rounds together
+    for (int round = 0; round < kRefineRounds && budget > 0; ++round) {
+        // (1) gamma1 is complete in gamma_io after this barrier
+        if (!grid_barrier(a.bar, epoch, a.status, a.wait_ns)) return false;
+        refine_scatter64(a);
+        if (!grid_barrier(a.bar, epoch, a.status, a.wait_ns)) return false;
+        double r64 = refine_row64(a, rs);
+        for (int r = tid + stride; r < nrows; r += stride) r64 = fmax(r64, refine_row64_mem(a, r));
+        {
+            double w4[kNred] = {0.0, 0.0, 0.0, r64};
+            block_reduce_store<double>(w4, 0x8u, sh_part);
+            if (threadIdx.x == 0) {
+                unsigned long long* o = a.partials + (size_t)blockIdx.x * kNred;
+                o[0] = to_word(0.f);
+                o[1] = to_word(0.f);
+                o[2] = to_word(0.f);
+                o[3] = to_word(sh_part[3]);
+            }
+        }
+        if (!grid_barrier(a.bar, epoch, a.status, a.wait_ns)) return false;
+        grid_reduce<float>(a.partials, 0x8u, tot);
+        resid = from_word<double>(tot[3]);
+        if (resid <= a.tol) return true;
+        // (2) the correction solve, two grid barriers per iteration; buffer 0
+        // holds its start (delta = 0, g = g64)
+        float alpha_r = alpha0;
+        if (threadIdx.x == 0) sh_alpha = alpha0;
+        int cur = 0, itc;
+        bool conv = false;
+        StallWatch sw;
+        for (itc = 1; itc <= budget; ++itc) {
+            const bool check = (itc % kMixedCheckEvery) == 0 || itc == budget;
+            unsigned long long* pc = a.partials + (size_t)(itc & 1) * kBuf;
+            refine_scatter(a, bs, cur, alpha_r);
+            if (!grid_barrier(a.bar, epoch, a.status, a.wait_ns)) return false;
+            const int npw = (int)gridDim.x * kNred;
+            unsigned pf = 0u;
+            if (itc >= 2 && (int)threadIdx.x < npw)
+                pf = __ldcg(reinterpret_cast<const unsigned*>(a.partials + (size_t)((itc - 1) & 1) * kBuf + threadIdx.x));
+            float v[3];
+            double res_t;
+            refine_gather(a, rs, 1 - cur, check, alpha_r, v, &res_t);
+            {
+                float acc[3] = {0.f, 0.f, 0.f};
+                for (int r = tid + stride; r < nrows; r += stride) refine_gather_mem(a, r, 1 - cur, cur, check, acc, res_t);
+                v[0] += acc[0];
+                v[1] += acc[1];
+                v[2] += acc[2];
+            }
+            if (itc >= 2) {
+                if ((int)threadIdx.x < npw) pbuf[threadIdx.x] = pf;
+                for (int t = threadIdx.x + kThreads; t < npw; t += kThreads)
+                    pbuf[t] = (unsigned)__ldcg(a.partials + (size_t)((itc - 1) & 1) * kBuf + t);
+            }
+            block_partials<float>(v, check ? (unsigned long long)__double_as_longlong(res_t) : 0ull,
+                                  pc + (size_t)blockIdx.x * kNred, itc >= 2 ? pbuf : nullptr, itc, &sh_alpha);
+            if (!grid_barrier(a.bar, epoch, a.status, a.wait_ns)) return false;
+            cur = 1 - cur;
+            alpha_r = sh_alpha;
+            if (check) {
+                grid_reduce<float>(pc, 0x8u, tot);
+                if (threadIdx.x == 0) sh_res = from_word<double>(tot[3]);
+                __syncthreads();
+                const double rsd = sh_res;
+                if (rsd <= a.tol) {
+                    conv = true;
+                    break;
+                }
+                if (sw.stalled(rsd, itc, kStallItersRefine)) break;
+            }
+        }
+        if (itc > budget) itc = budget;
+        it += itc;
+        budget -= itc;
+        resid = sh_res;
+        // (3) gamma = gamma1 + delta (buffer cur), Uc = U1 + K D delta
+        for (int r = tid; r < nrows; r += stride) a.gamma_io[r] = __ldcg(a.gamma_io + r) + __ldcg(&a.gg[cur][r].x);
+        for (int b = tid; b < a.nbodies; b += stride) {
+            float u[6];
+            load_rec(a.ucp + 8 * (int64_t)b, u);
+#pragma unroll
+            for (int k = 0; k < 6; ++k) a.ucd[k][b] = __ldcg(a.ucd[k] + b) + (double)u[k];
+        }
+        if (conv) return true;
+    }
+    return true;
 }
 
 template <class R>
@@ -1108,6 +1275,9 @@ __global__ void __launch_bounds__(kThreads) lcp_kernel(KArgs<R> a) {
     __syncthreads();
     R alpha_r = sh_alpha_r;
     int cur = 0, it = 0;
+    // both loops end in one call of refine_solve below (one inlined copy)
+    bool to_refine = false, done_1b = false;
+    __shared__ unsigned long long pbuf_g[kMaxBlocks * kNred];
     if constexpr (sizeof(R) == sizeof(float)) {
         if (one_bar) {
             // ---- one grid barrier per iteration (see scatter_1b), to tol, or
@@ -1115,7 +1285,7 @@ __global__ void __launch_bounds__(kThreads) lcp_kernel(KArgs<R> a) {
             int fin = 0;  // the iterate returned
             __shared__ float sh_tol[4];  // tol and tol_a, each rounded down and up to FP32
             constexpr size_t kBuf = (size_t)kMaxBlocks * kNred;
-            __shared__ unsigned long long pbuf1[kMaxBlocks * kNred];
+            unsigned long long* pbuf1 = pbuf_g;
             if (threadIdx.x == 0) {
                 sh_tol[0] = __double2float_rd(a.tol);
                 sh_tol[1] = __double2float_ru(a.tol);
@@ -1131,6 +1301,8 @@ __global__ void __launch_bounds__(kThreads) lcp_kernel(KArgs<R> a) {
                 __shared__ unsigned sh_rmax;
                 fin = -1;
                 int it_a = resid <= a.tol_a ? 0 : -1;  // the first iterate at or below tol_a
+                const bool refine = a.tol_a > a.tol;    // the FP32 iterations hand over to refine_solve
+                StallWatch sw;
                 for (it = 1; it <= a.max_iter; ++it) {
                     const bool check = (it % a.check_every) == 0 || it == a.max_iter;
                     const bool prev_check = it >= 2 && ((it - 1) % a.check_every) == 0;
@@ -1171,10 +1343,12 @@ __global__ void __launch_bounds__(kThreads) lcp_kernel(KArgs<R> a) {
                         // Below tol_a the iterations go on towards tol for up to
                         // kRefineWait more; only a solve still above tol then is
                         // refined (a light solve usually gets there first, and
-                        // the refinement's FP64 pass would cost it more)
+                        // the refinement's FP64 pass would cost it more).  A
+                        // stall hands over at once.
                         const double rsd = (double)__uint_as_float(sh_rmax);
                         if (rsd <= a.tol_a && it_a < 0) it_a = it - 1;
-                        if (rsd <= a.tol || (it_a >= 0 && it - 1 >= it_a + kRefineWait)) {
+                        const bool stall = refine && sw.stalled(rsd, it - 1, kStallIters);
+                        if (rsd <= a.tol || (refine && it_a >= 0 && it - 1 >= it_a + kRefineWait) || stall) {
                             resid = rsd;
                             fin = it - 1;
                             break;
@@ -1209,94 +1383,22 @@ __global__ void __launch_bounds__(kThreads) lcp_kernel(KArgs<R> a) {
 #pragma unroll
                 for (int k = 0; k < 6; ++k) a.ucd[k][b] = (double)u[k];
             }
-            if (a.tol_a > a.tol && !(resid <= a.tol)) {
-                // ---- iterative refinement (see refine_scatter64): the FP64
-                // residual of gamma1 = the iterate just written
-                if (!grid_barrier(a.bar, &epoch, a.status, a.wait_ns)) return;
-                refine_scatter64(a);
-                if (!grid_barrier(a.bar, &epoch, a.status, a.wait_ns)) return;
-                {
-                    const double r64 = refine_row64(a, rs);
-                    double w4[kNred] = {0.0, 0.0, 0.0, r64};
-                    block_reduce_store<double>(w4, 0x8u, part);
-                    if (threadIdx.x == 0) {
-                        unsigned long long* o = a.partials + (size_t)blockIdx.x * kNred;
-                        o[0] = to_word(R(0));
-                        o[1] = to_word(R(0));
-                        o[2] = to_word(R(0));
-                        o[3] = to_word(part[3]);
-                    }
-                }
-                if (!grid_barrier(a.bar, &epoch, a.status, a.wait_ns)) return;
-                grid_reduce<R>(a.partials, 0x8u, tot);
-                resid = from_word<double>(tot[3]);
-                if (!(resid <= a.tol)) {
-                    // the correction solve, two grid barriers per iteration;
-                    // buffer 0 holds its start (delta = 0, g = g64)
-                    alpha_r = sh_alpha0;
-                    cur = 0;
-                    int itc;
-                    for (itc = 1; itc <= a.max_iter; ++itc) {
-                        const bool check = (itc % kMixedCheckEvery) == 0 || itc == a.max_iter;
-                        unsigned long long* pc = a.partials + (size_t)(itc & 1) * kBuf;
-                        refine_scatter(a, bs, cur, alpha_r);
-                        if (!grid_barrier(a.bar, &epoch, a.status, a.wait_ns)) return;
-                        const int npw = (int)gridDim.x * kNred;
-                        unsigned pf = 0u;
-                        if (itc >= 2 && (int)threadIdx.x < npw)
-                            pf = __ldcg(reinterpret_cast<const unsigned*>(a.partials + (size_t)((itc - 1) & 1) * kBuf +
-                                                                          threadIdx.x));
-                        refine_gather(a, rs, 1 - cur, check, alpha_r, v, &res_t);
-                        if (itc >= 2) {
-                            if ((int)threadIdx.x < npw) pbuf1[threadIdx.x] = pf;
-                            for (int t = threadIdx.x + kThreads; t < npw; t += kThreads)
-                                pbuf1[t] = (unsigned)__ldcg(a.partials + (size_t)((itc - 1) & 1) * kBuf + t);
-                        }
-                        block_partials<R>(v, check ? (unsigned long long)__double_as_longlong(res_t) : 0ull,
-                                          pc + (size_t)blockIdx.x * kNred, itc >= 2 ? pbuf1 : nullptr, itc, &sh_alpha_r);
-                        if (!grid_barrier(a.bar, &epoch, a.status, a.wait_ns)) return;
-                        cur = 1 - cur;
-                        alpha_r = sh_alpha_r;
-                        if (check) {
-                            grid_reduce<R>(pc, 0x8u, tot);
-                            if (threadIdx.x == 0) {
-                                sh_resid = from_word<double>(tot[3]);
-                                sh_stop = sh_resid <= a.tol;
-                            }
-                            __syncthreads();
-                            if (sh_stop) break;
-                        }
-                    }
-                    if (itc > a.max_iter) itc = a.max_iter;
-                    it += itc;
-                    resid = sh_resid;
-                    // gamma = gamma1 + delta (buffer cur), Uc = U1 + K D delta
-                    for (int r = tid; r < nrows; r += stride)
-                        a.gamma_io[r] = __ldcg(a.gamma_io + r) + __ldcg(&a.gg[cur][r].x);
-                    for (int b = tid; b < a.nbodies; b += stride) {
-                        R u[6];
-                        load_rec(a.ucp + 8 * (int64_t)b, u);
-#pragma unroll
-                        for (int k = 0; k < 6; ++k) a.ucd[k][b] = __ldcg(a.ucd[k] + b) + (double)u[k];
-                    }
-                }
-            }
-            pdl_trigger();  // the next kernel in the stream may start launching
-            if (blockIdx.x == 0 && threadIdx.x == 0) {
-                a.result->iterations = (double)it;
-                a.result->residual = resid;
-                if (!(resid <= a.tol)) atomicOr(a.status, DEV_LCP_NOT_CONVERGED);
-            }
-            return;
+            done_1b = true;
         }
     }
+    if (!done_1b) {
     if (!sh_stop) {
 #ifdef RELCP_LCP_TRACE
         unsigned long long t_prev = gtimer();
 #endif
         constexpr bool kRetard = sizeof(R) == sizeof(float);
         constexpr size_t kBuf = (size_t)kMaxBlocks * kNred;
-        __shared__ unsigned long long pbuf[kMaxBlocks * kNred];
+        unsigned long long* pbuf = pbuf_g;
+        // mixed path: hand over to refine_solve below tol_a (after kRefineWait
+        // more iterations) or on a stall, as the one-barrier loop does
+        const bool refine = kRetard && a.tol_a > a.tol;
+        int it_a = sh_resid <= a.tol_a ? 0 : -1;
+        StallWatch sw;
         for (it = 1; it <= a.max_iter; ++it) {
             // all blocks have read partials before any block rewrites them:
             // the barrier after phase 1 separates the reads from the writes
@@ -1352,11 +1454,18 @@ __global__ void __launch_bounds__(kThreads) lcp_kernel(KArgs<R> a) {
             if (blockIdx.x == 0 && threadIdx.x == 0) g_lcp_trace[6] += 1;
 #endif
             if (sh_stop) break;
+            if (refine && check) {
+                const double rsd = sh_resid;
+                if (rsd <= a.tol_a && it_a < 0) it_a = it;
+                if ((it_a >= 0 && it >= it_a + kRefineWait) || sw.stalled(rsd, it, kStallIters)) {
+                    to_refine = true;
+                    break;
+                }
+            }
         }
         if (it > a.max_iter) it = a.max_iter;
     }
     resid = sh_resid;
-    pdl_trigger();  // the next kernel in the stream may start launching
     // outputs: gamma of the last iterate (buffer cur) and the contact velocity
     // in double; every write of the last iteration happened before the last
     // grid barrier
@@ -1367,6 +1476,15 @@ __global__ void __launch_bounds__(kThreads) lcp_kernel(KArgs<R> a) {
 #pragma unroll
         for (int k = 0; k < 6; ++k) a.ucd[k][b] = (double)u[k];
     }
+    }
+    if constexpr (sizeof(R) == sizeof(float)) {
+        // ---- iterative refinement of either loop's result (see refine_solve);
+        // a solve that reached max_iter above tol hands over too
+        if ((to_refine || (a.tol_a > a.tol && !(resid <= a.tol))) &&
+            !refine_solve(a, bs, rs, nrows, &epoch, sh_alpha0, pbuf_g, resid, it))
+            return;
+    }
+    pdl_trigger();  // the next kernel in the stream may start launching
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         a.result->iterations = (double)it;
         a.result->residual = resid;

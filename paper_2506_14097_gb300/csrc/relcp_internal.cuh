@@ -185,6 +185,46 @@ __device__ __forceinline__ bool near_pair_exact(double xi0, double xi1, double x
     return d2 <= __dmul_rn(s, s);
 }
 
+// A double truncated to FP32 by integer operations (FP64 conversions issue at
+// the FP64 rate on this part): relative error below 2^-23 for a normal value in
+// the FP32 range, exact for a widened float; other values by conversion.
+__device__ __forceinline__ float trunc_f32(double d) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(d);
+    const int e = (int)((b >> 52) & 0x7ffull) - 1023 + 127;
+    if (e <= 0 || e >= 255) return (float)d;
+    return __uint_as_float(((unsigned)(b >> 32) & 0x80000000u) | ((unsigned)e << 23) |
+                           (unsigned)((b >> 29) & 0x7fffffull));
+}
+
+// near_pair_exact's decision, taken in FP32 where a rounding-error bound
+// certifies it.  From the positions and radii truncated to FP32 (relative
+// error < 2^-23 each), the per-axis difference, minimum image (the FP32 image
+// may differ from the FP64 one only where |d| is near L/2, and the distance
+// is continuous across that switch) and the sum of squares give a distance
+// within 2^-22 (|x_i| + |x_j| + L) per axis of the FP64 one, and the radius sum
+// within 2^-22 s.  m = 2^-19 (max |x_i| + max |x_j| + max L + s) exceeds the
+// distance error more than fourfold: a pair further than s + m is out, one
+// nearer than s - m is in, and only the pairs in between take the FP64 test.
+__device__ __forceinline__ bool near_pair_fast(double xi0, double xi1, double xi2, double xj0, double xj1, double xj2,
+                                               double rbi, double rbj, double L0, double L1, double L2, double skin,
+                                               const float* Lf, const float* iLf, float Lmaxf, float skinf) {
+    const float a0 = trunc_f32(xi0), a1 = trunc_f32(xi1), a2 = trunc_f32(xi2);
+    const float b0 = trunc_f32(xj0), b1 = trunc_f32(xj1), b2 = trunc_f32(xj2);
+    float d0 = b0 - a0, d1 = b1 - a1, d2 = b2 - a2;
+    if (Lf[0] > 0.f) d0 -= Lf[0] * rintf(d0 * iLf[0]);
+    if (Lf[1] > 0.f) d1 -= Lf[1] * rintf(d1 * iLf[1]);
+    if (Lf[2] > 0.f) d2 -= Lf[2] * rintf(d2 * iLf[2]);
+    const float dd = d0 * d0 + d1 * d1 + d2 * d2;
+    const float sf = trunc_f32(rbi) + trunc_f32(rbj) + skinf;
+    const float A = fmaxf(fabsf(a0), fmaxf(fabsf(a1), fabsf(a2))) + fmaxf(fabsf(b0), fmaxf(fabsf(b1), fabsf(b2)));
+    const float m = 0x1p-19f * (A + Lmaxf + sf);
+    const float hi = sf + m;
+    if (dd > hi * hi) return false;
+    const float lo = sf - m;
+    if (lo > 0.f && dd < lo * lo) return true;
+    return near_pair_exact(xi0, xi1, xi2, xj0, xj1, xj2, rbi, rbj, L0, L1, L2, skin);
+}
+
 // ---------------------------------------------------------------------------
 // programmatic dependent launch: a kernel launched with launch_pdl may start
 // while the previous kernel in the stream drains (its launch overlaps that
