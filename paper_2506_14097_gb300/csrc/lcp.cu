@@ -1101,12 +1101,7 @@ struct StallWatch {
 // then hold gamma1 + delta and U1 + K D delta, the next round's start.  resid:
 // the last residual; it: incremented by the correction iterations.  Returns
 // false when a grid barrier timed out (the caller returns from the kernel).
-#ifdef RELCP_REFINE_NOINLINE
-__device__ __noinline__
-#else
-__device__
-#endif
-bool refine_solve(const KArgs<float>& a, const BodySlot<float>& bs, RowSlot<float>& rs, int nrows,
+__device__ bool refine_solve(const KArgs<float>& a, const BodySlot<float>& bs, RowSlot<float>& rs, int nrows,
                              unsigned* epoch, float alpha0, unsigned long long* pbuf, double& resid, int& it) {
     __shared__ double sh_part[kNred];
     __shared__ double sh_res;
@@ -1302,7 +1297,18 @@ __global__ void __launch_bounds__(kThreads) lcp_kernel(KArgs<R> a) {
                 fin = -1;
                 int it_a = resid <= a.tol_a ? 0 : -1;  // the first iterate at or below tol_a
                 const bool refine = a.tol_a > a.tol;    // the FP32 iterations hand over to refine_solve
-                StallWatch sw;
+                // the stall watch, block-uniform in shared memory (no per-thread
+                // registers in this loop): thread 0 updates it at check k and
+                // writes its verdict to slot (k + 1) & 1, which every thread reads
+                // at check k + 1, after the barriers in between
+                __shared__ double sh_best;
+                __shared__ int sh_itbest, sh_stall[2];
+                if (threadIdx.x == 0) {
+                    sh_best = 1e300;
+                    sh_itbest = 0;
+                    sh_stall[0] = sh_stall[1] = 0;
+                }
+                int ncheck = 0;
                 for (it = 1; it <= a.max_iter; ++it) {
                     const bool check = (it % a.check_every) == 0 || it == a.max_iter;
                     const bool prev_check = it >= 2 && ((it - 1) % a.check_every) == 0;
@@ -1347,7 +1353,15 @@ __global__ void __launch_bounds__(kThreads) lcp_kernel(KArgs<R> a) {
                         // stall hands over at once.
                         const double rsd = (double)__uint_as_float(sh_rmax);
                         if (rsd <= a.tol_a && it_a < 0) it_a = it - 1;
-                        const bool stall = refine && sw.stalled(rsd, it - 1, kStallIters);
+                        const bool stall = refine && sh_stall[ncheck & 1];
+                        if (threadIdx.x == 0) {
+                            if (rsd < 0.9 * sh_best) {
+                                sh_best = rsd;
+                                sh_itbest = it - 1;
+                            }
+                            sh_stall[(ncheck + 1) & 1] = it - 1 - sh_itbest > kStallIters;
+                        }
+                        ++ncheck;
                         if (rsd <= a.tol || (refine && it_a >= 0 && it - 1 >= it_a + kRefineWait) || stall) {
                             resid = rsd;
                             fin = it - 1;
