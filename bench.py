@@ -39,7 +39,7 @@ WORKLOAD = "compacting ellipsoid suspension, 32768 bodies, phi 0.1->0.55 over 20
 SCHEDULE_STEPS = 2000
 # DRAM bytes (read + write) of one lcp_kernel launch at the dense end of the
 # schedule, from the ncu capture summarised in profiles/
-LCP_DRAM_BYTES_PER_LAUNCH = 12.80e6
+LCP_DRAM_BYTES_PER_LAUNCH = 12.69e6
 
 
 def timed_indices(total: int, k: int) -> list:
@@ -897,7 +897,7 @@ def main():
                          "achieved": lcp_gbs, "peak": hbm, "unit": "GB/s", "frac": lcp_gbs / hbm,
                          "traffic": LCP_DRAM_BYTES_PER_LAUNCH,
                          "traffic_note": "dram__bytes_read.sum + dram__bytes_write.sum of the dense-end launch "
-                                         "(schedule step 1950, 105 iterations; 6.04 MB at step 1050): "
+                                         "(schedule step 1950, 103 iterations; 6.02 MB at step 1050): "
                                          "profiles/lcp_kernel_traffic_compaction32k.md",
                          "peak_kind": peak_kind, "launches": acc["lcp_launches"],
                          "kernel_ms_total": acc["lcp_ms"],
