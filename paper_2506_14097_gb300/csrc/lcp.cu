@@ -58,7 +58,10 @@ namespace {
 constexpr int kThreads = RELCP_LCP_THREADS;
 constexpr int kMaxCtasPerSm = 1;
 constexpr int kMixedCheckEvery = 2;  // mixed path: FP64 termination residual every 2nd iteration
-constexpr int kRefineWait = 8;       // one-barrier path: iterations past tol_a before the refinement
+#ifndef RELCP_REFINE_WAIT
+#define RELCP_REFINE_WAIT 8
+#endif
+constexpr int kRefineWait = RELCP_REFINE_WAIT;  // iterations past tol_a before the refinement
 
 __device__ __forceinline__ unsigned long long gtimer() {
     unsigned long long t;

@@ -443,7 +443,10 @@ struct LcpProblem {
     // an FP64 residual, an FP32 correction solve to tol); 0 turns it off
     int refine = 1;
 };
-constexpr double kRefineFactor = 10.0;
+#ifndef RELCP_REFINE_FACTOR
+#define RELCP_REFINE_FACTOR 10.0
+#endif
+constexpr double kRefineFactor = RELCP_REFINE_FACTOR;
 constexpr unsigned long long kLcpWaitNs = 2000000000ull;  // 2 s
 constexpr unsigned long long kFaultWaitNs = 2000000ull;   // 2 ms (RELCP_FAULT_LCP_TIMEOUT)
 // lcp_solve in two parts: the body incidence CSR of the rows, then the
