@@ -1,4 +1,4 @@
-"""Training driver of the learned SNSD guess: orchestration only.
+"""Training loop of the learned SNSD guess: orchestration only.
 
 harvest() collects (features, target) pairs that the method itself produces:
 candidate pairs of simulation states, their FP64 SNSD solutions (shared normal

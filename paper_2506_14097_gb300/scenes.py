@@ -242,7 +242,7 @@ class Colony:
     Cell i has length L_i and semi-axes (L_i/2, 0.5, 0.5), its long axis the
     body x axis, in the plane.  Each cell draws its growth rate once, at birth,
     from N(rate, rate_sd) (length per unit time).  After every time step the
-    driver advances L_i by rate_i dt; a cell that reaches L_div divides along
+    host loop advances L_i by rate_i dt; a cell that reaches L_div divides along
     its axis into two daughters of length L_i / 2 centred at c +- (L_i / 4) e,
     each turned by its own N(0, jitter) angle.  All random numbers come from
     the colony's own seeded generator, so a colony is a pure function of its

@@ -9,7 +9,7 @@ opposite unit forces, overdamped local drag (Eq. ellipsoid_mobility, xi = 1),
 overlap tolerance 1e-5.  The sweep runs each time step as a one-scene batch
 (the whole step loop of a launch stays on the device, which is what makes the
 4 x 10^6 steps of dt = 1e-5 affordable) and samples the state every `sample`
-time units.  With max_recursion = 0 the same driver runs LCP-SNSD, the
+time units.  With max_recursion = 0 the same study runs LCP-SNSD, the
 single-constraint formulation the recursion reduces to.
 """
 from __future__ import annotations
@@ -116,7 +116,7 @@ def colony_run(target_cells: int, shape: int = R.RELCP_SHAPE_ELLIPSOID, guess: i
     """Grow a colony (scenes.Colony: rate N(0.01, 0.001) per cell, division
     at L = 2 with N(0, 0.05) rad jitter, dt = 0.05, planar overdamped
     dynamics) from one cell until it holds `target_cells` cells (or
-    `max_seconds` pass), the GPU stepping it and the driver growing and
+    `max_seconds` pass), the GPU stepping it and the host loop growing and
     dividing the cells between steps (every step hands the library the new
     bodies); steps whose LCP hit its iteration cap or whose recursion hit its
     cap are counted and the run goes on.  Returns the steps, the

@@ -9,7 +9,7 @@ colony (Sec. 5.4 restated with ellipsoidal cells in the z = 0 plane):
 * a colony grown through several divisions stays in the plane exactly
   (z = 0, rotations about z only), meets the stopping rule every step, and its
   recursion invariants hold;
-* the colony driver is deterministic in its seed.
+* the colony model is deterministic in its seed.
 """
 import numpy as np
 
@@ -93,7 +93,7 @@ def test_colony_stays_planar_and_meets_the_stopping_rule(orc):
     assert col.n >= 12 and col.divisions >= 11 and seen["rows"] > 100
 
 
-def test_colony_driver_deterministic():
+def test_colony_model_deterministic():
     a, b = scenes.Colony(seed=9, rate=0.05), scenes.Colony(seed=9, rate=0.05)
     for _ in range(500):
         a.advance(a.x + 0.001, a.q())
