@@ -81,3 +81,40 @@ def test_product_path_does_not_import_oracle():
     for f in glob.glob(os.path.join(pkg, "**", "*"), recursive=True):
         if f.endswith((".py", ".cu", ".cuh", ".h")):
             assert not pat.search(open(f).read()), f
+
+
+def test_enum_constants_match_binding():
+    """Every RELCP_* enumerator of include/relcp.h has the same value in the
+    Python binding (a flag or status added to one side only fails here)."""
+    from paper_2506_14097_gb300 import relcp as R
+
+    src = open(os.path.join(ROOT, "include", "relcp.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    found = 0
+    for name, val in re.findall(r"\b(RELCP_[A-Z0-9_]+)\s*=\s*(\d+)u?\b", src):
+        if hasattr(R, name):
+            assert getattr(R, name) == int(val), name
+            found += 1
+    assert found >= 25
+    assert R.RELCP_FLAG_NO_LCP_REFINE == 256
+
+
+def test_default_lcp_stops():
+    """make_config's LCP stop in units of the length scale: 1e-12 on the FP64
+    path; on the mixed path 1e-8 for the overdamped laws (the contact velocity
+    is the whole non-affine motion of a compaction) and 1e-7 under inertia; an
+    explicit lcp_tol is kept."""
+    from paper_2506_14097_gb300 import relcp as R
+
+    a = 0.4
+    cases = [(R.RELCP_FP64, R.RELCP_OVERDAMPED, 1e-12), (R.RELCP_FP64, R.RELCP_INERTIAL, 1e-12),
+             (R.RELCP_MIXED, R.RELCP_OVERDAMPED, 1e-8), (R.RELCP_MIXED, R.RELCP_OVERDAMPED_2D, 1e-8),
+             (R.RELCP_MIXED, R.RELCP_INERTIAL, 1e-7)]
+    for prec, dyn, k in cases:
+        c = R.make_config(dynamics=dyn, precision=prec, eps_ncp=1e-3 * a, length_scale=a)
+        assert abs(c.lcp_tol - k * a) <= 1e-15 * k * a, (prec, dyn, c.lcp_tol)
+    c = R.make_config(dynamics=R.RELCP_OVERDAMPED, precision=R.RELCP_MIXED, eps_ncp=1e-3 * a, lcp_tol=3e-9)
+    assert c.lcp_tol == 3e-9
+    # without a length scale the smallest semi-axis is read off eps_ncp = 1e-3 a_min
+    c = R.make_config(dynamics=R.RELCP_OVERDAMPED, precision=R.RELCP_MIXED, eps_ncp=1e-3 * a)
+    assert abs(c.lcp_tol - 1e-8 * a) <= 1e-20
