@@ -554,7 +554,7 @@ int orc_lemke(int n, const double* M, const double* q, double* z, double* w, int
     if (status == 0) {
         /* re-solve the final basis from the original data: B xB = q, with
          * column j of B = e_j for basic w_j and -M[:, j] for basic z_j. */
-        double* B = malloc(sizeof(double) * (size_t)n * n);
+        double* B = calloc((size_t)n * n, sizeof(double));
         double* xb = malloc(sizeof(double) * n);
         double* B0 = malloc(sizeof(double) * (size_t)n * n);
         for (int i = 0; i < n; ++i)
