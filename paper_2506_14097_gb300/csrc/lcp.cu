@@ -35,6 +35,13 @@
 // (resid_certified): the same stop decisions at a fraction of the FP64 issue
 // slots, which this part has few of.
 //
+// On the mixed path both loops hand over to an iterative refinement inside the
+// launch (refine_solve): once the FP32 iterations are below 10 x tol and a few
+// more have not reached tol, or when they stall, the residual of the iterate
+// is taken in FP64 and the correction solved in FP32 (up to eight rounds), so
+// the FP32 rounding of the nearly cancelling contact forces no longer bounds
+// the attainable residual.
+//
 // The grid barrier spins a bounded number of times; a timeout sets
 // DEV_TIMEOUT and the kernel returns.  Data written inside the launch is read
 // with ld.global.cg or ld.relaxed.gpu (L2), never from a possibly stale L1
@@ -54,7 +61,8 @@ namespace {
 #define RELCP_LCP_INC_PER_LANE 5
 #endif
 // 640 threads leave 96 registers per thread at one CTA per SM: the row and
-// body slots and the 10 register-resident incidences per body fit unspilled
+// body slots and the 10 register-resident incidences per body fit (the
+// refinement's code adds a few spilled words outside the hot loop)
 constexpr int kThreads = RELCP_LCP_THREADS;
 constexpr int kMaxCtasPerSm = 1;
 constexpr int kMixedCheckEvery = 2;  // mixed path: FP64 termination residual every 2nd iteration
